@@ -1,0 +1,271 @@
+"""Pins for the CPU oracle: closed forms, brute force and invariants.
+
+Each test ties an oracle function to something other than itself, chosen so
+that a plausible slip (dropped term, wrong sign or index, transposed operand)
+fails at least one of them.  CPU only.
+"""
+import itertools
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+from oracle import dd, fem, solvers
+from workloads import random_rhs
+
+RNG = np.random.default_rng(12345)
+
+
+# --------------------------- double-double ---------------------------------
+
+def test_dd_two_prod_and_two_sum_are_exact():
+    """Dekker/Knuth transformations: p + e == a*b and s + e == a + b exactly
+    (checked in rational arithmetic)."""
+    a = RNG.standard_normal(200) * 10.0 ** RNG.integers(-8, 8, 200)
+    b = RNG.standard_normal(200) * 10.0 ** RNG.integers(-8, 8, 200)
+    p, e = dd.two_prod(a, b)
+    s, t = dd.two_sum(a, b)
+    for i in range(200):
+        assert Fraction(p[i]) + Fraction(e[i]) == Fraction(a[i]) * Fraction(b[i])
+        assert Fraction(s[i]) + Fraction(t[i]) == Fraction(a[i]) + Fraction(b[i])
+
+
+def test_residual_dd_matches_rational_arithmetic():
+    """f - A u in double-double equals the exact rational residual of the
+    operator with the same double entries, to ~1e-30 relative."""
+    shape, h, om = (4, 5), (0.31, 0.27), 3.7
+    u = random_rhs(shape, 1)
+    f = fem.apply_A(u, h, om) + 1e-12 * random_rhs(shape, 2)
+    r = fem.residual_dd(f, u, h, om)
+    # exact: build 1D matrices in Fractions with the same double entries
+    def mats(n, hh, kind):
+        sub, diag, sup = fem._tri_coeffs(n, hh, om, kind)
+        M = [[(Fraction(0), Fraction(0)) for _ in range(n)] for _ in range(n)]
+        for j in range(n):
+            M[j][j] = (Fraction(diag[j].real), Fraction(diag[j].imag))
+            if j > 0:
+                M[j][j - 1] = (Fraction(sub[j].real), Fraction(sub[j].imag))
+            if j < n - 1:
+                M[j][j + 1] = (Fraction(sup[j].real), Fraction(sup[j].imag))
+        return M
+
+    def cmul(a, b):
+        return (a[0] * b[0] - a[1] * b[1], a[0] * b[1] + a[1] * b[0])
+
+    def apply(M, X, axis):
+        n0, n1 = len(X), len(X[0])
+        Y = [[(Fraction(0), Fraction(0)) for _ in range(n1)] for _ in range(n0)]
+        for i in range(n0):
+            for j in range(n1):
+                acc = (Fraction(0), Fraction(0))
+                for k in range(n0 if axis == 0 else n1):
+                    m = M[i][k] if axis == 0 else M[j][k]
+                    x = X[k][j] if axis == 0 else X[i][k]
+                    if m != (0, 0):
+                        t = cmul(m, x)
+                        acc = (acc[0] + t[0], acc[1] + t[1])
+                Y[i][j] = acc
+        return Y
+
+    U = [[(Fraction(u[i, j].real), Fraction(u[i, j].imag)) for j in range(shape[1])] for i in range(shape[0])]
+    Kx, Mx = mats(shape[0], h[0], "K"), mats(shape[0], h[0], "M")
+    Ky, My = mats(shape[1], h[1], "K"), mats(shape[1], h[1], "M")
+    t1 = apply(Kx, apply(My, U, 1), 0)
+    t2 = apply(Mx, apply(Ky, U, 1), 0)
+    t3 = apply(Mx, apply(My, U, 1), 0)
+    w2 = Fraction(-om ** 2)
+    for i in range(shape[0]):
+        for j in range(shape[1]):
+            ex_re = Fraction(f[i, j].real) - (t1[i][j][0] + t2[i][j][0] + w2 * t3[i][j][0])
+            ex_im = Fraction(f[i, j].imag) - (t1[i][j][1] + t2[i][j][1] + w2 * t3[i][j][1])
+            assert abs(float(ex_re) - r[i, j].real) <= 1e-26 + 1e-15 * abs(float(ex_re))
+            assert abs(float(ex_im) - r[i, j].imag) <= 1e-26 + 1e-15 * abs(float(ex_im))
+
+
+# --------------------------- 1D matrices -------------------------------------
+
+def test_1d_matrices_match_element_assembly():
+    """eqs. matrixK / matrixM are the 1D element assembly of the weak form
+    (including the -i w boundary term at both ends)."""
+    n, h, om = 7, 0.2, 3.0
+    A1 = fem.assemble((n,), (h,), om).toarray()
+    K, M = fem.K1d(n, h, om), fem.M1d(n, h)
+    np.testing.assert_allclose(A1, K - om ** 2 * M, atol=1e-13)
+    # hand values of the paper's stencils
+    assert K[0, 0] == pytest.approx((1 - 1j * om * h) / h)
+    assert K[3, 3] == pytest.approx(2 / h) and K[3, 4] == pytest.approx(-1 / h)
+    assert M[0, 0] == pytest.approx(2 * h / 6) and M[3, 3] == pytest.approx(4 * h / 6)
+    assert M[3, 2] == pytest.approx(h / 6)
+
+
+@pytest.mark.parametrize("shape,h", [((6, 5), (0.2, 0.3)), ((4, 5, 3), (0.5, 0.25, 0.4)),
+                                     ((9, 2), (0.125, 1.0))])
+@pytest.mark.parametrize("bc", ["abc", "neumann"])
+def test_element_assembly_equals_kronecker_form(shape, h, bc):
+    """Element-by-element assembly by quadrature == eq. A2D / A3D."""
+    om = 4.1
+    A1 = fem.assemble(shape, h, om, bc)
+    A2 = fem.kron_operator(shape, h, om, bc=bc)
+    assert abs(A1 - A2).max() < 1e-12 * abs(A2).max()
+
+
+def test_operator_is_complex_symmetric_not_hermitian():
+    A = fem.assemble((5, 6), (0.25, 0.2), 5.0)
+    assert abs(A - A.T).max() == 0 or abs(A - A.T).max() < 1e-15
+    assert abs(A - A.conj().T).max() > 1.0  # the -i w boundary term
+
+
+def test_apply_A_matches_assembled_matrix():
+    shape, h, om = (5, 4, 6), (0.3, 0.2, 0.25), 2.5
+    u = random_rhs(shape, 3)
+    A = fem.assemble(shape, h, om)
+    np.testing.assert_allclose(fem.apply_A(u, h, om).ravel(), A @ u.ravel(), rtol=0, atol=1e-12)
+
+
+# --------------------------- closed-form eigenvalues -------------------------
+
+@pytest.mark.parametrize("n,h", [(9, 0.125), (33, 1 / 32), (16, 0.07)])
+def test_neumann_and_dirichlet_closed_forms(n, h):
+    """Linear-FEM eigenvalues 6/h^2 (1 - cos t)/(2 + cos t): Neumann with
+    t = k pi/(n-1), Dirichlet (interior block) with t = k pi h / L."""
+    K = fem.K1d(n, h, 0.0, bc="neumann").real
+    M = fem.M1d(n, h)
+    ev = np.sort(sl.eigh(K, M, eigvals_only=True))
+    np.testing.assert_allclose(ev, np.sort(fem.eig_neumann(n, h)), rtol=1e-10, atol=1e-9)
+    evd = np.sort(sl.eigh(K[1:-1, 1:-1], M[1:-1, 1:-1], eigvals_only=True))
+    np.testing.assert_allclose(evd, np.sort(fem.eig_dirichlet(n, h)), rtol=1e-10)
+
+
+@pytest.mark.parametrize("n,h", [(8, 0.1), (9, 1 / 8), (31, 0.03)])
+def test_periodic_pencil_eigenvalues_and_dft_diagonalisation(n, h):
+    """eq. eigvaluesPer equals the closed form, and the DFT matrix of eq.
+    eigvectorsPer diagonalises the circulant K^B, M^B (eqs. matrixKper/Mper)."""
+    lam = fem.eig_periodic(n, h)
+    np.testing.assert_allclose(lam, fem.eig_periodic_closed(n, h), rtol=1e-12, atol=1e-9)
+    KB, MB = fem.K1d_periodic(n, h), fem.M1d_periodic(n, h)
+    F = np.exp(-2j * np.pi * np.outer(np.arange(n), np.arange(n)) / n)
+    Fi = np.conj(F) / n
+    DK = F @ KB @ Fi
+    DM = F @ MB @ Fi
+    assert np.abs(DK - np.diag(np.diag(DK))).max() < 1e-10 / h
+    assert np.abs(DM - np.diag(np.diag(DM))).max() < 1e-12
+    np.testing.assert_allclose(np.diag(DK).real / np.diag(DM).real, lam, rtol=1e-10, atol=1e-8)
+    # the paper's FFT convention (eq. step1FFTfcoeff) is numpy's forward FFT
+    x = random_rhs((n,), 4)
+    naive = np.array([sum(np.exp(-2j * np.pi * l * k / n) * x[l] for l in range(n)) for k in range(n)])
+    np.testing.assert_allclose(np.fft.fft(x), naive, rtol=1e-12, atol=1e-12)
+
+
+def test_abc_pencil_eigenpairs():
+    """eq. EVP1a with eq. EVPcondA: K V = M V Lam, V^T M V = I, V^T K V = Lam;
+    and the w -> 0 limit reduces to the Neumann closed form."""
+    n, h = 41, 1 / 40
+    om = 2 * np.pi / (10 * h)
+    lam, V = solvers.abc_pencil_eig(n, h, om)
+    K, M = fem.K1d(n, h, om), fem.M1d(n, h)
+    assert np.abs(K @ V - M @ V * lam[None, :]).max() < 1e-9 * np.abs(K).max()
+    assert np.abs(V.T @ M @ V - np.eye(n)).max() < 1e-10
+    assert np.abs(V.T @ K @ V - np.diag(lam)).max() < 1e-9 * np.abs(lam).max()
+    # absorbing: every eigenvalue is pushed into the lower half plane
+    assert np.all(lam.imag < 0)
+    lam0, _ = solvers.abc_pencil_eig(n, h, 1e-9)
+    np.testing.assert_allclose(np.sort(lam0.real), np.sort(fem.eig_neumann(n, h)), rtol=1e-8, atol=1e-6)
+
+
+# --------------------------- solvers -----------------------------------------
+
+@pytest.mark.parametrize("shape,h,om", [((7, 9), (1 / 6, 1 / 8), 9.0),
+                                         ((5, 6, 4), (0.25, 0.2, 1 / 3), 6.0),
+                                         ((12, 3), (0.1, 0.4), 15.0)])
+def test_banded_and_tensor_agree_with_dense_lu(shape, h, om):
+    f = random_rhs(shape, 7)
+    u0 = solvers.solve_dense(f, h, om)
+    u1 = solvers.solve_banded_lu(f, h, om)
+    u2 = solvers.TensorSolver(shape, h, om).solve(f)
+    n0 = np.linalg.norm(u0)
+    assert np.linalg.norm(u1 - u0) / n0 < 1e-12
+    assert np.linalg.norm(u2 - u0) / n0 < 1e-11
+    # tensor solver with every choice of the tridiagonal axis
+    for t in range(len(shape)):
+        u3 = solvers.TensorSolver(shape, h, om, tri_axis=t).solve(f)
+        assert np.linalg.norm(u3 - u0) / n0 < 1e-11
+
+
+@pytest.mark.parametrize("k,m", [(0, 0), (3, 2), (5, 7)])
+def test_separable_closed_form_neumann(k, m):
+    """Neumann on all faces: f = (M1 phi_k) (x) (M2 phi_m) gives
+    u = phi_k (x) phi_m / (lam_k + lam_m - w^2), phi cosines (closed form)."""
+    n1, n2, h1, h2, om = 9, 11, 0.125, 0.1, 3.3
+    phik = np.cos(k * np.pi * np.arange(n1) / (n1 - 1))
+    phim = np.cos(m * np.pi * np.arange(n2) / (n2 - 1))
+    lam = fem.eig_neumann(n1, h1)[k] + fem.eig_neumann(n2, h2)[m]
+    f = np.outer(fem.M1d(n1, h1) @ phik, fem.M1d(n2, h2) @ phim).astype(complex)
+    u = solvers.solve_banded_lu(f, (h1, h2), om, bc="neumann")
+    np.testing.assert_allclose(u, np.outer(phik, phim) / (lam - om ** 2), rtol=1e-11, atol=1e-12)
+
+
+def test_reciprocity():
+    """A is complex symmetric, so g^T A^-1 f = f^T A^-1 g."""
+    shape, h, om = (10, 13), (0.1, 1 / 12), 12.0
+    f, g = random_rhs(shape, 8), random_rhs(shape, 9)
+    uf = solvers.solve_banded_lu(f, h, om)
+    ug = solvers.solve_banded_lu(g, h, om)
+    a, b = np.sum(g * uf), np.sum(f * ug)
+    assert abs(a - b) < 1e-12 * abs(a)
+
+
+def test_plane_wave_second_order_convergence():
+    """Manufactured plane wave with absorbing data: nodal error falls ~4x per
+    halving of h (linear elements, second order)."""
+    om, direction = 2 * np.pi, (math.cos(0.4), math.sin(0.4))
+    errs = []
+    for n in (17, 33, 65, 129):
+        h = (1 / (n - 1),) * 2
+        f, ue = fem.plane_wave_load((n, n), h, om, direction)
+        u = solvers.solve_banded_lu(f, h, om)
+        errs.append(np.linalg.norm(u - ue) / np.linalg.norm(ue))
+    ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert errs[-1] < 2e-3
+    assert all(3.5 < r < 4.5 for r in ratios[1:]), (errs, ratios)
+
+
+def test_plane_wave_3d_converges():
+    om, direction = 2 * np.pi, (0.3, 0.5, 0.8)
+    errs = []
+    for n in (9, 17):
+        h = (1 / (n - 1),) * 3
+        f, ue = fem.plane_wave_load((n, n, n), h, om, direction)
+        u = solvers.solve_banded_lu(f, h, om)
+        errs.append(np.linalg.norm(u - ue) / np.linalg.norm(ue))
+    assert 3.0 < errs[0] / errs[1] < 5.0, errs
+
+
+def test_refinement_reaches_double_precision():
+    shape, h, om = (33, 65), (1 / 32, 1 / 64), 2 * np.pi / (10 / 64)
+    f = random_rhs(shape, 10)
+    u, hist = solvers.oracle_solve(f, h, om, method="tensor")
+    assert hist[-1] < 1e-14
+    ub = solvers.solve_banded_lu(f, h, om)
+    assert np.linalg.norm(u - ub) / np.linalg.norm(ub) < 1e-12
+
+
+# --------------------------- Section 3.1 structure ---------------------------
+
+@pytest.mark.parametrize("shape,axis", [((7, 9), 1), ((7, 9), 0), ((5, 4, 6), 2)])
+def test_three_step_identities(shape, axis):
+    """B - A is supported on the boundary rows of the periodic axis only (eq.
+    BminA), and u = v + w after Step 2 (Section 3.1)."""
+    h = tuple(1.0 / (n - 1) for n in shape)
+    om = 7.0
+    A = fem.kron_operator(shape, h, om)
+    B = fem.kron_operator(shape, h, om, periodic_axis=axis)
+    D = (B - A).tocoo()
+    idx = np.array(np.unravel_index(np.arange(A.shape[0]), shape))
+    onb = (idx[axis] == 0) | (idx[axis] == shape[axis] - 1)
+    keep = np.abs(D.data) > 0
+    assert np.all(onb[D.row[keep]]) and np.all(onb[D.col[keep]])
+    f = random_rhs(shape, 11)
+    v, w, u = solvers.step_definitions(f, h, om, axis)
+    assert np.linalg.norm(v + w - u) / np.linalg.norm(u) < 1e-12
