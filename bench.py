@@ -1,0 +1,363 @@
+"""Benchmark: complex unknowns solved per second by the GB300 fast Helmholtz
+solver on the 8192 x 4096-node 2D workload (ABC on all sides, 10 nodes per
+wavelength, seeded complex Gaussian load times a Gaussian bump).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+One step = one full solve (Steps 1-3 of the paper's Section 4.2, with the
+forward and inverse transforms) of the whole workload with inputs resident in
+HBM.  `value` is the plain complex128 path (FP64 arithmetic throughout); the
+refined complex64 path (FP32 solves, FP64 residual, iterative refinement) is
+reported beside it under "variants".  Under torchrun every rank solves its own
+replica of the workload (the solve does not shard: replicas only).
+
+--impl reference times the CPU oracle (test infrastructure) on a bounded
+sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "complex unknowns solved/s at rel. err <=1e-10 vs FP64 oracle"
+UNIT = "unknowns/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 FMA throughput: 2 DFMA per clock per SM (measured on this GB300 with an
+# FMA-chain probe: 1.197 TFLOP/s at 1.995 GHz over 152 SMs), at the 2.07 GHz
+# maximum clock.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP64_PEAK_NOTE = "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FMA rate measured by probe)"
+
+
+def sample_shape():
+    """Bounded CPU sample: 2048 x 1024 nodes with the workload's spacing and
+    wave number (about 10-30 s of oracle work on the host cores)."""
+    return (2048, 1024)
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# Algorithmic traffic and arithmetic per unknown of each 2D kernel (per
+# launch: times N = nx * n1).  Bytes count the minimum reads/writes of the
+# kernel's own inputs and outputs in the compute precision (e bytes per
+# complex value); flops count real FP64/FP32 operations of the algorithm.
+def kernel_model(name, e, n1):
+    import math
+
+    log2n = math.log2(n1)
+    model = {
+        # DFT: read line, write line; ~5 n log2 n real flops per line
+        "dft_fwd": (2 * e, 5 * log2n),
+        "dft_inv": (2 * e, 5 * log2n),
+        # tridiagonal sweeps: rhs read, (c', d') scratch write + read; result write (step 3)
+        "tri_step1": (e + 4 * e, 40.0),
+        "tri_step2": (4 * e, 40.0),
+        "tri_step3": (e + 4 * e + e, 48.0),
+        # FP64 residual: read u (16) + f (16), write r (8)
+        "residual_fp64": (40.0, 40.0),
+    }
+    return model.get(name)
+
+
+def run_gb300(args):
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    try:
+        import paper_1809_03808_gb300 as helm
+    except ImportError:
+        import __graft_entry__
+
+        __graft_entry__.build()
+        import paper_1809_03808_gb300 as helm
+
+    p = workloads.config_2d_large()
+    N = p.N
+    f_host = workloads.rhs(p)
+    f = torch.from_numpy(f_host).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(plan, u, profile):
+        helm.helm_set_stream(plan.handle, stream.cuda_stream)
+        for _ in range(args.warmup):
+            helm.helm_solve(plan.handle, f, u)
+        torch.cuda.synchronize()
+        helm.helm_set_profiling(plan.handle, profile)
+        barrier()
+        torch.cuda.synchronize()
+        clk = ClockSampler(local)
+        clk.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            helm.helm_solve(plan.handle, f, u)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = clk.stop()
+        ms = e0.elapsed_time(e1)
+        prof = helm.helm_get_profile(plan.handle) if profile else {}
+        helm.helm_set_profiling(plan.handle, False)
+        return max_over_ranks(ms), prof, clocks
+
+    def sampled_error(u):
+        try:
+            sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+            from make_golden import load
+
+            d, idx, vals = load("2d_large")
+            got = u.reshape(-1)[torch.from_numpy(idx).to(dev)].cpu().numpy()
+            return float(np.linalg.norm(got - vals) / np.linalg.norm(vals))
+        except FileNotFoundError:
+            return None
+
+    # --- plain complex128 path (the headline) ---
+    plan = helm.Plan(p.shape, p.h, p.omega, helm.HELM_C128)
+    u = torch.empty_like(f)
+    ms, prof, clocks = timed(plan, u, True)
+    info, _ = plan.info()
+    err_c128 = sampled_error(u)
+    ms_step = ms / args.steps
+    value = world * N / (ms_step * 1e-3)
+
+    # e2e through the host-buffer entry point (H2D of f, solve, D2H of u)
+    e2e = None
+    if not args.no_e2e:
+        fh = torch.from_numpy(f_host).pin_memory()
+        uh = torch.empty_like(fh).pin_memory()
+        helm.helm_set_stream(plan.handle, stream.cuda_stream)
+        helm.lib.helm_solve_host(plan.handle, fh.data_ptr(), uh.data_ptr())
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            st = helm.lib.helm_solve_host(plan.handle, fh.data_ptr(), uh.data_ptr())
+            if st != 0:
+                raise RuntimeError(helm.lib.helm_status_string(st))
+        t1 = time.perf_counter()
+        dt = max_over_ranks((t1 - t0) / args.steps)
+        e2e = {"value": world * N / dt, "unit": UNIT, "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16,
+               "ms_per_step": dt * 1e3, "api": "helm_solve_host (pinned host buffers)"}
+    plan.close()
+    del u
+
+    # --- refined complex64 path ---
+    variants = {}
+    if not args.no_variants:
+        plan = helm.Plan(p.shape, p.h, p.omega, helm.HELM_C64_REFINED)
+        u = torch.empty_like(f)
+        ms_r, prof_r, _ = timed(plan, u, True)
+        info_r, st_r = plan.info()
+        variants["c64_refined"] = {
+            "value": world * N / (ms_r / args.steps * 1e-3), "unit": UNIT, "ms_per_step": ms_r / args.steps,
+            "dtype": "f32 solves + f64 residual", "refinement_sweeps": int(info_r.iterations),
+            "final_rel_residual": float(info_r.residual[info_r.iterations]),
+            "converged": bool(info_r.converged), "rel_err_sampled": sampled_error(u),
+            "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof_r.items()},
+        }
+        plan.close()
+        del u
+
+    # --- roofline of the dominant kernel of the timed (c128) step ---
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (launches, tot_ms) = dom
+    per_launch_ms = tot_ms / launches
+    model = kernel_model(name, 16, p.shape[1])
+    peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
+    roof = {"kernel": name, "launches_per_step": launches / args.steps, "ms_per_launch": per_launch_ms}
+    if model:
+        flops = model[1] * N
+        roof.update({"bound": "alu", "achieved": flops / (per_launch_ms * 1e-3) / 1e12,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": flops / (per_launch_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                     "peak_source": FP64_PEAK_NOTE, "traffic": None,
+                     "hbm_GBps": model[0] * N / (per_launch_ms * 1e-3) / 1e9,
+                     "hbm_peak_GBps": peaks.get("hbm_gbs")})
+    gpu_launches = sum(v[0] for v in prof.values())
+
+    # --- CPU oracle baseline (rank 0, N = 1 only) ---
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_run(p, 1)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded complex Gaussian x Gaussian bump)",
+        "config": {"workload": p.name, "nodes": list(p.shape), "h": list(p.h), "omega": p.omega,
+                   "precision": "complex128 plain", "rhs_per_step": 1,
+                   "l2": "inputs larger than L2 (f and u are 537 MB each)", "parallelism": f"replicas x{world}"},
+        "rel_err_sampled": err_c128,
+        "gpu_launches": gpu_launches,
+        "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()},
+        "roofline": roof, "clocks": clocks, "e2e": e2e, "variants": variants, "cpu_baseline": cpu,
+        "plan_seconds": info.plan_seconds,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def cpu_baseline_run(p, steps):
+    from oracle import solvers
+
+    shape = sample_shape()
+    sp = workloads.scaled(p, shape)
+    f = workloads.rhs(sp)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        solvers.oracle_solve(f, sp.h, sp.omega, method="tensor", iters=2)
+    dt = (time.perf_counter() - t0) / steps
+    cores = len(os.sched_getaffinity(0))
+    return {"value": sp.N / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{shape[0]}x{shape[1]} nodes, same h and omega (O2 tensor eigen-solve + 2 double-double "
+                      f"refinement sweeps), {dt:.2f} s per solve; BLAS threads = host cores"}
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return
+    p = workloads.config_2d_large()
+    from oracle import solvers
+
+    shape = sample_shape()
+    sp = workloads.scaled(p, shape)
+    f = workloads.rhs(sp)
+    for _ in range(args.warmup):
+        solvers.oracle_solve(f, sp.h, sp.omega, method="tensor", iters=2)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        solvers.oracle_solve(f, sp.h, sp.omega, method="tensor", iters=2)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = sp.N / dt
+    cores = len(os.sched_getaffinity(0))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded complex Gaussian x Gaussian bump)",
+        "config": {"workload": p.name, "nodes": list(p.shape), "h": list(p.h), "omega": p.omega,
+                   "sample": f"{shape[0]}x{shape[1]} nodes, same spacing and wave number"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cores,
+                         "sample": f"{shape[0]}x{shape[1]} nodes per step, O2 + 2 dd refinement sweeps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+    if args.impl == "reference":
+        if args.steps > 3:
+            args.steps = 3
+        args.warmup = min(args.warmup, 1)
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * helm.h -- C ABI of a GB300 (sm_103a) fast direct solver for the FEM
+ * discretised Helmholtz problem with first-order absorbing boundaries,
+ * following Toivanen & Wolfmayr, "A fast Fourier transform based direct
+ * solver for the Helmholtz problem" (arXiv 1809.03808).
+ *
+ * Problem (Section 2, eqs. helmholtz, 1st-order-abc, bf-1st-order-abc):
+ *     -Lap u - w^2 u = f  in a box,   du/dn - i w u = 0  on every face,
+ * discretised by bilinear (2D) / trilinear (3D) elements on a uniform tensor
+ * mesh with n_j nodes and spacing h_j along axis j.  The linear system is
+ * A u = f with A the Kronecker form of eq. A2D (2D) or eq. A3D (3D) built from
+ * the 1D matrices of eqs. matrixK / matrixM; every node is an unknown.
+ *
+ * Method (Sections 3-5): the absorbing rows of one axis ("x1") are replaced by
+ * periodic ones (auxiliary operator B, eqs. probB, B2D, B3D) so that axis is
+ * diagonalised by a DFT; three steps -- Step 1 B v = f, Step 2 A w = (B - A) v,
+ * Step 3 B u = f + (B - A)(v + w) (eqs. probStep2, probStep3) -- recover the
+ * exact solution, touching the non-periodic eigenvectors only on the two
+ * boundary rows (eqs. 2dBs1, step2-1..step2-3, step3term).  The remaining axis
+ * is a batch of complex tridiagonal solves, one per mode (Section 4.1.2).  In
+ * 3D each per-mode solve is itself the 2D solver (Section 5.1.2).
+ *
+ * Array layout (all entry points): interleaved complex (re, im), C order,
+ * LAST axis fastest: index (ix, iy) -> ix*ny + iy in 2D and (ix, iy, iz) ->
+ * (ix*ny + iy)*nz + iz in 3D.  In 2D x1 (the periodic/DFT axis) is y, the
+ * last axis.  In 3D the outer x1 is y and the inner x2 (the DFT axis of the
+ * per-mode 2D solves, Section 5.1.2) is z.  The tridiagonal axis is x in both.
+ * The choice of x1 is free (Remark Rem:ABCx1).
+ *
+ * Element types by precision mode:
+ *   HELM_C128         f, u complex128; all arithmetic FP64.
+ *   HELM_C64_REFINED  f, u complex128; solves in FP32 (complex64), residual
+ *                     r = f - A u in FP64, iterative refinement until
+ *                     ||r|| / ||f|| <= tol (default 1e-14) or max_iter.
+ *   HELM_C64_RAW      f, u complex64; one FP32 solve, no refinement.
+ *
+ * Errors: every entry point returns a helm_status; no exception crosses the
+ * ABI.  CUDA failures are reported as HELM_ECUDA and the plan keeps the CUDA
+ * error string (helm_last_error).
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct helm_plan* helm_plan_t;
+
+enum helm_dtype {
+  HELM_C128 = 0,
+  HELM_C64_REFINED = 1,
+  HELM_C64_RAW = 2
+};
+
+enum helm_status {
+  HELM_OK = 0,
+  HELM_EINVAL = -1,        /* bad argument (sizes, spacings, w, null pointer) */
+  HELM_ENOMEM = -2,        /* device or host allocation failed */
+  HELM_ECUDA = -3,         /* a CUDA runtime call failed */
+  HELM_ENOTCONV = -4,      /* refinement stopped above tol; u is still written */
+  HELM_ETIMEOUT = -5,      /* reserved: a bounded device wait gave up */
+  HELM_EUNSUPPORTED = -6,  /* size outside what the kernels support */
+  HELM_ENUMERIC = -7       /* plan eigen-data failed to converge / degenerate */
+};
+
+/* Diagnostics of the most recent solve (valid after the solve's stream has
+ * been synchronised; helm_get_info synchronises it). */
+typedef struct helm_info {
+  int32_t dim;
+  int32_t dtype;
+  int64_t n[3];            /* node counts (n[2] = 1 in 2D) */
+  int32_t iterations;      /* refinement sweeps performed (0 for plain modes) */
+  int32_t converged;       /* 1 if the last refinement residual met tol */
+  double residual[16];     /* ||f - A u||_2 / ||f||_2 after each sweep (FP64) */
+  double plan_seconds;     /* host time spent building the plan */
+  double tol;              /* refinement tolerance */
+  int32_t max_iter;        /* refinement sweep limit */
+  int32_t n_dft_stages;    /* stages of the x1 transform */
+  size_t device_bytes;     /* device memory owned by the plan */
+} helm_info;
+
+/* --- Plan (the paper's "Initialization", Section 6) -----------------------
+ * Builds the per-axis eigen-data: the periodic eigenvalues of eq.
+ * eigvaluesPer, the absorbing-pencil eigenvalues Lam^A and boundary rows of
+ * V (eqs. EVP1a, EVPcondA), the DFT twiddles; allocates all device scratch.
+ * nx, ny (, nz): node counts, >= 3.  hx, hy (, hz): spacings > 0, finite.
+ * omega: wave number > 0, finite.  dtype: helm_dtype.
+ * On success *out owns device memory until helm_destroy; on failure *out is
+ * set to NULL.  Limits: the x1 length must be <= 4096 (HELM_C128) or 8192
+ * (complex64 modes) in 2D, and the 3D transform lengths <= 1024; otherwise
+ * HELM_EUNSUPPORTED.  Requires a current CUDA device. */
+int helm_plan_2d(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy,
+                 double omega, int dtype);
+int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx,
+                 double hy, double hz, double omega, int dtype);
+
+/* Stream on which helm_solve enqueues its kernels (a cudaStream_t passed as
+ * void*; NULL = legacy default stream).  One plan serves one stream at a time. */
+int helm_set_stream(helm_plan_t p, void* cuda_stream);
+
+/* Refinement controls for HELM_C64_REFINED: stop when ||r||/||f|| <= tol or
+ * after max_iter sweeps (1 <= max_iter <= 16). */
+int helm_set_refinement(helm_plan_t p, double tol, int max_iter);
+
+/* --- Solve (Sections 4.2 and 5.2: Steps 1-3) ------------------------------
+ * f, u: DEVICE pointers to N = nx*ny(*nz) complex values in the layout above
+ * (complex128 or complex64 per dtype).  f is read only, u is overwritten; f
+ * and u must not overlap.  Asynchronous on the plan's stream: returns after
+ * enqueueing.  Convergence of refinement is reported by helm_get_info. */
+int helm_solve(helm_plan_t p, const void* f, void* u);
+
+/* Same solve with HOST pointers: copies f to the device, solves, copies u
+ * back and synchronises the stream before returning (for callers without
+ * device buffers; the copies are part of the call).  Page-locked host memory
+ * gives full copy bandwidth; pageable memory also works. */
+int helm_solve_host(helm_plan_t p, const void* f_host, void* u_host);
+
+/* Step-by-step variant for verification: runs the same kernels as helm_solve
+ * and also copies out, to DEVICE buffers the caller owns (any may be NULL):
+ *   fhat  : N values, the DFT of f along x1 (eq. step1FFTfcoeff) -- in the
+ *           solve's compute precision (complex64 in the C64 modes);
+ *   v_b   : the Step-1 boundary rows of v = B^-1 f (eq. 2dBs1 / 3dBs1), and
+ *   w_b   : the Step-2 boundary rows of w = A^-1 (B - A) v (eq. step2-3 /
+ *           step2-3-3d), each 2*N/n1 values: the x1 = first face, then the
+ *           x1 = last face, each in the layout of the remaining axes,
+ *           complex128 in HELM_C128 and complex64 otherwise.
+ * Only the first (unrefined) solve's intermediates are reported. */
+int helm_solve_debug(helm_plan_t p, const void* f, void* u, void* fhat, void* v_b,
+                     void* w_b);
+
+/* Synchronises the plan's stream and fills *info. */
+int helm_get_info(helm_plan_t p, helm_info* info);
+
+/* Per-kernel timing.  When enabled, every kernel launch of helm_solve is
+ * bracketed by CUDA events recorded on the plan's stream.  helm_get_profile
+ * synchronises the stream, writes up to max_entries aggregated entries (one
+ * per kernel kind: launches and summed device milliseconds), clears the
+ * record and returns the number of entries written (or a negative status). */
+typedef struct helm_profile_entry {
+  char name[32];
+  int32_t launches;
+  double total_ms;
+} helm_profile_entry;
+
+int helm_set_profiling(helm_plan_t p, int enable);
+int helm_get_profile(helm_plan_t p, helm_profile_entry* out, int max_entries);
+
+/* Frees everything the plan owns.  NULL is allowed. */
+int helm_destroy(helm_plan_t p);
+
+const char* helm_status_string(int status);
+
+/* Last CUDA/diagnostic message recorded by the plan (never NULL). */
+const char* helm_last_error(helm_plan_t p);
+
+/* --- Host-side plan helpers (no GPU needed) --------------------------------
+ * Eigen-data of the 1D absorbing pencil K V = M V Lam (eq. EVP1a) with
+ * V^T M V = I (eq. EVPcondA), K, M of eqs. matrixK / matrixM with n nodes,
+ * spacing h and corner 1 - i w h.  Outputs, caller-owned host arrays:
+ *   lam    : 2n doubles, eigenvalues (re, im) interleaved;
+ *   sigma  : 2n doubles, V[1,l]^2 (re, im) for the same eigenvector;
+ *   parity : n int8, +1 if V[n,l] = V[1,l], -1 if V[n,l] = -V[1,l].
+ * Order of the eigenpairs is unspecified.  Returns HELM_EINVAL for n < 2,
+ * h <= 0 or w <= 0, HELM_ENUMERIC if the eigenvalue iteration fails. */
+int helm_abc_eigen(int64_t n, double h, double omega, double* lam, double* sigma,
+                   int8_t* parity);
+
+/* Mixed-radix factorisation the DFT kernels use for length n: writes up to
+ * max_stages radices to `radices`, returns the number of stages (0 if n < 1).
+ * Radices are 8, 4, 2 first, then odd primes. */
+int helm_dft_factor(int64_t n, int32_t* radices, int32_t max_stages);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HELM_H */

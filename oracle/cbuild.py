@@ -1,0 +1,40 @@
+"""Compile the oracle's C helpers (test infrastructure only) with gcc and
+load them through ctypes.  Building the checker is not using it: the product
+path never loads this library."""
+from __future__ import annotations
+
+import ctypes
+import os
+import shutil
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "c", "dd_resid.c")
+LIB = os.path.join(HERE, "c", "liboracle_dd.so")
+
+
+def build(force: bool = False) -> str:
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+        return LIB
+    cc = os.environ.get("CC") or shutil.which("gcc") or "cc"
+    tmp = LIB + ".tmp"
+    cmd = [cc, "-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", SRC, "-o", tmp]
+    r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("oracle C build failed:\n" + r.stdout)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        f = _lib.helm_oracle_dd_residual
+        f.restype = None
+        f.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                      ctypes.c_void_p, ctypes.c_void_p]
+    return _lib

@@ -150,11 +150,12 @@ def refine(f, u, solve, h, omega, iters=2):
     double-double (fem.residual_dd).  Returns (u, [relative residuals])."""
     hist = []
     fn = np.linalg.norm(f)
+    resid = fem.residual_dd_c if f.size > 4096 else fem.residual_dd
     for _ in range(iters):
-        r = fem.residual_dd(f, u, h, omega)
+        r = resid(f, u, h, omega)
         hist.append(float(np.linalg.norm(r) / fn))
         u = u + solve(r)
-    r = fem.residual_dd(f, u, h, omega)
+    r = resid(f, u, h, omega)
     hist.append(float(np.linalg.norm(r) / fn))
     return u, hist
 

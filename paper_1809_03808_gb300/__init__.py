@@ -1,0 +1,225 @@
+"""Python binding of libhelm (include/helm.h): a GB300 (sm_103a) fast direct
+solver for the FEM Helmholtz problem with first-order absorbing boundaries
+(Toivanen & Wolfmayr, arXiv 1809.03808).
+
+Argument marshalling only: every step of a solve runs in the CUDA kernels of
+libhelm.so.  Device buffers are torch tensors (complex128 / complex64, C
+contiguous, on the current CUDA device); their data pointers and the current
+torch CUDA stream are passed through the C ABI.  If the library has not been
+built this module raises ImportError -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libhelm.so")
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libhelm.so not found at {_LIB_PATH}; run __graft_entry__.build() "
+                      "(or python -m paper_1809_03808_gb300._build)")
+
+lib = ctypes.CDLL(_LIB_PATH)
+
+HELM_C128, HELM_C64_REFINED, HELM_C64_RAW = 0, 1, 2
+HELM_OK, HELM_EINVAL, HELM_ENOMEM, HELM_ECUDA, HELM_ENOTCONV, HELM_ETIMEOUT, HELM_EUNSUPPORTED, HELM_ENUMERIC = \
+    0, -1, -2, -3, -4, -5, -6, -7
+
+_i64, _dbl, _vp, _i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_int
+
+
+class helm_info(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("dtype", ctypes.c_int32), ("n", ctypes.c_int64 * 3),
+                ("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("residual", ctypes.c_double * 16), ("plan_seconds", ctypes.c_double),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("n_dft_stages", ctypes.c_int32),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+class helm_profile_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int32), ("total_ms", ctypes.c_double)]
+
+
+_SIGS = {
+    "helm_plan_2d": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _dbl, _dbl, _dbl, _i32]),
+    "helm_plan_3d": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _i64, _dbl, _dbl, _dbl, _dbl, _i32]),
+    "helm_set_stream": (_i32, [_vp, _vp]),
+    "helm_set_refinement": (_i32, [_vp, _dbl, _i32]),
+    "helm_solve": (_i32, [_vp, _vp, _vp]),
+    "helm_solve_host": (_i32, [_vp, _vp, _vp]),
+    "helm_solve_debug": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "helm_get_info": (_i32, [_vp, ctypes.POINTER(helm_info)]),
+    "helm_destroy": (_i32, [_vp]),
+    "helm_status_string": (ctypes.c_char_p, [_i32]),
+    "helm_last_error": (ctypes.c_char_p, [_vp]),
+    "helm_abc_eigen": (_i32, [_i64, _dbl, _dbl, _vp, _vp, _vp]),
+    "helm_dft_factor": (_i32, [_i64, _vp, _i32]),
+    "helm_set_profiling": (_i32, [_vp, _i32]),
+    "helm_get_profile": (_i32, [_vp, ctypes.POINTER(helm_profile_entry), _i32]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+class HelmError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        msg = f"{where}: {lib.helm_status_string(status).decode()}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+        self.status = status
+
+
+def _check(status, where, plan=None):
+    if status != HELM_OK:
+        detail = lib.helm_last_error(plan).decode() if plan else ""
+        raise HelmError(status, where, detail)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+# ---- names of the C ABI (marshalling only) ---------------------------------
+
+def helm_plan_2d(nx, ny, hx, hy, omega, dtype=HELM_C128):
+    h = _vp()
+    _check(lib.helm_plan_2d(ctypes.byref(h), int(nx), int(ny), float(hx), float(hy), float(omega), int(dtype)),
+           "helm_plan_2d")
+    return h
+
+
+def helm_plan_3d(nx, ny, nz, hx, hy, hz, omega, dtype=HELM_C128):
+    h = _vp()
+    _check(lib.helm_plan_3d(ctypes.byref(h), int(nx), int(ny), int(nz), float(hx), float(hy), float(hz),
+                            float(omega), int(dtype)), "helm_plan_3d")
+    return h
+
+
+def helm_set_stream(plan, stream):
+    _check(lib.helm_set_stream(plan, _vp(int(stream) if stream is not None else 0)), "helm_set_stream", plan)
+
+
+def helm_set_refinement(plan, tol, max_iter):
+    _check(lib.helm_set_refinement(plan, float(tol), int(max_iter)), "helm_set_refinement", plan)
+
+
+def helm_solve(plan, f, u):
+    _check(lib.helm_solve(plan, _ptr(f), _ptr(u)), "helm_solve", plan)
+
+
+def helm_solve_host(plan, f, u):
+    """f, u: host buffers (numpy arrays or pinned torch CPU tensors)."""
+    fp = f.ctypes.data if hasattr(f, "ctypes") else _ptr(f)
+    up = u.ctypes.data if hasattr(u, "ctypes") else _ptr(u)
+    _check(lib.helm_solve_host(plan, fp, up), "helm_solve_host", plan)
+
+
+def helm_solve_debug(plan, f, u, fhat=None, v_b=None, w_b=None):
+    _check(lib.helm_solve_debug(plan, _ptr(f), _ptr(u), _ptr(fhat), _ptr(v_b), _ptr(w_b)), "helm_solve_debug", plan)
+
+
+def helm_get_info(plan):
+    info = helm_info()
+    st = lib.helm_get_info(plan, ctypes.byref(info))
+    if st not in (HELM_OK, HELM_ENOTCONV):
+        _check(st, "helm_get_info", plan)
+    return info, st
+
+
+def helm_set_profiling(plan, enable):
+    _check(lib.helm_set_profiling(plan, int(bool(enable))), "helm_set_profiling", plan)
+
+
+def helm_get_profile(plan):
+    """{kernel name: (launches, total device ms)} since the last call."""
+    buf = (helm_profile_entry * 64)()
+    k = lib.helm_get_profile(plan, buf, 64)
+    if k < 0:
+        _check(k, "helm_get_profile", plan)
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(k)}
+
+
+def helm_destroy(plan):
+    _check(lib.helm_destroy(plan), "helm_destroy")
+
+
+def helm_abc_eigen(n, h, omega):
+    """Host-side eigen-data of the absorbing 1D pencil: (lam, sigma, parity) numpy arrays."""
+    import numpy as np
+    lam = np.zeros(2 * n)
+    sig = np.zeros(2 * n)
+    par = np.zeros(n, dtype=np.int8)
+    _check(lib.helm_abc_eigen(int(n), float(h), float(omega), lam.ctypes.data, sig.ctypes.data, par.ctypes.data),
+           "helm_abc_eigen")
+    return lam[0::2] + 1j * lam[1::2], sig[0::2] + 1j * sig[1::2], par.astype(np.int64)
+
+
+def helm_dft_factor(n):
+    import numpy as np
+    r = np.zeros(32, dtype=np.int32)
+    ns = lib.helm_dft_factor(int(n), r.ctypes.data, 32)
+    return [int(x) for x in r[:ns]]
+
+
+# ---- convenience wrapper ----------------------------------------------------
+
+class Plan:
+    """Owns one helm plan; solve(f, u) on torch CUDA tensors, current stream."""
+
+    def __init__(self, shape, h, omega, dtype=HELM_C128):
+        shape = tuple(int(n) for n in shape)
+        self.shape = shape
+        self.dtype = dtype
+        if len(shape) == 2:
+            self.handle = helm_plan_2d(shape[0], shape[1], h[0], h[1], omega, dtype)
+        elif len(shape) == 3:
+            self.handle = helm_plan_3d(shape[0], shape[1], shape[2], h[0], h[1], h[2], omega, dtype)
+        else:
+            raise ValueError("shape must be 2D or 3D")
+
+    @property
+    def tensor_dtype(self):
+        import torch
+        return torch.complex64 if self.dtype == HELM_C64_RAW else torch.complex128
+
+    def _check_tensor(self, t, name):
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != self.tensor_dtype or tuple(t.shape) != self.shape or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {self.tensor_dtype} tensor of shape {self.shape}")
+
+    def solve(self, f, u=None, stream=None):
+        import torch
+        self._check_tensor(f, "f")
+        if u is None:
+            u = torch.empty_like(f)
+        self._check_tensor(u, "u")
+        s = torch.cuda.current_stream(f.device) if stream is None else stream
+        helm_set_stream(self.handle, s.cuda_stream)
+        helm_solve(self.handle, f, u)
+        return u
+
+    def info(self):
+        return helm_get_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            helm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,502 @@
+// C ABI of the fast Helmholtz solver: plan construction (the paper's
+// initialisation), solve orchestration (Steps 1-3 of Sections 4.2 / 5.2),
+// mixed-precision refinement, host-buffer and step-by-step variants.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "helm.h"
+#include "helm_dft.h"
+#include "helm_internal.h"
+#include "helm_solve.h"
+#include "helm_prof.h"
+#include "helm_solve3d.h"
+
+using namespace helm;
+
+struct helm_plan {
+  int dim = 2;
+  int64_t n[3] = {1, 1, 1};
+  double h[3] = {0, 0, 0};
+  double omega = 0;
+  int dtype = HELM_C128;
+  int prec = kPrecF64;  // compute precision of the solves
+  cudaStream_t stream = nullptr;
+  // 2D: x1 = axis 1 (ax[0] below); 3D: outer x1 = axis 1 (y), inner x2 = axis 2 (z)
+  AxisData axo;  // outer periodic axis
+  AxisData axi;  // inner periodic axis (3D only)
+  // device buffers
+  void* fhat = nullptr;
+  void* cbuf = nullptr;
+  void* dbuf = nullptr;
+  void* partial = nullptr;
+  void* faces = nullptr;  // v (2 faces), w (2 faces), c (2 faces), scratch
+  int64_t face_len = 0;   // values per face
+  int64_t nwarps = 0;
+  float2* rbuf = nullptr;
+  double* sums = nullptr;
+  RefineState* state = nullptr;
+  double2* host_f = nullptr;  // staging for helm_solve_host (allocated on first use)
+  double2* host_u = nullptr;
+  size_t bytes = 0;
+  double plan_seconds = 0;
+  double tol = 1e-14;
+  int max_iter = 10;
+  Plan3D p3;
+  Profiler prof;
+  std::string err;
+};
+
+namespace {
+
+int cuda_fail(helm_plan* p, cudaError_t e, const char* what) {
+  if (p) {
+    p->err = std::string(what) + ": " + cudaGetErrorString(e);
+  }
+  return HELM_ECUDA;
+}
+
+#define HELM_CK(call)                                             \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return cuda_fail(p, e_, #call);        \
+  } while (0)
+// HELM_CK with per-kernel event timing when profiling is enabled
+#define HELM_PK(name, call)                                       \
+  do {                                                            \
+    ProfScope ps_(&p->prof, name, p->stream);                     \
+    HELM_CK(call);                                                \
+  } while (0)
+
+int dev_alloc(helm_plan* p, void** ptr, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    p->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    *ptr = nullptr;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? HELM_ENOMEM : HELM_ECUDA;
+  }
+  p->bytes += bytes;
+  return HELM_OK;
+}
+
+void free_axis(AxisData& a) {
+  cudaFree(a.lamB);
+  cudaFree(a.muB);
+  cudaFree(a.lamA);
+  cudaFree(a.sigA);
+  cudaFree(a.parA);
+  cudaFree(a.tw);
+  cudaFree(a.tw32);
+  a = AxisData{};
+}
+
+// Eigen-data of one periodic axis (Section 3.2): periodic eigenvalues
+// Lam^B_l = kappa_l / mu_l (eq. eigvaluesPer, closed form), absorbing-pencil
+// eigen-data (eq. EVP1a, EVPcondA), DFT twiddles.
+int build_axis(helm_plan* p, AxisData& a, int64_t n, double h, double omega) {
+  a.n = n;
+  a.h = h;
+  dft_factor(n, &a.dft);
+  const double pi = 3.14159265358979323846;
+  std::vector<double> twre(n), twim(n);
+  unit_roots(n, twre.data(), twim.data());
+  std::vector<double> lamB(n), muB(n), tw(2 * n), lamA(2 * n), sigA(2 * n), parA(n);
+  std::vector<float> tw32(2 * n);
+  std::vector<int8_t> par8(n);
+  for (int64_t l = 0; l < n; ++l) {
+    const double c = twre[l];  // cos(2 pi l / n)
+    // 1 - cos(theta) = 2 sin^2(theta/2), evaluated without cancellation
+    const double s = std::sin(pi * (double)l / (double)n);
+    const double kappa = 2.0 * (2.0 * s * s) / h;  // (2 - 2 cos theta)/h
+    const double mu = h * (4.0 + 2.0 * c) / 6.0;
+    lamB[l] = kappa / mu;
+    muB[l] = mu;
+    tw[2 * l] = twre[l];
+    tw[2 * l + 1] = twim[l];
+    tw32[2 * l] = (float)twre[l];
+    tw32[2 * l + 1] = (float)twim[l];
+  }
+  int rc = abc_eigen(n, h, omega, lamA.data(), sigA.data(), par8.data());
+  if (rc != HELM_OK) {
+    p->err = "absorbing-pencil eigenvalue iteration failed";
+    return rc;
+  }
+  for (int64_t l = 0; l < n; ++l) parA[l] = par8[l];
+  auto up = [&](double** d, const std::vector<double>& v) -> int {
+    int r = dev_alloc(p, (void**)d, v.size() * sizeof(double));
+    if (r) return r;
+    cudaError_t e = cudaMemcpy(*d, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? HELM_OK : cuda_fail(p, e, "cudaMemcpy eigen-data");
+  };
+  if ((rc = up(&a.lamB, lamB)) || (rc = up(&a.muB, muB)) || (rc = up(&a.lamA, lamA)) ||
+      (rc = up(&a.sigA, sigA)) || (rc = up(&a.parA, parA)) || (rc = up(&a.tw, tw)))
+    return rc;
+  rc = dev_alloc(p, (void**)&a.tw32, tw32.size() * sizeof(float));
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpy(a.tw32, tw32.data(), tw32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(p, e, "cudaMemcpy twiddles");
+  return HELM_OK;
+}
+
+int validate_common(double omega, int dtype) {
+  if (!(omega > 0) || !std::isfinite(omega)) return HELM_EINVAL;
+  if (dtype != HELM_C128 && dtype != HELM_C64_REFINED && dtype != HELM_C64_RAW) return HELM_EINVAL;
+  return HELM_OK;
+}
+
+size_t cbytes(int prec) { return prec == kPrecF64 ? sizeof(double2) : sizeof(float2); }
+
+// ---------------------------------------------------------------------------
+// 2D solve: in (complex128 if in_is_double) -> out per out_mode.
+// ---------------------------------------------------------------------------
+int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int out_mode,
+                 double accum_scale, const int* skip, void* dbg_fhat, void* dbg_v, void* dbg_w) {
+  const int prec = p->prec;
+  const int64_t nx = p->n[0], n1 = p->n[1];
+  const size_t cb = cbytes(prec);
+  const AxisData& ax = p->axo;
+  const void* tw = prec == kPrecF64 ? (const void*)ax.tw : (const void*)ax.tw32;
+  cudaStream_t st = p->stream;
+  char* faces = (char*)p->faces;
+  void* fv = faces;                 // v_1, v_n
+  void* fw = faces + 2 * nx * cb;   // w_1, w_n
+  void* fc = faces + 4 * nx * cb;   // c (or d)
+  Solve2DArgs a{nx, n1, p->h[0], p->h[1], p->omega, ax.lamB, ax.muB, ax.lamA, ax.sigA, ax.parA, ax.tw};
+  const int fhat_mode = prec == kPrecF64 ? kOutC128 : kOutC64;
+  // a1: forward DFT along x1 (eq. step1FFTfcoeff), f_hat kept for Step 3
+  HELM_PK("dft_fwd", launch_dft_rows(prec, in, in_is_double, p->fhat, fhat_mode, nx, ax.dft, tw, -1, 1.0, 0.0, skip, st));
+  if (dbg_fhat) HELM_CK(cudaMemcpyAsync(dbg_fhat, p->fhat, nx * n1 * cb, cudaMemcpyDeviceToDevice, st));
+  // a2: Step 1
+  HELM_PK("tri_step1", launch_tri2d(prec, 1, p->fhat, p->cbuf, p->dbuf, p->partial, nullptr, a, skip, st));
+  HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fv, nx, p->nwarps, 1.0 / (double)n1, skip, st));
+  if (dbg_v) HELM_CK(cudaMemcpyAsync(dbg_v, fv, 2 * nx * cb, cudaMemcpyDeviceToDevice, st));
+  // a3: Step 2
+  HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, nullptr, fc, nx, p->h[0], p->h[1], p->omega, p->omega * p->omega, skip, st));
+  HELM_PK("tri_step2", launch_tri2d(prec, 2, nullptr, p->cbuf, p->dbuf, p->partial, fc, a, skip, st));
+  HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fw, nx, p->nwarps, 1.0, skip, st));
+  if (dbg_w) HELM_CK(cudaMemcpyAsync(dbg_w, fw, 2 * nx * cb, cudaMemcpyDeviceToDevice, st));
+  // a4: Step 3
+  HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, fw, fc, nx, p->h[0], p->h[1], p->omega, p->omega * p->omega, skip, st));
+  HELM_PK("tri_step3", launch_tri2d(prec, 3, p->fhat, p->cbuf, p->dbuf, p->partial, fc, a, skip, st));
+  // a5: inverse DFT along x1 (eq. step3IFFTz3coeff)
+  HELM_PK("dft_inv", launch_dft_rows(prec, p->dbuf, prec == kPrecF64, out, out_mode, nx, ax.dft, tw, +1, 1.0 / (double)n1,
+                          accum_scale, skip, st));
+  return HELM_OK;
+}
+
+int solve_core(helm_plan* p, const void* in, int in_is_double, void* out, int out_mode, double accum_scale,
+               const int* skip, void* dbg_fhat, void* dbg_v, void* dbg_w) {
+  if (p->dim == 2) return solve2d_core(p, in, in_is_double, out, out_mode, accum_scale, skip, dbg_fhat, dbg_v, dbg_w);
+  cudaError_t e = solve3d_core(p->p3, p->prec, in, in_is_double, out, out_mode, accum_scale, skip, dbg_fhat,
+                               dbg_v, dbg_w, p->stream, p->prof.on ? &p->prof : nullptr);
+  return e == cudaSuccess ? HELM_OK : cuda_fail(p, e, "solve3d");
+}
+
+int run_solve(helm_plan* p, const void* f, void* u, void* dbg_fhat, void* dbg_v, void* dbg_w) {
+  if (p->dtype == HELM_C128) return solve_core(p, f, 1, u, kOutC128, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
+  if (p->dtype == HELM_C64_RAW) return solve_core(p, f, 0, u, kOutC64, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
+  // HELM_C64_REFINED: u0 = S(f); then r = f - A u (FP64), u += S(r) until tol.
+  RefineState init{};
+  init.tol = p->tol;
+  HELM_CK(cudaMemcpyAsync(p->state, &init, sizeof(init), cudaMemcpyHostToDevice, p->stream));
+  int rc = solve_core(p, f, 1, u, kOutC128, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
+  if (rc) return rc;
+  const int* skip = &p->state->done;
+  int64_t nblocks = 0;
+  for (int it = 0; it <= p->max_iter; ++it) {
+    HELM_PK("residual_fp64", launch_residual(p->dim, p->n, p->h, p->omega, (const double2*)f, (const double2*)u, p->rbuf, p->sums,
+                            &nblocks, skip, p->stream));
+    HELM_PK("residual_finalize", launch_residual_finalize(p->sums, nblocks, p->state, it == p->max_iter, p->stream));
+    if (it == p->max_iter) break;
+    rc = solve_core(p, p->rbuf, 0, u, kOutAccumC128, 1.0, skip, nullptr, nullptr, nullptr);
+    if (rc) return rc;
+  }
+  return HELM_OK;
+}
+
+int alloc_buffers_2d(helm_plan* p) {
+  const int64_t nx = p->n[0], n1 = p->n[1], N = nx * n1;
+  const size_t cb = cbytes(p->prec);
+  int rc;
+  p->nwarps = (n1 + 31) / 32;
+  p->face_len = nx;
+  if ((rc = dev_alloc(p, &p->fhat, N * cb)) || (rc = dev_alloc(p, &p->cbuf, N * cb)) ||
+      (rc = dev_alloc(p, &p->dbuf, N * cb)) || (rc = dev_alloc(p, &p->partial, 2 * p->nwarps * nx * cb)) ||
+      (rc = dev_alloc(p, &p->faces, 8 * nx * cb)))
+    return rc;
+  return HELM_OK;
+}
+
+int alloc_refine(helm_plan* p) {
+  int64_t N = p->n[0] * p->n[1] * p->n[2];
+  int rc;
+  if (p->dtype != HELM_C64_REFINED) {
+    rc = dev_alloc(p, (void**)&p->state, sizeof(RefineState));
+    return rc;
+  }
+  if ((rc = dev_alloc(p, (void**)&p->rbuf, N * sizeof(float2))) ||
+      (rc = dev_alloc(p, (void**)&p->sums, ((N + 255) / 256) * 2 * sizeof(double))) ||
+      (rc = dev_alloc(p, (void**)&p->state, sizeof(RefineState))))
+    return rc;
+  return HELM_OK;
+}
+
+void destroy_plan(helm_plan* p) {
+  if (!p) return;
+  free_axis(p->axo);
+  free_axis(p->axi);
+  cudaFree(p->fhat);
+  cudaFree(p->cbuf);
+  cudaFree(p->dbuf);
+  cudaFree(p->partial);
+  cudaFree(p->faces);
+  cudaFree(p->rbuf);
+  cudaFree(p->sums);
+  cudaFree(p->state);
+  cudaFree(p->host_f);
+  cudaFree(p->host_u);
+  free_plan3d(p->p3);
+  p->prof.destroy();
+  delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+int helm_plan_2d(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy, double omega, int dtype) {
+  if (!out) return HELM_EINVAL;
+  *out = nullptr;
+  if (nx < 3 || ny < 3 || !(hx > 0) || !(hy > 0) || !std::isfinite(hx) || !std::isfinite(hy)) return HELM_EINVAL;
+  if (int rc = validate_common(omega, dtype)) return rc;
+  auto t0 = std::chrono::steady_clock::now();
+  helm_plan* p = new (std::nothrow) helm_plan();
+  if (!p) return HELM_ENOMEM;
+  p->dim = 2;
+  p->n[0] = nx;
+  p->n[1] = ny;
+  p->n[2] = 1;
+  p->h[0] = hx;
+  p->h[1] = hy;
+  p->omega = omega;
+  p->dtype = dtype;
+  p->prec = dtype == HELM_C128 ? kPrecF64 : kPrecF32;
+  DftPlan dp;
+  dft_factor(ny, &dp);
+  int dev = 0, smem = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return HELM_ECUDA;
+  }
+  if (!dft_supported(dp, cbytes(p->prec), smem)) {
+    delete p;
+    return HELM_EUNSUPPORTED;
+  }
+  int rc = build_axis(p, p->axo, ny, hy, omega);
+  if (!rc) rc = alloc_buffers_2d(p);
+  if (!rc) rc = alloc_refine(p);
+  if (rc) {
+    destroy_plan(p);
+    return rc;
+  }
+  p->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  *out = p;
+  return HELM_OK;
+}
+
+int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx, double hy, double hz,
+                 double omega, int dtype) {
+  if (!out) return HELM_EINVAL;
+  *out = nullptr;
+  if (nx < 3 || ny < 3 || nz < 3 || !(hx > 0) || !(hy > 0) || !(hz > 0) || !std::isfinite(hx) ||
+      !std::isfinite(hy) || !std::isfinite(hz))
+    return HELM_EINVAL;
+  if (int rc = validate_common(omega, dtype)) return rc;
+  auto t0 = std::chrono::steady_clock::now();
+  helm_plan* p = new (std::nothrow) helm_plan();
+  if (!p) return HELM_ENOMEM;
+  p->dim = 3;
+  p->n[0] = nx;
+  p->n[1] = ny;
+  p->n[2] = nz;
+  p->h[0] = hx;
+  p->h[1] = hy;
+  p->h[2] = hz;
+  p->omega = omega;
+  p->dtype = dtype;
+  p->prec = dtype == HELM_C128 ? kPrecF64 : kPrecF32;
+  int smem = 0, dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return HELM_ECUDA;
+  }
+  if (nz > 1024 || ny > 1024 ||
+      (size_t)(6 * nx + 2 * 32 * 32) * cbytes(p->prec) > (size_t)smem) {
+    delete p;
+    return HELM_EUNSUPPORTED;
+  }
+  int rc = build_axis(p, p->axo, ny, hy, omega);
+  if (!rc) rc = build_axis(p, p->axi, nz, hz, omega);
+  if (!rc) {
+    DftPlan a = p->axo.dft, b = p->axi.dft;
+    if (!dft_supported(a, cbytes(p->prec), smem) || !dft_supported(b, cbytes(p->prec), smem)) rc = HELM_EUNSUPPORTED;
+  }
+  if (!rc) {
+    cudaError_t ce = plan3d_init(p->p3, p->prec, p->n, p->h, omega, p->axo, p->axi, &p->bytes);
+    if (ce == cudaErrorMemoryAllocation) rc = HELM_ENOMEM;
+    else if (ce != cudaSuccess) rc = cuda_fail(p, ce, "plan3d_init");
+  }
+  if (!rc) rc = alloc_refine(p);
+  if (rc) {
+    destroy_plan(p);
+    return rc;
+  }
+  p->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  *out = p;
+  return HELM_OK;
+}
+
+int helm_set_stream(helm_plan_t p, void* s) {
+  if (!p) return HELM_EINVAL;
+  p->stream = (cudaStream_t)s;
+  return HELM_OK;
+}
+
+int helm_set_refinement(helm_plan_t p, double tol, int max_iter) {
+  if (!p || !(tol >= 0) || max_iter < 1 || max_iter > 15) return HELM_EINVAL;
+  p->tol = tol;
+  p->max_iter = max_iter;
+  return HELM_OK;
+}
+
+int helm_solve(helm_plan_t p, const void* f, void* u) {
+  if (!p || !f || !u || f == u) return HELM_EINVAL;
+  return run_solve(p, f, u, nullptr, nullptr, nullptr);
+}
+
+int helm_solve_debug(helm_plan_t p, const void* f, void* u, void* fhat, void* v_b, void* w_b) {
+  if (!p || !f || !u || f == u) return HELM_EINVAL;
+  return run_solve(p, f, u, fhat, v_b, w_b);
+}
+
+int helm_solve_host(helm_plan_t p, const void* f_host, void* u_host) {
+  if (!p || !f_host || !u_host) return HELM_EINVAL;
+  const int64_t N = p->n[0] * p->n[1] * p->n[2];
+  const size_t eb = p->dtype == HELM_C64_RAW ? sizeof(float2) : sizeof(double2);
+  int rc;
+  if (!p->host_f) {
+    if ((rc = dev_alloc(p, (void**)&p->host_f, N * eb)) || (rc = dev_alloc(p, (void**)&p->host_u, N * eb))) return rc;
+  }
+  HELM_CK(cudaMemcpyAsync(p->host_f, f_host, N * eb, cudaMemcpyHostToDevice, p->stream));
+  rc = run_solve(p, p->host_f, p->host_u, nullptr, nullptr, nullptr);
+  if (rc) return rc;
+  HELM_CK(cudaMemcpyAsync(u_host, p->host_u, N * eb, cudaMemcpyDeviceToHost, p->stream));
+  HELM_CK(cudaStreamSynchronize(p->stream));
+  return HELM_OK;
+}
+
+int helm_get_info(helm_plan_t p, helm_info* info) {
+  if (!p || !info) return HELM_EINVAL;
+  std::memset(info, 0, sizeof(*info));
+  HELM_CK(cudaStreamSynchronize(p->stream));
+  RefineState s{};
+  HELM_CK(cudaMemcpy(&s, p->state, sizeof(s), cudaMemcpyDeviceToHost));
+  info->dim = p->dim;
+  info->dtype = p->dtype;
+  for (int k = 0; k < 3; ++k) info->n[k] = p->n[k];
+  info->iterations = p->dtype == HELM_C64_REFINED ? std::max(0, s.iters - 1) : 0;
+  info->converged = p->dtype == HELM_C64_REFINED ? s.converged : 1;
+  for (int k = 0; k < 16 && k < s.iters; ++k) info->residual[k] = s.resid[k];
+  info->plan_seconds = p->plan_seconds;
+  info->tol = p->tol;
+  info->max_iter = p->max_iter;
+  info->n_dft_stages = p->axo.dft.nstages;
+  info->device_bytes = p->bytes;
+  if (p->dtype == HELM_C64_REFINED && !s.converged) return HELM_ENOTCONV;
+  return HELM_OK;
+}
+
+int helm_destroy(helm_plan_t p) {
+  if (!p) return HELM_OK;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  destroy_plan(p);
+  return HELM_OK;
+}
+
+const char* helm_status_string(int s) {
+  switch (s) {
+    case HELM_OK: return "HELM_OK";
+    case HELM_EINVAL: return "HELM_EINVAL: invalid argument";
+    case HELM_ENOMEM: return "HELM_ENOMEM: allocation failed";
+    case HELM_ECUDA: return "HELM_ECUDA: CUDA runtime error";
+    case HELM_ENOTCONV: return "HELM_ENOTCONV: refinement did not reach the tolerance";
+    case HELM_ETIMEOUT: return "HELM_ETIMEOUT: bounded device wait gave up";
+    case HELM_EUNSUPPORTED: return "HELM_EUNSUPPORTED: size not supported by the kernels";
+    case HELM_ENUMERIC: return "HELM_ENUMERIC: plan eigen-data failed";
+    default: return "unknown helm status";
+  }
+}
+
+const char* helm_last_error(helm_plan_t p) { return p ? p->err.c_str() : ""; }
+
+int helm_set_profiling(helm_plan_t p, int enable) {
+  if (!p) return HELM_EINVAL;
+  p->prof.on = enable != 0;
+  p->prof.reset();
+  return HELM_OK;
+}
+
+int helm_get_profile(helm_plan_t p, helm_profile_entry* out, int max_entries) {
+  if (!p || (max_entries > 0 && !out)) return HELM_EINVAL;
+  HELM_CK(cudaStreamSynchronize(p->stream));
+  std::vector<double> ms(p->prof.names.size(), 0.0);
+  std::vector<int> cnt(p->prof.names.size(), 0);
+  for (auto& m : p->prof.marks) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, m.a, m.b) == cudaSuccess) {
+      ms[m.name] += t;
+      cnt[m.name] += 1;
+    }
+  }
+  cudaGetLastError();
+  int k = 0;
+  for (size_t i = 0; i < ms.size() && k < max_entries; ++i) {
+    if (!cnt[i]) continue;
+    std::memset(&out[k], 0, sizeof(out[k]));
+    std::strncpy(out[k].name, p->prof.names[i].c_str(), sizeof(out[k].name) - 1);
+    out[k].launches = cnt[i];
+    out[k].total_ms = ms[i];
+    ++k;
+  }
+  p->prof.reset();
+  return k;
+}
+
+int helm_abc_eigen(int64_t n, double h, double omega, double* lam, double* sigma, int8_t* parity) {
+  if (!lam || !sigma || !parity) return HELM_EINVAL;
+  return abc_eigen(n, h, omega, lam, sigma, parity);
+}
+
+int helm_dft_factor(int64_t n, int32_t* radices, int32_t max_stages) {
+  DftPlan p;
+  int ns = dft_factor(n, &p);
+  if (radices)
+    for (int i = 0; i < ns && i < max_stages; ++i) radices[i] = p.radix[i];
+  return ns;
+}
+
+}  // extern "C"

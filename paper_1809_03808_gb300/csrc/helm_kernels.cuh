@@ -1,0 +1,123 @@
+// Device helpers shared by the sm_103a kernels of the Helmholtz fast solver.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "helm_internal.h"
+
+namespace helm {
+
+template <typename T>
+struct cpx;
+template <>
+struct cpx<float> {
+  using type = float2;
+};
+template <>
+struct cpx<double> {
+  using type = double2;
+};
+
+template <typename C>
+__device__ __forceinline__ C mk(double re, double im) {
+  C c;
+  c.x = (decltype(c.x))re;
+  c.y = (decltype(c.y))im;
+  return c;
+}
+template <typename C, typename S>
+__device__ __forceinline__ C cvt(S s) {
+  C c;
+  c.x = (decltype(c.x))s.x;
+  c.y = (decltype(c.y))s.y;
+  return c;
+}
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) {
+  a.x += b.x;
+  a.y += b.y;
+  return a;
+}
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) {
+  a.x -= b.x;
+  a.y -= b.y;
+  return a;
+}
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+// a * conj(b)
+template <typename C>
+__device__ __forceinline__ C cmulc(C a, C b) {
+  C r;
+  r.x = a.x * b.x + a.y * b.y;
+  r.y = a.y * b.x - a.x * b.y;
+  return r;
+}
+template <typename C, typename T>
+__device__ __forceinline__ C cscale(C a, T s) {
+  a.x *= s;
+  a.y *= s;
+  return a;
+}
+// 1 / a, scaled so that neither |a|^2 over- nor under-flows (Smith's method).
+template <typename C>
+__device__ __forceinline__ C crecip(C a) {
+  using T = decltype(a.x);
+  C r;
+  if (fabs(a.x) >= fabs(a.y)) {
+    T q = a.y / a.x;
+    T d = a.x + a.y * q;
+    T inv = T(1) / d;
+    r.x = inv;
+    r.y = -q * inv;
+  } else {
+    T q = a.x / a.y;
+    T d = a.x * q + a.y;
+    T inv = T(1) / d;
+    r.x = q * inv;
+    r.y = -inv;
+  }
+  return r;
+}
+
+template <typename C>
+__device__ __forceinline__ C shfl_down(C v, int off) {
+  v.x = __shfl_down_sync(0xffffffffu, v.x, off);
+  v.y = __shfl_down_sync(0xffffffffu, v.y, off);
+  return v;
+}
+template <typename C>
+__device__ __forceinline__ C warp_sum(C v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = cadd(v, shfl_down(v, off));
+  return v;
+}
+
+// Line matrix T = K + s M along the tridiagonal axis (eqs. matrixK/matrixM;
+// K with absorbing corners 1 - i w h).  diag in the interior, diag at both
+// ends, constant off-diagonal.
+template <typename C>
+struct LineCoef {
+  C a;   // interior diagonal
+  C ac;  // end diagonal (absorbing corner)
+  C b;   // off-diagonal
+};
+
+template <typename C>
+__device__ __forceinline__ LineCoef<C> line_coef(double sre, double sim, double h, double omega) {
+  LineCoef<C> c;
+  c.a = mk<C>(sre * (4.0 * h / 6.0) + 2.0 / h, sim * (4.0 * h / 6.0));
+  c.ac = mk<C>(sre * (2.0 * h / 6.0) + 1.0 / h, sim * (2.0 * h / 6.0) - omega);
+  c.b = mk<C>(sre * (h / 6.0) - 1.0 / h, sim * (h / 6.0));
+  return c;
+}
+
+}  // namespace helm

@@ -1,0 +1,57 @@
+// Host launchers and argument blocks for the solve kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "helm_internal.h"
+
+namespace helm {
+
+// Arguments of the 2D per-mode tridiagonal kernels (device pointers to the
+// x1-axis eigen-data, FP64).
+struct Solve2DArgs {
+  int64_t nx;     // points along the tridiagonal axis
+  int64_t n1;     // x1 length (modes)
+  double hx;      // tridiagonal-axis spacing
+  double h1;      // x1 spacing
+  double omega;
+  const double* lamB;
+  const double* muB;
+  const double* lamA;
+  const double* sigA;
+  const double* parA;
+  const double* tw;
+};
+
+cudaError_t launch_tri2d(int prec, int step, const void* fhat, void* cbuf, void* dbuf, void* partial,
+                         const void* faces, const Solve2DArgs& a, const int* skip, cudaStream_t st);
+cudaError_t launch_reduce_faces(int prec, const void* partial, void* out, int64_t nx, int64_t nwarps,
+                                double scale, const int* skip, cudaStream_t st);
+cudaError_t launch_apply_cbb(int prec, const void* in, const void* in2, void* out, int64_t nx, double hx,
+                             double h1, double omega, double p, const int* skip, cudaStream_t st);
+
+// Refinement state kept on the device (one per plan).
+struct RefineState {
+  int done;         // set when ||r||/||f|| <= tol; later sweeps skip their kernels
+  int iters;        // residual evaluations performed
+  int converged;
+  int pad;
+  double tol;
+  double fnorm2;
+  double resid[16];
+};
+
+// r = f - A u in FP64 (eq. A2D / A3D), r stored as complex64, per-block sums
+// of |r|^2 and |f|^2 into `sums` (2 doubles per block).  Returns the number of
+// blocks used through *nblocks.
+cudaError_t launch_residual(int dim, const int64_t* n, const double* h, double omega, const double2* f,
+                            const double2* u, float2* r, double* sums, int64_t* nblocks, const int* skip,
+                            cudaStream_t st);
+// Reduce the block sums, record ||r||/||f|| as the next residual of *state,
+// set state->done when it is <= tol or when `last` is set.
+cudaError_t launch_residual_finalize(const double* sums, int64_t nblocks, RefineState* state, int last,
+                                     cudaStream_t st);
+
+}  // namespace helm

@@ -1,0 +1,483 @@
+// 3D solve (Section 5): the three steps along the outer periodic axis, each
+// per-mode block solve H_A^-1 / H_B^-1 (eqs. HA3D, HB3D) done by the 2D fast
+// solver on the remaining plane (Section 5.1.2, eqs. A2D2, B2D2 and their
+// auxiliaries A2D2aux, B2D2aux).
+//
+// Array [nx][ny][nz], z fastest.  Outer periodic axis ("x1") = y, inner
+// periodic axis ("x2") = z, tridiagonal axis = x.  After the 2D DFT over
+// (y, z) the unknowns are indexed (x, l, m): l outer mode, m inner mode.
+//
+// k_plane3d: one CTA per outer mode l, one thread per inner mode m.  The CTA
+// runs the inner Steps 1-3 for plane l (the 2D algorithm of Section 4.2 with
+// mass shift p = w^2 - Lam_{1,l}; the absorbing corners keep the physical w),
+// reducing the inner boundary rows over m in shared memory.  Its output is the
+// inner-mode-space solution y3(x, l, m), written over the Thomas scratch.
+// The outer boundary rows are then reduced over l by k_reduce_outer.
+#include <algorithm>
+#include <type_traits>
+
+#include "helm_dft.h"
+#include "helm_kernels.cuh"
+#include "helm_solve3d.h"
+
+namespace helm {
+
+namespace {
+
+struct Plane3DArgs {
+  int64_t nx, ny, nz;
+  double hx, hy, hz, omega;
+  // outer axis (y) eigen-data
+  const double *lamBo, *muBo, *lamAo, *sigAo, *parAo, *two;
+  // inner axis (z) eigen-data
+  const double *lamBi, *muBi, *lamAi, *sigAi, *parAi, *twi;
+};
+
+constexpr int XC = 32;  // rows per reduction chunk
+
+template <typename C>
+struct ThomasRow {
+  LineCoef<C> k;
+  int n;
+  C c_prev, d_prev;
+  __device__ __forceinline__ void step(int ix, C r, C& c, C& d) {
+    if (ix == 0) {
+      C inv = crecip(k.ac);
+      c = cmul(k.b, inv);
+      d = cmul(r, inv);
+    } else {
+      C a = (ix == n - 1) ? k.ac : k.a;
+      C den = csub(a, cmul(k.b, c_prev));
+      C inv = crecip(den);
+      c = cmul(k.b, inv);
+      d = cmul(csub(r, cmul(k.b, d_prev)), inv);
+    }
+    c_prev = c;
+    d_prev = d;
+  }
+};
+
+// Inner C_bb of the plane problem (eq. Cbb for the auxiliary B2D2aux):
+//   c_1 = D11 M v_1 + E11 K v_1 + D1n M v_n + E1n K v_n  (and symmetric c_n),
+//   D11 = (1 + i w hz)/hz - p hz/3, D1n = -1/hz - p hz/6, E11 = hz/3, E1n = hz/6,
+// M, K along x; p = w^2 - Lam_{1,l} (complex for outer A modes).
+template <typename C>
+__device__ void plane_cbb(const C* v, const C* w2, C* out, int nx, double hx, double hz, double omega,
+                          double pre, double pim) {
+  for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
+    auto get = [&](int face, int j) -> C {
+      C t = v[face * nx + j];
+      if (w2) t = cadd(t, w2[face * nx + j]);
+      return t;
+    };
+    const bool end = (ix == 0 || ix == nx - 1);
+    const double md = end ? 2.0 * hx / 6.0 : 4.0 * hx / 6.0, mo = hx / 6.0;
+    const double kdr = end ? 1.0 / hx : 2.0 / hx, kdi = end ? -omega : 0.0, ko = -1.0 / hx;
+    C Mv[2], Kv[2];
+    for (int f = 0; f < 2; ++f) {
+      C v0 = get(f, ix);
+      C vm = ix > 0 ? get(f, ix - 1) : mk<C>(0, 0);
+      C vp = ix < nx - 1 ? get(f, ix + 1) : mk<C>(0, 0);
+      C nb = cadd(vm, vp);
+      Mv[f] = cadd(cscale(v0, (decltype(v0.x))md), cscale(nb, (decltype(v0.x))mo));
+      Kv[f] = cadd(cmul(v0, mk<C>(kdr, kdi)), cscale(nb, (decltype(v0.x))ko));
+    }
+    const C D11 = mk<C>(1.0 / hz - pre * hz / 3.0, omega - pim * hz / 3.0);
+    const C D1n = mk<C>(-1.0 / hz - pre * hz / 6.0, -pim * hz / 6.0);
+    const auto E11 = (decltype(D11.x))(hz / 3.0), E1n = (decltype(D11.x))(hz / 6.0);
+    out[ix] = cadd(cadd(cmul(D11, Mv[0]), cscale(Kv[0], E11)), cadd(cmul(D1n, Mv[1]), cscale(Kv[1], E1n)));
+    out[nx + ix] = cadd(cadd(cmul(D1n, Mv[0]), cscale(Kv[0], E1n)), cadd(cmul(D11, Mv[1]), cscale(Kv[1], E11)));
+  }
+}
+
+// OSTEP 1: G = fhat / mu_l                        (outer Step 1, eq. 3dHBs1)
+// OSTEP 2: G = chat_1 + par_l chat_n, outer A mode (outer Step 2, eq. step2-2-3d)
+// OSTEP 3: G = (fhat + dhat_1 + e^{+2 pi i l/ny} dhat_n) / mu_l  (eq. 3dHBs3)
+template <typename T, int OSTEP>
+__global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* __restrict__ fhat,
+                                                  typename cpx<T>::type* __restrict__ cbuf,
+                                                  typename cpx<T>::type* __restrict__ dbuf,
+                                                  const typename cpx<T>::type* __restrict__ gfaces,
+                                                  Plane3DArgs a, const int* __restrict__ skip) {
+  using C = typename cpx<T>::type;
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nx = (int)a.nx;
+  const int64_t ny = a.ny, nz = a.nz;
+  const int nw = blockDim.x >> 5;
+  C* vin = reinterpret_cast<C*>(smem_raw);  // [2][nx]
+  C* win = vin + 2 * nx;                     // [2][nx]
+  C* cin = win + 2 * nx;                     // [2][nx]
+  C* red = cin + 2 * nx;                     // [nw][2][XC]
+  const int64_t l = blockIdx.x;
+  const int m = threadIdx.x;
+  const bool act = m < nz;
+  const int64_t mc = act ? m : 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double w2 = a.omega * a.omega;
+  // outer-mode quantities
+  double lo_re, lo_im;
+  if (OSTEP == 2) {
+    lo_re = a.lamAo[2 * l];
+    lo_im = a.lamAo[2 * l + 1];
+  } else {
+    lo_re = a.lamBo[l];
+    lo_im = 0.0;
+  }
+  const T gscale = (OSTEP == 2) ? T(1) : (T)(1.0 / a.muBo[l]);
+  const T paro = (T)a.parAo[l];
+  const C two_l = mk<C>(a.two[2 * l], a.two[2 * l + 1]);  // e^{-2 pi i l / ny}
+  // inner-mode quantities
+  const double lBi = a.lamBi[mc];
+  const C twm = mk<C>(a.twi[2 * mc], a.twi[2 * mc + 1]);
+  const T invmu_i = (T)(1.0 / a.muBi[mc]);
+  const T pari = (T)a.parAi[mc];
+  const C sigi = mk<C>(a.sigAi[2 * mc], a.sigAi[2 * mc + 1]);
+  const int64_t plane = l * nz + mc;                 // offset inside an x slab
+  const int64_t xs = ny * nz;                         // x stride
+  const C* g1 = gfaces;                               // [2][nx][nz]
+  const C* gn = gfaces ? gfaces + (int64_t)nx * nz : nullptr;
+  auto G = [&](int ix) -> C {
+    if (OSTEP == 1) return cscale(fhat[ix * xs + plane], gscale);
+    if (OSTEP == 2) return cadd(g1[(int64_t)ix * nz + mc], cscale(gn[(int64_t)ix * nz + mc], paro));
+    C v = cadd(fhat[ix * xs + plane], g1[(int64_t)ix * nz + mc]);
+    v = cadd(v, cmulc(gn[(int64_t)ix * nz + mc], two_l));
+    return cscale(v, gscale);
+  };
+  ThomasRow<C> thB, thA;
+  thB.k = line_coef<C>(lo_re + lBi - w2, lo_im, a.hx, a.omega);
+  thB.n = nx;
+  thA.k = line_coef<C>(lo_re + a.lamAi[2 * mc] - w2, lo_im + a.lamAi[2 * mc + 1], a.hx, a.omega);
+  thA.n = nx;
+  const double pre = w2 - lo_re, pim = -lo_im;
+
+  // ---- generic sweep: forward with rhs(ix), backward with emit(ix, x) ----
+  auto forward = [&](ThomasRow<C>& th, auto rhs) {
+    if (!act) return;
+    for (int ix = 0; ix < nx; ++ix) {
+      C c, d;
+      th.step(ix, rhs(ix), c, d);
+      cbuf[ix * xs + plane] = c;
+      dbuf[ix * xs + plane] = d;
+    }
+  };
+  // backward sweep reducing (s1, sn) contributions over m into out[2][nx]
+  auto backward_reduce = [&](auto contrib, C* out, T scale) {
+    C x = mk<C>(0, 0);
+    for (int x0 = nx - 1; x0 >= 0; x0 -= XC) {
+      const int x1 = max(0, x0 - XC + 1);
+      for (int ix = x0; ix >= x1; --ix) {
+        if (act) {
+          C d = dbuf[ix * xs + plane];
+          x = (ix == nx - 1) ? d : csub(d, cmul(cbuf[ix * xs + plane], x));
+        }
+        C s1, sn;
+        contrib(act, x, s1, sn);
+        s1 = warp_sum(s1);
+        sn = warp_sum(sn);
+        if (lane == 0) {
+          red[(warp * 2 + 0) * XC + (x0 - ix)] = s1;
+          red[(warp * 2 + 1) * XC + (x0 - ix)] = sn;
+        }
+      }
+      __syncthreads();
+      const int cnt = x0 - x1 + 1;
+      for (int t = threadIdx.x; t < 2 * cnt; t += blockDim.x) {
+        const int face = t / cnt, j = t - face * cnt;
+        C acc = mk<C>(0, 0);
+        for (int w = 0; w < nw; ++w) acc = cadd(acc, red[(w * 2 + face) * XC + j]);
+        out[face * nx + (x0 - j)] = cscale(acc, scale);
+      }
+      __syncthreads();
+    }
+  };
+
+  // inner Step 1: B-aux solve, reduce to inner faces v_in
+  forward(thB, [&](int ix) { return cscale(G(ix), invmu_i); });
+  backward_reduce(
+      [&](bool ac, C x, C& s1, C& sn) {
+        s1 = ac ? x : mk<C>(0, 0);
+        sn = ac ? cmul(x, twm) : mk<C>(0, 0);
+      },
+      vin, (T)(1.0 / (double)nz));
+  plane_cbb(vin, (const C*)nullptr, cin, nx, a.hx, a.hz, a.omega, pre, pim);
+  __syncthreads();
+  // inner Step 2: A solve on the generated rhs, reduce to w_in
+  forward(thA, [&](int ix) { return cadd(cin[ix], cscale(cin[nx + ix], pari)); });
+  backward_reduce(
+      [&](bool ac, C x, C& s1, C& sn) {
+        C t = ac ? cmul(x, sigi) : mk<C>(0, 0);
+        s1 = t;
+        sn = cscale(t, pari);
+      },
+      win, T(1));
+  plane_cbb(vin, win, cin, nx, a.hx, a.hz, a.omega, pre, pim);
+  __syncthreads();
+  // inner Step 3: corrected B-aux solve, y3 written over the scratch
+  forward(thB, [&](int ix) {
+    C v = cadd(G(ix), cin[ix]);
+    v = cadd(v, cmulc(cin[nx + ix], twm));
+    return cscale(v, invmu_i);
+  });
+  if (act) {
+    C x = mk<C>(0, 0);
+    for (int ix = nx - 1; ix >= 0; --ix) {
+      C d = dbuf[ix * xs + plane];
+      x = (ix == nx - 1) ? d : csub(d, cmul(cbuf[ix * xs + plane], x));
+      dbuf[ix * xs + plane] = x;
+    }
+  }
+}
+
+// Outer boundary rows (eq. 3dBs1 / step2-3-3d) in inner-mode space:
+//   out[face][x][m] = sum_l wgt_face(l) * y3(x, l, m)
+// step 1: wgt = (1/ny, e^{-2 pi i l/ny}/ny); step 2: wgt = (sigma_l, par_l sigma_l).
+template <typename T, int OSTEP>
+__global__ void k_reduce_outer(const typename cpx<T>::type* __restrict__ y3, typename cpx<T>::type* __restrict__ out,
+                               Plane3DArgs a, const int* __restrict__ skip) {
+  using C = typename cpx<T>::type;
+  if (skip && *skip) return;
+  const int64_t ny = a.ny, nz = a.nz;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.nx * nz) return;
+  const int64_t ix = i / nz, m = i - ix * nz;
+  C s1 = mk<C>(0, 0), sn = mk<C>(0, 0);
+  for (int64_t l = 0; l < ny; ++l) {
+    const C v = y3[(ix * ny + l) * nz + m];
+    if (OSTEP == 1) {
+      s1 = cadd(s1, v);
+      sn = cadd(sn, cmul(v, mk<C>(a.two[2 * l], a.two[2 * l + 1])));
+    } else {
+      const C t = cmul(v, mk<C>(a.sigAo[2 * l], a.sigAo[2 * l + 1]));
+      s1 = cadd(s1, t);
+      sn = cadd(sn, cscale(t, (decltype(t.x))a.parAo[l]));
+    }
+  }
+  if (OSTEP == 1) {
+    s1 = cscale(s1, (decltype(s1.x))(1.0 / (double)ny));
+    sn = cscale(sn, (decltype(sn.x))(1.0 / (double)ny));
+  }
+  out[i] = s1;
+  out[a.nx * nz + i] = sn;
+}
+
+// Outer C_bb on the y faces (eq. Cbb for eq. B3D - A3D): with P = M_x (x) M_z
+// and S = K_x (x) M_z + M_x (x) K_z - w^2 M_x (x) M_z on the (x, z) plane,
+//   c_1 = (hy/3) S v_1 + ((1 + i w hy)/hy) P v_1 + (hy/6) S v_n - (1/hy) P v_n,
+//   c_n = (hy/6) S v_1 - (1/hy) P v_1 + (hy/3) S v_n + ((1 + i w hy)/hy) P v_n.
+template <typename T>
+__global__ void k_outer_cbb(const typename cpx<T>::type* __restrict__ v, const typename cpx<T>::type* __restrict__ w,
+                            typename cpx<T>::type* __restrict__ out, Plane3DArgs a, const int* __restrict__ skip) {
+  using C = typename cpx<T>::type;
+  if (skip && *skip) return;
+  const int64_t nx = a.nx, nz = a.nz;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx * nz) return;
+  const int64_t ix = i / nz, iz = i - ix * nz;
+  auto ent = [&](int64_t n, double h, int64_t j, int d, double& m, double& kr, double& ki) {
+    const bool end = (j == 0 || j == n - 1);
+    if (d == 0) {
+      m = (end ? 2.0 : 4.0) * h / 6.0;
+      kr = (end ? 1.0 : 2.0) / h;
+      ki = end ? -a.omega : 0.0;
+    } else {
+      m = h / 6.0;
+      kr = -1.0 / h;
+      ki = 0.0;
+    }
+  };
+  C Sv[2] = {mk<C>(0, 0), mk<C>(0, 0)}, Pv[2] = {mk<C>(0, 0), mk<C>(0, 0)};
+  const double w2 = a.omega * a.omega;
+  for (int dx = -1; dx <= 1; ++dx) {
+    const int64_t jx = ix + dx;
+    if (jx < 0 || jx >= nx) continue;
+    double mx, kxr, kxi;
+    ent(nx, a.hx, ix, dx, mx, kxr, kxi);
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int64_t jz = iz + dz;
+      if (jz < 0 || jz >= nz) continue;
+      double mz, kzr, kzi;
+      ent(nz, a.hz, iz, dz, mz, kzr, kzi);
+      const C cs = mk<C>(kxr * mz + mx * kzr - w2 * mx * mz, kxi * mz + mx * kzi);
+      const auto cp = (decltype(cs.x))(mx * mz);
+      for (int f = 0; f < 2; ++f) {
+        C t = v[f * nx * nz + jx * nz + jz];
+        if (w) t = cadd(t, w[f * nx * nz + jx * nz + jz]);
+        Sv[f] = cadd(Sv[f], cmul(cs, t));
+        Pv[f] = cadd(Pv[f], cscale(t, cp));
+      }
+    }
+  }
+  using T2 = decltype(Sv[0].x);
+  const T2 e11 = (T2)(a.hy / 3.0), e1n = (T2)(a.hy / 6.0);
+  const C d11 = mk<C>(1.0 / a.hy, a.omega);
+  const T2 d1n = (T2)(-1.0 / a.hy);
+  out[i] = cadd(cadd(cscale(Sv[0], e11), cmul(d11, Pv[0])), cadd(cscale(Sv[1], e1n), cscale(Pv[1], d1n)));
+  out[nx * nz + i] = cadd(cadd(cscale(Sv[0], e1n), cscale(Pv[0], d1n)), cadd(cscale(Sv[1], e11), cmul(d11, Pv[1])));
+}
+
+Plane3DArgs make_args(const Plan3D& p) {
+  Plane3DArgs a;
+  a.nx = p.n[0];
+  a.ny = p.n[1];
+  a.nz = p.n[2];
+  a.hx = p.h[0];
+  a.hy = p.h[1];
+  a.hz = p.h[2];
+  a.omega = p.omega;
+  a.lamBo = p.axo->lamB;
+  a.muBo = p.axo->muB;
+  a.lamAo = p.axo->lamA;
+  a.sigAo = p.axo->sigA;
+  a.parAo = p.axo->parA;
+  a.two = p.axo->tw;
+  a.lamBi = p.axi->lamB;
+  a.muBi = p.axi->muB;
+  a.lamAi = p.axi->lamA;
+  a.sigAi = p.axi->sigA;
+  a.parAi = p.axi->parA;
+  a.twi = p.axi->tw;
+  return a;
+}
+
+template <typename T>
+cudaError_t launch_plane(int ostep, const Plan3D& p, const void* gfaces, const int* skip, cudaStream_t st) {
+  using C = typename cpx<T>::type;
+  const int bs = (int)((p.n[2] + 31) / 32 * 32);
+  const int nw = bs / 32;
+  const size_t smem = (size_t)(6 * p.n[0] + nw * 2 * XC) * sizeof(C);
+  Plane3DArgs a = make_args(p);
+  auto run = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<(unsigned)p.n[1], bs, smem, st>>>((const C*)p.fhat, (C*)p.cbuf, (C*)p.dbuf, (const C*)gfaces, a, skip);
+  };
+  if (ostep == 1) run(k_plane3d<T, 1>);
+  else if (ostep == 2) run(k_plane3d<T, 2>);
+  else run(k_plane3d<T, 3>);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_reduce_outer(int ostep, const Plan3D& p, void* out, const int* skip, cudaStream_t st) {
+  using C = typename cpx<T>::type;
+  const int bs = 256;
+  const unsigned grid = (unsigned)((p.n[0] * p.n[2] + bs - 1) / bs);
+  Plane3DArgs a = make_args(p);
+  if (ostep == 1) k_reduce_outer<T, 1><<<grid, bs, 0, st>>>((const C*)p.dbuf, (C*)out, a, skip);
+  else k_reduce_outer<T, 2><<<grid, bs, 0, st>>>((const C*)p.dbuf, (C*)out, a, skip);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_outer_cbb(const Plan3D& p, const void* v, const void* w, void* out, const int* skip, cudaStream_t st) {
+  using C = typename cpx<T>::type;
+  const int bs = 256;
+  const unsigned grid = (unsigned)((p.n[0] * p.n[2] + bs - 1) / bs);
+  k_outer_cbb<T><<<grid, bs, 0, st>>>((const C*)v, (const C*)w, (C*)out, make_args(p), skip);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t solve3d_t(Plan3D& p, const void* in, int in_is_double, void* out, int out_mode, double accum_scale,
+                      const int* skip, void* dbg_fhat, void* dbg_v, void* dbg_w, cudaStream_t st, Profiler* prof) {
+  using C = typename cpx<T>::type;
+  const int prec = std::is_same<T, double>::value ? kPrecF64 : kPrecF32;
+  const int64_t nx = p.n[0], ny = p.n[1], nz = p.n[2];
+  const int64_t F = nx * nz;  // values per outer face
+  const void* two = prec == kPrecF64 ? (const void*)p.axo->tw : (const void*)p.axo->tw32;
+  const void* twi = prec == kPrecF64 ? (const void*)p.axi->tw : (const void*)p.axi->tw32;
+  const int cmode = prec == kPrecF64 ? kOutC128 : kOutC64;
+  C* faces = (C*)p.faces;
+  C* Vh = faces;           // reduced outer rows, inner-mode space   [2][nx][nz]
+  C* v = faces + 2 * F;    // outer rows of v, physical
+  C* w = faces + 4 * F;    // outer rows of w, physical
+  C* c = faces + 6 * F;    // C_bb applied, physical
+  C* ch = faces + 8 * F;   // its inner DFT
+  cudaError_t e;
+#define CK(x)                               \
+  do {                                      \
+    if ((e = (x)) != cudaSuccess) return e; \
+  } while (0)
+#define PK(name, x)                         \
+  do {                                      \
+    ProfScope ps_(prof, name, st);          \
+    CK(x);                                  \
+  } while (0)
+  // a1: 2D DFT over (y, z): rows along z, then columns along y (in place)
+  PK("dft_z_fwd", launch_dft_rows(prec, in, in_is_double, p.fhat, cmode, nx * ny, p.axi->dft, twi, -1, 1.0, 0.0, skip, st));
+  PK("dft_y_fwd", launch_dft_cols(prec, p.fhat, prec == kPrecF64, p.fhat, cmode, nx, nz, p.axo->dft, two, -1, 1.0, 0.0, skip, st));
+  if (dbg_fhat) CK(cudaMemcpyAsync(dbg_fhat, p.fhat, nx * ny * nz * sizeof(C), cudaMemcpyDeviceToDevice, st));
+  // outer Step 1
+  PK("plane3d_step1", launch_plane<T>(1, p, nullptr, skip, st));
+  PK("reduce_outer", launch_reduce_outer<T>(1, p, Vh, skip, st));
+  CK(launch_dft_rows(prec, Vh, prec == kPrecF64, v, cmode, 2 * nx, p.axi->dft, twi, +1, 1.0 / (double)nz, 0.0, skip, st));
+  if (dbg_v) CK(cudaMemcpyAsync(dbg_v, v, 2 * F * sizeof(C), cudaMemcpyDeviceToDevice, st));
+  CK(launch_outer_cbb<T>(p, v, nullptr, c, skip, st));
+  CK(launch_dft_rows(prec, c, prec == kPrecF64, ch, cmode, 2 * nx, p.axi->dft, twi, -1, 1.0, 0.0, skip, st));
+  // outer Step 2
+  PK("plane3d_step2", launch_plane<T>(2, p, ch, skip, st));
+  PK("reduce_outer", launch_reduce_outer<T>(2, p, Vh, skip, st));
+  CK(launch_dft_rows(prec, Vh, prec == kPrecF64, w, cmode, 2 * nx, p.axi->dft, twi, +1, 1.0 / (double)nz, 0.0, skip, st));
+  if (dbg_w) CK(cudaMemcpyAsync(dbg_w, w, 2 * F * sizeof(C), cudaMemcpyDeviceToDevice, st));
+  CK(launch_outer_cbb<T>(p, v, w, c, skip, st));
+  CK(launch_dft_rows(prec, c, prec == kPrecF64, ch, cmode, 2 * nx, p.axi->dft, twi, -1, 1.0, 0.0, skip, st));
+  // outer Step 3, then the inverse 2D DFT
+  PK("plane3d_step3", launch_plane<T>(3, p, ch, skip, st));
+  PK("dft_y_inv", launch_dft_cols(prec, p.dbuf, prec == kPrecF64, p.dbuf, cmode, nx, nz, p.axo->dft, two, +1, 1.0 / (double)ny, 0.0,
+                     skip, st));
+  PK("dft_z_inv", launch_dft_rows(prec, p.dbuf, prec == kPrecF64, out, out_mode, nx * ny, p.axi->dft, twi, +1, 1.0 / (double)nz,
+                     accum_scale, skip, st));
+#undef PK
+#undef CK
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t plan3d_init(Plan3D& p, int prec, const int64_t* n, const double* h, double omega, const AxisData& axo,
+                        const AxisData& axi, size_t* bytes) {
+  p.prec = prec;
+  for (int k = 0; k < 3; ++k) {
+    p.n[k] = n[k];
+    p.h[k] = h[k];
+  }
+  p.omega = omega;
+  p.axo = &axo;
+  p.axi = &axi;
+  const size_t cb = prec == kPrecF64 ? sizeof(double2) : sizeof(float2);
+  const int64_t N = n[0] * n[1] * n[2];
+  const int64_t F = n[0] * n[2];
+  cudaError_t e;
+  void** bufs[4] = {&p.fhat, &p.cbuf, &p.dbuf, &p.faces};
+  size_t sizes[4] = {N * cb, N * cb, N * cb, 10 * F * cb};
+  for (int i = 0; i < 4; ++i) {
+    if ((e = cudaMalloc(bufs[i], sizes[i])) != cudaSuccess) {
+      cudaGetLastError();
+      return e;
+    }
+    *bytes += sizes[i];
+  }
+  p.ready = true;
+  return cudaSuccess;
+}
+
+void free_plan3d(Plan3D& p) {
+  cudaFree(p.fhat);
+  cudaFree(p.cbuf);
+  cudaFree(p.dbuf);
+  cudaFree(p.ybuf);
+  cudaFree(p.faces);
+  cudaFree(p.partial);
+  p = Plan3D{};
+}
+
+cudaError_t solve3d_core(Plan3D& p, int prec, const void* in, int in_is_double, void* out, int out_mode,
+                         double accum_scale, const int* skip, void* dbg_fhat, void* dbg_v, void* dbg_w,
+                         cudaStream_t st, Profiler* prof) {
+  if (!p.ready) return cudaErrorNotReady;
+  if (prec == kPrecF64)
+    return solve3d_t<double>(p, in, in_is_double, out, out_mode, accum_scale, skip, dbg_fhat, dbg_v, dbg_w, st, prof);
+  return solve3d_t<float>(p, in, in_is_double, out, out_mode, accum_scale, skip, dbg_fhat, dbg_v, dbg_w, st, prof);
+}
+
+}  // namespace helm

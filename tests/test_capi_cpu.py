@@ -1,0 +1,84 @@
+"""C-ABI library checks that need no GPU: it loads, exports every symbol the
+header declares, validates arguments, and its host-side plan logic (the
+absorbing-pencil eigen-data of eqs. EVP1a / EVPcondA, the DFT factorisation)
+agrees with the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def helm():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1809_03808_gb300 as h
+
+    return h
+
+
+def test_every_header_symbol_is_exported(helm):
+    hdr = open(os.path.join(ROOT, "include", "helm.h")).read()
+    names = set(re.findall(r"^\s*(?:int|const char\*)\s+(helm_\w+)\s*\(", hdr, flags=re.M))
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(helm.lib, n), n
+    assert names == set(helm.EXPORTED)
+
+
+def test_status_strings(helm):
+    for s in range(-7, 1):
+        assert helm.lib.helm_status_string(s).decode().startswith("HELM_")
+
+
+@pytest.mark.parametrize("args", [(2, 5, 0.1, 0.1, 1.0, 0), (5, 5, 0.0, 0.1, 1.0, 0), (5, 5, 0.1, 0.1, -1.0, 0),
+                                  (5, 5, 0.1, float("nan"), 1.0, 0), (5, 5, 0.1, 0.1, 1.0, 7)])
+def test_plan_rejects_bad_arguments_before_touching_the_device(helm, args):
+    import ctypes
+
+    h = ctypes.c_void_p(1234)
+    st = helm.lib.helm_plan_2d(ctypes.byref(h), *args)
+    assert st == helm.HELM_EINVAL
+    assert h.value is None
+
+
+def test_null_plan_and_destroy_null(helm):
+    assert helm.lib.helm_destroy(None) == helm.HELM_OK
+    assert helm.lib.helm_solve(None, None, None) == helm.HELM_EINVAL
+    assert helm.lib.helm_set_refinement(None, 1e-12, 3) == helm.HELM_EINVAL
+
+
+@pytest.mark.parametrize("n", [4, 9, 64, 129, 512, 1000, 1021, 4096, 8192, 6 * 49])
+def test_dft_factorisation(helm, n):
+    r = helm.helm_dft_factor(n)
+    assert int(np.prod(r)) == n
+    assert all(x >= 2 for x in r)
+
+
+@pytest.mark.parametrize("n,h,ppw", [(17, 1 / 16, 6), (129, 1 / 128, 16), (257, 1 / 256, 10), (300, 0.003, 8)])
+def test_abc_eigen_matches_dense_oracle(helm, n, h, ppw):
+    from oracle import solvers
+
+    omega = 2 * np.pi / (ppw * h)
+    lam, sig, par = helm.helm_abc_eigen(n, h, omega)
+    lo, V = solvers.abc_pencil_eig(n, h, omega)
+    scale = np.abs(lo).max()
+    # same spectrum (as a set)
+    for i, l in enumerate(lam):
+        j = int(np.argmin(np.abs(lo - l)))
+        assert abs(lo[j] - l) <= 1e-9 * scale
+        # sigma = V[1,l]^2 and parity = V[n,l]/V[1,l] for the matching eigenvector
+        assert abs(V[0, j] ** 2 - sig[i]) <= 1e-7 * abs(sig[i])
+        assert abs(V[-1, j] - par[i] * V[0, j]) <= 1e-6 * abs(V[0, j])
+    assert len(np.unique(np.round(lam, 6))) == n
+
+
+def test_abc_eigen_rejects_bad_input(helm):
+    with pytest.raises(helm.HelmError):
+        helm.helm_abc_eigen(1, 0.1, 1.0)
+    with pytest.raises(helm.HelmError):
+        helm.helm_abc_eigen(10, 0.1, 0.0)

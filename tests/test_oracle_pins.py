@@ -269,3 +269,15 @@ def test_three_step_identities(shape, axis):
     f = random_rhs(shape, 11)
     v, w, u = solvers.step_definitions(f, h, om, axis)
     assert np.linalg.norm(v + w - u) / np.linalg.norm(u) < 1e-12
+
+
+@pytest.mark.parametrize("shape,h", [((7, 9), (0.2, 0.13)), ((5, 6, 4), (0.3, 0.2, 0.25)),
+                                     ((40, 33), (0.01, 0.02)), ((3, 3, 3), (1.0, 0.5, 0.25))])
+def test_c_residual_equals_pinned_numpy_residual(shape, h):
+    """The C double-double residual (for large grids) reproduces the numpy one,
+    which is pinned to exact rational arithmetic above."""
+    u = random_rhs(shape, 1)
+    f = fem.apply_A(u, h, 3.3) + 1e-9 * random_rhs(shape, 2)
+    r1 = fem.residual_dd(f, u, h, 3.3)
+    r2 = fem.residual_dd_c(f, u, h, 3.3)
+    assert np.array_equal(r1, r2)
