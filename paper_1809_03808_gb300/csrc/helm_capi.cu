@@ -37,6 +37,9 @@ struct helm_plan {
   void* dbuf = nullptr;
   void* partial = nullptr;
   void* faces = nullptr;  // v (2 faces), w (2 faces), c (2 faces), scratch
+  void* ustartB = nullptr;  // 2D: pivot entering each chunk, B-type lines
+  void* ustartA = nullptr;  // 2D: same for A-type lines
+  void* rec = nullptr;      // 2D: chunk records
   int64_t face_len = 0;   // values per face
   int64_t nwarps = 0;
   float2* rbuf = nullptr;
@@ -154,6 +157,14 @@ int validate_common(double omega, int dtype) {
 
 size_t cbytes(int prec) { return prec == kPrecF64 ? sizeof(double2) : sizeof(float2); }
 
+Solve2DArgs args2d(const helm_plan* p) {
+  const AxisData& ax = p->axo;
+  Solve2DArgs a{p->n[0], p->n[1], p->h[0], p->h[1], p->omega, ax.lamB, ax.muB, ax.lamA, ax.sigA, ax.parA, ax.tw, 0, 0};
+  a.ch = p->prec == kPrecF64 ? kChunkF64 : kChunkF32;
+  a.nchunks = (p->n[0] + a.ch - 1) / a.ch;
+  return a;
+}
+
 // ---------------------------------------------------------------------------
 // 2D solve: in (complex128 if in_is_double) -> out per out_mode.
 // ---------------------------------------------------------------------------
@@ -169,23 +180,23 @@ int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int 
   void* fv = faces;                 // v_1, v_n
   void* fw = faces + 2 * nx * cb;   // w_1, w_n
   void* fc = faces + 4 * nx * cb;   // c (or d)
-  Solve2DArgs a{nx, n1, p->h[0], p->h[1], p->omega, ax.lamB, ax.muB, ax.lamA, ax.sigA, ax.parA, ax.tw};
+  Solve2DArgs a = args2d(p);
   const int fhat_mode = prec == kPrecF64 ? kOutC128 : kOutC64;
   // a1: forward DFT along x1 (eq. step1FFTfcoeff), f_hat kept for Step 3
   HELM_PK("dft_fwd", launch_dft_rows(prec, in, in_is_double, p->fhat, fhat_mode, nx, ax.dft, tw, -1, 1.0, 0.0, skip, st));
   if (dbg_fhat) HELM_CK(cudaMemcpyAsync(dbg_fhat, p->fhat, nx * n1 * cb, cudaMemcpyDeviceToDevice, st));
   // a2: Step 1
-  HELM_PK("tri_step1", launch_tri2d(prec, 1, p->fhat, p->cbuf, p->dbuf, p->partial, nullptr, a, skip, st));
+  HELM_PK("tri_step1", launch_tri2d(prec, 1, p->fhat, nullptr, p->ustartB, p->rec, nullptr, p->partial, a, skip, st));
   HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fv, nx, p->nwarps, 1.0 / (double)n1, skip, st));
   if (dbg_v) HELM_CK(cudaMemcpyAsync(dbg_v, fv, 2 * nx * cb, cudaMemcpyDeviceToDevice, st));
   // a3: Step 2
   HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, nullptr, fc, nx, p->h[0], p->h[1], p->omega, p->omega * p->omega, skip, st));
-  HELM_PK("tri_step2", launch_tri2d(prec, 2, nullptr, p->cbuf, p->dbuf, p->partial, fc, a, skip, st));
+  HELM_PK("tri_step2", launch_tri2d(prec, 2, nullptr, fc, p->ustartA, p->rec, nullptr, p->partial, a, skip, st));
   HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fw, nx, p->nwarps, 1.0, skip, st));
   if (dbg_w) HELM_CK(cudaMemcpyAsync(dbg_w, fw, 2 * nx * cb, cudaMemcpyDeviceToDevice, st));
   // a4: Step 3
   HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, fw, fc, nx, p->h[0], p->h[1], p->omega, p->omega * p->omega, skip, st));
-  HELM_PK("tri_step3", launch_tri2d(prec, 3, p->fhat, p->cbuf, p->dbuf, p->partial, fc, a, skip, st));
+  HELM_PK("tri_step3", launch_tri2d(prec, 3, p->fhat, fc, p->ustartB, p->rec, p->dbuf, nullptr, a, skip, st));
   // a5: inverse DFT along x1 (eq. step3IFFTz3coeff)
   HELM_PK("dft_inv", launch_dft_rows(prec, p->dbuf, prec == kPrecF64, out, out_mode, nx, ax.dft, tw, +1, 1.0 / (double)n1,
                           accum_scale, skip, st));
@@ -228,10 +239,17 @@ int alloc_buffers_2d(helm_plan* p) {
   int rc;
   p->nwarps = (n1 + 31) / 32;
   p->face_len = nx;
-  if ((rc = dev_alloc(p, &p->fhat, N * cb)) || (rc = dev_alloc(p, &p->cbuf, N * cb)) ||
-      (rc = dev_alloc(p, &p->dbuf, N * cb)) || (rc = dev_alloc(p, &p->partial, 2 * p->nwarps * nx * cb)) ||
-      (rc = dev_alloc(p, &p->faces, 8 * nx * cb)))
+  const Solve2DArgs a = args2d(p);
+  const size_t nrec = (size_t)a.nchunks * n1;
+  if ((rc = dev_alloc(p, &p->fhat, N * cb)) || (rc = dev_alloc(p, &p->dbuf, N * cb)) ||
+      (rc = dev_alloc(p, &p->partial, 2 * p->nwarps * nx * cb)) || (rc = dev_alloc(p, &p->faces, 8 * nx * cb)) ||
+      (rc = dev_alloc(p, &p->ustartB, nrec * cb)) || (rc = dev_alloc(p, &p->ustartA, nrec * cb)) ||
+      (rc = dev_alloc(p, &p->rec, nrec * chunk_record_bytes(p->prec))))
     return rc;
+  // pivots entering each chunk (rhs independent, once per plan)
+  HELM_CK(launch_pivots(p->prec, p->ustartB, a, 1, nullptr));
+  HELM_CK(launch_pivots(p->prec, p->ustartA, a, 2, nullptr));
+  HELM_CK(cudaDeviceSynchronize());
   return HELM_OK;
 }
 
@@ -243,7 +261,7 @@ int alloc_refine(helm_plan* p) {
     return rc;
   }
   if ((rc = dev_alloc(p, (void**)&p->rbuf, N * sizeof(float2))) ||
-      (rc = dev_alloc(p, (void**)&p->sums, ((N + 255) / 256) * 2 * sizeof(double))) ||
+      (rc = dev_alloc(p, (void**)&p->sums, ((N + 255) / 256 + p->n[0]) * 2 * sizeof(double))) ||
       (rc = dev_alloc(p, (void**)&p->state, sizeof(RefineState))))
     return rc;
   return HELM_OK;
@@ -258,6 +276,9 @@ void destroy_plan(helm_plan* p) {
   cudaFree(p->dbuf);
   cudaFree(p->partial);
   cudaFree(p->faces);
+  cudaFree(p->ustartB);
+  cudaFree(p->ustartA);
+  cudaFree(p->rec);
   cudaFree(p->rbuf);
   cudaFree(p->sums);
   cudaFree(p->state);

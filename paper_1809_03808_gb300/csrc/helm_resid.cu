@@ -142,6 +142,99 @@ __global__ void __launch_bounds__(256) k_residual(ResidArgs a, const double2* __
   }
 }
 
+// 2D residual, one thread per y column segment of RX rows: rolling
+// registers over x (rows x-1, x, x+1 of the three y neighbours), interior
+// points with the nine precomputed real coefficients.
+constexpr int RX2 = 16;
+
+__global__ void __launch_bounds__(256) k_residual2d(ResidArgs a, const double2* __restrict__ f,
+                                                    const double2* __restrict__ u, float2* __restrict__ r,
+                                                    double* __restrict__ sums, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ double sr[8], sf[8];
+  const int64_t nx = a.ax[0].n, ny = a.ax[1].n;
+  const int64_t iy = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t x0 = (int64_t)blockIdx.y * RX2;
+  double r2 = 0.0, f2 = 0.0;
+  if (iy < ny) {
+    const bool ym = iy > 0, yp = iy < ny - 1;
+    auto ld = [&](int64_t ix, int64_t jy) -> double2 {
+      return (ix >= 0 && ix < nx) ? __ldg(&u[ix * ny + jy]) : make_double2(0.0, 0.0);
+    };
+    double2 w[3][3];  // [dx+1][dy+1]
+    for (int d = 0; d < 2; ++d) {
+      const int64_t ix = x0 - 1 + d;
+      w[d][0] = ym ? ld(ix, iy - 1) : make_double2(0, 0);
+      w[d][1] = ld(ix, iy);
+      w[d][2] = yp ? ld(ix, iy + 1) : make_double2(0, 0);
+    }
+    const int64_t x1 = min(x0 + RX2, nx);
+    for (int64_t ix = x0; ix < x1; ++ix) {
+      w[2][0] = ym ? ld(ix + 1, iy - 1) : make_double2(0, 0);
+      w[2][1] = ld(ix + 1, iy);
+      w[2][2] = yp ? ld(ix + 1, iy + 1) : make_double2(0, 0);
+      double ar = 0.0, ai = 0.0;
+      const bool interior = ix > 0 && ix < nx - 1 && iy > 0 && iy < ny - 1;
+      if (interior) {
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy) {
+            const double c = a.cin[dx * 3 + dy];
+            ar = fma(c, w[dx][dy].x, ar);
+            ai = fma(c, w[dx][dy].y, ai);
+          }
+      } else {
+        for (int dx = -1; dx <= 1; ++dx) {
+          if (ix + dx < 0 || ix + dx >= nx) continue;
+          double m0, k0r, k0i;
+          entries(a.ax[0], ix, dx, a.omega, m0, k0r, k0i);
+          for (int dy = -1; dy <= 1; ++dy) {
+            if (iy + dy < 0 || iy + dy >= ny) continue;
+            double m1, k1r, k1i;
+            entries(a.ax[1], iy, dy, a.omega, m1, k1r, k1i);
+            const double cre = k0r * m1 + m0 * k1r - a.omega * a.omega * m0 * m1;
+            const double cim = k0i * m1 + m0 * k1i;
+            const double2 v = w[dx + 1][dy + 1];
+            ar += cre * v.x - cim * v.y;
+            ai += cre * v.y + cim * v.x;
+          }
+        }
+      }
+      const double2 fv = __ldg(&f[ix * ny + iy]);
+      const double rr = fv.x - ar, ri = fv.y - ai;
+      r[ix * ny + iy] = make_float2((float)rr, (float)ri);
+      r2 = fma(rr, rr, fma(ri, ri, r2));
+      f2 = fma(fv.x, fv.x, fma(fv.y, fv.y, f2));
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy) {
+        w[0][dy] = w[1][dy];
+        w[1][dy] = w[2][dy];
+      }
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    r2 += __shfl_down_sync(0xffffffffu, r2, off);
+    f2 += __shfl_down_sync(0xffffffffu, f2, off);
+  }
+  const int wp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    sr[wp] = r2;
+    sf[wp] = f2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a2 = 0, b2 = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      a2 += sr[i];
+      b2 += sf[i];
+    }
+    const int64_t bid = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    sums[2 * bid] = a2;
+    sums[2 * bid + 1] = b2;
+  }
+}
+
 __global__ void k_residual_finalize(const double* __restrict__ sums, int64_t nblocks, RefineState* st,
                                     int last) {
   if (st->done) return;
@@ -211,6 +304,12 @@ cudaError_t launch_residual(int dim, const int64_t* n, const double* h, double o
                                         omega * omega * m[0][d0] * m[1][d1] * m[2][d2];
   }
   const int bs = 256;
+  if (dim == 2) {
+    const dim3 grid((unsigned)((n[1] + bs - 1) / bs), (unsigned)((n[0] + RX2 - 1) / RX2));
+    *nblocks = (int64_t)grid.x * grid.y;
+    k_residual2d<<<grid, bs, 0, st>>>(a, f, u, r, sums, skip);
+    return cudaGetLastError();
+  }
   const int64_t grid = (N + bs - 1) / bs;
   *nblocks = grid;
   k_residual<<<(unsigned)grid, bs, 0, st>>>(a, f, u, r, sums, N, skip);

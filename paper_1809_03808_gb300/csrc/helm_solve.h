@@ -23,10 +23,21 @@ struct Solve2DArgs {
   const double* sigA;
   const double* parA;
   const double* tw;
+  int64_t ch;       // rows per chunk of the tridiagonal sweeps
+  int64_t nchunks;  // ceil(nx / ch)
 };
 
-cudaError_t launch_tri2d(int prec, int step, const void* fhat, void* cbuf, void* dbuf, void* partial,
-                         const void* faces, const Solve2DArgs& a, const int* skip, cudaStream_t st);
+constexpr int kChunkF32 = 16;
+constexpr int kChunkF64 = 8;
+
+// One per-mode tridiagonal step (1, 2 or 3): pass 1, carry scan, pass 2.
+// ustart: pivot entering each chunk (launch_pivots, per step type: B for 1 and
+// 3, A for 2); rec: nchunks*n1 chunk records; out: x (step 3); partial: face
+// sums (steps 1, 2).
+cudaError_t launch_tri2d(int prec, int step, const void* fhat, const void* faces, const void* ustart, void* rec,
+                         void* out, void* partial, const Solve2DArgs& a, const int* skip, cudaStream_t st);
+cudaError_t launch_pivots(int prec, void* ustart, const Solve2DArgs& a, int step, cudaStream_t st);
+size_t chunk_record_bytes(int prec);
 cudaError_t launch_reduce_faces(int prec, const void* partial, void* out, int64_t nx, int64_t nwarps,
                                 double scale, const int* skip, cudaStream_t st);
 cudaError_t launch_apply_cbb(int prec, const void* in, const void* in2, void* out, int64_t nx, double hx,

@@ -10,8 +10,9 @@
 // Per-mode tridiagonal (Section 4.1.2, blocks of eqs. HB2D / HA2D):
 //   B modes: mu_l [K_x + (Lam^B_l - w^2) M_x],  Lam^B real (eq. eigvaluesPer)
 //   A modes:       K_x + (Lam^A_l - w^2) M_x,    Lam^A complex (eq. EVP1a)
-// solved by the Thomas algorithm (LU without pivoting).  The forward sweep
-// stores (c'_ix, d'_ix) in scratch; the backward sweep reads them back.
+// solved by the Thomas algorithm (LU without pivoting), evaluated in chunks of
+// rows so that every (line, chunk) pair is a thread: no N-sized scratch, and
+// enough parallelism for long lines.
 #include <algorithm>
 
 #include "helm_dft.h"
@@ -22,116 +23,234 @@ namespace helm {
 
 namespace {
 
+// Chunked Thomas.  T = L U with pivots u_j (u_0 = a_0, u_j = a_j - b^2/u_{j-1}),
+// multipliers m_j = b/u_{j-1}; forward y_j = r_j - m_j y_{j-1}; backward
+// x_j = (y_j - b x_{j+1}) / u_j.  The line is cut into chunks of CH rows.
+// Inside chunk k (rows s..e), with Y = y_{s-1} and X = x_{e+1} the carries,
+//   y_j = ylo_j + P_j Y,          P_j = prod_{i=s..j} (-m_i),
+//   x_s = sum_j w_j y_j - b w_e X, w_j = (U_kk^-1)_{s,j} = w_{j-1} (-b)/u_j,
+// so the carries obey  Y(k) = a_k + Pe_k Y(k-1)  and
+//   X(k) = bsum_k + cc_k Y(k-1) - b we_k X(k+1)
+// with a_k = ylo_e, bsum_k = sum_j w_j ylo_j, cc_k = sum_j w_j P_j.  Pass 1
+// computes the chunk summaries, k_tri_carry runs the two short scans per line,
+// pass 2 redoes Thomas inside each chunk from the exact carries.  The pivots
+// are the same sequence as plain Thomas: each chunk restarts it from u_{s-1},
+// computed once per plan (k_pivots).
+
+// Per-chunk summary record (one per line and chunk).
 template <typename C>
-struct Thomas {
-  LineCoef<C> k;
-  int n;
-  C c_prev, d_prev;
-  __device__ __forceinline__ void first(C r, C& c, C& d) {
-    C inv = crecip(k.ac);
-    c = cmul(k.b, inv);
-    d = cmul(r, inv);
-    c_prev = c;
-    d_prev = d;
-  }
-  __device__ __forceinline__ void step(int ix, C r, C& c, C& d) {
-    C a = (ix == n - 1) ? k.ac : k.a;
-    C den = csub(a, cmul(k.b, c_prev));
-    C inv = crecip(den);
-    c = cmul(k.b, inv);
-    d = cmul(csub(r, cmul(k.b, d_prev)), inv);
-    c_prev = c;
-    d_prev = d;
-  }
+struct ChunkRec {
+  C a, bsum, pe, cc, we;
 };
 
-// Step 1 (eqs. 2dLUBs1, 2dBs1): z_l = (1/mu_l) T_l^-1 fhat_l, reduced to the
-// x1 faces v_1 = (1/n1) sum_l z_l, v_n = (1/n1) sum_l e^{-2 pi i l/n1} z_l.
-// Step 3 (eqs. 2dLUBs3): rhs fhat_l + d_1 + e^{+2 pi i l/n1} d_n (the DFT of
-// the rank-2 correction, eq. step3term), z3 written to `out`.
-// Step 2 (eqs. step2-1..step2-3): rhs (c_1 + par_l c_n) (= g_l / V[1,l]),
-// solve with T^A_l, reduce w_1 = sum sigma_l z, w_n = sum par_l sigma_l z.
+template <typename C>
+__device__ __forceinline__ C line_rhs(int step, int64_t ix, int64_t lc, int64_t n1, const C* __restrict__ fhat,
+                                      const C* __restrict__ f1, const C* __restrict__ fn, decltype(C().x) scal,
+                                      decltype(C().x) par, C twl) {
+  if (step == 1) return cscale(fhat[ix * n1 + lc], scal);
+  if (step == 2) return cadd(f1[ix], cscale(fn[ix], par));
+  C v = cadd(fhat[ix * n1 + lc], f1[ix]);
+  v = cadd(v, cmulc(fn[ix], twl));
+  return cscale(v, scal);
+}
+
+struct LineParams {
+  double sre, sim;
+};
+
+__device__ __forceinline__ LineParams line_params(int step, const Solve2DArgs& a, int64_t lc) {
+  LineParams p;
+  if (step == 2) {
+    p.sre = a.lamA[2 * lc] - a.omega * a.omega;
+    p.sim = a.lamA[2 * lc + 1];
+  } else {
+    p.sre = a.lamB[lc] - a.omega * a.omega;
+    p.sim = 0.0;
+  }
+  return p;
+}
+
 template <typename T, int STEP>
-__global__ void __launch_bounds__(128) k_tri2d(const typename cpx<T>::type* __restrict__ fhat,
-                                               typename cpx<T>::type* __restrict__ cbuf,
-                                               typename cpx<T>::type* __restrict__ dbuf,
-                                               typename cpx<T>::type* __restrict__ partial,
-                                               const typename cpx<T>::type* __restrict__ faces,
-                                               Solve2DArgs a, const int* __restrict__ skip) {
+__global__ void __launch_bounds__(128) k_tri_pass1(const typename cpx<T>::type* __restrict__ fhat,
+                                                   const typename cpx<T>::type* __restrict__ faces,
+                                                   const typename cpx<T>::type* __restrict__ ustart,
+                                                   ChunkRec<typename cpx<T>::type>* __restrict__ rec,
+                                                   Solve2DArgs a, const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
   if (skip && *skip) return;
   const int64_t n1 = a.n1, nx = a.nx;
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // a warp lying entirely beyond the last mode has no work and no partial slot
-  if ((l & ~(int64_t)31) >= n1) return;
+  if (l >= n1) return;
+  const int64_t k = blockIdx.y;
+  const int64_t s = k * a.ch, e = min(s + a.ch, nx) - 1;
+  const LineParams lp = line_params(STEP, a, l);
+  const LineCoef<C> co = line_coef<C>(lp.sre, lp.sim, a.hx, a.omega);
+  const T scal = (STEP == 2) ? T(1) : (T)(1.0 / a.muB[l]);
+  const C twl = mk<C>(a.tw[2 * l], a.tw[2 * l + 1]);
+  const T par = (T)a.parA[l];
+  const C* f1 = faces;
+  const C* fn = faces + nx;
+  const C zero = mk<C>(0, 0);
+  C u = (k > 0) ? ustart[k * n1 + l] : zero;
+  C ylo = zero, P = zero, w = zero, bsum = zero, cc = zero;
+  const C mb = mk<C>(-(double)co.b.x, -(double)co.b.y);  // -b
+  for (int64_t j = s; j <= e; ++j) {
+    const C aj = (j == 0 || j == nx - 1) ? co.ac : co.a;
+    const C r = line_rhs<C>(STEP, j, l, n1, fhat, f1, fn, scal, par, twl);
+    C m = zero;
+    if (j > 0) {
+      m = cmul(co.b, crecip(u));
+      u = csub(aj, cmul(m, co.b));
+    } else {
+      u = aj;
+    }
+    const C inv = crecip(u);
+    ylo = (j == s) ? r : csub(r, cmul(m, ylo));
+    const C mm = mk<C>(-(double)m.x, -(double)m.y);
+    P = (j == s) ? mm : cmul(P, mm);
+    w = (j == s) ? inv : cmul(cmul(w, mb), inv);
+    bsum = cadd(bsum, cmul(w, ylo));
+    cc = cadd(cc, cmul(w, P));
+  }
+  ChunkRec<C> R;
+  R.a = ylo;
+  R.bsum = bsum;
+  R.pe = (k > 0) ? P : zero;
+  R.cc = (k > 0) ? cc : zero;
+  R.we = w;
+  rec[k * n1 + l] = R;
+}
+
+// Two scans per line over its chunks: forward carry Y, backward carry X.
+// Overwrites rec[k].a with Y(k-1) and rec[k].bsum with X(k+1).
+template <typename T, int STEP>
+__global__ void k_tri_carry(ChunkRec<typename cpx<T>::type>* __restrict__ rec, Solve2DArgs a,
+                            const int* __restrict__ skip) {
+  using C = typename cpx<T>::type;
+  if (skip && *skip) return;
+  const int64_t n1 = a.n1;
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n1) return;
+  const int64_t K = a.nchunks;
+  const LineParams lp = line_params(STEP, a, l);
+  const LineCoef<C> co = line_coef<C>(lp.sre, lp.sim, a.hx, a.omega);
+  C Y = mk<C>(0, 0);
+  for (int64_t k = 0; k < K; ++k) {
+    ChunkRec<C>& R = rec[k * n1 + l];
+    const C ak = R.a;
+    R.a = Y;  // Y(k-1)
+    Y = cadd(ak, cmul(R.pe, Y));
+  }
+  C X = mk<C>(0, 0);
+  for (int64_t k = K - 1; k >= 0; --k) {
+    ChunkRec<C>& R = rec[k * n1 + l];
+    const C bk = R.bsum;
+    R.bsum = X;  // X(k+1)
+    // X(k) = bsum + cc Y(k-1) - b we X(k+1)
+    X = csub(cadd(bk, cmul(R.cc, R.a)), cmul(cmul(co.b, R.we), X));
+  }
+}
+
+// Pass 2: Thomas inside each chunk from the exact carries; emit x.
+template <typename T, int STEP, int CH>
+__global__ void __launch_bounds__(128) k_tri_pass2(const typename cpx<T>::type* __restrict__ fhat,
+                                                   const typename cpx<T>::type* __restrict__ faces,
+                                                   const typename cpx<T>::type* __restrict__ ustart,
+                                                   const ChunkRec<typename cpx<T>::type>* __restrict__ rec,
+                                                   typename cpx<T>::type* __restrict__ out,
+                                                   typename cpx<T>::type* __restrict__ partial, Solve2DArgs a,
+                                                   const int* __restrict__ skip) {
+  using C = typename cpx<T>::type;
+  if (skip && *skip) return;
+  const int64_t n1 = a.n1, nx = a.nx;
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((l & ~(int64_t)31) >= n1) return;  // whole warp beyond the last line
   const bool act = l < n1;
   const int64_t lc = act ? l : 0;
-  // line coefficients
-  double sre, sim;
-  if (STEP == 2) {
-    sre = a.lamA[2 * lc] - a.omega * a.omega;
-    sim = a.lamA[2 * lc + 1];
-  } else {
-    sre = a.lamB[lc] - a.omega * a.omega;
-    sim = 0.0;
-  }
-  Thomas<C> th;
-  th.k = line_coef<C>(sre, sim, a.hx, a.omega);
-  th.n = (int)nx;
+  const int64_t k = blockIdx.y;
+  const int64_t s = k * CH, e = min(s + CH, nx) - 1;
+  const int cnt = (int)(e - s + 1);
+  const LineParams lp = line_params(STEP, a, lc);
+  const LineCoef<C> co = line_coef<C>(lp.sre, lp.sim, a.hx, a.omega);
   const T scal = (STEP == 2) ? T(1) : (T)(1.0 / a.muB[lc]);
-  const C twl = mk<C>(a.tw[2 * lc], a.tw[2 * lc + 1]);  // e^{-2 pi i l / n1}
+  const C twl = mk<C>(a.tw[2 * lc], a.tw[2 * lc + 1]);
   const T par = (T)a.parA[lc];
   const C sig = mk<C>(a.sigA[2 * lc], a.sigA[2 * lc + 1]);
-  const C* f1 = faces;       // Step 2: c_1 ; Step 3: d_1
-  const C* fn = faces + nx;  // Step 2: c_n ; Step 3: d_n
-  auto rhs = [&](int64_t ix) -> C {
-    if (STEP == 1) return cscale(fhat[ix * n1 + lc], scal);
-    if (STEP == 2) return cadd(f1[ix], cscale(fn[ix], par));
-    // STEP 3: fhat + d_1 + conj(twl) d_n
-    C v = cadd(fhat[ix * n1 + lc], f1[ix]);
-    v = cadd(v, cmulc(fn[ix], twl));
-    return cscale(v, scal);
-  };
-  if (act) {
-    C c, d;
-    th.first(rhs(0), c, d);
-    cbuf[lc] = c;
-    dbuf[lc] = d;
-    for (int64_t ix = 1; ix < nx; ++ix) {
-      th.step((int)ix, rhs(ix), c, d);
-      cbuf[ix * n1 + lc] = c;
-      dbuf[ix * n1 + lc] = d;
+  const C* f1 = faces;
+  const C* fn = faces + nx;
+  const C zero = mk<C>(0, 0);
+  C y[CH], iu[CH];
+  const ChunkRec<C> R = rec[k * n1 + lc];
+  C u = (k > 0) ? ustart[k * n1 + lc] : zero;
+  C yp = R.a;  // Y(k-1)
+#pragma unroll
+  for (int t = 0; t < CH; ++t) {
+    if (t < cnt) {
+      const int64_t j = s + t;
+      const C aj = (j == 0 || j == nx - 1) ? co.ac : co.a;
+      const C r = line_rhs<C>(STEP, j, lc, n1, fhat, f1, fn, scal, par, twl);
+      C m = zero;
+      if (j > 0) {
+        m = cmul(co.b, crecip(u));
+        u = csub(aj, cmul(m, co.b));
+      } else {
+        u = aj;
+      }
+      iu[t] = crecip(u);
+      yp = csub(r, cmul(m, yp));
+      y[t] = yp;
     }
   }
-  // backward sweep
   const int lane = threadIdx.x & 31;
   const int64_t warp = l >> 5;
   const int64_t nwarps = (n1 + 31) >> 5;
-  C x = mk<C>(0, 0);
-  for (int64_t ix = nx - 1; ix >= 0; --ix) {
-    if (act) {
-      C d = dbuf[ix * n1 + lc];
-      x = (ix == nx - 1) ? d : csub(d, cmul(cbuf[ix * n1 + lc], x));
-    }
-    if (STEP == 3) {
-      if (act) dbuf[ix * n1 + lc] = x;
-    } else {
-      C s1, sn;
-      if (STEP == 1) {
-        s1 = act ? x : mk<C>(0, 0);
-        sn = act ? cmul(x, twl) : mk<C>(0, 0);
+  C xn = R.bsum;  // X(k+1)
+#pragma unroll
+  for (int t = CH - 1; t >= 0; --t) {
+    if (t < cnt) {
+      const int64_t j = s + t;
+      const C x = cmul(csub(y[t], cmul(co.b, xn)), iu[t]);
+      xn = x;
+      if (STEP == 3) {
+        if (act) out[j * n1 + lc] = x;
       } else {
-        C t = act ? cmul(x, sig) : mk<C>(0, 0);
-        s1 = t;
-        sn = cscale(t, par);
-      }
-      s1 = warp_sum(s1);
-      sn = warp_sum(sn);
-      if (lane == 0) {
-        partial[warp * nx + ix] = s1;
-        partial[(nwarps + warp) * nx + ix] = sn;
+        C s1, sn;
+        if (STEP == 1) {
+          s1 = act ? x : zero;
+          sn = act ? cmul(x, twl) : zero;
+        } else {
+          const C tt = act ? cmul(x, sig) : zero;
+          s1 = tt;
+          sn = cscale(tt, par);
+        }
+        s1 = warp_sum(s1);
+        sn = warp_sum(sn);
+        if (lane == 0) {
+          partial[warp * nx + j] = s1;
+          partial[(nwarps + warp) * nx + j] = sn;
+        }
       }
     }
+  }
+}
+
+// Pivot entering each chunk, u_{kCH-1}, for every line: FP64 sequential
+// recurrence once per plan (same sequence as plain Thomas).
+template <typename T>
+__global__ void k_pivots(typename cpx<T>::type* __restrict__ ustart, Solve2DArgs a, int step) {
+  using C = typename cpx<T>::type;
+  const int64_t n1 = a.n1, nx = a.nx;
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n1) return;
+  const LineParams lp = line_params(step, a, l);
+  const LineCoef<double2> co = line_coef<double2>(lp.sre, lp.sim, a.hx, a.omega);
+  double2 u = co.ac;
+  const double2 b2 = cmul(co.b, co.b);
+  if ((a.ch - 1) == 0 && a.nchunks > 1) ustart[1 * n1 + l] = cvt<C>(u);
+  for (int64_t j = 1; j < nx; ++j) {
+    const double2 aj = (j == nx - 1) ? co.ac : co.a;
+    u = csub(aj, cmul(b2, crecip(u)));
+    if ((j + 1) % a.ch == 0 && (j + 1) / a.ch < a.nchunks) ustart[((j + 1) / a.ch) * n1 + l] = cvt<C>(u);
   }
 }
 
@@ -193,26 +312,46 @@ __global__ void k_apply_cbb(const typename cpx<T>::type* __restrict__ in,
 
 }  // namespace
 
-cudaError_t launch_tri2d(int prec, int step, const void* fhat, void* cbuf, void* dbuf, void* partial,
-                         const void* faces, const Solve2DArgs& a, const int* skip, cudaStream_t st) {
+cudaError_t launch_tri2d(int prec, int step, const void* fhat, const void* faces, const void* ustart, void* rec,
+                         void* out, void* partial, const Solve2DArgs& a, const int* skip, cudaStream_t st) {
   const int bs = 128;
-  const unsigned grid = (unsigned)((a.n1 + bs - 1) / bs);
-#define HELM_TRI_LAUNCH(T, S)                                                                          \
-  k_tri2d<T, S><<<grid, bs, 0, st>>>(                                                                  \
-      (const cpx<T>::type*)fhat, (cpx<T>::type*)cbuf, (cpx<T>::type*)dbuf, (cpx<T>::type*)partial,   \
-      (const cpx<T>::type*)faces, a, skip)
+  const dim3 grid((unsigned)((a.n1 + bs - 1) / bs), (unsigned)a.nchunks);
+  const unsigned gl = (unsigned)((a.n1 + bs - 1) / bs);
+#define HELM_TRI(T, S, CH)                                                                                        \
+  do {                                                                                                         \
+    using C = cpx<T>::type;                                                                                    \
+    k_tri_pass1<T, S><<<grid, bs, 0, st>>>((const C*)fhat, (const C*)faces, (const C*)ustart, (ChunkRec<C>*)rec, \
+                                          a, skip);                                                           \
+    k_tri_carry<T, S><<<gl, bs, 0, st>>>((ChunkRec<C>*)rec, a, skip);                                          \
+    k_tri_pass2<T, S, CH><<<grid, bs, 0, st>>>((const C*)fhat, (const C*)faces, (const C*)ustart,              \
+                                              (const ChunkRec<C>*)rec, (C*)out, (C*)partial, a, skip);        \
+  } while (0)
   if (prec == kPrecF64) {
-    if (step == 1) HELM_TRI_LAUNCH(double, 1);
-    else if (step == 2) HELM_TRI_LAUNCH(double, 2);
-    else HELM_TRI_LAUNCH(double, 3);
+    if (a.ch != kChunkF64) return cudaErrorInvalidValue;
+    if (step == 1) HELM_TRI(double, 1, kChunkF64);
+    else if (step == 2) HELM_TRI(double, 2, kChunkF64);
+    else HELM_TRI(double, 3, kChunkF64);
   } else {
-    if (step == 1) HELM_TRI_LAUNCH(float, 1);
-    else if (step == 2) HELM_TRI_LAUNCH(float, 2);
-    else HELM_TRI_LAUNCH(float, 3);
+    if (a.ch != kChunkF32) return cudaErrorInvalidValue;
+    if (step == 1) HELM_TRI(float, 1, kChunkF32);
+    else if (step == 2) HELM_TRI(float, 2, kChunkF32);
+    else HELM_TRI(float, 3, kChunkF32);
   }
-#undef HELM_TRI_LAUNCH
+#undef HELM_TRI
   return cudaGetLastError();
 }
+
+cudaError_t launch_pivots(int prec, void* ustart, const Solve2DArgs& a, int step, cudaStream_t st) {
+  const int bs = 128;
+  const unsigned grid = (unsigned)((a.n1 + bs - 1) / bs);
+  if (prec == kPrecF64)
+    k_pivots<double><<<grid, bs, 0, st>>>((double2*)ustart, a, step);
+  else
+    k_pivots<float><<<grid, bs, 0, st>>>((float2*)ustart, a, step);
+  return cudaGetLastError();
+}
+
+size_t chunk_record_bytes(int prec) { return prec == kPrecF64 ? sizeof(ChunkRec<double2>) : sizeof(ChunkRec<float2>); }
 
 cudaError_t launch_reduce_faces(int prec, const void* partial, void* out, int64_t nx, int64_t nwarps,
                                 double scale, const int* skip, cudaStream_t st) {
