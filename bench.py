@@ -104,26 +104,53 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# Algorithmic traffic and arithmetic per unknown of each 2D kernel (per
-# launch: times N = nx * n1).  Bytes count the minimum reads/writes of the
-# kernel's own inputs and outputs in the compute precision (e bytes per
-# complex value); flops count real FP64/FP32 operations of the algorithm.
-def kernel_model(name, e, n1):
+# Algorithmic traffic and arithmetic per unknown of each 2D kernel, per
+# launch (multiply by N = nx * n1).  Bytes: the kernel's own minimum reads and
+# writes, e = bytes per complex value of the compute precision (16 FP64, 8
+# FP32); the first solve reads f as complex128, refinement sweeps read the
+# complex64 residual, the last transform writes (or updates) complex128 u.
+# Flops: real operations of the algorithm as written (complex multiply 6,
+# complex add 2, complex reciprocal 5 counting each division as 1).
+def kernel_model(name, e, n1, accum=False, first=True):
     import math
 
     log2n = math.log2(n1)
-    model = {
-        # DFT: read line, write line; ~5 n log2 n real flops per line
-        "dft_fwd": (2 * e, 5 * log2n),
-        "dft_inv": (2 * e, 5 * log2n),
-        # tridiagonal sweeps: rhs read, (c', d') scratch write + read; result write (step 3)
-        "tri_step1": (e + 4 * e, 40.0),
-        "tri_step2": (4 * e, 40.0),
-        "tri_step3": (e + 4 * e + e, 48.0),
-        # FP64 residual: read u (16) + f (16), write r (8)
+    fin = 16 if first else e
+    tab = {
+        "dft_fwd": (fin + e, 5.0 * log2n),
+        "dft_inv": (e + (32 if accum else 16 if e == 16 else 8), 5.0 * log2n),
+        "tri_step1_pass1": (e, 67.0),
+        "tri_step2_pass1": (0.0, 61.0),
+        "tri_step3_pass1": (e, 75.0),
+        "tri_step1_pass2": (e, 53.0),
+        "tri_step2_pass2": (0.0, 47.0),
+        "tri_step3_pass2": (2.0 * e, 55.0),
         "residual_fp64": (40.0, 40.0),
     }
-    return model.get(name)
+    return tab.get(name)
+
+
+def roofline_entry(name, launches, tot_ms, steps, N, e, n1, peaks, fp64, accum=False):
+    per_launch_ms = tot_ms / launches
+    model = kernel_model(name, e, n1, accum=accum)
+    out = {"kernel": name, "launches_per_step": launches / steps, "ms_per_launch": per_launch_ms}
+    if model is None:
+        return out
+    byts, flops = model[0] * N, model[1] * N
+    gbs = byts / (per_launch_ms * 1e-3) / 1e9
+    tfl = flops / (per_launch_ms * 1e-3) / 1e12
+    hbm = peaks.get("hbm_gbs")
+    if fp64 or name == "residual_fp64":
+        out.update({"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tfl / FP64_PEAK_TFLOPS, "peak_source": FP64_PEAK_NOTE,
+                    "algorithmic_flops_per_launch": flops,
+                    "hbm_GBps": gbs, "hbm_frac_of_measured": gbs / hbm if hbm else None})
+    else:
+        out.update({"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                    "frac": gbs / hbm if hbm else None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                    "algorithmic_bytes_per_launch": byts})
+    out["traffic"] = None
+    return out
 
 
 def run_gb300(args):
@@ -244,25 +271,22 @@ def run_gb300(args):
             "final_rel_residual": float(info_r.residual[info_r.iterations]),
             "converged": bool(info_r.converged), "rel_err_sampled": sampled_error(u),
             "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof_r.items()},
+            "_prof": prof_r,
         }
         plan.close()
         del u
 
     # --- roofline of the dominant kernel of the timed (c128) step ---
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
-    name, (launches, tot_ms) = dom
-    per_launch_ms = tot_ms / launches
-    model = kernel_model(name, 16, p.shape[1])
     peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
-    roof = {"kernel": name, "launches_per_step": launches / args.steps, "ms_per_launch": per_launch_ms}
-    if model:
-        flops = model[1] * N
-        roof.update({"bound": "alu", "achieved": flops / (per_launch_ms * 1e-3) / 1e12,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": flops / (per_launch_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
-                     "peak_source": FP64_PEAK_NOTE, "traffic": None,
-                     "hbm_GBps": model[0] * N / (per_launch_ms * 1e-3) / 1e9,
-                     "hbm_peak_GBps": peaks.get("hbm_gbs")})
+    n1 = p.shape[1]
+    name, (launches, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    roof = roofline_entry(name, launches, tot_ms, args.steps, N, 16, n1, peaks, fp64=True)
+    kernels_c128 = {k: roofline_entry(k, v[0], v[1], args.steps, N, 16, n1, peaks, fp64=True) for k, v in prof.items()}
+    if variants.get("c64_refined"):
+        pr = variants["c64_refined"].pop("_prof")
+        variants["c64_refined"]["kernels"] = {
+            k: roofline_entry(k, v[0], v[1], args.steps, N, 8, n1, peaks, fp64=False, accum=(k == "dft_inv"))
+            for k, v in pr.items()}
     gpu_launches = sum(v[0] for v in prof.values())
 
     # --- CPU oracle baseline (rank 0, N = 1 only) ---
@@ -280,6 +304,7 @@ def run_gb300(args):
         "rel_err_sampled": err_c128,
         "gpu_launches": gpu_launches,
         "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()},
+        "kernels": kernels_c128,
         "roofline": roof, "clocks": clocks, "e2e": e2e, "variants": variants, "cpu_baseline": cpu,
         "plan_seconds": info.plan_seconds,
     }

@@ -98,6 +98,20 @@ int helm_plan_2d(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy,
 int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx,
                  double hy, double hz, double omega, int dtype);
 
+/* Auxiliary problem B.  The paper makes x1 periodic (eqs. matrixKper,
+ * matrixMper).  Here the wrap-around entries of those circulant matrices are
+ * multiplied by g (last row) and 1/g (first row), with g = e^{rho + i q pi/2}.
+ * B - A is still supported on the x1 boundary rows, so Steps 1-3 are
+ * unchanged.  B is diagonalised by F D^-1, D = diag(e^{t j}),
+ * t = (rho + i q pi/2)/n1, with eigenvalues (2 - 2cosh(t + i theta_l))/h and
+ * h (4 + 2cosh(t + i theta_l))/6.  rho = q = 0 is the paper's periodic
+ * auxiliary.  rho > 0 damps waves that travel around the periodic loop, which
+ * keeps B far from resonance and the solve accurate.  Default: rho = 1, q = 1.
+ * Applies to every periodic axis of the plan.  rho must be in [0, 8]; any
+ * integer q is taken mod 4.  Rebuilds the plan's auxiliary tables; call it
+ * between solves, not while a solve is in flight on another stream. */
+int helm_set_auxiliary(helm_plan_t p, double rho, int phase_quarters);
+
 /* Stream on which helm_solve enqueues its kernels (a cudaStream_t passed as
  * void*; NULL = legacy default stream).  One plan serves one stream at a time. */
 int helm_set_stream(helm_plan_t p, void* cuda_stream);

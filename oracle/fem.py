@@ -144,23 +144,30 @@ def M1d(n, h):
     return M * (h / 6.0)
 
 
-def K1d_periodic(n, h):
-    """Circulant stiffness matrix of eq. matrixKper."""
-    K = 2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
-    K[0, -1] = K[-1, 0] = -1.0
+def K1d_periodic(n, h, gamma=1.0):
+    """Circulant stiffness matrix of eq. matrixKper.  With gamma != 1 the
+    wrap-around entries become gamma * (-1/h) (last row, first column) and
+    (-1/h) / gamma (first row, last column): a gamma-circulant, the damped
+    periodic auxiliary (gamma = 1 is the paper's matrix)."""
+    K = (2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)).astype(np.complex128)
+    K[-1, 0] = -1.0 * gamma
+    K[0, -1] = -1.0 / gamma
     return K / h
 
 
-def M1d_periodic(n, h):
-    """Circulant mass matrix of eq. matrixMper."""
-    M = 4.0 * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)
-    M[0, -1] = M[-1, 0] = 1.0
+def M1d_periodic(n, h, gamma=1.0):
+    """Circulant mass matrix of eq. matrixMper (gamma-circulant as above)."""
+    M = (4.0 * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)).astype(np.complex128)
+    M[-1, 0] = 1.0 * gamma
+    M[0, -1] = 1.0 / gamma
     return M * (h / 6.0)
 
 
-def kron_operator(shape, h, omega, periodic_axis=None, bc="abc"):
+def kron_operator(shape, h, omega, periodic_axis=None, bc="abc", gamma=None):
     """Sparse Kronecker-form operator: eq. A2D / A3D, or with `periodic_axis`
-    replaced by the circulant matrices, eq. B2D / B3D.
+    replaced by the circulant matrices, eq. B2D / B3D.  `gamma` (a scalar,
+    or a dict axis -> gamma; periodic_axis may then be a tuple) selects the
+    gamma-circulant auxiliary on that axis.
 
     General d: sum_j (x)_k [K_k if k == j else M_k]  -  w^2 (x)_k M_k.
     """
@@ -168,10 +175,12 @@ def kron_operator(shape, h, omega, periodic_axis=None, bc="abc"):
     if isinstance(bc, str):
         bc = (bc,) * d
     Ks, Ms = [], []
+    paxes = periodic_axis if isinstance(periodic_axis, (tuple, list)) else (periodic_axis,)
     for j in range(d):
-        if j == periodic_axis:
-            Ks.append(sp.csr_matrix(K1d_periodic(shape[j], h[j])))
-            Ms.append(sp.csr_matrix(M1d_periodic(shape[j], h[j])))
+        if j in paxes:
+            g = 1.0 if gamma is None else (gamma[j] if isinstance(gamma, dict) else gamma)
+            Ks.append(sp.csr_matrix(K1d_periodic(shape[j], h[j], g)))
+            Ms.append(sp.csr_matrix(M1d_periodic(shape[j], h[j], g)))
         else:
             Ks.append(sp.csr_matrix(K1d(shape[j], h[j], omega, bc[j])))
             Ms.append(sp.csr_matrix(M1d(shape[j], h[j])))

@@ -184,13 +184,14 @@ def oracle_solve(f, h, omega, method="auto", iters=2, tri_axis=None):
 # Plain definitions of the three-step solve's intermediates (Section 3.1)
 # ---------------------------------------------------------------------------
 
-def step_definitions(f, h, omega, axis):
+def step_definitions(f, h, omega, axis, gamma=None):
     """Return (v, w, u): v = B^-1 f (Step 1), w = A^-1 (B - A) v (Step 2),
-    u = A^-1 f, with B periodic along `axis` (eqs. probB, probStep2, B2D/B3D).
-    Uses sparse LU on the Kronecker forms; meant for small grids."""
+    u = A^-1 f, with B periodic along `axis` (eqs. probB, probStep2, B2D/B3D),
+    or gamma-circulant when `gamma` is given.  Uses sparse LU on the Kronecker
+    forms; meant for small grids."""
     f = np.asarray(f, dtype=np.complex128)
     A = fem.kron_operator(f.shape, h, omega).tocsc()
-    B = fem.kron_operator(f.shape, h, omega, periodic_axis=axis).tocsc()
+    B = fem.kron_operator(f.shape, h, omega, periodic_axis=axis, gamma=gamma).tocsc()
     v = spl.spsolve(B, f.ravel())
     w = spl.spsolve(A, (B - A) @ v)
     u = spl.spsolve(A, f.ravel())

@@ -46,6 +46,7 @@ _SIGS = {
     "helm_plan_3d": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _i64, _dbl, _dbl, _dbl, _dbl, _i32]),
     "helm_set_stream": (_i32, [_vp, _vp]),
     "helm_set_refinement": (_i32, [_vp, _dbl, _i32]),
+    "helm_set_auxiliary": (_i32, [_vp, _dbl, _i32]),
     "helm_solve": (_i32, [_vp, _vp, _vp]),
     "helm_solve_host": (_i32, [_vp, _vp, _vp]),
     "helm_solve_debug": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -107,6 +108,10 @@ def helm_plan_3d(nx, ny, nz, hx, hy, hz, omega, dtype=HELM_C128):
 
 def helm_set_stream(plan, stream):
     _check(lib.helm_set_stream(plan, _vp(int(stream) if stream is not None else 0)), "helm_set_stream", plan)
+
+
+def helm_set_auxiliary(plan, rho, phase_quarters):
+    _check(lib.helm_set_auxiliary(plan, float(rho), int(phase_quarters)), "helm_set_auxiliary", plan)
 
 
 def helm_set_refinement(plan, tol, max_iter):

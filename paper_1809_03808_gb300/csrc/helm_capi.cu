@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <complex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -92,7 +93,11 @@ int dev_alloc(helm_plan* p, void** ptr, size_t bytes) {
 
 void free_axis(AxisData& a) {
   cudaFree(a.lamB);
-  cudaFree(a.muB);
+  cudaFree(a.invmu);
+  cudaFree(a.sc_in);
+  cudaFree(a.sc_out);
+  cudaFree(a.sc_in32);
+  cudaFree(a.sc_out32);
   cudaFree(a.lamA);
   cudaFree(a.sigA);
   cudaFree(a.parA);
@@ -101,27 +106,114 @@ void free_axis(AxisData& a) {
   a = AxisData{};
 }
 
-// Eigen-data of one periodic axis (Section 3.2): periodic eigenvalues
-// Lam^B_l = kappa_l / mu_l (eq. eigvaluesPer, closed form), absorbing-pencil
-// eigen-data (eq. EVP1a, EVPcondA), DFT twiddles.
-int build_axis(helm_plan* p, AxisData& a, int64_t n, double h, double omega) {
+// Default auxiliary: damped periodic wrap, g = e^{1 + i pi/2} (see helm.h).
+constexpr double kDefaultAuxRho = 1.0;
+constexpr int kDefaultAuxQ = 1;
+
+int upload(helm_plan* p, double** d, const std::vector<double>& v) {
+  if (!*d) {
+    int r = dev_alloc(p, (void**)d, v.size() * sizeof(double));
+    if (r) return r;
+  }
+  cudaError_t e = cudaMemcpy(*d, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? HELM_OK : cuda_fail(p, e, "cudaMemcpy plan tables");
+}
+
+int upload32(helm_plan* p, float** d, const std::vector<float>& v) {
+  if (!*d) {
+    int r = dev_alloc(p, (void**)d, v.size() * sizeof(float));
+    if (r) return r;
+  }
+  cudaError_t e = cudaMemcpy(*d, v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? HELM_OK : cuda_fail(p, e, "cudaMemcpy plan tables");
+}
+
+// Auxiliary (B) tables of one periodic axis for t = (rho + i q pi/2)/n:
+// Lam^B_l = kappa_l/mu_l and 1/mu_l with kappa_l = -4 s^2/h,
+// mu_l = h (1 + 2 s^2/3), s = sinh((t + i theta_l)/2) -- eq. eigvaluesPer for
+// t = 0, written without cancellation at small theta -- and the scalings
+// e^{-+t j} that turn the DFT into the transform of the gamma-circulant.
+int build_axis_aux(helm_plan* p, AxisData& a, double rho, int q) {
+  const int64_t n = a.n;
+  const double h = a.h;
+  a.rho = rho;
+  a.q = ((q % 4) + 4) % 4;
+  const double pi = 3.14159265358979323846;
+  std::vector<double> r4re(4 * n), r4im(4 * n);  // e^{-2 pi i k/(4n)} = e^{-i pi k/(2n)}
+  unit_roots(4 * n, r4re.data(), r4im.data());
+  std::vector<double> lamB(2 * n), invmu(2 * n);
+  const double ar = 0.5 * rho / (double)n;  // Re(t)/2
+  for (int64_t l = 0; l < n; ++l) {
+    // b = Im(t + i theta_l)/2 = (q pi/2 + 2 pi l)/(2n)
+    const double b = (0.5 * pi * a.q + 2.0 * pi * (double)l) / (2.0 * (double)n);
+    const std::complex<double> sh(std::sinh(ar) * std::cos(b), std::cosh(ar) * std::sin(b));
+    const std::complex<double> s2 = sh * sh;
+    const std::complex<double> kappa = -4.0 * s2 / h;
+    const std::complex<double> mu = h * (1.0 + (2.0 / 3.0) * s2);
+    const std::complex<double> lb = kappa / mu, im = 1.0 / mu;
+    lamB[2 * l] = lb.real();
+    lamB[2 * l + 1] = lb.imag();
+    invmu[2 * l] = im.real();
+    invmu[2 * l + 1] = im.imag();
+  }
+  int rc;
+  if ((rc = upload(p, &a.lamB, lamB)) || (rc = upload(p, &a.invmu, invmu))) return rc;
+  // e^{t j} = e^{rho j/n} e^{+i q pi j/(2n)}
+  auto et = [&](int64_t j, double sign) -> std::complex<double> {
+    const int64_t k = (a.q * j) % (4 * n);
+    const std::complex<double> ph(r4re[k], -sign * r4im[k]);  // sign +1: conj(root) = e^{+i ..}
+    return std::exp(sign * rho * (double)j / (double)n) * ph;
+  };
+  const std::complex<double> en = et(n - 1, +1.0), eninv = et(n - 1, -1.0);
+  a.en[0] = en.real();
+  a.en[1] = en.imag();
+  a.eninv[0] = eninv.real();
+  a.eninv[1] = eninv.imag();
+  const double gr[4] = {1, 0, -1, 0}, gi[4] = {0, 1, 0, -1};  // e^{i q pi/2}
+  a.g[0] = std::exp(rho) * gr[a.q];
+  a.g[1] = std::exp(rho) * gi[a.q];
+  a.ginv[0] = std::exp(-rho) * gr[a.q];
+  a.ginv[1] = -std::exp(-rho) * gi[a.q];
+  if (rho == 0.0 && a.q == 0) {
+    cudaFree(a.sc_in);
+    cudaFree(a.sc_out);
+    cudaFree(a.sc_in32);
+    cudaFree(a.sc_out32);
+    a.sc_in = a.sc_out = nullptr;
+    a.sc_in32 = a.sc_out32 = nullptr;
+    return HELM_OK;
+  }
+  std::vector<double> si(2 * n), so(2 * n);
+  std::vector<float> si32(2 * n), so32(2 * n);
+  for (int64_t j = 0; j < n; ++j) {
+    const std::complex<double> ei = et(j, -1.0), eo = et(j, +1.0);
+    si[2 * j] = ei.real();
+    si[2 * j + 1] = ei.imag();
+    so[2 * j] = eo.real();
+    so[2 * j + 1] = eo.imag();
+    si32[2 * j] = (float)ei.real();
+    si32[2 * j + 1] = (float)ei.imag();
+    so32[2 * j] = (float)eo.real();
+    so32[2 * j + 1] = (float)eo.imag();
+  }
+  if ((rc = upload(p, &a.sc_in, si)) || (rc = upload(p, &a.sc_out, so)) || (rc = upload32(p, &a.sc_in32, si32)) ||
+      (rc = upload32(p, &a.sc_out32, so32)))
+    return rc;
+  return HELM_OK;
+}
+
+// Eigen-data of one periodic axis (Section 3.2): absorbing-pencil eigen-data
+// (eqs. EVP1a, EVPcondA), DFT twiddles, and the auxiliary tables.
+int build_axis(helm_plan* p, AxisData& a, int64_t n, double h, double omega, double rho, int q) {
   a.n = n;
   a.h = h;
   dft_factor(n, &a.dft);
-  const double pi = 3.14159265358979323846;
   std::vector<double> twre(n), twim(n);
   unit_roots(n, twre.data(), twim.data());
-  std::vector<double> lamB(n), muB(n), tw(2 * n), lamA(2 * n), sigA(2 * n), parA(n);
+  std::vector<double> tw(2 * n), lamA(2 * n), sigA(2 * n), parA(n);
   std::vector<float> tw32(2 * n);
   std::vector<int8_t> par8(n);
   for (int64_t l = 0; l < n; ++l) {
-    const double c = twre[l];  // cos(2 pi l / n)
-    // 1 - cos(theta) = 2 sin^2(theta/2), evaluated without cancellation
-    const double s = std::sin(pi * (double)l / (double)n);
-    const double kappa = 2.0 * (2.0 * s * s) / h;  // (2 - 2 cos theta)/h
-    const double mu = h * (4.0 + 2.0 * c) / 6.0;
-    lamB[l] = kappa / mu;
-    muB[l] = mu;
     tw[2 * l] = twre[l];
     tw[2 * l + 1] = twim[l];
     tw32[2 * l] = (float)twre[l];
@@ -133,20 +225,10 @@ int build_axis(helm_plan* p, AxisData& a, int64_t n, double h, double omega) {
     return rc;
   }
   for (int64_t l = 0; l < n; ++l) parA[l] = par8[l];
-  auto up = [&](double** d, const std::vector<double>& v) -> int {
-    int r = dev_alloc(p, (void**)d, v.size() * sizeof(double));
-    if (r) return r;
-    cudaError_t e = cudaMemcpy(*d, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
-    return e == cudaSuccess ? HELM_OK : cuda_fail(p, e, "cudaMemcpy eigen-data");
-  };
-  if ((rc = up(&a.lamB, lamB)) || (rc = up(&a.muB, muB)) || (rc = up(&a.lamA, lamA)) ||
-      (rc = up(&a.sigA, sigA)) || (rc = up(&a.parA, parA)) || (rc = up(&a.tw, tw)))
+  if ((rc = upload(p, &a.lamA, lamA)) || (rc = upload(p, &a.sigA, sigA)) || (rc = upload(p, &a.parA, parA)) ||
+      (rc = upload(p, &a.tw, tw)) || (rc = upload32(p, &a.tw32, tw32)))
     return rc;
-  rc = dev_alloc(p, (void**)&a.tw32, tw32.size() * sizeof(float));
-  if (rc) return rc;
-  cudaError_t e = cudaMemcpy(a.tw32, tw32.data(), tw32.size() * sizeof(float), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(p, e, "cudaMemcpy twiddles");
-  return HELM_OK;
+  return build_axis_aux(p, a, rho, q);
 }
 
 int validate_common(double omega, int dtype) {
@@ -159,7 +241,8 @@ size_t cbytes(int prec) { return prec == kPrecF64 ? sizeof(double2) : sizeof(flo
 
 Solve2DArgs args2d(const helm_plan* p) {
   const AxisData& ax = p->axo;
-  Solve2DArgs a{p->n[0], p->n[1], p->h[0], p->h[1], p->omega, ax.lamB, ax.muB, ax.lamA, ax.sigA, ax.parA, ax.tw, 0, 0};
+  Solve2DArgs a{p->n[0], p->n[1], p->h[0], p->h[1], p->omega, ax.lamB, ax.invmu, ax.lamA, ax.sigA, ax.parA, ax.tw,
+                0, 0, {ax.eninv[0], ax.eninv[1]}};
   a.ch = p->prec == kPrecF64 ? kChunkF64 : kChunkF32;
   a.nchunks = (p->n[0] + a.ch - 1) / a.ch;
   return a;
@@ -183,23 +266,31 @@ int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int 
   Solve2DArgs a = args2d(p);
   const int fhat_mode = prec == kPrecF64 ? kOutC128 : kOutC64;
   // a1: forward DFT along x1 (eq. step1FFTfcoeff), f_hat kept for Step 3
-  HELM_PK("dft_fwd", launch_dft_rows(prec, in, in_is_double, p->fhat, fhat_mode, nx, ax.dft, tw, -1, 1.0, 0.0, skip, st));
+  const bool f64 = prec == kPrecF64;
+  const void* sci = f64 ? (const void*)ax.sc_in : (const void*)ax.sc_in32;
+  const void* sco = f64 ? (const void*)ax.sc_out : (const void*)ax.sc_out32;
+  const double one[2] = {1.0, 0.0}, inv_n1[2] = {1.0 / (double)n1, 0.0};
+  const double en_n1[2] = {ax.en[0] / (double)n1, ax.en[1] / (double)n1};
+  HELM_PK("dft_fwd", launch_dft_rows(prec, in, in_is_double, p->fhat, fhat_mode, nx, ax.dft, tw, -1, 1.0, 0.0, sci,
+                                     nullptr, skip, st));
   if (dbg_fhat) HELM_CK(cudaMemcpyAsync(dbg_fhat, p->fhat, nx * n1 * cb, cudaMemcpyDeviceToDevice, st));
   // a2: Step 1
-  HELM_PK("tri_step1", launch_tri2d(prec, 1, p->fhat, nullptr, p->ustartB, p->rec, nullptr, p->partial, a, skip, st));
-  HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fv, nx, p->nwarps, 1.0 / (double)n1, skip, st));
+  HELM_CK(launch_tri2d(prec, 1, p->fhat, nullptr, p->ustartB, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr));
+  HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fv, nx, p->nwarps, inv_n1, en_n1, skip, st));
   if (dbg_v) HELM_CK(cudaMemcpyAsync(dbg_v, fv, 2 * nx * cb, cudaMemcpyDeviceToDevice, st));
   // a3: Step 2
-  HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, nullptr, fc, nx, p->h[0], p->h[1], p->omega, p->omega * p->omega, skip, st));
-  HELM_PK("tri_step2", launch_tri2d(prec, 2, nullptr, fc, p->ustartA, p->rec, nullptr, p->partial, a, skip, st));
-  HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fw, nx, p->nwarps, 1.0, skip, st));
+  HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, nullptr, fc, nx, p->h[0], p->h[1], p->omega, p->omega * p->omega, ax.g,
+                                        ax.ginv, skip, st));
+  HELM_CK(launch_tri2d(prec, 2, nullptr, fc, p->ustartA, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr));
+  HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fw, nx, p->nwarps, one, one, skip, st));
   if (dbg_w) HELM_CK(cudaMemcpyAsync(dbg_w, fw, 2 * nx * cb, cudaMemcpyDeviceToDevice, st));
   // a4: Step 3
-  HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, fw, fc, nx, p->h[0], p->h[1], p->omega, p->omega * p->omega, skip, st));
-  HELM_PK("tri_step3", launch_tri2d(prec, 3, p->fhat, fc, p->ustartB, p->rec, p->dbuf, nullptr, a, skip, st));
+  HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, fw, fc, nx, p->h[0], p->h[1], p->omega, p->omega * p->omega, ax.g,
+                                        ax.ginv, skip, st));
+  HELM_CK(launch_tri2d(prec, 3, p->fhat, fc, p->ustartB, p->rec, p->dbuf, nullptr, a, skip, st, p->prof.on ? &p->prof : nullptr));
   // a5: inverse DFT along x1 (eq. step3IFFTz3coeff)
   HELM_PK("dft_inv", launch_dft_rows(prec, p->dbuf, prec == kPrecF64, out, out_mode, nx, ax.dft, tw, +1, 1.0 / (double)n1,
-                          accum_scale, skip, st));
+                                     accum_scale, nullptr, sco, skip, st));
   return HELM_OK;
 }
 
@@ -324,7 +415,7 @@ int helm_plan_2d(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy,
     delete p;
     return HELM_EUNSUPPORTED;
   }
-  int rc = build_axis(p, p->axo, ny, hy, omega);
+  int rc = build_axis(p, p->axo, ny, hy, omega, kDefaultAuxRho, kDefaultAuxQ);
   if (!rc) rc = alloc_buffers_2d(p);
   if (!rc) rc = alloc_refine(p);
   if (rc) {
@@ -370,8 +461,8 @@ int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx
     delete p;
     return HELM_EUNSUPPORTED;
   }
-  int rc = build_axis(p, p->axo, ny, hy, omega);
-  if (!rc) rc = build_axis(p, p->axi, nz, hz, omega);
+  int rc = build_axis(p, p->axo, ny, hy, omega, kDefaultAuxRho, kDefaultAuxQ);
+  if (!rc) rc = build_axis(p, p->axi, nz, hz, omega, kDefaultAuxRho, kDefaultAuxQ);
   if (!rc) {
     DftPlan a = p->axo.dft, b = p->axi.dft;
     if (!dft_supported(a, cbytes(p->prec), smem) || !dft_supported(b, cbytes(p->prec), smem)) rc = HELM_EUNSUPPORTED;
@@ -388,6 +479,20 @@ int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx
   }
   p->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *out = p;
+  return HELM_OK;
+}
+
+int helm_set_auxiliary(helm_plan_t p, double rho, int phase_quarters) {
+  if (!p || !std::isfinite(rho) || rho < 0.0 || rho > 8.0) return HELM_EINVAL;
+  HELM_CK(cudaStreamSynchronize(p->stream));
+  int rc = build_axis_aux(p, p->axo, rho, phase_quarters);
+  if (!rc && p->dim == 3) rc = build_axis_aux(p, p->axi, rho, phase_quarters);
+  if (rc) return rc;
+  if (p->dim == 2) {
+    const Solve2DArgs a = args2d(p);
+    HELM_CK(launch_pivots(p->prec, p->ustartB, a, 1, nullptr));
+    HELM_CK(cudaDeviceSynchronize());
+  }
   return HELM_OK;
 }
 

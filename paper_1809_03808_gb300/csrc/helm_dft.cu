@@ -146,6 +146,8 @@ __global__ void __launch_bounds__(256) k_dft_rows(const void* __restrict__ in, i
                                                   int L, DftPlan p,
                                                   const typename cpx<T>::type* __restrict__ tw, int sign,
                                                   T scale, double accum_scale,
+                                                  const typename cpx<T>::type* __restrict__ sc_in,
+                                                  const typename cpx<T>::type* __restrict__ sc_out,
                                                   const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
   if (skip && *skip) return;
@@ -157,7 +159,11 @@ __global__ void __launch_bounds__(256) k_dft_rows(const void* __restrict__ in, i
   const int Lh = (int)min((int64_t)L, nrows - row0);
   const int tot = Lh * n;
   const int64_t g0 = row0 * n;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) buf0[e] = load_in<T>(in, in_is_double, g0 + e);
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    C v = load_in<T>(in, in_is_double, g0 + e);
+    if (sc_in) v = cmul(v, sc_in[e % n]);
+    buf0[e] = v;
+  }
   __syncthreads();
   C* cur = buf0;
   C* nxt = buf1;
@@ -181,7 +187,11 @@ __global__ void __launch_bounds__(256) k_dft_rows(const void* __restrict__ in, i
     nxt = t;
     Ns *= R;
   }
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) store_out<C>(out, out_mode, g0 + e, cscale(cur[e], scale), accum_scale);
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    C v = cscale(cur[e], scale);
+    if (sc_out) v = cmul(v, sc_out[e % n]);
+    store_out<C>(out, out_mode, g0 + e, v, accum_scale);
+  }
 }
 
 // Column transform along a middle axis: array viewed as [outer][n][inner];
@@ -193,6 +203,8 @@ __global__ void __launch_bounds__(256) k_dft_cols(const void* __restrict__ in, i
                                                   int64_t inner, int TC, DftPlan p,
                                                   const typename cpx<T>::type* __restrict__ tw, int sign,
                                                   T scale, double accum_scale,
+                                                  const typename cpx<T>::type* __restrict__ sc_in,
+                                                  const typename cpx<T>::type* __restrict__ sc_out,
                                                   const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
   if (skip && *skip) return;
@@ -207,7 +219,11 @@ __global__ void __launch_bounds__(256) k_dft_cols(const void* __restrict__ in, i
   const int64_t g0 = slab * (int64_t)n * inner + c0;
   for (int e = threadIdx.x; e < n * TC; e += blockDim.x) {
     const int k = e / TC, c = e - k * TC;
-    if (c < TCh) buf0[e] = load_in<T>(in, in_is_double, g0 + (int64_t)k * inner + c);
+    if (c < TCh) {
+      C v = load_in<T>(in, in_is_double, g0 + (int64_t)k * inner + c);
+      if (sc_in) v = cmul(v, sc_in[k]);
+      buf0[e] = v;
+    }
   }
   __syncthreads();
   C* cur = buf0;
@@ -234,7 +250,11 @@ __global__ void __launch_bounds__(256) k_dft_cols(const void* __restrict__ in, i
   }
   for (int e = threadIdx.x; e < n * TC; e += blockDim.x) {
     const int k = e / TC, c = e - k * TC;
-    if (c < TCh) store_out<C>(out, out_mode, g0 + (int64_t)k * inner + c, cscale(cur[e], scale), accum_scale);
+    if (c < TCh) {
+      C v = cscale(cur[e], scale);
+      if (sc_out) v = cmul(v, sc_out[k]);
+      store_out<C>(out, out_mode, g0 + (int64_t)k * inner + c, v, accum_scale);
+    }
   }
 }
 
@@ -248,7 +268,8 @@ bool dft_supported(const DftPlan& p, size_t elem_bytes, int max_smem) {
 
 cudaError_t launch_dft_rows(int prec, const void* in, int in_is_double, void* out, int out_mode,
                             int64_t nrows, const DftPlan& p, const void* tw, int sign, double scale,
-                            double accum_scale, const int* skip, cudaStream_t st) {
+                            double accum_scale, const void* sc_in, const void* sc_out, const int* skip,
+                            cudaStream_t st) {
   const size_t es = prec == kPrecF64 ? sizeof(double2) : sizeof(float2);
   // lines per CTA: enough points to keep 256 threads busy, bounded by smem
   int L = (int)std::max<int64_t>(1, std::min<int64_t>(nrows, 2048 / std::max(1, p.n)));
@@ -260,21 +281,22 @@ cudaError_t launch_dft_rows(int prec, const void* in, int in_is_double, void* ou
     auto k = k_dft_rows<double>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<(unsigned)grid, 256, smem, st>>>(in, in_is_double, out, out_mode, nrows, L, p,
-                                         reinterpret_cast<const double2*>(tw), sign, scale,
-                                         accum_scale, skip);
+                                         reinterpret_cast<const double2*>(tw), sign, scale, accum_scale,
+                                         (const double2*)sc_in, (const double2*)sc_out, skip);
   } else {
     auto k = k_dft_rows<float>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<(unsigned)grid, 256, smem, st>>>(in, in_is_double, out, out_mode, nrows, L, p,
-                                         reinterpret_cast<const float2*>(tw), sign, (float)scale,
-                                         accum_scale, skip);
+                                         reinterpret_cast<const float2*>(tw), sign, (float)scale, accum_scale,
+                                         (const float2*)sc_in, (const float2*)sc_out, skip);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_dft_cols(int prec, const void* in, int in_is_double, void* out, int out_mode,
                             int64_t outer, int64_t inner, const DftPlan& p, const void* tw, int sign,
-                            double scale, double accum_scale, const int* skip, cudaStream_t st) {
+                            double scale, double accum_scale, const void* sc_in, const void* sc_out,
+                            const int* skip, cudaStream_t st) {
   const size_t es = prec == kPrecF64 ? sizeof(double2) : sizeof(float2);
   int TC = 16;
   while (TC > 1 && (size_t)2 * TC * p.n * es > 200 * 1024) TC /= 2;
@@ -286,14 +308,14 @@ cudaError_t launch_dft_cols(int prec, const void* in, int in_is_double, void* ou
     auto k = k_dft_cols<double>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<(unsigned)grid, 256, smem, st>>>(in, in_is_double, out, out_mode, outer, inner, TC, p,
-                                         reinterpret_cast<const double2*>(tw), sign, scale,
-                                         accum_scale, skip);
+                                         reinterpret_cast<const double2*>(tw), sign, scale, accum_scale,
+                                         (const double2*)sc_in, (const double2*)sc_out, skip);
   } else {
     auto k = k_dft_cols<float>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<(unsigned)grid, 256, smem, st>>>(in, in_is_double, out, out_mode, outer, inner, TC, p,
-                                         reinterpret_cast<const float2*>(tw), sign, (float)scale,
-                                         accum_scale, skip);
+                                         reinterpret_cast<const float2*>(tw), sign, (float)scale, accum_scale,
+                                         (const float2*)sc_in, (const float2*)sc_out, skip);
   }
   return cudaGetLastError();
 }

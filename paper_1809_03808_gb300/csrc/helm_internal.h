@@ -27,12 +27,30 @@ void unit_roots(int64_t n, double* re, double* im);
 
 // Per-axis eigen-data of an axis that carries a periodic auxiliary
 // (the paper's x1 in 2D; x1 and x2 in 3D), stored on the device as doubles.
+//
+// The auxiliary is the gamma-circulant pencil (K^B_g, M^B_g): the circulant
+// matrices of eqs. matrixKper / matrixMper with the wrap-around entries
+// multiplied by g (last row) and 1/g (first row), g = e^{n t},
+// t = (rho + i q pi/2)/n.  g = 1 (rho = q = 0) is the paper's periodic
+// auxiliary.  It is diagonalised by F D^-1 with D = diag(e^{t j}):
+//   K^B_g = D F^-1 diag(kappa_l) F D^-1,  kappa_l = (2 - 2 cosh(t + i theta_l))/h,
+//   M^B_g = D F^-1 diag(mu_l) F D^-1,     mu_l = h (4 + 2 cosh(t + i theta_l))/6.
 struct AxisData {
   int64_t n = 0;
   double h = 0;
+  double rho = 0;  // damping of the auxiliary (0: periodic)
+  int q = 0;       // phase of the auxiliary in quarter turns
   // device arrays (double)
-  double* lamB = nullptr;   // periodic eigenvalues Lam^B_l = kappa_l / mu_l (eq. eigvaluesPer)
-  double* muB = nullptr;    // mu_l = h (4 + 2 cos theta_l) / 6, eigenvalues of M^B
+  double* lamB = nullptr;   // Lam^B_l = kappa_l / mu_l, complex (re, im)
+  double* invmu = nullptr;  // 1 / mu_l, complex
+  double* sc_in = nullptr;  // e^{-t j}, j = 0..n-1, complex (nullptr when g = 1)
+  double* sc_out = nullptr; // e^{+t j}
+  float* sc_in32 = nullptr;
+  float* sc_out32 = nullptr;
+  double en[2] = {1, 0};     // e^{t (n-1)}
+  double eninv[2] = {1, 0};  // e^{-t (n-1)}
+  double g[2] = {1, 0};      // e^{n t}
+  double ginv[2] = {1, 0};   // e^{-n t}
   double* lamA = nullptr;   // absorbing eigenvalues (re, im) interleaved (eq. EVP1a)
   double* sigA = nullptr;   // V[1,l]^2 (re, im) interleaved (eq. EVPcondA)
   double* parA = nullptr;   // +-1 : V[n,l] = par * V[1,l]

@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "helm_internal.h"
+#include "helm_prof.h"
 
 namespace helm {
 
@@ -17,14 +18,15 @@ struct Solve2DArgs {
   double hx;      // tridiagonal-axis spacing
   double h1;      // x1 spacing
   double omega;
-  const double* lamB;
-  const double* muB;
+  const double* lamB;   // complex Lam^B_l of the auxiliary
+  const double* invmu;  // complex 1/mu_l
   const double* lamA;
   const double* sigA;
   const double* parA;
   const double* tw;
   int64_t ch;       // rows per chunk of the tridiagonal sweeps
   int64_t nchunks;  // ceil(nx / ch)
+  double eninv[2];  // e^{-t (n1-1)}: weight of the last x1 face in the Step-3 rhs
 };
 
 constexpr int kChunkF32 = 16;
@@ -35,13 +37,17 @@ constexpr int kChunkF64 = 8;
 // 3, A for 2); rec: nchunks*n1 chunk records; out: x (step 3); partial: face
 // sums (steps 1, 2).
 cudaError_t launch_tri2d(int prec, int step, const void* fhat, const void* faces, const void* ustart, void* rec,
-                         void* out, void* partial, const Solve2DArgs& a, const int* skip, cudaStream_t st);
+                         void* out, void* partial, const Solve2DArgs& a, const int* skip, cudaStream_t st,
+                         Profiler* prof);
 cudaError_t launch_pivots(int prec, void* ustart, const Solve2DArgs& a, int step, cudaStream_t st);
 size_t chunk_record_bytes(int prec);
+// out[face][ix] = scale_face * sum_w partial (complex scales, face 0 then 1).
 cudaError_t launch_reduce_faces(int prec, const void* partial, void* out, int64_t nx, int64_t nwarps,
-                                double scale, const int* skip, cudaStream_t st);
+                                const double* scale0, const double* scale1, const int* skip, cudaStream_t st);
+// C_bb of the auxiliary with wrap factor g (eq. Cbb; g = 1: periodic).
 cudaError_t launch_apply_cbb(int prec, const void* in, const void* in2, void* out, int64_t nx, double hx,
-                             double h1, double omega, double p, const int* skip, cudaStream_t st);
+                             double h1, double omega, double p, const double* g, const double* ginv,
+                             const int* skip, cudaStream_t st);
 
 // Refinement state kept on the device (one per plan).
 struct RefineState {

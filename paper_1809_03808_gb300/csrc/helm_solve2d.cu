@@ -43,15 +43,25 @@ struct ChunkRec {
   C a, bsum, pe, cc, we;
 };
 
+// Right-hand side of line lc at row ix.  Step 1: fhat / mu_l.  Step 2:
+// c_1 + par_l c_n.  Step 3: (fhat + d_1 + e^{+i theta_l} e^{-t(n1-1)} d_n) / mu_l
+// (wl = e^{+i theta_l} e^{-t(n1-1)}).
 template <typename C>
 __device__ __forceinline__ C line_rhs(int step, int64_t ix, int64_t lc, int64_t n1, const C* __restrict__ fhat,
-                                      const C* __restrict__ f1, const C* __restrict__ fn, decltype(C().x) scal,
-                                      decltype(C().x) par, C twl) {
-  if (step == 1) return cscale(fhat[ix * n1 + lc], scal);
+                                      const C* __restrict__ f1, const C* __restrict__ fn, C scal,
+                                      decltype(C().x) par, C wl) {
+  if (step == 1) return cmul(fhat[ix * n1 + lc], scal);
   if (step == 2) return cadd(f1[ix], cscale(fn[ix], par));
   C v = cadd(fhat[ix * n1 + lc], f1[ix]);
-  v = cadd(v, cmulc(fn[ix], twl));
-  return cscale(v, scal);
+  v = cadd(v, cmul(fn[ix], wl));
+  return cmul(v, scal);
+}
+
+template <typename C>
+__device__ __forceinline__ C step3_weight(const Solve2DArgs& a, int64_t l) {
+  // conj(tw_l) * e^{-t(n1-1)}
+  const C twc = mk<C>(a.tw[2 * l], -a.tw[2 * l + 1]);
+  return cmul(twc, mk<C>(a.eninv[0], a.eninv[1]));
 }
 
 struct LineParams {
@@ -64,8 +74,8 @@ __device__ __forceinline__ LineParams line_params(int step, const Solve2DArgs& a
     p.sre = a.lamA[2 * lc] - a.omega * a.omega;
     p.sim = a.lamA[2 * lc + 1];
   } else {
-    p.sre = a.lamB[lc] - a.omega * a.omega;
-    p.sim = 0.0;
+    p.sre = a.lamB[2 * lc] - a.omega * a.omega;
+    p.sim = a.lamB[2 * lc + 1];
   }
   return p;
 }
@@ -85,26 +95,28 @@ __global__ void __launch_bounds__(128) k_tri_pass1(const typename cpx<T>::type* 
   const int64_t s = k * a.ch, e = min(s + a.ch, nx) - 1;
   const LineParams lp = line_params(STEP, a, l);
   const LineCoef<C> co = line_coef<C>(lp.sre, lp.sim, a.hx, a.omega);
-  const T scal = (STEP == 2) ? T(1) : (T)(1.0 / a.muB[l]);
-  const C twl = mk<C>(a.tw[2 * l], a.tw[2 * l + 1]);
+  const C scal = (STEP == 2) ? mk<C>(1, 0) : mk<C>(a.invmu[2 * l], a.invmu[2 * l + 1]);
+  const C wl = step3_weight<C>(a, l);
   const T par = (T)a.parA[l];
   const C* f1 = faces;
   const C* fn = faces + nx;
   const C zero = mk<C>(0, 0);
-  C u = (k > 0) ? ustart[k * n1 + l] : zero;
+  // 1/u of the row before the chunk (the pivot entering it); carried so that
+  // each row needs one complex reciprocal
+  C inv = (k > 0) ? crecip(ustart[k * n1 + l]) : zero;
   C ylo = zero, P = zero, w = zero, bsum = zero, cc = zero;
   const C mb = mk<C>(-(double)co.b.x, -(double)co.b.y);  // -b
   for (int64_t j = s; j <= e; ++j) {
     const C aj = (j == 0 || j == nx - 1) ? co.ac : co.a;
-    const C r = line_rhs<C>(STEP, j, l, n1, fhat, f1, fn, scal, par, twl);
-    C m = zero;
+    const C r = line_rhs<C>(STEP, j, l, n1, fhat, f1, fn, scal, par, wl);
+    C m = zero, u;
     if (j > 0) {
-      m = cmul(co.b, crecip(u));
+      m = cmul(co.b, inv);
       u = csub(aj, cmul(m, co.b));
     } else {
       u = aj;
     }
-    const C inv = crecip(u);
+    inv = crecip(u);
     ylo = (j == s) ? r : csub(r, cmul(m, ylo));
     const C mm = mk<C>(-(double)m.x, -(double)m.y);
     P = (j == s) ? mm : cmul(P, mm);
@@ -172,8 +184,9 @@ __global__ void __launch_bounds__(128) k_tri_pass2(const typename cpx<T>::type* 
   const int cnt = (int)(e - s + 1);
   const LineParams lp = line_params(STEP, a, lc);
   const LineCoef<C> co = line_coef<C>(lp.sre, lp.sim, a.hx, a.omega);
-  const T scal = (STEP == 2) ? T(1) : (T)(1.0 / a.muB[lc]);
+  const C scal = (STEP == 2) ? mk<C>(1, 0) : mk<C>(a.invmu[2 * lc], a.invmu[2 * lc + 1]);
   const C twl = mk<C>(a.tw[2 * lc], a.tw[2 * lc + 1]);
+  const C wl = step3_weight<C>(a, lc);
   const T par = (T)a.parA[lc];
   const C sig = mk<C>(a.sigA[2 * lc], a.sigA[2 * lc + 1]);
   const C* f1 = faces;
@@ -181,22 +194,23 @@ __global__ void __launch_bounds__(128) k_tri_pass2(const typename cpx<T>::type* 
   const C zero = mk<C>(0, 0);
   C y[CH], iu[CH];
   const ChunkRec<C> R = rec[k * n1 + lc];
-  C u = (k > 0) ? ustart[k * n1 + lc] : zero;
+  C inv = (k > 0) ? crecip(ustart[k * n1 + lc]) : zero;
   C yp = R.a;  // Y(k-1)
 #pragma unroll
   for (int t = 0; t < CH; ++t) {
     if (t < cnt) {
       const int64_t j = s + t;
       const C aj = (j == 0 || j == nx - 1) ? co.ac : co.a;
-      const C r = line_rhs<C>(STEP, j, lc, n1, fhat, f1, fn, scal, par, twl);
-      C m = zero;
+      const C r = line_rhs<C>(STEP, j, lc, n1, fhat, f1, fn, scal, par, wl);
+      C m = zero, u;
       if (j > 0) {
-        m = cmul(co.b, crecip(u));
+        m = cmul(co.b, inv);
         u = csub(aj, cmul(m, co.b));
       } else {
         u = aj;
       }
-      iu[t] = crecip(u);
+      inv = crecip(u);
+      iu[t] = inv;
       yp = csub(r, cmul(m, yp));
       y[t] = yp;
     }
@@ -257,8 +271,8 @@ __global__ void k_pivots(typename cpx<T>::type* __restrict__ ustart, Solve2DArgs
 // Sum the per-warp partials: out[face * nx + ix] = scale * sum_w partial.
 template <typename T>
 __global__ void k_reduce_faces(const typename cpx<T>::type* __restrict__ partial,
-                               typename cpx<T>::type* __restrict__ out, int64_t nx, int64_t nwarps,
-                               double scale, const int* __restrict__ skip) {
+                               typename cpx<T>::type* __restrict__ out, int64_t nx, int64_t nwarps, double s0r,
+                               double s0i, double s1r, double s1i, const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
   if (skip && *skip) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -266,7 +280,7 @@ __global__ void k_reduce_faces(const typename cpx<T>::type* __restrict__ partial
   const int64_t face = i / nx, ix = i - face * nx;
   C acc = mk<C>(0, 0);
   for (int64_t w = 0; w < nwarps; ++w) acc = cadd(acc, partial[(face * nwarps + w) * nx + ix]);
-  out[i] = cscale(acc, (decltype(acc.x))scale);
+  out[i] = cmul(acc, face == 0 ? mk<C>(s0r, s0i) : mk<C>(s1r, s1i));
 }
 
 // C_bb applied to the x1 faces (eqs. BminA, Cbb):
@@ -278,7 +292,8 @@ template <typename T>
 __global__ void k_apply_cbb(const typename cpx<T>::type* __restrict__ in,
                             const typename cpx<T>::type* __restrict__ in2,
                             typename cpx<T>::type* __restrict__ out, int64_t nx, double hx, double h1,
-                            double omega, double p, const int* __restrict__ skip) {
+                            double omega, double p, double gr, double gi, double gir, double gii,
+                            const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
   if (skip && *skip) return;
   const int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -304,8 +319,11 @@ __global__ void k_apply_cbb(const typename cpx<T>::type* __restrict__ in,
   const C D11 = mk<C>(1.0 / h1 - p * h1 / 3.0, omega);
   const C D1n = mk<C>(-1.0 / h1 - p * h1 / 6.0, 0.0);
   const auto E11 = (decltype(D11.x))(h1 / 3.0), E1n = (decltype(D11.x))(h1 / 6.0);
-  C c1 = cadd(cadd(cmul(D11, Mv[0]), cscale(Kv[0], E11)), cadd(cmul(D1n, Mv[1]), cscale(Kv[1], E1n)));
-  C cn = cadd(cadd(cmul(D1n, Mv[0]), cscale(Kv[0], E1n)), cadd(cmul(D11, Mv[1]), cscale(Kv[1], E11)));
+  // wrap entries of the gamma-circulant: first row x 1/g, last row x g
+  C c1 = cadd(cadd(cmul(D11, Mv[0]), cscale(Kv[0], E11)),
+              cmul(mk<C>(gir, gii), cadd(cmul(D1n, Mv[1]), cscale(Kv[1], E1n))));
+  C cn = cadd(cmul(mk<C>(gr, gi), cadd(cmul(D1n, Mv[0]), cscale(Kv[0], E1n))),
+              cadd(cmul(D11, Mv[1]), cscale(Kv[1], E11)));
   out[ix] = c1;
   out[nx + ix] = cn;
 }
@@ -313,18 +331,31 @@ __global__ void k_apply_cbb(const typename cpx<T>::type* __restrict__ in,
 }  // namespace
 
 cudaError_t launch_tri2d(int prec, int step, const void* fhat, const void* faces, const void* ustart, void* rec,
-                         void* out, void* partial, const Solve2DArgs& a, const int* skip, cudaStream_t st) {
+                         void* out, void* partial, const Solve2DArgs& a, const int* skip, cudaStream_t st,
+                         Profiler* prof) {
+  static const char* n1s[3] = {"tri_step1_pass1", "tri_step2_pass1", "tri_step3_pass1"};
+  static const char* ncs[3] = {"tri_step1_carry", "tri_step2_carry", "tri_step3_carry"};
+  static const char* n2s[3] = {"tri_step1_pass2", "tri_step2_pass2", "tri_step3_pass2"};
   const int bs = 128;
   const dim3 grid((unsigned)((a.n1 + bs - 1) / bs), (unsigned)a.nchunks);
   const unsigned gl = (unsigned)((a.n1 + bs - 1) / bs);
 #define HELM_TRI(T, S, CH)                                                                                        \
   do {                                                                                                         \
     using C = cpx<T>::type;                                                                                    \
-    k_tri_pass1<T, S><<<grid, bs, 0, st>>>((const C*)fhat, (const C*)faces, (const C*)ustart, (ChunkRec<C>*)rec, \
-                                          a, skip);                                                           \
-    k_tri_carry<T, S><<<gl, bs, 0, st>>>((ChunkRec<C>*)rec, a, skip);                                          \
-    k_tri_pass2<T, S, CH><<<grid, bs, 0, st>>>((const C*)fhat, (const C*)faces, (const C*)ustart,              \
-                                              (const ChunkRec<C>*)rec, (C*)out, (C*)partial, a, skip);        \
+    {                                                                                                          \
+      ProfScope ps(prof, n1s[S - 1], st);                                                                      \
+      k_tri_pass1<T, S><<<grid, bs, 0, st>>>((const C*)fhat, (const C*)faces, (const C*)ustart,                \
+                                            (ChunkRec<C>*)rec, a, skip);                                      \
+    }                                                                                                          \
+    {                                                                                                          \
+      ProfScope ps(prof, ncs[S - 1], st);                                                                      \
+      k_tri_carry<T, S><<<gl, bs, 0, st>>>((ChunkRec<C>*)rec, a, skip);                                        \
+    }                                                                                                          \
+    {                                                                                                          \
+      ProfScope ps(prof, n2s[S - 1], st);                                                                      \
+      k_tri_pass2<T, S, CH><<<grid, bs, 0, st>>>((const C*)fhat, (const C*)faces, (const C*)ustart,            \
+                                                (const ChunkRec<C>*)rec, (C*)out, (C*)partial, a, skip);      \
+    }                                                                                                          \
   } while (0)
   if (prec == kPrecF64) {
     if (a.ch != kChunkF64) return cudaErrorInvalidValue;
@@ -354,26 +385,29 @@ cudaError_t launch_pivots(int prec, void* ustart, const Solve2DArgs& a, int step
 size_t chunk_record_bytes(int prec) { return prec == kPrecF64 ? sizeof(ChunkRec<double2>) : sizeof(ChunkRec<float2>); }
 
 cudaError_t launch_reduce_faces(int prec, const void* partial, void* out, int64_t nx, int64_t nwarps,
-                                double scale, const int* skip, cudaStream_t st) {
+                                const double* s0, const double* s1, const int* skip, cudaStream_t st) {
   const int bs = 256;
   const unsigned grid = (unsigned)((2 * nx + bs - 1) / bs);
   if (prec == kPrecF64)
-    k_reduce_faces<double><<<grid, bs, 0, st>>>((const double2*)partial, (double2*)out, nx, nwarps, scale, skip);
+    k_reduce_faces<double><<<grid, bs, 0, st>>>((const double2*)partial, (double2*)out, nx, nwarps, s0[0], s0[1],
+                                                s1[0], s1[1], skip);
   else
-    k_reduce_faces<float><<<grid, bs, 0, st>>>((const float2*)partial, (float2*)out, nx, nwarps, scale, skip);
+    k_reduce_faces<float><<<grid, bs, 0, st>>>((const float2*)partial, (float2*)out, nx, nwarps, s0[0], s0[1], s1[0],
+                                               s1[1], skip);
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply_cbb(int prec, const void* in, const void* in2, void* out, int64_t nx, double hx,
-                             double h1, double omega, double p, const int* skip, cudaStream_t st) {
+                             double h1, double omega, double p, const double* g, const double* ginv,
+                             const int* skip, cudaStream_t st) {
   const int bs = 256;
   const unsigned grid = (unsigned)((nx + bs - 1) / bs);
   if (prec == kPrecF64)
     k_apply_cbb<double><<<grid, bs, 0, st>>>((const double2*)in, (const double2*)in2, (double2*)out, nx, hx,
-                                             h1, omega, p, skip);
+                                             h1, omega, p, g[0], g[1], ginv[0], ginv[1], skip);
   else
     k_apply_cbb<float><<<grid, bs, 0, st>>>((const float2*)in, (const float2*)in2, (float2*)out, nx, hx, h1,
-                                            omega, p, skip);
+                                            omega, p, g[0], g[1], ginv[0], ginv[1], skip);
   return cudaGetLastError();
 }
 

@@ -27,10 +27,12 @@ namespace {
 struct Plane3DArgs {
   int64_t nx, ny, nz;
   double hx, hy, hz, omega;
-  // outer axis (y) eigen-data
-  const double *lamBo, *muBo, *lamAo, *sigAo, *parAo, *two;
+  // outer axis (y) eigen-data (Lam^B and 1/mu complex: gamma-circulant auxiliary)
+  const double *lamBo, *invmuo, *lamAo, *sigAo, *parAo, *two;
   // inner axis (z) eigen-data
-  const double *lamBi, *muBi, *lamAi, *sigAi, *parAi, *twi;
+  const double *lamBi, *invmui, *lamAi, *sigAi, *parAi, *twi;
+  double en_o[2], eninv_o[2], g_o[2], ginv_o[2];
+  double en_i[2], eninv_i[2], g_i[2], ginv_i[2];
 };
 
 constexpr int XC = 32;  // rows per reduction chunk
@@ -63,7 +65,7 @@ struct ThomasRow {
 // M, K along x; p = w^2 - Lam_{1,l} (complex for outer A modes).
 template <typename C>
 __device__ void plane_cbb(const C* v, const C* w2, C* out, int nx, double hx, double hz, double omega,
-                          double pre, double pim) {
+                          double pre, double pim, C g, C ginv) {
   for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
     auto get = [&](int face, int j) -> C {
       C t = v[face * nx + j];
@@ -85,14 +87,14 @@ __device__ void plane_cbb(const C* v, const C* w2, C* out, int nx, double hx, do
     const C D11 = mk<C>(1.0 / hz - pre * hz / 3.0, omega - pim * hz / 3.0);
     const C D1n = mk<C>(-1.0 / hz - pre * hz / 6.0, -pim * hz / 6.0);
     const auto E11 = (decltype(D11.x))(hz / 3.0), E1n = (decltype(D11.x))(hz / 6.0);
-    out[ix] = cadd(cadd(cmul(D11, Mv[0]), cscale(Kv[0], E11)), cadd(cmul(D1n, Mv[1]), cscale(Kv[1], E1n)));
-    out[nx + ix] = cadd(cadd(cmul(D1n, Mv[0]), cscale(Kv[0], E1n)), cadd(cmul(D11, Mv[1]), cscale(Kv[1], E11)));
+    out[ix] = cadd(cadd(cmul(D11, Mv[0]), cscale(Kv[0], E11)), cmul(ginv, cadd(cmul(D1n, Mv[1]), cscale(Kv[1], E1n))));
+    out[nx + ix] = cadd(cmul(g, cadd(cmul(D1n, Mv[0]), cscale(Kv[0], E1n))), cadd(cmul(D11, Mv[1]), cscale(Kv[1], E11)));
   }
 }
 
 // OSTEP 1: G = fhat / mu_l                        (outer Step 1, eq. 3dHBs1)
 // OSTEP 2: G = chat_1 + par_l chat_n, outer A mode (outer Step 2, eq. step2-2-3d)
-// OSTEP 3: G = (fhat + dhat_1 + e^{+2 pi i l/ny} dhat_n) / mu_l  (eq. 3dHBs3)
+// OSTEP 3: G = (fhat + dhat_1 + e^{+i theta_l} e^{-t(ny-1)} dhat_n) / mu_l  (eq. 3dHBs3)
 template <typename T, int OSTEP>
 __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* __restrict__ fhat,
                                                   typename cpx<T>::type* __restrict__ cbuf,
@@ -121,16 +123,19 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
     lo_re = a.lamAo[2 * l];
     lo_im = a.lamAo[2 * l + 1];
   } else {
-    lo_re = a.lamBo[l];
-    lo_im = 0.0;
+    lo_re = a.lamBo[2 * l];
+    lo_im = a.lamBo[2 * l + 1];
   }
-  const T gscale = (OSTEP == 2) ? T(1) : (T)(1.0 / a.muBo[l]);
+  const C gscale = (OSTEP == 2) ? mk<C>(1, 0) : mk<C>(a.invmuo[2 * l], a.invmuo[2 * l + 1]);
   const T paro = (T)a.parAo[l];
-  const C two_l = mk<C>(a.two[2 * l], a.two[2 * l + 1]);  // e^{-2 pi i l / ny}
+  // e^{+i theta_l} e^{-t(ny-1)}: weight of the last outer face in the Step-3 rhs
+  const C wl = cmul(mk<C>(a.two[2 * l], -a.two[2 * l + 1]), mk<C>(a.eninv_o[0], a.eninv_o[1]));
   // inner-mode quantities
-  const double lBi = a.lamBi[mc];
+  const double lBi_re = a.lamBi[2 * mc], lBi_im = a.lamBi[2 * mc + 1];
   const C twm = mk<C>(a.twi[2 * mc], a.twi[2 * mc + 1]);
-  const T invmu_i = (T)(1.0 / a.muBi[mc]);
+  const C wm = cmul(mk<C>(a.twi[2 * mc], -a.twi[2 * mc + 1]), mk<C>(a.eninv_i[0], a.eninv_i[1]));
+  const C invmu_i = mk<C>(a.invmui[2 * mc], a.invmui[2 * mc + 1]);
+  const C gi = mk<C>(a.g_i[0], a.g_i[1]), giv = mk<C>(a.ginv_i[0], a.ginv_i[1]);
   const T pari = (T)a.parAi[mc];
   const C sigi = mk<C>(a.sigAi[2 * mc], a.sigAi[2 * mc + 1]);
   const int64_t plane = l * nz + mc;                 // offset inside an x slab
@@ -138,14 +143,14 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
   const C* g1 = gfaces;                               // [2][nx][nz]
   const C* gn = gfaces ? gfaces + (int64_t)nx * nz : nullptr;
   auto G = [&](int ix) -> C {
-    if (OSTEP == 1) return cscale(fhat[ix * xs + plane], gscale);
+    if (OSTEP == 1) return cmul(fhat[ix * xs + plane], gscale);
     if (OSTEP == 2) return cadd(g1[(int64_t)ix * nz + mc], cscale(gn[(int64_t)ix * nz + mc], paro));
     C v = cadd(fhat[ix * xs + plane], g1[(int64_t)ix * nz + mc]);
-    v = cadd(v, cmulc(gn[(int64_t)ix * nz + mc], two_l));
-    return cscale(v, gscale);
+    v = cadd(v, cmul(gn[(int64_t)ix * nz + mc], wl));
+    return cmul(v, gscale);
   };
   ThomasRow<C> thB, thA;
-  thB.k = line_coef<C>(lo_re + lBi - w2, lo_im, a.hx, a.omega);
+  thB.k = line_coef<C>(lo_re + lBi_re - w2, lo_im + lBi_im, a.hx, a.omega);
   thB.n = nx;
   thA.k = line_coef<C>(lo_re + a.lamAi[2 * mc] - w2, lo_im + a.lamAi[2 * mc + 1], a.hx, a.omega);
   thA.n = nx;
@@ -162,7 +167,7 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
     }
   };
   // backward sweep reducing (s1, sn) contributions over m into out[2][nx]
-  auto backward_reduce = [&](auto contrib, C* out, T scale) {
+  auto backward_reduce = [&](auto contrib, C* out, C scale0, C scale1) {
     C x = mk<C>(0, 0);
     for (int x0 = nx - 1; x0 >= 0; x0 -= XC) {
       const int x1 = max(0, x0 - XC + 1);
@@ -186,21 +191,21 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
         const int face = t / cnt, j = t - face * cnt;
         C acc = mk<C>(0, 0);
         for (int w = 0; w < nw; ++w) acc = cadd(acc, red[(w * 2 + face) * XC + j]);
-        out[face * nx + (x0 - j)] = cscale(acc, scale);
+        out[face * nx + (x0 - j)] = cmul(acc, face == 0 ? scale0 : scale1);
       }
       __syncthreads();
     }
   };
 
   // inner Step 1: B-aux solve, reduce to inner faces v_in
-  forward(thB, [&](int ix) { return cscale(G(ix), invmu_i); });
+  forward(thB, [&](int ix) { return cmul(G(ix), invmu_i); });
   backward_reduce(
       [&](bool ac, C x, C& s1, C& sn) {
         s1 = ac ? x : mk<C>(0, 0);
         sn = ac ? cmul(x, twm) : mk<C>(0, 0);
       },
-      vin, (T)(1.0 / (double)nz));
-  plane_cbb(vin, (const C*)nullptr, cin, nx, a.hx, a.hz, a.omega, pre, pim);
+      vin, mk<C>(1.0 / (double)nz, 0), mk<C>(a.en_i[0] / (double)nz, a.en_i[1] / (double)nz));
+  plane_cbb(vin, (const C*)nullptr, cin, nx, a.hx, a.hz, a.omega, pre, pim, gi, giv);
   __syncthreads();
   // inner Step 2: A solve on the generated rhs, reduce to w_in
   forward(thA, [&](int ix) { return cadd(cin[ix], cscale(cin[nx + ix], pari)); });
@@ -210,14 +215,14 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
         s1 = t;
         sn = cscale(t, pari);
       },
-      win, T(1));
-  plane_cbb(vin, win, cin, nx, a.hx, a.hz, a.omega, pre, pim);
+      win, mk<C>(1, 0), mk<C>(1, 0));
+  plane_cbb(vin, win, cin, nx, a.hx, a.hz, a.omega, pre, pim, gi, giv);
   __syncthreads();
   // inner Step 3: corrected B-aux solve, y3 written over the scratch
   forward(thB, [&](int ix) {
     C v = cadd(G(ix), cin[ix]);
-    v = cadd(v, cmulc(cin[nx + ix], twm));
-    return cscale(v, invmu_i);
+    v = cadd(v, cmul(cin[nx + ix], wm));
+    return cmul(v, invmu_i);
   });
   if (act) {
     C x = mk<C>(0, 0);
@@ -255,7 +260,7 @@ __global__ void k_reduce_outer(const typename cpx<T>::type* __restrict__ y3, typ
   }
   if (OSTEP == 1) {
     s1 = cscale(s1, (decltype(s1.x))(1.0 / (double)ny));
-    sn = cscale(sn, (decltype(sn.x))(1.0 / (double)ny));
+    sn = cmul(sn, mk<C>(a.en_o[0] / (double)ny, a.en_o[1] / (double)ny));
   }
   out[i] = s1;
   out[a.nx * nz + i] = sn;
@@ -263,8 +268,9 @@ __global__ void k_reduce_outer(const typename cpx<T>::type* __restrict__ y3, typ
 
 // Outer C_bb on the y faces (eq. Cbb for eq. B3D - A3D): with P = M_x (x) M_z
 // and S = K_x (x) M_z + M_x (x) K_z - w^2 M_x (x) M_z on the (x, z) plane,
-//   c_1 = (hy/3) S v_1 + ((1 + i w hy)/hy) P v_1 + (hy/6) S v_n - (1/hy) P v_n,
-//   c_n = (hy/6) S v_1 - (1/hy) P v_1 + (hy/3) S v_n + ((1 + i w hy)/hy) P v_n.
+//   c_1 = (hy/3) S v_1 + ((1 + i w hy)/hy) P v_1 + g^-1 [(hy/6) S v_n - (1/hy) P v_n],
+//   c_n = g [(hy/6) S v_1 - (1/hy) P v_1] + (hy/3) S v_n + ((1 + i w hy)/hy) P v_n,
+// g the wrap factor of the gamma-circulant auxiliary (1: periodic).
 template <typename T>
 __global__ void k_outer_cbb(const typename cpx<T>::type* __restrict__ v, const typename cpx<T>::type* __restrict__ w,
                             typename cpx<T>::type* __restrict__ out, Plane3DArgs a, const int* __restrict__ skip) {
@@ -312,8 +318,9 @@ __global__ void k_outer_cbb(const typename cpx<T>::type* __restrict__ v, const t
   const T2 e11 = (T2)(a.hy / 3.0), e1n = (T2)(a.hy / 6.0);
   const C d11 = mk<C>(1.0 / a.hy, a.omega);
   const T2 d1n = (T2)(-1.0 / a.hy);
-  out[i] = cadd(cadd(cscale(Sv[0], e11), cmul(d11, Pv[0])), cadd(cscale(Sv[1], e1n), cscale(Pv[1], d1n)));
-  out[nx * nz + i] = cadd(cadd(cscale(Sv[0], e1n), cscale(Pv[0], d1n)), cadd(cscale(Sv[1], e11), cmul(d11, Pv[1])));
+  const C g = mk<C>(a.g_o[0], a.g_o[1]), gv = mk<C>(a.ginv_o[0], a.ginv_o[1]);
+  out[i] = cadd(cadd(cscale(Sv[0], e11), cmul(d11, Pv[0])), cmul(gv, cadd(cscale(Sv[1], e1n), cscale(Pv[1], d1n))));
+  out[nx * nz + i] = cadd(cmul(g, cadd(cscale(Sv[0], e1n), cscale(Pv[0], d1n))), cadd(cscale(Sv[1], e11), cmul(d11, Pv[1])));
 }
 
 Plane3DArgs make_args(const Plan3D& p) {
@@ -326,17 +333,27 @@ Plane3DArgs make_args(const Plan3D& p) {
   a.hz = p.h[2];
   a.omega = p.omega;
   a.lamBo = p.axo->lamB;
-  a.muBo = p.axo->muB;
+  a.invmuo = p.axo->invmu;
   a.lamAo = p.axo->lamA;
   a.sigAo = p.axo->sigA;
   a.parAo = p.axo->parA;
   a.two = p.axo->tw;
   a.lamBi = p.axi->lamB;
-  a.muBi = p.axi->muB;
+  a.invmui = p.axi->invmu;
   a.lamAi = p.axi->lamA;
   a.sigAi = p.axi->sigA;
   a.parAi = p.axi->parA;
   a.twi = p.axi->tw;
+  for (int k = 0; k < 2; ++k) {
+    a.en_o[k] = p.axo->en[k];
+    a.eninv_o[k] = p.axo->eninv[k];
+    a.g_o[k] = p.axo->g[k];
+    a.ginv_o[k] = p.axo->ginv[k];
+    a.en_i[k] = p.axi->en[k];
+    a.eninv_i[k] = p.axi->eninv[k];
+    a.g_i[k] = p.axi->g[k];
+    a.ginv_i[k] = p.axi->ginv[k];
+  }
   return a;
 }
 
@@ -387,6 +404,11 @@ cudaError_t solve3d_t(Plan3D& p, const void* in, int in_is_double, void* out, in
   const void* two = prec == kPrecF64 ? (const void*)p.axo->tw : (const void*)p.axo->tw32;
   const void* twi = prec == kPrecF64 ? (const void*)p.axi->tw : (const void*)p.axi->tw32;
   const int cmode = prec == kPrecF64 ? kOutC128 : kOutC64;
+  const bool f64 = prec == kPrecF64;
+  const void* sci_i = f64 ? (const void*)p.axi->sc_in : (const void*)p.axi->sc_in32;
+  const void* sco_i = f64 ? (const void*)p.axi->sc_out : (const void*)p.axi->sc_out32;
+  const void* sci_o = f64 ? (const void*)p.axo->sc_in : (const void*)p.axo->sc_in32;
+  const void* sco_o = f64 ? (const void*)p.axo->sc_out : (const void*)p.axo->sc_out32;
   C* faces = (C*)p.faces;
   C* Vh = faces;           // reduced outer rows, inner-mode space   [2][nx][nz]
   C* v = faces + 2 * F;    // outer rows of v, physical
@@ -404,29 +426,31 @@ cudaError_t solve3d_t(Plan3D& p, const void* in, int in_is_double, void* out, in
     CK(x);                                  \
   } while (0)
   // a1: 2D DFT over (y, z): rows along z, then columns along y (in place)
-  PK("dft_z_fwd", launch_dft_rows(prec, in, in_is_double, p.fhat, cmode, nx * ny, p.axi->dft, twi, -1, 1.0, 0.0, skip, st));
-  PK("dft_y_fwd", launch_dft_cols(prec, p.fhat, prec == kPrecF64, p.fhat, cmode, nx, nz, p.axo->dft, two, -1, 1.0, 0.0, skip, st));
+  PK("dft_z_fwd", launch_dft_rows(prec, in, in_is_double, p.fhat, cmode, nx * ny, p.axi->dft, twi, -1, 1.0, 0.0, sci_i,
+                                  nullptr, skip, st));
+  PK("dft_y_fwd", launch_dft_cols(prec, p.fhat, f64, p.fhat, cmode, nx, nz, p.axo->dft, two, -1, 1.0, 0.0, sci_o, nullptr,
+                                  skip, st));
   if (dbg_fhat) CK(cudaMemcpyAsync(dbg_fhat, p.fhat, nx * ny * nz * sizeof(C), cudaMemcpyDeviceToDevice, st));
   // outer Step 1
   PK("plane3d_step1", launch_plane<T>(1, p, nullptr, skip, st));
   PK("reduce_outer", launch_reduce_outer<T>(1, p, Vh, skip, st));
-  CK(launch_dft_rows(prec, Vh, prec == kPrecF64, v, cmode, 2 * nx, p.axi->dft, twi, +1, 1.0 / (double)nz, 0.0, skip, st));
+  CK(launch_dft_rows(prec, Vh, f64, v, cmode, 2 * nx, p.axi->dft, twi, +1, 1.0 / (double)nz, 0.0, nullptr, sco_i, skip, st));
   if (dbg_v) CK(cudaMemcpyAsync(dbg_v, v, 2 * F * sizeof(C), cudaMemcpyDeviceToDevice, st));
   CK(launch_outer_cbb<T>(p, v, nullptr, c, skip, st));
-  CK(launch_dft_rows(prec, c, prec == kPrecF64, ch, cmode, 2 * nx, p.axi->dft, twi, -1, 1.0, 0.0, skip, st));
+  CK(launch_dft_rows(prec, c, f64, ch, cmode, 2 * nx, p.axi->dft, twi, -1, 1.0, 0.0, sci_i, nullptr, skip, st));
   // outer Step 2
   PK("plane3d_step2", launch_plane<T>(2, p, ch, skip, st));
   PK("reduce_outer", launch_reduce_outer<T>(2, p, Vh, skip, st));
-  CK(launch_dft_rows(prec, Vh, prec == kPrecF64, w, cmode, 2 * nx, p.axi->dft, twi, +1, 1.0 / (double)nz, 0.0, skip, st));
+  CK(launch_dft_rows(prec, Vh, f64, w, cmode, 2 * nx, p.axi->dft, twi, +1, 1.0 / (double)nz, 0.0, nullptr, sco_i, skip, st));
   if (dbg_w) CK(cudaMemcpyAsync(dbg_w, w, 2 * F * sizeof(C), cudaMemcpyDeviceToDevice, st));
   CK(launch_outer_cbb<T>(p, v, w, c, skip, st));
-  CK(launch_dft_rows(prec, c, prec == kPrecF64, ch, cmode, 2 * nx, p.axi->dft, twi, -1, 1.0, 0.0, skip, st));
+  CK(launch_dft_rows(prec, c, f64, ch, cmode, 2 * nx, p.axi->dft, twi, -1, 1.0, 0.0, sci_i, nullptr, skip, st));
   // outer Step 3, then the inverse 2D DFT
   PK("plane3d_step3", launch_plane<T>(3, p, ch, skip, st));
-  PK("dft_y_inv", launch_dft_cols(prec, p.dbuf, prec == kPrecF64, p.dbuf, cmode, nx, nz, p.axo->dft, two, +1, 1.0 / (double)ny, 0.0,
-                     skip, st));
-  PK("dft_z_inv", launch_dft_rows(prec, p.dbuf, prec == kPrecF64, out, out_mode, nx * ny, p.axi->dft, twi, +1, 1.0 / (double)nz,
-                     accum_scale, skip, st));
+  PK("dft_y_inv", launch_dft_cols(prec, p.dbuf, f64, p.dbuf, cmode, nx, nz, p.axo->dft, two, +1, 1.0 / (double)ny, 0.0,
+                                  nullptr, sco_o, skip, st));
+  PK("dft_z_inv", launch_dft_rows(prec, p.dbuf, f64, out, out_mode, nx * ny, p.axi->dft, twi, +1, 1.0 / (double)nz,
+                                  accum_scale, nullptr, sco_i, skip, st));
 #undef PK
 #undef CK
   return cudaSuccess;

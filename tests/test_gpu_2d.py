@@ -60,12 +60,15 @@ def _oracle(shape, h, omega, seed):
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("dtype", ["c128", "c64_refined", "c64_raw"])
-def test_solve_matches_oracle(env, name, dtype):
+@pytest.mark.parametrize("aux", ["damped", "periodic"])
+def test_solve_matches_oracle(env, name, dtype, aux):
     helm, torch = env
     shape, h, omega = CASES[name]
-    f, u_ref = _oracle(shape, h, omega, seed=hash(name) % 1000)
+    f, u_ref = _oracle(shape, h, omega, seed=sum(map(ord, name)) % 1000)
     code = {"c128": helm.HELM_C128, "c64_refined": helm.HELM_C64_REFINED, "c64_raw": helm.HELM_C64_RAW}[dtype]
     plan = helm.Plan(shape, h, omega, code)
+    if aux == "periodic":
+        helm.helm_set_auxiliary(plan.handle, 0.0, 0)
     tdt = torch.complex64 if dtype == "c64_raw" else torch.complex128
     fd = torch.from_numpy(f).to("cuda").to(tdt)
     u = plan.solve(fd)
@@ -74,7 +77,7 @@ def test_solve_matches_oracle(env, name, dtype):
     un = u.cpu().numpy().astype(np.complex128)
     err = np.linalg.norm(un - u_ref) / np.linalg.norm(u_ref)
     errmax = np.abs(un - u_ref).max() / np.abs(u_ref).max()
-    print(f"{name} {dtype}: rel_err={err:.3e} max={errmax:.3e} iters={info.iterations} "
+    print(f"{name} {dtype} {aux}: rel_err={err:.3e} max={errmax:.3e} iters={info.iterations} "
           f"resid={list(info.residual[:info.iterations + 1])}")
     assert np.all(np.isfinite(un))
     if dtype == "c64_raw":
@@ -85,16 +88,25 @@ def test_solve_matches_oracle(env, name, dtype):
             assert st == helm.HELM_OK and info.converged == 1
 
 
+AUX = [(0.0, 0), (1.0, 1), (0.5, 2)]
+
+
 @pytest.mark.parametrize("name", ["tiny_9x7", "aniso_40x24", "c1_129x129_16pi"])
-def test_stepwise_intermediates(env, name):
+@pytest.mark.parametrize("rho,q", AUX)
+def test_stepwise_intermediates(env, name, rho, q):
     """Each step of Section 4.2 against its plain definition: f_hat = DFT of f
-    along x1 (eq. step1FFTfcoeff), v_b = boundary rows of B^-1 f (eq. 2dBs1),
-    w_b = boundary rows of A^-1 (B - A) v (eq. step2-3)."""
+    along x1 (eq. step1FFTfcoeff; with the gamma-circulant auxiliary, of
+    e^{-t j} f), v_b = boundary rows of B^-1 f (eq. 2dBs1), w_b = boundary rows
+    of A^-1 (B - A) v (eq. step2-3), for the paper's periodic B (rho = q = 0)
+    and damped ones."""
     helm, torch = env
     shape, h, omega = CASES[name]
     f = random_rhs(shape, 77)
-    v, w, u_ref = solvers.step_definitions(f, h, omega, axis=1)
+    g = np.exp(rho + 0.5j * np.pi * q)
+    t = (rho + 0.5j * np.pi * q) / shape[1]
+    v, w, u_ref = solvers.step_definitions(f, h, omega, axis=1, gamma=g)
     plan = helm.Plan(shape, h, omega, helm.HELM_C128)
+    helm.helm_set_auxiliary(plan.handle, rho, q)
     fd = torch.from_numpy(f).cuda()
     u = torch.empty_like(fd)
     fhat = torch.empty_like(fd)
@@ -104,7 +116,7 @@ def test_stepwise_intermediates(env, name):
     helm.helm_solve_debug(plan.handle, fd, u, fhat, vb, wb)
     torch.cuda.synchronize()
     plan.close()
-    fh_ref = np.fft.fft(f, axis=1)
+    fh_ref = np.fft.fft(f * np.exp(-t * np.arange(shape[1]))[None, :], axis=1)
     assert np.linalg.norm(fhat.cpu().numpy() - fh_ref) / np.linalg.norm(fh_ref) < 1e-13
     vb_ref = np.stack([v[:, 0], v[:, -1]])
     wb_ref = np.stack([w[:, 0], w[:, -1]])

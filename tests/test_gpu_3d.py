@@ -46,7 +46,8 @@ CASES = {
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("dtype", ["c128", "c64_refined", "c64_raw"])
-def test_solve3d_matches_oracle(env, name, dtype):
+@pytest.mark.parametrize("aux", ["damped", "periodic"])
+def test_solve3d_matches_oracle(env, name, dtype, aux):
     helm, torch = env
     shape, h, omega = CASES[name]
     f = random_rhs(shape, 31 + len(name))
@@ -54,13 +55,15 @@ def test_solve3d_matches_oracle(env, name, dtype):
     assert hist[-1] < 1e-13
     code = {"c128": helm.HELM_C128, "c64_refined": helm.HELM_C64_REFINED, "c64_raw": helm.HELM_C64_RAW}[dtype]
     plan = helm.Plan(shape, h, omega, code)
+    if aux == "periodic":
+        helm.helm_set_auxiliary(plan.handle, 0.0, 0)
     tdt = torch.complex64 if dtype == "c64_raw" else torch.complex128
     u = plan.solve(torch.from_numpy(f).to("cuda").to(tdt))
     info, st = plan.info()
     plan.close()
     un = u.cpu().numpy().astype(np.complex128)
     err = np.linalg.norm(un - u_ref) / np.linalg.norm(u_ref)
-    print(f"{name} {dtype}: rel_err={err:.3e} iters={info.iterations}")
+    print(f"{name} {dtype} {aux}: rel_err={err:.3e} iters={info.iterations}")
     assert np.all(np.isfinite(un))
     if dtype == "c64_raw":
         assert err < 5e-2
@@ -69,15 +72,20 @@ def test_solve3d_matches_oracle(env, name, dtype):
 
 
 @pytest.mark.parametrize("name", ["tiny_5x6x7", "aniso_12x17x10"])
-def test_stepwise_intermediates_3d(env, name):
+@pytest.mark.parametrize("rho,q", [(0.0, 0), (1.0, 1)])
+def test_stepwise_intermediates_3d(env, name, rho, q):
     """Outer Steps of Section 5.2 against their definitions: f_hat is the DFT
-    over the two periodic axes, v_b / w_b the outer boundary rows of B^-1 f and
-    A^-1 (B - A) v (eqs. 3dBs1, step2-3-3d), with B periodic along y."""
+    over the two periodic axes (of the scaled f for the gamma-circulant
+    auxiliary), v_b / w_b the outer boundary rows of B^-1 f and
+    A^-1 (B - A) v (eqs. 3dBs1, step2-3-3d), with B periodic (or damped
+    periodic) along y."""
     helm, torch = env
     shape, h, omega = CASES[name]
     f = random_rhs(shape, 99)
-    v, w, u_ref = solvers.step_definitions(f, h, omega, axis=1)
+    g = np.exp(rho + 0.5j * np.pi * q)
+    v, w, u_ref = solvers.step_definitions(f, h, omega, axis=1, gamma=g)
     plan = helm.Plan(shape, h, omega, helm.HELM_C128)
+    helm.helm_set_auxiliary(plan.handle, rho, q)
     fd = torch.from_numpy(f).cuda()
     u = torch.empty_like(fd)
     fhat = torch.empty_like(fd)
@@ -87,7 +95,10 @@ def test_stepwise_intermediates_3d(env, name):
     helm.helm_solve_debug(plan.handle, fd, u, fhat, vb, wb)
     torch.cuda.synchronize()
     plan.close()
-    fh_ref = np.fft.fft2(f, axes=(1, 2))
+    ty = (rho + 0.5j * np.pi * q) / shape[1]
+    tz = (rho + 0.5j * np.pi * q) / shape[2]
+    scale = np.exp(-ty * np.arange(shape[1]))[None, :, None] * np.exp(-tz * np.arange(shape[2]))[None, None, :]
+    fh_ref = np.fft.fft2(f * scale, axes=(1, 2))
     assert np.linalg.norm(fhat.cpu().numpy() - fh_ref) / np.linalg.norm(fh_ref) < 1e-13
     vb_ref = np.stack([v[:, 0, :], v[:, -1, :]])
     wb_ref = np.stack([w[:, 0, :], w[:, -1, :]])

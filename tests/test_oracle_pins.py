@@ -281,3 +281,42 @@ def test_c_residual_equals_pinned_numpy_residual(shape, h):
     r1 = fem.residual_dd(f, u, h, 3.3)
     r2 = fem.residual_dd_c(f, u, h, 3.3)
     assert np.array_equal(r1, r2)
+
+
+@pytest.mark.parametrize("n,h,rho,phi", [(8, 0.1, 1.0, np.pi / 2), (9, 1 / 8, 0.5, 0.0), (31, 0.03, 2.0, np.pi)])
+def test_gamma_circulant_is_diagonalised_by_scaled_dft(n, h, rho, phi):
+    """The damped auxiliary: with gamma = e^{rho + i phi} and t = (rho + i phi)/n,
+    F D^-1 K^B_gamma D F^-1 is diagonal with D = diag(e^{t j}), eigenvalues
+    (2 - 2 cosh(t + i theta_l))/h and h (4 + 2 cosh(t + i theta_l))/6
+    (gamma = 1 reduces to eq. eigvaluesPer)."""
+    g = np.exp(rho + 1j * phi)
+    t = (rho + 1j * phi) / n
+    KB, MB = fem.K1d_periodic(n, h, g), fem.M1d_periodic(n, h, g)
+    F = np.exp(-2j * np.pi * np.outer(np.arange(n), np.arange(n)) / n)
+    D = np.diag(np.exp(t * np.arange(n)))
+    Di = np.diag(np.exp(-t * np.arange(n)))
+    Fi = np.conj(F) / n
+    th = 2 * np.pi * np.arange(n) / n
+    for Mat, ev in ((KB, (2 - 2 * np.cosh(t + 1j * th)) / h), (MB, h * (4 + 2 * np.cosh(t + 1j * th)) / 6)):
+        Dg = F @ Di @ Mat @ D @ Fi
+        assert np.abs(Dg - np.diag(np.diag(Dg))).max() < 1e-10 * np.abs(ev).max()
+        np.testing.assert_allclose(np.diag(Dg), ev, rtol=1e-10, atol=1e-10 * np.abs(ev).max())
+    # gamma = 1 is the paper's circulant
+    assert np.allclose(fem.K1d_periodic(n, h, 1.0), fem.K1d_periodic(n, h).real)
+
+
+def test_damped_auxiliary_step_identities():
+    """u = v + w also holds with the gamma-circulant auxiliary (B - A stays on
+    the boundary rows of the periodic axis)."""
+    shape, h, om = (7, 9), (1 / 6, 1 / 8), 7.0
+    f = random_rhs(shape, 12)
+    g = np.exp(1.0 + 0.5j * np.pi)
+    v, w, u = solvers.step_definitions(f, h, om, axis=1, gamma=g)
+    assert np.linalg.norm(v + w - u) / np.linalg.norm(u) < 1e-12
+    A = fem.kron_operator(shape, h, om)
+    B = fem.kron_operator(shape, h, om, periodic_axis=1, gamma=g)
+    D = (B - A).tocoo()
+    keep = np.abs(D.data) > 0
+    iy = np.unravel_index(np.arange(A.shape[0]), shape)[1]
+    onb = (iy == 0) | (iy == shape[1] - 1)
+    assert np.all(onb[D.row[keep]]) and np.all(onb[D.col[keep]])
