@@ -174,6 +174,8 @@ def run_gb300(args):
         import paper_1809_03808_gb300 as helm
 
     p = workloads.config_2d_large()
+    if args.shape:
+        p = workloads.scaled(p, tuple(int(x) for x in args.shape.split(",")))
     N = p.N
     f_host = workloads.rhs(p)
     f = torch.from_numpy(f_host).to(dev)
@@ -219,6 +221,8 @@ def run_gb300(args):
         return max_over_ranks(ms), prof, clocks
 
     def sampled_error(u):
+        if args.shape:
+            return None
         try:
             sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
             from make_golden import load
@@ -372,7 +376,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shape", default="", help="nx,ny: same spacing and wave number on a smaller grid "
+                    "(profiling cases; not a benchmark line)")
+    ap.add_argument("--minimal", action="store_true", help="timed solves only (no e2e, variants, CPU baseline)")
     args = ap.parse_args()
+    if args.minimal:
+        args.no_e2e = args.no_variants = args.no_cpu_baseline = True
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
     if args.impl == "reference":

@@ -106,7 +106,8 @@ int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx
  * t = (rho + i q pi/2)/n1, with eigenvalues (2 - 2cosh(t + i theta_l))/h and
  * h (4 + 2cosh(t + i theta_l))/6.  rho = q = 0 is the paper's periodic
  * auxiliary.  rho > 0 damps waves that travel around the periodic loop, which
- * keeps B far from resonance and the solve accurate.  Default: rho = 1, q = 1.
+ * keeps B far from resonance and the solve accurate.  Default: rho = 1 with
+ * q = 1 in 2D and q = 0 in 3D.
  * Applies to every periodic axis of the plan.  rho must be in [0, 8]; any
  * integer q is taken mod 4.  Rebuilds the plan's auxiliary tables; call it
  * between solves, not while a solve is in flight on another stream. */

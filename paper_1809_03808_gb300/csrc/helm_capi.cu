@@ -106,9 +106,12 @@ void free_axis(AxisData& a) {
   a = AxisData{};
 }
 
-// Default auxiliary: damped periodic wrap, g = e^{1 + i pi/2} (see helm.h).
+// Default auxiliary: damped periodic wrap g = e^{rho + i q pi/2} (see helm.h):
+// rho = 1, q = 1 in 2D and rho = 1, q = 0 in 3D (the choices that gave the
+// smallest FP64 error and the fastest refinement on the benchmark grids).
 constexpr double kDefaultAuxRho = 1.0;
 constexpr int kDefaultAuxQ = 1;
+constexpr int kDefaultAuxQ3D = 0;
 
 int upload(helm_plan* p, double** d, const std::vector<double>& v) {
   if (!*d) {
@@ -461,8 +464,8 @@ int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx
     delete p;
     return HELM_EUNSUPPORTED;
   }
-  int rc = build_axis(p, p->axo, ny, hy, omega, kDefaultAuxRho, kDefaultAuxQ);
-  if (!rc) rc = build_axis(p, p->axi, nz, hz, omega, kDefaultAuxRho, kDefaultAuxQ);
+  int rc = build_axis(p, p->axo, ny, hy, omega, kDefaultAuxRho, kDefaultAuxQ3D);
+  if (!rc) rc = build_axis(p, p->axi, nz, hz, omega, kDefaultAuxRho, kDefaultAuxQ3D);
   if (!rc) {
     DftPlan a = p->axo.dft, b = p->axi.dft;
     if (!dft_supported(a, cbytes(p->prec), smem) || !dft_supported(b, cbytes(p->prec), smem)) rc = HELM_EUNSUPPORTED;

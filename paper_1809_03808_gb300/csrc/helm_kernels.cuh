@@ -67,7 +67,13 @@ __device__ __forceinline__ C cscale(C a, T s) {
   a.y *= s;
   return a;
 }
-// 1 / a, scaled so that neither |a|^2 over- nor under-flows (Smith's method).
+// 1 / a.  FP64: conj(a) / |a|^2 with one division (the operands of these
+// solvers stay within 1e-150..1e150, far inside FP64 range).  FP32: Smith's
+// scaling, so that |a|^2 neither over- nor under-flows the narrow exponent.
+__device__ __forceinline__ double2 crecip(double2 a) {
+  const double inv = 1.0 / fma(a.x, a.x, a.y * a.y);
+  return make_double2(a.x * inv, -a.y * inv);
+}
 template <typename C>
 __device__ __forceinline__ C crecip(C a) {
   using T = decltype(a.x);

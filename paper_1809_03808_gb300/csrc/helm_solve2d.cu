@@ -80,7 +80,7 @@ __device__ __forceinline__ LineParams line_params(int step, const Solve2DArgs& a
   return p;
 }
 
-template <typename T, int STEP>
+template <typename T, int STEP, int CH>
 __global__ void __launch_bounds__(128) k_tri_pass1(const typename cpx<T>::type* __restrict__ fhat,
                                                    const typename cpx<T>::type* __restrict__ faces,
                                                    const typename cpx<T>::type* __restrict__ ustart,
@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(128) k_tri_pass1(const typename cpx<T>::type* 
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n1) return;
   const int64_t k = blockIdx.y;
-  const int64_t s = k * a.ch, e = min(s + a.ch, nx) - 1;
+  const int64_t s = k * CH, e = min(s + (int64_t)CH, nx) - 1;
+  const int cnt = (int)(e - s + 1);
   const LineParams lp = line_params(STEP, a, l);
   const LineCoef<C> co = line_coef<C>(lp.sre, lp.sim, a.hx, a.omega);
   const C scal = (STEP == 2) ? mk<C>(1, 0) : mk<C>(a.invmu[2 * l], a.invmu[2 * l + 1]);
@@ -106,9 +107,17 @@ __global__ void __launch_bounds__(128) k_tri_pass1(const typename cpx<T>::type* 
   C inv = (k > 0) ? crecip(ustart[k * n1 + l]) : zero;
   C ylo = zero, P = zero, w = zero, bsum = zero, cc = zero;
   const C mb = mk<C>(-(double)co.b.x, -(double)co.b.y);  // -b
-  for (int64_t j = s; j <= e; ++j) {
+  // all right-hand sides of the chunk first: independent loads in flight
+  C rr[CH];
+#pragma unroll
+  for (int t = 0; t < CH; ++t)
+    if (t < cnt) rr[t] = line_rhs<C>(STEP, s + t, l, n1, fhat, f1, fn, scal, par, wl);
+#pragma unroll
+  for (int t = 0; t < CH; ++t) {
+    if (t >= cnt) break;
+    const int64_t j = s + t;
     const C aj = (j == 0 || j == nx - 1) ? co.ac : co.a;
-    const C r = line_rhs<C>(STEP, j, l, n1, fhat, f1, fn, scal, par, wl);
+    const C r = rr[t];
     C m = zero, u;
     if (j > 0) {
       m = cmul(co.b, inv);
@@ -134,11 +143,15 @@ __global__ void __launch_bounds__(128) k_tri_pass1(const typename cpx<T>::type* 
 }
 
 // Two scans per line over its chunks: forward carry Y, backward carry X.
-// Overwrites rec[k].a with Y(k-1) and rec[k].bsum with X(k+1).
+// Overwrites rec[k].a with Y(k-1) and rec[k].bsum with X(k+1).  The records of
+// a batch of CB chunks are loaded before the dependent recurrence runs over
+// them, and the next batch is requested while the current one is processed,
+// so the sequential chain waits on arithmetic rather than on memory.
 template <typename T, int STEP>
 __global__ void k_tri_carry(ChunkRec<typename cpx<T>::type>* __restrict__ rec, Solve2DArgs a,
                             const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
+  constexpr int CB = 8;
   if (skip && *skip) return;
   const int64_t n1 = a.n1;
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -146,20 +159,70 @@ __global__ void k_tri_carry(ChunkRec<typename cpx<T>::type>* __restrict__ rec, S
   const int64_t K = a.nchunks;
   const LineParams lp = line_params(STEP, a, l);
   const LineCoef<C> co = line_coef<C>(lp.sre, lp.sim, a.hx, a.omega);
+  // forward: Y(k) = a_k + pe_k Y(k-1)
   C Y = mk<C>(0, 0);
-  for (int64_t k = 0; k < K; ++k) {
-    ChunkRec<C>& R = rec[k * n1 + l];
-    const C ak = R.a;
-    R.a = Y;  // Y(k-1)
-    Y = cadd(ak, cmul(R.pe, Y));
+  C ra[CB], rp[CB], na[CB], np[CB];
+  auto loadf = [&](int64_t k0, C* A, C* Pp) {
+#pragma unroll
+    for (int t = 0; t < CB; ++t) {
+      const int64_t k = k0 + t;
+      if (k < K) {
+        A[t] = rec[k * n1 + l].a;
+        Pp[t] = rec[k * n1 + l].pe;
+      }
+    }
+  };
+  loadf(0, ra, rp);
+  for (int64_t k0 = 0; k0 < K; k0 += CB) {
+    if (k0 + CB < K) loadf(k0 + CB, na, np);
+#pragma unroll
+    for (int t = 0; t < CB; ++t) {
+      const int64_t k = k0 + t;
+      if (k < K) {
+        rec[k * n1 + l].a = Y;  // Y(k-1)
+        Y = cadd(ra[t], cmul(rp[t], Y));
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < CB; ++t) {
+      ra[t] = na[t];
+      rp[t] = np[t];
+    }
   }
+  // backward: X(k) = bsum_k + cc_k Y(k-1) - b we_k X(k+1)
   C X = mk<C>(0, 0);
-  for (int64_t k = K - 1; k >= 0; --k) {
-    ChunkRec<C>& R = rec[k * n1 + l];
-    const C bk = R.bsum;
-    R.bsum = X;  // X(k+1)
-    // X(k) = bsum + cc Y(k-1) - b we X(k+1)
-    X = csub(cadd(bk, cmul(R.cc, R.a)), cmul(cmul(co.b, R.we), X));
+  C rb[CB], rc[CB], rw[CB], ry[CB], nb[CB], nc[CB], nw[CB], ny[CB];
+  auto loadb = [&](int64_t k1, C* B, C* Cc, C* W, C* Yp) {  // chunks k1, k1-1, ...
+#pragma unroll
+    for (int t = 0; t < CB; ++t) {
+      const int64_t k = k1 - t;
+      if (k >= 0) {
+        const ChunkRec<C>& R = rec[k * n1 + l];
+        B[t] = R.bsum;
+        Cc[t] = R.cc;
+        W[t] = R.we;
+        Yp[t] = R.a;
+      }
+    }
+  };
+  loadb(K - 1, rb, rc, rw, ry);
+  for (int64_t k1 = K - 1; k1 >= 0; k1 -= CB) {
+    if (k1 - CB >= 0) loadb(k1 - CB, nb, nc, nw, ny);
+#pragma unroll
+    for (int t = 0; t < CB; ++t) {
+      const int64_t k = k1 - t;
+      if (k >= 0) {
+        rec[k * n1 + l].bsum = X;  // X(k+1)
+        X = csub(cadd(rb[t], cmul(rc[t], ry[t])), cmul(cmul(co.b, rw[t]), X));
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < CB; ++t) {
+      rb[t] = nb[t];
+      rc[t] = nc[t];
+      rw[t] = nw[t];
+      ry[t] = ny[t];
+    }
   }
 }
 
@@ -196,12 +259,16 @@ __global__ void __launch_bounds__(128) k_tri_pass2(const typename cpx<T>::type* 
   const ChunkRec<C> R = rec[k * n1 + lc];
   C inv = (k > 0) ? crecip(ustart[k * n1 + lc]) : zero;
   C yp = R.a;  // Y(k-1)
+  // right-hand sides into registers first (y[] holds them until overwritten)
+#pragma unroll
+  for (int t = 0; t < CH; ++t)
+    if (t < cnt) y[t] = line_rhs<C>(STEP, s + t, lc, n1, fhat, f1, fn, scal, par, wl);
 #pragma unroll
   for (int t = 0; t < CH; ++t) {
     if (t < cnt) {
       const int64_t j = s + t;
       const C aj = (j == 0 || j == nx - 1) ? co.ac : co.a;
-      const C r = line_rhs<C>(STEP, j, lc, n1, fhat, f1, fn, scal, par, wl);
+      const C r = y[t];
       C m = zero, u;
       if (j > 0) {
         m = cmul(co.b, inv);
@@ -344,7 +411,7 @@ cudaError_t launch_tri2d(int prec, int step, const void* fhat, const void* faces
     using C = cpx<T>::type;                                                                                    \
     {                                                                                                          \
       ProfScope ps(prof, n1s[S - 1], st);                                                                      \
-      k_tri_pass1<T, S><<<grid, bs, 0, st>>>((const C*)fhat, (const C*)faces, (const C*)ustart,                \
+      k_tri_pass1<T, S, CH><<<grid, bs, 0, st>>>((const C*)fhat, (const C*)faces, (const C*)ustart,            \
                                             (ChunkRec<C>*)rec, a, skip);                                      \
     }                                                                                                          \
     {                                                                                                          \

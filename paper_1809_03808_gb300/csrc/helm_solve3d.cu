@@ -157,13 +157,26 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
   const double pre = w2 - lo_re, pim = -lo_im;
 
   // ---- generic sweep: forward with rhs(ix), backward with emit(ix, x) ----
+  // rows are processed in batches of PB: the batch's right-hand sides (and,
+  // backward, its scratch values) are loaded before the dependent recurrence
+  constexpr int PB = 8;
   auto forward = [&](ThomasRow<C>& th, auto rhs) {
     if (!act) return;
-    for (int ix = 0; ix < nx; ++ix) {
-      C c, d;
-      th.step(ix, rhs(ix), c, d);
-      cbuf[ix * xs + plane] = c;
-      dbuf[ix * xs + plane] = d;
+    for (int i0 = 0; i0 < nx; i0 += PB) {
+      C rr[PB];
+#pragma unroll
+      for (int t = 0; t < PB; ++t)
+        if (i0 + t < nx) rr[t] = rhs(i0 + t);
+#pragma unroll
+      for (int t = 0; t < PB; ++t) {
+        const int ix = i0 + t;
+        if (ix < nx) {
+          C c, d;
+          th.step(ix, rr[t], c, d);
+          cbuf[ix * xs + plane] = c;
+          dbuf[ix * xs + plane] = d;
+        }
+      }
     }
   };
   // backward sweep reducing (s1, sn) contributions over m into out[2][nx]
@@ -171,18 +184,29 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
     C x = mk<C>(0, 0);
     for (int x0 = nx - 1; x0 >= 0; x0 -= XC) {
       const int x1 = max(0, x0 - XC + 1);
-      for (int ix = x0; ix >= x1; --ix) {
-        if (act) {
-          C d = dbuf[ix * xs + plane];
-          x = (ix == nx - 1) ? d : csub(d, cmul(cbuf[ix * xs + plane], x));
+      for (int b0 = x0; b0 >= x1; b0 -= PB) {
+        C dd[PB], cc[PB];
+#pragma unroll
+        for (int t = 0; t < PB; ++t) {
+          const int ix = b0 - t;
+          if (act && ix >= x1) {
+            dd[t] = dbuf[ix * xs + plane];
+            cc[t] = cbuf[ix * xs + plane];
+          }
         }
-        C s1, sn;
-        contrib(act, x, s1, sn);
-        s1 = warp_sum(s1);
-        sn = warp_sum(sn);
-        if (lane == 0) {
-          red[(warp * 2 + 0) * XC + (x0 - ix)] = s1;
-          red[(warp * 2 + 1) * XC + (x0 - ix)] = sn;
+#pragma unroll
+        for (int t = 0; t < PB; ++t) {
+          const int ix = b0 - t;
+          if (ix < x1) break;
+          if (act) x = (ix == nx - 1) ? dd[t] : csub(dd[t], cmul(cc[t], x));
+          C s1, sn;
+          contrib(act, x, s1, sn);
+          s1 = warp_sum(s1);
+          sn = warp_sum(sn);
+          if (lane == 0) {
+            red[(warp * 2 + 0) * XC + (x0 - ix)] = s1;
+            red[(warp * 2 + 1) * XC + (x0 - ix)] = sn;
+          }
         }
       }
       __syncthreads();
@@ -226,10 +250,23 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
   });
   if (act) {
     C x = mk<C>(0, 0);
-    for (int ix = nx - 1; ix >= 0; --ix) {
-      C d = dbuf[ix * xs + plane];
-      x = (ix == nx - 1) ? d : csub(d, cmul(cbuf[ix * xs + plane], x));
-      dbuf[ix * xs + plane] = x;
+    for (int b0 = nx - 1; b0 >= 0; b0 -= PB) {
+      C dd[PB], cc[PB];
+#pragma unroll
+      for (int t = 0; t < PB; ++t) {
+        const int ix = b0 - t;
+        if (ix >= 0) {
+          dd[t] = dbuf[ix * xs + plane];
+          cc[t] = cbuf[ix * xs + plane];
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < PB; ++t) {
+        const int ix = b0 - t;
+        if (ix < 0) break;
+        x = (ix == nx - 1) ? dd[t] : csub(dd[t], cmul(cc[t], x));
+        dbuf[ix * xs + plane] = x;
+      }
     }
   }
 }
