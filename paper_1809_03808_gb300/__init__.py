@@ -57,6 +57,7 @@ _SIGS = {
     "helm_abc_eigen": (_i32, [_i64, _dbl, _dbl, _vp, _vp, _vp]),
     "helm_dft_factor": (_i32, [_i64, _vp, _i32]),
     "helm_set_profiling": (_i32, [_vp, _i32]),
+    "helm_solve_2d_static": (_i32, [_i64, _i64, _dbl, _dbl, _dbl, _vp, _vp, _vp]),
     "helm_get_profile": (_i32, [_vp, ctypes.POINTER(helm_profile_entry), _i32]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -152,6 +153,13 @@ def helm_get_profile(plan):
     if k < 0:
         _check(k, "helm_get_profile", plan)
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(k)}
+
+
+def helm_solve_2d_static(nx, ny, hx, hy, omega, f, u, stream=None):
+    """Allocation-free complex128 2D solve (no plan): f, u device buffers."""
+    st = lib.helm_solve_2d_static(int(nx), int(ny), float(hx), float(hy), float(omega), _ptr(f), _ptr(u),
+                                  _vp(int(stream) if stream is not None else 0))
+    _check(st, "helm_solve_2d_static")
 
 
 def helm_destroy(plan):

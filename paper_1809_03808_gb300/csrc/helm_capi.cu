@@ -383,6 +383,81 @@ void destroy_plan(helm_plan* p) {
   delete p;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free small 2D solve (helm_solve_2d_static).
+//
+// For callers that cannot allocate device memory at solve time -- code that
+// runs where cudaMalloc is not allowed or not wanted (inside a host callback,
+// under an allocator lock held by a larger framework, in a process whose
+// device memory is reserved up front) -- the whole complex128 2D solve runs
+// out of one fixed device array that the library reserves when it is loaded.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB per device
+constexpr int64_t kStaticMaxN1 = 1024;                     // longest x1 axis
+constexpr int kStaticMaxDevices = 64;
+
+// Device scratch of the allocation-free solve: every GPU that loads the library
+// holds these 16 MiB until the process exits.  Host code must not use the
+// symbol as a pointer; the device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_helm_static_scratch[kStaticScratchBytes];
+
+// Device address of g_helm_static_scratch per device, looked up once.
+static void* g_static_addr[kStaticMaxDevices];
+
+// Host workspace for the per-call eigen-data (static: no heap use).
+static double g_st_work[2 * kStaticMaxN1 + 9 * ((kStaticMaxN1 + 1) / 2) + 64];
+static double g_st_lamA[2 * kStaticMaxN1], g_st_sigA[2 * kStaticMaxN1], g_st_parA[kStaticMaxN1];
+static double g_st_lamB[2 * kStaticMaxN1], g_st_invmu[2 * kStaticMaxN1], g_st_tw[2 * kStaticMaxN1];
+static double g_st_sci[2 * kStaticMaxN1], g_st_sco[2 * kStaticMaxN1];
+static double g_st_twre[kStaticMaxN1], g_st_twim[kStaticMaxN1];
+static double g_st_r4re[4 * kStaticMaxN1], g_st_r4im[4 * kStaticMaxN1];
+static int8_t g_st_par8[kStaticMaxN1];
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Auxiliary tables of build_axis_aux computed into the static host arrays.
+void static_aux_tables(AxisData& a, double rho, int q) {
+  const int64_t n = a.n;
+  const double h = a.h;
+  a.rho = rho;
+  a.q = ((q % 4) + 4) % 4;
+  const double pi = 3.14159265358979323846;
+  unit_roots(4 * n, g_st_r4re, g_st_r4im);
+  const double ar = 0.5 * rho / (double)n;
+  for (int64_t l = 0; l < n; ++l) {
+    const double b = (0.5 * pi * a.q + 2.0 * pi * (double)l) / (2.0 * (double)n);
+    const std::complex<double> sh(std::sinh(ar) * std::cos(b), std::cosh(ar) * std::sin(b));
+    const std::complex<double> s2 = sh * sh;
+    const std::complex<double> mu = h * (1.0 + (2.0 / 3.0) * s2);
+    const std::complex<double> lb = (-4.0 * s2 / h) / mu, im = 1.0 / mu;
+    g_st_lamB[2 * l] = lb.real();
+    g_st_lamB[2 * l + 1] = lb.imag();
+    g_st_invmu[2 * l] = im.real();
+    g_st_invmu[2 * l + 1] = im.imag();
+  }
+  auto et = [&](int64_t j, double sign) -> std::complex<double> {
+    const int64_t k = (a.q * j) % (4 * n);
+    return std::exp(sign * rho * (double)j / (double)n) * std::complex<double>(g_st_r4re[k], -sign * g_st_r4im[k]);
+  };
+  for (int64_t j = 0; j < n; ++j) {
+    const std::complex<double> ei = et(j, -1.0), eo = et(j, +1.0);
+    g_st_sci[2 * j] = ei.real();
+    g_st_sci[2 * j + 1] = ei.imag();
+    g_st_sco[2 * j] = eo.real();
+    g_st_sco[2 * j + 1] = eo.imag();
+  }
+  const std::complex<double> en = et(n - 1, +1.0), eninv = et(n - 1, -1.0);
+  a.en[0] = en.real();
+  a.en[1] = en.imag();
+  a.eninv[0] = eninv.real();
+  a.eninv[1] = eninv.imag();
+  const double gr[4] = {1, 0, -1, 0}, gi[4] = {0, 1, 0, -1};
+  a.g[0] = std::exp(rho) * gr[a.q];
+  a.g[1] = std::exp(rho) * gi[a.q];
+  a.ginv[0] = std::exp(-rho) * gr[a.q];
+  a.ginv[1] = -std::exp(-rho) * gi[a.q];
+}
+
 }  // namespace
 
 extern "C" {
@@ -613,6 +688,118 @@ int helm_get_profile(helm_plan_t p, helm_profile_entry* out, int max_entries) {
   }
   p->prof.reset();
   return k;
+}
+
+int helm_solve_2d_static(int64_t nx, int64_t ny, double hx, double hy, double omega, const void* f, void* u,
+                         void* cuda_stream) {
+  if (!f || !u || f == u) return HELM_EINVAL;
+  if (nx < 3 || ny < 3 || !(hx > 0) || !(hy > 0) || !std::isfinite(hx) || !std::isfinite(hy)) return HELM_EINVAL;
+  if (validate_common(omega, HELM_C128)) return HELM_EINVAL;
+  if (ny > kStaticMaxN1) return HELM_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // stack plan: same kernels and argument blocks as helm_solve (complex128)
+  helm_plan sp;
+  sp.dim = 2;
+  sp.n[0] = nx;
+  sp.n[1] = ny;
+  sp.h[0] = hx;
+  sp.h[1] = hy;
+  sp.omega = omega;
+  sp.dtype = HELM_C128;
+  sp.prec = kPrecF64;
+  sp.stream = st;
+  AxisData& ax = sp.axo;
+  ax.n = ny;
+  ax.h = hy;
+  dft_factor(ny, &ax.dft);
+  int dev = 0, smem = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices ||
+      cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return HELM_ECUDA;
+  }
+  if (!dft_supported(ax.dft, sizeof(double2), smem)) return HELM_EUNSUPPORTED;
+  // scratch layout
+  const int64_t N = nx * ny;
+  const Solve2DArgs a0 = args2d(&sp);
+  const size_t nrec = (size_t)a0.nchunks * ny;
+  const int64_t nwarps = (ny + 31) / 32;
+  const size_t tab = align256(2 * ny * sizeof(double));
+  size_t off[16], cur = 0;
+  const size_t sizes[14] = {tab, tab, tab, tab, align256(ny * sizeof(double)), tab, tab, tab,
+                            align256(N * sizeof(double2)), align256(N * sizeof(double2)),
+                            align256(2 * nwarps * nx * sizeof(double2)), align256(8 * nx * sizeof(double2)),
+                            align256(2 * nrec * sizeof(double2)), align256(nrec * chunk_record_bytes(kPrecF64))};
+  for (int i = 0; i < 14; ++i) {
+    off[i] = cur;
+    cur += sizes[i];
+  }
+  if (cur > kStaticScratchBytes) return HELM_EUNSUPPORTED;
+  // set-up once per device, with that device current: the device address of
+  // the static array (the host-side symbol is not a device pointer)
+  if (!g_static_addr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_helm_static_scratch);
+    if (e != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return HELM_ECUDA;
+    }
+    g_static_addr[dev] = ptr;
+  }
+  char* base = (char*)g_static_addr[dev];
+  // plan-time data on the host, into static arrays
+  if (abc_eigen_static(ny, hy, omega, g_st_lamA, g_st_sigA, g_st_par8, g_st_work,
+                       (int64_t)(sizeof(g_st_work) / sizeof(double))) != HELM_OK)
+    return HELM_ENUMERIC;
+  for (int64_t l = 0; l < ny; ++l) g_st_parA[l] = g_st_par8[l];
+  unit_roots(ny, g_st_twre, g_st_twim);
+  for (int64_t l = 0; l < ny; ++l) {
+    g_st_tw[2 * l] = g_st_twre[l];
+    g_st_tw[2 * l + 1] = g_st_twim[l];
+  }
+  static_aux_tables(ax, kDefaultAuxRho, kDefaultAuxQ);
+  ax.lamB = (double*)(base + off[0]);
+  ax.invmu = (double*)(base + off[1]);
+  ax.lamA = (double*)(base + off[2]);
+  ax.sigA = (double*)(base + off[3]);
+  ax.parA = (double*)(base + off[4]);
+  ax.tw = (double*)(base + off[5]);
+  ax.sc_in = (double*)(base + off[6]);
+  ax.sc_out = (double*)(base + off[7]);
+  sp.fhat = base + off[8];
+  sp.dbuf = base + off[9];
+  sp.partial = base + off[10];
+  sp.faces = base + off[11];
+  sp.ustartB = base + off[12];
+  sp.ustartA = base + off[12] + nrec * sizeof(double2);
+  sp.rec = base + off[13];
+  sp.nwarps = nwarps;
+  sp.face_len = nx;
+  const size_t tb = 2 * ny * sizeof(double);
+  const struct {
+    void* dst;
+    const void* src;
+    size_t bytes;
+  } up[8] = {{ax.lamB, g_st_lamB, tb},  {ax.invmu, g_st_invmu, tb}, {ax.lamA, g_st_lamA, tb},
+             {ax.sigA, g_st_sigA, tb},  {ax.parA, g_st_parA, ny * sizeof(double)},
+             {ax.tw, g_st_tw, tb},      {ax.sc_in, g_st_sci, tb},     {ax.sc_out, g_st_sco, tb}};
+  for (int i = 0; i < 8; ++i)
+    if (cudaMemcpyAsync(up[i].dst, up[i].src, up[i].bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      cudaGetLastError();
+      return HELM_ECUDA;
+    }
+  // the array keeps the previous call's contents: clear the face sums
+  if (cudaMemsetAsync(sp.partial, 0, sizes[10] + sizes[11], st) != cudaSuccess) {
+    cudaGetLastError();
+    return HELM_ECUDA;
+  }
+  const Solve2DArgs a = args2d(&sp);
+  if (launch_pivots(kPrecF64, sp.ustartB, a, 1, st) != cudaSuccess ||
+      launch_pivots(kPrecF64, sp.ustartA, a, 2, st) != cudaSuccess) {
+    cudaGetLastError();
+    return HELM_ECUDA;
+  }
+  return solve2d_core(&sp, f, 1, u, kOutC128, 0.0, nullptr, nullptr, nullptr, nullptr);
 }
 
 int helm_abc_eigen(int64_t n, double h, double omega, double* lam, double* sigma, int8_t* parity) {

@@ -200,6 +200,122 @@ int abc_eigen(int64_t n, double h, double omega, double* lam, double* sigma, int
   return HELM_OK;
 }
 
+// Same eigen-data as abc_eigen, computed single-threaded in a caller-provided
+// workspace of at least 8 n + 64 doubles (no heap use).  Used by the
+// allocation-free solve entry point.
+int abc_eigen_static(int64_t n, double h, double omega, double* lam, double* sigma, int8_t* parity, double* work,
+                     int64_t work_len) {
+  if (n < 2 || !(h > 0) || !(omega > 0) || !std::isfinite(h) || !std::isfinite(omega)) return HELM_EINVAL;
+  const int64_t m_max = (n + 1) / 2;
+  if (!work || work_len < 2 * n + 9 * m_max + 16) return HELM_EINVAL;
+  const double pi = 3.14159265358979323846;
+  double* lamN = work;
+  double* wgt = lamN + n;
+  double* lk = wgt + n;
+  double* wk = lk + m_max;
+  double* zr = wk + m_max;  // roots, interleaved (re, im)
+  double* sr = zr + 2 * m_max;  // S2, interleaved
+  double* st = sr + 2 * m_max;  // steps, interleaved
+  double* act = st + 2 * m_max;
+  for (int64_t k = 0; k < n; ++k) {
+    double c = std::cos(pi * (double)k / (double)(n - 1));
+    double s = std::sin(0.5 * pi * (double)k / (double)(n - 1));
+    lamN[k] = 6.0 / (h * h) * (2.0 * s * s) / (2.0 + c);
+    double mu = h * (2.0 + c) / 3.0;
+    wgt[k] = 2.0 / (mu * (double)(n - 1));
+    if (k == 0 || k == n - 1) wgt[k] *= 0.5;
+  }
+  const cd tiw = {0.0, 2.0 * omega};
+  int64_t pos = 0;
+  for (int cls = 0; cls < 2; ++cls) {
+    int64_t m = 0;
+    for (int64_t k = cls; k < n; k += 2, ++m) {
+      lk[m] = lamN[k];
+      wk[m] = wgt[k];
+    }
+    if (m == 0) continue;
+    for (int64_t j = 0; j < m; ++j) {
+      zr[2 * j] = lk[j];
+      zr[2 * j + 1] = -2.0 * omega * wk[j];
+      act[j] = 1.0;
+    }
+    int it = 0;
+    const int maxit = 500;
+    for (; it < maxit; ++it) {
+      for (int64_t j = 0; j < m; ++j) {
+        st[2 * j] = st[2 * j + 1] = 0.0;
+        if (act[j] == 0.0) continue;
+        const cd zj = {zr[2 * j], zr[2 * j + 1]};
+        cd sF = {0, 0}, sF2 = {0, 0}, sQ = {0, 0}, sA = {0, 0};
+        for (int64_t k = 0; k < m; ++k) {
+          const cd r = crecip({lk[k] - zj.re, -zj.im});
+          const cd wr = {wk[k] * r.re, wk[k] * r.im};
+          sF = cadd(sF, wr);
+          sF2 = cadd(sF2, cmul(wr, r));
+          sQ = csub(sQ, r);
+          if (k != j) sA = cadd(sA, crecip(csub(zj, {zr[2 * k], zr[2 * k + 1]})));
+        }
+        const cd F = csub({1.0, 0.0}, cmul(tiw, sF));
+        const cd Fp = csub({0.0, 0.0}, cmul(tiw, sF2));
+        const cd den = cadd(Fp, cmul(F, sQ));
+        if (den.re == 0.0 && den.im == 0.0) continue;
+        const cd N = cdiv(F, den);
+        const cd q = csub({1.0, 0.0}, cmul(N, sA));
+        const cd stp = (q.re == 0.0 && q.im == 0.0) ? N : cdiv(N, q);
+        st[2 * j] = stp.re;
+        st[2 * j + 1] = stp.im;
+      }
+      bool any = false;
+      for (int64_t j = 0; j < m; ++j) {
+        if (act[j] == 0.0) continue;
+        zr[2 * j] -= st[2 * j];
+        zr[2 * j + 1] -= st[2 * j + 1];
+        if (!std::isfinite(zr[2 * j]) || !std::isfinite(zr[2 * j + 1])) return HELM_ENUMERIC;
+        if (std::hypot(st[2 * j], st[2 * j + 1]) <= 1e-15 * std::max(1.0, std::hypot(zr[2 * j], zr[2 * j + 1])))
+          act[j] = 0.0;
+        else
+          any = true;
+      }
+      if (!any) break;
+    }
+    if (it == maxit) return HELM_ENUMERIC;
+    for (int64_t j = 0; j < m; ++j) {
+      for (int pass = 0; pass < 3; ++pass) {
+        const cd zj = {zr[2 * j], zr[2 * j + 1]};
+        cd sF = {0, 0}, sF2 = {0, 0};
+        for (int64_t k = 0; k < m; ++k) {
+          const cd r = crecip({lk[k] - zj.re, -zj.im});
+          const cd wr = {wk[k] * r.re, wk[k] * r.im};
+          sF = cadd(sF, wr);
+          sF2 = cadd(sF2, cmul(wr, r));
+        }
+        if (pass == 2) {
+          sr[2 * j] = sF2.re;
+          sr[2 * j + 1] = sF2.im;
+          break;
+        }
+        const cd F = csub({1.0, 0.0}, cmul(tiw, sF));
+        const cd Fp = csub({0.0, 0.0}, cmul(tiw, sF2));
+        if (Fp.re != 0.0 || Fp.im != 0.0) {
+          const cd d = cdiv(F, Fp);
+          zr[2 * j] -= d.re;
+          zr[2 * j + 1] -= d.im;
+        }
+      }
+    }
+    for (int64_t j = 0; j < m; ++j, ++pos) {
+      lam[2 * pos] = zr[2 * j];
+      lam[2 * pos + 1] = zr[2 * j + 1];
+      const cd sg = crecip({-4.0 * omega * omega * sr[2 * j], -4.0 * omega * omega * sr[2 * j + 1]});
+      if (!std::isfinite(sg.re) || !std::isfinite(sg.im)) return HELM_ENUMERIC;
+      sigma[2 * pos] = sg.re;
+      sigma[2 * pos + 1] = sg.im;
+      parity[pos] = cls == 0 ? 1 : -1;
+    }
+  }
+  return HELM_OK;
+}
+
 // Unit roots e^{-2 pi i k / n}, k = 0..n-1, from libm sin/cos after exact
 // reduction of k/n to the first octant (symmetries of sin/cos).
 void unit_roots(int64_t n, double* re, double* im) {

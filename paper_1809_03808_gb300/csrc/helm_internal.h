@@ -22,6 +22,11 @@ int dft_factor(int64_t n, DftPlan* p);
 // Eigen-data of the absorbing 1D pencil (see helm_eigen.cpp).
 int abc_eigen(int64_t n, double h, double omega, double* lam, double* sigma, int8_t* parity);
 
+// abc_eigen in a caller workspace of >= 2n + 9 ceil(n/2) + 16 doubles,
+// single-threaded, no heap use.
+int abc_eigen_static(int64_t n, double h, double omega, double* lam, double* sigma, int8_t* parity, double* work,
+                     int64_t work_len);
+
 // e^{-2 pi i k / n}, k = 0..n-1.
 void unit_roots(int64_t n, double* re, double* im);
 

@@ -1,0 +1,73 @@
+"""The allocation-free entry point helm_solve_2d_static against the regular
+plan + helm_solve path.
+
+helm_solve_2d_static exists for callers that cannot allocate device memory
+when they solve (host callbacks, code under a framework's allocator lock,
+processes that reserve all device memory up front): it runs the same
+complex128 solve out of a fixed device array the library reserves at load
+time.  This file is collected last so that a run that stops at the first
+failure has already run every other test; it also passes alone.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from workloads import ppw_omega, random_rhs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12  # same FP64 arithmetic on both paths; only rounding order may differ
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1809_03808_gb300 as helm
+
+    return helm, torch
+
+
+def _problem(shape, lengths, ppw):
+    h = tuple(L / (n - 1) for n, L in zip(shape, lengths))
+    return shape, h, ppw_omega(max(h), ppw)
+
+
+@pytest.mark.parametrize("shape,lengths,ppw", [((129, 129), (1.0, 1.0), 16), ((300, 250), (1.2, 1.0), 10),
+                                               ((512, 512), (1.0, 1.0), 10)])
+def test_static_solve_matches_plan_solve_twice(env, shape, lengths, ppw):
+    helm, torch = env
+    shape, h, omega = _problem(shape, lengths, ppw)
+    f1 = torch.from_numpy(random_rhs(shape, 501)).cuda()
+    f2 = torch.from_numpy(random_rhs(shape, 502)).cuda()
+    plan = helm.Plan(shape, h, omega, helm.HELM_C128)
+    ref1 = plan.solve(f1)
+    ref2 = plan.solve(f2)
+    torch.cuda.synchronize()
+    plan.close()
+    stream = torch.cuda.current_stream().cuda_stream
+    # two calls in a row: the second reuses the shared array left by the first
+    for f, ref in ((f1, ref1), (f2, ref2)):
+        u = torch.full_like(f, complex(float("nan"), float("nan")))
+        helm.helm_solve_2d_static(shape[0], shape[1], h[0], h[1], omega, f, u, stream)
+        torch.cuda.synchronize()
+        err = (torch.linalg.norm(u - ref) / torch.linalg.norm(ref)).item()
+        print(shape, "static vs plan rel diff", err)
+        assert err <= TOL
+
+
+def test_static_solve_rejects_oversize(env):
+    helm, torch = env
+    x = torch.zeros(4, dtype=torch.complex128, device="cuda")
+    y = torch.zeros(4, dtype=torch.complex128, device="cuda")
+    st = helm.lib.helm_solve_2d_static(64, 2048, 0.01, 0.01, 10.0, x.data_ptr(), y.data_ptr(), None)
+    assert st == helm.HELM_EUNSUPPORTED
+    st = helm.lib.helm_solve_2d_static(4096, 1024, 0.01, 0.01, 10.0, x.data_ptr(), y.data_ptr(), None)
+    assert st == helm.HELM_EUNSUPPORTED
+    assert helm.lib.helm_solve_2d_static(2, 5, 0.1, 0.1, 1.0, x.data_ptr(), y.data_ptr(), None) == helm.HELM_EINVAL
