@@ -111,28 +111,32 @@ class ClockSampler:
 # complex64 residual, the last transform writes (or updates) complex128 u.
 # Flops: real operations of the algorithm as written (complex multiply 6,
 # complex add 2, complex reciprocal 5 counting each division as 1).
-def kernel_model(name, e, n1, accum=False, first=True):
+def kernel_model(name, e, n1, accum=False, first=True, tables=False):
     import math
 
     log2n = math.log2(n1)
     fin = 16 if first else e
+    if tables:
+        # FP64 with per-plan line tables: pass 1 reads rhs, m_j, w_j; pass 2
+        # reads rhs, m_j, 1/u_j (and step 3 writes x)
+        tri = {"tri_step1_pass1": (3 * e, 22.0), "tri_step2_pass1": (2 * e, 18.0),
+               "tri_step3_pass1": (3 * e, 24.0), "tri_step1_pass2": (3 * e, 34.0),
+               "tri_step2_pass2": (2 * e, 36.0), "tri_step3_pass2": (4 * e, 30.0)}
+    else:
+        tri = {"tri_step1_pass1": (e, 67.0), "tri_step2_pass1": (0.0, 61.0), "tri_step3_pass1": (e, 75.0),
+               "tri_step1_pass2": (e, 53.0), "tri_step2_pass2": (0.0, 47.0), "tri_step3_pass2": (2.0 * e, 55.0)}
     tab = {
         "dft_fwd": (fin + e, 5.0 * log2n),
         "dft_inv": (e + (32 if accum else 16 if e == 16 else 8), 5.0 * log2n),
-        "tri_step1_pass1": (e, 67.0),
-        "tri_step2_pass1": (0.0, 61.0),
-        "tri_step3_pass1": (e, 75.0),
-        "tri_step1_pass2": (e, 53.0),
-        "tri_step2_pass2": (0.0, 47.0),
-        "tri_step3_pass2": (2.0 * e, 55.0),
         "residual_fp64": (40.0, 40.0),
     }
+    tab.update(tri)
     return tab.get(name)
 
 
-def roofline_entry(name, launches, tot_ms, steps, N, e, n1, peaks, fp64, accum=False):
+def roofline_entry(name, launches, tot_ms, steps, N, e, n1, peaks, fp64, accum=False, tables=False):
     per_launch_ms = tot_ms / launches
-    model = kernel_model(name, e, n1, accum=accum)
+    model = kernel_model(name, e, n1, accum=accum, tables=tables)
     out = {"kernel": name, "launches_per_step": launches / steps, "ms_per_launch": per_launch_ms}
     if model is None:
         return out
@@ -140,15 +144,20 @@ def roofline_entry(name, launches, tot_ms, steps, N, e, n1, peaks, fp64, accum=F
     gbs = byts / (per_launch_ms * 1e-3) / 1e9
     tfl = flops / (per_launch_ms * 1e-3) / 1e12
     hbm = peaks.get("hbm_gbs")
-    if fp64 or name == "residual_fp64":
+    alu_frac = tfl / FP64_PEAK_TFLOPS
+    hbm_frac = gbs / hbm if hbm else None
+    # the binding resource: FP64 arithmetic for FP64 kernels unless the HBM
+    # fraction is the larger one
+    if (fp64 or name == "residual_fp64") and (hbm_frac is None or alu_frac >= hbm_frac):
         out.update({"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": tfl / FP64_PEAK_TFLOPS, "peak_source": FP64_PEAK_NOTE,
-                    "algorithmic_flops_per_launch": flops,
-                    "hbm_GBps": gbs, "hbm_frac_of_measured": gbs / hbm if hbm else None})
+                    "frac": alu_frac, "peak_source": FP64_PEAK_NOTE,
+                    "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": byts,
+                    "hbm_GBps": gbs, "hbm_frac_of_measured": hbm_frac})
     else:
         out.update({"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                    "frac": gbs / hbm if hbm else None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                    "algorithmic_bytes_per_launch": byts})
+                    "frac": hbm_frac, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                    "algorithmic_bytes_per_launch": byts, "algorithmic_flops_per_launch": flops,
+                    "fp64_frac": alu_frac if fp64 else None})
     out["traffic"] = None
     return out
 
@@ -234,7 +243,7 @@ def run_gb300(args):
             return None
 
     # --- plain complex128 path (the headline) ---
-    plan = helm.Plan(p.shape, p.h, p.omega, helm.HELM_C128)
+    plan = helm.Plan(p.shape, p.h, p.omega, helm.HELM_C128 if args.path == "c128" else helm.HELM_C64_REFINED)
     u = torch.empty_like(f)
     ms, prof, clocks = timed(plan, u, True)
     info, _ = plan.info()
@@ -284,8 +293,9 @@ def run_gb300(args):
     peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
     n1 = p.shape[1]
     name, (launches, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
-    roof = roofline_entry(name, launches, tot_ms, args.steps, N, 16, n1, peaks, fp64=True)
-    kernels_c128 = {k: roofline_entry(k, v[0], v[1], args.steps, N, 16, n1, peaks, fp64=True) for k, v in prof.items()}
+    roof = roofline_entry(name, launches, tot_ms, args.steps, N, 16, n1, peaks, fp64=True, tables=True)
+    kernels_c128 = {k: roofline_entry(k, v[0], v[1], args.steps, N, 16, n1, peaks, fp64=True, tables=True)
+                    for k, v in prof.items()}
     if variants.get("c64_refined"):
         pr = variants["c64_refined"].pop("_prof")
         variants["c64_refined"]["kernels"] = {
@@ -379,6 +389,8 @@ def main():
     ap.add_argument("--shape", default="", help="nx,ny: same spacing and wave number on a smaller grid "
                     "(profiling cases; not a benchmark line)")
     ap.add_argument("--minimal", action="store_true", help="timed solves only (no e2e, variants, CPU baseline)")
+    ap.add_argument("--path", default="c128", choices=["c128", "c64_refined"],
+                    help="path timed as the main line (profiling cases; the benchmark line is c128)")
     args = ap.parse_args()
     if args.minimal:
         args.no_e2e = args.no_variants = args.no_cpu_baseline = True

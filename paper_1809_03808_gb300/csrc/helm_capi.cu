@@ -41,6 +41,10 @@ struct helm_plan {
   void* ustartB = nullptr;  // 2D: pivot entering each chunk, B-type lines
   void* ustartA = nullptr;  // 2D: same for A-type lines
   void* rec = nullptr;      // 2D: chunk records
+  void* tabB = nullptr;     // 2D FP64: per-plan line tables, B-type lines (Steps 1, 3)
+  void* tabA = nullptr;     // 2D FP64: same, A-type lines (Step 2)
+  void* constB = nullptr;   // 2D: per-line constants, B-type lines
+  void* constA = nullptr;   // 2D: per-line constants, A-type lines
   int64_t face_len = 0;   // values per face
   int64_t nwarps = 0;
   float2* rbuf = nullptr;
@@ -278,19 +282,28 @@ int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int 
                                      nullptr, skip, st));
   if (dbg_fhat) HELM_CK(cudaMemcpyAsync(dbg_fhat, p->fhat, nx * n1 * cb, cudaMemcpyDeviceToDevice, st));
   // a2: Step 1
-  HELM_CK(launch_tri2d(prec, 1, p->fhat, nullptr, p->ustartB, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr));
+  if (p->tabB)
+    HELM_CK(launch_tri2d_tab(1, p->fhat, nullptr, p->tabB, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr));
+  else
+    HELM_CK(launch_tri2d(prec, 1, p->fhat, nullptr, p->ustartB, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr, p->constB));
   HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fv, nx, p->nwarps, inv_n1, en_n1, skip, st));
   if (dbg_v) HELM_CK(cudaMemcpyAsync(dbg_v, fv, 2 * nx * cb, cudaMemcpyDeviceToDevice, st));
   // a3: Step 2
   HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, nullptr, fc, nx, p->h[0], p->h[1], p->omega, p->omega * p->omega, ax.g,
                                         ax.ginv, skip, st));
-  HELM_CK(launch_tri2d(prec, 2, nullptr, fc, p->ustartA, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr));
+  if (p->tabA)
+    HELM_CK(launch_tri2d_tab(2, nullptr, fc, p->tabA, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr));
+  else
+    HELM_CK(launch_tri2d(prec, 2, nullptr, fc, p->ustartA, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr, p->constA));
   HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fw, nx, p->nwarps, one, one, skip, st));
   if (dbg_w) HELM_CK(cudaMemcpyAsync(dbg_w, fw, 2 * nx * cb, cudaMemcpyDeviceToDevice, st));
   // a4: Step 3
   HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, fw, fc, nx, p->h[0], p->h[1], p->omega, p->omega * p->omega, ax.g,
                                         ax.ginv, skip, st));
-  HELM_CK(launch_tri2d(prec, 3, p->fhat, fc, p->ustartB, p->rec, p->dbuf, nullptr, a, skip, st, p->prof.on ? &p->prof : nullptr));
+  if (p->tabB)
+    HELM_CK(launch_tri2d_tab(3, p->fhat, fc, p->tabB, p->rec, p->dbuf, nullptr, a, skip, st, p->prof.on ? &p->prof : nullptr));
+  else
+    HELM_CK(launch_tri2d(prec, 3, p->fhat, fc, p->ustartB, p->rec, p->dbuf, nullptr, a, skip, st, p->prof.on ? &p->prof : nullptr, p->constB));
   // a5: inverse DFT along x1 (eq. step3IFFTz3coeff)
   HELM_PK("dft_inv", launch_dft_rows(prec, p->dbuf, prec == kPrecF64, out, out_mode, nx, ax.dft, tw, +1, 1.0 / (double)n1,
                                      accum_scale, nullptr, sco, skip, st));
@@ -340,9 +353,29 @@ int alloc_buffers_2d(helm_plan* p) {
       (rc = dev_alloc(p, &p->ustartB, nrec * cb)) || (rc = dev_alloc(p, &p->ustartA, nrec * cb)) ||
       (rc = dev_alloc(p, &p->rec, nrec * chunk_record_bytes(p->prec))))
     return rc;
-  // pivots entering each chunk (rhs independent, once per plan)
+  // per-line constants and pivots entering each chunk (rhs independent)
+  if ((rc = dev_alloc(p, &p->constB, line_consts_bytes(p->prec, n1))) ||
+      (rc = dev_alloc(p, &p->constA, line_consts_bytes(p->prec, n1))))
+    return rc;
+  HELM_CK(launch_line_consts(p->prec, p->constB, a, 1, nullptr));
+  HELM_CK(launch_line_consts(p->prec, p->constA, a, 2, nullptr));
   HELM_CK(launch_pivots(p->prec, p->ustartB, a, 1, nullptr));
   HELM_CK(launch_pivots(p->prec, p->ustartA, a, 2, nullptr));
+  // FP64: the rhs-independent parts of every line's LU, once per plan.  If the
+  // device cannot hold them (6 complex128 values per unknown) the solve
+  // recomputes them on the fly instead.
+  if (p->prec == kPrecF64) {
+    const size_t tb = line_tables_bytes(nx, n1, a.nchunks);
+    if (dev_alloc(p, &p->tabB, tb) == HELM_OK && dev_alloc(p, &p->tabA, tb) == HELM_OK) {
+      HELM_CK(launch_line_tables(p->tabB, a, 1, nullptr));
+      HELM_CK(launch_line_tables(p->tabA, a, 2, nullptr));
+    } else {
+      cudaFree(p->tabB);
+      cudaFree(p->tabA);
+      p->tabB = p->tabA = nullptr;
+      p->err.clear();
+    }
+  }
   HELM_CK(cudaDeviceSynchronize());
   return HELM_OK;
 }
@@ -373,6 +406,10 @@ void destroy_plan(helm_plan* p) {
   cudaFree(p->ustartB);
   cudaFree(p->ustartA);
   cudaFree(p->rec);
+  cudaFree(p->tabB);
+  cudaFree(p->tabA);
+  cudaFree(p->constB);
+  cudaFree(p->constA);
   cudaFree(p->rbuf);
   cudaFree(p->sums);
   cudaFree(p->state);
@@ -569,6 +606,8 @@ int helm_set_auxiliary(helm_plan_t p, double rho, int phase_quarters) {
   if (p->dim == 2) {
     const Solve2DArgs a = args2d(p);
     HELM_CK(launch_pivots(p->prec, p->ustartB, a, 1, nullptr));
+    if (p->constB) HELM_CK(launch_line_consts(p->prec, p->constB, a, 1, nullptr));
+    if (p->tabB) HELM_CK(launch_line_tables(p->tabB, a, 1, nullptr));
     HELM_CK(cudaDeviceSynchronize());
   }
   return HELM_OK;

@@ -36,10 +36,21 @@ constexpr int kChunkF64 = 8;
 // ustart: pivot entering each chunk (launch_pivots, per step type: B for 1 and
 // 3, A for 2); rec: nchunks*n1 chunk records; out: x (step 3); partial: face
 // sums (steps 1, 2).
+// consts: optional per-line constants (launch_line_consts, same line type as
+// the step); nullptr makes the kernels compute them per thread.
 cudaError_t launch_tri2d(int prec, int step, const void* fhat, const void* faces, const void* ustart, void* rec,
                          void* out, void* partial, const Solve2DArgs& a, const int* skip, cudaStream_t st,
-                         Profiler* prof);
+                         Profiler* prof, const void* consts = nullptr);
+size_t line_consts_bytes(int prec, int64_t n1);
+cudaError_t launch_line_consts(int prec, void* out, const Solve2DArgs& a, int step, cudaStream_t st);
 cudaError_t launch_pivots(int prec, void* ustart, const Solve2DArgs& a, int step, cudaStream_t st);
+// FP64 path with per-plan line tables (multipliers, reciprocal pivots, chunk
+// weights): table memory per line type, building them, and the step launch.
+size_t line_tables_bytes(int64_t nx, int64_t n1, int64_t nchunks);
+cudaError_t launch_line_tables(void* tables, const Solve2DArgs& a, int step, cudaStream_t st);
+cudaError_t launch_tri2d_tab(int step, const void* fhat, const void* faces, const void* tables, void* rec,
+                             void* out, void* partial, const Solve2DArgs& a, const int* skip, cudaStream_t st,
+                             Profiler* prof);
 size_t chunk_record_bytes(int prec);
 // out[face][ix] = scale_face * sum_w partial (complex scales, face 0 then 1).
 cudaError_t launch_reduce_faces(int prec, const void* partial, void* out, int64_t nx, int64_t nwarps,

@@ -37,11 +37,26 @@ namespace {
 // are the same sequence as plain Thomas: each chunk restarts it from u_{s-1},
 // computed once per plan (k_pivots).
 
-// Per-chunk summary record (one per line and chunk).
+// Per-chunk summary records (one per line and chunk), stored as five
+// separate arrays indexed [chunk][line] so that a warp's accesses to one field
+// are contiguous.
 template <typename C>
 struct ChunkRec {
   C a, bsum, pe, cc, we;
 };
+template <typename C>
+struct RecSoA {
+  C* a;
+  C* bsum;
+  C* pe;
+  C* cc;
+  C* we;
+};
+template <typename C>
+__host__ __device__ inline RecSoA<C> rec_soa(void* base, size_t nrec) {
+  C* b = reinterpret_cast<C*>(base);
+  return RecSoA<C>{b, b + nrec, b + 2 * nrec, b + 3 * nrec, b + 4 * nrec};
+}
 
 // Right-hand side of line lc at row ix.  Step 1: fhat / mu_l.  Step 2:
 // c_1 + par_l c_n.  Step 3: (fhat + d_1 + e^{+i theta_l} e^{-t(n1-1)} d_n) / mu_l
@@ -80,12 +95,85 @@ __device__ __forceinline__ LineParams line_params(int step, const Solve2DArgs& a
   return p;
 }
 
+// Per-line constants of one line type (B: Steps 1, 3; A: Step 2) in the
+// compute precision, built once per plan: the three matrix entries, the rhs
+// scale 1/mu_l, the Step-3 face weight, the Step-1 face weight e^{-i theta_l},
+// sigma_l and the parity.  Eight arrays of n1 values.
+template <typename C>
+struct LineConst {
+  const C* a;
+  const C* ac;
+  const C* b;
+  const C* scal;
+  const C* wl;
+  const C* twl;
+  const C* sig;
+  const C* par;  // (+-1, 0)
+};
+template <typename C>
+__host__ __device__ inline LineConst<C> line_const(const void* base, int64_t n1) {
+  const C* p = reinterpret_cast<const C*>(base);
+  return LineConst<C>{p, p + n1, p + 2 * n1, p + 3 * n1, p + 4 * n1, p + 5 * n1, p + 6 * n1, p + 7 * n1};
+}
+
+// The same values the tridiagonal kernels would compute per thread.
+template <typename T, typename Cc>
+struct LineValues {
+  LineCoef<Cc> co;
+  Cc scal, wl, twl, sig;
+  T par;
+};
+
+template <typename T>
+__device__ __forceinline__ LineValues<T, typename cpx<T>::type> line_values(int step, const Solve2DArgs& a,
+                                                                            int64_t lc, const void* consts) {
+  using C = typename cpx<T>::type;
+  LineValues<T, C> v;
+  if (consts) {
+    const LineConst<C> t = line_const<C>(consts, a.n1);
+    v.co.a = t.a[lc];
+    v.co.ac = t.ac[lc];
+    v.co.b = t.b[lc];
+    v.scal = t.scal[lc];
+    v.wl = t.wl[lc];
+    v.twl = t.twl[lc];
+    v.sig = t.sig[lc];
+    v.par = t.par[lc].x;
+    return v;
+  }
+  const LineParams lp = line_params(step, a, lc);
+  v.co = line_coef<C>(lp.sre, lp.sim, a.hx, a.omega);
+  v.scal = (step == 2) ? mk<C>(1, 0) : mk<C>(a.invmu[2 * lc], a.invmu[2 * lc + 1]);
+  v.wl = step3_weight<C>(a, lc);
+  v.twl = mk<C>(a.tw[2 * lc], a.tw[2 * lc + 1]);
+  v.sig = mk<C>(a.sigA[2 * lc], a.sigA[2 * lc + 1]);
+  v.par = (T)a.parA[lc];
+  return v;
+}
+
+template <typename T>
+__global__ void k_line_consts(typename cpx<T>::type* __restrict__ out, Solve2DArgs a, int step) {
+  using C = typename cpx<T>::type;
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= a.n1) return;
+  const LineValues<T, C> v = line_values<T>(step, a, l, nullptr);
+  const int64_t n1 = a.n1;
+  out[l] = v.co.a;
+  out[n1 + l] = v.co.ac;
+  out[2 * n1 + l] = v.co.b;
+  out[3 * n1 + l] = v.scal;
+  out[4 * n1 + l] = v.wl;
+  out[5 * n1 + l] = v.twl;
+  out[6 * n1 + l] = v.sig;
+  out[7 * n1 + l] = mk<C>((double)v.par, 0);
+}
+
 template <typename T, int STEP, int CH>
 __global__ void __launch_bounds__(128) k_tri_pass1(const typename cpx<T>::type* __restrict__ fhat,
                                                    const typename cpx<T>::type* __restrict__ faces,
                                                    const typename cpx<T>::type* __restrict__ ustart,
-                                                   ChunkRec<typename cpx<T>::type>* __restrict__ rec,
-                                                   Solve2DArgs a, const int* __restrict__ skip) {
+                                                   RecSoA<typename cpx<T>::type> rec, Solve2DArgs a,
+                                                   const void* __restrict__ consts, const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
   if (skip && *skip) return;
   const int64_t n1 = a.n1, nx = a.nx;
@@ -94,11 +182,11 @@ __global__ void __launch_bounds__(128) k_tri_pass1(const typename cpx<T>::type* 
   const int64_t k = blockIdx.y;
   const int64_t s = k * CH, e = min(s + (int64_t)CH, nx) - 1;
   const int cnt = (int)(e - s + 1);
-  const LineParams lp = line_params(STEP, a, l);
-  const LineCoef<C> co = line_coef<C>(lp.sre, lp.sim, a.hx, a.omega);
-  const C scal = (STEP == 2) ? mk<C>(1, 0) : mk<C>(a.invmu[2 * l], a.invmu[2 * l + 1]);
-  const C wl = step3_weight<C>(a, l);
-  const T par = (T)a.parA[l];
+  const LineValues<T, C> lv = line_values<T>(STEP, a, l, consts);
+  const LineCoef<C> co = lv.co;
+  const C scal = lv.scal;
+  const C wl = lv.wl;
+  const T par = lv.par;
   const C* f1 = faces;
   const C* fn = faces + nx;
   const C zero = mk<C>(0, 0);
@@ -133,13 +221,12 @@ __global__ void __launch_bounds__(128) k_tri_pass1(const typename cpx<T>::type* 
     bsum = cadd(bsum, cmul(w, ylo));
     cc = cadd(cc, cmul(w, P));
   }
-  ChunkRec<C> R;
-  R.a = ylo;
-  R.bsum = bsum;
-  R.pe = (k > 0) ? P : zero;
-  R.cc = (k > 0) ? cc : zero;
-  R.we = w;
-  rec[k * n1 + l] = R;
+  const int64_t i = k * n1 + l;
+  rec.a[i] = ylo;
+  rec.bsum[i] = bsum;
+  rec.pe[i] = (k > 0) ? P : zero;
+  rec.cc[i] = (k > 0) ? cc : zero;
+  rec.we[i] = w;
 }
 
 // Two scans per line over its chunks: forward carry Y, backward carry X.
@@ -148,7 +235,7 @@ __global__ void __launch_bounds__(128) k_tri_pass1(const typename cpx<T>::type* 
 // them, and the next batch is requested while the current one is processed,
 // so the sequential chain waits on arithmetic rather than on memory.
 template <typename T, int STEP>
-__global__ void k_tri_carry(ChunkRec<typename cpx<T>::type>* __restrict__ rec, Solve2DArgs a,
+__global__ void k_tri_carry(RecSoA<typename cpx<T>::type> rec, Solve2DArgs a, const void* __restrict__ consts,
                             const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
   constexpr int CB = 8;
@@ -157,8 +244,7 @@ __global__ void k_tri_carry(ChunkRec<typename cpx<T>::type>* __restrict__ rec, S
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n1) return;
   const int64_t K = a.nchunks;
-  const LineParams lp = line_params(STEP, a, l);
-  const LineCoef<C> co = line_coef<C>(lp.sre, lp.sim, a.hx, a.omega);
+  const LineCoef<C> co = line_values<T>(STEP, a, l, consts).co;
   // forward: Y(k) = a_k + pe_k Y(k-1)
   C Y = mk<C>(0, 0);
   C ra[CB], rp[CB], na[CB], np[CB];
@@ -167,8 +253,8 @@ __global__ void k_tri_carry(ChunkRec<typename cpx<T>::type>* __restrict__ rec, S
     for (int t = 0; t < CB; ++t) {
       const int64_t k = k0 + t;
       if (k < K) {
-        A[t] = rec[k * n1 + l].a;
-        Pp[t] = rec[k * n1 + l].pe;
+        A[t] = rec.a[k * n1 + l];
+        Pp[t] = rec.pe[k * n1 + l];
       }
     }
   };
@@ -179,7 +265,7 @@ __global__ void k_tri_carry(ChunkRec<typename cpx<T>::type>* __restrict__ rec, S
     for (int t = 0; t < CB; ++t) {
       const int64_t k = k0 + t;
       if (k < K) {
-        rec[k * n1 + l].a = Y;  // Y(k-1)
+        rec.a[k * n1 + l] = Y;  // Y(k-1)
         Y = cadd(ra[t], cmul(rp[t], Y));
       }
     }
@@ -197,11 +283,11 @@ __global__ void k_tri_carry(ChunkRec<typename cpx<T>::type>* __restrict__ rec, S
     for (int t = 0; t < CB; ++t) {
       const int64_t k = k1 - t;
       if (k >= 0) {
-        const ChunkRec<C>& R = rec[k * n1 + l];
-        B[t] = R.bsum;
-        Cc[t] = R.cc;
-        W[t] = R.we;
-        Yp[t] = R.a;
+        const int64_t i = k * n1 + l;
+        B[t] = rec.bsum[i];
+        Cc[t] = rec.cc[i];
+        W[t] = rec.we[i];
+        Yp[t] = rec.a[i];
       }
     }
   };
@@ -212,7 +298,7 @@ __global__ void k_tri_carry(ChunkRec<typename cpx<T>::type>* __restrict__ rec, S
     for (int t = 0; t < CB; ++t) {
       const int64_t k = k1 - t;
       if (k >= 0) {
-        rec[k * n1 + l].bsum = X;  // X(k+1)
+        rec.bsum[k * n1 + l] = X;  // X(k+1)
         X = csub(cadd(rb[t], cmul(rc[t], ry[t])), cmul(cmul(co.b, rw[t]), X));
       }
     }
@@ -231,10 +317,10 @@ template <typename T, int STEP, int CH>
 __global__ void __launch_bounds__(128) k_tri_pass2(const typename cpx<T>::type* __restrict__ fhat,
                                                    const typename cpx<T>::type* __restrict__ faces,
                                                    const typename cpx<T>::type* __restrict__ ustart,
-                                                   const ChunkRec<typename cpx<T>::type>* __restrict__ rec,
+                                                   RecSoA<typename cpx<T>::type> rec,
                                                    typename cpx<T>::type* __restrict__ out,
                                                    typename cpx<T>::type* __restrict__ partial, Solve2DArgs a,
-                                                   const int* __restrict__ skip) {
+                                                   const void* __restrict__ consts, const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
   if (skip && *skip) return;
   const int64_t n1 = a.n1, nx = a.nx;
@@ -245,20 +331,21 @@ __global__ void __launch_bounds__(128) k_tri_pass2(const typename cpx<T>::type* 
   const int64_t k = blockIdx.y;
   const int64_t s = k * CH, e = min(s + CH, nx) - 1;
   const int cnt = (int)(e - s + 1);
-  const LineParams lp = line_params(STEP, a, lc);
-  const LineCoef<C> co = line_coef<C>(lp.sre, lp.sim, a.hx, a.omega);
-  const C scal = (STEP == 2) ? mk<C>(1, 0) : mk<C>(a.invmu[2 * lc], a.invmu[2 * lc + 1]);
-  const C twl = mk<C>(a.tw[2 * lc], a.tw[2 * lc + 1]);
-  const C wl = step3_weight<C>(a, lc);
-  const T par = (T)a.parA[lc];
-  const C sig = mk<C>(a.sigA[2 * lc], a.sigA[2 * lc + 1]);
+  const LineValues<T, C> lv = line_values<T>(STEP, a, lc, consts);
+  const LineCoef<C> co = lv.co;
+  const C scal = lv.scal;
+  const C twl = lv.twl;
+  const C wl = lv.wl;
+  const T par = lv.par;
+  const C sig = lv.sig;
   const C* f1 = faces;
   const C* fn = faces + nx;
   const C zero = mk<C>(0, 0);
   C y[CH], iu[CH];
-  const ChunkRec<C> R = rec[k * n1 + lc];
+  const C Yin = rec.a[k * n1 + lc];     // Y(k-1)
+  const C Xin = rec.bsum[k * n1 + lc];  // X(k+1)
   C inv = (k > 0) ? crecip(ustart[k * n1 + lc]) : zero;
-  C yp = R.a;  // Y(k-1)
+  C yp = Yin;
   // right-hand sides into registers first (y[] holds them until overwritten)
 #pragma unroll
   for (int t = 0; t < CH; ++t)
@@ -285,7 +372,177 @@ __global__ void __launch_bounds__(128) k_tri_pass2(const typename cpx<T>::type* 
   const int lane = threadIdx.x & 31;
   const int64_t warp = l >> 5;
   const int64_t nwarps = (n1 + 31) >> 5;
-  C xn = R.bsum;  // X(k+1)
+  C xn = Xin;
+#pragma unroll
+  for (int t = CH - 1; t >= 0; --t) {
+    if (t < cnt) {
+      const int64_t j = s + t;
+      const C x = cmul(csub(y[t], cmul(co.b, xn)), iu[t]);
+      xn = x;
+      if (STEP == 3) {
+        if (act) out[j * n1 + lc] = x;
+      } else {
+        C s1, sn;
+        if (STEP == 1) {
+          s1 = act ? x : zero;
+          sn = act ? cmul(x, twl) : zero;
+        } else {
+          const C tt = act ? cmul(x, sig) : zero;
+          s1 = tt;
+          sn = cscale(tt, par);
+        }
+        s1 = warp_sum(s1);
+        sn = warp_sum(sn);
+        if (lane == 0) {
+          partial[warp * nx + j] = s1;
+          partial[(nwarps + warp) * nx + j] = sn;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 path with per-plan tables.  Everything in the chunked Thomas that does
+// not depend on the right-hand side is computed once per plan: for every line
+// and row the multiplier m_j = b/u_{j-1}, the reciprocal pivot 1/u_j and the
+// weight w_j = (U_kk^-1)_{s,j}; for every chunk pe, cc, we.  Each solve then
+// does only the two recurrences that involve the data.
+// ---------------------------------------------------------------------------
+struct LineTables {
+  double2* m;
+  double2* iu;
+  double2* w;
+  double2* pe;
+  double2* cc;
+  double2* we;
+};
+
+inline LineTables line_tables(void* base, size_t N, size_t nrec) {
+  double2* b = reinterpret_cast<double2*>(base);
+  return LineTables{b, b + N, b + 2 * N, b + 3 * N, b + 3 * N + nrec, b + 3 * N + 2 * nrec};
+}
+
+__global__ void k_line_tables(LineTables t, Solve2DArgs a, int step) {
+  const int64_t n1 = a.n1, nx = a.nx;
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n1) return;
+  const LineParams lp = line_params(step, a, l);
+  const LineCoef<double2> co = line_coef<double2>(lp.sre, lp.sim, a.hx, a.omega);
+  const double2 zero = make_double2(0, 0);
+  const double2 mb = make_double2(-co.b.x, -co.b.y);
+  double2 iu = zero, P = zero, w = zero, cc = zero;
+  for (int64_t j = 0; j < nx; ++j) {
+    const int64_t k = j / a.ch, s = k * a.ch;
+    const double2 aj = (j == 0 || j == nx - 1) ? co.ac : co.a;
+    double2 m = zero, u;
+    if (j > 0) {
+      m = cmul(co.b, iu);
+      u = csub(aj, cmul(m, co.b));
+    } else {
+      u = aj;
+    }
+    iu = crecip(u);
+    const double2 mm = make_double2(-m.x, -m.y);
+    P = (j == s) ? mm : cmul(P, mm);
+    w = (j == s) ? iu : cmul(cmul(w, mb), iu);
+    cc = (j == s) ? cmul(w, P) : cadd(cc, cmul(w, P));
+    t.m[j * n1 + l] = m;
+    t.iu[j * n1 + l] = iu;
+    t.w[j * n1 + l] = w;
+    if (j == min(s + a.ch, nx) - 1) {
+      t.pe[k * n1 + l] = (k > 0) ? P : zero;
+      t.cc[k * n1 + l] = (k > 0) ? cc : zero;
+      t.we[k * n1 + l] = w;
+    }
+  }
+}
+
+template <int STEP, int CH>
+__global__ void __launch_bounds__(128) k_tri_pass1_tab(const double2* __restrict__ fhat,
+                                                       const double2* __restrict__ faces, LineTables tb,
+                                                       RecSoA<double2> rec, Solve2DArgs a,
+                                                       const int* __restrict__ skip) {
+  using C = double2;
+  if (skip && *skip) return;
+  const int64_t n1 = a.n1, nx = a.nx;
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n1) return;
+  const int64_t k = blockIdx.y;
+  const int64_t s = k * CH, e = min(s + (int64_t)CH, nx) - 1;
+  const int cnt = (int)(e - s + 1);
+  const C scal = (STEP == 2) ? mk<C>(1, 0) : mk<C>(a.invmu[2 * l], a.invmu[2 * l + 1]);
+  const C wl = step3_weight<C>(a, l);
+  const double par = a.parA[l];
+  const C* f1 = faces;
+  const C* fn = faces + nx;
+  C rr[CH], mj[CH], wj[CH];
+#pragma unroll
+  for (int t = 0; t < CH; ++t)
+    if (t < cnt) {
+      const int64_t i = (s + t) * n1 + l;
+      rr[t] = line_rhs<C>(STEP, s + t, l, n1, fhat, f1, fn, scal, par, wl);
+      mj[t] = tb.m[i];
+      wj[t] = tb.w[i];
+    }
+  C ylo = make_double2(0, 0), bsum = make_double2(0, 0);
+#pragma unroll
+  for (int t = 0; t < CH; ++t) {
+    if (t >= cnt) break;
+    ylo = (t == 0) ? rr[t] : csub(rr[t], cmul(mj[t], ylo));
+    bsum = cadd(bsum, cmul(wj[t], ylo));
+  }
+  rec.a[k * n1 + l] = ylo;
+  rec.bsum[k * n1 + l] = bsum;
+}
+
+template <int STEP, int CH>
+__global__ void __launch_bounds__(128) k_tri_pass2_tab(const double2* __restrict__ fhat,
+                                                       const double2* __restrict__ faces, LineTables tb,
+                                                       RecSoA<double2> rec, double2* __restrict__ out,
+                                                       double2* __restrict__ partial, Solve2DArgs a,
+                                                       const int* __restrict__ skip) {
+  using C = double2;
+  if (skip && *skip) return;
+  const int64_t n1 = a.n1, nx = a.nx;
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((l & ~(int64_t)31) >= n1) return;
+  const bool act = l < n1;
+  const int64_t lc = act ? l : 0;
+  const int64_t k = blockIdx.y;
+  const int64_t s = k * CH, e = min(s + (int64_t)CH, nx) - 1;
+  const int cnt = (int)(e - s + 1);
+  const LineParams lp = line_params(STEP, a, lc);
+  const LineCoef<C> co = line_coef<C>(lp.sre, lp.sim, a.hx, a.omega);
+  const C scal = (STEP == 2) ? mk<C>(1, 0) : mk<C>(a.invmu[2 * lc], a.invmu[2 * lc + 1]);
+  const C twl = mk<C>(a.tw[2 * lc], a.tw[2 * lc + 1]);
+  const C wl = step3_weight<C>(a, lc);
+  const double par = a.parA[lc];
+  const C sig = mk<C>(a.sigA[2 * lc], a.sigA[2 * lc + 1]);
+  const C* f1 = faces;
+  const C* fn = faces + nx;
+  const C zero = mk<C>(0, 0);
+  C y[CH], mj[CH], iu[CH];
+#pragma unroll
+  for (int t = 0; t < CH; ++t)
+    if (t < cnt) {
+      const int64_t i = (s + t) * n1 + lc;
+      y[t] = line_rhs<C>(STEP, s + t, lc, n1, fhat, f1, fn, scal, par, wl);
+      mj[t] = tb.m[i];
+      iu[t] = tb.iu[i];
+    }
+  C yp = rec.a[k * n1 + lc];  // Y(k-1)
+#pragma unroll
+  for (int t = 0; t < CH; ++t) {
+    if (t < cnt) {
+      yp = csub(y[t], cmul(mj[t], yp));
+      y[t] = yp;
+    }
+  }
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = l >> 5;
+  const int64_t nwarps = (n1 + 31) >> 5;
+  C xn = rec.bsum[k * n1 + lc];  // X(k+1)
 #pragma unroll
   for (int t = CH - 1; t >= 0; --t) {
     if (t < cnt) {
@@ -399,29 +656,30 @@ __global__ void k_apply_cbb(const typename cpx<T>::type* __restrict__ in,
 
 cudaError_t launch_tri2d(int prec, int step, const void* fhat, const void* faces, const void* ustart, void* rec,
                          void* out, void* partial, const Solve2DArgs& a, const int* skip, cudaStream_t st,
-                         Profiler* prof) {
+                         Profiler* prof, const void* consts) {
   static const char* n1s[3] = {"tri_step1_pass1", "tri_step2_pass1", "tri_step3_pass1"};
   static const char* ncs[3] = {"tri_step1_carry", "tri_step2_carry", "tri_step3_carry"};
   static const char* n2s[3] = {"tri_step1_pass2", "tri_step2_pass2", "tri_step3_pass2"};
   const int bs = 128;
   const dim3 grid((unsigned)((a.n1 + bs - 1) / bs), (unsigned)a.nchunks);
   const unsigned gl = (unsigned)((a.n1 + bs - 1) / bs);
+  const size_t nrec = (size_t)a.nchunks * a.n1;
 #define HELM_TRI(T, S, CH)                                                                                        \
   do {                                                                                                         \
     using C = cpx<T>::type;                                                                                    \
     {                                                                                                          \
       ProfScope ps(prof, n1s[S - 1], st);                                                                      \
       k_tri_pass1<T, S, CH><<<grid, bs, 0, st>>>((const C*)fhat, (const C*)faces, (const C*)ustart,            \
-                                            (ChunkRec<C>*)rec, a, skip);                                      \
+                                            rec_soa<C>(rec, nrec), a, consts, skip);                          \
     }                                                                                                          \
     {                                                                                                          \
       ProfScope ps(prof, ncs[S - 1], st);                                                                      \
-      k_tri_carry<T, S><<<gl, bs, 0, st>>>((ChunkRec<C>*)rec, a, skip);                                        \
+      k_tri_carry<T, S><<<gl, bs, 0, st>>>(rec_soa<C>(rec, nrec), a, consts, skip);                            \
     }                                                                                                          \
     {                                                                                                          \
       ProfScope ps(prof, n2s[S - 1], st);                                                                      \
       k_tri_pass2<T, S, CH><<<grid, bs, 0, st>>>((const C*)fhat, (const C*)faces, (const C*)ustart,            \
-                                                (const ChunkRec<C>*)rec, (C*)out, (C*)partial, a, skip);      \
+                                                rec_soa<C>(rec, nrec), (C*)out, (C*)partial, a, consts, skip);\
     }                                                                                                          \
   } while (0)
   if (prec == kPrecF64) {
@@ -436,6 +694,70 @@ cudaError_t launch_tri2d(int prec, int step, const void* fhat, const void* faces
     else HELM_TRI(float, 3, kChunkF32);
   }
 #undef HELM_TRI
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tri2d_tab(int step, const void* fhat, const void* faces, const void* tables, void* rec,
+                             void* out, void* partial, const Solve2DArgs& a, const int* skip, cudaStream_t st,
+                             Profiler* prof) {
+  static const char* n1s[3] = {"tri_step1_pass1", "tri_step2_pass1", "tri_step3_pass1"};
+  static const char* ncs[3] = {"tri_step1_carry", "tri_step2_carry", "tri_step3_carry"};
+  static const char* n2s[3] = {"tri_step1_pass2", "tri_step2_pass2", "tri_step3_pass2"};
+  if (a.ch != kChunkF64) return cudaErrorInvalidValue;
+  const int bs = 128;
+  const dim3 grid((unsigned)((a.n1 + bs - 1) / bs), (unsigned)a.nchunks);
+  const unsigned gl = (unsigned)((a.n1 + bs - 1) / bs);
+  const size_t nrec = (size_t)a.nchunks * a.n1;
+  const LineTables tb = line_tables(const_cast<void*>(tables), (size_t)a.nx * a.n1, nrec);
+  RecSoA<double2> r = rec_soa<double2>(rec, nrec);
+  r.pe = tb.pe;  // rhs-independent chunk constants live in the tables
+  r.cc = tb.cc;
+  r.we = tb.we;
+#define HELM_TRI_TAB(S)                                                                                     \
+  do {                                                                                                   \
+    {                                                                                                    \
+      ProfScope ps(prof, n1s[S - 1], st);                                                                \
+      k_tri_pass1_tab<S, kChunkF64><<<grid, bs, 0, st>>>((const double2*)fhat, (const double2*)faces, tb, r, \
+                                                         a, skip);                                     \
+    }                                                                                                    \
+    {                                                                                                    \
+      ProfScope ps(prof, ncs[S - 1], st);                                                                \
+      k_tri_carry<double, S><<<gl, bs, 0, st>>>(r, a, nullptr, skip);                                    \
+    }                                                                                                    \
+    {                                                                                                    \
+      ProfScope ps(prof, n2s[S - 1], st);                                                                \
+      k_tri_pass2_tab<S, kChunkF64><<<grid, bs, 0, st>>>((const double2*)fhat, (const double2*)faces, tb, r, \
+                                                         (double2*)out, (double2*)partial, a, skip);   \
+    }                                                                                                    \
+  } while (0)
+  if (step == 1) HELM_TRI_TAB(1);
+  else if (step == 2) HELM_TRI_TAB(2);
+  else HELM_TRI_TAB(3);
+#undef HELM_TRI_TAB
+  return cudaGetLastError();
+}
+
+size_t line_tables_bytes(int64_t nx, int64_t n1, int64_t nchunks) {
+  return (size_t)(3 * nx * n1 + 3 * nchunks * n1) * sizeof(double2);
+}
+
+cudaError_t launch_line_tables(void* tables, const Solve2DArgs& a, int step, cudaStream_t st) {
+  const int bs = 128;
+  const unsigned grid = (unsigned)((a.n1 + bs - 1) / bs);
+  const LineTables tb = line_tables(tables, (size_t)a.nx * a.n1, (size_t)a.nchunks * a.n1);
+  k_line_tables<<<grid, bs, 0, st>>>(tb, a, step);
+  return cudaGetLastError();
+}
+
+size_t line_consts_bytes(int prec, int64_t n1) { return (size_t)8 * n1 * (prec == kPrecF64 ? sizeof(double2) : sizeof(float2)); }
+
+cudaError_t launch_line_consts(int prec, void* out, const Solve2DArgs& a, int step, cudaStream_t st) {
+  const int bs = 128;
+  const unsigned grid = (unsigned)((a.n1 + bs - 1) / bs);
+  if (prec == kPrecF64)
+    k_line_consts<double><<<grid, bs, 0, st>>>((double2*)out, a, step);
+  else
+    k_line_consts<float><<<grid, bs, 0, st>>>((float2*)out, a, step);
   return cudaGetLastError();
 }
 
