@@ -182,7 +182,7 @@ def run_gb300(args):
         __graft_entry__.build()
         import paper_1809_03808_gb300 as helm
 
-    p = workloads.config_2d_large()
+    p = workloads.config_3d() if args.workload == "3d" else workloads.config_2d_large()
     if args.shape:
         p = workloads.scaled(p, tuple(int(x) for x in args.shape.split(",")))
     N = p.N
@@ -236,7 +236,7 @@ def run_gb300(args):
             sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
             from make_golden import load
 
-            d, idx, vals = load("2d_large")
+            d, idx, vals = load(args.workload)
             got = u.reshape(-1)[torch.from_numpy(idx).to(dev)].cpu().numpy()
             return float(np.linalg.norm(got - vals) / np.linalg.norm(vals))
         except FileNotFoundError:
@@ -389,6 +389,8 @@ def main():
     ap.add_argument("--shape", default="", help="nx,ny: same spacing and wave number on a smaller grid "
                     "(profiling cases; not a benchmark line)")
     ap.add_argument("--minimal", action="store_true", help="timed solves only (no e2e, variants, CPU baseline)")
+    ap.add_argument("--workload", default="2d_large", choices=["2d_large", "3d"],
+                    help="2d_large: the benchmark workload; 3d: the 512^3 workload (measurement, not the bench line)")
     ap.add_argument("--path", default="c128", choices=["c128", "c64_refined"],
                     help="path timed as the main line (profiling cases; the benchmark line is c128)")
     args = ap.parse_args()

@@ -278,6 +278,7 @@ int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int 
   const void* sco = f64 ? (const void*)ax.sc_out : (const void*)ax.sc_out32;
   const double one[2] = {1.0, 0.0}, inv_n1[2] = {1.0 / (double)n1, 0.0};
   const double en_n1[2] = {ax.en[0] / (double)n1, ax.en[1] / (double)n1};
+  const int64_t nparts = (n1 + 127) / 128;  // face partials: one per block of 128 lines
   HELM_PK("dft_fwd", launch_dft_rows(prec, in, in_is_double, p->fhat, fhat_mode, nx, ax.dft, tw, -1, 1.0, 0.0, sci,
                                      nullptr, skip, st));
   if (dbg_fhat) HELM_CK(cudaMemcpyAsync(dbg_fhat, p->fhat, nx * n1 * cb, cudaMemcpyDeviceToDevice, st));
@@ -286,7 +287,7 @@ int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int 
     HELM_CK(launch_tri2d_tab(1, p->fhat, nullptr, p->tabB, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr));
   else
     HELM_CK(launch_tri2d(prec, 1, p->fhat, nullptr, p->ustartB, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr, p->constB));
-  HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fv, nx, p->nwarps, inv_n1, en_n1, skip, st));
+  HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fv, nx, nparts, inv_n1, en_n1, skip, st));
   if (dbg_v) HELM_CK(cudaMemcpyAsync(dbg_v, fv, 2 * nx * cb, cudaMemcpyDeviceToDevice, st));
   // a3: Step 2
   HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, nullptr, fc, nx, p->h[0], p->h[1], p->omega, p->omega * p->omega, ax.g,
@@ -295,7 +296,7 @@ int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int 
     HELM_CK(launch_tri2d_tab(2, nullptr, fc, p->tabA, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr));
   else
     HELM_CK(launch_tri2d(prec, 2, nullptr, fc, p->ustartA, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr, p->constA));
-  HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fw, nx, p->nwarps, one, one, skip, st));
+  HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fw, nx, nparts, one, one, skip, st));
   if (dbg_w) HELM_CK(cudaMemcpyAsync(dbg_w, fw, 2 * nx * cb, cudaMemcpyDeviceToDevice, st));
   // a4: Step 3
   HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, fw, fc, nx, p->h[0], p->h[1], p->omega, p->omega * p->omega, ax.g,

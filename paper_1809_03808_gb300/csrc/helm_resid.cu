@@ -155,6 +155,9 @@ __global__ void __launch_bounds__(256) k_residual2d(ResidArgs a, const double2* 
   const int64_t nx = a.ax[0].n, ny = a.ax[1].n;
   const int64_t iy = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t x0 = (int64_t)blockIdx.y * RX2;
+  // |r|^2 and |f|^2 only decide convergence: per-thread sums in FP32 (from the
+  // rounded values), FP64 across threads and blocks
+  float r2f = 0.f, f2f = 0.f;
   double r2 = 0.0, f2 = 0.0;
   if (iy < ny) {
     const bool ym = iy > 0, yp = iy < ny - 1;
@@ -202,10 +205,11 @@ __global__ void __launch_bounds__(256) k_residual2d(ResidArgs a, const double2* 
         }
       }
       const double2 fv = __ldg(&f[ix * ny + iy]);
-      const double rr = fv.x - ar, ri = fv.y - ai;
-      r[ix * ny + iy] = make_float2((float)rr, (float)ri);
-      r2 = fma(rr, rr, fma(ri, ri, r2));
-      f2 = fma(fv.x, fv.x, fma(fv.y, fv.y, f2));
+      const float2 rf = make_float2((float)(fv.x - ar), (float)(fv.y - ai));
+      r[ix * ny + iy] = rf;
+      const float2 ff = make_float2((float)fv.x, (float)fv.y);
+      r2f = fmaf(rf.x, rf.x, fmaf(rf.y, rf.y, r2f));
+      f2f = fmaf(ff.x, ff.x, fmaf(ff.y, ff.y, f2f));
 #pragma unroll
       for (int dy = 0; dy < 3; ++dy) {
         w[0][dy] = w[1][dy];
@@ -213,6 +217,8 @@ __global__ void __launch_bounds__(256) k_residual2d(ResidArgs a, const double2* 
       }
     }
   }
+  r2 = r2f;
+  f2 = f2f;
   for (int off = 16; off > 0; off >>= 1) {
     r2 += __shfl_down_sync(0xffffffffu, r2, off);
     f2 += __shfl_down_sync(0xffffffffu, f2, off);

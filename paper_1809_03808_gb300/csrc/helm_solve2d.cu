@@ -226,89 +226,109 @@ __global__ void __launch_bounds__(128) k_tri_pass1(const typename cpx<T>::type* 
   rec.bsum[i] = bsum;
   rec.pe[i] = (k > 0) ? P : zero;
   rec.cc[i] = (k > 0) ? cc : zero;
-  rec.we[i] = w;
+  rec.we[i] = cmul(mb, w);  // q = -b we
 }
 
 // Two scans per line over its chunks: forward carry Y, backward carry X.
-// Overwrites rec[k].a with Y(k-1) and rec[k].bsum with X(k+1).  The records of
-// a batch of CB chunks are loaded before the dependent recurrence runs over
-// them, and the next batch is requested while the current one is processed,
-// so the sequential chain waits on arithmetic rather than on memory.
-template <typename T, int STEP>
-__global__ void k_tri_carry(RecSoA<typename cpx<T>::type> rec, Solve2DArgs a, const void* __restrict__ consts,
-                            const int* __restrict__ skip) {
+// Overwrites rec.a[k] with Y(k-1) and rec.bsum[k] with X(k+1).
+//
+// Each chunk's carry step is an affine map: Y(k) = a_k + pe_k Y(k-1) forward,
+// X(k) = c_k + q_k X(k+1) backward with c_k = bsum_k + cc_k Y(k-1) and
+// q_k = -b we_k (stored in rec.we).  A block takes kCarryLines lines (one per
+// x thread, so every load of a field is a contiguous run of lines) and splits
+// their chunks into kCarrySeg contiguous segments (one per y thread).  Each
+// thread composes the maps of its segment, the segment maps are folded in
+// shared memory to give each segment its incoming carry, and each thread then
+// runs its segment's recurrence from that carry.  Same recurrences as the
+// sequential scan, regrouped once; FP64 arithmetic for both precisions.
+constexpr int kCarryLines = 16;
+constexpr int kCarrySeg = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(kCarryLines* kCarrySeg)
+    k_tri_carry(RecSoA<typename cpx<T>::type> rec, int64_t n1, int64_t K, const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
-  constexpr int CB = 8;
-  if (skip && *skip) return;
-  const int64_t n1 = a.n1;
-  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= n1) return;
-  const int64_t K = a.nchunks;
-  const LineCoef<C> co = line_values<T>(STEP, a, l, consts).co;
-  // forward: Y(k) = a_k + pe_k Y(k-1)
-  C Y = mk<C>(0, 0);
-  C ra[CB], rp[CB], na[CB], np[CB];
-  auto loadf = [&](int64_t k0, C* A, C* Pp) {
-#pragma unroll
-    for (int t = 0; t < CB; ++t) {
-      const int64_t k = k0 + t;
-      if (k < K) {
-        A[t] = rec.a[k * n1 + l];
-        Pp[t] = rec.pe[k * n1 + l];
-      }
+  if (skip && *skip) return;  // uniform over the grid
+  __shared__ double2 shC[kCarrySeg][kCarryLines], shP[kCarrySeg][kCarryLines];
+  const int lx = threadIdx.x, sg = threadIdx.y;
+  const int64_t l = (int64_t)blockIdx.x * kCarryLines + lx;
+  const bool act = l < n1;
+  const int64_t S = (K + kCarrySeg - 1) / kCarrySeg;
+  const int64_t k0 = min(K, sg * S), k1 = min(K, k0 + S);
+  const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
+  // forward: compose the segment's maps
+  double2 A = zero, P = one;
+  if (act)
+    for (int64_t k = k0; k < k1; ++k) {
+      const int64_t i = k * n1 + l;
+      const double2 pk = cvt<double2>(rec.pe[i]);
+      A = cadd(cvt<double2>(rec.a[i]), cmul(pk, A));
+      P = cmul(pk, P);
     }
-  };
-  loadf(0, ra, rp);
-  for (int64_t k0 = 0; k0 < K; k0 += CB) {
-    if (k0 + CB < K) loadf(k0 + CB, na, np);
-#pragma unroll
-    for (int t = 0; t < CB; ++t) {
-      const int64_t k = k0 + t;
-      if (k < K) {
-        rec.a[k * n1 + l] = Y;  // Y(k-1)
-        Y = cadd(ra[t], cmul(rp[t], Y));
-      }
+  shC[sg][lx] = A;
+  shP[sg][lx] = P;
+  __syncthreads();
+  double2 Y = zero;
+  for (int g = 0; g < sg; ++g) Y = cadd(shC[g][lx], cmul(shP[g][lx], Y));
+  // forward recurrence; c_k replaces bsum_k
+  if (act)
+    for (int64_t k = k0; k < k1; ++k) {
+      const int64_t i = k * n1 + l;
+      const double2 ak = cvt<double2>(rec.a[i]), pk = cvt<double2>(rec.pe[i]);
+      const double2 bk = cvt<double2>(rec.bsum[i]), ck = cvt<double2>(rec.cc[i]);
+      rec.a[i] = cvt<C>(Y);  // Y(k-1)
+      rec.bsum[i] = cvt<C>(cadd(bk, cmul(ck, Y)));
+      Y = cadd(ak, cmul(pk, Y));
     }
-#pragma unroll
-    for (int t = 0; t < CB; ++t) {
-      ra[t] = na[t];
-      rp[t] = np[t];
+  __syncthreads();
+  // backward: compose the segment's maps, last chunk first
+  double2 Cs = zero, Q = one;
+  if (act)
+    for (int64_t k = k1 - 1; k >= k0; --k) {
+      const int64_t i = k * n1 + l;
+      const double2 qk = cvt<double2>(rec.we[i]);
+      Cs = cadd(cvt<double2>(rec.bsum[i]), cmul(qk, Cs));
+      Q = cmul(qk, Q);
     }
+  shC[sg][lx] = Cs;
+  shP[sg][lx] = Q;
+  __syncthreads();
+  double2 X = zero;
+  for (int g = kCarrySeg - 1; g > sg; --g) X = cadd(shC[g][lx], cmul(shP[g][lx], X));
+  if (act)
+    for (int64_t k = k1 - 1; k >= k0; --k) {
+      const int64_t i = k * n1 + l;
+      const double2 ck = cvt<double2>(rec.bsum[i]), qk = cvt<double2>(rec.we[i]);
+      rec.bsum[i] = cvt<C>(X);  // X(k+1)
+      X = cadd(ck, cmul(qk, X));
+    }
+}
+
+// Sum the face contributions of a block's 128 lines for each of its `cnt`
+// rows (red[face][row][thread]) and write one partial per block and row:
+// partial[(face * nparts + blk) * nx + row0 + t].  Fixed summation order.
+template <typename C, int CH>
+__device__ __forceinline__ void block_face_sums(C* red, int cnt, C* __restrict__ partial, int64_t blk,
+                                                int64_t nparts, int64_t nx, int64_t row0) {
+  __shared__ C seg[2 * CH * 8];
+  __syncthreads();
+  // stage 1: thread -> (sum index q = face * CH + t, segment g of 16 lines)
+  for (int w = threadIdx.x; w < 2 * CH * 8; w += blockDim.x) {
+    const int q = w >> 3, g = w & 7;
+    const C* src = red + q * 128 + g * 16;
+    C acc = src[0];
+#pragma unroll
+    for (int i = 1; i < 16; ++i) acc = cadd(acc, src[i]);
+    seg[w] = acc;
   }
-  // backward: X(k) = bsum_k + cc_k Y(k-1) - b we_k X(k+1)
-  C X = mk<C>(0, 0);
-  C rb[CB], rc[CB], rw[CB], ry[CB], nb[CB], nc[CB], nw[CB], ny[CB];
-  auto loadb = [&](int64_t k1, C* B, C* Cc, C* W, C* Yp) {  // chunks k1, k1-1, ...
+  __syncthreads();
+  for (int q = threadIdx.x; q < 2 * CH; q += blockDim.x) {
+    const int face = q / CH, t = q - face * CH;
+    if (t >= cnt) continue;
+    C acc = seg[q * 8];
 #pragma unroll
-    for (int t = 0; t < CB; ++t) {
-      const int64_t k = k1 - t;
-      if (k >= 0) {
-        const int64_t i = k * n1 + l;
-        B[t] = rec.bsum[i];
-        Cc[t] = rec.cc[i];
-        W[t] = rec.we[i];
-        Yp[t] = rec.a[i];
-      }
-    }
-  };
-  loadb(K - 1, rb, rc, rw, ry);
-  for (int64_t k1 = K - 1; k1 >= 0; k1 -= CB) {
-    if (k1 - CB >= 0) loadb(k1 - CB, nb, nc, nw, ny);
-#pragma unroll
-    for (int t = 0; t < CB; ++t) {
-      const int64_t k = k1 - t;
-      if (k >= 0) {
-        rec.bsum[k * n1 + l] = X;  // X(k+1)
-        X = csub(cadd(rb[t], cmul(rc[t], ry[t])), cmul(cmul(co.b, rw[t]), X));
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < CB; ++t) {
-      rb[t] = nb[t];
-      rc[t] = nc[t];
-      rw[t] = nw[t];
-      ry[t] = ny[t];
-    }
+    for (int g = 1; g < 8; ++g) acc = cadd(acc, seg[q * 8 + g]);
+    partial[(face * nparts + blk) * nx + row0 + t] = acc;
   }
 }
 
@@ -325,7 +345,7 @@ __global__ void __launch_bounds__(128) k_tri_pass2(const typename cpx<T>::type* 
   if (skip && *skip) return;
   const int64_t n1 = a.n1, nx = a.nx;
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if ((l & ~(int64_t)31) >= n1) return;  // whole warp beyond the last line
+  if (STEP == 3 && (l & ~(int64_t)31) >= n1) return;  // no block sync in Step 3
   const bool act = l < n1;
   const int64_t lc = act ? l : 0;
   const int64_t k = blockIdx.y;
@@ -369,9 +389,9 @@ __global__ void __launch_bounds__(128) k_tri_pass2(const typename cpx<T>::type* 
       y[t] = yp;
     }
   }
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = l >> 5;
-  const int64_t nwarps = (n1 + 31) >> 5;
+  // face contributions of the block's 128 lines, reduced per row in shared memory
+  __shared__ C red[2 * CH * 128];
+  const int64_t nparts = (n1 + 127) / 128;
   C xn = Xin;
 #pragma unroll
   for (int t = CH - 1; t >= 0; --t) {
@@ -391,15 +411,12 @@ __global__ void __launch_bounds__(128) k_tri_pass2(const typename cpx<T>::type* 
           s1 = tt;
           sn = cscale(tt, par);
         }
-        s1 = warp_sum(s1);
-        sn = warp_sum(sn);
-        if (lane == 0) {
-          partial[warp * nx + j] = s1;
-          partial[(nwarps + warp) * nx + j] = sn;
-        }
+        red[(0 * CH + t) * 128 + threadIdx.x] = s1;
+        red[(1 * CH + t) * 128 + threadIdx.x] = sn;
       }
     }
   }
+  if (STEP != 3) block_face_sums<C, CH>(red, cnt, partial, (int64_t)blockIdx.x, nparts, nx, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -453,7 +470,7 @@ __global__ void k_line_tables(LineTables t, Solve2DArgs a, int step) {
     if (j == min(s + a.ch, nx) - 1) {
       t.pe[k * n1 + l] = (k > 0) ? P : zero;
       t.cc[k * n1 + l] = (k > 0) ? cc : zero;
-      t.we[k * n1 + l] = w;
+      t.we[k * n1 + l] = cmul(mb, w);  // q = -b we
     }
   }
 }
@@ -506,7 +523,7 @@ __global__ void __launch_bounds__(128) k_tri_pass2_tab(const double2* __restrict
   if (skip && *skip) return;
   const int64_t n1 = a.n1, nx = a.nx;
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if ((l & ~(int64_t)31) >= n1) return;
+  if (STEP == 3 && (l & ~(int64_t)31) >= n1) return;  // no block sync in Step 3
   const bool act = l < n1;
   const int64_t lc = act ? l : 0;
   const int64_t k = blockIdx.y;
@@ -539,9 +556,9 @@ __global__ void __launch_bounds__(128) k_tri_pass2_tab(const double2* __restrict
       y[t] = yp;
     }
   }
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = l >> 5;
-  const int64_t nwarps = (n1 + 31) >> 5;
+  // face contributions of the block's 128 lines, reduced per row in shared memory
+  __shared__ C red[2 * CH * 128];
+  const int64_t nparts = (n1 + 127) / 128;
   C xn = rec.bsum[k * n1 + lc];  // X(k+1)
 #pragma unroll
   for (int t = CH - 1; t >= 0; --t) {
@@ -561,15 +578,12 @@ __global__ void __launch_bounds__(128) k_tri_pass2_tab(const double2* __restrict
           s1 = tt;
           sn = cscale(tt, par);
         }
-        s1 = warp_sum(s1);
-        sn = warp_sum(sn);
-        if (lane == 0) {
-          partial[warp * nx + j] = s1;
-          partial[(nwarps + warp) * nx + j] = sn;
-        }
+        red[(0 * CH + t) * 128 + threadIdx.x] = s1;
+        red[(1 * CH + t) * 128 + threadIdx.x] = sn;
       }
     }
   }
+  if (STEP != 3) block_face_sums<C, CH>(red, cnt, partial, (int64_t)blockIdx.x, nparts, nx, s);
 }
 
 // Pivot entering each chunk, u_{kCH-1}, for every line: FP64 sequential
@@ -662,7 +676,8 @@ cudaError_t launch_tri2d(int prec, int step, const void* fhat, const void* faces
   static const char* n2s[3] = {"tri_step1_pass2", "tri_step2_pass2", "tri_step3_pass2"};
   const int bs = 128;
   const dim3 grid((unsigned)((a.n1 + bs - 1) / bs), (unsigned)a.nchunks);
-  const unsigned gl = (unsigned)((a.n1 + bs - 1) / bs);
+  const unsigned gcar = (unsigned)((a.n1 + kCarryLines - 1) / kCarryLines);
+  const dim3 bcar(kCarryLines, kCarrySeg);
   const size_t nrec = (size_t)a.nchunks * a.n1;
 #define HELM_TRI(T, S, CH)                                                                                        \
   do {                                                                                                         \
@@ -674,7 +689,7 @@ cudaError_t launch_tri2d(int prec, int step, const void* fhat, const void* faces
     }                                                                                                          \
     {                                                                                                          \
       ProfScope ps(prof, ncs[S - 1], st);                                                                      \
-      k_tri_carry<T, S><<<gl, bs, 0, st>>>(rec_soa<C>(rec, nrec), a, consts, skip);                            \
+      k_tri_carry<T><<<gcar, bcar, 0, st>>>(rec_soa<C>(rec, nrec), a.n1, a.nchunks, skip);                         \
     }                                                                                                          \
     {                                                                                                          \
       ProfScope ps(prof, n2s[S - 1], st);                                                                      \
@@ -706,7 +721,8 @@ cudaError_t launch_tri2d_tab(int step, const void* fhat, const void* faces, cons
   if (a.ch != kChunkF64) return cudaErrorInvalidValue;
   const int bs = 128;
   const dim3 grid((unsigned)((a.n1 + bs - 1) / bs), (unsigned)a.nchunks);
-  const unsigned gl = (unsigned)((a.n1 + bs - 1) / bs);
+  const unsigned gcar = (unsigned)((a.n1 + kCarryLines - 1) / kCarryLines);
+  const dim3 bcar(kCarryLines, kCarrySeg);
   const size_t nrec = (size_t)a.nchunks * a.n1;
   const LineTables tb = line_tables(const_cast<void*>(tables), (size_t)a.nx * a.n1, nrec);
   RecSoA<double2> r = rec_soa<double2>(rec, nrec);
@@ -722,7 +738,7 @@ cudaError_t launch_tri2d_tab(int step, const void* fhat, const void* faces, cons
     }                                                                                                    \
     {                                                                                                    \
       ProfScope ps(prof, ncs[S - 1], st);                                                                \
-      k_tri_carry<double, S><<<gl, bs, 0, st>>>(r, a, nullptr, skip);                                    \
+      k_tri_carry<double><<<gcar, bcar, 0, st>>>(r, a.n1, a.nchunks, skip);                                 \
     }                                                                                                    \
     {                                                                                                    \
       ProfScope ps(prof, n2s[S - 1], st);                                                                \
