@@ -42,6 +42,20 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP64_PEAK_NOTE = "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FMA rate measured by probe)"
 
+# Solve paths: (helm dtype, refinement residual kind or None).  dtype codes of
+# include/helm.h: HELM_C128 = 0, HELM_C64_REFINED = 1; residual kinds
+# HELM_RESID_FP64 = 0, HELM_RESID_FF = 1.
+PATHS = {"c128": (0, None), "c64_refined": (1, 0), "c64_ff": (1, 1)}
+PATHS_NAMES = tuple(PATHS)
+PATH_DTYPE = {"c128": "f64", "c64_refined": "f32 solves + f64 residual",
+              "c64_ff": "f32 solves + float-float residual"}
+PATH_PRECISION = {"c128": "complex128 plain",
+                  "c64_refined": "complex64 solves, FP64 residual, refined to ||r||/||f|| <= 1e-11",
+                  "c64_ff": "complex64 solves, float-float residual, refined to ||r||/||f|| <= 1e-11"}
+# Refinement stop: with the error/residual ratio measured on the 2D and 3D
+# workloads (<= 3.1), ||r||/||f|| <= 1e-11 keeps the error below 1e-10.
+REFINE_TOL = 1e-11
+
 
 def sample_shape():
     """Bounded CPU sample: 2048 x 1024 nodes with the workload's spacing and
@@ -111,7 +125,7 @@ class ClockSampler:
 # complex64 residual, the last transform writes (or updates) complex128 u.
 # Flops: real operations of the algorithm as written (complex multiply 6,
 # complex add 2, complex reciprocal 5 counting each division as 1).
-def kernel_model(name, e, n1, accum=False, first=True, tables=False):
+def kernel_model(name, e, n1, accum=False, first=True, tables=False, ff=False):
     import math
 
     log2n = math.log2(n1)
@@ -128,15 +142,20 @@ def kernel_model(name, e, n1, accum=False, first=True, tables=False):
     tab = {
         "dft_fwd": (fin + e, 5.0 * log2n),
         "dft_inv": (e + (32 if accum else 16 if e == 16 else 8), 5.0 * log2n),
+        # f, u complex128 in, r complex64 out; 9-point complex stencil
         "residual_fp64": (40.0, 40.0),
+        # f, u float-float (16 B each) in, r complex64 out
+        "residual_ff": (40.0, 40.0),
+        "split_ff": (32.0, 4.0),
+        "join_ff": (32.0, 2.0),
     }
     tab.update(tri)
     return tab.get(name)
 
 
-def roofline_entry(name, launches, tot_ms, steps, N, e, n1, peaks, fp64, accum=False, tables=False):
+def roofline_entry(name, launches, tot_ms, steps, N, e, n1, peaks, fp64, accum=False, tables=False, ff=False):
     per_launch_ms = tot_ms / launches
-    model = kernel_model(name, e, n1, accum=accum, tables=tables)
+    model = kernel_model(name, e, n1, accum=accum, tables=tables, ff=ff)
     out = {"kernel": name, "launches_per_step": launches / steps, "ms_per_launch": per_launch_ms}
     if model is None:
         return out
@@ -242,14 +261,24 @@ def run_gb300(args):
         except FileNotFoundError:
             return None
 
-    # --- plain complex128 path (the headline) ---
-    plan = helm.Plan(p.shape, p.h, p.omega, helm.HELM_C128 if args.path == "c128" else helm.HELM_C64_REFINED)
+    def make_plan(path):
+        code, kind = PATHS[path]
+        plan = helm.Plan(p.shape, p.h, p.omega, code)
+        if kind is not None:
+            helm.helm_set_residual(plan.handle, kind)
+            helm.helm_set_refinement(plan.handle, REFINE_TOL, 15)
+        return plan
+
+    # --- the timed path (the headline) ---
+    plan = make_plan(args.path)
     u = torch.empty_like(f)
     ms, prof, clocks = timed(plan, u, True)
     info, _ = plan.info()
     err_c128 = sampled_error(u)
     ms_step = ms / args.steps
     value = world * N / (ms_step * 1e-3)
+    if args.path != "c128" and (err_c128 is not None and err_c128 > 1e-10):
+        raise RuntimeError(f"{args.path}: sampled error {err_c128:.3e} above the 1e-10 bar")
 
     # e2e through the host-buffer entry point (H2D of f, solve, D2H of u)
     e2e = None
@@ -271,21 +300,24 @@ def run_gb300(args):
     plan.close()
     del u
 
-    # --- refined complex64 path ---
+    # --- the other paths ---
     variants = {}
-    if not args.no_variants:
-        plan = helm.Plan(p.shape, p.h, p.omega, helm.HELM_C64_REFINED)
+    for vpath in ([] if args.no_variants else [q for q in PATHS if q != args.path]):
+        plan = make_plan(vpath)
         u = torch.empty_like(f)
         ms_r, prof_r, _ = timed(plan, u, True)
         info_r, st_r = plan.info()
-        variants["c64_refined"] = {
+        variants[vpath] = {
             "value": world * N / (ms_r / args.steps * 1e-3), "unit": UNIT, "ms_per_step": ms_r / args.steps,
-            "dtype": "f32 solves + f64 residual", "refinement_sweeps": int(info_r.iterations),
-            "final_rel_residual": float(info_r.residual[info_r.iterations]),
-            "converged": bool(info_r.converged), "rel_err_sampled": sampled_error(u),
+            "dtype": PATH_DTYPE[vpath], "rel_err_sampled": sampled_error(u),
             "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof_r.items()},
             "_prof": prof_r,
         }
+        if PATHS[vpath][1] is not None:
+            variants[vpath].update({
+                "refinement_sweeps": int(info_r.iterations), "tol": REFINE_TOL,
+                "final_rel_residual": float(info_r.residual[info_r.iterations]),
+                "converged": bool(info_r.converged)})
         plan.close()
         del u
 
@@ -293,15 +325,22 @@ def run_gb300(args):
     peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
     n1 = p.shape[1]
     name, (launches, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
-    roof = roofline_entry(name, launches, tot_ms, args.steps, N, 16, n1, peaks, fp64=True, tables=True)
-    kernels_c128 = {k: roofline_entry(k, v[0], v[1], args.steps, N, 16, n1, peaks, fp64=True, tables=True)
-                    for k, v in prof.items()}
-    if variants.get("c64_refined"):
-        pr = variants["c64_refined"].pop("_prof")
-        variants["c64_refined"]["kernels"] = {
-            k: roofline_entry(k, v[0], v[1], args.steps, N, 8, n1, peaks, fp64=False, accum=(k == "dft_inv"))
-            for k, v in pr.items()}
+    def kernels_of(path, pr):
+        f64 = path == "c128"
+        return {k: roofline_entry(k, v[0], v[1], args.steps, N, 16 if f64 else 8, n1, peaks, fp64=f64,
+                                  accum=(k == "dft_inv" and not f64), tables=f64, ff=(path == "c64_ff"))
+                for k, v in pr.items()}
+
+    kernels_main = kernels_of(args.path, prof)
+    roof = dict(kernels_main[name])
+    for vpath, v in variants.items():
+        v["kernels"] = kernels_of(vpath, v.pop("_prof"))
     gpu_launches = sum(v[0] for v in prof.values())
+    if info.iterations:
+        refine = {"refinement_sweeps": int(info.iterations), "tol": REFINE_TOL,
+                  "final_rel_residual": float(info.residual[info.iterations]), "converged": bool(info.converged)}
+    else:
+        refine = None
 
     # --- CPU oracle baseline (rank 0, N = 1 only) ---
     cpu = None
@@ -311,14 +350,15 @@ def run_gb300(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded complex Gaussian x Gaussian bump)",
+        "vs_baseline": None, "dtype": PATH_DTYPE[args.path],
+        "data": "synthetic (seeded complex Gaussian x Gaussian bump)",
         "config": {"workload": p.name, "nodes": list(p.shape), "h": list(p.h), "omega": p.omega,
-                   "precision": "complex128 plain", "rhs_per_step": 1,
+                   "precision": PATH_PRECISION[args.path], "rhs_per_step": 1,
                    "l2": "inputs larger than L2 (f and u are 537 MB each)", "parallelism": f"replicas x{world}"},
-        "rel_err_sampled": err_c128,
+        "rel_err_sampled": err_c128, "refinement": refine,
         "gpu_launches": gpu_launches,
         "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()},
-        "kernels": kernels_c128,
+        "kernels": kernels_main,
         "roofline": roof, "clocks": clocks, "e2e": e2e, "variants": variants, "cpu_baseline": cpu,
         "plan_seconds": info.plan_seconds,
     }
@@ -391,7 +431,7 @@ def main():
     ap.add_argument("--minimal", action="store_true", help="timed solves only (no e2e, variants, CPU baseline)")
     ap.add_argument("--workload", default="2d_large", choices=["2d_large", "3d"],
                     help="2d_large: the benchmark workload; 3d: the 512^3 workload (measurement, not the bench line)")
-    ap.add_argument("--path", default="c128", choices=["c128", "c64_refined"],
+    ap.add_argument("--path", default="c128", choices=list(PATHS_NAMES),
                     help="path timed as the main line (profiling cases; the benchmark line is c128)")
     args = ap.parse_args()
     if args.minimal:

@@ -30,8 +30,9 @@
  * Element types by precision mode:
  *   HELM_C128         f, u complex128; all arithmetic FP64.
  *   HELM_C64_REFINED  f, u complex128; solves in FP32 (complex64), residual
- *                     r = f - A u in FP64, iterative refinement until
- *                     ||r|| / ||f|| <= tol (default 1e-14) or max_iter.
+ *                     r = f - A u in FP64 (or float-float, helm_set_residual),
+ *                     iterative refinement until ||r|| / ||f|| <= tol
+ *                     (default 1e-14) or max_iter.
  *   HELM_C64_RAW      f, u complex64; one FP32 solve, no refinement.
  *
  * Errors: every entry point returns a helm_status; no exception crosses the
@@ -54,6 +55,17 @@ enum helm_dtype {
   HELM_C128 = 0,
   HELM_C64_REFINED = 1,
   HELM_C64_RAW = 2
+};
+
+/* Arithmetic of the refinement residual r = f - A u (HELM_C64_REFINED).
+ *   HELM_RESID_FP64  u accumulated in complex128, residual in FP64.
+ *   HELM_RESID_FF    f and u held as float-float pairs (hi + lo floats, about
+ *                    48 significant bits), residual and accumulation on the
+ *                    FP32 pipes; u converted to complex128 once at the end.
+ *                    Residual floor about 1e-13 relative: use tol >= 1e-12. */
+enum helm_residual {
+  HELM_RESID_FP64 = 0,
+  HELM_RESID_FF = 1
 };
 
 enum helm_status {
@@ -81,6 +93,7 @@ typedef struct helm_info {
   int32_t max_iter;        /* refinement sweep limit */
   int32_t n_dft_stages;    /* stages of the x1 transform */
   size_t device_bytes;     /* device memory owned by the plan */
+  int32_t residual_kind;   /* helm_residual of the plan */
 } helm_info;
 
 /* --- Plan (the paper's "Initialization", Section 6) -----------------------
@@ -118,8 +131,16 @@ int helm_set_auxiliary(helm_plan_t p, double rho, int phase_quarters);
 int helm_set_stream(helm_plan_t p, void* cuda_stream);
 
 /* Refinement controls for HELM_C64_REFINED: stop when ||r||/||f|| <= tol or
- * after max_iter sweeps (1 <= max_iter <= 16). */
+ * after max_iter sweeps (tol >= 0, 1 <= max_iter <= 15). */
 int helm_set_refinement(helm_plan_t p, double tol, int max_iter);
+
+/* Residual arithmetic of HELM_C64_REFINED (helm_residual; default
+ * HELM_RESID_FP64).  Iterative refinement is not part of the paper's method;
+ * this selects how its residual is formed.  HELM_RESID_FF allocates two more
+ * float-float vectors (32 bytes per unknown) at its first solve.  Returns
+ * HELM_EINVAL for another kind or a plan of another dtype.  Call between
+ * solves. */
+int helm_set_residual(helm_plan_t p, int kind);
 
 /* --- Solve (Sections 4.2 and 5.2: Steps 1-3) ------------------------------
  * f, u: DEVICE pointers to N = nx*ny(*nz) complex values in the layout above

@@ -23,6 +23,7 @@ if not os.path.exists(_LIB_PATH):
 lib = ctypes.CDLL(_LIB_PATH)
 
 HELM_C128, HELM_C64_REFINED, HELM_C64_RAW = 0, 1, 2
+HELM_RESID_FP64, HELM_RESID_FF = 0, 1
 HELM_OK, HELM_EINVAL, HELM_ENOMEM, HELM_ECUDA, HELM_ENOTCONV, HELM_ETIMEOUT, HELM_EUNSUPPORTED, HELM_ENUMERIC = \
     0, -1, -2, -3, -4, -5, -6, -7
 
@@ -34,7 +35,7 @@ class helm_info(ctypes.Structure):
                 ("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("residual", ctypes.c_double * 16), ("plan_seconds", ctypes.c_double),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("n_dft_stages", ctypes.c_int32),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("residual_kind", ctypes.c_int32)]
 
 
 class helm_profile_entry(ctypes.Structure):
@@ -47,6 +48,7 @@ _SIGS = {
     "helm_set_stream": (_i32, [_vp, _vp]),
     "helm_set_refinement": (_i32, [_vp, _dbl, _i32]),
     "helm_set_auxiliary": (_i32, [_vp, _dbl, _i32]),
+    "helm_set_residual": (_i32, [_vp, _i32]),
     "helm_solve": (_i32, [_vp, _vp, _vp]),
     "helm_solve_host": (_i32, [_vp, _vp, _vp]),
     "helm_solve_debug": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -117,6 +119,10 @@ def helm_set_auxiliary(plan, rho, phase_quarters):
 
 def helm_set_refinement(plan, tol, max_iter):
     _check(lib.helm_set_refinement(plan, float(tol), int(max_iter)), "helm_set_refinement", plan)
+
+
+def helm_set_residual(plan, kind):
+    _check(lib.helm_set_residual(plan, int(kind)), "helm_set_residual", plan)
 
 
 def helm_solve(plan, f, u):

@@ -56,6 +56,9 @@ struct helm_plan {
   double plan_seconds = 0;
   double tol = 1e-14;
   int max_iter = 10;
+  int resid_kind = HELM_RESID_FP64;
+  float4* ffb = nullptr;  // float-float refinement: f (hi, lo) ...
+  float4* ufb = nullptr;  // ... and the accumulated u
   Plan3D p3;
   Profiler prof;
   std::string err;
@@ -319,14 +322,43 @@ int solve_core(helm_plan* p, const void* in, int in_is_double, void* out, int ou
   return e == cudaSuccess ? HELM_OK : cuda_fail(p, e, "solve3d");
 }
 
+// Refinement with f and u as float-float vectors: split f once, accumulate the
+// FP32 corrections into (hi, lo) in the inverse-transform epilogue, form the
+// residual in float-float, convert u to complex128 at the end.
+int run_refine_ff(helm_plan* p, const void* f, void* u, void* dbg_fhat, void* dbg_v, void* dbg_w) {
+  const int64_t N = p->n[0] * p->n[1] * p->n[2];
+  int rc;
+  if (!p->ffb) {
+    if ((rc = dev_alloc(p, (void**)&p->ffb, N * sizeof(float4))) ||
+        (rc = dev_alloc(p, (void**)&p->ufb, N * sizeof(float4))))
+      return rc;
+  }
+  HELM_PK("split_ff", launch_split_ff((const double2*)f, p->ffb, N, p->stream));
+  rc = solve_core(p, p->ffb, kInFF, p->ufb, kOutFF, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
+  if (rc) return rc;
+  const int* skip = &p->state->done;
+  int64_t nblocks = 0;
+  for (int it = 0; it <= p->max_iter; ++it) {
+    HELM_PK("residual_ff", launch_residual_ff(p->dim, p->n, p->h, p->omega, p->ffb, p->ufb, p->rbuf, p->sums,
+                                              &nblocks, skip, p->stream));
+    HELM_PK("residual_finalize", launch_residual_finalize(p->sums, nblocks, p->state, it == p->max_iter, p->stream));
+    if (it == p->max_iter) break;
+    rc = solve_core(p, p->rbuf, kInC64, p->ufb, kOutAccumFF, 1.0, skip, nullptr, nullptr, nullptr);
+    if (rc) return rc;
+  }
+  HELM_PK("join_ff", launch_join_ff(p->ufb, (double2*)u, N, p->stream));
+  return HELM_OK;
+}
+
 int run_solve(helm_plan* p, const void* f, void* u, void* dbg_fhat, void* dbg_v, void* dbg_w) {
-  if (p->dtype == HELM_C128) return solve_core(p, f, 1, u, kOutC128, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
-  if (p->dtype == HELM_C64_RAW) return solve_core(p, f, 0, u, kOutC64, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
+  if (p->dtype == HELM_C128) return solve_core(p, f, kInC128, u, kOutC128, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
+  if (p->dtype == HELM_C64_RAW) return solve_core(p, f, kInC64, u, kOutC64, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
   // HELM_C64_REFINED: u0 = S(f); then r = f - A u (FP64), u += S(r) until tol.
   RefineState init{};
   init.tol = p->tol;
   HELM_CK(cudaMemcpyAsync(p->state, &init, sizeof(init), cudaMemcpyHostToDevice, p->stream));
-  int rc = solve_core(p, f, 1, u, kOutC128, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
+  if (p->resid_kind == HELM_RESID_FF) return run_refine_ff(p, f, u, dbg_fhat, dbg_v, dbg_w);
+  int rc = solve_core(p, f, kInC128, u, kOutC128, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
   if (rc) return rc;
   const int* skip = &p->state->done;
   int64_t nblocks = 0;
@@ -335,7 +367,7 @@ int run_solve(helm_plan* p, const void* f, void* u, void* dbg_fhat, void* dbg_v,
                             &nblocks, skip, p->stream));
     HELM_PK("residual_finalize", launch_residual_finalize(p->sums, nblocks, p->state, it == p->max_iter, p->stream));
     if (it == p->max_iter) break;
-    rc = solve_core(p, p->rbuf, 0, u, kOutAccumC128, 1.0, skip, nullptr, nullptr, nullptr);
+    rc = solve_core(p, p->rbuf, kInC64, u, kOutAccumC128, 1.0, skip, nullptr, nullptr, nullptr);
     if (rc) return rc;
   }
   return HELM_OK;
@@ -389,7 +421,7 @@ int alloc_refine(helm_plan* p) {
     return rc;
   }
   if ((rc = dev_alloc(p, (void**)&p->rbuf, N * sizeof(float2))) ||
-      (rc = dev_alloc(p, (void**)&p->sums, ((N + 255) / 256 + p->n[0]) * 2 * sizeof(double))) ||
+      (rc = dev_alloc(p, (void**)&p->sums, residual_blocks(p->dim, p->n) * 2 * sizeof(double))) ||
       (rc = dev_alloc(p, (void**)&p->state, sizeof(RefineState))))
     return rc;
   return HELM_OK;
@@ -413,6 +445,8 @@ void destroy_plan(helm_plan* p) {
   cudaFree(p->constA);
   cudaFree(p->rbuf);
   cudaFree(p->sums);
+  cudaFree(p->ffb);
+  cudaFree(p->ufb);
   cudaFree(p->state);
   cudaFree(p->host_f);
   cudaFree(p->host_u);
@@ -627,6 +661,12 @@ int helm_set_refinement(helm_plan_t p, double tol, int max_iter) {
   return HELM_OK;
 }
 
+int helm_set_residual(helm_plan_t p, int kind) {
+  if (!p || p->dtype != HELM_C64_REFINED || (kind != HELM_RESID_FP64 && kind != HELM_RESID_FF)) return HELM_EINVAL;
+  p->resid_kind = kind;
+  return HELM_OK;
+}
+
 int helm_solve(helm_plan_t p, const void* f, void* u) {
   if (!p || !f || !u || f == u) return HELM_EINVAL;
   return run_solve(p, f, u, nullptr, nullptr, nullptr);
@@ -670,6 +710,7 @@ int helm_get_info(helm_plan_t p, helm_info* info) {
   info->max_iter = p->max_iter;
   info->n_dft_stages = p->axo.dft.nstages;
   info->device_bytes = p->bytes;
+  info->residual_kind = p->resid_kind;
   if (p->dtype == HELM_C64_REFINED && !s.converged) return HELM_ENOTCONV;
   return HELM_OK;
 }

@@ -119,7 +119,11 @@ __device__ __forceinline__ void butterfly(const C* __restrict__ src, C* __restri
 template <typename T>
 __device__ __forceinline__ typename cpx<T>::type load_in(const void* p, int in_is_double, int64_t i) {
   using C = typename cpx<T>::type;
-  if (in_is_double) return cvt<C>(reinterpret_cast<const double2*>(p)[i]);
+  if (in_is_double == kInC128) return cvt<C>(reinterpret_cast<const double2*>(p)[i]);
+  if (in_is_double == kInFF) {
+    const float4 q = reinterpret_cast<const float4*>(p)[i];
+    return mk<C>(q.x, q.y);
+  }
   return cvt<C>(reinterpret_cast<const float2*>(p)[i]);
 }
 
@@ -129,11 +133,18 @@ __device__ __forceinline__ void store_out(void* p, int mode, int64_t i, C v, dou
     reinterpret_cast<double2*>(p)[i] = make_double2((double)v.x, (double)v.y);
   } else if (mode == kOutC64) {
     reinterpret_cast<float2*>(p)[i] = make_float2((float)v.x, (float)v.y);
-  } else {  // kOutAccumC128: u += accum_scale * v
+  } else if (mode == kOutAccumC128) {  // u += accum_scale * v
     double2 u = reinterpret_cast<double2*>(p)[i];
     u.x += accum_scale * (double)v.x;
     u.y += accum_scale * (double)v.y;
     reinterpret_cast<double2*>(p)[i] = u;
+  } else if (mode == kOutFF) {
+    reinterpret_cast<float4*>(p)[i] = make_float4((float)v.x, (float)v.y, 0.f, 0.f);
+  } else {  // kOutAccumFF: float-float u += accum_scale * v
+    float4 u = reinterpret_cast<float4*>(p)[i];
+    ff_add_f(u.x, u.z, (float)accum_scale * (float)v.x);
+    ff_add_f(u.y, u.w, (float)accum_scale * (float)v.y);
+    reinterpret_cast<float4*>(p)[i] = u;
   }
 }
 
@@ -270,6 +281,9 @@ cudaError_t launch_dft_rows(int prec, const void* in, int in_is_double, void* ou
                             int64_t nrows, const DftPlan& p, const void* tw, int sign, double scale,
                             double accum_scale, const void* sc_in, const void* sc_out, const int* skip,
                             cudaStream_t st) {
+  if (dft_rows_pow2_supported(p.n))
+    return launch_dft_rows_pow2(prec, in, in_is_double, out, out_mode, nrows, p.n, tw, sign, scale, accum_scale,
+                                sc_in, sc_out, skip, st);
   const size_t es = prec == kPrecF64 ? sizeof(double2) : sizeof(float2);
   // lines per CTA: enough points to keep 256 threads busy, bounded by smem
   int L = (int)std::max<int64_t>(1, std::min<int64_t>(nrows, 2048 / std::max(1, p.n)));

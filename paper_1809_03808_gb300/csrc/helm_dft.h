@@ -10,13 +10,18 @@
 namespace helm {
 
 enum { kPrecF64 = 0, kPrecF32 = 1 };
-enum { kOutC128 = 0, kOutC64 = 1, kOutAccumC128 = 2 };
+enum { kOutC128 = 0, kOutC64 = 1, kOutAccumC128 = 2, kOutFF = 3, kOutAccumFF = 4 };
+// Input kinds (the in_is_double argument): complex64, complex128, or a
+// float-float complex vector (float4 per point: re_hi, im_hi, re_lo, im_lo),
+// of which the transform reads the leading (hi) part.
+enum { kInC64 = 0, kInC128 = 1, kInFF = 2 };
 
 bool dft_supported(const DftPlan& p, size_t elem_bytes, int max_smem);
 
 // Lines along the contiguous (last) axis: nrows lines of length p.n.
-// in: complex128 if in_is_double else complex64; computed in `prec`; out per
-// out_mode (kOutAccumC128: out += accum_scale * result).  sign -1 forward,
+// in: of kind in_is_double (kIn*); computed in `prec`; out per out_mode
+// (kOutAccumC128: out += accum_scale * result; kOutFF: float-float vector
+// (result, 0); kOutAccumFF: float-float out += accum_scale * result).  sign -1 forward,
 // +1 inverse; `scale` multiplies the transform.  skip: optional device flag,
 // the kernel returns at once when *skip != 0.
 // sc_in / sc_out: optional per-point complex factors (length p.n, compute
@@ -26,6 +31,13 @@ cudaError_t launch_dft_rows(int prec, const void* in, int in_is_double, void* ou
                             int64_t nrows, const DftPlan& p, const void* tw, int sign, double scale,
                             double accum_scale, const void* sc_in, const void* sc_out, const int* skip,
                             cudaStream_t st);
+
+// Power-of-two lines (16 <= n <= 8192) along the contiguous axis: the same
+// contract as launch_dft_rows with the radices fixed at compile time.
+bool dft_rows_pow2_supported(int64_t n);
+cudaError_t launch_dft_rows_pow2(int prec, const void* in, int in_is_double, void* out, int out_mode, int64_t nrows,
+                                 int64_t n, const void* tw, int sign, double scale, double accum_scale,
+                                 const void* sc_in, const void* sc_out, const int* skip, cudaStream_t st);
 
 // Lines along a middle axis: the array viewed as [outer][p.n][inner].
 cudaError_t launch_dft_cols(int prec, const void* in, int in_is_double, void* out, int out_mode,

@@ -1,0 +1,358 @@
+// Batched DFT of power-of-two lines along the contiguous axis (the transform
+// of eqs. step1FFTfcoeff / step3IFFTz3coeff for n = 2^m, 16 <= n <= 8192).
+//
+// Stockham auto-sort with the radices fixed at compile time: one leading pass
+// of radix 2^(m mod 4) when m is not a multiple of 4, then radix-16 passes.
+// Every thread owns 16 points of a line in registers through every pass
+// (n / 16 threads per line): it reads its butterflies' inputs, multiplies by
+// the twiddles, runs the 16 / R R-point DFTs in registers and writes the
+// outputs to their Stockham positions.  The first pass reads global memory
+// directly (coalesced across the threads of a line), the last pass writes it
+// directly; the passes in between exchange through shared memory padded by
+// one point per 16 so that both the strided writes and the unit-stride reads
+// are free of bank conflicts.
+#include "helm_dft.h"
+#include "helm_kernels.cuh"
+
+namespace helm {
+
+namespace {
+
+template <typename C, int SIGN>
+__device__ __forceinline__ C twid(const C* __restrict__ tw, int e) {
+  C w = __ldg(&tw[e]);  // forward table e^{-2 pi i e / n}
+  if (SIGN > 0) w.y = -w.y;
+  return w;
+}
+
+// (SIGN i) a
+template <typename C, int SIGN>
+__device__ __forceinline__ C mul_si(C a) {
+  C o;
+  if (SIGN > 0) {
+    o.x = -a.y;
+    o.y = a.x;
+  } else {
+    o.x = a.y;
+    o.y = -a.x;
+  }
+  return o;
+}
+
+// (cr + i ci) a for compile-time constants
+template <typename C>
+__device__ __forceinline__ C mul_c(C a, double cr, double ci) {
+  using T = decltype(a.x);
+  C o;
+  o.x = a.x * (T)cr - a.y * (T)ci;
+  o.y = a.x * (T)ci + a.y * (T)cr;
+  return o;
+}
+
+// In-register R-point DFTs, natural order in and out:
+// y_q = sum_r v_r e^{SIGN 2 pi i r q / R}.
+template <typename C, int SIGN>
+__device__ __forceinline__ void dft2(C* v) {
+  const C a = v[0];
+  v[0] = cadd(a, v[1]);
+  v[1] = csub(a, v[1]);
+}
+
+template <typename C, int SIGN>
+__device__ __forceinline__ void dft4s(C& v0, C& v1, C& v2, C& v3) {
+  const C t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3), t3 = mul_si<C, SIGN>(csub(v1, v3));
+  v0 = cadd(t0, t2);
+  v1 = cadd(t1, t3);
+  v2 = csub(t0, t2);
+  v3 = csub(t1, t3);
+}
+
+template <typename C, int SIGN>
+__device__ __forceinline__ void dft4(C* v) {
+  dft4s<C, SIGN>(v[0], v[1], v[2], v[3]);
+}
+
+constexpr double kH = 0.70710678118654752440;   // cos(pi/4)
+constexpr double kC8 = 0.92387953251128675613;  // cos(pi/8)
+constexpr double kS8 = 0.38268343236508977173;  // sin(pi/8)
+
+template <typename C, int SIGN>
+__device__ __forceinline__ void dft8(C* v) {
+  // even and odd halves: E_q in v[2q], O_q in v[2q+1]
+  dft4s<C, SIGN>(v[0], v[2], v[4], v[6]);
+  dft4s<C, SIGN>(v[1], v[3], v[5], v[7]);
+  const double s = SIGN;
+  const C o1 = mul_c(v[3], kH, s * kH);     // W8^1 O_1
+  const C o2 = mul_si<C, SIGN>(v[5]);       // W8^2 O_2
+  const C o3 = mul_c(v[7], -kH, s * kH);    // W8^3 O_3
+  const C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1);
+  v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2);
+  v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3);
+  v[7] = csub(e3, o3);
+}
+
+template <typename C, int SIGN>
+__device__ __forceinline__ void dft16(C* v) {
+  // r = b + 4a: DFT4 over a for each b (results Z_b[q1] at v[b + 4 q1])
+#pragma unroll
+  for (int b = 0; b < 4; ++b) dft4s<C, SIGN>(v[b], v[b + 4], v[b + 8], v[b + 12]);
+  // twiddles W16^{b q1}
+  const double s = SIGN;
+  v[5] = mul_c(v[5], kC8, s * kS8);     // b1 q1 = 1
+  v[9] = mul_c(v[9], kH, s * kH);       // b1 q2 = 2
+  v[13] = mul_c(v[13], kS8, s * kC8);   // b1 q3 = 3
+  v[6] = mul_c(v[6], kH, s * kH);       // b2 q1 = 2
+  v[10] = mul_si<C, SIGN>(v[10]);       // b2 q2 = 4
+  v[14] = mul_c(v[14], -kH, s * kH);    // b2 q3 = 6
+  v[7] = mul_c(v[7], kS8, s * kC8);     // b3 q1 = 3
+  v[11] = mul_c(v[11], -kH, s * kH);    // b3 q2 = 6
+  v[15] = mul_c(v[15], -kC8, -s * kS8); // b3 q3 = 9
+  // DFT4 over b for each q1: y[q1 + 4 q2] lands at v[4 q1 + q2]
+#pragma unroll
+  for (int q1 = 0; q1 < 4; ++q1) dft4s<C, SIGN>(v[4 * q1], v[4 * q1 + 1], v[4 * q1 + 2], v[4 * q1 + 3]);
+  C y[16];
+#pragma unroll
+  for (int q1 = 0; q1 < 4; ++q1)
+#pragma unroll
+    for (int q2 = 0; q2 < 4; ++q2) y[q1 + 4 * q2] = v[4 * q1 + q2];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = y[i];
+}
+
+template <typename C, int R, int SIGN>
+__device__ __forceinline__ void dft_r(C* v) {
+  if constexpr (R == 2) dft2<C, SIGN>(v);
+  else if constexpr (R == 4) dft4<C, SIGN>(v);
+  else if constexpr (R == 8) dft8<C, SIGN>(v);
+  else dft16<C, SIGN>(v);
+}
+
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+// Butterfly q of thread t in a pass of radix R: j = t + q n/16; its input r
+// is point j + r n/R; its output r' goes to (j - k) R + k + r' NS, k = j mod NS.
+template <int N, int R>
+__device__ __forceinline__ int in_index(int t, int q, int r) {
+  return t + q * (N / 16) + r * (N / R);
+}
+template <int N, int R, int NS>
+__device__ __forceinline__ int out_index(int t, int q, int rp) {
+  const int j = t + q * (N / 16);
+  const int k = j & (NS - 1);
+  return (j - k) * R + k + rp * NS;
+}
+
+// Twiddles and R-point DFTs of one pass on the thread's 16 registers.
+template <typename C, int N, int R, int NS, int SIGN>
+__device__ __forceinline__ void pass_compute(C* v, int t, const C* __restrict__ tw) {
+#pragma unroll
+  for (int q = 0; q < 16 / R; ++q) {
+    if constexpr (NS > 1) {
+      const int k = (t + q * (N / 16)) & (NS - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], twid<C, SIGN>(tw, r * k * (N / (NS * R))));
+    }
+    dft_r<C, R, SIGN>(v + q * R);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ typename cpx<T>::type load_pt(const void* p, int in_is_double, int64_t i) {
+  using C = typename cpx<T>::type;
+  if (in_is_double == kInC128) return cvt<C>(__ldg(reinterpret_cast<const double2*>(p) + i));
+  if (in_is_double == kInFF) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p) + i);
+    return mk<C>(q.x, q.y);
+  }
+  return cvt<C>(__ldg(reinterpret_cast<const float2*>(p) + i));
+}
+
+template <typename C>
+__device__ __forceinline__ void store_pt(void* p, int mode, int64_t i, C v, double accum_scale) {
+  if (mode == kOutC128) {
+    reinterpret_cast<double2*>(p)[i] = make_double2((double)v.x, (double)v.y);
+  } else if (mode == kOutC64) {
+    reinterpret_cast<float2*>(p)[i] = make_float2((float)v.x, (float)v.y);
+  } else if (mode == kOutAccumC128) {  // u += accum_scale * v
+    double2 u = reinterpret_cast<double2*>(p)[i];
+    u.x += accum_scale * (double)v.x;
+    u.y += accum_scale * (double)v.y;
+    reinterpret_cast<double2*>(p)[i] = u;
+  } else if (mode == kOutFF) {
+    reinterpret_cast<float4*>(p)[i] = make_float4((float)v.x, (float)v.y, 0.f, 0.f);
+  } else {  // kOutAccumFF: float-float u += accum_scale * v
+    float4 u = reinterpret_cast<float4*>(p)[i];
+    ff_add_f(u.x, u.z, (float)accum_scale * (float)v.x);
+    ff_add_f(u.y, u.w, (float)accum_scale * (float)v.y);
+    reinterpret_cast<float4*>(p)[i] = u;
+  }
+}
+
+// Passes 1 .. NP-1 (radix 16, span NS): shared memory in, shared memory or
+// (last pass) global memory out.
+template <typename T, int N, int SIGN, int NS, int LEFT>
+__device__ __forceinline__ void later_passes(typename cpx<T>::type* v, typename cpx<T>::type* buf, int t,
+                                             bool act, int64_t g0, void* __restrict__ out, int out_mode,
+                                             const typename cpx<T>::type* __restrict__ tw, T scale,
+                                             double accum_scale, const typename cpx<T>::type* __restrict__ sc_out) {
+  using C = typename cpx<T>::type;
+  __syncthreads();  // the previous pass's outputs are in buf
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = buf[pad16(in_index<N, 16>(t, 0, r))];
+  pass_compute<C, N, 16, NS, SIGN>(v, t, tw);
+  if constexpr (LEFT == 1) {
+    if (act) {
+#pragma unroll
+      for (int rp = 0; rp < 16; ++rp) {
+        const int o = out_index<N, 16, NS>(t, 0, rp);
+        C x = cscale(v[rp], scale);
+        if (sc_out) x = cmul(x, __ldg(&sc_out[o]));
+        store_pt<C>(out, out_mode, g0 + o, x, accum_scale);
+      }
+    }
+  } else {
+    __syncthreads();  // every thread has read its inputs
+#pragma unroll
+    for (int rp = 0; rp < 16; ++rp) buf[pad16(out_index<N, 16, NS>(t, 0, rp))] = v[rp];
+    later_passes<T, N, SIGN, NS * 16, LEFT - 1>(v, buf, t, act, g0, out, out_mode, tw, scale, accum_scale, sc_out);
+  }
+}
+
+template <int LOG2N>
+__host__ __device__ constexpr int pow2_threads() {
+  return LOG2N >= 13 ? (1 << LOG2N) / 16 : 256;
+}
+
+template <typename T, int LOG2N, int SIGN>
+__global__ void __launch_bounds__(pow2_threads<LOG2N>())
+    k_dft_rows_pow2(const void* __restrict__ in, int in_is_double, void* __restrict__ out, int out_mode,
+                    int64_t nrows, const typename cpx<T>::type* __restrict__ tw, T scale, double accum_scale,
+                    const typename cpx<T>::type* __restrict__ sc_in,
+                    const typename cpx<T>::type* __restrict__ sc_out, const int* __restrict__ skip) {
+  using C = typename cpx<T>::type;
+  constexpr int N = 1 << LOG2N;
+  constexpr int TPL = N / 16;                      // threads per line
+  constexpr int L = pow2_threads<LOG2N>() / TPL;  // lines per CTA
+  constexpr int NPAD = N + N / 16;
+  constexpr int E = LOG2N % 4;
+  constexpr int R0 = E ? (1 << E) : 16;
+  constexpr int NP = (LOG2N + 3) / 4;
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int t = threadIdx.x % TPL;
+  const int line = threadIdx.x / TPL;
+  const int64_t row = (int64_t)blockIdx.x * L + line;
+  const bool act = row < nrows;
+  const int64_t g0 = row * N;
+  C* buf = reinterpret_cast<C*>(smem_raw) + line * NPAD;
+  C v[16];
+  // pass 0 (radix R0, no twiddles): global memory in
+#pragma unroll
+  for (int q = 0; q < 16 / R0; ++q)
+#pragma unroll
+    for (int r = 0; r < R0; ++r) {
+      const int i = in_index<N, R0>(t, q, r);
+      C x = mk<C>(0, 0);
+      if (act) {
+        x = load_pt<T>(in, in_is_double, g0 + i);
+        if (sc_in) x = cmul(x, __ldg(&sc_in[i]));
+      }
+      v[q * R0 + r] = x;
+    }
+  pass_compute<C, N, R0, 1, SIGN>(v, t, tw);
+  if constexpr (NP == 1) {
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < 16 / R0; ++q)
+#pragma unroll
+        for (int rp = 0; rp < R0; ++rp) {
+          const int o = out_index<N, R0, 1>(t, q, rp);
+          C x = cscale(v[q * R0 + rp], scale);
+          if (sc_out) x = cmul(x, __ldg(&sc_out[o]));
+          store_pt<C>(out, out_mode, g0 + o, x, accum_scale);
+        }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16 / R0; ++q)
+#pragma unroll
+      for (int rp = 0; rp < R0; ++rp) buf[pad16(out_index<N, R0, 1>(t, q, rp))] = v[q * R0 + rp];
+    later_passes<T, N, SIGN, R0, NP - 1>(v, buf, t, act, g0, out, out_mode, tw, scale, accum_scale, sc_out);
+  }
+}
+
+template <typename T, int LOG2N, int SIGN>
+cudaError_t launch_pow2_t(const void* in, int in_is_double, void* out, int out_mode, int64_t nrows,
+                          const void* tw, double scale, double accum_scale, const void* sc_in, const void* sc_out,
+                          const int* skip, cudaStream_t st) {
+  using C = typename cpx<T>::type;
+  constexpr int N = 1 << LOG2N;
+  constexpr int threads = pow2_threads<LOG2N>();
+  constexpr int L = threads / (N / 16);
+  constexpr int NP = (LOG2N + 3) / 4;
+  const size_t smem = NP > 1 ? (size_t)L * (N + N / 16) * sizeof(C) : 0;
+  const int64_t grid = (nrows + L - 1) / L;
+  if (grid == 0) return cudaSuccess;
+  auto k = k_dft_rows_pow2<T, LOG2N, SIGN>;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<(unsigned)grid, threads, smem, st>>>(in, in_is_double, out, out_mode, nrows, (const C*)tw, (T)scale,
+                                           accum_scale, (const C*)sc_in, (const C*)sc_out, skip);
+  return cudaGetLastError();
+}
+
+template <typename T, int SIGN>
+cudaError_t launch_pow2_s(int log2n, const void* in, int in_is_double, void* out, int out_mode, int64_t nrows,
+                          const void* tw, double scale, double accum_scale, const void* sc_in, const void* sc_out,
+                          const int* skip, cudaStream_t st) {
+#define HELM_POW2(LG)                                                                                       \
+  case LG:                                                                                                  \
+    return launch_pow2_t<T, LG, SIGN>(in, in_is_double, out, out_mode, nrows, tw, scale, accum_scale, sc_in, \
+                                      sc_out, skip, st);
+  switch (log2n) {
+    HELM_POW2(4)
+    HELM_POW2(5)
+    HELM_POW2(6)
+    HELM_POW2(7)
+    HELM_POW2(8)
+    HELM_POW2(9)
+    HELM_POW2(10)
+    HELM_POW2(11)
+    HELM_POW2(12)
+    HELM_POW2(13)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef HELM_POW2
+}
+
+}  // namespace
+
+bool dft_rows_pow2_supported(int64_t n) { return n >= 16 && n <= 8192 && (n & (n - 1)) == 0; }
+
+cudaError_t launch_dft_rows_pow2(int prec, const void* in, int in_is_double, void* out, int out_mode, int64_t nrows,
+                                 int64_t n, const void* tw, int sign, double scale, double accum_scale,
+                                 const void* sc_in, const void* sc_out, const int* skip, cudaStream_t st) {
+  if (!dft_rows_pow2_supported(n)) return cudaErrorInvalidValue;
+  int log2n = 0;
+  while ((int64_t(1) << log2n) < n) ++log2n;
+  if (prec == kPrecF64) {
+    return sign < 0 ? launch_pow2_s<double, -1>(log2n, in, in_is_double, out, out_mode, nrows, tw, scale,
+                                                 accum_scale, sc_in, sc_out, skip, st)
+                    : launch_pow2_s<double, 1>(log2n, in, in_is_double, out, out_mode, nrows, tw, scale,
+                                                accum_scale, sc_in, sc_out, skip, st);
+  }
+  return sign < 0 ? launch_pow2_s<float, -1>(log2n, in, in_is_double, out, out_mode, nrows, tw, scale, accum_scale,
+                                            sc_in, sc_out, skip, st)
+                  : launch_pow2_s<float, 1>(log2n, in, in_is_double, out, out_mode, nrows, tw, scale, accum_scale,
+                                           sc_in, sc_out, skip, st);
+}
+
+}  // namespace helm

@@ -107,6 +107,37 @@ __device__ __forceinline__ C warp_sum(C v) {
   return v;
 }
 
+// Float-float arithmetic: a real value held as hi + lo with |lo| <= ulp(hi)/2
+// (about 48 significant bits) and computed on the FP32 pipes.  Built from the
+// error-free transformations TwoSum (Knuth), FastTwoSum (Dekker, |a| >= |b|)
+// and TwoProduct through a fused multiply-add.  The build never reassociates
+// floating-point additions, which these rely on.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+// (sh, sl) += (ch + cl) (uh + ul), dropping cl ul (below 2^-48 relative)
+__device__ __forceinline__ void ff_mac(float& sh, float& sl, float ch, float cl, float uh, float ul) {
+  const float p = ch * uh;
+  float e = fmaf(ch, uh, -p);
+  e = fmaf(ch, ul, fmaf(cl, uh, e));
+  float s, t;
+  two_sum(sh, p, s, t);
+  sh = s;
+  sl += t + e;
+}
+// (hi, lo) += v, renormalised
+__device__ __forceinline__ void ff_add_f(float& hi, float& lo, float v) {
+  float s, e;
+  two_sum(hi, v, s, e);
+  fast_two_sum(s, lo + e, hi, lo);
+}
+
 // Line matrix T = K + s M along the tridiagonal axis (eqs. matrixK/matrixM;
 // K with absorbing corners 1 - i w h).  diag in the interior, diag at both
 // ends, constant off-diagonal.

@@ -41,6 +41,24 @@ struct ResidArgs {
   double cin[27];  // interior coefficients, index (d0+1)*9 + (d1+1)*3 + (d2+1) (3D) or (d0+1)*3+(d1+1)
 };
 
+// Float-float copies of the coefficients (each value as hi + lo floats).
+struct FF2 {
+  float h, l;
+};
+struct AxisFF {
+  FF2 mdi, mde, mo;   // M: interior diagonal, end diagonal, off-diagonal
+  FF2 kdi, kder, ko;  // K: interior diagonal, end diagonal (real part), off-diagonal
+  FF2 kdei;           // K end diagonal, imaginary part (-w)
+  FF2 cdi, cde, co;   // K - w^2 M: interior diagonal, end diagonal (real), off-diagonal
+};
+struct ResidFFArgs {
+  int64_t n[3];
+  double h[3];
+  double omega;
+  AxisFF ax[3];
+  FF2 cin[9];  // 2D interior coefficients, index (d0+1)*3 + (d1+1)
+};
+
 __global__ void __launch_bounds__(256) k_residual(ResidArgs a, const double2* __restrict__ f,
                                                   const double2* __restrict__ u, float2* __restrict__ r,
                                                   double* __restrict__ sums, int64_t N,
@@ -241,6 +259,376 @@ __global__ void __launch_bounds__(256) k_residual2d(ResidArgs a, const double2* 
   }
 }
 
+// 3D residual through the tensor structure of eq. A3D:
+//   A = (Kx - w^2 Mx) (x) My (x) Mz + Mx (x) (Ky (x) Mz + My (x) Kz).
+// A CTA owns a TY x TZ tile of (y, z) columns and a run of RX3 x-planes.  For
+// each x-plane (one before and one after the run included) it stages the
+// tile plus a one-point halo in shared memory, applies Mz and Kz along z,
+// then My, Ky along y, giving P_M = (My Mz) u and P_K = (Ky Mz + My Kz) u of
+// that plane; the last three planes' (P_M, P_K) stay in registers and the x
+// operators finish A u.  The 1D entries follow eqs. matrixK / matrixM, with
+// the absorbing corner 1/h - i w at both ends of every axis.
+constexpr int TZ3 = 32, TY3 = 8, RX3 = 32;
+
+struct Coef1D {
+  double md, mo;   // M diagonal (2h/6 at an end, 4h/6 inside), off-diagonal h/6
+  double kdr, kdi; // K diagonal (1/h - i w at an end, 2/h inside)
+  double ko;       // K off-diagonal -1/h
+};
+
+__device__ __forceinline__ Coef1D coef1d(const Axis1D& ax, int64_t i, double omega) {
+  const bool end = (i == 0 || i == ax.n - 1);
+  Coef1D c;
+  c.md = (end ? 2.0 : 4.0) * ax.h / 6.0;
+  c.mo = ax.h / 6.0;
+  c.kdr = (end ? 1.0 : 2.0) / ax.h;
+  c.kdi = end ? -omega : 0.0;
+  c.ko = -1.0 / ax.h;
+  return c;
+}
+
+// d * v with d = (dr, di); di is nonzero only at an absorbing end
+__device__ __forceinline__ double2 cmul_rd(double dr, double di, double2 v) {
+  double2 o;
+  o.x = dr * v.x;
+  o.y = dr * v.y;
+  if (di != 0.0) {
+    o.x = fma(-di, v.y, o.x);
+    o.y = fma(di, v.x, o.y);
+  }
+  return o;
+}
+
+__global__ void __launch_bounds__(TZ3* TY3) k_residual3d(ResidArgs a, const double2* __restrict__ f,
+                                                         const double2* __restrict__ u, float2* __restrict__ r,
+                                                         double* __restrict__ sums, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ double2 sU[TY3 + 2][TZ3 + 2];
+  __shared__ double2 sTM[TY3 + 2][TZ3], sTK[TY3 + 2][TZ3];
+  __shared__ double sr[TY3], sf[TY3];
+  const int64_t nx = a.ax[0].n, ny = a.ax[1].n, nz = a.ax[2].n;
+  const int tz = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * TZ3 + tz;
+  const int64_t z0 = (int64_t)blockIdx.x * TZ3, y0 = (int64_t)blockIdx.y * TY3;
+  const int64_t xs = (int64_t)blockIdx.z * RX3, xe = min(xs + RX3, nx);  // outputs [xs, xe)
+  const int64_t gz = z0 + tz, gy = y0 + ty;
+  const bool own = gz < nz && gy < ny;
+  const double w2 = a.omega * a.omega;
+  const Coef1D cy = coef1d(a.ax[1], gy, a.omega);
+  float r2f = 0.f, f2f = 0.f;
+  const double2 zero = make_double2(0, 0);
+  double2 PM[3] = {zero, zero, zero}, PK[3] = {zero, zero, zero};  // planes x-1, x, x+1
+  for (int64_t ip = xs - 1; ip <= xe; ++ip) {
+    // stage plane ip (zero outside the domain)
+    const bool pin = ip >= 0 && ip < nx;
+    for (int e = tid; e < (TY3 + 2) * (TZ3 + 2); e += TZ3 * TY3) {
+      const int yy = e / (TZ3 + 2), zz = e - yy * (TZ3 + 2);
+      const int64_t jy = y0 - 1 + yy, jz = z0 - 1 + zz;
+      double2 v = zero;
+      if (pin && jy >= 0 && jy < ny && jz >= 0 && jz < nz) v = __ldg(&u[(ip * ny + jy) * nz + jz]);
+      sU[yy][zz] = v;
+    }
+    __syncthreads();
+    // Mz and Kz along z for the TY+2 staged rows
+    for (int e = tid; e < (TY3 + 2) * TZ3; e += TZ3 * TY3) {
+      const int yy = e / TZ3, zc = e - yy * TZ3;
+      const Coef1D cz = coef1d(a.ax[2], z0 + zc, a.omega);
+      const double2 c0 = sU[yy][zc + 1];
+      const double2 sn = make_double2(sU[yy][zc].x + sU[yy][zc + 2].x, sU[yy][zc].y + sU[yy][zc + 2].y);
+      sTM[yy][zc] = make_double2(fma(cz.md, c0.x, cz.mo * sn.x), fma(cz.md, c0.y, cz.mo * sn.y));
+      const double2 kc = cmul_rd(cz.kdr, cz.kdi, c0);
+      sTK[yy][zc] = make_double2(fma(cz.ko, sn.x, kc.x), fma(cz.ko, sn.y, kc.y));
+    }
+    __syncthreads();
+    // My and Ky along y: this plane's P_M, P_K at the thread's column
+    {
+      const double2 m0 = sTM[ty + 1][tz], mm = sTM[ty][tz], mp = sTM[ty + 2][tz];
+      const double2 k0 = sTK[ty + 1][tz], km = sTK[ty][tz], kp = sTK[ty + 2][tz];
+      const double2 sm = make_double2(mm.x + mp.x, mm.y + mp.y), sk = make_double2(km.x + kp.x, km.y + kp.y);
+      PM[0] = PM[1];
+      PK[0] = PK[1];
+      PM[1] = PM[2];
+      PK[1] = PK[2];
+      PM[2] = make_double2(fma(cy.md, m0.x, cy.mo * sm.x), fma(cy.md, m0.y, cy.mo * sm.y));
+      const double2 km0 = cmul_rd(cy.kdr, cy.kdi, m0);
+      double2 pk;
+      pk.x = fma(cy.ko, sm.x, km0.x);
+      pk.y = fma(cy.ko, sm.y, km0.y);
+      pk.x = fma(cy.md, k0.x, fma(cy.mo, sk.x, pk.x));
+      pk.y = fma(cy.md, k0.y, fma(cy.mo, sk.y, pk.y));
+      PK[2] = pk;
+    }
+    // along x: output plane ix = ip - 1 once planes ix-1, ix, ix+1 are in
+    const int64_t ix = ip - 1;
+    if (own && ix >= xs && ix < xe) {
+      const Coef1D cx = coef1d(a.ax[0], ix, a.omega);
+      const double2 spm = make_double2(PM[0].x + PM[2].x, PM[0].y + PM[2].y);
+      const double2 spk = make_double2(PK[0].x + PK[2].x, PK[0].y + PK[2].y);
+      // (Kx - w^2 Mx) P_M + Mx P_K
+      double2 au = cmul_rd(cx.kdr - w2 * cx.md, cx.kdi, PM[1]);
+      const double od = cx.ko - w2 * cx.mo;
+      au.x = fma(od, spm.x, au.x);
+      au.y = fma(od, spm.y, au.y);
+      au.x = fma(cx.md, PK[1].x, fma(cx.mo, spk.x, au.x));
+      au.y = fma(cx.md, PK[1].y, fma(cx.mo, spk.y, au.y));
+      const int64_t gi = (ix * ny + gy) * nz + gz;
+      const double2 fv = __ldg(&f[gi]);
+      const float2 rf = make_float2((float)(fv.x - au.x), (float)(fv.y - au.y));
+      r[gi] = rf;
+      const float2 ff = make_float2((float)fv.x, (float)fv.y);
+      r2f = fmaf(rf.x, rf.x, fmaf(rf.y, rf.y, r2f));
+      f2f = fmaf(ff.x, ff.x, fmaf(ff.y, ff.y, f2f));
+    }
+  }
+  double r2 = r2f, f2 = f2f;
+  for (int off = 16; off > 0; off >>= 1) {
+    r2 += __shfl_down_sync(0xffffffffu, r2, off);
+    f2 += __shfl_down_sync(0xffffffffu, f2, off);
+  }
+  if (tz == 0) {
+    sr[ty] = r2;
+    sf[ty] = f2;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a2 = 0, b2 = 0;
+    for (int i = 0; i < TY3; ++i) {
+      a2 += sr[i];
+      b2 += sf[i];
+    }
+    const int64_t bid = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    sums[2 * bid] = a2;
+    sums[2 * bid + 1] = b2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Float-float residual r = f - A u (f and u as float-float complex vectors,
+// float4 per point: re_hi, im_hi, re_lo, im_lo), about 48 significant bits
+// per value, on the FP32 pipes; the products and sums of the stencil are
+// exact up to the dropped lo x lo terms and the rounding of the lo parts.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 ffc_add(float4 a, float4 b) {
+  float4 o;
+  float e;
+  two_sum(a.x, b.x, o.x, e);
+  o.z = e + (a.z + b.z);
+  two_sum(a.y, b.y, o.y, e);
+  o.w = e + (a.w + b.w);
+  return o;
+}
+// acc += c v, c a real float-float constant
+__device__ __forceinline__ void ffc_mac_r(float4& acc, FF2 c, float4 v) {
+  ff_mac(acc.x, acc.z, c.h, c.l, v.x, v.z);
+  ff_mac(acc.y, acc.w, c.h, c.l, v.y, v.w);
+}
+// acc += (cr + i ci) v
+__device__ __forceinline__ void ffc_mac_c(float4& acc, FF2 cr, FF2 ci, float4 v) {
+  ff_mac(acc.x, acc.z, cr.h, cr.l, v.x, v.z);
+  ff_mac(acc.x, acc.z, -ci.h, -ci.l, v.y, v.w);
+  ff_mac(acc.y, acc.w, cr.h, cr.l, v.y, v.w);
+  ff_mac(acc.y, acc.w, ci.h, ci.l, v.x, v.z);
+}
+__device__ __forceinline__ FF2 ff_split(double x) {
+  FF2 c;
+  c.h = (float)x;
+  c.l = (float)(x - (double)c.h);
+  return c;
+}
+// r = f - a, rounded to complex64; the norms' per-thread FP32 sums
+__device__ __forceinline__ float2 ff_resid(float4 fv, float4 au, float& r2f, float& f2f) {
+  float dr, er, di, ei;
+  two_sum(fv.x, -au.x, dr, er);
+  two_sum(fv.y, -au.y, di, ei);
+  const float2 rf = make_float2(dr + (er + (fv.z - au.z)), di + (ei + (fv.w - au.w)));
+  r2f = fmaf(rf.x, rf.x, fmaf(rf.y, rf.y, r2f));
+  f2f = fmaf(fv.x, fv.x, fmaf(fv.y, fv.y, f2f));
+  return rf;
+}
+
+template <int NW>
+__device__ __forceinline__ void block_norm_sums(float r2f, float f2f, double* __restrict__ sums, int64_t bid) {
+  __shared__ double sr[NW], sf[NW];
+  double r2 = r2f, f2 = f2f;
+  for (int off = 16; off > 0; off >>= 1) {
+    r2 += __shfl_down_sync(0xffffffffu, r2, off);
+    f2 += __shfl_down_sync(0xffffffffu, f2, off);
+  }
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if ((tid & 31) == 0) {
+    sr[tid >> 5] = r2;
+    sf[tid >> 5] = f2;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a2 = 0, b2 = 0;
+    for (int i = 0; i < NW; ++i) {
+      a2 += sr[i];
+      b2 += sf[i];
+    }
+    sums[2 * bid] = a2;
+    sums[2 * bid + 1] = b2;
+  }
+}
+
+// 2D: same traversal as k_residual2d (thread per y column, RX2 rows rolling).
+__global__ void __launch_bounds__(256) k_residual2d_ff(ResidFFArgs a, ResidArgs ad, const float4* __restrict__ f,
+                                                       const float4* __restrict__ u, float2* __restrict__ r,
+                                                       double* __restrict__ sums, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t nx = a.n[0], ny = a.n[1];
+  const int64_t iy = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t x0 = (int64_t)blockIdx.y * RX2;
+  float r2f = 0.f, f2f = 0.f;
+  if (iy < ny) {
+    const bool ym = iy > 0, yp = iy < ny - 1;
+    const float4 z4 = make_float4(0, 0, 0, 0);
+    auto ld = [&](int64_t ix, int64_t jy) -> float4 { return (ix >= 0 && ix < nx) ? __ldg(&u[ix * ny + jy]) : z4; };
+    float4 w[3][3];
+    for (int d = 0; d < 2; ++d) {
+      const int64_t ix = x0 - 1 + d;
+      w[d][0] = ym ? ld(ix, iy - 1) : z4;
+      w[d][1] = ld(ix, iy);
+      w[d][2] = yp ? ld(ix, iy + 1) : z4;
+    }
+    const int64_t x1 = min(x0 + RX2, nx);
+    for (int64_t ix = x0; ix < x1; ++ix) {
+      w[2][0] = ym ? ld(ix + 1, iy - 1) : z4;
+      w[2][1] = ld(ix + 1, iy);
+      w[2][2] = yp ? ld(ix + 1, iy + 1) : z4;
+      float4 au = z4;
+      const bool interior = ix > 0 && ix < nx - 1 && iy > 0 && iy < ny - 1;
+      if (interior) {
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy) ffc_mac_r(au, a.cin[dx * 3 + dy], w[dx][dy]);
+      } else {
+        // perimeter: the complex corner entries, formed in FP64 and split
+        for (int dx = -1; dx <= 1; ++dx) {
+          double m0, k0r, k0i;
+          entries(ad.ax[0], ix, dx, ad.omega, m0, k0r, k0i);
+          for (int dy = -1; dy <= 1; ++dy) {
+            double m1, k1r, k1i;
+            entries(ad.ax[1], iy, dy, ad.omega, m1, k1r, k1i);
+            const double cre = k0r * m1 + m0 * k1r - ad.omega * ad.omega * m0 * m1;
+            const double cim = k0i * m1 + m0 * k1i;
+            ffc_mac_c(au, ff_split(cre), ff_split(cim), w[dx + 1][dy + 1]);  // zero outside the domain
+          }
+        }
+      }
+      const float4 fv = __ldg(&f[ix * ny + iy]);
+      r[ix * ny + iy] = ff_resid(fv, au, r2f, f2f);
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy) {
+        w[0][dy] = w[1][dy];
+        w[1][dy] = w[2][dy];
+      }
+    }
+  }
+  block_norm_sums<8>(r2f, f2f, sums, (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// 3D: the separable traversal of k_residual3d in float-float.
+__global__ void __launch_bounds__(TZ3* TY3) k_residual3d_ff(ResidFFArgs a, const float4* __restrict__ f,
+                                                            const float4* __restrict__ u, float2* __restrict__ r,
+                                                            double* __restrict__ sums, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ float4 sU[TY3 + 2][TZ3 + 2];
+  __shared__ float4 sTM[TY3 + 2][TZ3], sTK[TY3 + 2][TZ3];
+  const int64_t nx = a.n[0], ny = a.n[1], nz = a.n[2];
+  const int tz = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * TZ3 + tz;
+  const int64_t z0 = (int64_t)blockIdx.x * TZ3, y0 = (int64_t)blockIdx.y * TY3;
+  const int64_t xs = (int64_t)blockIdx.z * RX3, xe = min(xs + RX3, nx);
+  const int64_t gz = z0 + tz, gy = y0 + ty;
+  const bool own = gz < nz && gy < ny;
+  const float4 z4 = make_float4(0, 0, 0, 0);
+  const AxisFF& AY = a.ax[1];
+  const AxisFF& AZ = a.ax[2];
+  const AxisFF& AX = a.ax[0];
+  const bool yend = gy == 0 || gy == ny - 1;
+  float r2f = 0.f, f2f = 0.f;
+  float4 PM[3] = {z4, z4, z4}, PK[3] = {z4, z4, z4};
+  for (int64_t ip = xs - 1; ip <= xe; ++ip) {
+    const bool pin = ip >= 0 && ip < nx;
+    for (int e = tid; e < (TY3 + 2) * (TZ3 + 2); e += TZ3 * TY3) {
+      const int yy = e / (TZ3 + 2), zz = e - yy * (TZ3 + 2);
+      const int64_t jy = y0 - 1 + yy, jz = z0 - 1 + zz;
+      float4 v = z4;
+      if (pin && jy >= 0 && jy < ny && jz >= 0 && jz < nz) v = __ldg(&u[(ip * ny + jy) * nz + jz]);
+      sU[yy][zz] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < (TY3 + 2) * TZ3; e += TZ3 * TY3) {
+      const int yy = e / TZ3, zc = e - yy * TZ3;
+      const int64_t jz = z0 + zc;
+      const bool zend = jz == 0 || jz == nz - 1;
+      const float4 c0 = sU[yy][zc + 1];
+      const float4 sn = ffc_add(sU[yy][zc], sU[yy][zc + 2]);
+      float4 tm = z4, tk = z4;
+      ffc_mac_r(tm, zend ? AZ.mde : AZ.mdi, c0);
+      ffc_mac_r(tm, AZ.mo, sn);
+      if (zend) ffc_mac_c(tk, AZ.kder, AZ.kdei, c0);
+      else ffc_mac_r(tk, AZ.kdi, c0);
+      ffc_mac_r(tk, AZ.ko, sn);
+      sTM[yy][zc] = tm;
+      sTK[yy][zc] = tk;
+    }
+    __syncthreads();
+    {
+      const float4 m0 = sTM[ty + 1][tz], k0 = sTK[ty + 1][tz];
+      const float4 sm = ffc_add(sTM[ty][tz], sTM[ty + 2][tz]);
+      const float4 sk = ffc_add(sTK[ty][tz], sTK[ty + 2][tz]);
+      PM[0] = PM[1];
+      PK[0] = PK[1];
+      PM[1] = PM[2];
+      PK[1] = PK[2];
+      float4 pm = z4, pk = z4;
+      ffc_mac_r(pm, yend ? AY.mde : AY.mdi, m0);
+      ffc_mac_r(pm, AY.mo, sm);
+      if (yend) ffc_mac_c(pk, AY.kder, AY.kdei, m0);
+      else ffc_mac_r(pk, AY.kdi, m0);
+      ffc_mac_r(pk, AY.ko, sm);
+      ffc_mac_r(pk, yend ? AY.mde : AY.mdi, k0);
+      ffc_mac_r(pk, AY.mo, sk);
+      PM[2] = pm;
+      PK[2] = pk;
+    }
+    const int64_t ix = ip - 1;
+    if (own && ix >= xs && ix < xe) {
+      const bool xend = ix == 0 || ix == nx - 1;
+      const float4 spm = ffc_add(PM[0], PM[2]), spk = ffc_add(PK[0], PK[2]);
+      float4 au = z4;
+      // (Kx - w^2 Mx) P_M + Mx P_K
+      if (xend) ffc_mac_c(au, AX.cde, AX.kdei, PM[1]);
+      else ffc_mac_r(au, AX.cdi, PM[1]);
+      ffc_mac_r(au, AX.co, spm);
+      ffc_mac_r(au, xend ? AX.mde : AX.mdi, PK[1]);
+      ffc_mac_r(au, AX.mo, spk);
+      const int64_t gi = (ix * ny + gy) * nz + gz;
+      r[gi] = ff_resid(__ldg(&f[gi]), au, r2f, f2f);
+    }
+  }
+  block_norm_sums<TZ3 * TY3 / 32>(r2f, f2f, sums,
+                                 ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+}
+
+// f (complex128) -> float-float; u (float-float) -> complex128.
+__global__ void k_split_ff(const double2* __restrict__ f, float4* __restrict__ o, int64_t N) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = f[i];
+    const float hx = (float)v.x, hy = (float)v.y;
+    o[i] = make_float4(hx, hy, (float)(v.x - (double)hx), (float)(v.y - (double)hy));
+  }
+}
+__global__ void k_join_ff(const float4* __restrict__ q, double2* __restrict__ o, int64_t N) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = q[i];
+    o[i] = make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+  }
+}
+
 __global__ void k_residual_finalize(const double* __restrict__ sums, int64_t nblocks, RefineState* st,
                                     int last) {
   if (st->done) return;
@@ -316,10 +704,93 @@ cudaError_t launch_residual(int dim, const int64_t* n, const double* h, double o
     k_residual2d<<<grid, bs, 0, st>>>(a, f, u, r, sums, skip);
     return cudaGetLastError();
   }
+  if (dim == 3) {
+    const dim3 grid((unsigned)((n[2] + TZ3 - 1) / TZ3), (unsigned)((n[1] + TY3 - 1) / TY3),
+                    (unsigned)((n[0] + RX3 - 1) / RX3));
+    *nblocks = (int64_t)grid.x * grid.y * grid.z;
+    k_residual3d<<<grid, dim3(TZ3, TY3), 0, st>>>(a, f, u, r, sums, skip);
+    return cudaGetLastError();
+  }
   const int64_t grid = (N + bs - 1) / bs;
   *nblocks = grid;
   k_residual<<<(unsigned)grid, bs, 0, st>>>(a, f, u, r, sums, N, skip);
   return cudaGetLastError();
+}
+
+static FF2 split_host(double x) {
+  FF2 c;
+  c.h = (float)x;
+  c.l = (float)(x - (double)c.h);
+  return c;
+}
+
+cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, double omega, const float4* f,
+                               const float4* u, float2* r, double* sums, int64_t* nblocks, const int* skip,
+                               cudaStream_t st) {
+  ResidFFArgs a{};
+  ResidArgs ad{};
+  a.omega = ad.omega = omega;
+  ad.dim = dim;
+  const double w2 = omega * omega;
+  for (int k = 0; k < dim; ++k) {
+    a.n[k] = n[k];
+    a.h[k] = h[k];
+    ad.ax[k].n = n[k];
+    ad.ax[k].h = h[k];
+    const double hk = h[k];
+    AxisFF& x = a.ax[k];
+    x.mdi = split_host(4.0 * hk / 6.0);
+    x.mde = split_host(2.0 * hk / 6.0);
+    x.mo = split_host(hk / 6.0);
+    x.kdi = split_host(2.0 / hk);
+    x.kder = split_host(1.0 / hk);
+    x.ko = split_host(-1.0 / hk);
+    x.kdei = split_host(-omega);
+    x.cdi = split_host(2.0 / hk - w2 * (4.0 * hk / 6.0));
+    x.cde = split_host(1.0 / hk - w2 * (2.0 * hk / 6.0));
+    x.co = split_host(-1.0 / hk - w2 * (hk / 6.0));
+  }
+  if (dim == 2) {
+    double m[2][3], kk[2][3];
+    for (int k = 0; k < 2; ++k) {
+      m[k][0] = m[k][2] = h[k] / 6.0;
+      m[k][1] = 4.0 * h[k] / 6.0;
+      kk[k][0] = kk[k][2] = -1.0 / h[k];
+      kk[k][1] = 2.0 / h[k];
+    }
+    for (int d0 = 0; d0 < 3; ++d0)
+      for (int d1 = 0; d1 < 3; ++d1)
+        a.cin[d0 * 3 + d1] = split_host(kk[0][d0] * m[1][d1] + m[0][d0] * kk[1][d1] - w2 * m[0][d0] * m[1][d1]);
+    const int bs = 256;
+    const dim3 grid((unsigned)((n[1] + bs - 1) / bs), (unsigned)((n[0] + RX2 - 1) / RX2));
+    *nblocks = (int64_t)grid.x * grid.y;
+    k_residual2d_ff<<<grid, bs, 0, st>>>(a, ad, f, u, r, sums, skip);
+    return cudaGetLastError();
+  }
+  const dim3 grid((unsigned)((n[2] + TZ3 - 1) / TZ3), (unsigned)((n[1] + TY3 - 1) / TY3),
+                  (unsigned)((n[0] + RX3 - 1) / RX3));
+  *nblocks = (int64_t)grid.x * grid.y * grid.z;
+  k_residual3d_ff<<<grid, dim3(TZ3, TY3), 0, st>>>(a, f, u, r, sums, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_ff(const double2* f, float4* out, int64_t N, cudaStream_t st) {
+  if (N == 0) return cudaSuccess;
+  const int64_t grid = std::min<int64_t>((N + 255) / 256, 152 * 16);
+  k_split_ff<<<(unsigned)grid, 256, 0, st>>>(f, out, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_join_ff(const float4* u, double2* out, int64_t N, cudaStream_t st) {
+  if (N == 0) return cudaSuccess;
+  const int64_t grid = std::min<int64_t>((N + 255) / 256, 152 * 16);
+  k_join_ff<<<(unsigned)grid, 256, 0, st>>>(u, out, N);
+  return cudaGetLastError();
+}
+
+int64_t residual_blocks(int dim, const int64_t* n) {
+  if (dim == 2) return ((n[1] + 255) / 256) * ((n[0] + RX2 - 1) / RX2);
+  return ((n[2] + TZ3 - 1) / TZ3) * ((n[1] + TY3 - 1) / TY3) * ((n[0] + RX3 - 1) / RX3);
 }
 
 cudaError_t launch_residual_finalize(const double* sums, int64_t nblocks, RefineState* state, int last,

@@ -77,6 +77,17 @@ struct RefineState {
 cudaError_t launch_residual(int dim, const int64_t* n, const double* h, double omega, const double2* f,
                             const double2* u, float2* r, double* sums, int64_t* nblocks, const int* skip,
                             cudaStream_t st);
+// The same residual with f and u as float-float complex vectors (float4 per
+// point: re_hi, im_hi, re_lo, im_lo), about 48 significant bits, computed on
+// the FP32 pipes.  Same grid and sums layout as launch_residual.
+cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, double omega, const float4* f,
+                               const float4* u, float2* r, double* sums, int64_t* nblocks, const int* skip,
+                               cudaStream_t st);
+// complex128 -> float-float (hi = round(x), lo = round(x - hi)) and back.
+cudaError_t launch_split_ff(const double2* f, float4* out, int64_t N, cudaStream_t st);
+cudaError_t launch_join_ff(const float4* u, double2* out, int64_t N, cudaStream_t st);
+// Number of per-block sums launch_residual writes for this grid.
+int64_t residual_blocks(int dim, const int64_t* n);
 // Reduce the block sums, record ||r||/||f|| as the next residual of *state,
 // set state->done when it is <= tol or when `last` is set.
 cudaError_t launch_residual_finalize(const double* sums, int64_t nblocks, RefineState* state, int last,

@@ -240,67 +240,110 @@ __global__ void __launch_bounds__(128) k_tri_pass1(const typename cpx<T>::type* 
 // thread composes the maps of its segment, the segment maps are folded in
 // shared memory to give each segment its incoming carry, and each thread then
 // runs its segment's recurrence from that carry.  Same recurrences as the
-// sequential scan, regrouped once; FP64 arithmetic for both precisions.
+// sequential scan, regrouped once, in the precision of the records.
 constexpr int kCarryLines = 16;
-constexpr int kCarrySeg = 16;
+constexpr int kCarrySeg = 32;
+constexpr int kCarryBatch = 8;  // chunk records loaded ahead of each recurrence
 
 template <typename T>
 __global__ void __launch_bounds__(kCarryLines* kCarrySeg)
     k_tri_carry(RecSoA<typename cpx<T>::type> rec, int64_t n1, int64_t K, const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
+  constexpr int B = kCarryBatch;
   if (skip && *skip) return;  // uniform over the grid
-  __shared__ double2 shC[kCarrySeg][kCarryLines], shP[kCarrySeg][kCarryLines];
+  __shared__ C shC[kCarrySeg][kCarryLines], shP[kCarrySeg][kCarryLines];
   const int lx = threadIdx.x, sg = threadIdx.y;
   const int64_t l = (int64_t)blockIdx.x * kCarryLines + lx;
   const bool act = l < n1;
   const int64_t S = (K + kCarrySeg - 1) / kCarrySeg;
   const int64_t k0 = min(K, sg * S), k1 = min(K, k0 + S);
-  const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
+  const C one = mk<C>(1, 0), zero = mk<C>(0, 0);
   // forward: compose the segment's maps
-  double2 A = zero, P = one;
+  C A = zero, P = one;
   if (act)
-    for (int64_t k = k0; k < k1; ++k) {
-      const int64_t i = k * n1 + l;
-      const double2 pk = cvt<double2>(rec.pe[i]);
-      A = cadd(cvt<double2>(rec.a[i]), cmul(pk, A));
-      P = cmul(pk, P);
+    for (int64_t kb = k0; kb < k1; kb += B) {
+      C av[B], pv[B];
+#pragma unroll
+      for (int t = 0; t < B; ++t)
+        if (kb + t < k1) {
+          av[t] = rec.a[(kb + t) * n1 + l];
+          pv[t] = rec.pe[(kb + t) * n1 + l];
+        }
+#pragma unroll
+      for (int t = 0; t < B; ++t)
+        if (kb + t < k1) {
+          const C pk = pv[t];
+          A = cadd(av[t], cmul(pk, A));
+          P = cmul(pk, P);
+        }
     }
   shC[sg][lx] = A;
   shP[sg][lx] = P;
   __syncthreads();
-  double2 Y = zero;
+  C Y = zero;
   for (int g = 0; g < sg; ++g) Y = cadd(shC[g][lx], cmul(shP[g][lx], Y));
   // forward recurrence; c_k replaces bsum_k
   if (act)
-    for (int64_t k = k0; k < k1; ++k) {
-      const int64_t i = k * n1 + l;
-      const double2 ak = cvt<double2>(rec.a[i]), pk = cvt<double2>(rec.pe[i]);
-      const double2 bk = cvt<double2>(rec.bsum[i]), ck = cvt<double2>(rec.cc[i]);
-      rec.a[i] = cvt<C>(Y);  // Y(k-1)
-      rec.bsum[i] = cvt<C>(cadd(bk, cmul(ck, Y)));
-      Y = cadd(ak, cmul(pk, Y));
+    for (int64_t kb = k0; kb < k1; kb += B) {
+      C av[B], pv[B], bv[B], cv[B];
+#pragma unroll
+      for (int t = 0; t < B; ++t)
+        if (kb + t < k1) {
+          const int64_t i = (kb + t) * n1 + l;
+          av[t] = rec.a[i];
+          pv[t] = rec.pe[i];
+          bv[t] = rec.bsum[i];
+          cv[t] = rec.cc[i];
+        }
+#pragma unroll
+      for (int t = 0; t < B; ++t)
+        if (kb + t < k1) {
+          const int64_t i = (kb + t) * n1 + l;
+          rec.a[i] = Y;  // Y(k-1)
+          rec.bsum[i] = cadd(bv[t], cmul(cv[t], Y));
+          Y = cadd(av[t], cmul(pv[t], Y));
+        }
     }
   __syncthreads();
   // backward: compose the segment's maps, last chunk first
-  double2 Cs = zero, Q = one;
+  C Cs = zero, Q = one;
   if (act)
-    for (int64_t k = k1 - 1; k >= k0; --k) {
-      const int64_t i = k * n1 + l;
-      const double2 qk = cvt<double2>(rec.we[i]);
-      Cs = cadd(cvt<double2>(rec.bsum[i]), cmul(qk, Cs));
-      Q = cmul(qk, Q);
+    for (int64_t kb = k1 - 1; kb >= k0; kb -= B) {
+      C cv[B], qv[B];
+#pragma unroll
+      for (int t = 0; t < B; ++t)
+        if (kb - t >= k0) {
+          cv[t] = rec.bsum[(kb - t) * n1 + l];
+          qv[t] = rec.we[(kb - t) * n1 + l];
+        }
+#pragma unroll
+      for (int t = 0; t < B; ++t)
+        if (kb - t >= k0) {
+          const C qk = qv[t];
+          Cs = cadd(cv[t], cmul(qk, Cs));
+          Q = cmul(qk, Q);
+        }
     }
   shC[sg][lx] = Cs;
   shP[sg][lx] = Q;
   __syncthreads();
-  double2 X = zero;
+  C X = zero;
   for (int g = kCarrySeg - 1; g > sg; --g) X = cadd(shC[g][lx], cmul(shP[g][lx], X));
   if (act)
-    for (int64_t k = k1 - 1; k >= k0; --k) {
-      const int64_t i = k * n1 + l;
-      const double2 ck = cvt<double2>(rec.bsum[i]), qk = cvt<double2>(rec.we[i]);
-      rec.bsum[i] = cvt<C>(X);  // X(k+1)
-      X = cadd(ck, cmul(qk, X));
+    for (int64_t kb = k1 - 1; kb >= k0; kb -= B) {
+      C cv[B], qv[B];
+#pragma unroll
+      for (int t = 0; t < B; ++t)
+        if (kb - t >= k0) {
+          cv[t] = rec.bsum[(kb - t) * n1 + l];
+          qv[t] = rec.we[(kb - t) * n1 + l];
+        }
+#pragma unroll
+      for (int t = 0; t < B; ++t)
+        if (kb - t >= k0) {
+          rec.bsum[(kb - t) * n1 + l] = X;  // X(k+1)
+          X = cadd(cv[t], cmul(qv[t], X));
+        }
     }
 }
 

@@ -50,6 +50,7 @@ def test_null_plan_and_destroy_null(helm):
     assert helm.lib.helm_destroy(None) == helm.HELM_OK
     assert helm.lib.helm_solve(None, None, None) == helm.HELM_EINVAL
     assert helm.lib.helm_set_refinement(None, 1e-12, 3) == helm.HELM_EINVAL
+    assert helm.lib.helm_set_residual(None, helm.HELM_RESID_FF) == helm.HELM_EINVAL
 
 
 @pytest.mark.parametrize("n", [4, 9, 64, 129, 512, 1000, 1021, 4096, 8192, 6 * 49])

@@ -59,14 +59,19 @@ def _oracle(shape, h, omega, seed):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("dtype", ["c128", "c64_refined", "c64_raw"])
+@pytest.mark.parametrize("dtype", ["c128", "c64_refined", "c64_ff", "c64_raw"])
 @pytest.mark.parametrize("aux", ["damped", "periodic"])
 def test_solve_matches_oracle(env, name, dtype, aux):
     helm, torch = env
     shape, h, omega = CASES[name]
     f, u_ref = _oracle(shape, h, omega, seed=sum(map(ord, name)) % 1000)
-    code = {"c128": helm.HELM_C128, "c64_refined": helm.HELM_C64_REFINED, "c64_raw": helm.HELM_C64_RAW}[dtype]
+    code = {"c128": helm.HELM_C128, "c64_refined": helm.HELM_C64_REFINED, "c64_ff": helm.HELM_C64_REFINED,
+            "c64_raw": helm.HELM_C64_RAW}[dtype]
     plan = helm.Plan(shape, h, omega, code)
+    if dtype == "c64_ff":
+        # float-float residual: floor near 1e-13 relative, so a tolerance above it
+        helm.helm_set_residual(plan.handle, helm.HELM_RESID_FF)
+        helm.helm_set_refinement(plan.handle, 1e-12, 15)
     if aux == "periodic":
         helm.helm_set_auxiliary(plan.handle, 0.0, 0)
     tdt = torch.complex64 if dtype == "c64_raw" else torch.complex128
@@ -84,7 +89,7 @@ def test_solve_matches_oracle(env, name, dtype, aux):
         assert err < 5e-2
     else:
         assert err <= TOL
-        if dtype == "c64_refined":
+        if dtype in ("c64_refined", "c64_ff"):
             assert st == helm.HELM_OK and info.converged == 1
 
 
@@ -154,3 +159,42 @@ def test_unsupported_and_invalid(env):
     with pytest.raises(helm.HelmError):
         helm.helm_solve(plan.handle, x, x)  # aliasing f and u is rejected
     plan.close()
+
+
+def test_set_residual_validation(env):
+    helm, torch = env
+    shape, h, omega = CASES["tiny_9x7"]
+    plan = helm.Plan(shape, h, omega, helm.HELM_C128)
+    assert helm.lib.helm_set_residual(plan.handle, helm.HELM_RESID_FF) == helm.HELM_EINVAL  # not refined
+    plan.close()
+    plan = helm.Plan(shape, h, omega, helm.HELM_C64_REFINED)
+    assert helm.lib.helm_set_residual(plan.handle, 7) == helm.HELM_EINVAL
+    assert helm.lib.helm_set_residual(plan.handle, helm.HELM_RESID_FF) == helm.HELM_OK
+    info, st = plan.info()
+    assert info.residual_kind == helm.HELM_RESID_FF
+    plan.close()
+
+
+def test_ff_and_fp64_residuals_agree(env):
+    """Both refinement residuals converge to the same solution.  The first
+    residual is of the same u0 (the FP32 solve of f) in both and agrees to
+    FP32 rounding; later iterates differ by FP32-solve rounding of slightly
+    different residuals, so only the converged solutions are compared."""
+    helm, torch = env
+    shape, h, omega = CASES["c1_129x129_16pi"]
+    f = torch.from_numpy(random_rhs(shape, 5)).cuda()
+    out = {}
+    for kind in (helm.HELM_RESID_FP64, helm.HELM_RESID_FF):
+        plan = helm.Plan(shape, h, omega, helm.HELM_C64_REFINED)
+        helm.helm_set_residual(plan.handle, kind)
+        helm.helm_set_refinement(plan.handle, 1e-12, 15)
+        u = plan.solve(f)
+        info, st = plan.info()
+        assert st == helm.HELM_OK and info.converged == 1
+        out[kind] = (u.cpu().numpy(), list(info.residual[:info.iterations + 1]))
+        plan.close()
+    (u64, r64), (uff, rff) = out[helm.HELM_RESID_FP64], out[helm.HELM_RESID_FF]
+    print("fp64", r64, "ff", rff)
+    assert abs(r64[0] - rff[0]) <= 1e-5 * r64[0]
+    assert abs(len(r64) - len(rff)) <= 1
+    assert np.linalg.norm(u64 - uff) / np.linalg.norm(u64) < 1e-10

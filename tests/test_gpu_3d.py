@@ -45,7 +45,7 @@ CASES = {
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("dtype", ["c128", "c64_refined", "c64_raw"])
+@pytest.mark.parametrize("dtype", ["c128", "c64_refined", "c64_ff", "c64_raw"])
 @pytest.mark.parametrize("aux", ["damped", "periodic"])
 def test_solve3d_matches_oracle(env, name, dtype, aux):
     helm, torch = env
@@ -53,8 +53,12 @@ def test_solve3d_matches_oracle(env, name, dtype, aux):
     f = random_rhs(shape, 31 + len(name))
     u_ref, hist = solvers.oracle_solve(f, h, omega, method="banded")
     assert hist[-1] < 1e-13
-    code = {"c128": helm.HELM_C128, "c64_refined": helm.HELM_C64_REFINED, "c64_raw": helm.HELM_C64_RAW}[dtype]
+    code = {"c128": helm.HELM_C128, "c64_refined": helm.HELM_C64_REFINED, "c64_ff": helm.HELM_C64_REFINED,
+            "c64_raw": helm.HELM_C64_RAW}[dtype]
     plan = helm.Plan(shape, h, omega, code)
+    if dtype == "c64_ff":
+        helm.helm_set_residual(plan.handle, helm.HELM_RESID_FF)
+        helm.helm_set_refinement(plan.handle, 1e-12, 15)
     if aux == "periodic":
         helm.helm_set_auxiliary(plan.handle, 0.0, 0)
     tdt = torch.complex64 if dtype == "c64_raw" else torch.complex128
@@ -69,6 +73,8 @@ def test_solve3d_matches_oracle(env, name, dtype, aux):
         assert err < 5e-2
     else:
         assert err <= TOL
+        if dtype in ("c64_refined", "c64_ff"):
+            assert st == helm.HELM_OK and info.converged == 1
 
 
 @pytest.mark.parametrize("name", ["tiny_5x6x7", "aniso_12x17x10"])

@@ -42,7 +42,7 @@ CONFIGS = {"2d_large": workloads.config_2d_large, "3d": workloads.config_3d}
 
 
 @pytest.mark.parametrize("name", ["2d_large", "3d"])
-@pytest.mark.parametrize("dtype", ["c128", "c64_refined"])
+@pytest.mark.parametrize("dtype", ["c128", "c64_refined", "c64_ff"])
 def test_fullsize_sampled_parity(env, name, dtype):
     helm, torch = env
     path = os.path.join(HERE, "golden", f"{name}_samples.json")
@@ -55,6 +55,9 @@ def test_fullsize_sampled_parity(env, name, dtype):
     fd = torch.from_numpy(f).cuda()
     code = helm.HELM_C128 if dtype == "c128" else helm.HELM_C64_REFINED
     plan = helm.Plan(p.shape, p.h, p.omega, code)
+    if dtype == "c64_ff":
+        helm.helm_set_residual(plan.handle, helm.HELM_RESID_FF)
+        helm.helm_set_refinement(plan.handle, 1e-12, 15)
     u = plan.solve(fd)
     info, st = plan.info()
     plan.close()
