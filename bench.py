@@ -266,7 +266,7 @@ def run_gb300(args):
         plan = helm.Plan(p.shape, p.h, p.omega, code)
         if kind is not None:
             helm.helm_set_residual(plan.handle, kind)
-            helm.helm_set_refinement(plan.handle, REFINE_TOL, 15)
+            helm.helm_set_refinement(plan.handle, REFINE_TOL, 10)
         return plan
 
     # --- the timed path (the headline) ---

@@ -41,8 +41,8 @@ struct helm_plan {
   void* ustartB = nullptr;  // 2D: pivot entering each chunk, B-type lines
   void* ustartA = nullptr;  // 2D: same for A-type lines
   void* rec = nullptr;      // 2D: chunk records
-  void* tabB = nullptr;     // 2D FP64: per-plan line tables, B-type lines (Steps 1, 3)
-  void* tabA = nullptr;     // 2D FP64: same, A-type lines (Step 2)
+  void* tabB = nullptr;     // 2D: per-plan line tables, B-type lines (Steps 1, 3)
+  void* tabA = nullptr;     // 2D: same, A-type lines (Step 2)
   void* constB = nullptr;   // 2D: per-line constants, B-type lines
   void* constA = nullptr;   // 2D: per-line constants, A-type lines
   int64_t face_len = 0;   // values per face
@@ -286,8 +286,11 @@ int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int 
                                      nullptr, skip, st));
   if (dbg_fhat) HELM_CK(cudaMemcpyAsync(dbg_fhat, p->fhat, nx * n1 * cb, cudaMemcpyDeviceToDevice, st));
   // a2: Step 1
-  if (p->tabB)
+  if (p->tabB && prec == kPrecF64)
     HELM_CK(launch_tri2d_tab(1, p->fhat, nullptr, p->tabB, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr));
+  else if (p->tabB)
+    HELM_CK(launch_tri2d_t32(1, p->fhat, nullptr, p->tabB, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr,
+                             p->constB));
   else
     HELM_CK(launch_tri2d(prec, 1, p->fhat, nullptr, p->ustartB, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr, p->constB));
   HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fv, nx, nparts, inv_n1, en_n1, skip, st));
@@ -295,8 +298,11 @@ int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int 
   // a3: Step 2
   HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, nullptr, fc, nx, p->h[0], p->h[1], p->omega, p->omega * p->omega, ax.g,
                                         ax.ginv, skip, st));
-  if (p->tabA)
+  if (p->tabA && prec == kPrecF64)
     HELM_CK(launch_tri2d_tab(2, nullptr, fc, p->tabA, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr));
+  else if (p->tabA)
+    HELM_CK(launch_tri2d_t32(2, nullptr, fc, p->tabA, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr,
+                             p->constA));
   else
     HELM_CK(launch_tri2d(prec, 2, nullptr, fc, p->ustartA, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr, p->constA));
   HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fw, nx, nparts, one, one, skip, st));
@@ -304,8 +310,11 @@ int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int 
   // a4: Step 3
   HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, fw, fc, nx, p->h[0], p->h[1], p->omega, p->omega * p->omega, ax.g,
                                         ax.ginv, skip, st));
-  if (p->tabB)
+  if (p->tabB && prec == kPrecF64)
     HELM_CK(launch_tri2d_tab(3, p->fhat, fc, p->tabB, p->rec, p->dbuf, nullptr, a, skip, st, p->prof.on ? &p->prof : nullptr));
+  else if (p->tabB)
+    HELM_CK(launch_tri2d_t32(3, p->fhat, fc, p->tabB, p->rec, p->dbuf, nullptr, a, skip, st, p->prof.on ? &p->prof : nullptr,
+                             p->constB));
   else
     HELM_CK(launch_tri2d(prec, 3, p->fhat, fc, p->ustartB, p->rec, p->dbuf, nullptr, a, skip, st, p->prof.on ? &p->prof : nullptr, p->constB));
   // a5: inverse DFT along x1 (eq. step3IFFTz3coeff)
@@ -394,14 +403,17 @@ int alloc_buffers_2d(helm_plan* p) {
   HELM_CK(launch_line_consts(p->prec, p->constA, a, 2, nullptr));
   HELM_CK(launch_pivots(p->prec, p->ustartB, a, 1, nullptr));
   HELM_CK(launch_pivots(p->prec, p->ustartA, a, 2, nullptr));
-  // FP64: the rhs-independent parts of every line's LU, once per plan.  If the
-  // device cannot hold them (6 complex128 values per unknown) the solve
-  // recomputes them on the fly instead.
-  if (p->prec == kPrecF64) {
-    const size_t tb = line_tables_bytes(nx, n1, a.nchunks);
+  // The rhs-independent parts of every line's LU, once per plan: FP64 keeps
+  // multipliers, reciprocal pivots and chunk weights (3 complex128 values per
+  // unknown and line type), complex64 the rounded reciprocal pivots alone (1
+  // complex64 value).  If the device cannot hold them the solve recomputes
+  // them on the fly instead.
+  {
+    const bool f64 = p->prec == kPrecF64;
+    const size_t tb = f64 ? line_tables_bytes(nx, n1, a.nchunks) : line_tables32_bytes(nx, n1, a.nchunks);
     if (dev_alloc(p, &p->tabB, tb) == HELM_OK && dev_alloc(p, &p->tabA, tb) == HELM_OK) {
-      HELM_CK(launch_line_tables(p->tabB, a, 1, nullptr));
-      HELM_CK(launch_line_tables(p->tabA, a, 2, nullptr));
+      HELM_CK(f64 ? launch_line_tables(p->tabB, a, 1, nullptr) : launch_line_tables32(p->tabB, a, 1, nullptr));
+      HELM_CK(f64 ? launch_line_tables(p->tabA, a, 2, nullptr) : launch_line_tables32(p->tabA, a, 2, nullptr));
     } else {
       cudaFree(p->tabB);
       cudaFree(p->tabA);
@@ -642,7 +654,9 @@ int helm_set_auxiliary(helm_plan_t p, double rho, int phase_quarters) {
     const Solve2DArgs a = args2d(p);
     HELM_CK(launch_pivots(p->prec, p->ustartB, a, 1, nullptr));
     if (p->constB) HELM_CK(launch_line_consts(p->prec, p->constB, a, 1, nullptr));
-    if (p->tabB) HELM_CK(launch_line_tables(p->tabB, a, 1, nullptr));
+    if (p->tabB)
+      HELM_CK(p->prec == kPrecF64 ? launch_line_tables(p->tabB, a, 1, nullptr)
+                                  : launch_line_tables32(p->tabB, a, 1, nullptr));
     HELM_CK(cudaDeviceSynchronize());
   }
   return HELM_OK;

@@ -311,6 +311,9 @@ cudaError_t launch_dft_cols(int prec, const void* in, int in_is_double, void* ou
                             int64_t outer, int64_t inner, const DftPlan& p, const void* tw, int sign,
                             double scale, double accum_scale, const void* sc_in, const void* sc_out,
                             const int* skip, cudaStream_t st) {
+  if (dft_cols_pow2_supported(p.n))
+    return launch_dft_cols_pow2(prec, in, in_is_double, out, out_mode, outer, inner, p.n, tw, sign, scale,
+                                accum_scale, sc_in, sc_out, skip, st);
   const size_t es = prec == kPrecF64 ? sizeof(double2) : sizeof(float2);
   int TC = 16;
   while (TC > 1 && (size_t)2 * TC * p.n * es > 200 * 1024) TC /= 2;

@@ -39,6 +39,13 @@ cudaError_t launch_dft_rows_pow2(int prec, const void* in, int in_is_double, voi
                                  int64_t n, const void* tw, int sign, double scale, double accum_scale,
                                  const void* sc_in, const void* sc_out, const int* skip, cudaStream_t st);
 
+// Power-of-two lines (16 <= n <= 1024) along a middle axis: the contract of
+// launch_dft_cols with compile-time radices; in place (out == in) allowed.
+bool dft_cols_pow2_supported(int64_t n);
+cudaError_t launch_dft_cols_pow2(int prec, const void* in, int in_is_double, void* out, int out_mode, int64_t outer,
+                                 int64_t inner, int64_t n, const void* tw, int sign, double scale, double accum_scale,
+                                 const void* sc_in, const void* sc_out, const int* skip, cudaStream_t st);
+
 // Lines along a middle axis: the array viewed as [outer][p.n][inner].
 cudaError_t launch_dft_cols(int prec, const void* in, int in_is_double, void* out, int out_mode,
                             int64_t outer, int64_t inner, const DftPlan& p, const void* tw, int sign,

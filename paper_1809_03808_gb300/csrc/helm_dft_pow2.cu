@@ -147,15 +147,34 @@ __device__ __forceinline__ int out_index(int t, int q, int rp) {
   return (j - k) * R + k + rp * NS;
 }
 
-// Twiddles and R-point DFTs of one pass on the thread's 16 registers.
+// Twiddles and R-point DFTs of one pass on the thread's 16 registers.  The
+// input r of a butterfly is multiplied by w^r, w = e^{SIGN 2 pi i k / (NS R)}.
+// FP64 reads every w^r from the table (FP64 multiplies are the scarce
+// resource); FP32 reads w once and forms w^2 .. w^(R-1) by binary powering
+// (at most four dependent products, a few ulps).
 template <typename C, int N, int R, int NS, int SIGN>
 __device__ __forceinline__ void pass_compute(C* v, int t, const C* __restrict__ tw) {
+  using T = decltype(C().x);
 #pragma unroll
   for (int q = 0; q < 16 / R; ++q) {
     if constexpr (NS > 1) {
       const int k = (t + q * (N / 16)) & (NS - 1);
+      constexpr int S = N / (NS * R);
+      if constexpr (sizeof(T) == 8) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], twid<C, SIGN>(tw, r * k * (N / (NS * R))));
+        for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], twid<C, SIGN>(tw, r * k * S));
+      } else {
+        C w[R];
+        w[1] = twid<C, SIGN>(tw, k * S);
+#pragma unroll
+        for (int r = 2; r < R; ++r) {
+          // r = hb + rest with hb the highest power of two <= r
+          const int hb = (r >= 8) ? 8 : (r >= 4) ? 4 : 2;
+          w[r] = (r == hb) ? cmul(w[hb / 2], w[hb / 2]) : cmul(w[hb], w[r - hb]);
+        }
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], w[r]);
+      }
     }
     dft_r<C, R, SIGN>(v + q * R);
   }
@@ -286,6 +305,154 @@ __global__ void __launch_bounds__(pow2_threads<LOG2N>())
   }
 }
 
+// Column variant: lines along a middle axis of an array viewed as
+// [outer][N][inner].  A CTA takes TC consecutive inner indices (columns) of
+// one outer slab; thread (t, c) = (threadIdx.x / TC, threadIdx.x % TC) owns
+// 16 points of column c, so the lanes of a warp touch TC consecutive columns
+// of the same line point (contiguous in global and in shared memory, where
+// point i of column c sits at i * TC + c).
+// Columns per CTA: TC * N / 16 threads, at most 512 (complex64) or 256
+// (complex128, whose CTAs also need twice the shared memory per column).
+template <typename T, int LOG2N>
+__host__ __device__ constexpr int cols_tc() {
+  return sizeof(T) == 4 ? ((8192 >> LOG2N) > 64 ? 64 : (8192 >> LOG2N))
+                        : ((4096 >> LOG2N) > 32 ? 32 : ((4096 >> LOG2N) < 1 ? 1 : (4096 >> LOG2N)));
+}
+
+template <typename T, int N, int SIGN, int NS, int LEFT, int TC>
+__device__ __forceinline__ void later_passes_cols(typename cpx<T>::type* v, typename cpx<T>::type* buf, int t, int c,
+                                                  bool act, int64_t g0, int64_t inner, void* __restrict__ out,
+                                                  int out_mode, const typename cpx<T>::type* __restrict__ tw, T scale,
+                                                  double accum_scale,
+                                                  const typename cpx<T>::type* __restrict__ sc_out) {
+  using C = typename cpx<T>::type;
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = buf[in_index<N, 16>(t, 0, r) * TC + c];
+  pass_compute<C, N, 16, NS, SIGN>(v, t, tw);
+  if constexpr (LEFT == 1) {
+    if (act) {
+#pragma unroll
+      for (int rp = 0; rp < 16; ++rp) {
+        const int o = out_index<N, 16, NS>(t, 0, rp);
+        C x = cscale(v[rp], scale);
+        if (sc_out) x = cmul(x, __ldg(&sc_out[o]));
+        store_pt<C>(out, out_mode, g0 + (int64_t)o * inner, x, accum_scale);
+      }
+    }
+  } else {
+    __syncthreads();
+#pragma unroll
+    for (int rp = 0; rp < 16; ++rp) buf[out_index<N, 16, NS>(t, 0, rp) * TC + c] = v[rp];
+    later_passes_cols<T, N, SIGN, NS * 16, LEFT - 1, TC>(v, buf, t, c, act, g0, inner, out, out_mode, tw, scale,
+                                                         accum_scale, sc_out);
+  }
+}
+
+template <typename T, int LOG2N, int SIGN>
+__global__ void __launch_bounds__(cols_tc<T, LOG2N>() * (1 << LOG2N) / 16)
+    k_dft_cols_pow2(const void* __restrict__ in, int in_is_double, void* __restrict__ out, int out_mode,
+                    int64_t outer, int64_t inner, const typename cpx<T>::type* __restrict__ tw, T scale,
+                    double accum_scale, const typename cpx<T>::type* __restrict__ sc_in,
+                    const typename cpx<T>::type* __restrict__ sc_out, const int* __restrict__ skip) {
+  using C = typename cpx<T>::type;
+  constexpr int N = 1 << LOG2N;
+  constexpr int TC = cols_tc<T, LOG2N>();
+  constexpr int E = LOG2N % 4;
+  constexpr int R0 = E ? (1 << E) : 16;
+  constexpr int NP = (LOG2N + 3) / 4;
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int c = threadIdx.x % TC;
+  const int t = threadIdx.x / TC;
+  const int64_t tiles = (inner + TC - 1) / TC;
+  const int64_t slab = blockIdx.x / tiles;
+  const int64_t col = (blockIdx.x - slab * tiles) * TC + c;
+  const bool act = col < inner;
+  const int64_t g0 = slab * (int64_t)N * inner + col;  // point i at g0 + i * inner
+  C v[16];
+#pragma unroll
+  for (int q = 0; q < 16 / R0; ++q)
+#pragma unroll
+    for (int r = 0; r < R0; ++r) {
+      const int i = in_index<N, R0>(t, q, r);
+      C x = mk<C>(0, 0);
+      if (act) {
+        x = load_pt<T>(in, in_is_double, g0 + (int64_t)i * inner);
+        if (sc_in) x = cmul(x, __ldg(&sc_in[i]));
+      }
+      v[q * R0 + r] = x;
+    }
+  pass_compute<C, N, R0, 1, SIGN>(v, t, tw);
+  if constexpr (NP == 1) {
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < 16 / R0; ++q)
+#pragma unroll
+        for (int rp = 0; rp < R0; ++rp) {
+          const int o = out_index<N, R0, 1>(t, q, rp);
+          C x = cscale(v[q * R0 + rp], scale);
+          if (sc_out) x = cmul(x, __ldg(&sc_out[o]));
+          store_pt<C>(out, out_mode, g0 + (int64_t)o * inner, x, accum_scale);
+        }
+    }
+  } else {
+    // in place (out == in) is safe: every input of the CTA is read before
+    // the first output is written
+#pragma unroll
+    for (int q = 0; q < 16 / R0; ++q)
+#pragma unroll
+      for (int rp = 0; rp < R0; ++rp) buf[out_index<N, R0, 1>(t, q, rp) * TC + c] = v[q * R0 + rp];
+    later_passes_cols<T, N, SIGN, R0, NP - 1, TC>(v, buf, t, c, act, g0, inner, out, out_mode, tw, scale,
+                                                  accum_scale, sc_out);
+  }
+}
+
+template <typename T, int LOG2N, int SIGN>
+cudaError_t launch_cols_pow2_t(const void* in, int in_is_double, void* out, int out_mode, int64_t outer,
+                               int64_t inner, const void* tw, double scale, double accum_scale, const void* sc_in,
+                               const void* sc_out, const int* skip, cudaStream_t st) {
+  using C = typename cpx<T>::type;
+  constexpr int N = 1 << LOG2N;
+  constexpr int TC = cols_tc<T, LOG2N>();
+  constexpr int threads = TC * N / 16;
+  constexpr int NP = (LOG2N + 3) / 4;
+  const size_t smem = NP > 1 ? (size_t)TC * N * sizeof(C) : 0;
+  const int64_t grid = outer * ((inner + TC - 1) / TC);
+  if (grid == 0) return cudaSuccess;
+  auto k = k_dft_cols_pow2<T, LOG2N, SIGN>;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<(unsigned)grid, threads, smem, st>>>(in, in_is_double, out, out_mode, outer, inner, (const C*)tw, (T)scale,
+                                           accum_scale, (const C*)sc_in, (const C*)sc_out, skip);
+  return cudaGetLastError();
+}
+
+template <typename T, int SIGN>
+cudaError_t launch_cols_pow2_s(int log2n, const void* in, int in_is_double, void* out, int out_mode, int64_t outer,
+                               int64_t inner, const void* tw, double scale, double accum_scale, const void* sc_in,
+                               const void* sc_out, const int* skip, cudaStream_t st) {
+#define HELM_COLS2(LG)                                                                                          \
+  case LG:                                                                                                      \
+    return launch_cols_pow2_t<T, LG, SIGN>(in, in_is_double, out, out_mode, outer, inner, tw, scale, accum_scale, \
+                                           sc_in, sc_out, skip, st);
+  switch (log2n) {
+    HELM_COLS2(4)
+    HELM_COLS2(5)
+    HELM_COLS2(6)
+    HELM_COLS2(7)
+    HELM_COLS2(8)
+    HELM_COLS2(9)
+    HELM_COLS2(10)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef HELM_COLS2
+}
+
 template <typename T, int LOG2N, int SIGN>
 cudaError_t launch_pow2_t(const void* in, int in_is_double, void* out, int out_mode, int64_t nrows,
                           const void* tw, double scale, double accum_scale, const void* sc_in, const void* sc_out,
@@ -336,6 +503,25 @@ cudaError_t launch_pow2_s(int log2n, const void* in, int in_is_double, void* out
 }  // namespace
 
 bool dft_rows_pow2_supported(int64_t n) { return n >= 16 && n <= 8192 && (n & (n - 1)) == 0; }
+bool dft_cols_pow2_supported(int64_t n) { return n >= 16 && n <= 1024 && (n & (n - 1)) == 0; }
+
+cudaError_t launch_dft_cols_pow2(int prec, const void* in, int in_is_double, void* out, int out_mode, int64_t outer,
+                                 int64_t inner, int64_t n, const void* tw, int sign, double scale, double accum_scale,
+                                 const void* sc_in, const void* sc_out, const int* skip, cudaStream_t st) {
+  if (!dft_cols_pow2_supported(n)) return cudaErrorInvalidValue;
+  int log2n = 0;
+  while ((int64_t(1) << log2n) < n) ++log2n;
+  if (prec == kPrecF64) {
+    return sign < 0 ? launch_cols_pow2_s<double, -1>(log2n, in, in_is_double, out, out_mode, outer, inner, tw, scale,
+                                                      accum_scale, sc_in, sc_out, skip, st)
+                    : launch_cols_pow2_s<double, 1>(log2n, in, in_is_double, out, out_mode, outer, inner, tw, scale,
+                                                     accum_scale, sc_in, sc_out, skip, st);
+  }
+  return sign < 0 ? launch_cols_pow2_s<float, -1>(log2n, in, in_is_double, out, out_mode, outer, inner, tw, scale,
+                                                 accum_scale, sc_in, sc_out, skip, st)
+                  : launch_cols_pow2_s<float, 1>(log2n, in, in_is_double, out, out_mode, outer, inner, tw, scale,
+                                                accum_scale, sc_in, sc_out, skip, st);
+}
 
 cudaError_t launch_dft_rows_pow2(int prec, const void* in, int in_is_double, void* out, int out_mode, int64_t nrows,
                                  int64_t n, const void* tw, int sign, double scale, double accum_scale,

@@ -472,7 +472,7 @@ __device__ __forceinline__ void block_norm_sums(float r2f, float f2f, double* __
 }
 
 // 2D: same traversal as k_residual2d (thread per y column, RX2 rows rolling).
-__global__ void __launch_bounds__(256) k_residual2d_ff(ResidFFArgs a, ResidArgs ad, const float4* __restrict__ f,
+__global__ void __launch_bounds__(256, 3) k_residual2d_ff(ResidFFArgs a, ResidArgs ad, const float4* __restrict__ f,
                                                        const float4* __restrict__ u, float2* __restrict__ r,
                                                        double* __restrict__ sums, const int* __restrict__ skip) {
   if (skip && *skip) return;

@@ -51,6 +51,13 @@ cudaError_t launch_line_tables(void* tables, const Solve2DArgs& a, int step, cud
 cudaError_t launch_tri2d_tab(int step, const void* fhat, const void* faces, const void* tables, void* rec,
                              void* out, void* partial, const Solve2DArgs& a, const int* skip, cudaStream_t st,
                              Profiler* prof);
+// complex64 path with a per-plan pivot table (1/u_j rounded from FP64, chunk
+// constants): table memory per line type, building it, and the step launch.
+size_t line_tables32_bytes(int64_t nx, int64_t n1, int64_t nchunks);
+cudaError_t launch_line_tables32(void* tables, const Solve2DArgs& a, int step, cudaStream_t st);
+cudaError_t launch_tri2d_t32(int step, const void* fhat, const void* faces, const void* tables, void* rec, void* out,
+                             void* partial, const Solve2DArgs& a, const int* skip, cudaStream_t st, Profiler* prof,
+                             const void* consts);
 size_t chunk_record_bytes(int prec);
 // out[face][ix] = scale_face * sum_w partial (complex scales, face 0 then 1).
 cudaError_t launch_reduce_faces(int prec, const void* partial, void* out, int64_t nx, int64_t nwarps,

@@ -629,6 +629,162 @@ __global__ void __launch_bounds__(128) k_tri_pass2_tab(const double2* __restrict
   if (STEP != 3) block_face_sums<C, CH>(red, cnt, partial, (int64_t)blockIdx.x, nparts, nx, s);
 }
 
+// ---------------------------------------------------------------------------
+// complex64 path with a per-plan pivot table.  The reciprocal pivots 1/u_j of
+// every line are computed once per plan in FP64 and stored rounded to FP32
+// (8 bytes per unknown and line type), with the chunk constants pe, cc and
+// q = -b we.  The solves rebuild the multipliers m_j = b / u_{j-1} and the
+// chunk weights w_j from the table with one complex multiply each, so no
+// division is left in the recurrences.
+// ---------------------------------------------------------------------------
+struct LineTables32 {
+  float2* iu;
+  float2* pe;
+  float2* cc;
+  float2* we;
+};
+
+inline LineTables32 line_tables32(void* base, size_t N, size_t nrec) {
+  float2* b = reinterpret_cast<float2*>(base);
+  return LineTables32{b, b + N, b + N + nrec, b + N + 2 * nrec};
+}
+
+__global__ void k_line_tables32(LineTables32 t, Solve2DArgs a, int step) {
+  const int64_t n1 = a.n1, nx = a.nx;
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n1) return;
+  const LineParams lp = line_params(step, a, l);
+  const LineCoef<double2> co = line_coef<double2>(lp.sre, lp.sim, a.hx, a.omega);
+  const double2 zero = make_double2(0, 0);
+  const double2 mb = make_double2(-co.b.x, -co.b.y);
+  double2 iu = zero, P = zero, w = zero, cc = zero;
+  for (int64_t j = 0; j < nx; ++j) {
+    const int64_t k = j / a.ch, s = k * a.ch;
+    const double2 aj = (j == 0 || j == nx - 1) ? co.ac : co.a;
+    double2 m = zero, u;
+    if (j > 0) {
+      m = cmul(co.b, iu);
+      u = csub(aj, cmul(m, co.b));
+    } else {
+      u = aj;
+    }
+    iu = crecip(u);
+    const double2 mm = make_double2(-m.x, -m.y);
+    P = (j == s) ? mm : cmul(P, mm);
+    w = (j == s) ? iu : cmul(cmul(w, mb), iu);
+    cc = (j == s) ? cmul(w, P) : cadd(cc, cmul(w, P));
+    t.iu[j * n1 + l] = cvt<float2>(iu);
+    if (j == min(s + a.ch, nx) - 1) {
+      t.pe[k * n1 + l] = cvt<float2>((k > 0) ? P : zero);
+      t.cc[k * n1 + l] = cvt<float2>((k > 0) ? cc : zero);
+      t.we[k * n1 + l] = cvt<float2>(cmul(mb, w));  // q = -b we
+    }
+  }
+}
+
+template <int STEP, int CH>
+__global__ void __launch_bounds__(128) k_tri_pass1_t32(const float2* __restrict__ fhat, const float2* __restrict__ faces,
+                                                       LineTables32 tb, RecSoA<float2> rec, Solve2DArgs a,
+                                                       const void* __restrict__ consts, const int* __restrict__ skip) {
+  using C = float2;
+  if (skip && *skip) return;
+  const int64_t n1 = a.n1, nx = a.nx;
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n1) return;
+  const int64_t k = blockIdx.y;
+  const int64_t s = k * CH, e = min(s + (int64_t)CH, nx) - 1;
+  const int cnt = (int)(e - s + 1);
+  const LineValues<float, C> lv = line_values<float>(STEP, a, l, consts);
+  const C b = lv.co.b, mb = mk<C>(-b.x, -b.y);
+  const C* f1 = faces;
+  const C* fn = faces + nx;
+  C rr[CH], iu[CH];
+#pragma unroll
+  for (int t = 0; t < CH; ++t)
+    if (t < cnt) {
+      rr[t] = line_rhs<C>(STEP, s + t, l, n1, fhat, f1, fn, lv.scal, lv.par, lv.wl);
+      iu[t] = tb.iu[(s + t) * n1 + l];
+    }
+  C ylo = rr[0], w = iu[0];
+  C bsum = cmul(w, ylo);
+#pragma unroll
+  for (int t = 1; t < CH; ++t) {
+    if (t >= cnt) break;
+    const C m = cmul(b, iu[t - 1]);
+    ylo = csub(rr[t], cmul(m, ylo));
+    w = cmul(cmul(w, mb), iu[t]);
+    bsum = cadd(bsum, cmul(w, ylo));
+  }
+  rec.a[k * n1 + l] = ylo;
+  rec.bsum[k * n1 + l] = bsum;
+}
+
+template <int STEP, int CH>
+__global__ void __launch_bounds__(128) k_tri_pass2_t32(const float2* __restrict__ fhat, const float2* __restrict__ faces,
+                                                       LineTables32 tb, RecSoA<float2> rec, float2* __restrict__ out,
+                                                       float2* __restrict__ partial, Solve2DArgs a,
+                                                       const void* __restrict__ consts, const int* __restrict__ skip) {
+  using C = float2;
+  if (skip && *skip) return;
+  const int64_t n1 = a.n1, nx = a.nx;
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (STEP == 3 && (l & ~(int64_t)31) >= n1) return;  // no block sync in Step 3
+  const bool act = l < n1;
+  const int64_t lc = act ? l : 0;
+  const int64_t k = blockIdx.y;
+  const int64_t s = k * CH, e = min(s + (int64_t)CH, nx) - 1;
+  const int cnt = (int)(e - s + 1);
+  const LineValues<float, C> lv = line_values<float>(STEP, a, lc, consts);
+  const C b = lv.co.b;
+  const C* f1 = faces;
+  const C* fn = faces + nx;
+  const C zero = mk<C>(0, 0);
+  C y[CH], iu[CH];
+#pragma unroll
+  for (int t = 0; t < CH; ++t)
+    if (t < cnt) {
+      y[t] = line_rhs<C>(STEP, s + t, lc, n1, fhat, f1, fn, lv.scal, lv.par, lv.wl);
+      iu[t] = tb.iu[(s + t) * n1 + lc];
+    }
+  C iprev = (s > 0) ? tb.iu[(s - 1) * n1 + lc] : zero;  // 1/u_{s-1}
+  C yp = rec.a[k * n1 + lc];                               // Y(k-1)
+#pragma unroll
+  for (int t = 0; t < CH; ++t) {
+    if (t < cnt) {
+      yp = csub(y[t], cmul(cmul(b, iprev), yp));
+      y[t] = yp;
+      iprev = iu[t];
+    }
+  }
+  __shared__ C red[2 * CH * 128];
+  const int64_t nparts = (n1 + 127) / 128;
+  C xn = rec.bsum[k * n1 + lc];  // X(k+1)
+#pragma unroll
+  for (int t = CH - 1; t >= 0; --t) {
+    if (t < cnt) {
+      const int64_t j = s + t;
+      const C x = cmul(csub(y[t], cmul(b, xn)), iu[t]);
+      xn = x;
+      if (STEP == 3) {
+        if (act) out[j * n1 + lc] = x;
+      } else {
+        C s1, sn;
+        if (STEP == 1) {
+          s1 = act ? x : zero;
+          sn = act ? cmul(x, lv.twl) : zero;
+        } else {
+          const C tt = act ? cmul(x, lv.sig) : zero;
+          s1 = tt;
+          sn = cscale(tt, lv.par);
+        }
+        red[(0 * CH + t) * 128 + threadIdx.x] = s1;
+        red[(1 * CH + t) * 128 + threadIdx.x] = sn;
+      }
+    }
+  }
+  if (STEP != 3) block_face_sums<C, CH>(red, cnt, partial, (int64_t)blockIdx.x, nparts, nx, s);
+}
+
 // Pivot entering each chunk, u_{kCH-1}, for every line: FP64 sequential
 // recurrence once per plan (same sequence as plain Thomas).
 template <typename T>
@@ -793,6 +949,59 @@ cudaError_t launch_tri2d_tab(int step, const void* fhat, const void* faces, cons
   else if (step == 2) HELM_TRI_TAB(2);
   else HELM_TRI_TAB(3);
 #undef HELM_TRI_TAB
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tri2d_t32(int step, const void* fhat, const void* faces, const void* tables, void* rec, void* out,
+                             void* partial, const Solve2DArgs& a, const int* skip, cudaStream_t st, Profiler* prof,
+                             const void* consts) {
+  static const char* n1s[3] = {"tri_step1_pass1", "tri_step2_pass1", "tri_step3_pass1"};
+  static const char* ncs[3] = {"tri_step1_carry", "tri_step2_carry", "tri_step3_carry"};
+  static const char* n2s[3] = {"tri_step1_pass2", "tri_step2_pass2", "tri_step3_pass2"};
+  if (a.ch != kChunkF32) return cudaErrorInvalidValue;
+  const int bs = 128;
+  const dim3 grid((unsigned)((a.n1 + bs - 1) / bs), (unsigned)a.nchunks);
+  const unsigned gcar = (unsigned)((a.n1 + kCarryLines - 1) / kCarryLines);
+  const dim3 bcar(kCarryLines, kCarrySeg);
+  const size_t nrec = (size_t)a.nchunks * a.n1;
+  const LineTables32 tb = line_tables32(const_cast<void*>(tables), (size_t)a.nx * a.n1, nrec);
+  RecSoA<float2> r = rec_soa<float2>(rec, nrec);
+  r.pe = tb.pe;  // rhs-independent chunk constants live in the tables
+  r.cc = tb.cc;
+  r.we = tb.we;
+#define HELM_TRI_T32(S)                                                                                        \
+  do {                                                                                                        \
+    {                                                                                                         \
+      ProfScope ps(prof, n1s[S - 1], st);                                                                     \
+      k_tri_pass1_t32<S, kChunkF32><<<grid, bs, 0, st>>>((const float2*)fhat, (const float2*)faces, tb, r, a, \
+                                                         consts, skip);                                       \
+    }                                                                                                         \
+    {                                                                                                         \
+      ProfScope ps(prof, ncs[S - 1], st);                                                                     \
+      k_tri_carry<float><<<gcar, bcar, 0, st>>>(r, a.n1, a.nchunks, skip);                                    \
+    }                                                                                                         \
+    {                                                                                                         \
+      ProfScope ps(prof, n2s[S - 1], st);                                                                     \
+      k_tri_pass2_t32<S, kChunkF32><<<grid, bs, 0, st>>>((const float2*)fhat, (const float2*)faces, tb, r,    \
+                                                         (float2*)out, (float2*)partial, a, consts, skip);    \
+    }                                                                                                         \
+  } while (0)
+  if (step == 1) HELM_TRI_T32(1);
+  else if (step == 2) HELM_TRI_T32(2);
+  else HELM_TRI_T32(3);
+#undef HELM_TRI_T32
+  return cudaGetLastError();
+}
+
+size_t line_tables32_bytes(int64_t nx, int64_t n1, int64_t nchunks) {
+  return (size_t)(nx * n1 + 3 * nchunks * n1) * sizeof(float2);
+}
+
+cudaError_t launch_line_tables32(void* tables, const Solve2DArgs& a, int step, cudaStream_t st) {
+  const int bs = 128;
+  const unsigned grid = (unsigned)((a.n1 + bs - 1) / bs);
+  const LineTables32 tb = line_tables32(tables, (size_t)a.nx * a.n1, (size_t)a.nchunks * a.n1);
+  k_line_tables32<<<grid, bs, 0, st>>>(tb, a, step);
   return cudaGetLastError();
 }
 
