@@ -142,6 +142,16 @@ int helm_set_refinement(helm_plan_t p, double tol, int max_iter);
  * solves. */
 int helm_set_residual(helm_plan_t p, int kind);
 
+/* HELM_C64_REFINED: launch the first solve and the refinement loop as one
+ * CUDA graph whose loop is a device-side conditional while node (default 1),
+ * or kernel by kernel (0).  The graph is captured at the first solve and
+ * reused; it is recaptured when f or u move (FP64 residual), the residual kind
+ * or the auxiliary change.  Profiling (helm_set_profiling) and
+ * helm_solve_debug always launch kernel by kernel.  Both give the same
+ * result; the graph avoids the host launches of the sweeps after
+ * convergence. */
+int helm_set_graphs(helm_plan_t p, int enable);
+
 /* --- Solve (Sections 4.2 and 5.2: Steps 1-3) ------------------------------
  * f, u: DEVICE pointers to N = nx*ny(*nz) complex values in the layout above
  * (complex128 or complex64 per dtype).  f is read only, u is overwritten; f

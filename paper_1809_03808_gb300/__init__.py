@@ -49,6 +49,7 @@ _SIGS = {
     "helm_set_refinement": (_i32, [_vp, _dbl, _i32]),
     "helm_set_auxiliary": (_i32, [_vp, _dbl, _i32]),
     "helm_set_residual": (_i32, [_vp, _i32]),
+    "helm_set_graphs": (_i32, [_vp, _i32]),
     "helm_solve": (_i32, [_vp, _vp, _vp]),
     "helm_solve_host": (_i32, [_vp, _vp, _vp]),
     "helm_solve_debug": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -123,6 +124,10 @@ def helm_set_refinement(plan, tol, max_iter):
 
 def helm_set_residual(plan, kind):
     _check(lib.helm_set_residual(plan, int(kind)), "helm_set_residual", plan)
+
+
+def helm_set_graphs(plan, enable):
+    _check(lib.helm_set_graphs(plan, int(bool(enable))), "helm_set_graphs", plan)
 
 
 def helm_solve(plan, f, u):

@@ -59,6 +59,13 @@ struct helm_plan {
   int resid_kind = HELM_RESID_FP64;
   float4* ffb = nullptr;  // float-float refinement: f (hi, lo) ...
   float4* ufb = nullptr;  // ... and the accumulated u
+  // refinement loop as a CUDA graph (see build_refine_graph)
+  bool use_graphs = true;
+  cudaStream_t cap[2] = {nullptr, nullptr};  // private capture streams
+  cudaGraph_t rg_graph = nullptr;
+  cudaGraphExec_t rg_exec = nullptr;
+  const void* rg_f = nullptr;  // f, u baked into the graph (FP64 residual)
+  void* rg_u = nullptr;
   Plan3D p3;
   Profiler prof;
   std::string err;
@@ -331,55 +338,166 @@ int solve_core(helm_plan* p, const void* in, int in_is_double, void* out, int ou
   return e == cudaSuccess ? HELM_OK : cuda_fail(p, e, "solve3d");
 }
 
-// Refinement with f and u as float-float vectors: split f once, accumulate the
-// FP32 corrections into (hi, lo) in the inverse-transform epilogue, form the
-// residual in float-float, convert u to complex128 at the end.
-int run_refine_ff(helm_plan* p, const void* f, void* u, void* dbg_fhat, void* dbg_v, void* dbg_w) {
-  const int64_t N = p->n[0] * p->n[1] * p->n[2];
-  int rc;
-  if (!p->ffb) {
-    if ((rc = dev_alloc(p, (void**)&p->ffb, N * sizeof(float4))) ||
-        (rc = dev_alloc(p, (void**)&p->ufb, N * sizeof(float4))))
-      return rc;
-  }
-  HELM_PK("split_ff", launch_split_ff((const double2*)f, p->ffb, N, p->stream));
-  rc = solve_core(p, p->ffb, kInFF, p->ufb, kOutFF, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
-  if (rc) return rc;
+// --- iterative refinement (HELM_C64_REFINED) -------------------------------
+// u0 = S(f); then r = f - A u, u += S(r) until ||r||/||f|| <= tol or max_iter
+// corrections.  S is the complex64 solve.  HELM_RESID_FP64 keeps u in the
+// caller's complex128 buffer and forms r in FP64; HELM_RESID_FF splits f once
+// into a float-float vector, accumulates u as float-float in the inverse
+// transform's epilogue, forms r in float-float and writes u at the end.
+
+bool refine_ff(const helm_plan* p) { return p->resid_kind == HELM_RESID_FF; }
+
+// u0 = S(f)
+int refine_first(helm_plan* p, const void* f, void* u, void* dbg_fhat, void* dbg_v, void* dbg_w) {
+  if (refine_ff(p)) return solve_core(p, p->ffb, kInFF, p->ufb, kOutFF, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
+  return solve_core(p, f, kInC128, u, kOutC128, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
+}
+
+// residual + convergence test (cond: graph while-node handle, 0 outside a graph)
+int refine_check(helm_plan* p, const void* f, const void* u, unsigned long long cond) {
   const int* skip = &p->state->done;
   int64_t nblocks = 0;
-  for (int it = 0; it <= p->max_iter; ++it) {
+  if (refine_ff(p))
     HELM_PK("residual_ff", launch_residual_ff(p->dim, p->n, p->h, p->omega, p->ffb, p->ufb, p->rbuf, p->sums,
                                               &nblocks, skip, p->stream));
-    HELM_PK("residual_finalize", launch_residual_finalize(p->sums, nblocks, p->state, it == p->max_iter, p->stream));
-    if (it == p->max_iter) break;
-    rc = solve_core(p, p->rbuf, kInC64, p->ufb, kOutAccumFF, 1.0, skip, nullptr, nullptr, nullptr);
-    if (rc) return rc;
+  else
+    HELM_PK("residual_fp64", launch_residual(p->dim, p->n, p->h, p->omega, (const double2*)f, (const double2*)u,
+                                             p->rbuf, p->sums, &nblocks, skip, p->stream));
+  HELM_PK("residual_finalize", launch_residual_finalize(p->sums, nblocks, p->state, cond, p->stream));
+  return HELM_OK;
+}
+
+// u += S(r), skipped on the device once the state is done
+int refine_correct(helm_plan* p, void* u) {
+  const int* skip = &p->state->done;
+  if (refine_ff(p)) return solve_core(p, p->rbuf, kInC64, p->ufb, kOutAccumFF, 1.0, skip, nullptr, nullptr, nullptr);
+  return solve_core(p, p->rbuf, kInC64, u, kOutAccumC128, 1.0, skip, nullptr, nullptr, nullptr);
+}
+
+void drop_refine_graph(helm_plan* p) {
+  if (p->rg_exec) cudaGraphExecDestroy(p->rg_exec);
+  if (p->rg_graph) cudaGraphDestroy(p->rg_graph);
+  p->rg_exec = nullptr;
+  p->rg_graph = nullptr;
+  p->rg_f = nullptr;
+  p->rg_u = nullptr;
+}
+
+// Capture u0 = S(f) and the refinement loop as one CUDA graph: the loop is a
+// conditional while node whose body (residual, test, correction) runs again
+// while the test kernel leaves the condition at 1.  The test sets it to 0 once
+// the state is done, which happens after at most max_iter + 1 residuals, so
+// the loop always ends.  Kernel arguments are baked in: the graph is rebuilt
+// when f or u (FP64 residual) or the auxiliary change.
+int build_refine_graph(helm_plan* p, const void* f, void* u) {
+  drop_refine_graph(p);
+  for (int k = 0; k < 2; ++k)
+    if (!p->cap[k]) HELM_CK(cudaStreamCreateWithFlags(&p->cap[k], cudaStreamNonBlocking));
+  cudaStream_t saved = p->stream;
+  p->stream = p->cap[0];
+  HELM_CK(cudaStreamBeginCapture(p->cap[0], cudaStreamCaptureModeThreadLocal));
+  int rc = HELM_OK;
+  cudaGraph_t g = nullptr;
+  bool body_open = false;
+  auto fail = [&](int code) {
+    if (body_open) {
+      cudaGraph_t b = nullptr;
+      cudaStreamEndCapture(p->cap[1], &b);
+    }
+    cudaGraph_t gg = nullptr;
+    cudaStreamEndCapture(p->cap[0], &gg);
+    if (gg) cudaGraphDestroy(gg);
+    cudaGetLastError();
+    p->stream = saved;
+    return code;
+  };
+  if ((rc = refine_first(p, f, u, nullptr, nullptr, nullptr))) return fail(rc);
+  cudaStreamCaptureStatus status;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(p->cap[0], &status, nullptr, &g, &deps, nullptr, &ndeps);
+  if (e != cudaSuccess || status != cudaStreamCaptureStatusActive) return fail(cuda_fail(p, e, "capture info"));
+  cudaGraphConditionalHandle h;
+  if ((e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+    return fail(cuda_fail(p, e, "cudaGraphConditionalHandleCreate"));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t cn;
+  if ((e = cudaGraphAddNode(&cn, g, deps, nullptr, ndeps, &np)) != cudaSuccess)
+    return fail(cuda_fail(p, e, "cudaGraphAddNode(while)"));
+  if ((e = cudaStreamUpdateCaptureDependencies(p->cap[0], &cn, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+      cudaSuccess)
+    return fail(cuda_fail(p, e, "cudaStreamUpdateCaptureDependencies"));
+  // the body, captured on the second stream into the while node's graph
+  if ((e = cudaStreamBeginCaptureToGraph(p->cap[1], np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    return fail(cuda_fail(p, e, "cudaStreamBeginCaptureToGraph"));
+  body_open = true;
+  p->stream = p->cap[1];
+  if ((rc = refine_check(p, f, u, (unsigned long long)h)) || (rc = refine_correct(p, u))) return fail(rc);
+  cudaGraph_t body = nullptr;
+  e = cudaStreamEndCapture(p->cap[1], &body);
+  body_open = false;
+  if (e != cudaSuccess) return fail(cuda_fail(p, e, "end body capture"));
+  p->stream = p->cap[0];
+  e = cudaStreamEndCapture(p->cap[0], &g);
+  p->stream = saved;
+  if (e != cudaSuccess) return cuda_fail(p, e, "end capture");
+  p->rg_graph = g;
+  if ((e = cudaGraphInstantiate(&p->rg_exec, g, 0)) != cudaSuccess) {
+    drop_refine_graph(p);
+    return cuda_fail(p, e, "cudaGraphInstantiate");
   }
-  HELM_PK("join_ff", launch_join_ff(p->ufb, (double2*)u, N, p->stream));
+  p->rg_f = f;
+  p->rg_u = u;
+  return HELM_OK;
+}
+
+int run_refined(helm_plan* p, const void* f, void* u, void* dbg_fhat, void* dbg_v, void* dbg_w) {
+  const int64_t N = p->n[0] * p->n[1] * p->n[2];
+  int rc;
+  RefineState init{};
+  init.tol = p->tol;
+  init.max_iter = p->max_iter;
+  HELM_CK(cudaMemcpyAsync(p->state, &init, sizeof(init), cudaMemcpyHostToDevice, p->stream));
+  if (refine_ff(p)) {
+    if (!p->ffb) {
+      if ((rc = dev_alloc(p, (void**)&p->ffb, N * sizeof(float4))) ||
+          (rc = dev_alloc(p, (void**)&p->ufb, N * sizeof(float4))))
+        return rc;
+    }
+    HELM_PK("split_ff", launch_split_ff((const double2*)f, p->ffb, N, p->stream));
+  }
+  const bool graph = p->use_graphs && !p->prof.on && !dbg_fhat && !dbg_v && !dbg_w;
+  if (graph) {
+    // the float-float graph touches plan buffers only; the FP64 one reads f, u
+    const void* kf = refine_ff(p) ? nullptr : f;
+    void* ku = refine_ff(p) ? nullptr : u;
+    if (!p->rg_exec || p->rg_f != kf || p->rg_u != ku) {
+      if ((rc = build_refine_graph(p, f, u))) return rc;
+      p->rg_f = kf;
+      p->rg_u = ku;
+    }
+    HELM_CK(cudaGraphLaunch(p->rg_exec, p->stream));
+  } else {
+    if ((rc = refine_first(p, f, u, dbg_fhat, dbg_v, dbg_w))) return rc;
+    for (int it = 0; it <= p->max_iter; ++it) {
+      if ((rc = refine_check(p, f, u, 0))) return rc;
+      if (it == p->max_iter) break;
+      if ((rc = refine_correct(p, u))) return rc;
+    }
+  }
+  if (refine_ff(p)) HELM_PK("join_ff", launch_join_ff(p->ufb, (double2*)u, N, p->stream));
   return HELM_OK;
 }
 
 int run_solve(helm_plan* p, const void* f, void* u, void* dbg_fhat, void* dbg_v, void* dbg_w) {
   if (p->dtype == HELM_C128) return solve_core(p, f, kInC128, u, kOutC128, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
   if (p->dtype == HELM_C64_RAW) return solve_core(p, f, kInC64, u, kOutC64, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
-  // HELM_C64_REFINED: u0 = S(f); then r = f - A u (FP64), u += S(r) until tol.
-  RefineState init{};
-  init.tol = p->tol;
-  HELM_CK(cudaMemcpyAsync(p->state, &init, sizeof(init), cudaMemcpyHostToDevice, p->stream));
-  if (p->resid_kind == HELM_RESID_FF) return run_refine_ff(p, f, u, dbg_fhat, dbg_v, dbg_w);
-  int rc = solve_core(p, f, kInC128, u, kOutC128, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
-  if (rc) return rc;
-  const int* skip = &p->state->done;
-  int64_t nblocks = 0;
-  for (int it = 0; it <= p->max_iter; ++it) {
-    HELM_PK("residual_fp64", launch_residual(p->dim, p->n, p->h, p->omega, (const double2*)f, (const double2*)u, p->rbuf, p->sums,
-                            &nblocks, skip, p->stream));
-    HELM_PK("residual_finalize", launch_residual_finalize(p->sums, nblocks, p->state, it == p->max_iter, p->stream));
-    if (it == p->max_iter) break;
-    rc = solve_core(p, p->rbuf, kInC64, u, kOutAccumC128, 1.0, skip, nullptr, nullptr, nullptr);
-    if (rc) return rc;
-  }
-  return HELM_OK;
+  return run_refined(p, f, u, dbg_fhat, dbg_v, dbg_w);
 }
 
 int alloc_buffers_2d(helm_plan* p) {
@@ -463,6 +581,9 @@ void destroy_plan(helm_plan* p) {
   cudaFree(p->host_f);
   cudaFree(p->host_u);
   free_plan3d(p->p3);
+  drop_refine_graph(p);
+  for (int k = 0; k < 2; ++k)
+    if (p->cap[k]) cudaStreamDestroy(p->cap[k]);
   p->prof.destroy();
   delete p;
 }
@@ -647,6 +768,7 @@ int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx
 int helm_set_auxiliary(helm_plan_t p, double rho, int phase_quarters) {
   if (!p || !std::isfinite(rho) || rho < 0.0 || rho > 8.0) return HELM_EINVAL;
   HELM_CK(cudaStreamSynchronize(p->stream));
+  drop_refine_graph(p);  // its kernels hold the old eigen-data
   int rc = build_axis_aux(p, p->axo, rho, phase_quarters);
   if (!rc && p->dim == 3) rc = build_axis_aux(p, p->axi, rho, phase_quarters);
   if (rc) return rc;
@@ -658,6 +780,8 @@ int helm_set_auxiliary(helm_plan_t p, double rho, int phase_quarters) {
       HELM_CK(p->prec == kPrecF64 ? launch_line_tables(p->tabB, a, 1, nullptr)
                                   : launch_line_tables32(p->tabB, a, 1, nullptr));
     HELM_CK(cudaDeviceSynchronize());
+  } else {
+    HELM_CK(plan3d_tables(p->p3));
   }
   return HELM_OK;
 }
@@ -677,7 +801,14 @@ int helm_set_refinement(helm_plan_t p, double tol, int max_iter) {
 
 int helm_set_residual(helm_plan_t p, int kind) {
   if (!p || p->dtype != HELM_C64_REFINED || (kind != HELM_RESID_FP64 && kind != HELM_RESID_FF)) return HELM_EINVAL;
+  if (p->resid_kind != kind) drop_refine_graph(p);
   p->resid_kind = kind;
+  return HELM_OK;
+}
+
+int helm_set_graphs(helm_plan_t p, int enable) {
+  if (!p) return HELM_EINVAL;
+  p->use_graphs = enable != 0;
   return HELM_OK;
 }
 

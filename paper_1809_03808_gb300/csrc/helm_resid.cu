@@ -630,8 +630,11 @@ __global__ void k_join_ff(const float4* __restrict__ q, double2* __restrict__ o,
 }
 
 __global__ void k_residual_finalize(const double* __restrict__ sums, int64_t nblocks, RefineState* st,
-                                    int last) {
-  if (st->done) return;
+                                    cudaGraphConditionalHandle cond) {
+  if (st->done) {
+    if (cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+    return;
+  }
   __shared__ double sr[256], sf[256];
   double a2 = 0, b2 = 0;
   for (int64_t i = threadIdx.x; i < nblocks; i += blockDim.x) {
@@ -657,9 +660,10 @@ __global__ void k_residual_finalize(const double* __restrict__ sums, int64_t nbl
     if (rel <= st->tol) {
       st->converged = 1;
       st->done = 1;
-    } else if (last) {
+    } else if (it + 1 >= st->max_iter + 1) {
       st->done = 1;
     }
+    if (cond) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
   }
 }
 
@@ -793,9 +797,9 @@ int64_t residual_blocks(int dim, const int64_t* n) {
   return ((n[2] + TZ3 - 1) / TZ3) * ((n[1] + TY3 - 1) / TY3) * ((n[0] + RX3 - 1) / RX3);
 }
 
-cudaError_t launch_residual_finalize(const double* sums, int64_t nblocks, RefineState* state, int last,
-                                     cudaStream_t st) {
-  k_residual_finalize<<<1, 256, 0, st>>>(sums, nblocks, state, last);
+cudaError_t launch_residual_finalize(const double* sums, int64_t nblocks, RefineState* state,
+                                     unsigned long long cond, cudaStream_t st) {
+  k_residual_finalize<<<1, 256, 0, st>>>(sums, nblocks, state, (cudaGraphConditionalHandle)cond);
   return cudaGetLastError();
 }
 

@@ -72,7 +72,7 @@ struct RefineState {
   int done;         // set when ||r||/||f|| <= tol; later sweeps skip their kernels
   int iters;        // residual evaluations performed
   int converged;
-  int pad;
+  int max_iter;     // correction sweeps allowed: done after max_iter + 1 residuals
   double tol;
   double fnorm2;
   double resid[16];
@@ -96,8 +96,10 @@ cudaError_t launch_join_ff(const float4* u, double2* out, int64_t N, cudaStream_
 // Number of per-block sums launch_residual writes for this grid.
 int64_t residual_blocks(int dim, const int64_t* n);
 // Reduce the block sums, record ||r||/||f|| as the next residual of *state,
-// set state->done when it is <= tol or when `last` is set.
-cudaError_t launch_residual_finalize(const double* sums, int64_t nblocks, RefineState* state, int last,
-                                     cudaStream_t st);
+// set state->done when it is <= tol or after max_iter + 1 residuals.  With
+// `cond` != 0 also set that graph conditional to !done (the while node of a
+// captured refinement loop); cond = 0 outside a graph.
+cudaError_t launch_residual_finalize(const double* sums, int64_t nblocks, RefineState* state,
+                                     unsigned long long cond, cudaStream_t st);
 
 }  // namespace helm

@@ -95,11 +95,17 @@ __device__ void plane_cbb(const C* v, const C* w2, C* out, int nx, double hx, do
 // OSTEP 1: G = fhat / mu_l                        (outer Step 1, eq. 3dHBs1)
 // OSTEP 2: G = chat_1 + par_l chat_n, outer A mode (outer Step 2, eq. step2-2-3d)
 // OSTEP 3: G = (fhat + dhat_1 + e^{+i theta_l} e^{-t(ny-1)} dhat_n) / mu_l  (eq. 3dHBs3)
-template <typename T, int OSTEP>
+// TAB: read the reciprocal pivots 1/den_ix of the inner lines from per-plan
+// tables (tabB: inner B-type lines, tabA: inner A-type, both for this outer
+// mode type) instead of recomputing them; the forward sweep then stores only
+// d and the backward sweep rebuilds c = b / den from the table.
+template <typename T, int OSTEP, bool TAB>
 __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* __restrict__ fhat,
                                                   typename cpx<T>::type* __restrict__ cbuf,
                                                   typename cpx<T>::type* __restrict__ dbuf,
                                                   const typename cpx<T>::type* __restrict__ gfaces,
+                                                  const typename cpx<T>::type* __restrict__ tabB,
+                                                  const typename cpx<T>::type* __restrict__ tabA,
                                                   Plane3DArgs a, const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
   if (skip && *skip) return;
@@ -160,27 +166,41 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
   // rows are processed in batches of PB: the batch's right-hand sides (and,
   // backward, its scratch values) are loaded before the dependent recurrence
   constexpr int PB = 8;
-  auto forward = [&](ThomasRow<C>& th, auto rhs) {
+  auto forward = [&](ThomasRow<C>& th, const C* tab, auto rhs) {
     if (!act) return;
     for (int i0 = 0; i0 < nx; i0 += PB) {
-      C rr[PB];
+      C rr[PB], iv[PB];
 #pragma unroll
       for (int t = 0; t < PB; ++t)
-        if (i0 + t < nx) rr[t] = rhs(i0 + t);
+        if (i0 + t < nx) {
+          rr[t] = rhs(i0 + t);
+          if (TAB) iv[t] = tab[(i0 + t) * xs + plane];
+        }
 #pragma unroll
       for (int t = 0; t < PB; ++t) {
         const int ix = i0 + t;
         if (ix < nx) {
-          C c, d;
-          th.step(ix, rr[t], c, d);
-          cbuf[ix * xs + plane] = c;
-          dbuf[ix * xs + plane] = d;
+          if (TAB) {
+            const C d = cmul(ix == 0 ? rr[t] : csub(rr[t], cmul(th.k.b, th.d_prev)), iv[t]);
+            th.d_prev = d;
+            dbuf[ix * xs + plane] = d;
+          } else {
+            C c, d;
+            th.step(ix, rr[t], c, d);
+            cbuf[ix * xs + plane] = c;
+            dbuf[ix * xs + plane] = d;
+          }
         }
       }
     }
   };
+  // c_ix of the line: from the scratch, or b / den_ix from the table
+  auto cval = [&](const ThomasRow<C>& th, const C* tab, int ix) -> C {
+    if (TAB) return cmul(th.k.b, tab[ix * xs + plane]);
+    return cbuf[ix * xs + plane];
+  };
   // backward sweep reducing (s1, sn) contributions over m into out[2][nx]
-  auto backward_reduce = [&](auto contrib, C* out, C scale0, C scale1) {
+  auto backward_reduce = [&](const ThomasRow<C>& th, const C* tab, auto contrib, C* out, C scale0, C scale1) {
     C x = mk<C>(0, 0);
     for (int x0 = nx - 1; x0 >= 0; x0 -= XC) {
       const int x1 = max(0, x0 - XC + 1);
@@ -191,7 +211,7 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
           const int ix = b0 - t;
           if (act && ix >= x1) {
             dd[t] = dbuf[ix * xs + plane];
-            cc[t] = cbuf[ix * xs + plane];
+            cc[t] = cval(th, tab, ix);
           }
         }
 #pragma unroll
@@ -222,8 +242,9 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
   };
 
   // inner Step 1: B-aux solve, reduce to inner faces v_in
-  forward(thB, [&](int ix) { return cmul(G(ix), invmu_i); });
+  forward(thB, tabB, [&](int ix) { return cmul(G(ix), invmu_i); });
   backward_reduce(
+      thB, tabB,
       [&](bool ac, C x, C& s1, C& sn) {
         s1 = ac ? x : mk<C>(0, 0);
         sn = ac ? cmul(x, twm) : mk<C>(0, 0);
@@ -232,8 +253,9 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
   plane_cbb(vin, (const C*)nullptr, cin, nx, a.hx, a.hz, a.omega, pre, pim, gi, giv);
   __syncthreads();
   // inner Step 2: A solve on the generated rhs, reduce to w_in
-  forward(thA, [&](int ix) { return cadd(cin[ix], cscale(cin[nx + ix], pari)); });
+  forward(thA, tabA, [&](int ix) { return cadd(cin[ix], cscale(cin[nx + ix], pari)); });
   backward_reduce(
+      thA, tabA,
       [&](bool ac, C x, C& s1, C& sn) {
         C t = ac ? cmul(x, sigi) : mk<C>(0, 0);
         s1 = t;
@@ -243,7 +265,7 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
   plane_cbb(vin, win, cin, nx, a.hx, a.hz, a.omega, pre, pim, gi, giv);
   __syncthreads();
   // inner Step 3: corrected B-aux solve, y3 written over the scratch
-  forward(thB, [&](int ix) {
+  forward(thB, tabB, [&](int ix) {
     C v = cadd(G(ix), cin[ix]);
     v = cadd(v, cmul(cin[nx + ix], wm));
     return cmul(v, invmu_i);
@@ -257,7 +279,7 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
         const int ix = b0 - t;
         if (ix >= 0) {
           dd[t] = dbuf[ix * xs + plane];
-          cc[t] = cbuf[ix * xs + plane];
+          cc[t] = cval(thB, tabB, ix);
         }
       }
 #pragma unroll
@@ -360,6 +382,30 @@ __global__ void k_outer_cbb(const typename cpx<T>::type* __restrict__ v, const t
   out[nx * nz + i] = cadd(cmul(g, cadd(cscale(Sv[0], e1n), cscale(Pv[0], d1n))), cadd(cscale(Sv[1], e11), cmul(d11, Pv[1])));
 }
 
+// Reciprocal pivots of the inner tridiagonal lines of one line type (outer
+// mode type x inner mode type), for every (x, l, m): the FP64 recurrence of
+// ThomasRow, stored in the compute precision at the layout of the scratch.
+template <typename T>
+__global__ void k_plane_tables(typename cpx<T>::type* __restrict__ tab, Plane3DArgs a, int outerA, int innerA) {
+  using C = typename cpx<T>::type;
+  const int64_t ny = a.ny, nz = a.nz, nx = a.nx;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // l * nz + m
+  if (i >= ny * nz) return;
+  const int64_t l = i / nz, m = i - l * nz;
+  const double* lo = outerA ? a.lamAo : a.lamBo;
+  const double* li = innerA ? a.lamAi : a.lamBi;
+  const double w2 = a.omega * a.omega;
+  const LineCoef<double2> k = line_coef<double2>(lo[2 * l] + li[2 * m] - w2, lo[2 * l + 1] + li[2 * m + 1], a.hx, a.omega);
+  double2 c = make_double2(0, 0);
+  for (int64_t ix = 0; ix < nx; ++ix) {
+    const double2 aj = (ix == 0 || ix == nx - 1) ? k.ac : k.a;
+    const double2 den = ix == 0 ? aj : csub(aj, cmul(k.b, c));
+    const double2 inv = crecip(den);
+    c = cmul(k.b, inv);
+    tab[ix * ny * nz + i] = cvt<C>(inv);
+  }
+}
+
 Plane3DArgs make_args(const Plan3D& p) {
   Plane3DArgs a;
   a.nx = p.n[0];
@@ -401,13 +447,19 @@ cudaError_t launch_plane(int ostep, const Plan3D& p, const void* gfaces, const i
   const int nw = bs / 32;
   const size_t smem = (size_t)(6 * p.n[0] + nw * 2 * XC) * sizeof(C);
   Plane3DArgs a = make_args(p);
+  // tables of this outer mode type: [outer A][inner A]
+  const int oA = ostep == 2 ? 1 : 0;
+  const C* tB = (const C*)p.tab[2 * oA + 0];
+  const C* tA = (const C*)p.tab[2 * oA + 1];
   auto run = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<(unsigned)p.n[1], bs, smem, st>>>((const C*)p.fhat, (C*)p.cbuf, (C*)p.dbuf, (const C*)gfaces, a, skip);
+    kern<<<(unsigned)p.n[1], bs, smem, st>>>((const C*)p.fhat, (C*)p.cbuf, (C*)p.dbuf, (const C*)gfaces, tB, tA, a,
+                                             skip);
   };
-  if (ostep == 1) run(k_plane3d<T, 1>);
-  else if (ostep == 2) run(k_plane3d<T, 2>);
-  else run(k_plane3d<T, 3>);
+  const bool tab = tB && tA;
+  if (ostep == 1) tab ? run(k_plane3d<T, 1, true>) : run(k_plane3d<T, 1, false>);
+  else if (ostep == 2) tab ? run(k_plane3d<T, 2, true>) : run(k_plane3d<T, 2, false>);
+  else tab ? run(k_plane3d<T, 3, true>) : run(k_plane3d<T, 3, false>);
   return cudaGetLastError();
 }
 
@@ -518,11 +570,42 @@ cudaError_t plan3d_init(Plan3D& p, int prec, const int64_t* n, const double* h, 
     }
     *bytes += sizes[i];
   }
+  // per-plan pivot tables of the four inner line types; without room for
+  // them the kernels recompute the pivots
+  for (int t = 0; t < 4; ++t) {
+    if (cudaMalloc(&p.tab[t], N * cb) != cudaSuccess) {
+      cudaGetLastError();
+      for (int u = 0; u < 4; ++u) {
+        cudaFree(p.tab[u]);
+        p.tab[u] = nullptr;
+      }
+      *bytes -= (size_t)t * N * cb;
+      break;
+    }
+    *bytes += N * cb;
+  }
   p.ready = true;
-  return cudaSuccess;
+  return plan3d_tables(p);
+}
+
+cudaError_t plan3d_tables(Plan3D& p) {
+  if (!p.tab[0]) return cudaSuccess;
+  const Plane3DArgs a = make_args(p);
+  const int bs = 128;
+  const unsigned grid = (unsigned)((p.n[1] * p.n[2] + bs - 1) / bs);
+  for (int t = 0; t < 4; ++t) {
+    if (p.prec == kPrecF64)
+      k_plane_tables<double><<<grid, bs>>>((double2*)p.tab[t], a, t >> 1, t & 1);
+    else
+      k_plane_tables<float><<<grid, bs>>>((float2*)p.tab[t], a, t >> 1, t & 1);
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaDeviceSynchronize();
 }
 
 void free_plan3d(Plan3D& p) {
+  for (int t = 0; t < 4; ++t) cudaFree(p.tab[t]);
   cudaFree(p.fhat);
   cudaFree(p.cbuf);
   cudaFree(p.dbuf);

@@ -23,11 +23,16 @@ struct Plan3D {
   void* ybuf = nullptr;
   void* faces = nullptr;
   void* partial = nullptr;
+  // reciprocal pivots of the inner lines, [outer A][inner A] (nullptr: none)
+  void* tab[4] = {nullptr, nullptr, nullptr, nullptr};
   bool ready = false;
 };
 
 cudaError_t plan3d_init(Plan3D& p, int prec, const int64_t* n, const double* h, double omega, const AxisData& axo,
                         const AxisData& axi, size_t* bytes);
+// (Re)build the pivot tables from the current eigen-data (after a change of
+// the auxiliary).
+cudaError_t plan3d_tables(Plan3D& p);
 void free_plan3d(Plan3D& p);
 cudaError_t solve3d_core(Plan3D& p, int prec, const void* in, int in_is_double, void* out, int out_mode,
                          double accum_scale, const int* skip, void* dbg_fhat, void* dbg_v, void* dbg_w,

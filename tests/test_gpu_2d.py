@@ -198,3 +198,35 @@ def test_ff_and_fp64_residuals_agree(env):
     assert abs(r64[0] - rff[0]) <= 1e-5 * r64[0]
     assert abs(len(r64) - len(rff)) <= 1
     assert np.linalg.norm(u64 - uff) / np.linalg.norm(u64) < 1e-10
+
+
+@pytest.mark.parametrize("kind", ["fp64", "ff"])
+def test_graph_and_eager_refinement_agree(env, kind):
+    """The refinement loop captured as a CUDA graph (device-side while node)
+    runs the same kernels as the kernel-by-kernel loop: identical results and
+    residual histories, also when the graph is reused and when u moves."""
+    helm, torch = env
+    shape, h, omega = CASES["ragged_65x100"]
+    f = torch.from_numpy(random_rhs(shape, 11)).cuda()
+    res = {}
+    for graphs in (0, 1):
+        plan = helm.Plan(shape, h, omega, helm.HELM_C64_REFINED)
+        helm.helm_set_residual(plan.handle, helm.HELM_RESID_FF if kind == "ff" else helm.HELM_RESID_FP64)
+        helm.helm_set_refinement(plan.handle, 1e-12, 10)
+        helm.helm_set_graphs(plan.handle, graphs)
+        outs = []
+        for rep in range(3):
+            u = plan.solve(f)  # a fresh u every time: the FP64 graph is recaptured
+            info, st = plan.info()
+            assert st == helm.HELM_OK and info.converged == 1
+            outs.append((u.cpu().numpy(), list(info.residual[:info.iterations + 1])))
+        u2 = torch.empty_like(f)
+        plan.solve(f, u2)
+        plan.solve(f, u2)  # same buffers: the captured graph is reused
+        outs.append((u2.cpu().numpy(), None))
+        plan.close()
+        res[graphs] = outs
+    for (a, ra), (b, rb) in zip(res[0], res[1]):
+        assert np.array_equal(a, b)
+        if ra is not None:
+            assert ra == rb
