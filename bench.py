@@ -147,6 +147,23 @@ def kernel_model(name, e, n1, accum=False, first=True, tables=False, ff=False):
     else:
         tri = {"tri_step1_pass1": (e, 67.0), "tri_step2_pass1": (0.0, 61.0), "tri_step3_pass1": (e, 75.0),
                "tri_step1_pass2": (e, 53.0), "tri_step2_pass2": (0.0, 47.0), "tri_step3_pass2": (2.0 * e, 55.0)}
+    # 3D (n1 = the y / z length): z transforms on rows, y transforms in place
+    # on columns; k_plane3d per outer step: per inner step the forward sweep
+    # reads 1/den and writes d, the backward sweep reads both (4e), x3 steps,
+    # plus f_hat read in inner Steps 1 and 3 (outer Steps 1, 3) and y3 written
+    c128 = e == 16
+    tab3 = {
+        "dft_z_fwd": ((16 if c128 else 8) + e, 5.0 * log2n),
+        "dft_y_fwd": (2 * e, 5.0 * log2n),
+        "dft_y_inv": (2 * e, 5.0 * log2n),
+        "dft_z_inv": (e + (16 if c128 else 32), 5.0 * log2n),
+        "plane3d_step1": (15 * e, 100.0),
+        "plane3d_step2": (13 * e, 90.0),
+        "plane3d_step3": (15 * e, 100.0),
+        "reduce_outer": (e, 8.0),
+    }
+    if name in tab3:
+        return tab3[name]
     tab = {
         "dft_fwd": (fin + e, 5.0 * log2n),
         "dft_inv": (e + (32 if accum else 16 if e == 16 else 8), 5.0 * log2n),
@@ -347,7 +364,7 @@ def run_gb300(args):
 
     # --- roofline of the dominant kernel of the timed (c128) step ---
     peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
-    n1 = p.shape[1]
+    n1 = p.shape[-1]
     name, (launches, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
     def kernels_of(path, pr):
         f64 = path == "c128"
@@ -363,7 +380,8 @@ def run_gb300(args):
     gpu_launches = int(round(sum(v[0] for v in prof.values()) / PROFILE_SOLVES)) * args.steps
     if info.iterations:
         refine = {"refinement_sweeps": int(info.iterations), "tol": REFINE_TOL,
-                  "final_rel_residual": float(info.residual[info.iterations]), "converged": bool(info.converged)}
+                  "final_rel_residual": float(info.residual[info.iterations]), "converged": bool(info.converged),
+                  "residual_history": [float(x) for x in info.residual[:info.iterations + 1]]}
     else:
         refine = None
 
@@ -386,6 +404,8 @@ def run_gb300(args):
         "kernels": kernels_main,
         "roofline": roof, "clocks": clocks, "e2e": e2e, "variants": variants, "cpu_baseline": cpu,
         "plan_seconds": info.plan_seconds,
+        "auxiliary": {"rho": info.aux_rho, "q": info.aux_q, "trial_rel_residual": info.aux_trial_residual},
+        "device_bytes": int(info.device_bytes),
     }
     if rank == 0:
         print(json.dumps(line))

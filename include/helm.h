@@ -74,7 +74,7 @@ enum helm_status {
   HELM_ENOMEM = -2,        /* device or host allocation failed */
   HELM_ECUDA = -3,         /* a CUDA runtime call failed */
   HELM_ENOTCONV = -4,      /* refinement stopped above tol; u is still written */
-  HELM_ETIMEOUT = -5,      /* reserved: a bounded device wait gave up */
+  HELM_ETIMEOUT = -5,      /* a bounded device wait gave up (helm_get_info; sticky) */
   HELM_EUNSUPPORTED = -6,  /* size outside what the kernels support */
   HELM_ENUMERIC = -7       /* plan eigen-data failed to converge / degenerate */
 };
@@ -94,12 +94,18 @@ typedef struct helm_info {
   int32_t n_dft_stages;    /* stages of the x1 transform */
   size_t device_bytes;     /* device memory owned by the plan */
   int32_t residual_kind;   /* helm_residual of the plan */
+  int32_t aux_q;           /* auxiliary of the periodic axes: phase q ... */
+  double aux_rho;          /* ... and damping rho (see helm_set_auxiliary) */
+  double aux_trial_residual; /* plan-time trial residual of the chosen auxiliary
+                                (-1 if set by helm_set_auxiliary) */
 } helm_info;
 
 /* --- Plan (the paper's "Initialization", Section 6) -----------------------
  * Builds the per-axis eigen-data: the periodic eigenvalues of eq.
  * eigvaluesPer, the absorbing-pencil eigenvalues Lam^A and boundary rows of
- * V (eqs. EVP1a, EVPcondA), the DFT twiddles; allocates all device scratch.
+ * V (eqs. EVP1a, EVPcondA), the DFT twiddles and the per-plan pivot tables;
+ * allocates all device scratch; chooses the auxiliary (see helm_set_auxiliary)
+ * by trial solves, which is most of the plan time on large grids.
  * nx, ny (, nz): node counts, >= 3.  hx, hy (, hz): spacings > 0, finite.
  * omega: wave number > 0, finite.  dtype: helm_dtype.
  * On success *out owns device memory until helm_destroy; on failure *out is
@@ -118,9 +124,11 @@ int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx
  * unchanged.  B is diagonalised by F D^-1, D = diag(e^{t j}),
  * t = (rho + i q pi/2)/n1, with eigenvalues (2 - 2cosh(t + i theta_l))/h and
  * h (4 + 2cosh(t + i theta_l))/6.  rho = q = 0 is the paper's periodic
- * auxiliary.  rho > 0 damps waves that travel around the periodic loop, which
- * keeps B far from resonance and the solve accurate.  Default: rho = 1 with
- * q = 1 in 2D and q = 0 in 3D.
+ * auxiliary.  Which (rho, q) keeps B's own problems well conditioned depends
+ * on the grid, so a new plan tries five candidates, (rho, q) in {(1, 1),
+ * (0.5, 0), (1, 0), (0.5, 1), (0, 0)}: one solve of a fixed pseudo-random
+ * load each, in the plan's precision, keeping the smallest relative residual
+ * (helm_info reports the choice).  This call overrides that choice.
  * Applies to every periodic axis of the plan.  rho must be in [0, 8]; any
  * integer q is taken mod 4.  Rebuilds the plan's auxiliary tables; call it
  * between solves, not while a solve is in flight on another stream. */

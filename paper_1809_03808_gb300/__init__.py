@@ -35,7 +35,8 @@ class helm_info(ctypes.Structure):
                 ("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("residual", ctypes.c_double * 16), ("plan_seconds", ctypes.c_double),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("n_dft_stages", ctypes.c_int32),
-                ("device_bytes", ctypes.c_size_t), ("residual_kind", ctypes.c_int32)]
+                ("device_bytes", ctypes.c_size_t), ("residual_kind", ctypes.c_int32),
+                ("aux_q", ctypes.c_int32), ("aux_rho", ctypes.c_double), ("aux_trial_residual", ctypes.c_double)]
 
 
 class helm_profile_entry(ctypes.Structure):

@@ -56,6 +56,8 @@ struct helm_plan {
   double plan_seconds = 0;
   double tol = 1e-14;
   int max_iter = 10;
+  double aux_trial_resid = -1.0;  // plan-time trial residual of the chosen auxiliary
+  int* dev_err = nullptr;         // device error word of the kernels' bounded waits
   int resid_kind = HELM_RESID_FP64;
   float4* ffb = nullptr;  // float-float refinement: f (hi, lo) ...
   float4* ufb = nullptr;  // ... and the accumulated u
@@ -297,7 +299,7 @@ int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int 
     HELM_CK(launch_tri2d_tab(1, p->fhat, nullptr, p->tabB, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr));
   else if (p->tabB)
     HELM_CK(launch_tri2d_t32(1, p->fhat, nullptr, p->tabB, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr,
-                             p->constB));
+                             p->constB, p->dev_err));
   else
     HELM_CK(launch_tri2d(prec, 1, p->fhat, nullptr, p->ustartB, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr, p->constB));
   HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fv, nx, nparts, inv_n1, en_n1, skip, st));
@@ -309,7 +311,7 @@ int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int 
     HELM_CK(launch_tri2d_tab(2, nullptr, fc, p->tabA, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr));
   else if (p->tabA)
     HELM_CK(launch_tri2d_t32(2, nullptr, fc, p->tabA, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr,
-                             p->constA));
+                             p->constA, p->dev_err));
   else
     HELM_CK(launch_tri2d(prec, 2, nullptr, fc, p->ustartA, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr, p->constA));
   HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fw, nx, nparts, one, one, skip, st));
@@ -321,7 +323,7 @@ int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int 
     HELM_CK(launch_tri2d_tab(3, p->fhat, fc, p->tabB, p->rec, p->dbuf, nullptr, a, skip, st, p->prof.on ? &p->prof : nullptr));
   else if (p->tabB)
     HELM_CK(launch_tri2d_t32(3, p->fhat, fc, p->tabB, p->rec, p->dbuf, nullptr, a, skip, st, p->prof.on ? &p->prof : nullptr,
-                             p->constB));
+                             p->constB, p->dev_err));
   else
     HELM_CK(launch_tri2d(prec, 3, p->fhat, fc, p->ustartB, p->rec, p->dbuf, nullptr, a, skip, st, p->prof.on ? &p->prof : nullptr, p->constB));
   // a5: inverse DFT along x1 (eq. step3IFFTz3coeff)
@@ -546,6 +548,8 @@ int alloc_buffers_2d(helm_plan* p) {
 int alloc_refine(helm_plan* p) {
   int64_t N = p->n[0] * p->n[1] * p->n[2];
   int rc;
+  if ((rc = dev_alloc(p, (void**)&p->dev_err, sizeof(int)))) return rc;
+  HELM_CK(cudaMemset(p->dev_err, 0, sizeof(int)));
   if (p->dtype != HELM_C64_REFINED) {
     rc = dev_alloc(p, (void**)&p->state, sizeof(RefineState));
     return rc;
@@ -577,6 +581,7 @@ void destroy_plan(helm_plan* p) {
   cudaFree(p->sums);
   cudaFree(p->ffb);
   cudaFree(p->ufb);
+  cudaFree(p->dev_err);
   cudaFree(p->state);
   cudaFree(p->host_f);
   cudaFree(p->host_u);
@@ -663,6 +668,104 @@ void static_aux_tables(AxisData& a, double rho, int q) {
   a.ginv[1] = -std::exp(-rho) * gi[a.q];
 }
 
+// Rebuild every table that depends on the auxiliary of the periodic axes.
+int apply_aux(helm_plan* p, double rho, int phase_quarters) {
+  drop_refine_graph(p);  // its kernels hold the old eigen-data
+  int rc = build_axis_aux(p, p->axo, rho, phase_quarters);
+  if (!rc && p->dim == 3) rc = build_axis_aux(p, p->axi, rho, phase_quarters);
+  if (rc) return rc;
+  if (p->dim == 2) {
+    const Solve2DArgs a = args2d(p);
+    HELM_CK(launch_pivots(p->prec, p->ustartB, a, 1, nullptr));
+    if (p->constB) HELM_CK(launch_line_consts(p->prec, p->constB, a, 1, nullptr));
+    if (p->tabB)
+      HELM_CK(p->prec == kPrecF64 ? launch_line_tables(p->tabB, a, 1, nullptr)
+                                  : launch_line_tables32(p->tabB, a, 1, nullptr));
+    HELM_CK(cudaDeviceSynchronize());
+  } else {
+    HELM_CK(plan3d_tables(p->p3));
+  }
+  return HELM_OK;
+}
+
+// The auxiliary B (damping rho and phase q of the gamma-circulant, reading
+// R13) is chosen per plan.  Steps 1-3 are exact for every B, but the rounding
+// errors of a solve grow with the conditioning of B's own problems, which
+// depends on where the grid's modes fall relative to w^2: no fixed (rho, q)
+// suits every grid.  Each candidate gets one solve, in the plan's precision,
+// of a fixed pseudo-random load f; the candidate with the smallest relative
+// residual ||f - A u|| / ||f|| (FP64, eq. A2D / A3D) is kept.  For the
+// refined mode that residual is the contraction factor of one sweep.
+struct AuxCand {
+  double rho;
+  int q;
+};
+constexpr AuxCand kAuxCandidates[] = {{1.0, 1}, {0.5, 0}, {1.0, 0}, {0.5, 1}, {0.0, 0}};
+
+int tune_auxiliary(helm_plan* p) {
+  const int64_t N = p->n[0] * p->n[1] * p->n[2];
+  double2 *tf = nullptr, *tu = nullptr;
+  float2* tr = p->rbuf;
+  double* ts = p->sums;
+  bool own_r = false;
+  auto cleanup = [&]() {
+    cudaFree(tf);
+    cudaFree(tu);
+    if (own_r) {
+      cudaFree(tr);
+      cudaFree(ts);
+    }
+    cudaGetLastError();
+  };
+  const int64_t nb_max = residual_blocks(p->dim, p->n);
+  if (cudaMalloc(&tf, N * sizeof(double2)) != cudaSuccess || cudaMalloc(&tu, N * sizeof(double2)) != cudaSuccess) {
+    cleanup();
+    return HELM_OK;  // no room for the trials: keep the default auxiliary
+  }
+  if (!tr) {
+    own_r = true;
+    if (cudaMalloc(&tr, N * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&ts, nb_max * 2 * sizeof(double)) != cudaSuccess) {
+      cleanup();
+      return HELM_OK;
+    }
+  }
+  cudaStream_t saved = p->stream;
+  p->stream = nullptr;
+  std::vector<double> hs(2 * nb_max);
+  double best = HUGE_VAL;
+  AuxCand pick = kAuxCandidates[0];
+  int rc = HELM_OK;
+  if (launch_trial_rhs(tf, N, 0x5eedull, nullptr) != cudaSuccess) rc = cuda_fail(p, cudaGetLastError(), "trial rhs");
+  for (const AuxCand& c : kAuxCandidates) {
+    if (rc) break;
+    if ((rc = apply_aux(p, c.rho, c.q))) break;
+    if ((rc = solve_core(p, tf, kInC128, tu, kOutC128, 0.0, nullptr, nullptr, nullptr, nullptr))) break;
+    int64_t nb = 0;
+    cudaError_t e = launch_residual(p->dim, p->n, p->h, p->omega, tf, tu, tr, ts, &nb, nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(hs.data(), ts, nb * 2 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(p, e, "auxiliary trial");
+      break;
+    }
+    double r2 = 0, f2 = 0;
+    for (int64_t i = 0; i < nb; ++i) {
+      r2 += hs[2 * i];
+      f2 += hs[2 * i + 1];
+    }
+    const double rel = f2 > 0 ? std::sqrt(r2 / f2) : HUGE_VAL;
+    if (rel < best) {
+      best = rel;
+      pick = c;
+    }
+  }
+  if (!rc) rc = apply_aux(p, pick.rho, pick.q);
+  p->stream = saved;
+  p->aux_trial_resid = best;
+  cleanup();
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -701,6 +804,7 @@ int helm_plan_2d(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy,
   int rc = build_axis(p, p->axo, ny, hy, omega, kDefaultAuxRho, kDefaultAuxQ);
   if (!rc) rc = alloc_buffers_2d(p);
   if (!rc) rc = alloc_refine(p);
+  if (!rc) rc = tune_auxiliary(p);
   if (rc) {
     destroy_plan(p);
     return rc;
@@ -756,6 +860,7 @@ int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx
     else if (ce != cudaSuccess) rc = cuda_fail(p, ce, "plan3d_init");
   }
   if (!rc) rc = alloc_refine(p);
+  if (!rc) rc = tune_auxiliary(p);
   if (rc) {
     destroy_plan(p);
     return rc;
@@ -768,22 +873,8 @@ int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx
 int helm_set_auxiliary(helm_plan_t p, double rho, int phase_quarters) {
   if (!p || !std::isfinite(rho) || rho < 0.0 || rho > 8.0) return HELM_EINVAL;
   HELM_CK(cudaStreamSynchronize(p->stream));
-  drop_refine_graph(p);  // its kernels hold the old eigen-data
-  int rc = build_axis_aux(p, p->axo, rho, phase_quarters);
-  if (!rc && p->dim == 3) rc = build_axis_aux(p, p->axi, rho, phase_quarters);
-  if (rc) return rc;
-  if (p->dim == 2) {
-    const Solve2DArgs a = args2d(p);
-    HELM_CK(launch_pivots(p->prec, p->ustartB, a, 1, nullptr));
-    if (p->constB) HELM_CK(launch_line_consts(p->prec, p->constB, a, 1, nullptr));
-    if (p->tabB)
-      HELM_CK(p->prec == kPrecF64 ? launch_line_tables(p->tabB, a, 1, nullptr)
-                                  : launch_line_tables32(p->tabB, a, 1, nullptr));
-    HELM_CK(cudaDeviceSynchronize());
-  } else {
-    HELM_CK(plan3d_tables(p->p3));
-  }
-  return HELM_OK;
+  p->aux_trial_resid = -1.0;  // chosen by the caller, not by the plan's trials
+  return apply_aux(p, rho, phase_quarters);
 }
 
 int helm_set_stream(helm_plan_t p, void* s) {
@@ -856,6 +947,15 @@ int helm_get_info(helm_plan_t p, helm_info* info) {
   info->n_dft_stages = p->axo.dft.nstages;
   info->device_bytes = p->bytes;
   info->residual_kind = p->resid_kind;
+  info->aux_q = p->axo.q;
+  info->aux_rho = p->axo.rho;
+  info->aux_trial_residual = p->aux_trial_resid;
+  int derr = 0;
+  if (p->dev_err) HELM_CK(cudaMemcpy(&derr, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (derr) {
+    p->err = "a bounded device wait gave up (copies did not arrive)";
+    return HELM_ETIMEOUT;
+  }
   if (p->dtype == HELM_C64_REFINED && !s.converged) return HELM_ENOTCONV;
   return HELM_OK;
 }

@@ -614,18 +614,54 @@ __global__ void __launch_bounds__(TZ3* TY3) k_residual3d_ff(ResidFFArgs a, const
                                  ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
 }
 
-// f (complex128) -> float-float; u (float-float) -> complex128.
+// f (complex128) -> float-float; u (float-float) -> complex128.  Both work on
+// the bit fields with integer instructions (FP64 instructions are the scarce
+// resource here).  hi is x rounded to nearest (ties to even) float, the same
+// value as a plain conversion; lo = x - hi is the remaining signed fraction
+// (|lo| <= 2^-24 |hi|, 29 bits) rounded to float by one integer-to-float
+// conversion, so |x - (hi + lo)| <= 2^-48 |x|.  Values whose hi or lo would
+// leave the normal float range, and infinities and NaNs, take the plain
+// conversions.
+__device__ __forceinline__ void split_d(double x, float& hi, float& lo) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const uint32_t sgn = (uint32_t)(b >> 32) & 0x80000000u;
+  if (e - 948 <= 0 || e - 896 >= 254) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+    return;
+  }
+  const uint64_t m = b & 0xfffffffffffffull;
+  const uint32_t top = (uint32_t)(m >> 29), rem = (uint32_t)(m & 0x1fffffffull);
+  const bool up = rem > 0x10000000u || (rem == 0x10000000u && (top & 1u));
+  // the carry of top + 1 runs into the exponent field when the fraction is all ones
+  hi = __uint_as_float((sgn | ((uint32_t)(e - 896) << 23) | top) + (up ? 1u : 0u));
+  // x - hi = (rem - up 2^29) 2^(e - 1075), with the sign of x
+  const int32_t r = (int32_t)rem - (up ? 0x20000000 : 0);
+  const float scale = __uint_as_float((uint32_t)(e - 948) << 23);
+  lo = __uint_as_float(__float_as_uint(__int2float_rn(r) * scale) ^ sgn);
+}
+// float -> double by the bit fields (normal floats and zero; the rest converts)
+__device__ __forceinline__ double widen_f(float v) {
+  const uint32_t u = __float_as_uint(v);
+  const uint32_t e = (u >> 23) & 0xff;
+  if (e == 0 || e == 0xff) return (double)v;
+  const uint64_t b = ((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(e + 896) << 52) | ((uint64_t)(u & 0x7fffff) << 29);
+  return __longlong_as_double((long long)b);
+}
 __global__ void k_split_ff(const double2* __restrict__ f, float4* __restrict__ o, int64_t N) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const double2 v = f[i];
-    const float hx = (float)v.x, hy = (float)v.y;
-    o[i] = make_float4(hx, hy, (float)(v.x - (double)hx), (float)(v.y - (double)hy));
+    float4 q;
+    split_d(v.x, q.x, q.z);
+    split_d(v.y, q.y, q.w);
+    o[i] = q;
   }
 }
 __global__ void k_join_ff(const float4* __restrict__ q, double2* __restrict__ o, int64_t N) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const float4 v = q[i];
-    o[i] = make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+    o[i] = make_double2(widen_f(v.x) + widen_f(v.z), widen_f(v.y) + widen_f(v.w));
   }
 }
 
@@ -789,6 +825,28 @@ cudaError_t launch_join_ff(const float4* u, double2* out, int64_t N, cudaStream_
   if (N == 0) return cudaSuccess;
   const int64_t grid = std::min<int64_t>((N + 255) / 256, 152 * 16);
   k_join_ff<<<(unsigned)grid, 256, 0, st>>>(u, out, N);
+  return cudaGetLastError();
+}
+
+// Deterministic pseudo-random complex load for plan-time trials: the
+// splitmix64 finaliser of (seed, index), mapped to [-1, 1) per component.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+__global__ void k_trial_rhs(double2* __restrict__ f, int64_t N, uint64_t seed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = mix64(seed + 0x9e3779b97f4a7c15ull * (uint64_t)(2 * i + 1));
+    const uint64_t b = mix64(seed + 0x9e3779b97f4a7c15ull * (uint64_t)(2 * i + 2));
+    f[i] = make_double2((double)(a >> 11) * 0x1.0p-52 - 1.0, (double)(b >> 11) * 0x1.0p-52 - 1.0);
+  }
+}
+
+cudaError_t launch_trial_rhs(double2* f, int64_t N, uint64_t seed, cudaStream_t st) {
+  if (N == 0) return cudaSuccess;
+  const int64_t grid = std::min<int64_t>((N + 255) / 256, 152 * 16);
+  k_trial_rhs<<<(unsigned)grid, 256, 0, st>>>(f, N, seed);
   return cudaGetLastError();
 }
 

@@ -55,9 +55,10 @@ cudaError_t launch_tri2d_tab(int step, const void* fhat, const void* faces, cons
 // constants): table memory per line type, building it, and the step launch.
 size_t line_tables32_bytes(int64_t nx, int64_t n1, int64_t nchunks);
 cudaError_t launch_line_tables32(void* tables, const Solve2DArgs& a, int step, cudaStream_t st);
+// err: device error word (bounded waits of the bulk-copy fed kernels).
 cudaError_t launch_tri2d_t32(int step, const void* fhat, const void* faces, const void* tables, void* rec, void* out,
                              void* partial, const Solve2DArgs& a, const int* skip, cudaStream_t st, Profiler* prof,
-                             const void* consts);
+                             const void* consts, int* err);
 size_t chunk_record_bytes(int prec);
 // out[face][ix] = scale_face * sum_w partial (complex scales, face 0 then 1).
 cudaError_t launch_reduce_faces(int prec, const void* partial, void* out, int64_t nx, int64_t nwarps,
@@ -93,6 +94,8 @@ cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, doubl
 // complex128 -> float-float (hi = round(x), lo = round(x - hi)) and back.
 cudaError_t launch_split_ff(const double2* f, float4* out, int64_t N, cudaStream_t st);
 cudaError_t launch_join_ff(const float4* u, double2* out, int64_t N, cudaStream_t st);
+// Deterministic pseudo-random complex128 vector (plan-time trials).
+cudaError_t launch_trial_rhs(double2* f, int64_t N, uint64_t seed, cudaStream_t st);
 // Number of per-block sums launch_residual writes for this grid.
 int64_t residual_blocks(int dim, const int64_t* n);
 // Reduce the block sums, record ||r||/||f|| as the next residual of *state,

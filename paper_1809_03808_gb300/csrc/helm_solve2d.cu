@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "helm_dft.h"
+#include "helm_async.cuh"
 #include "helm_kernels.cuh"
 #include "helm_solve.h"
 
@@ -355,13 +356,15 @@ __device__ __forceinline__ void block_face_sums(C* red, int cnt, C* __restrict__
                                                 int64_t nparts, int64_t nx, int64_t row0) {
   __shared__ C seg[2 * CH * 8];
   __syncthreads();
-  // stage 1: thread -> (sum index q = face * CH + t, segment g of 16 lines)
+  // stage 1: thread -> (sum index q = face * CH + t, residue class g of the
+  // lines mod 8: lines g, g + 8, ..., g + 120), so that the threads of a warp
+  // read consecutive words (no bank conflicts)
   for (int w = threadIdx.x; w < 2 * CH * 8; w += blockDim.x) {
     const int q = w >> 3, g = w & 7;
-    const C* src = red + q * 128 + g * 16;
+    const C* src = red + q * 128 + g;
     C acc = src[0];
 #pragma unroll
-    for (int i = 1; i < 16; ++i) acc = cadd(acc, src[i]);
+    for (int i = 1; i < 16; ++i) acc = cadd(acc, src[8 * i]);
     seg[w] = acc;
   }
   __syncthreads();
@@ -785,6 +788,174 @@ __global__ void __launch_bounds__(128) k_tri_pass2_t32(const float2* __restrict_
   if (STEP != 3) block_face_sums<C, CH>(red, cnt, partial, (int64_t)blockIdx.x, nparts, nx, s);
 }
 
+// ---------------------------------------------------------------------------
+// complex64 chunk passes fed by bulk copies.  A CTA owns 128 consecutive lines
+// and a run of kBulkChunks consecutive chunks.  Its tiles (the chunk's rows of
+// f_hat and of the pivot table, 1 KB per row and array) arrive in shared
+// memory by cp.async.bulk into two buffers: while the CTA computes chunk k,
+// the copies of chunk k+1 are in flight, so the memory system is kept busy
+// without holding the tiles in registers.  Same arithmetic as
+// k_tri_pass1_t32 / k_tri_pass2_t32.  Needs 16-byte aligned rows (even n1).
+// ---------------------------------------------------------------------------
+constexpr int kBulkLines = 128;
+constexpr int kBulkChunks = 8;
+
+template <int CH>
+constexpr size_t bulk_tile_bytes() {
+  return (size_t)2 * 2 * CH * kBulkLines * sizeof(float2);  // [buffer][array][row][line]
+}
+
+template <int PASS, int STEP, int CH>
+__global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __restrict__ fhat,
+                                                             const float2* __restrict__ faces, LineTables32 tb,
+                                                             RecSoA<float2> rec, float2* __restrict__ out,
+                                                             float2* __restrict__ partial, Solve2DArgs a,
+                                                             const void* __restrict__ consts,
+                                                             const int* __restrict__ skip, int* __restrict__ err) {
+  using C = float2;
+  constexpr int TILE = 2 * CH * kBulkLines;  // values per buffer
+  constexpr bool RHS = STEP != 2;            // Step 2 takes its rhs from the face vectors
+  if (skip && *skip) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  C* const tile = reinterpret_cast<C*>(smem_raw);
+  __shared__ __align__(8) uint64_t bar[2];
+  const int64_t n1 = a.n1, nx = a.nx;
+  const int64_t l0 = (int64_t)blockIdx.x * kBulkLines;
+  const int nl = (int)min((int64_t)kBulkLines, n1 - l0);
+  const int64_t kb = (int64_t)blockIdx.y * kBulkChunks, ke = min(kb + (int64_t)kBulkChunks, a.nchunks);
+  const int tid = threadIdx.x;
+  const bool act = tid < nl;
+  const int64_t l = l0 + (act ? tid : 0);
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  // thread 0: the copies of chunk k into buffer bsel
+  auto issue = [&](int64_t k, int bsel) {
+    const int64_t s = k * CH;
+    const int cnt = (int)min((int64_t)CH, nx - s);
+    const uint32_t row_bytes = (uint32_t)nl * (uint32_t)sizeof(C);
+    mbar_arrive_expect_tx(&bar[bsel], (uint32_t)cnt * row_bytes * (RHS ? 2u : 1u));
+    C* buf = tile + bsel * TILE;
+    for (int t = 0; t < cnt; ++t) {
+      if (RHS) bulk_g2s(buf + t * kBulkLines, fhat + (s + t) * n1 + l0, row_bytes, &bar[bsel]);
+      bulk_g2s(buf + (CH + t) * kBulkLines, tb.iu + (s + t) * n1 + l0, row_bytes, &bar[bsel]);
+    }
+  };
+  // thread 0's book of copies in flight: buffer busy, parity of its phase
+  bool pending[2] = {false, false};
+  uint32_t want[2] = {0, 0};
+  if (tid == 0) {
+    issue(kb, 0);
+    pending[0] = true;
+    if (kb + 1 < ke) {
+      issue(kb + 1, 1);
+      pending[1] = true;
+    }
+  }
+  const LineValues<float, C> lv = line_values<float>(STEP, a, l, consts);
+  const C b = lv.co.b, mb = mk<C>(-b.x, -b.y);
+  const C* f1 = faces;
+  const C* fn = faces + nx;
+  const C zero = mk<C>(0, 0);
+  const int64_t nparts = (n1 + kBulkLines - 1) / kBulkLines;
+  C iprev = (PASS == 2 && kb > 0) ? tb.iu[(kb * CH - 1) * n1 + l] : zero;  // 1/u of the row before the run
+  bool failed = false;
+  for (int64_t k = kb; k < ke; ++k) {
+    const int bsel = (int)((k - kb) & 1);
+    const uint32_t parity = (uint32_t)(((k - kb) >> 1) & 1);
+    const int64_t s = k * CH;
+    const int cnt = (int)min((int64_t)CH, nx - s);
+    C yp = zero, xn = zero;
+    if (PASS == 2) {
+      yp = rec.a[k * n1 + l];     // Y(k-1)
+      xn = rec.bsum[k * n1 + l];  // X(k+1)
+    }
+    const bool got = mbar_wait_bounded(&bar[bsel], parity, err);
+    if (__syncthreads_or(!got)) {  // block-uniform decision
+      failed = true;
+      break;
+    }
+    if (tid == 0) pending[bsel] = false;
+    C* const frow = tile + bsel * TILE;      // [CH][128] f_hat rows
+    C* const irow = frow + CH * kBulkLines;  // [CH][128] 1/u rows
+    auto rhs = [&](int t) -> C {
+      const int64_t j = s + t;
+      if (STEP == 1) return cmul(frow[t * kBulkLines + tid], lv.scal);
+      if (STEP == 2) return cadd(f1[j], cscale(fn[j], lv.par));
+      C v = cadd(frow[t * kBulkLines + tid], f1[j]);
+      v = cadd(v, cmul(fn[j], lv.wl));
+      return cmul(v, lv.scal);
+    };
+    if (PASS == 1) {
+      C ylo = rhs(0), w = irow[tid];
+      C bsum = cmul(w, ylo);
+#pragma unroll
+      for (int t = 1; t < CH; ++t) {
+        if (t >= cnt) break;
+        const C m = cmul(b, irow[(t - 1) * kBulkLines + tid]);
+        ylo = csub(rhs(t), cmul(m, ylo));
+        w = cmul(cmul(w, mb), irow[t * kBulkLines + tid]);
+        bsum = cadd(bsum, cmul(w, ylo));
+      }
+      if (act) {
+        rec.a[k * n1 + l] = ylo;
+        rec.bsum[k * n1 + l] = bsum;
+      }
+    } else {
+      C y[CH];
+#pragma unroll
+      for (int t = 0; t < CH; ++t) {
+        if (t < cnt) {
+          yp = csub(rhs(t), cmul(cmul(b, iprev), yp));
+          y[t] = yp;
+          iprev = irow[t * kBulkLines + tid];
+        }
+      }
+      // backward sweep; Steps 1, 2 put their face contributions over the
+      // consumed tile (each thread only rewrites its own column)
+      C* const red = frow;  // [2][CH][128]
+#pragma unroll
+      for (int t = CH - 1; t >= 0; --t) {
+        if (t < cnt) {
+          const C x = cmul(csub(y[t], cmul(b, xn)), irow[t * kBulkLines + tid]);
+          xn = x;
+          if (STEP == 3) {
+            if (act) out[(s + t) * n1 + l] = x;
+          } else {
+            C s1, sn;
+            if (STEP == 1) {
+              s1 = act ? x : zero;
+              sn = act ? cmul(x, lv.twl) : zero;
+            } else {
+              const C tt = act ? cmul(x, lv.sig) : zero;
+              s1 = tt;
+              sn = cscale(tt, lv.par);
+            }
+            red[t * kBulkLines + tid] = s1;
+            red[(CH + t) * kBulkLines + tid] = sn;
+          }
+        }
+      }
+      if (STEP != 3) block_face_sums<C, CH>(red, cnt, partial, (int64_t)blockIdx.x, nparts, nx, s);
+    }
+    __syncthreads();  // the buffer is consumed: it may be refilled
+    if (tid == 0 && k + 2 < ke) {
+      issue(k + 2, bsel);
+      pending[bsel] = true;
+      want[bsel] = parity ^ 1u;
+    }
+  }
+  if (failed && tid == 0) {
+    // let the copies still in flight land (bounded) before the CTA's shared
+    // memory is released
+    for (int bsel = 0; bsel < 2; ++bsel)
+      if (pending[bsel]) mbar_wait_bounded(&bar[bsel], want[bsel], nullptr);
+  }
+}
+
 // Pivot entering each chunk, u_{kCH-1}, for every line: FP64 sequential
 // recurrence once per plan (same sequence as plain Thomas).
 template <typename T>
@@ -954,7 +1125,7 @@ cudaError_t launch_tri2d_tab(int step, const void* fhat, const void* faces, cons
 
 cudaError_t launch_tri2d_t32(int step, const void* fhat, const void* faces, const void* tables, void* rec, void* out,
                              void* partial, const Solve2DArgs& a, const int* skip, cudaStream_t st, Profiler* prof,
-                             const void* consts) {
+                             const void* consts, int* err) {
   static const char* n1s[3] = {"tri_step1_pass1", "tri_step2_pass1", "tri_step3_pass1"};
   static const char* ncs[3] = {"tri_step1_carry", "tri_step2_carry", "tri_step3_carry"};
   static const char* n2s[3] = {"tri_step1_pass2", "tri_step2_pass2", "tri_step3_pass2"};
@@ -969,8 +1140,34 @@ cudaError_t launch_tri2d_t32(int step, const void* fhat, const void* faces, cons
   r.pe = tb.pe;  // rhs-independent chunk constants live in the tables
   r.cc = tb.cc;
   r.we = tb.we;
+  // even n1: 16-byte aligned rows, the bulk-copy fed kernels
+  const bool bulk = (a.n1 % 2) == 0;
+  const dim3 gbulk((unsigned)((a.n1 + kBulkLines - 1) / kBulkLines),
+                   (unsigned)((a.nchunks + kBulkChunks - 1) / kBulkChunks));
+  const size_t sbulk = bulk_tile_bytes<kChunkF32>();
 #define HELM_TRI_T32(S)                                                                                        \
   do {                                                                                                        \
+    if (bulk) {                                                                                               \
+      auto k1 = k_tri_bulk_t32<1, S, kChunkF32>;                                                              \
+      auto k2 = k_tri_bulk_t32<2, S, kChunkF32>;                                                              \
+      cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbulk);                     \
+      cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbulk);                     \
+      {                                                                                                       \
+        ProfScope ps(prof, n1s[S - 1], st);                                                                   \
+        k1<<<gbulk, kBulkLines, sbulk, st>>>((const float2*)fhat, (const float2*)faces, tb, r, nullptr, nullptr, \
+                                             a, consts, skip, err);                                           \
+      }                                                                                                       \
+      {                                                                                                       \
+        ProfScope ps(prof, ncs[S - 1], st);                                                                   \
+        k_tri_carry<float><<<gcar, bcar, 0, st>>>(r, a.n1, a.nchunks, skip);                                  \
+      }                                                                                                       \
+      {                                                                                                       \
+        ProfScope ps(prof, n2s[S - 1], st);                                                                   \
+        k2<<<gbulk, kBulkLines, sbulk, st>>>((const float2*)fhat, (const float2*)faces, tb, r, (float2*)out,  \
+                                             (float2*)partial, a, consts, skip, err);                         \
+      }                                                                                                       \
+      break;                                                                                                  \
+    }                                                                                                         \
     {                                                                                                         \
       ProfScope ps(prof, n1s[S - 1], st);                                                                     \
       k_tri_pass1_t32<S, kChunkF32><<<grid, bs, 0, st>>>((const float2*)fhat, (const float2*)faces, tb, r, a, \

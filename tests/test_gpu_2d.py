@@ -48,6 +48,11 @@ CASES = {
     "tall_300x64": _case((300, 64), (3.0, 0.63), ppw=12),
     "wide_17x512": _case((17, 512), (0.1, 3.0), ppw=10),
     "pow2_256x128_x1_3x43": _case((256, 129), (2.0, 1.0), ppw=10),
+    # power-of-two x1 lengths: compile-time-radix transforms with 1..3 passes
+    "pow2_6x32": _case((6, 32), (0.5, 1.0), ppw=8),
+    "pow2_5x256": _case((5, 256), (0.1, 2.0), ppw=10),
+    "pow2_7x2048": _case((7, 2048), (0.1, 8.0), ppw=10),
+    "pow2_4x4096": _case((4, 4096), (0.05, 10.0), ppw=12),
 }
 
 

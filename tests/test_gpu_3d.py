@@ -41,6 +41,11 @@ CASES = {
     "primes_13x11x7": _case((13, 11, 7), (1.0, 1.0, 1.0), ppw=5),
     "cube_17": _case((17, 17, 17), (1.0, 1.0, 1.0), ppw=8),
     "flat_40x16x8": _case((40, 16, 8), (2.0, 0.75, 0.35), ppw=10),
+    # power-of-two periodic axes: the compile-time-radix row (z) and column
+    # (y) transforms with one, two and three passes
+    "pow2_4x32x64": _case((4, 32, 64), (0.3, 1.0, 2.0), ppw=10),
+    "pow2_3x256x16": _case((3, 256, 16), (0.2, 3.0, 0.5), ppw=10),
+    "pow2_4x16x512": _case((4, 16, 512), (0.3, 0.5, 5.0), ppw=10),
 }
 
 
