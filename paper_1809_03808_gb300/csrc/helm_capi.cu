@@ -693,9 +693,10 @@ int apply_aux(helm_plan* p, double rho, int phase_quarters) {
 // errors of a solve grow with the conditioning of B's own problems, which
 // depends on where the grid's modes fall relative to w^2: no fixed (rho, q)
 // suits every grid.  Each candidate gets one solve, in the plan's precision,
-// of a fixed pseudo-random load f; the candidate with the smallest relative
-// residual ||f - A u|| / ||f|| (FP64, eq. A2D / A3D) is kept.  For the
-// refined mode that residual is the contraction factor of one sweep.
+// of a fixed pseudo-random load f (refined plans: and one correction sweep);
+// the candidate with the smallest relative residual ||f - A u|| / ||f||
+// (FP64, eq. A2D / A3D) is kept.  For refined plans that residual is the
+// product of the first two contraction factors of the refinement.
 struct AuxCand {
   double rho;
   int q;
@@ -743,6 +744,12 @@ int tune_auxiliary(helm_plan* p) {
     if ((rc = solve_core(p, tf, kInC128, tu, kOutC128, 0.0, nullptr, nullptr, nullptr, nullptr))) break;
     int64_t nb = 0;
     cudaError_t e = launch_residual(p->dim, p->n, p->h, p->omega, tf, tu, tr, ts, &nb, nullptr, nullptr);
+    if (e == cudaSuccess && p->dtype == HELM_C64_REFINED) {
+      // refined plans: one correction sweep as well, so that the residual
+      // measures the contraction of the sweeps, not only the first solve
+      if ((rc = solve_core(p, tr, kInC64, tu, kOutAccumC128, 1.0, nullptr, nullptr, nullptr, nullptr))) break;
+      e = launch_residual(p->dim, p->n, p->h, p->omega, tf, tu, tr, ts, &nb, nullptr, nullptr);
+    }
     if (e == cudaSuccess) e = cudaMemcpy(hs.data(), ts, nb * 2 * sizeof(double), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) {
       rc = cuda_fail(p, e, "auxiliary trial");

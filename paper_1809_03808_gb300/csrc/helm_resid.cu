@@ -471,8 +471,33 @@ __device__ __forceinline__ void block_norm_sums(float r2f, float f2f, double* __
   }
 }
 
-// 2D: same traversal as k_residual2d (thread per y column, RX2 rows rolling).
-__global__ void __launch_bounds__(256, 3) k_residual2d_ff(ResidFFArgs a, ResidArgs ad, const float4* __restrict__ f,
+// 2D: thread per y column, RX2 rows rolling along x.  Away from the
+// perimeter the nine coefficients of eq. A2D take four values (centre, x
+// pair, y pair, corners), so the neighbours are first summed in float-float,
+// with the y-pair sum of each row reused for the corners of the next rows:
+// three float-float sums and four products per component.  Perimeter points
+// (0.07% of the 2D workload) form their complex corner entries in FP64.
+__device__ __forceinline__ float4 perimeter_ff(const ResidArgs& ad, const float4* __restrict__ u, int64_t ix,
+                                               int64_t iy) {
+  const int64_t nx = ad.ax[0].n, ny = ad.ax[1].n;
+  float4 au = make_float4(0, 0, 0, 0);
+  for (int dx = -1; dx <= 1; ++dx) {
+    if (ix + dx < 0 || ix + dx >= nx) continue;
+    double m0, k0r, k0i;
+    entries(ad.ax[0], ix, dx, ad.omega, m0, k0r, k0i);
+    for (int dy = -1; dy <= 1; ++dy) {
+      if (iy + dy < 0 || iy + dy >= ny) continue;
+      double m1, k1r, k1i;
+      entries(ad.ax[1], iy, dy, ad.omega, m1, k1r, k1i);
+      const double cre = k0r * m1 + m0 * k1r - ad.omega * ad.omega * m0 * m1;
+      const double cim = k0i * m1 + m0 * k1i;
+      ffc_mac_c(au, ff_split(cre), ff_split(cim), __ldg(&u[(ix + dx) * ny + iy + dy]));
+    }
+  }
+  return au;
+}
+
+__global__ void __launch_bounds__(256) k_residual2d_ff(ResidFFArgs a, ResidArgs ad, const float4* __restrict__ f,
                                                        const float4* __restrict__ u, float2* __restrict__ r,
                                                        double* __restrict__ sums, const int* __restrict__ skip) {
   if (skip && *skip) return;
@@ -481,49 +506,36 @@ __global__ void __launch_bounds__(256, 3) k_residual2d_ff(ResidFFArgs a, ResidAr
   const int64_t x0 = (int64_t)blockIdx.y * RX2;
   float r2f = 0.f, f2f = 0.f;
   if (iy < ny) {
-    const bool ym = iy > 0, yp = iy < ny - 1;
     const float4 z4 = make_float4(0, 0, 0, 0);
-    auto ld = [&](int64_t ix, int64_t jy) -> float4 { return (ix >= 0 && ix < nx) ? __ldg(&u[ix * ny + jy]) : z4; };
-    float4 w[3][3];
-    for (int d = 0; d < 2; ++d) {
-      const int64_t ix = x0 - 1 + d;
-      w[d][0] = ym ? ld(ix, iy - 1) : z4;
-      w[d][1] = ld(ix, iy);
-      w[d][2] = yp ? ld(ix, iy + 1) : z4;
-    }
+    const bool ycol = iy > 0 && iy < ny - 1;  // interior column
+    // interior coefficients [dx+1][dy+1]: centre (1,1), x pair (0,1), y pair (1,0), corners (0,0)
+    const FF2 cc = a.cin[4], cxp = a.cin[1], cyp = a.cin[3], ccn = a.cin[0];
+    auto ldc = [&](int64_t ix) -> float4 { return (ix >= 0 && ix < nx) ? __ldg(&u[ix * ny + iy]) : z4; };
+    auto ldp = [&](int64_t ix) -> float4 {  // u(ix, iy-1) + u(ix, iy+1) in float-float
+      if (ix < 0 || ix >= nx || !ycol) return z4;
+      return ffc_add(__ldg(&u[ix * ny + iy - 1]), __ldg(&u[ix * ny + iy + 1]));
+    };
+    float4 cm = ldc(x0 - 1), c0 = ldc(x0);
+    float4 pm = ldp(x0 - 1), p0 = ldp(x0);
     const int64_t x1 = min(x0 + RX2, nx);
     for (int64_t ix = x0; ix < x1; ++ix) {
-      w[2][0] = ym ? ld(ix + 1, iy - 1) : z4;
-      w[2][1] = ld(ix + 1, iy);
-      w[2][2] = yp ? ld(ix + 1, iy + 1) : z4;
-      float4 au = z4;
-      const bool interior = ix > 0 && ix < nx - 1 && iy > 0 && iy < ny - 1;
-      if (interior) {
-#pragma unroll
-        for (int dx = 0; dx < 3; ++dx)
-#pragma unroll
-          for (int dy = 0; dy < 3; ++dy) ffc_mac_r(au, a.cin[dx * 3 + dy], w[dx][dy]);
-      } else {
-        // perimeter: the complex corner entries, formed in FP64 and split
-        for (int dx = -1; dx <= 1; ++dx) {
-          double m0, k0r, k0i;
-          entries(ad.ax[0], ix, dx, ad.omega, m0, k0r, k0i);
-          for (int dy = -1; dy <= 1; ++dy) {
-            double m1, k1r, k1i;
-            entries(ad.ax[1], iy, dy, ad.omega, m1, k1r, k1i);
-            const double cre = k0r * m1 + m0 * k1r - ad.omega * ad.omega * m0 * m1;
-            const double cim = k0i * m1 + m0 * k1i;
-            ffc_mac_c(au, ff_split(cre), ff_split(cim), w[dx + 1][dy + 1]);  // zero outside the domain
-          }
-        }
-      }
+      const float4 cp = ldc(ix + 1), pp = ldp(ix + 1);
       const float4 fv = __ldg(&f[ix * ny + iy]);
-      r[ix * ny + iy] = ff_resid(fv, au, r2f, f2f);
-#pragma unroll
-      for (int dy = 0; dy < 3; ++dy) {
-        w[0][dy] = w[1][dy];
-        w[1][dy] = w[2][dy];
+      float4 au;
+      if (ycol && ix > 0 && ix < nx - 1) {
+        au = z4;
+        ffc_mac_r(au, cc, c0);
+        ffc_mac_r(au, cxp, ffc_add(cm, cp));
+        ffc_mac_r(au, cyp, p0);
+        ffc_mac_r(au, ccn, ffc_add(pm, pp));
+      } else {
+        au = perimeter_ff(ad, u, ix, iy);
       }
+      r[ix * ny + iy] = ff_resid(fv, au, r2f, f2f);
+      cm = c0;
+      c0 = cp;
+      pm = p0;
+      p0 = pp;
     }
   }
   block_norm_sums<8>(r2f, f2f, sums, (int64_t)blockIdx.y * gridDim.x + blockIdx.x);

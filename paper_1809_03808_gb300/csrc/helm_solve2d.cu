@@ -354,26 +354,27 @@ __global__ void __launch_bounds__(kCarryLines* kCarrySeg)
 template <typename C, int CH>
 __device__ __forceinline__ void block_face_sums(C* red, int cnt, C* __restrict__ partial, int64_t blk,
                                                 int64_t nparts, int64_t nx, int64_t row0) {
-  __shared__ C seg[2 * CH * 8];
+  constexpr int NQ = 2 * CH;    // sums: face * CH + row
+  constexpr int SP = NQ + 1;    // padded stride of the segment sums
+  __shared__ C seg[16 * SP];
   __syncthreads();
-  // stage 1: thread -> (sum index q = face * CH + t, residue class g of the
-  // lines mod 8: lines g, g + 8, ..., g + 120), so that the threads of a warp
-  // read consecutive words (no bank conflicts)
-  for (int w = threadIdx.x; w < 2 * CH * 8; w += blockDim.x) {
-    const int q = w >> 3, g = w & 7;
+  // stage 1: thread -> (sum q, segment g of 8 consecutive lines, lines g, g+16,
+  // ..., g+112); a half-warp reads 16 consecutive values (no bank conflicts)
+  for (int w = threadIdx.x; w < NQ * 16; w += blockDim.x) {
+    const int q = w >> 4, g = w & 15;
     const C* src = red + q * 128 + g;
     C acc = src[0];
 #pragma unroll
-    for (int i = 1; i < 16; ++i) acc = cadd(acc, src[8 * i]);
-    seg[w] = acc;
+    for (int i = 1; i < 8; ++i) acc = cadd(acc, src[16 * i]);
+    seg[g * SP + q] = acc;
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < 2 * CH; q += blockDim.x) {
+  for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
     const int face = q / CH, t = q - face * CH;
     if (t >= cnt) continue;
-    C acc = seg[q * 8];
+    C acc = seg[q];
 #pragma unroll
-    for (int g = 1; g < 8; ++g) acc = cadd(acc, seg[q * 8 + g]);
+    for (int g = 1; g < 16; ++g) acc = cadd(acc, seg[g * SP + q]);
     partial[(face * nparts + blk) * nx + row0 + t] = acc;
   }
 }
