@@ -292,7 +292,7 @@ int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int 
   const double en_n1[2] = {ax.en[0] / (double)n1, ax.en[1] / (double)n1};
   const int64_t nparts = (n1 + 127) / 128;  // face partials: one per block of 128 lines
   HELM_PK("dft_fwd", launch_dft_rows(prec, in, in_is_double, p->fhat, fhat_mode, nx, ax.dft, tw, -1, 1.0, 0.0, sci,
-                                     nullptr, skip, st));
+                                     nullptr, skip, st, p->dev_err));
   if (dbg_fhat) HELM_CK(cudaMemcpyAsync(dbg_fhat, p->fhat, nx * n1 * cb, cudaMemcpyDeviceToDevice, st));
   // a2: Step 1
   if (p->tabB && prec == kPrecF64)

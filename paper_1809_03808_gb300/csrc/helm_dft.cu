@@ -280,10 +280,10 @@ bool dft_supported(const DftPlan& p, size_t elem_bytes, int max_smem) {
 cudaError_t launch_dft_rows(int prec, const void* in, int in_is_double, void* out, int out_mode,
                             int64_t nrows, const DftPlan& p, const void* tw, int sign, double scale,
                             double accum_scale, const void* sc_in, const void* sc_out, const int* skip,
-                            cudaStream_t st) {
+                            cudaStream_t st, int* err) {
   if (dft_rows_pow2_supported(p.n))
     return launch_dft_rows_pow2(prec, in, in_is_double, out, out_mode, nrows, p.n, tw, sign, scale, accum_scale,
-                                sc_in, sc_out, skip, st);
+                                sc_in, sc_out, skip, st, err);
   const size_t es = prec == kPrecF64 ? sizeof(double2) : sizeof(float2);
   // lines per CTA: enough points to keep 256 threads busy, bounded by smem
   int L = (int)std::max<int64_t>(1, std::min<int64_t>(nrows, 2048 / std::max(1, p.n)));

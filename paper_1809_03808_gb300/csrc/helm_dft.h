@@ -27,17 +27,21 @@ bool dft_supported(const DftPlan& p, size_t elem_bytes, int max_smem);
 // sc_in / sc_out: optional per-point complex factors (length p.n, compute
 // precision) applied to the input before and to the output after the
 // transform: the diagonal scalings of the gamma-circulant auxiliary.
+// err: optional device error word; when given, complex64 input lines of 4096
+// or 8192 points use a persistent kernel fed by bulk copies with bounded
+// waits, which report there.
 cudaError_t launch_dft_rows(int prec, const void* in, int in_is_double, void* out, int out_mode,
                             int64_t nrows, const DftPlan& p, const void* tw, int sign, double scale,
                             double accum_scale, const void* sc_in, const void* sc_out, const int* skip,
-                            cudaStream_t st);
+                            cudaStream_t st, int* err = nullptr);
 
 // Power-of-two lines (16 <= n <= 8192) along the contiguous axis: the same
 // contract as launch_dft_rows with the radices fixed at compile time.
 bool dft_rows_pow2_supported(int64_t n);
 cudaError_t launch_dft_rows_pow2(int prec, const void* in, int in_is_double, void* out, int out_mode, int64_t nrows,
                                  int64_t n, const void* tw, int sign, double scale, double accum_scale,
-                                 const void* sc_in, const void* sc_out, const int* skip, cudaStream_t st);
+                                 const void* sc_in, const void* sc_out, const int* skip, cudaStream_t st,
+                                 int* err = nullptr);
 
 // Power-of-two lines (16 <= n <= 1024) along a middle axis: the contract of
 // launch_dft_cols with compile-time radices; in place (out == in) allowed.

@@ -11,6 +11,9 @@
 // directly; the passes in between exchange through shared memory padded by
 // one point per 16 so that both the strided writes and the unit-stride reads
 // are free of bank conflicts.
+#include <algorithm>
+
+#include "helm_async.cuh"
 #include "helm_dft.h"
 #include "helm_kernels.cuh"
 
@@ -453,6 +456,118 @@ cudaError_t launch_cols_pow2_s(int log2n, const void* in, int in_is_double, void
 #undef HELM_COLS2
 }
 
+// Persistent variant for complex64 lines of 4096 or 8192 points: each CTA
+// loops over lines (row = blockIdx.x + i gridDim.x) and the next line
+// arrives in shared memory by one cp.async.bulk while the current one is
+// transformed (two input buffers, mbarrier completion, bounded waits).  The
+// passes, the twiddles and the epilogue are those of k_dft_rows_pow2.
+template <int LOG2N, int SIGN>
+__global__ void __launch_bounds__(pow2_threads<LOG2N>())
+    k_dft_rows_pow2_bulk(const float2* __restrict__ in, void* __restrict__ out, int out_mode, int64_t nrows,
+                         const float2* __restrict__ tw, float scale, double accum_scale,
+                         const float2* __restrict__ sc_in, const float2* __restrict__ sc_out,
+                         const int* __restrict__ skip, int* __restrict__ err) {
+  using C = float2;
+  constexpr int N = 1 << LOG2N;
+  constexpr int E = LOG2N % 4;
+  constexpr int R0 = E ? (1 << E) : 16;
+  constexpr int NP = (LOG2N + 3) / 4;
+  static_assert(pow2_threads<LOG2N>() == N / 16, "one line per CTA");
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* const inbuf = reinterpret_cast<C*>(smem_raw);  // [2][N]
+  C* const buf = inbuf + 2 * N;                      // exchange, [NPAD]
+  __shared__ __align__(8) uint64_t bar[2];
+  const int t = threadIdx.x;
+  const int64_t stride = gridDim.x;
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int64_t row, int b) {
+    mbar_arrive_expect_tx(&bar[b], (uint32_t)(N * sizeof(C)));
+    bulk_g2s(inbuf + b * N, in + row * N, (uint32_t)(N * sizeof(C)), &bar[b]);
+  };
+  // thread 0's book of copies in flight: bit b of `pending` (buffer b busy),
+  // bit b of `want` (parity of its phase)
+  uint32_t pending = 0, want = 0;
+  const int64_t r0 = blockIdx.x;
+  if (t == 0) {
+    if (r0 < nrows) {
+      issue(r0, 0);
+      pending |= 1u;
+    }
+    if (r0 + stride < nrows) {
+      issue(r0 + stride, 1);
+      pending |= 2u;
+    }
+  }
+  bool failed = false;
+  int64_t i = 0;
+  for (int64_t row = r0; row < nrows; row += stride, ++i) {
+    const int b = (int)(i & 1);
+    const uint32_t parity = (uint32_t)((i >> 1) & 1);
+    const bool got = mbar_wait_bounded(&bar[b], parity, err);
+    if (__syncthreads_or(!got)) {
+      failed = true;
+      break;
+    }
+    if (t == 0) pending &= ~(1u << b);
+    const C* src = inbuf + b * N;
+    C v[16];
+#pragma unroll
+    for (int q = 0; q < 16 / R0; ++q)
+#pragma unroll
+      for (int r = 0; r < R0; ++r) {
+        const int k = in_index<N, R0>(t, q, r);
+        C x = src[k];
+        if (sc_in) x = cmul(x, __ldg(&sc_in[k]));
+        v[q * R0 + r] = x;
+      }
+    // every thread has read this buffer (and the previous line's exchange
+    // reads are over): refill the buffer with the line after next
+    __syncthreads();
+    if (t == 0 && row + 2 * stride < nrows) {
+      issue(row + 2 * stride, b);
+      pending |= 1u << b;
+      want = (want & ~(1u << b)) | ((parity ^ 1u) << b);
+    }
+    pass_compute<C, N, R0, 1, SIGN>(v, t, tw);
+#pragma unroll
+    for (int q = 0; q < 16 / R0; ++q)
+#pragma unroll
+      for (int rp = 0; rp < R0; ++rp) buf[pad16(out_index<N, R0, 1>(t, q, rp))] = v[q * R0 + rp];
+    later_passes<float, N, SIGN, R0, NP - 1>(v, buf, t, true, row * N, out, out_mode, tw, scale, accum_scale, sc_out);
+  }
+  if (failed && t == 0) {
+    for (int b = 0; b < 2; ++b)
+      if (pending & (1u << b)) mbar_wait_bounded(&bar[b], (want >> b) & 1u, nullptr);
+  }
+}
+
+template <int LOG2N, int SIGN>
+cudaError_t launch_pow2_bulk(const void* in, void* out, int out_mode, int64_t nrows, const void* tw, double scale,
+                             double accum_scale, const void* sc_in, const void* sc_out, const int* skip, int* err,
+                             cudaStream_t st) {
+  constexpr int N = 1 << LOG2N;
+  const size_t smem = (size_t)(2 * N + N + N / 16) * sizeof(float2);
+  auto k = k_dft_rows_pow2_bulk<LOG2N, SIGN>;
+  const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, pow2_threads<LOG2N>(), smem);
+  const int64_t grid = std::min<int64_t>(nrows, (int64_t)std::max(1, nsm) * std::max(1, per_sm));
+  if (grid <= 0) return cudaSuccess;
+  k<<<(unsigned)grid, pow2_threads<LOG2N>(), smem, st>>>((const float2*)in, out, out_mode, nrows, (const float2*)tw,
+                                                         (float)scale, accum_scale, (const float2*)sc_in,
+                                                         (const float2*)sc_out, skip, err);
+  return cudaGetLastError();
+}
+
 template <typename T, int LOG2N, int SIGN>
 cudaError_t launch_pow2_t(const void* in, int in_is_double, void* out, int out_mode, int64_t nrows,
                           const void* tw, double scale, double accum_scale, const void* sc_in, const void* sc_out,
@@ -525,10 +640,22 @@ cudaError_t launch_dft_cols_pow2(int prec, const void* in, int in_is_double, voi
 
 cudaError_t launch_dft_rows_pow2(int prec, const void* in, int in_is_double, void* out, int out_mode, int64_t nrows,
                                  int64_t n, const void* tw, int sign, double scale, double accum_scale,
-                                 const void* sc_in, const void* sc_out, const int* skip, cudaStream_t st) {
+                                 const void* sc_in, const void* sc_out, const int* skip, cudaStream_t st, int* err) {
   if (!dft_rows_pow2_supported(n)) return cudaErrorInvalidValue;
   int log2n = 0;
   while ((int64_t(1) << log2n) < n) ++log2n;
+  // long complex64 lines: the persistent kernel with bulk prefetch
+  if (prec == kPrecF32 && in_is_double == kInC64 && err && (log2n == 12 || log2n == 13)) {
+    if (log2n == 12)
+      return sign < 0 ? launch_pow2_bulk<12, -1>(in, out, out_mode, nrows, tw, scale, accum_scale, sc_in, sc_out, skip,
+                                                 err, st)
+                      : launch_pow2_bulk<12, 1>(in, out, out_mode, nrows, tw, scale, accum_scale, sc_in, sc_out, skip,
+                                                err, st);
+    return sign < 0 ? launch_pow2_bulk<13, -1>(in, out, out_mode, nrows, tw, scale, accum_scale, sc_in, sc_out, skip,
+                                               err, st)
+                    : launch_pow2_bulk<13, 1>(in, out, out_mode, nrows, tw, scale, accum_scale, sc_in, sc_out, skip,
+                                              err, st);
+  }
   if (prec == kPrecF64) {
     return sign < 0 ? launch_pow2_s<double, -1>(log2n, in, in_is_double, out, out_mode, nrows, tw, scale,
                                                  accum_scale, sc_in, sc_out, skip, st)

@@ -562,16 +562,34 @@ __global__ void __launch_bounds__(TZ3* TY3) k_residual3d_ff(ResidFFArgs a, const
   const bool yend = gy == 0 || gy == ny - 1;
   float r2f = 0.f, f2f = 0.f;
   float4 PM[3] = {z4, z4, z4}, PK[3] = {z4, z4, z4};
-  for (int64_t ip = xs - 1; ip <= xe; ++ip) {
+  // the staged tile of plane ip is loaded into registers one plane ahead
+  // (each thread owns at most kStage of its points), so the loads of the next
+  // plane are in flight while the current one is computed
+  constexpr int kStage = ((TY3 + 2) * (TZ3 + 2) + TZ3 * TY3 - 1) / (TZ3 * TY3);
+  float4 nxt[kStage];
+  auto fetch = [&](int64_t ip) {
     const bool pin = ip >= 0 && ip < nx;
-    for (int e = tid; e < (TY3 + 2) * (TZ3 + 2); e += TZ3 * TY3) {
-      const int yy = e / (TZ3 + 2), zz = e - yy * (TZ3 + 2);
-      const int64_t jy = y0 - 1 + yy, jz = z0 - 1 + zz;
+#pragma unroll
+    for (int q = 0; q < kStage; ++q) {
+      const int e = tid + q * TZ3 * TY3;
       float4 v = z4;
-      if (pin && jy >= 0 && jy < ny && jz >= 0 && jz < nz) v = __ldg(&u[(ip * ny + jy) * nz + jz]);
-      sU[yy][zz] = v;
+      if (e < (TY3 + 2) * (TZ3 + 2)) {
+        const int yy = e / (TZ3 + 2), zz = e - yy * (TZ3 + 2);
+        const int64_t jy = y0 - 1 + yy, jz = z0 - 1 + zz;
+        if (pin && jy >= 0 && jy < ny && jz >= 0 && jz < nz) v = __ldg(&u[(ip * ny + jy) * nz + jz]);
+      }
+      nxt[q] = v;
+    }
+  };
+  fetch(xs - 1);
+  for (int64_t ip = xs - 1; ip <= xe; ++ip) {
+#pragma unroll
+    for (int q = 0; q < kStage; ++q) {
+      const int e = tid + q * TZ3 * TY3;
+      if (e < (TY3 + 2) * (TZ3 + 2)) sU[e / (TZ3 + 2)][e % (TZ3 + 2)] = nxt[q];
     }
     __syncthreads();
+    if (ip < xe) fetch(ip + 1);
     for (int e = tid; e < (TY3 + 2) * TZ3; e += TZ3 * TY3) {
       const int yy = e / TZ3, zc = e - yy * TZ3;
       const int64_t jz = z0 + zc;

@@ -845,15 +845,15 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
       bulk_g2s(buf + (CH + t) * kBulkLines, tb.iu + (s + t) * n1 + l0, row_bytes, &bar[bsel]);
     }
   };
-  // thread 0's book of copies in flight: buffer busy, parity of its phase
-  bool pending[2] = {false, false};
-  uint32_t want[2] = {0, 0};
+  // thread 0's book of copies in flight: bit b of `pending` (buffer b busy),
+  // bit b of `want` (parity of its phase)
+  uint32_t pending = 0, want = 0;
   if (tid == 0) {
     issue(kb, 0);
-    pending[0] = true;
+    pending |= 1u;
     if (kb + 1 < ke) {
       issue(kb + 1, 1);
-      pending[1] = true;
+      pending |= 2u;
     }
   }
   const LineValues<float, C> lv = line_values<float>(STEP, a, l, consts);
@@ -879,7 +879,7 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
       failed = true;
       break;
     }
-    if (tid == 0) pending[bsel] = false;
+    if (tid == 0) pending &= ~(1u << bsel);
     C* const frow = tile + bsel * TILE;      // [CH][128] f_hat rows
     C* const irow = frow + CH * kBulkLines;  // [CH][128] 1/u rows
     auto rhs = [&](int t) -> C {
@@ -945,15 +945,15 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
     __syncthreads();  // the buffer is consumed: it may be refilled
     if (tid == 0 && k + 2 < ke) {
       issue(k + 2, bsel);
-      pending[bsel] = true;
-      want[bsel] = parity ^ 1u;
+      pending |= 1u << bsel;
+      want = (want & ~(1u << bsel)) | ((parity ^ 1u) << bsel);
     }
   }
   if (failed && tid == 0) {
     // let the copies still in flight land (bounded) before the CTA's shared
     // memory is released
     for (int bsel = 0; bsel < 2; ++bsel)
-      if (pending[bsel]) mbar_wait_bounded(&bar[bsel], want[bsel], nullptr);
+      if (pending & (1u << bsel)) mbar_wait_bounded(&bar[bsel], (want >> bsel) & 1u, nullptr);
   }
 }
 

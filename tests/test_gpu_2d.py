@@ -235,3 +235,28 @@ def test_graph_and_eager_refinement_agree(env, kind):
         assert np.array_equal(a, b)
         if ra is not None:
             assert ra == rb
+
+
+@pytest.mark.parametrize("dtype", ["c64_refined", "c64_ff", "c64_raw"])
+def test_long_x1_complex64(env, dtype):
+    """x1 length 8192 (complex64 plans only): the persistent bulk-copy fed
+    transform of 8192-point lines against the oracle."""
+    helm, torch = env
+    shape, h, omega = _case((4, 8192), (0.05, 16.0), ppw=12)
+    f, u_ref = _oracle(shape, h, omega, seed=8192)
+    code = helm.HELM_C64_RAW if dtype == "c64_raw" else helm.HELM_C64_REFINED
+    plan = helm.Plan(shape, h, omega, code)
+    if dtype == "c64_ff":
+        helm.helm_set_residual(plan.handle, helm.HELM_RESID_FF)
+        helm.helm_set_refinement(plan.handle, 1e-12, 15)
+    tdt = torch.complex64 if dtype == "c64_raw" else torch.complex128
+    u = plan.solve(torch.from_numpy(f).to("cuda").to(tdt))
+    info, st = plan.info()
+    plan.close()
+    un = u.cpu().numpy().astype(np.complex128)
+    err = np.linalg.norm(un - u_ref) / np.linalg.norm(u_ref)
+    print(f"8192 {dtype}: rel_err={err:.3e} iters={info.iterations}")
+    if dtype == "c64_raw":
+        assert err < 5e-2
+    else:
+        assert err <= TOL and st == helm.HELM_OK
