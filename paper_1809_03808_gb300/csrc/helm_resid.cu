@@ -57,6 +57,9 @@ struct ResidFFArgs {
   double omega;
   AxisFF ax[3];
   FF2 cin[9];  // 2D interior coefficients, index (d0+1)*3 + (d1+1)
+  // 2D perimeter coefficients (complex: [0] re, [1] im) by the end class of
+  // each index (0: first, 1: inside, 2: last), index (d0+1)*3 + (d1+1)
+  FF2 per[3][3][9][2];
 };
 
 __global__ void __launch_bounds__(256) k_residual(ResidArgs a, const double2* __restrict__ f,
@@ -429,12 +432,6 @@ __device__ __forceinline__ void ffc_mac_c(float4& acc, FF2 cr, FF2 ci, float4 v)
   ff_mac(acc.y, acc.w, cr.h, cr.l, v.y, v.w);
   ff_mac(acc.y, acc.w, ci.h, ci.l, v.x, v.z);
 }
-__device__ __forceinline__ FF2 ff_split(double x) {
-  FF2 c;
-  c.h = (float)x;
-  c.l = (float)(x - (double)c.h);
-  return c;
-}
 // r = f - a, rounded to complex64; the norms' per-thread FP32 sums
 __device__ __forceinline__ float2 ff_resid(float4 fv, float4 au, float& r2f, float& f2f) {
   float dr, er, di, ei;
@@ -446,14 +443,16 @@ __device__ __forceinline__ float2 ff_resid(float4 fv, float4 au, float& r2f, flo
   return rf;
 }
 
+// Block sums of the two norms: warp stage in FP32 (the norms only decide
+// convergence; FP64 instructions are the scarce resource), block stage in FP64.
 template <int NW>
 __device__ __forceinline__ void block_norm_sums(float r2f, float f2f, double* __restrict__ sums, int64_t bid) {
   __shared__ double sr[NW], sf[NW];
-  double r2 = r2f, f2 = f2f;
   for (int off = 16; off > 0; off >>= 1) {
-    r2 += __shfl_down_sync(0xffffffffu, r2, off);
-    f2 += __shfl_down_sync(0xffffffffu, f2, off);
+    r2f += __shfl_down_sync(0xffffffffu, r2f, off);
+    f2f += __shfl_down_sync(0xffffffffu, f2f, off);
   }
+  const double r2 = r2f, f2 = f2f;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   if ((tid & 31) == 0) {
     sr[tid >> 5] = r2;
@@ -471,67 +470,40 @@ __device__ __forceinline__ void block_norm_sums(float r2f, float f2f, double* __
   }
 }
 
-// 2D: thread per y column, RX2 rows rolling along x.  Away from the
-// perimeter the nine coefficients of eq. A2D take four values (centre, x
-// pair, y pair, corners), so the neighbours are first summed in float-float,
-// with the y-pair sum of each row reused for the corners of the next rows:
-// three float-float sums and four products per component.  Perimeter points
-// (0.07% of the 2D workload) form their complex corner entries in FP64.
-__device__ __forceinline__ float4 perimeter_ff(const ResidArgs& ad, const float4* __restrict__ u, int64_t ix,
-                                               int64_t iy) {
-  const int64_t nx = ad.ax[0].n, ny = ad.ax[1].n;
-  float4 au = make_float4(0, 0, 0, 0);
-  for (int dx = -1; dx <= 1; ++dx) {
-    if (ix + dx < 0 || ix + dx >= nx) continue;
-    double m0, k0r, k0i;
-    entries(ad.ax[0], ix, dx, ad.omega, m0, k0r, k0i);
-    for (int dy = -1; dy <= 1; ++dy) {
-      if (iy + dy < 0 || iy + dy >= ny) continue;
-      double m1, k1r, k1i;
-      entries(ad.ax[1], iy, dy, ad.omega, m1, k1r, k1i);
-      const double cre = k0r * m1 + m0 * k1r - ad.omega * ad.omega * m0 * m1;
-      const double cim = k0i * m1 + m0 * k1i;
-      ffc_mac_c(au, ff_split(cre), ff_split(cim), __ldg(&u[(ix + dx) * ny + iy + dy]));
-    }
-  }
-  return au;
-}
-
-__global__ void __launch_bounds__(256) k_residual2d_ff(ResidFFArgs a, ResidArgs ad, const float4* __restrict__ f,
+// 2D, interior points (the perimeter is k_perimeter2d_ff): thread per y
+// column, RX2 rows rolling along x, rows advanced by pointer increments.  The
+// nine coefficients of eq. A2D take four values inside (centre, x pair,
+// y pair, corners), so the neighbours are first summed in float-float, with
+// the y-pair sum of each row reused for the corners of the next rows: three
+// float-float sums and four products per component.
+__global__ void __launch_bounds__(256) k_residual2d_ff(ResidFFArgs a, const float4* __restrict__ f,
                                                        const float4* __restrict__ u, float2* __restrict__ r,
                                                        double* __restrict__ sums, const int* __restrict__ skip) {
   if (skip && *skip) return;
   const int64_t nx = a.n[0], ny = a.n[1];
-  const int64_t iy = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t x0 = (int64_t)blockIdx.y * RX2;
+  const int64_t iy = 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t x0 = 1 + (int64_t)blockIdx.y * RX2;
+  const int64_t x1 = min(x0 + RX2, nx - 1);
   float r2f = 0.f, f2f = 0.f;
-  if (iy < ny) {
-    const float4 z4 = make_float4(0, 0, 0, 0);
-    const bool ycol = iy > 0 && iy < ny - 1;  // interior column
+  if (iy < ny - 1) {
     // interior coefficients [dx+1][dy+1]: centre (1,1), x pair (0,1), y pair (1,0), corners (0,0)
     const FF2 cc = a.cin[4], cxp = a.cin[1], cyp = a.cin[3], ccn = a.cin[0];
-    auto ldc = [&](int64_t ix) -> float4 { return (ix >= 0 && ix < nx) ? __ldg(&u[ix * ny + iy]) : z4; };
-    auto ldp = [&](int64_t ix) -> float4 {  // u(ix, iy-1) + u(ix, iy+1) in float-float
-      if (ix < 0 || ix >= nx || !ycol) return z4;
-      return ffc_add(__ldg(&u[ix * ny + iy - 1]), __ldg(&u[ix * ny + iy + 1]));
-    };
-    float4 cm = ldc(x0 - 1), c0 = ldc(x0);
-    float4 pm = ldp(x0 - 1), p0 = ldp(x0);
-    const int64_t x1 = min(x0 + RX2, nx);
-    for (int64_t ix = x0; ix < x1; ++ix) {
-      const float4 cp = ldc(ix + 1), pp = ldp(ix + 1);
-      const float4 fv = __ldg(&f[ix * ny + iy]);
-      float4 au;
-      if (ycol && ix > 0 && ix < nx - 1) {
-        au = z4;
-        ffc_mac_r(au, cc, c0);
-        ffc_mac_r(au, cxp, ffc_add(cm, cp));
-        ffc_mac_r(au, cyp, p0);
-        ffc_mac_r(au, ccn, ffc_add(pm, pp));
-      } else {
-        au = perimeter_ff(ad, u, ix, iy);
-      }
-      r[ix * ny + iy] = ff_resid(fv, au, r2f, f2f);
+    const float4* un = u + (x0 + 1) * ny + iy;  // row ix + 1 (exists: ix + 1 <= nx - 1)
+    const float4* fp = f + x0 * ny + iy;
+    float2* rp = r + x0 * ny + iy;
+    const float4* qm = un - 2 * ny;
+    const float4* q0 = un - ny;
+    float4 cm = __ldg(qm), pm = ffc_add(__ldg(qm - 1), __ldg(qm + 1));
+    float4 c0 = __ldg(q0), p0 = ffc_add(__ldg(q0 - 1), __ldg(q0 + 1));
+    for (int64_t ix = x0; ix < x1; ++ix, un += ny, fp += ny, rp += ny) {
+      const float4 cp = __ldg(un), pp = ffc_add(__ldg(un - 1), __ldg(un + 1));
+      const float4 fv = __ldg(fp);
+      float4 au = make_float4(0, 0, 0, 0);
+      ffc_mac_r(au, cc, c0);
+      ffc_mac_r(au, cxp, ffc_add(cm, cp));
+      ffc_mac_r(au, cyp, p0);
+      ffc_mac_r(au, ccn, ffc_add(pm, pp));
+      *rp = ff_resid(fv, au, r2f, f2f);
       cm = c0;
       c0 = cp;
       pm = p0;
@@ -539,6 +511,49 @@ __global__ void __launch_bounds__(256) k_residual2d_ff(ResidFFArgs a, ResidArgs 
     }
   }
   block_norm_sums<8>(r2f, f2f, sums, (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// 2D perimeter (rows 0 and nx-1, columns 0 and ny-1): one thread per point,
+// the complex corner entries from the float-float table of its end class.
+// Its block sums follow the interior kernel's, from sums + 2 * sum0.
+__global__ void __launch_bounds__(256) k_perimeter2d_ff(ResidFFArgs a, const float4* __restrict__ f,
+                                                        const float4* __restrict__ u, float2* __restrict__ r,
+                                                        double* __restrict__ sums, int64_t sum0,
+                                                        const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t nx = a.n[0], ny = a.n[1];
+  const int64_t P = 2 * ny + 2 * (nx - 2);
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float r2f = 0.f, f2f = 0.f;
+  if (p < P) {
+    int64_t ix, iy;
+    if (p < ny) {
+      ix = 0;
+      iy = p;
+    } else if (p < 2 * ny) {
+      ix = nx - 1;
+      iy = p - ny;
+    } else if (p < 2 * ny + nx - 2) {
+      ix = 1 + (p - 2 * ny);
+      iy = 0;
+    } else {
+      ix = 1 + (p - 2 * ny - (nx - 2));
+      iy = ny - 1;
+    }
+    const int cx = ix == 0 ? 0 : (ix == nx - 1 ? 2 : 1);
+    const int cy = iy == 0 ? 0 : (iy == ny - 1 ? 2 : 1);
+    float4 au = make_float4(0, 0, 0, 0);
+    for (int dx = -1; dx <= 1; ++dx) {
+      if (ix + dx < 0 || ix + dx >= nx) continue;
+      for (int dy = -1; dy <= 1; ++dy) {
+        if (iy + dy < 0 || iy + dy >= ny) continue;
+        const int k = (dx + 1) * 3 + (dy + 1);
+        ffc_mac_c(au, a.per[cx][cy][k][0], a.per[cx][cy][k][1], __ldg(&u[(ix + dx) * ny + iy + dy]));
+      }
+    }
+    r[ix * ny + iy] = ff_resid(__ldg(&f[ix * ny + iy]), au, r2f, f2f);
+  }
+  block_norm_sums<8>(r2f, f2f, sums, sum0 + blockIdx.x);
 }
 
 // 3D: the separable traversal of k_residual3d in float-float.
@@ -798,15 +813,11 @@ cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, doubl
                                const float4* u, float2* r, double* sums, int64_t* nblocks, const int* skip,
                                cudaStream_t st) {
   ResidFFArgs a{};
-  ResidArgs ad{};
-  a.omega = ad.omega = omega;
-  ad.dim = dim;
+  a.omega = omega;
   const double w2 = omega * omega;
   for (int k = 0; k < dim; ++k) {
     a.n[k] = n[k];
     a.h[k] = h[k];
-    ad.ax[k].n = n[k];
-    ad.ax[k].h = h[k];
     const double hk = h[k];
     AxisFF& x = a.ax[k];
     x.mdi = split_host(4.0 * hk / 6.0);
@@ -832,9 +843,40 @@ cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, doubl
       for (int d1 = 0; d1 < 3; ++d1)
         a.cin[d0 * 3 + d1] = split_host(kk[0][d0] * m[1][d1] + m[0][d0] * kk[1][d1] - w2 * m[0][d0] * m[1][d1]);
     const int bs = 256;
-    const dim3 grid((unsigned)((n[1] + bs - 1) / bs), (unsigned)((n[0] + RX2 - 1) / RX2));
-    *nblocks = (int64_t)grid.x * grid.y;
-    k_residual2d_ff<<<grid, bs, 0, st>>>(a, ad, f, u, r, sums, skip);
+    // perimeter table: entries of eqs. matrixK / matrixM at the first, an inner
+    // and the last index of each axis
+    auto ent = [&](int k, int64_t i, int d, double& m, double& kr, double& ki) {
+      const bool end = (i == 0 || i == n[k] - 1);
+      if (d == 0) {
+        m = (end ? 2.0 : 4.0) * h[k] / 6.0;
+        kr = (end ? 1.0 : 2.0) / h[k];
+        ki = end ? -omega : 0.0;
+      } else {
+        m = h[k] / 6.0;
+        kr = -1.0 / h[k];
+        ki = 0.0;
+      }
+    };
+    for (int cx = 0; cx < 3; ++cx)
+      for (int cy = 0; cy < 3; ++cy) {
+        const int64_t ix = cx == 0 ? 0 : (cx == 1 ? 1 : n[0] - 1), iy = cy == 0 ? 0 : (cy == 1 ? 1 : n[1] - 1);
+        for (int dx = -1; dx <= 1; ++dx)
+          for (int dy = -1; dy <= 1; ++dy) {
+            double m0, k0r, k0i, m1, k1r, k1i;
+            ent(0, ix, dx, m0, k0r, k0i);
+            ent(1, iy, dy, m1, k1r, k1i);
+            const int k = (dx + 1) * 3 + (dy + 1);
+            a.per[cx][cy][k][0] = split_host(k0r * m1 + m0 * k1r - w2 * m0 * m1);
+            a.per[cx][cy][k][1] = split_host(k0i * m1 + m0 * k1i);
+          }
+      }
+    const dim3 grid((unsigned)((n[1] - 2 + bs - 1) / bs), (unsigned)((n[0] - 2 + RX2 - 1) / RX2));
+    const int64_t nmain = (int64_t)grid.x * grid.y;
+    const int64_t P = 2 * n[1] + 2 * (n[0] - 2);
+    const int64_t gper = (P + bs - 1) / bs;
+    *nblocks = nmain + gper;
+    k_residual2d_ff<<<grid, bs, 0, st>>>(a, f, u, r, sums, skip);
+    k_perimeter2d_ff<<<(unsigned)gper, bs, 0, st>>>(a, f, u, r, sums, nmain, skip);
     return cudaGetLastError();
   }
   const dim3 grid((unsigned)((n[2] + TZ3 - 1) / TZ3), (unsigned)((n[1] + TY3 - 1) / TY3),
@@ -881,7 +923,12 @@ cudaError_t launch_trial_rhs(double2* f, int64_t N, uint64_t seed, cudaStream_t 
 }
 
 int64_t residual_blocks(int dim, const int64_t* n) {
-  if (dim == 2) return ((n[1] + 255) / 256) * ((n[0] + RX2 - 1) / RX2);
+  if (dim == 2) {
+    // the larger of the FP64 grid and the float-float interior + perimeter grids
+    const int64_t fp64 = ((n[1] + 255) / 256) * ((n[0] + RX2 - 1) / RX2);
+    const int64_t ff = ((n[1] - 2 + 255) / 256) * ((n[0] - 2 + RX2 - 1) / RX2) + (2 * n[1] + 2 * (n[0] - 2) + 255) / 256;
+    return std::max(fp64, ff);
+  }
   return ((n[2] + TZ3 - 1) / TZ3) * ((n[1] + TY3 - 1) / TY3) * ((n[0] + RX3 - 1) / RX3);
 }
 
