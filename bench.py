@@ -226,6 +226,8 @@ def run_gb300(args):
         __graft_entry__.build()
         import paper_1809_03808_gb300 as helm
 
+    if args.workload == "batch2d":
+        return run_batch(args, helm, torch, dev, world, rank, local)
     p = workloads.config_3d() if args.workload == "3d" else workloads.config_2d_large()
     if args.shape:
         p = workloads.scaled(p, tuple(int(x) for x in args.shape.split(",")))
@@ -415,6 +417,75 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
+def run_batch(args, helm, torch, dev, world, rank, local):
+    """The batched 2D workload (workloads.batch_2d): every problem refined in
+    complex64 with the float-float residual to ||r||/||f|| <= REFINE_TOL, all
+    solved by one helm_batch_solve (one CUDA graph launch) per step.  The same
+    plans solved one helm_solve after another are reported beside it."""
+    probs = workloads.batch_2d(args.batch_count)
+    t0 = time.perf_counter()
+    plans = []
+    for q in probs:
+        pl = helm.Plan(q.shape, q.h, q.omega, helm.HELM_C64_REFINED)
+        helm.helm_set_residual(pl.handle, helm.HELM_RESID_FF)
+        helm.helm_set_refinement(pl.handle, REFINE_TOL, 10)
+        plans.append(pl)
+    plan_s = time.perf_counter() - t0
+    fs = [torch.from_numpy(workloads.rhs(q)).to(dev) for q in probs]
+    us = [torch.empty_like(f) for f in fs]
+    N = sum(q.N for q in probs)
+    stream = torch.cuda.current_stream(dev)
+    batch = helm.Batch(plans)
+
+    def timed(step):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        clk = ClockSampler(local)
+        clk.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps, clk.stop()
+
+    ms_b, clocks = timed(lambda: batch.solve(fs, us))
+    sweeps, conv, worst = [], 0, 0.0
+    for pl in plans:
+        info, st = pl.info()
+        sweeps.append(int(info.iterations))
+        conv += int(info.converged)
+        worst = max(worst, float(info.residual[info.iterations]))
+
+    def one_by_one():
+        for pl, f, u in zip(plans, fs, us):
+            pl.solve(f, u)
+
+    ms_s, _ = timed(one_by_one)
+    batch.close()
+    line = {
+        "metric": METRIC, "value": world * N / (ms_b * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": PATH_DTYPE["c64_ff"], "data": "synthetic (seeded complex Gaussians)",
+        "config": {"workload": f"batch2d_{len(probs)}", "problems": len(probs), "unknowns": N,
+                   "nodes_range": [min(min(q.shape) for q in probs), max(max(q.shape) for q in probs)],
+                   "near_resonance": sum(1 for q in probs if q.note), "precision": PATH_PRECISION["c64_ff"],
+                   "launch": "one CUDA graph per step (helm_batch_solve)", "parallelism": f"replicas x{world}"},
+        "refinement": {"converged": conv, "problems": len(probs), "sweeps_min": min(sweeps),
+                       "sweeps_max": max(sweeps), "worst_final_rel_residual": worst, "tol": REFINE_TOL},
+        "variants": {"one_by_one": {"value": world * N / (ms_s * 1e-3), "unit": UNIT, "ms_per_step": ms_s,
+                                    "launch": "helm_solve per problem (each refinement loop one graph)"}},
+        "plan_seconds": plan_s, "clocks": clocks,
+    }
+    for pl in plans:
+        pl.close()
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def cpu_baseline_run(p, steps):
     from oracle import solvers
 
@@ -474,8 +545,10 @@ def main():
     ap.add_argument("--shape", default="", help="nx,ny: same spacing and wave number on a smaller grid "
                     "(profiling cases; not a benchmark line)")
     ap.add_argument("--minimal", action="store_true", help="timed solves only (no e2e, variants, CPU baseline)")
-    ap.add_argument("--workload", default="2d_large", choices=["2d_large", "3d"],
-                    help="2d_large: the benchmark workload; 3d: the 512^3 workload (measurement, not the bench line)")
+    ap.add_argument("--batch-count", type=int, default=512, help="problems of --workload batch2d")
+    ap.add_argument("--workload", default="2d_large", choices=["2d_large", "3d", "batch2d"],
+                    help="2d_large: the benchmark workload; 3d: the 512^3 workload; batch2d: 512 independent 2D "
+                    "problems in one graph launch (measurements, not the bench line)")
     ap.add_argument("--path", default="c64_ff", choices=list(PATHS_NAMES),
                     help="path timed as the main line (the others are reported as variants)")
     args = ap.parse_args()

@@ -211,6 +211,35 @@ const char* helm_status_string(int status);
 /* Last CUDA/diagnostic message recorded by the plan (never NULL). */
 const char* helm_last_error(helm_plan_t p);
 
+/* --- Batches of independent problems --------------------------------------
+ * Many problems of different sizes, wave numbers and modes solved together
+ * (the paper solves one problem at a time; it has no batch layer).  A batch
+ * groups existing plans (2D or 3D, any dtype, any residual kind); it does not
+ * own them, and they must outlive it.  helm_batch_solve runs every plan's
+ * whole solve - for refined plans including the refinement loop - as ONE
+ * CUDA graph launch in which each plan is an independent branch, so the GPU
+ * overlaps the small problems and no host launches happen per problem.
+ * Each plan's result is the same as its helm_solve (the same kernels on the
+ * same data); helm_get_info(plan) reports its refinement afterwards.
+ *
+ * helm_batch_create: count >= 1 plans, none NULL.  Allocates the
+ *   float-float vectors of refined plans with that residual kind.
+ * helm_batch_solve: f[i], u[i] are device pointers of plan i, as for
+ *   helm_solve (host arrays of count pointers).  Asynchronous on the batch
+ *   stream.  The graph is captured at the first call and reused while the
+ *   pointers and the plans' settings (refinement, residual kind, auxiliary)
+ *   stay the same; otherwise it is captured again (the device is
+ *   synchronised first).  Rejects plans with profiling on (HELM_EINVAL).
+ *   Plans of one batch must not be solved concurrently by other calls.
+ * helm_batch_set_stream: stream of the launches (NULL: legacy stream).
+ * helm_batch_destroy: NULL is allowed; the plans are untouched. */
+typedef struct helm_batch* helm_batch_t;
+int helm_batch_create(helm_batch_t* out, int32_t count, const helm_plan_t* plans);
+int helm_batch_set_stream(helm_batch_t b, void* cuda_stream);
+int helm_batch_solve(helm_batch_t b, const void* const* f, void* const* u);
+const char* helm_batch_last_error(helm_batch_t b);
+int helm_batch_destroy(helm_batch_t b);
+
 /* --- Allocation-free small solve (the paper has no counterpart) -------------
  * For callers that cannot allocate device memory when they need a solve:
  * code running inside a host callback or a CUDA-graph host node, under a

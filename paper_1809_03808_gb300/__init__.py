@@ -63,6 +63,11 @@ _SIGS = {
     "helm_set_profiling": (_i32, [_vp, _i32]),
     "helm_solve_2d_static": (_i32, [_i64, _i64, _dbl, _dbl, _dbl, _vp, _vp, _vp]),
     "helm_get_profile": (_i32, [_vp, ctypes.POINTER(helm_profile_entry), _i32]),
+    "helm_batch_create": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp)]),
+    "helm_batch_set_stream": (_i32, [_vp, _vp]),
+    "helm_batch_solve": (_i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+    "helm_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "helm_batch_destroy": (_i32, [_vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -241,6 +246,49 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             helm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Plans solved together as one CUDA graph launch (helm_batch_*).
+
+    solve(fs, us) takes lists of CUDA tensors, one pair per plan, laid out as
+    for Plan.solve; the current torch stream is used."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (_vp * len(self.plans))(*[p.handle for p in self.plans])
+        h = _vp()
+        st = lib.helm_batch_create(ctypes.byref(h), len(self.plans), arr)
+        if st != HELM_OK:
+            raise HelmError(st, "helm_batch_create")
+        self.handle = h
+
+    def solve(self, fs, us, stream=None):
+        import torch
+        if len(fs) != len(self.plans) or len(us) != len(self.plans):
+            raise ValueError("one f and one u per plan")
+        for p, f, u in zip(self.plans, fs, us):
+            p._check_tensor(f, "f")
+            p._check_tensor(u, "u")
+        s = torch.cuda.current_stream(fs[0].device) if stream is None else stream
+        lib.helm_batch_set_stream(self.handle, _vp(s.cuda_stream))
+        fa = (_vp * len(fs))(*[f.data_ptr() for f in fs])
+        ua = (_vp * len(us))(*[u.data_ptr() for u in us])
+        st = lib.helm_batch_solve(self.handle, fa, ua)
+        if st != HELM_OK:
+            raise HelmError(st, "helm_batch_solve", lib.helm_batch_last_error(self.handle).decode())
+        return us
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.helm_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

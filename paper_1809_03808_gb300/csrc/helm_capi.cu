@@ -68,8 +68,22 @@ struct helm_plan {
   cudaGraphExec_t rg_exec = nullptr;
   const void* rg_f = nullptr;  // f, u baked into the graph (FP64 residual)
   void* rg_u = nullptr;
+  uint64_t version = 0;  // bumped by every setting a captured solve depends on
   Plan3D p3;
   Profiler prof;
+  std::string err;
+};
+
+// A group of plans solved as one CUDA graph (helm_batch_*).
+struct helm_batch {
+  std::vector<helm_plan*> plans;
+  cudaStream_t stream = nullptr;            // launch stream
+  cudaStream_t cap[2] = {nullptr, nullptr};  // private capture streams
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> kf;  // pointers and plan settings baked into the graph
+  std::vector<void*> ku;
+  std::vector<uint64_t> kv;
   std::string err;
 };
 
@@ -391,37 +405,21 @@ void drop_refine_graph(helm_plan* p) {
 // the state is done, which happens after at most max_iter + 1 residuals, so
 // the loop always ends.  Kernel arguments are baked in: the graph is rebuilt
 // when f or u (FP64 residual) or the auxiliary change.
-int build_refine_graph(helm_plan* p, const void* f, void* u) {
-  drop_refine_graph(p);
-  for (int k = 0; k < 2; ++k)
-    if (!p->cap[k]) HELM_CK(cudaStreamCreateWithFlags(&p->cap[k], cudaStreamNonBlocking));
-  cudaStream_t saved = p->stream;
-  p->stream = p->cap[0];
-  HELM_CK(cudaStreamBeginCapture(p->cap[0], cudaStreamCaptureModeThreadLocal));
-  int rc = HELM_OK;
-  cudaGraph_t g = nullptr;
-  bool body_open = false;
-  auto fail = [&](int code) {
-    if (body_open) {
-      cudaGraph_t b = nullptr;
-      cudaStreamEndCapture(p->cap[1], &b);
-    }
-    cudaGraph_t gg = nullptr;
-    cudaStreamEndCapture(p->cap[0], &gg);
-    if (gg) cudaGraphDestroy(gg);
-    cudaGetLastError();
-    p->stream = saved;
-    return code;
-  };
-  if ((rc = refine_first(p, f, u, nullptr, nullptr, nullptr))) return fail(rc);
+// With a stream capture in progress on `cap` and p->stream == cap: append the
+// refinement loop after the captured work, as a conditional while node whose
+// body (residual, test, correction) is captured on `body`.  The test kernel
+// sets the node's condition; it ends the loop after at most max_iter + 1
+// residuals, so the loop always ends.
+int append_refine_loop(helm_plan* p, const void* f, void* u, cudaStream_t cap, cudaStream_t body) {
   cudaStreamCaptureStatus status;
+  cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
-  cudaError_t e = cudaStreamGetCaptureInfo(p->cap[0], &status, nullptr, &g, &deps, nullptr, &ndeps);
-  if (e != cudaSuccess || status != cudaStreamCaptureStatusActive) return fail(cuda_fail(p, e, "capture info"));
+  cudaError_t e = cudaStreamGetCaptureInfo(cap, &status, nullptr, &g, &deps, nullptr, &ndeps);
+  if (e != cudaSuccess || status != cudaStreamCaptureStatusActive) return cuda_fail(p, e, "capture info");
   cudaGraphConditionalHandle h;
   if ((e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
-    return fail(cuda_fail(p, e, "cudaGraphConditionalHandleCreate"));
+    return cuda_fail(p, e, "cudaGraphConditionalHandleCreate");
   cudaGraphNodeParams np{};
   np.type = cudaGraphNodeTypeConditional;
   np.conditional.handle = h;
@@ -429,29 +427,48 @@ int build_refine_graph(helm_plan* p, const void* f, void* u) {
   np.conditional.size = 1;
   cudaGraphNode_t cn;
   if ((e = cudaGraphAddNode(&cn, g, deps, nullptr, ndeps, &np)) != cudaSuccess)
-    return fail(cuda_fail(p, e, "cudaGraphAddNode(while)"));
-  if ((e = cudaStreamUpdateCaptureDependencies(p->cap[0], &cn, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
-      cudaSuccess)
-    return fail(cuda_fail(p, e, "cudaStreamUpdateCaptureDependencies"));
-  // the body, captured on the second stream into the while node's graph
-  if ((e = cudaStreamBeginCaptureToGraph(p->cap[1], np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+    return cuda_fail(p, e, "cudaGraphAddNode(while)");
+  if ((e = cudaStreamUpdateCaptureDependencies(cap, &cn, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+    return cuda_fail(p, e, "cudaStreamUpdateCaptureDependencies");
+  if ((e = cudaStreamBeginCaptureToGraph(body, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                          cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-    return fail(cuda_fail(p, e, "cudaStreamBeginCaptureToGraph"));
-  body_open = true;
-  p->stream = p->cap[1];
-  if ((rc = refine_check(p, f, u, (unsigned long long)h)) || (rc = refine_correct(p, u))) return fail(rc);
-  cudaGraph_t body = nullptr;
-  e = cudaStreamEndCapture(p->cap[1], &body);
-  body_open = false;
-  if (e != cudaSuccess) return fail(cuda_fail(p, e, "end body capture"));
+    return cuda_fail(p, e, "cudaStreamBeginCaptureToGraph");
+  p->stream = body;
+  int rc = refine_check(p, f, u, (unsigned long long)h);
+  if (!rc) rc = refine_correct(p, u);
+  cudaGraph_t bg = nullptr;
+  e = cudaStreamEndCapture(body, &bg);
+  p->stream = cap;
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(p, e, "end body capture");
+  return HELM_OK;
+}
+
+// Capture u0 = S(f) and the refinement loop of one plan as a CUDA graph.
+// Kernel arguments are baked in: the graph is rebuilt when f or u (FP64
+// residual), the residual kind or the auxiliary change.
+int build_refine_graph(helm_plan* p, const void* f, void* u) {
+  drop_refine_graph(p);
+  for (int k = 0; k < 2; ++k)
+    if (!p->cap[k]) HELM_CK(cudaStreamCreateWithFlags(&p->cap[k], cudaStreamNonBlocking));
+  cudaStream_t saved = p->stream;
   p->stream = p->cap[0];
-  e = cudaStreamEndCapture(p->cap[0], &g);
+  HELM_CK(cudaStreamBeginCapture(p->cap[0], cudaStreamCaptureModeThreadLocal));
+  int rc = refine_first(p, f, u, nullptr, nullptr, nullptr);
+  if (!rc) rc = append_refine_loop(p, f, u, p->cap[0], p->cap[1]);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(p->cap[0], &g);
   p->stream = saved;
-  if (e != cudaSuccess) return cuda_fail(p, e, "end capture");
+  if (rc || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc ? rc : cuda_fail(p, e, "end capture");
+  }
   p->rg_graph = g;
-  if ((e = cudaGraphInstantiate(&p->rg_exec, g, 0)) != cudaSuccess) {
+  cudaError_t ei;
+  if ((ei = cudaGraphInstantiate(&p->rg_exec, g, 0)) != cudaSuccess) {
     drop_refine_graph(p);
-    return cuda_fail(p, e, "cudaGraphInstantiate");
+    return cuda_fail(p, ei, "cudaGraphInstantiate");
   }
   p->rg_f = f;
   p->rg_u = u;
@@ -671,6 +688,7 @@ void static_aux_tables(AxisData& a, double rho, int q) {
 // Rebuild every table that depends on the auxiliary of the periodic axes.
 int apply_aux(helm_plan* p, double rho, int phase_quarters) {
   drop_refine_graph(p);  // its kernels hold the old eigen-data
+  ++p->version;
   int rc = build_axis_aux(p, p->axo, rho, phase_quarters);
   if (!rc && p->dim == 3) rc = build_axis_aux(p, p->axi, rho, phase_quarters);
   if (rc) return rc;
@@ -771,6 +789,94 @@ int tune_auxiliary(helm_plan* p) {
   p->aux_trial_resid = best;
   cleanup();
   return rc;
+}
+
+// Append plan p's whole solve (f -> u) to the capture in progress on `cap`:
+// the plain solve, or for refined plans the state reset, the float-float
+// split, u0 = S(f), the refinement loop (while node, body on `body`) and the
+// final join.
+int append_solve(helm_plan* p, const void* f, void* u, cudaStream_t cap, cudaStream_t body) {
+  const int64_t N = p->n[0] * p->n[1] * p->n[2];
+  cudaStream_t saved = p->stream;
+  p->stream = cap;
+  int rc = HELM_OK;
+  if (p->dtype == HELM_C128) {
+    rc = solve_core(p, f, kInC128, u, kOutC128, 0.0, nullptr, nullptr, nullptr, nullptr);
+  } else if (p->dtype == HELM_C64_RAW) {
+    rc = solve_core(p, f, kInC64, u, kOutC64, 0.0, nullptr, nullptr, nullptr, nullptr);
+  } else {
+    cudaError_t e = launch_refine_init(p->state, p->tol, p->max_iter, cap);
+    if (e != cudaSuccess) rc = cuda_fail(p, e, "refine init");
+    if (!rc && refine_ff(p) && (e = launch_split_ff((const double2*)f, p->ffb, N, cap)) != cudaSuccess)
+      rc = cuda_fail(p, e, "split");
+    if (!rc) rc = refine_first(p, f, u, nullptr, nullptr, nullptr);
+    if (!rc) rc = append_refine_loop(p, f, u, cap, body);
+    if (!rc && refine_ff(p) && (e = launch_join_ff(p->ufb, (double2*)u, N, cap)) != cudaSuccess)
+      rc = cuda_fail(p, e, "join");
+  }
+  p->stream = saved;
+  return rc;
+}
+
+void drop_batch_graph(helm_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->kf.clear();
+  b->ku.clear();
+  b->kv.clear();
+}
+
+// One graph for the whole batch: every plan's solve hangs from an empty root
+// node, so the plans are independent branches that the GPU runs side by side.
+int build_batch_graph(helm_batch* b, const void* const* f, void* const* u) {
+  drop_batch_graph(b);
+  for (int k = 0; k < 2; ++k)
+    if (!b->cap[k] && cudaStreamCreateWithFlags(&b->cap[k], cudaStreamNonBlocking) != cudaSuccess) {
+      b->err = "cudaStreamCreate";
+      return HELM_ECUDA;
+    }
+  cudaStream_t cs = b->cap[0];
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    b->err = "cudaStreamBeginCapture";
+    return HELM_ECUDA;
+  }
+  int rc = HELM_OK;
+  cudaStreamCaptureStatus status;
+  cudaGraph_t g = nullptr;
+  cudaGraphNode_t root = nullptr;
+  if (cudaStreamGetCaptureInfo(cs, &status, nullptr, &g) != cudaSuccess || cudaGraphAddEmptyNode(&root, g, nullptr, 0) != cudaSuccess) {
+    b->err = "batch graph root";
+    rc = HELM_ECUDA;
+  }
+  for (size_t i = 0; i < b->plans.size() && !rc; ++i) {
+    if (cudaStreamUpdateCaptureDependencies(cs, &root, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess) {
+      b->err = "cudaStreamUpdateCaptureDependencies";
+      rc = HELM_ECUDA;
+      break;
+    }
+    rc = append_solve(b->plans[i], f[i], u[i], cs, b->cap[1]);
+    if (rc) b->err = std::string("plan ") + std::to_string(i) + ": " + b->plans[i]->err;
+  }
+  cudaGraph_t out = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cs, &out);
+  if (rc || e != cudaSuccess) {
+    if (out) cudaGraphDestroy(out);
+    cudaGetLastError();
+    if (!rc) b->err = "cudaStreamEndCapture";
+    return rc ? rc : HELM_ECUDA;
+  }
+  b->graph = out;
+  if (cudaGraphInstantiate(&b->exec, out, 0) != cudaSuccess) {
+    drop_batch_graph(b);
+    b->err = "cudaGraphInstantiate";
+    return HELM_ECUDA;
+  }
+  b->kf.assign(f, f + b->plans.size());
+  b->ku.assign(u, u + b->plans.size());
+  for (helm_plan* p : b->plans) b->kv.push_back(p->version);
+  return HELM_OK;
 }
 
 }  // namespace
@@ -892,6 +998,7 @@ int helm_set_stream(helm_plan_t p, void* s) {
 
 int helm_set_refinement(helm_plan_t p, double tol, int max_iter) {
   if (!p || !(tol >= 0) || max_iter < 1 || max_iter > 15) return HELM_EINVAL;
+  ++p->version;
   p->tol = tol;
   p->max_iter = max_iter;
   return HELM_OK;
@@ -899,6 +1006,7 @@ int helm_set_refinement(helm_plan_t p, double tol, int max_iter) {
 
 int helm_set_residual(helm_plan_t p, int kind) {
   if (!p || p->dtype != HELM_C64_REFINED || (kind != HELM_RESID_FP64 && kind != HELM_RESID_FF)) return HELM_EINVAL;
+  ++p->version;
   if (p->resid_kind != kind) drop_refine_graph(p);
   p->resid_kind = kind;
   return HELM_OK;
@@ -964,6 +1072,75 @@ int helm_get_info(helm_plan_t p, helm_info* info) {
     return HELM_ETIMEOUT;
   }
   if (p->dtype == HELM_C64_REFINED && !s.converged) return HELM_ENOTCONV;
+  return HELM_OK;
+}
+
+int helm_batch_create(helm_batch_t* out, int32_t count, const helm_plan_t* plans) {
+  if (!out) return HELM_EINVAL;
+  *out = nullptr;
+  if (count < 1 || !plans) return HELM_EINVAL;
+  for (int32_t i = 0; i < count; ++i)
+    if (!plans[i]) return HELM_EINVAL;
+  helm_batch* b = new (std::nothrow) helm_batch();
+  if (!b) return HELM_ENOMEM;
+  b->plans.assign(plans, plans + count);
+  // float-float buffers must exist before a capture (no allocation inside it)
+  for (helm_plan* p : b->plans)
+    if (p->dtype == HELM_C64_REFINED && refine_ff(p) && !p->ffb) {
+      const int64_t N = p->n[0] * p->n[1] * p->n[2];
+      int rc;
+      if ((rc = dev_alloc(p, (void**)&p->ffb, N * sizeof(float4))) ||
+          (rc = dev_alloc(p, (void**)&p->ufb, N * sizeof(float4)))) {
+        delete b;
+        return rc;
+      }
+    }
+  *out = b;
+  return HELM_OK;
+}
+
+int helm_batch_set_stream(helm_batch_t b, void* s) {
+  if (!b) return HELM_EINVAL;
+  b->stream = (cudaStream_t)s;
+  return HELM_OK;
+}
+
+int helm_batch_solve(helm_batch_t b, const void* const* f, void* const* u) {
+  if (!b || !f || !u) return HELM_EINVAL;
+  const size_t n = b->plans.size();
+  for (size_t i = 0; i < n; ++i) {
+    if (!f[i] || !u[i] || f[i] == u[i]) return HELM_EINVAL;
+    helm_plan* p = b->plans[i];
+    if (p->prof.on) return HELM_EINVAL;  // event timing cannot live inside the graph
+    if (p->dtype == HELM_C64_REFINED && refine_ff(p) && !p->ffb) return HELM_EINVAL;  // kind changed after create
+  }
+  bool same = b->exec && b->kf.size() == n;
+  for (size_t i = 0; same && i < n; ++i)
+    same = b->kf[i] == f[i] && b->ku[i] == u[i] && b->kv[i] == b->plans[i]->version;
+  if (!same) {
+    // the capture reads plan state built by earlier work on other streams
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+      b->err = "cudaDeviceSynchronize";
+      return HELM_ECUDA;
+    }
+    if (int rc = build_batch_graph(b, f, u)) return rc;
+  }
+  if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) {
+    cudaGetLastError();
+    b->err = "cudaGraphLaunch";
+    return HELM_ECUDA;
+  }
+  return HELM_OK;
+}
+
+const char* helm_batch_last_error(helm_batch_t b) { return b ? b->err.c_str() : "null batch"; }
+
+int helm_batch_destroy(helm_batch_t b) {
+  if (!b) return HELM_OK;
+  drop_batch_graph(b);
+  for (int k = 0; k < 2; ++k)
+    if (b->cap[k]) cudaStreamDestroy(b->cap[k]);
+  delete b;
   return HELM_OK;
 }
 

@@ -922,6 +922,20 @@ cudaError_t launch_trial_rhs(double2* f, int64_t N, uint64_t seed, cudaStream_t 
   return cudaGetLastError();
 }
 
+__global__ void k_refine_init(RefineState* st, double tol, int max_iter) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    RefineState s{};
+    s.tol = tol;
+    s.max_iter = max_iter;
+    *st = s;
+  }
+}
+
+cudaError_t launch_refine_init(RefineState* st, double tol, int max_iter, cudaStream_t stream) {
+  k_refine_init<<<1, 32, 0, stream>>>(st, tol, max_iter);
+  return cudaGetLastError();
+}
+
 int64_t residual_blocks(int dim, const int64_t* n) {
   if (dim == 2) {
     // the larger of the FP64 grid and the float-float interior + perimeter grids

@@ -94,6 +94,8 @@ cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, doubl
 // complex128 -> float-float (hi = round(x), lo = round(x - hi)) and back.
 cudaError_t launch_split_ff(const double2* f, float4* out, int64_t N, cudaStream_t st);
 cudaError_t launch_join_ff(const float4* u, double2* out, int64_t N, cudaStream_t st);
+// Reset *st to the start of a refinement (a kernel, so that it can be captured).
+cudaError_t launch_refine_init(RefineState* st, double tol, int max_iter, cudaStream_t stream);
 // Deterministic pseudo-random complex128 vector (plan-time trials).
 cudaError_t launch_trial_rhs(double2* f, int64_t N, uint64_t seed, cudaStream_t st);
 // Number of per-block sums launch_residual writes for this grid.

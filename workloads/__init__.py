@@ -75,6 +75,51 @@ def config_3d() -> Problem:
                name="3d_512cube")
 
 
+def _max_prime_factor(n: int) -> int:
+    m, p, big = n, 2, 1
+    while p * p <= m:
+        while m % p == 0:
+            big, m = p, m // p
+        p += 1
+    return max(big, m) if m > 1 else big
+
+
+def batch_2d(count: int = 512, seed: int = 1000) -> list:
+    """Batched 2D workload: `count` independent problems.
+
+    nx uniform on {63..1023}; ny (the x1 / transform length) uniform on the
+    values in {63..1023} whose prime factors are all <= 64 (the transform
+    lengths the library supports); anisotropic spacings h_j = s_j / (n_j - 1)
+    with s_j uniform on [0.5, 2]; omega for a uniform 6..20 nodes per
+    wavelength at max(h).  One problem in eight is moved next to a discrete
+    resonance: omega^2 is set to the nearest sum of the closed-form
+    Neumann-Laplacian eigenvalues of linear elements,
+    6/h^2 (1 - cos(k pi/(n-1))) / (2 + cos(k pi/(n-1))), of the two axes (the
+    absorbing boundary keeps the problem solvable).  Right-hand sides are
+    seeded complex Gaussians (seed + 1 + index)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    smooth = [n for n in range(63, 1024) if _max_prime_factor(n) <= 64]
+    out = []
+    for i in range(count):
+        nx = int(rng.integers(63, 1024))
+        ny = int(smooth[int(rng.integers(0, len(smooth)))])
+        hx = float(rng.uniform(0.5, 2.0)) / (nx - 1)
+        hy = float(rng.uniform(0.5, 2.0)) / (ny - 1)
+        ppw = float(rng.uniform(6.0, 20.0))
+        omega = ppw_omega(max(hx, hy), ppw)
+        note = ""
+        if i % 8 == 7:
+            def eig(n, h):
+                t = np.pi * np.arange(n) / (n - 1)
+                return 6.0 / h ** 2 * (1.0 - np.cos(t)) / (2.0 + np.cos(t))
+            sums = (eig(nx, hx)[:, None] + eig(ny, hy)[None, :]).ravel()
+            omega = float(np.sqrt(sums[np.argmin(np.abs(sums - omega ** 2))]))
+            note = "near resonance"
+        out.append(Problem(name=f"batch2d_{i}", shape=(nx, ny), h=(hx, hy), omega=omega, seed=seed + 1 + i,
+                           note=note))
+    return out
+
+
 def scaled(p: Problem, shape, seed=None, name=None) -> Problem:
     """Same spacing and wave number as `p` on a smaller node grid (bounded samples)."""
     return Problem(name=name or f"{p.name}_sample{'x'.join(map(str, shape))}",
