@@ -801,9 +801,16 @@ __global__ void __launch_bounds__(128) k_tri_pass2_t32(const float2* __restrict_
 constexpr int kBulkLines = 128;
 constexpr int kBulkChunks = 8;
 
+// Values per tile buffer: [array: f_hat, 1/u][row][line], then the chunk's
+// face values f1 (CH) and fn (CH + 2, starting one early when needed for a
+// 16-byte aligned source).
+template <int CH>
+__host__ __device__ constexpr int bulk_tile_values() {
+  return 2 * CH * kBulkLines + 2 * CH + 2;
+}
 template <int CH>
 constexpr size_t bulk_tile_bytes() {
-  return (size_t)2 * 2 * CH * kBulkLines * sizeof(float2);  // [buffer][array][row][line]
+  return (size_t)2 * bulk_tile_values<CH>() * sizeof(float2);  // two buffers
 }
 
 template <int PASS, int STEP, int CH>
@@ -814,8 +821,9 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
                                                              const void* __restrict__ consts,
                                                              const int* __restrict__ skip, int* __restrict__ err) {
   using C = float2;
-  constexpr int TILE = 2 * CH * kBulkLines;  // values per buffer
-  constexpr bool RHS = STEP != 2;            // Step 2 takes its rhs from the face vectors
+  constexpr int TILE = bulk_tile_values<CH>();  // values per buffer
+  constexpr bool RHS = STEP != 2;               // Step 2 takes its rhs from the face vectors
+  constexpr bool FACES = STEP != 1;             // Steps 2, 3 read the face vectors f1, fn
   if (skip && *skip) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   C* const tile = reinterpret_cast<C*>(smem_raw);
@@ -838,11 +846,23 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
     const int64_t s = k * CH;
     const int cnt = (int)min((int64_t)CH, nx - s);
     const uint32_t row_bytes = (uint32_t)nl * (uint32_t)sizeof(C);
-    mbar_arrive_expect_tx(&bar[bsel], (uint32_t)cnt * row_bytes * (RHS ? 2u : 1u));
+    // face values f1[s, s+cnt) and fn[s, s+cnt) = faces[nx+s, nx+s+cnt),
+    // each widened to whole 16-byte pairs: f1 from s (even), fn from the even
+    // index at or before nx + s; the widened ends stay inside [0, 2 nx)
+    const int64_t fa = (nx + s) & ~(int64_t)1;
+    const uint32_t n_f1 = (uint32_t)((cnt + 1) & ~1);
+    const uint32_t n_fn = (uint32_t)((((nx + s + cnt + 1) & ~(int64_t)1)) - fa);
+    const uint32_t face_bytes = FACES ? (n_f1 + n_fn) * (uint32_t)sizeof(C) : 0u;
+    mbar_arrive_expect_tx(&bar[bsel], (uint32_t)cnt * row_bytes * (RHS ? 2u : 1u) + face_bytes);
     C* buf = tile + bsel * TILE;
     for (int t = 0; t < cnt; ++t) {
       if (RHS) bulk_g2s(buf + t * kBulkLines, fhat + (s + t) * n1 + l0, row_bytes, &bar[bsel]);
       bulk_g2s(buf + (CH + t) * kBulkLines, tb.iu + (s + t) * n1 + l0, row_bytes, &bar[bsel]);
+    }
+    if (FACES) {
+      C* fb = buf + 2 * CH * kBulkLines;
+      bulk_g2s(fb, faces + s, n_f1 * (uint32_t)sizeof(C), &bar[bsel]);
+      bulk_g2s(fb + CH, faces + fa, n_fn * (uint32_t)sizeof(C), &bar[bsel]);
     }
   };
   // thread 0's book of copies in flight: bit b of `pending` (buffer b busy),
@@ -858,8 +878,6 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
   }
   const LineValues<float, C> lv = line_values<float>(STEP, a, l, consts);
   const C b = lv.co.b, mb = mk<C>(-b.x, -b.y);
-  const C* f1 = faces;
-  const C* fn = faces + nx;
   const C zero = mk<C>(0, 0);
   const int64_t nparts = (n1 + kBulkLines - 1) / kBulkLines;
   C iprev = (PASS == 2 && kb > 0) ? tb.iu[(kb * CH - 1) * n1 + l] : zero;  // 1/u of the row before the run
@@ -882,12 +900,13 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
     if (tid == 0) pending &= ~(1u << bsel);
     C* const frow = tile + bsel * TILE;      // [CH][128] f_hat rows
     C* const irow = frow + CH * kBulkLines;  // [CH][128] 1/u rows
+    const C* const sf1 = frow + 2 * CH * kBulkLines;                   // f1[s + t]
+    const C* const sfn = sf1 + CH + (int)((nx + s) & 1);               // fn[s + t]
     auto rhs = [&](int t) -> C {
-      const int64_t j = s + t;
       if (STEP == 1) return cmul(frow[t * kBulkLines + tid], lv.scal);
-      if (STEP == 2) return cadd(f1[j], cscale(fn[j], lv.par));
-      C v = cadd(frow[t * kBulkLines + tid], f1[j]);
-      v = cadd(v, cmul(fn[j], lv.wl));
+      if (STEP == 2) return cadd(sf1[t], cscale(sfn[t], lv.par));
+      C v = cadd(frow[t * kBulkLines + tid], sf1[t]);
+      v = cadd(v, cmul(sfn[t], lv.wl));
       return cmul(v, lv.scal);
     };
     if (PASS == 1) {
