@@ -145,8 +145,9 @@ def kernel_model(name, e, n1, accum=False, first=True, tables=False, ff=False):
                "tri_step3_pass1": (3 * e, 24.0), "tri_step1_pass2": (3 * e, 34.0),
                "tri_step2_pass2": (2 * e, 36.0), "tri_step3_pass2": (4 * e, 30.0)}
     else:
-        tri = {"tri_step1_pass1": (e, 67.0), "tri_step2_pass1": (0.0, 61.0), "tri_step3_pass1": (e, 75.0),
-               "tri_step1_pass2": (e, 53.0), "tri_step2_pass2": (0.0, 47.0), "tri_step3_pass2": (2.0 * e, 55.0)}
+        # complex64: each pass reads the per-plan 1/u_j table beside the rhs
+        tri = {"tri_step1_pass1": (2 * e, 67.0), "tri_step2_pass1": (e, 61.0), "tri_step3_pass1": (2 * e, 75.0),
+               "tri_step1_pass2": (2 * e, 53.0), "tri_step2_pass2": (e, 47.0), "tri_step3_pass2": (3 * e, 55.0)}
     # 3D (n1 = the y / z length): z transforms on rows, y transforms in place
     # on columns; k_plane3d per outer step: per inner step the forward sweep
     # reads 1/den and writes d, the backward sweep reads both (4e), x3 steps,

@@ -495,9 +495,19 @@ __global__ void __launch_bounds__(256) k_residual2d_ff(ResidFFArgs a, const floa
     const float4* q0 = un - ny;
     float4 cm = __ldg(qm), pm = ffc_add(__ldg(qm - 1), __ldg(qm + 1));
     float4 c0 = __ldg(q0), p0 = ffc_add(__ldg(q0 - 1), __ldg(q0 + 1));
-    for (int64_t ix = x0; ix < x1; ++ix, un += ny, fp += ny, rp += ny) {
-      const float4 cp = __ldg(un), pp = ffc_add(__ldg(un - 1), __ldg(un + 1));
-      const float4 fv = __ldg(fp);
+    // software pipeline: row ix + 2 and f of row ix + 1 load while row ix computes
+    float4 nl = __ldg(un - 1), nc = __ldg(un), nr = __ldg(un + 1), nf = __ldg(fp);
+    for (int64_t ix = x0; ix < x1; ++ix, rp += ny) {
+      const float4 cp = nc, pp = ffc_add(nl, nr);
+      const float4 fv = nf;
+      if (ix + 1 < x1) {
+        un += ny;
+        fp += ny;
+        nl = __ldg(un - 1);
+        nc = __ldg(un);
+        nr = __ldg(un + 1);
+        nf = __ldg(fp);
+      }
       float4 au = make_float4(0, 0, 0, 0);
       ffc_mac_r(au, cc, c0);
       ffc_mac_r(au, cxp, ffc_add(cm, cp));
@@ -686,16 +696,47 @@ __device__ __forceinline__ void split_d(double x, float& hi, float& lo) {
   const float scale = __uint_as_float((uint32_t)(e - 948) << 23);
   lo = __uint_as_float(__float_as_uint(__int2float_rn(r) * scale) ^ sgn);
 }
-// float -> double by the bit fields (normal floats and zero; the rest converts)
+// float -> double by the bit fields, exact for normal floats and zeros: the
+// exponent is rebiased (+896) and the fraction moves 29 bits up.
 __device__ __forceinline__ double widen_f(float v) {
   const uint32_t u = __float_as_uint(v);
-  const uint32_t e = (u >> 23) & 0xff;
-  if (e == 0 || e == 0xff) return (double)v;
-  const uint64_t b = ((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(e + 896) << 52) | ((uint64_t)(u & 0x7fffff) << 29);
-  return __longlong_as_double((long long)b);
+  const uint32_t mag = u & 0x7fffffffu;
+  const uint32_t hi = (u & 0x80000000u) | (mag ? (mag >> 3) + (896u << 20) : 0u);
+  return __hiloint2double((int)hi, (int)(u << 29));
 }
-__global__ void k_split_ff(const double2* __restrict__ f, float4* __restrict__ o, int64_t N) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+// subnormal, infinite or NaN (the values widen_f does not cover)
+__device__ __forceinline__ bool widen_special(float v) {
+  const uint32_t mag = __float_as_uint(v) & 0x7fffffffu;
+  return mag != 0 && mag - 0x00800000u >= 0x7f000000u;
+}
+// the plain conversions, kept out of line so that the common path holds no
+// FP64 conversion (a select would evaluate both sides)
+__device__ __noinline__ double2 join_plain(float4 v) {
+  return make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+}
+__device__ __forceinline__ double2 join_one(float4 v) {
+  if (widen_special(v.x) | widen_special(v.y) | widen_special(v.z) | widen_special(v.w)) return join_plain(v);
+  return make_double2(widen_f(v.x) + widen_f(v.z), widen_f(v.y) + widen_f(v.w));
+}
+// Element-wise kernels: each thread issues kEw independent loads before it
+// converts and stores them (enough bytes in flight to cover HBM latency).
+constexpr int kEw = 4;
+__global__ void __launch_bounds__(256) k_split_ff(const double2* __restrict__ f, float4* __restrict__ o, int64_t N) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (kEw - 1) * stride < N; i += kEw * stride) {
+    double2 v[kEw];
+#pragma unroll
+    for (int j = 0; j < kEw; ++j) v[j] = __ldcs(&f[i + j * stride]);
+#pragma unroll
+    for (int j = 0; j < kEw; ++j) {
+      float4 q;
+      split_d(v[j].x, q.x, q.z);
+      split_d(v[j].y, q.y, q.w);
+      o[i + j * stride] = q;
+    }
+  }
+  for (; i < N; i += stride) {
     const double2 v = f[i];
     float4 q;
     split_d(v.x, q.x, q.z);
@@ -703,10 +744,20 @@ __global__ void k_split_ff(const double2* __restrict__ f, float4* __restrict__ o
     o[i] = q;
   }
 }
-__global__ void k_join_ff(const float4* __restrict__ q, double2* __restrict__ o, int64_t N) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(256) k_join_ff(const float4* __restrict__ q, double2* __restrict__ o, int64_t N) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (kEw - 1) * stride < N; i += kEw * stride) {
+    float4 v[kEw];
+#pragma unroll
+    for (int j = 0; j < kEw; ++j) v[j] = __ldcs(&q[i + j * stride]);
+#pragma unroll
+    for (int j = 0; j < kEw; ++j)
+      o[i + j * stride] = join_one(v[j]);
+  }
+  for (; i < N; i += stride) {
     const float4 v = q[i];
-    o[i] = make_double2(widen_f(v.x) + widen_f(v.z), widen_f(v.y) + widen_f(v.w));
+    o[i] = join_one(v);
   }
 }
 
@@ -886,16 +937,23 @@ cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, doubl
   return cudaGetLastError();
 }
 
+// One resident wave of 256-thread blocks (8 per SM), fewer for small N.
+static int64_t ew_grid(int64_t N) {
+  int dev = 0, nsm = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, (int64_t)nsm * 8));
+}
+
 cudaError_t launch_split_ff(const double2* f, float4* out, int64_t N, cudaStream_t st) {
   if (N == 0) return cudaSuccess;
-  const int64_t grid = std::min<int64_t>((N + 255) / 256, 152 * 16);
+  const int64_t grid = ew_grid(N);
   k_split_ff<<<(unsigned)grid, 256, 0, st>>>(f, out, N);
   return cudaGetLastError();
 }
 
 cudaError_t launch_join_ff(const float4* u, double2* out, int64_t N, cudaStream_t st) {
   if (N == 0) return cudaSuccess;
-  const int64_t grid = std::min<int64_t>((N + 255) / 256, 152 * 16);
+  const int64_t grid = ew_grid(N);
   k_join_ff<<<(unsigned)grid, 256, 0, st>>>(u, out, N);
   return cudaGetLastError();
 }

@@ -803,10 +803,19 @@ constexpr int kBulkChunks = 8;
 
 // Values per tile buffer: [array: f_hat, 1/u][row][line], then the chunk's
 // face values f1 (CH) and fn (CH + 2, starting one early when needed for a
-// 16-byte aligned source).
+// 16-byte aligned source), then (pass 2) the carries Y(k-1), X(k+1) of the
+// block's lines.
+template <int CH>
+__host__ __device__ constexpr int bulk_face_offset() {
+  return 2 * CH * kBulkLines;
+}
+template <int CH>
+__host__ __device__ constexpr int bulk_carry_offset() {
+  return bulk_face_offset<CH>() + 2 * CH + 2;
+}
 template <int CH>
 __host__ __device__ constexpr int bulk_tile_values() {
-  return 2 * CH * kBulkLines + 2 * CH + 2;
+  return bulk_carry_offset<CH>() + 2 * kBulkLines;
 }
 template <int CH>
 constexpr size_t bulk_tile_bytes() {
@@ -825,7 +834,7 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
   constexpr bool RHS = STEP != 2;               // Step 2 takes its rhs from the face vectors
   constexpr bool FACES = STEP != 1;             // Steps 2, 3 read the face vectors f1, fn
   if (skip && *skip) return;
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* const tile = reinterpret_cast<C*>(smem_raw);
   __shared__ __align__(8) uint64_t bar[2];
   const int64_t n1 = a.n1, nx = a.nx;
@@ -853,16 +862,22 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
     const uint32_t n_f1 = (uint32_t)((cnt + 1) & ~1);
     const uint32_t n_fn = (uint32_t)((((nx + s + cnt + 1) & ~(int64_t)1)) - fa);
     const uint32_t face_bytes = FACES ? (n_f1 + n_fn) * (uint32_t)sizeof(C) : 0u;
-    mbar_arrive_expect_tx(&bar[bsel], (uint32_t)cnt * row_bytes * (RHS ? 2u : 1u) + face_bytes);
+    const uint32_t carry_bytes = PASS == 2 ? 2u * row_bytes : 0u;
+    mbar_arrive_expect_tx(&bar[bsel], (uint32_t)cnt * row_bytes * (RHS ? 2u : 1u) + face_bytes + carry_bytes);
     C* buf = tile + bsel * TILE;
     for (int t = 0; t < cnt; ++t) {
       if (RHS) bulk_g2s(buf + t * kBulkLines, fhat + (s + t) * n1 + l0, row_bytes, &bar[bsel]);
       bulk_g2s(buf + (CH + t) * kBulkLines, tb.iu + (s + t) * n1 + l0, row_bytes, &bar[bsel]);
     }
     if (FACES) {
-      C* fb = buf + 2 * CH * kBulkLines;
+      C* fb = buf + bulk_face_offset<CH>();
       bulk_g2s(fb, faces + s, n_f1 * (uint32_t)sizeof(C), &bar[bsel]);
       bulk_g2s(fb + CH, faces + fa, n_fn * (uint32_t)sizeof(C), &bar[bsel]);
+    }
+    if (PASS == 2) {
+      C* cb = buf + bulk_carry_offset<CH>();
+      bulk_g2s(cb, rec.a + k * n1 + l0, row_bytes, &bar[bsel]);
+      bulk_g2s(cb + kBulkLines, rec.bsum + k * n1 + l0, row_bytes, &bar[bsel]);
     }
   };
   // thread 0's book of copies in flight: bit b of `pending` (buffer b busy),
@@ -887,11 +902,6 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
     const uint32_t parity = (uint32_t)(((k - kb) >> 1) & 1);
     const int64_t s = k * CH;
     const int cnt = (int)min((int64_t)CH, nx - s);
-    C yp = zero, xn = zero;
-    if (PASS == 2) {
-      yp = rec.a[k * n1 + l];     // Y(k-1)
-      xn = rec.bsum[k * n1 + l];  // X(k+1)
-    }
     const bool got = mbar_wait_bounded(&bar[bsel], parity, err);
     if (__syncthreads_or(!got)) {  // block-uniform decision
       failed = true;
@@ -900,8 +910,13 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
     if (tid == 0) pending &= ~(1u << bsel);
     C* const frow = tile + bsel * TILE;      // [CH][128] f_hat rows
     C* const irow = frow + CH * kBulkLines;  // [CH][128] 1/u rows
-    const C* const sf1 = frow + 2 * CH * kBulkLines;                   // f1[s + t]
-    const C* const sfn = sf1 + CH + (int)((nx + s) & 1);               // fn[s + t]
+    const C* const sf1 = frow + bulk_face_offset<CH>();  // f1[s + t]
+    const C* const sfn = sf1 + CH + (int)((nx + s) & 1);  // fn[s + t]
+    C yp = zero, xn = zero;
+    if (PASS == 2) {
+      yp = frow[bulk_carry_offset<CH>() + tid];               // Y(k-1)
+      xn = frow[bulk_carry_offset<CH>() + kBulkLines + tid];  // X(k+1)
+    }
     auto rhs = [&](int t) -> C {
       if (STEP == 1) return cmul(frow[t * kBulkLines + tid], lv.scal);
       if (STEP == 2) return cadd(sf1[t], cscale(sfn[t], lv.par));
@@ -961,7 +976,9 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
       }
       if (STEP != 3) block_face_sums<C, CH>(red, cnt, partial, (int64_t)blockIdx.x, nparts, nx, s);
     }
-    __syncthreads();  // the buffer is consumed: it may be refilled
+    // the buffer is consumed: it may be refilled (in pass 2 of Steps 1, 2 the
+    // face sums' second barrier already follows the last read of the tile)
+    if (PASS == 1 || STEP == 3) __syncthreads();
     if (tid == 0 && k + 2 < ke) {
       issue(k + 2, bsel);
       pending |= 1u << bsel;
