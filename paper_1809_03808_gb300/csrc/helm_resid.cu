@@ -761,29 +761,51 @@ __global__ void __launch_bounds__(256) k_join_ff(const float4* __restrict__ q, d
   }
 }
 
-__global__ void k_residual_finalize(const double* __restrict__ sums, int64_t nblocks, RefineState* st,
+__global__ void __launch_bounds__(1024) k_residual_finalize(const double* __restrict__ sums, int64_t nblocks, RefineState* st,
                                     cudaGraphConditionalHandle cond) {
   if (st->done) {
     if (cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
     return;
   }
-  __shared__ double sr[256], sf[256];
-  double a2 = 0, b2 = 0;
-  for (int64_t i = threadIdx.x; i < nblocks; i += blockDim.x) {
-    a2 += sums[2 * i];
-    b2 += sums[2 * i + 1];
-  }
-  sr[threadIdx.x] = a2;
-  sf[threadIdx.x] = b2;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) {
-      sr[threadIdx.x] += sr[threadIdx.x + s];
-      sf[threadIdx.x] += sf[threadIdx.x + s];
+  // fixed order: kFinStreams interleaved partial sums per thread (independent
+  // loads in flight), then the warps, then the block
+  constexpr int kFinStreams = 4;
+  __shared__ double sr[32], sf[32];
+  const double2* s2 = reinterpret_cast<const double2*>(sums);
+  double2 acc[kFinStreams];
+#pragma unroll
+  for (int j = 0; j < kFinStreams; ++j) acc[j] = make_double2(0.0, 0.0);
+  const int64_t step = (int64_t)blockDim.x * kFinStreams;
+  for (int64_t i0 = threadIdx.x; i0 < nblocks; i0 += step) {
+    double2 v[kFinStreams];
+#pragma unroll
+    for (int j = 0; j < kFinStreams; ++j) {
+      const int64_t i = i0 + (int64_t)j * blockDim.x;
+      v[j] = i < nblocks ? s2[i] : make_double2(0.0, 0.0);
     }
-    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kFinStreams; ++j) {
+      acc[j].x += v[j].x;
+      acc[j].y += v[j].y;
+    }
   }
+  double a2 = (acc[0].x + acc[1].x) + (acc[2].x + acc[3].x);
+  double b2 = (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y);
+  for (int off = 16; off > 0; off >>= 1) {
+    a2 += __shfl_down_sync(0xffffffffu, a2, off);
+    b2 += __shfl_down_sync(0xffffffffu, b2, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sr[threadIdx.x >> 5] = a2;
+    sf[threadIdx.x >> 5] = b2;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+    for (int w = 1; w < nw; ++w) {
+      sr[0] += sr[w];
+      sf[0] += sf[w];
+    }
     const double rel = sf[0] > 0 ? sqrt(sr[0] / sf[0]) : sqrt(sr[0]);
     const int it = st->iters;
     if (it < 16) st->resid[it] = rel;
@@ -1006,7 +1028,7 @@ int64_t residual_blocks(int dim, const int64_t* n) {
 
 cudaError_t launch_residual_finalize(const double* sums, int64_t nblocks, RefineState* state,
                                      unsigned long long cond, cudaStream_t st) {
-  k_residual_finalize<<<1, 256, 0, st>>>(sums, nblocks, state, (cudaGraphConditionalHandle)cond);
+  k_residual_finalize<<<1, 1024, 0, st>>>(sums, nblocks, state, (cudaGraphConditionalHandle)cond);
   return cudaGetLastError();
 }
 

@@ -244,13 +244,18 @@ __global__ void __launch_bounds__(128) k_tri_pass1(const typename cpx<T>::type* 
 // sequential scan, regrouped once, in the precision of the records.
 constexpr int kCarryLines = 16;
 constexpr int kCarrySeg = 32;
-constexpr int kCarryBatch = 8;  // chunk records loaded ahead of each recurrence
+// chunk records loaded ahead of each recurrence; complex64 takes half as many
+// so that two blocks fit on an SM (every block of a 4096-line solve resident)
+template <typename T>
+__host__ __device__ constexpr int carry_batch() {
+  return sizeof(T) == 4 ? 4 : 8;
+}
 
 template <typename T>
-__global__ void __launch_bounds__(kCarryLines* kCarrySeg)
+__global__ void __launch_bounds__(kCarryLines* kCarrySeg, sizeof(T) == 4 ? 2 : 1)
     k_tri_carry(RecSoA<typename cpx<T>::type> rec, int64_t n1, int64_t K, const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
-  constexpr int B = kCarryBatch;
+  constexpr int B = carry_batch<T>();
   if (skip && *skip) return;  // uniform over the grid
   __shared__ C shC[kCarrySeg][kCarryLines], shP[kCarrySeg][kCarryLines];
   const int lx = threadIdx.x, sg = threadIdx.y;
@@ -1013,19 +1018,33 @@ __global__ void k_pivots(typename cpx<T>::type* __restrict__ ustart, Solve2DArgs
   }
 }
 
-// Sum the per-warp partials: out[face * nx + ix] = scale * sum_w partial.
+// Sum the per-block partials: out[face * nx + ix] = scale * sum_w partial.
+// Four lanes per output (lanes j, j+8, j+16, j+24 of a warp), each summing
+// the partials w = q, q+4, ... (independent loads), combined by two fixed
+// shuffles: a fixed summation order.
+constexpr int kFaceLanes = 4;
 template <typename T>
-__global__ void k_reduce_faces(const typename cpx<T>::type* __restrict__ partial,
-                               typename cpx<T>::type* __restrict__ out, int64_t nx, int64_t nwarps, double s0r,
-                               double s0i, double s1r, double s1i, const int* __restrict__ skip) {
+__global__ void __launch_bounds__(256) k_reduce_faces(const typename cpx<T>::type* __restrict__ partial,
+                                                      typename cpx<T>::type* __restrict__ out, int64_t nx,
+                                                      int64_t nwarps, double s0r, double s0i, double s1r,
+                                                      double s1i, const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
   if (skip && *skip) return;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * nx) return;
-  const int64_t face = i / nx, ix = i - face * nx;
+  const int lane = threadIdx.x & 31, q = lane >> 3;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / kFaceLanes + (lane & 7);
+  const bool act = i < 2 * nx;
+  const int64_t face = act ? i / nx : 0, ix = act ? i - face * nx : 0;
   C acc = mk<C>(0, 0);
-  for (int64_t w = 0; w < nwarps; ++w) acc = cadd(acc, partial[(face * nwarps + w) * nx + ix]);
-  out[i] = cmul(acc, face == 0 ? mk<C>(s0r, s0i) : mk<C>(s1r, s1i));
+  if (act) {
+    const C* src = partial + (face * nwarps) * nx + ix;
+#pragma unroll 8
+    for (int64_t w = q; w < nwarps; w += kFaceLanes) acc = cadd(acc, src[w * nx]);
+  }
+  for (int off = 8; off < 32; off <<= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+  }
+  if (act && q == 0) out[i] = cmul(acc, face == 0 ? mk<C>(s0r, s0i) : mk<C>(s1r, s1i));
 }
 
 // C_bb applied to the x1 faces (eqs. BminA, Cbb):
@@ -1033,13 +1052,22 @@ __global__ void k_reduce_faces(const typename cpx<T>::type* __restrict__ partial
 // with D11 = (1 + i w h1)/h1 - p h1/3, D1n = -1/h1 - p h1/6, E11 = h1/3,
 // E1n = h1/6 (p = w^2 for the outer problem), M, K along x (spacing hx,
 // absorbing corners).  in = v (+ w if `in2`), out = c.
+struct CbbConsts {
+  double md_end, md_in, mo;        // M rows: diagonal (end, inner), off-diagonal
+  double kd_end_re, kd_end_im;     // K diagonal at the absorbing ends
+  double kd_in, ko;                // K diagonal inside, off-diagonal
+  double d11_re, d11_im, d1n_re;   // D11, D1n (real)
+  double e11, e1n;                 // E11, E1n
+  double gr, gi, gir, gii;         // g and 1/g: wrap entries of the gamma-circulant
+};
+
 template <typename T>
 __global__ void k_apply_cbb(const typename cpx<T>::type* __restrict__ in,
                             const typename cpx<T>::type* __restrict__ in2,
-                            typename cpx<T>::type* __restrict__ out, int64_t nx, double hx, double h1,
-                            double omega, double p, double gr, double gi, double gir, double gii,
+                            typename cpx<T>::type* __restrict__ out, int64_t nx, CbbConsts k,
                             const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
+  using R = decltype(C().x);
   if (skip && *skip) return;
   const int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (ix >= nx) return;
@@ -1050,24 +1078,24 @@ __global__ void k_apply_cbb(const typename cpx<T>::type* __restrict__ in,
   };
   // M and K rows of x at ix
   const bool end = (ix == 0 || ix == nx - 1);
-  const double md = end ? 2.0 * hx / 6.0 : 4.0 * hx / 6.0, mo = hx / 6.0;
-  const double kd_re = end ? 1.0 / hx : 2.0 / hx, kd_im = end ? -omega : 0.0, ko = -1.0 / hx;
+  const R md = (R)(end ? k.md_end : k.md_in), mo = (R)k.mo, ko = (R)k.ko;
+  const C kd = end ? mk<C>(k.kd_end_re, k.kd_end_im) : mk<C>(k.kd_in, 0.0);
   C Mv[2], Kv[2];
   for (int f = 0; f < 2; ++f) {
     C v0 = get(f, ix);
     C vm = ix > 0 ? get(f, ix - 1) : mk<C>(0, 0);
     C vp = ix < nx - 1 ? get(f, ix + 1) : mk<C>(0, 0);
     C nb = cadd(vm, vp);
-    Mv[f] = cadd(cscale(v0, (decltype(v0.x))md), cscale(nb, (decltype(v0.x))mo));
-    Kv[f] = cadd(cmul(v0, mk<C>(kd_re, kd_im)), cscale(nb, (decltype(v0.x))ko));
+    Mv[f] = cadd(cscale(v0, md), cscale(nb, mo));
+    Kv[f] = cadd(cmul(v0, kd), cscale(nb, ko));
   }
-  const C D11 = mk<C>(1.0 / h1 - p * h1 / 3.0, omega);
-  const C D1n = mk<C>(-1.0 / h1 - p * h1 / 6.0, 0.0);
-  const auto E11 = (decltype(D11.x))(h1 / 3.0), E1n = (decltype(D11.x))(h1 / 6.0);
+  const C D11 = mk<C>(k.d11_re, k.d11_im);
+  const C D1n = mk<C>(k.d1n_re, 0.0);
+  const R E11 = (R)k.e11, E1n = (R)k.e1n;
   // wrap entries of the gamma-circulant: first row x 1/g, last row x g
   C c1 = cadd(cadd(cmul(D11, Mv[0]), cscale(Kv[0], E11)),
-              cmul(mk<C>(gir, gii), cadd(cmul(D1n, Mv[1]), cscale(Kv[1], E1n))));
-  C cn = cadd(cmul(mk<C>(gr, gi), cadd(cmul(D1n, Mv[0]), cscale(Kv[0], E1n))),
+              cmul(mk<C>(k.gir, k.gii), cadd(cmul(D1n, Mv[1]), cscale(Kv[1], E1n))));
+  C cn = cadd(cmul(mk<C>(k.gr, k.gi), cadd(cmul(D1n, Mv[0]), cscale(Kv[0], E1n))),
               cadd(cmul(D11, Mv[1]), cscale(Kv[1], E11)));
   out[ix] = c1;
   out[nx + ix] = cn;
@@ -1278,7 +1306,7 @@ size_t chunk_record_bytes(int prec) { return prec == kPrecF64 ? sizeof(ChunkRec<
 cudaError_t launch_reduce_faces(int prec, const void* partial, void* out, int64_t nx, int64_t nwarps,
                                 const double* s0, const double* s1, const int* skip, cudaStream_t st) {
   const int bs = 256;
-  const unsigned grid = (unsigned)((2 * nx + bs - 1) / bs);
+  const unsigned grid = (unsigned)((2 * nx * kFaceLanes + bs - 1) / bs);
   if (prec == kPrecF64)
     k_reduce_faces<double><<<grid, bs, 0, st>>>((const double2*)partial, (double2*)out, nx, nwarps, s0[0], s0[1],
                                                 s1[0], s1[1], skip);
@@ -1291,14 +1319,30 @@ cudaError_t launch_reduce_faces(int prec, const void* partial, void* out, int64_
 cudaError_t launch_apply_cbb(int prec, const void* in, const void* in2, void* out, int64_t nx, double hx,
                              double h1, double omega, double p, const double* g, const double* ginv,
                              const int* skip, cudaStream_t st) {
+  // the entries of eqs. BminA, Cbb once, in double, on the host
+  CbbConsts k;
+  k.md_end = 2.0 * hx / 6.0;
+  k.md_in = 4.0 * hx / 6.0;
+  k.mo = hx / 6.0;
+  k.kd_end_re = 1.0 / hx;
+  k.kd_end_im = -omega;
+  k.kd_in = 2.0 / hx;
+  k.ko = -1.0 / hx;
+  k.d11_re = 1.0 / h1 - p * h1 / 3.0;
+  k.d11_im = omega;
+  k.d1n_re = -1.0 / h1 - p * h1 / 6.0;
+  k.e11 = h1 / 3.0;
+  k.e1n = h1 / 6.0;
+  k.gr = g[0];
+  k.gi = g[1];
+  k.gir = ginv[0];
+  k.gii = ginv[1];
   const int bs = 256;
   const unsigned grid = (unsigned)((nx + bs - 1) / bs);
   if (prec == kPrecF64)
-    k_apply_cbb<double><<<grid, bs, 0, st>>>((const double2*)in, (const double2*)in2, (double2*)out, nx, hx,
-                                             h1, omega, p, g[0], g[1], ginv[0], ginv[1], skip);
+    k_apply_cbb<double><<<grid, bs, 0, st>>>((const double2*)in, (const double2*)in2, (double2*)out, nx, k, skip);
   else
-    k_apply_cbb<float><<<grid, bs, 0, st>>>((const float2*)in, (const float2*)in2, (float2*)out, nx, hx, h1,
-                                            omega, p, g[0], g[1], ginv[0], ginv[1], skip);
+    k_apply_cbb<float><<<grid, bs, 0, st>>>((const float2*)in, (const float2*)in2, (float2*)out, nx, k, skip);
   return cudaGetLastError();
 }
 
