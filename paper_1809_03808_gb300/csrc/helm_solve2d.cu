@@ -814,13 +814,16 @@ template <int CH>
 __host__ __device__ constexpr int bulk_face_offset() {
   return 2 * CH * kBulkLines;
 }
+// (offsets and the buffer size are whole 128-byte rows: a warp's 32
+// consecutive values then take the minimum two shared-memory wavefronts)
+__host__ __device__ constexpr int bulk_round16(int v) { return (v + 15) & ~15; }
 template <int CH>
 __host__ __device__ constexpr int bulk_carry_offset() {
-  return bulk_face_offset<CH>() + 2 * CH + 2;
+  return bulk_round16(bulk_face_offset<CH>() + 2 * CH + 2);
 }
 template <int CH>
 __host__ __device__ constexpr int bulk_tile_values() {
-  return bulk_carry_offset<CH>() + 2 * kBulkLines;
+  return bulk_round16(bulk_carry_offset<CH>() + 2 * kBulkLines);
 }
 template <int CH>
 constexpr size_t bulk_tile_bytes() {
