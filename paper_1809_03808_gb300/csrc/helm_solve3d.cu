@@ -296,27 +296,61 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
 // Outer boundary rows (eq. 3dBs1 / step2-3-3d) in inner-mode space:
 //   out[face][x][m] = sum_l wgt_face(l) * y3(x, l, m)
 // step 1: wgt = (1/ny, e^{-2 pi i l/ny}/ny); step 2: wgt = (sigma_l, par_l sigma_l).
+// The weights of a run of outer modes are staged in shared memory in the
+// compute precision; each thread sums over l in order, loading kOuterBatch
+// values ahead of the dependent sums.
+constexpr int kOuterChunk = 1024;
+constexpr int kOuterBatch = 8;
 template <typename T, int OSTEP>
-__global__ void k_reduce_outer(const typename cpx<T>::type* __restrict__ y3, typename cpx<T>::type* __restrict__ out,
-                               Plane3DArgs a, const int* __restrict__ skip) {
+__global__ void __launch_bounds__(256) k_reduce_outer(const typename cpx<T>::type* __restrict__ y3,
+                                                      typename cpx<T>::type* __restrict__ out, Plane3DArgs a,
+                                                      const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
-  if (skip && *skip) return;
+  if (skip && *skip) return;  // uniform over the grid
+  __shared__ C sw[kOuterChunk];
+  __shared__ T sp[OSTEP == 2 ? kOuterChunk : 1];
   const int64_t ny = a.ny, nz = a.nz;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.nx * nz) return;
-  const int64_t ix = i / nz, m = i - ix * nz;
+  const bool act = i < a.nx * nz;
+  const int64_t ix = act ? i / nz : 0, m = act ? i - ix * nz : 0;
+  const C* src = y3 + ix * ny * nz + m;
   C s1 = mk<C>(0, 0), sn = mk<C>(0, 0);
-  for (int64_t l = 0; l < ny; ++l) {
-    const C v = y3[(ix * ny + l) * nz + m];
+  auto add = [&](C v, int j) {
     if (OSTEP == 1) {
       s1 = cadd(s1, v);
-      sn = cadd(sn, cmul(v, mk<C>(a.two[2 * l], a.two[2 * l + 1])));
+      sn = cadd(sn, cmul(v, sw[j]));
     } else {
-      const C t = cmul(v, mk<C>(a.sigAo[2 * l], a.sigAo[2 * l + 1]));
+      const C t = cmul(v, sw[j]);
       s1 = cadd(s1, t);
-      sn = cadd(sn, cscale(t, (decltype(t.x))a.parAo[l]));
+      sn = cadd(sn, cscale(t, sp[j]));
+    }
+  };
+  for (int64_t l0 = 0; l0 < ny; l0 += kOuterChunk) {
+    const int cnt = (int)min((int64_t)kOuterChunk, ny - l0);
+    __syncthreads();  // the previous run's weights are consumed
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+      const int64_t l = l0 + j;
+      if (OSTEP == 1) {
+        sw[j] = mk<C>(a.two[2 * l], a.two[2 * l + 1]);
+      } else {
+        sw[j] = mk<C>(a.sigAo[2 * l], a.sigAo[2 * l + 1]);
+        sp[j] = (T)a.parAo[l];
+      }
+    }
+    __syncthreads();
+    if (act) {
+      int j = 0;
+      for (; j + kOuterBatch <= cnt; j += kOuterBatch) {
+        C v[kOuterBatch];
+#pragma unroll
+        for (int q = 0; q < kOuterBatch; ++q) v[q] = src[(l0 + j + q) * nz];
+#pragma unroll
+        for (int q = 0; q < kOuterBatch; ++q) add(v[q], j + q);
+      }
+      for (; j < cnt; ++j) add(src[(l0 + j) * nz], j);
     }
   }
+  if (!act) return;
   if (OSTEP == 1) {
     s1 = cscale(s1, (decltype(s1.x))(1.0 / (double)ny));
     sn = cmul(sn, mk<C>(a.en_o[0] / (double)ny, a.en_o[1] / (double)ny));
