@@ -179,6 +179,18 @@ def kernel_model(name, e, n1, accum=False, first=True, tables=False, ff=False):
     return tab.get(name)
 
 
+# DRAM bytes (read + write) per unknown of one launch, from an ncu capture of
+# the same kernel on a smaller grid with the workload's spacing and wave
+# number (the traffic of these kernels grows with the number of unknowns);
+# kept only while the kernel is unchanged since the capture.
+NCU_TRAFFIC_PER_UNKNOWN = {
+    ("2d", "c64_ff", "residual_ff"): (
+        (546.5e6 + 118.0e6 + 2.5e6) / (4096 * 4096),
+        "ncu --set full, 4096 x 4096: k_residual2d_ff + k_perimeter2d_ff "
+        "(profiles/ncu_2d_kernels_4096x4096.md)"),
+}
+
+
 def roofline_entry(name, launches, tot_ms, steps, N, e, n1, peaks, fp64, accum=False, tables=False, ff=False):
     per_launch_ms = tot_ms / launches
     model = kernel_model(name, e, n1, accum=accum, tables=tables, ff=ff)
@@ -376,6 +388,11 @@ def run_gb300(args):
                 for k, v in pr.items()}
 
     kernels_main = kernels_of(args.path, prof)
+    tkey = ("3d" if len(p.shape) == 3 else "2d", args.path, name)
+    if tkey in NCU_TRAFFIC_PER_UNKNOWN and "achieved" in kernels_main[name]:
+        per_u, src = NCU_TRAFFIC_PER_UNKNOWN[tkey]
+        kernels_main[name]["traffic"] = per_u * N
+        kernels_main[name]["traffic_source"] = src
     roof = dict(kernels_main[name])
     for vpath, v in variants.items():
         v["kernels"] = kernels_of(vpath, v.pop("_prof"))
