@@ -806,28 +806,53 @@ __global__ void __launch_bounds__(128) k_tri_pass2_t32(const float2* __restrict_
 constexpr int kBulkLines = 128;
 constexpr int kBulkChunks = 8;
 
-// Values per tile buffer: [array: f_hat, 1/u][row][line], then the chunk's
-// face values f1 (CH) and fn (CH + 2, starting one early when needed for a
-// 16-byte aligned source), then (pass 2) the carries Y(k-1), X(k+1) of the
-// block's lines.
-template <int CH>
-__host__ __device__ constexpr int bulk_face_offset() {
-  return 2 * CH * kBulkLines;
-}
-// (offsets and the buffer size are whole 128-byte rows: a warp's 32
-// consecutive values then take the minimum two shared-memory wavefronts)
+// Tile of one buffer, per kernel instance: [f_hat rows (Steps 1, 3)][1/u
+// rows][face values f1 (CH) and fn (CH + 2, from the even index at or before
+// nx + s: 16-byte aligned sources)][carries Y(k-1), X(k+1) of the block's
+// lines (pass 2)].  Offsets and the buffer size are whole 128-byte rows: a
+// warp's 32 consecutive values then take the minimum two shared-memory
+// wavefronts.
 __host__ __device__ constexpr int bulk_round16(int v) { return (v + 15) & ~15; }
-template <int CH>
+template <int STEP, int CH>
+__host__ __device__ constexpr int bulk_iu_offset() {
+  return STEP != 2 ? CH * kBulkLines : 0;
+}
+template <int STEP, int CH>
+__host__ __device__ constexpr int bulk_face_offset() {
+  return bulk_iu_offset<STEP, CH>() + CH * kBulkLines;
+}
+template <int STEP, int CH>
 __host__ __device__ constexpr int bulk_carry_offset() {
-  return bulk_round16(bulk_face_offset<CH>() + 2 * CH + 2);
+  return bulk_round16(bulk_face_offset<STEP, CH>() + 2 * CH + 2);
 }
-template <int CH>
+template <int PASS, int STEP, int CH>
 __host__ __device__ constexpr int bulk_tile_values() {
-  return bulk_round16(bulk_carry_offset<CH>() + 2 * kBulkLines);
+  return bulk_round16(bulk_carry_offset<STEP, CH>() + (PASS == 2 ? 2 * kBulkLines : 0));
 }
-template <int CH>
+template <int PASS, int STEP, int CH>
 constexpr size_t bulk_tile_bytes() {
-  return (size_t)2 * bulk_tile_values<CH>() * sizeof(float2);  // two buffers
+  return (size_t)2 * bulk_tile_values<PASS, STEP, CH>() * sizeof(float2);  // two buffers
+}
+
+// Sum over the 32 lanes of a warp of NQ = 32 complex values per lane by
+// recursive halving: at each level a lane keeps the half of its values chosen
+// by one bit of its lane index and adds the partner's copy of that half;
+// afterwards lane q holds the warp's sum of v[q].  Fixed summation order.
+template <int NQ>
+__device__ __forceinline__ float2 warp_transpose_sum(float2 (&v)[NQ], int lane) {
+  static_assert(NQ == 32, "one sum per lane");
+#pragma unroll
+  for (int n = NQ, off = 16; off >= 1; n >>= 1, off >>= 1) {
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const float2 keep = upper ? v[i + n / 2] : v[i];
+      const float2 send = upper ? v[i] : v[i + n / 2];
+      v[i].x = keep.x + __shfl_xor_sync(0xffffffffu, send.x, off);
+      v[i].y = keep.y + __shfl_xor_sync(0xffffffffu, send.y, off);
+    }
+  }
+  return v[0];
 }
 
 template <int PASS, int STEP, int CH>
@@ -838,13 +863,19 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
                                                              const void* __restrict__ consts,
                                                              const int* __restrict__ skip, int* __restrict__ err) {
   using C = float2;
-  constexpr int TILE = bulk_tile_values<CH>();  // values per buffer
+  constexpr int TILE = bulk_tile_values<PASS, STEP, CH>();  // values per buffer
+  constexpr int IU = bulk_iu_offset<STEP, CH>();
+  constexpr int FO = bulk_face_offset<STEP, CH>();
+  constexpr int CO = bulk_carry_offset<STEP, CH>();
+  constexpr bool SUMS = PASS == 2 && STEP != 3;  // face contributions reduced per block
+  static_assert(!SUMS || 2 * CH == 32, "one face sum per lane");
   constexpr bool RHS = STEP != 2;               // Step 2 takes its rhs from the face vectors
   constexpr bool FACES = STEP != 1;             // Steps 2, 3 read the face vectors f1, fn
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* const tile = reinterpret_cast<C*>(smem_raw);
   __shared__ __align__(8) uint64_t bar[2];
+  __shared__ C wpart[SUMS ? kBulkLines : 1];  // [warp][quantity] warp sums of the face contributions
   const int64_t n1 = a.n1, nx = a.nx;
   const int64_t l0 = (int64_t)blockIdx.x * kBulkLines;
   const int nl = (int)min((int64_t)kBulkLines, n1 - l0);
@@ -875,15 +906,15 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
     C* buf = tile + bsel * TILE;
     for (int t = 0; t < cnt; ++t) {
       if (RHS) bulk_g2s(buf + t * kBulkLines, fhat + (s + t) * n1 + l0, row_bytes, &bar[bsel]);
-      bulk_g2s(buf + (CH + t) * kBulkLines, tb.iu + (s + t) * n1 + l0, row_bytes, &bar[bsel]);
+      bulk_g2s(buf + IU + t * kBulkLines, tb.iu + (s + t) * n1 + l0, row_bytes, &bar[bsel]);
     }
     if (FACES) {
-      C* fb = buf + bulk_face_offset<CH>();
+      C* fb = buf + FO;
       bulk_g2s(fb, faces + s, n_f1 * (uint32_t)sizeof(C), &bar[bsel]);
       bulk_g2s(fb + CH, faces + fa, n_fn * (uint32_t)sizeof(C), &bar[bsel]);
     }
     if (PASS == 2) {
-      C* cb = buf + bulk_carry_offset<CH>();
+      C* cb = buf + CO;
       bulk_g2s(cb, rec.a + k * n1 + l0, row_bytes, &bar[bsel]);
       bulk_g2s(cb + kBulkLines, rec.bsum + k * n1 + l0, row_bytes, &bar[bsel]);
     }
@@ -916,14 +947,14 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
       break;
     }
     if (tid == 0) pending &= ~(1u << bsel);
-    C* const frow = tile + bsel * TILE;      // [CH][128] f_hat rows
-    C* const irow = frow + CH * kBulkLines;  // [CH][128] 1/u rows
-    const C* const sf1 = frow + bulk_face_offset<CH>();  // f1[s + t]
+    const C* const frow = tile + bsel * TILE;  // [CH][128] f_hat rows (Steps 1, 3)
+    const C* const irow = frow + IU;           // [CH][128] 1/u rows
+    const C* const sf1 = frow + FO;            // f1[s + t]
     const C* const sfn = sf1 + CH + (int)((nx + s) & 1);  // fn[s + t]
     C yp = zero, xn = zero;
     if (PASS == 2) {
-      yp = frow[bulk_carry_offset<CH>() + tid];               // Y(k-1)
-      xn = frow[bulk_carry_offset<CH>() + kBulkLines + tid];  // X(k+1)
+      yp = frow[CO + tid];               // Y(k-1)
+      xn = frow[CO + kBulkLines + tid];  // X(k+1)
     }
     auto rhs = [&](int t) -> C {
       if (STEP == 1) return cmul(frow[t * kBulkLines + tid], lv.scal);
@@ -957,15 +988,15 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
           iprev = irow[t * kBulkLines + tid];
         }
       }
-      // backward sweep; Steps 1, 2 put their face contributions over the
-      // consumed tile (each thread only rewrites its own column)
-      C* const red = frow;  // [2][CH][128]
+      // backward sweep; Steps 1, 2 keep their face contributions in
+      // registers (sv[face * CH + row]) for the warp sums
+      C sv[SUMS ? 2 * CH : 1];
 #pragma unroll
       for (int t = CH - 1; t >= 0; --t) {
         if (t < cnt) {
           const C x = cmul(csub(y[t], cmul(b, xn)), irow[t * kBulkLines + tid]);
           xn = x;
-          if (STEP == 3) {
+          if constexpr (!SUMS) {
             if (act) out[(s + t) * n1 + l] = x;
           } else {
             C s1, sn;
@@ -977,16 +1008,34 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
               s1 = tt;
               sn = cscale(tt, lv.par);
             }
-            red[t * kBulkLines + tid] = s1;
-            red[(CH + t) * kBulkLines + tid] = sn;
+            sv[t] = s1;
+            sv[CH + t] = sn;
+          }
+        } else if constexpr (SUMS) {
+          sv[t] = zero;
+          sv[CH + t] = zero;
+        }
+      }
+      if constexpr (SUMS) {
+        // lane q of each warp: the warp's sum of quantity q = face * CH + row;
+        // then thread q adds the four warps' sums in order
+        const int lane = tid & 31, warp = tid >> 5;
+        wpart[warp * 32 + lane] = warp_transpose_sum<2 * CH>(sv, lane);
+        __syncthreads();  // also: every thread has finished with the tile
+        if (tid < 2 * CH) {
+          const int face = tid / CH, t = tid - face * CH;
+          if (t < cnt) {
+            C acc = wpart[tid];
+#pragma unroll
+            for (int w = 1; w < kBulkLines / 32; ++w) acc = cadd(acc, wpart[w * 32 + tid]);
+            partial[(face * nparts + (int64_t)blockIdx.x) * nx + s + t] = acc;
           }
         }
       }
-      if (STEP != 3) block_face_sums<C, CH>(red, cnt, partial, (int64_t)blockIdx.x, nparts, nx, s);
     }
     // the buffer is consumed: it may be refilled (in pass 2 of Steps 1, 2 the
-    // face sums' second barrier already follows the last read of the tile)
-    if (PASS == 1 || STEP == 3) __syncthreads();
+    // barrier of the warp sums already follows the last read of the tile)
+    if (!SUMS) __syncthreads();
     if (tid == 0 && k + 2 < ke) {
       issue(k + 2, bsel);
       pending |= 1u << bsel;
@@ -1212,17 +1261,18 @@ cudaError_t launch_tri2d_t32(int step, const void* fhat, const void* faces, cons
   const bool bulk = (a.n1 % 2) == 0;
   const dim3 gbulk((unsigned)((a.n1 + kBulkLines - 1) / kBulkLines),
                    (unsigned)((a.nchunks + kBulkChunks - 1) / kBulkChunks));
-  const size_t sbulk = bulk_tile_bytes<kChunkF32>();
+
 #define HELM_TRI_T32(S)                                                                                        \
   do {                                                                                                        \
     if (bulk) {                                                                                               \
       auto k1 = k_tri_bulk_t32<1, S, kChunkF32>;                                                              \
       auto k2 = k_tri_bulk_t32<2, S, kChunkF32>;                                                              \
-      cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbulk);                     \
-      cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbulk);                     \
+      const size_t sb1 = bulk_tile_bytes<1, S, kChunkF32>(), sb2 = bulk_tile_bytes<2, S, kChunkF32>();        \
+      cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb1);                       \
+      cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb2);                       \
       {                                                                                                       \
         ProfScope ps(prof, n1s[S - 1], st);                                                                   \
-        k1<<<gbulk, kBulkLines, sbulk, st>>>((const float2*)fhat, (const float2*)faces, tb, r, nullptr, nullptr, \
+        k1<<<gbulk, kBulkLines, sb1, st>>>((const float2*)fhat, (const float2*)faces, tb, r, nullptr, nullptr, \
                                              a, consts, skip, err);                                           \
       }                                                                                                       \
       {                                                                                                       \
@@ -1231,7 +1281,7 @@ cudaError_t launch_tri2d_t32(int step, const void* fhat, const void* faces, cons
       }                                                                                                       \
       {                                                                                                       \
         ProfScope ps(prof, n2s[S - 1], st);                                                                   \
-        k2<<<gbulk, kBulkLines, sbulk, st>>>((const float2*)fhat, (const float2*)faces, tb, r, (float2*)out,  \
+        k2<<<gbulk, kBulkLines, sb2, st>>>((const float2*)fhat, (const float2*)faces, tb, r, (float2*)out,  \
                                              (float2*)partial, a, consts, skip, err);                         \
       }                                                                                                       \
       break;                                                                                                  \
