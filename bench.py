@@ -9,7 +9,7 @@ One step = one full solve (Steps 1-3 of the paper's Section 4.2, with the
 forward and inverse transforms) of the whole workload with inputs resident in
 HBM.  The main line (`--path`, default c64_ff) is the mixed-precision solve:
 complex64 solves with per-plan FP64-built pivot tables, iterative refinement
-on a float-float residual to ||r||/||f|| <= 1e-11, the loop launched as one
+on a float-float residual to ||r||/||f|| <= 2e-11, the loop launched as one
 CUDA graph.  Its sampled error against the stored oracle solution is checked
 in the run.  The plain complex128 path (FP64 arithmetic throughout) and the
 refinement with an FP64 residual are reported under "variants".  Under
@@ -55,11 +55,13 @@ PATHS_NAMES = tuple(PATHS)
 PATH_DTYPE = {"c128": "f64", "c64_refined": "f32 solves + f64 residual",
               "c64_ff": "f32 solves + float-float residual"}
 PATH_PRECISION = {"c128": "complex128 plain",
-                  "c64_refined": "complex64 solves, FP64 residual, refined to ||r||/||f|| <= 1e-11",
-                  "c64_ff": "complex64 solves, float-float residual, refined to ||r||/||f|| <= 1e-11"}
+                  "c64_refined": "complex64 solves, FP64 residual, refined to ||r||/||f|| <= 2e-11",
+                  "c64_ff": "complex64 solves, float-float residual, refined to ||r||/||f|| <= 2e-11"}
 # Refinement stop: with the error/residual ratio measured on the 2D and 3D
-# workloads (<= 3.1), ||r||/||f|| <= 1e-11 keeps the error below 1e-10.
-REFINE_TOL = 1e-11
+# workloads (<= 3.1), ||r||/||f|| <= 2e-11 keeps the error below 6.2e-11;
+# every run also checks the sampled error against the oracle's solution and
+# fails above 1e-10.
+REFINE_TOL = 2e-11
 # solves run under the library's per-kernel event profiler after the timed
 # region (the per-kernel breakdown; never part of `value`)
 PROFILE_SOLVES = 2
