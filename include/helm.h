@@ -266,6 +266,93 @@ int helm_batch_destroy(helm_batch_t b);
 int helm_solve_2d_static(int64_t nx, int64_t ny, double hx, double hy, double omega,
                          const void* f, void* u, void* cuda_stream);
 
+/* --- Server: a stream of independent requests with plan reuse -------------
+ * The paper's method has no serving layer; this one keeps plans and their
+ * eigen-data on the device between requests (domain-decomposition sweeps
+ * solve one operator for many right-hand sides), and overlaps independent
+ * requests on the GPU.
+ *
+ * A server owns one scheduler thread, `nslots` CUDA streams (1..16) and a
+ * cache of plans keyed by (dim, n, h, omega, dtype, residual, tol, max_iter).
+ * Requests enter a FIFO queue.  The scheduler starts the oldest request that
+ * can start whenever a slot is free: its operator's plan is taken from the
+ * cache, or built if the device memory in use (cached plans, counted by
+ * their helm_info.device_bytes) plus an estimate of the new plan stays within
+ * `device_budget_bytes` after idle cached plans are evicted least recently
+ * used first.  The estimate is 64 MiB plus, per unknown, 100 B (2D complex64
+ * modes), 200 B (2D HELM_C128), 112 B (3D complex64) or 128 B (3D
+ * HELM_C128).  A request whose plan is busy with another request waits while
+ * later requests for other operators start (a plan serves one request at a
+ * time).  Building a plan synchronises the device, so it waits for the work
+ * in flight.  A request's right-hand sides are solved one after another on
+ * its slot's stream.  Every solve is the plan's helm_solve: each result is
+ * the same as the one helm_solve gives for that request alone.
+ *
+ * f and u are DEVICE pointers of the server's device, nrhs * N complex
+ * values each (complex64 for HELM_C64_RAW, complex128 otherwise; N = nx ny
+ * (nz)), right-hand side after right-hand side; they must stay valid and
+ * untouched until the request is reported done, and f must not overlap u.
+ * The caller owns them. */
+typedef struct helm_server* helm_server_t;
+
+typedef struct helm_request {
+  int32_t dim;       /* 2 or 3 */
+  int64_t n[3];      /* node counts, n[2] ignored in 2D */
+  double h[3];       /* spacings, h[2] ignored in 2D */
+  double omega;      /* wave number */
+  int32_t dtype;     /* helm_dtype */
+  int32_t residual;  /* helm_residual (HELM_C64_REFINED only, else ignored) */
+  double tol;        /* refinement tolerance (HELM_C64_REFINED only) */
+  int32_t max_iter;  /* refinement sweep limit 1..15 (HELM_C64_REFINED only) */
+  int32_t nrhs;      /* right-hand sides, >= 1 */
+  const void* f;     /* device, nrhs * N values */
+  void* u;           /* device, nrhs * N values */
+} helm_request;
+
+typedef struct helm_request_result {
+  int32_t done;        /* 1 once the request has finished (or failed) */
+  int32_t status;      /* helm_status of the request (valid when done) */
+  double queue_s;      /* submit -> start of its first launch (host clock) */
+  double latency_s;    /* submit -> completion seen by the scheduler */
+  int32_t plan_reused; /* 1 if its plan came from the cache */
+  int32_t iterations;  /* refinement sweeps of its last right-hand side */
+  int32_t converged;   /* 1 if its last right-hand side met tol (refined modes;
+                          status HELM_ENOTCONV otherwise, u still written) */
+  double residual;     /* final ||r||/||f|| of its last right-hand side */
+} helm_request_result;
+
+typedef struct helm_server_stats {
+  int64_t submitted, completed, failed;
+  int64_t plans_built, plans_reused, plans_evicted;
+  double unknowns_solved;   /* sum of N * nrhs over completed requests */
+  double elapsed_s;         /* first submit -> last completion */
+  double latency_p50_s, latency_p99_s, latency_mean_s;  /* completed requests */
+  size_t device_bytes_in_use, device_bytes_peak;        /* cached plans */
+} helm_server_stats;
+
+/* helm_server_create: nslots 1..16, device_budget_bytes > 0 (plans only; the
+ * request buffers are the caller's).  Uses the CUDA device current in the
+ * calling thread.  HELM_EINVAL on bad arguments, HELM_ECUDA if no device.
+ * helm_server_submit: validates the request (HELM_EINVAL), copies it, and
+ * returns at once with *ticket >= 1.  A request that cannot fit the budget
+ * even with every idle plan evicted fails with HELM_ENOMEM; one the kernels
+ * cannot run fails with that plan's status (e.g. HELM_EUNSUPPORTED).
+ * helm_server_wait: waits up to timeout_s (< 0: no limit) for the request;
+ * fills *res (may be NULL); returns HELM_ETIMEOUT if it is still running,
+ * HELM_EINVAL for an unknown ticket, else HELM_OK (the request's own status
+ * is res->status).  A finished request's result stays available until the
+ * server is destroyed.
+ * helm_server_drain: waits (bounded as above) until every submitted request
+ * has finished.  helm_server_get_stats: counters and latency percentiles of
+ * the completed requests.  helm_server_destroy: waits for the queued and
+ * running requests, frees the plans, streams and thread; NULL is allowed. */
+int helm_server_create(helm_server_t* out, int32_t nslots, size_t device_budget_bytes);
+int helm_server_submit(helm_server_t s, const helm_request* req, int64_t* ticket);
+int helm_server_wait(helm_server_t s, int64_t ticket, double timeout_s, helm_request_result* res);
+int helm_server_drain(helm_server_t s, double timeout_s);
+int helm_server_get_stats(helm_server_t s, helm_server_stats* st);
+int helm_server_destroy(helm_server_t s);
+
 /* --- Host-side plan helpers (no GPU needed) --------------------------------
  * Eigen-data of the 1D absorbing pencil K V = M V Lam (eq. EVP1a) with
  * V^T M V = I (eq. EVPcondA), K, M of eqs. matrixK / matrixM with n nodes,

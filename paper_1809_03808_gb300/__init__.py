@@ -43,6 +43,28 @@ class helm_profile_entry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int32), ("total_ms", ctypes.c_double)]
 
 
+class helm_request(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("n", ctypes.c_int64 * 3), ("h", ctypes.c_double * 3),
+                ("omega", ctypes.c_double), ("dtype", ctypes.c_int32), ("residual", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("nrhs", ctypes.c_int32),
+                ("f", ctypes.c_void_p), ("u", ctypes.c_void_p)]
+
+
+class helm_request_result(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int32), ("queue_s", ctypes.c_double),
+                ("latency_s", ctypes.c_double), ("plan_reused", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("residual", ctypes.c_double)]
+
+
+class helm_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("plans_built", ctypes.c_int64), ("plans_reused", ctypes.c_int64),
+                ("plans_evicted", ctypes.c_int64), ("unknowns_solved", ctypes.c_double),
+                ("elapsed_s", ctypes.c_double), ("latency_p50_s", ctypes.c_double),
+                ("latency_p99_s", ctypes.c_double), ("latency_mean_s", ctypes.c_double),
+                ("device_bytes_in_use", ctypes.c_size_t), ("device_bytes_peak", ctypes.c_size_t)]
+
+
 _SIGS = {
     "helm_plan_2d": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _dbl, _dbl, _dbl, _i32]),
     "helm_plan_3d": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _i64, _dbl, _dbl, _dbl, _dbl, _i32]),
@@ -68,6 +90,12 @@ _SIGS = {
     "helm_batch_solve": (_i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "helm_batch_last_error": (ctypes.c_char_p, [_vp]),
     "helm_batch_destroy": (_i32, [_vp]),
+    "helm_server_create": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.c_size_t]),
+    "helm_server_submit": (_i32, [_vp, ctypes.POINTER(helm_request), ctypes.POINTER(_i64)]),
+    "helm_server_wait": (_i32, [_vp, _i64, _dbl, ctypes.POINTER(helm_request_result)]),
+    "helm_server_drain": (_i32, [_vp, _dbl]),
+    "helm_server_get_stats": (_i32, [_vp, ctypes.POINTER(helm_server_stats)]),
+    "helm_server_destroy": (_i32, [_vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -290,6 +318,71 @@ class Batch:
         if getattr(self, "handle", None):
             lib.helm_batch_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """A request server (helm_server_*): plan cache under a device-memory
+    budget, `nslots` CUDA streams, one scheduler thread.
+
+    submit() takes CUDA tensors f and u holding nrhs right-hand sides one
+    after another (shape (nrhs, *shape) or the plan layout when nrhs = 1);
+    they must stay alive until wait() reports the request done."""
+
+    def __init__(self, nslots=4, device_budget_bytes=64 << 30):
+        h = _vp()
+        st = lib.helm_server_create(ctypes.byref(h), int(nslots), int(device_budget_bytes))
+        if st != HELM_OK:
+            raise HelmError(st, "helm_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, shape, h, omega, f, u, dtype=HELM_C64_REFINED, residual=HELM_RESID_FF, tol=1e-12,
+               max_iter=10, nrhs=1):
+        r = helm_request()
+        r.dim = len(shape)
+        for k, n in enumerate(shape):
+            r.n[k] = int(n)
+            r.h[k] = float(h[k])
+        r.omega = float(omega)
+        r.dtype, r.residual, r.tol, r.max_iter, r.nrhs = int(dtype), int(residual), float(tol), int(max_iter), int(nrhs)
+        r.f, r.u = _ptr(f), _ptr(u)
+        t = _i64()
+        st = lib.helm_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t))
+        if st != HELM_OK:
+            raise HelmError(st, "helm_server_submit")
+        self._keep[t.value] = (f, u)
+        return t.value
+
+    def wait(self, ticket, timeout_s=-1.0):
+        res = helm_request_result()
+        st = lib.helm_server_wait(self.handle, int(ticket), float(timeout_s), ctypes.byref(res))
+        if st not in (HELM_OK, HELM_ETIMEOUT):
+            raise HelmError(st, "helm_server_wait")
+        if res.done:
+            self._keep.pop(int(ticket), None)
+        return res
+
+    def drain(self, timeout_s=-1.0):
+        st = lib.helm_server_drain(self.handle, float(timeout_s))
+        if st != HELM_OK:
+            raise HelmError(st, "helm_server_drain")
+
+    def stats(self):
+        st = helm_server_stats()
+        _check(lib.helm_server_get_stats(self.handle, ctypes.byref(st)), "helm_server_get_stats")
+        return st
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.helm_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
 
     def __del__(self):
         try:
