@@ -243,6 +243,8 @@ def run_gb300(args):
 
     if args.workload == "batch2d":
         return run_batch(args, helm, torch, dev, world, rank, local)
+    if args.workload == "serve3d":
+        return run_serve(args, helm, torch, dev, world, rank, local)
     p = workloads.config_3d() if args.workload == "3d" else workloads.config_2d_large()
     if args.shape:
         p = workloads.scaled(p, tuple(int(x) for x in args.shape.split(",")))
@@ -506,6 +508,90 @@ def run_batch(args, helm, torch, dev, world, rank, local):
         print(json.dumps(line))
 
 
+def run_serve(args, helm, torch, dev, world, rank, local):
+    """The serving workload (workloads.serve_3d): a Poisson stream of 3D
+    requests, 1-64 right-hand sides each, over a pool of operators, submitted
+    at their arrival times to one helm_server (plan cache under a device
+    budget, several streams).  Complex64 solves refined on the float-float
+    residual to ||r||/||f|| <= REFINE_TOL.  value = unknowns x right-hand
+    sides solved / wall time from the first arrival to the last completion
+    (plan builds included); latency percentiles from submit to completion."""
+    reqs = workloads.serve_3d(args.serve_count, rate_per_s=args.serve_rate)
+    budget = int(args.serve_budget_gb * (1 << 30))
+    gen = torch.Generator(device=dev)
+
+    def make_rhs(q, nrhs):
+        gen.manual_seed(q.seed)
+        re = torch.randn((nrhs, *q.shape), dtype=torch.float64, device=dev, generator=gen)
+        im = torch.randn((nrhs, *q.shape), dtype=torch.float64, device=dev, generator=gen)
+        return torch.complex(re, im)
+
+    # warm-up: library load and one small request on a separate server
+    q0, _, _ = reqs[0]
+    w = helm.Server(nslots=1, device_budget_bytes=budget)
+    f0 = make_rhs(workloads.scaled(q0, (31, 32, 32)), 1)
+    u0 = torch.empty_like(f0)
+    torch.cuda.synchronize()
+    w.wait(w.submit((31, 32, 32), q0.h, q0.omega, f0, u0, tol=REFINE_TOL, max_iter=10), -1.0)
+    w.close()
+    del f0, u0
+
+    srv = helm.Server(nslots=args.serve_slots, device_budget_bytes=budget)
+    clk = ClockSampler(local)
+    clk.start()
+    t0 = time.perf_counter()
+    tickets, results = [], {}
+
+    def collect(block):
+        for t in tickets:
+            if t not in results:
+                r = srv.wait(t, -1.0 if block else 0.0)
+                if r.done:
+                    results[t] = r  # the server drops its references to f, u
+
+    for q, nrhs, at in reqs:
+        delay = at - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        f = make_rhs(q, nrhs)
+        u = torch.empty_like(f)
+        torch.cuda.current_stream(dev).synchronize()  # the server's streams do not wait on torch's
+        tickets.append(srv.submit(q.shape, q.h, q.omega, f, u, tol=REFINE_TOL, max_iter=10, nrhs=nrhs))
+        del f, u
+        collect(False)
+    collect(True)
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    st = srv.stats()
+    srv.close()
+    ok = [r for r in results.values() if r.status == helm.HELM_OK]
+    line = {
+        "metric": METRIC, "value": world * st.unknowns_solved / wall, "unit": UNIT, "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": PATH_DTYPE["c64_ff"],
+        "data": "synthetic (complex Gaussians from a seeded torch CUDA generator)",
+        "config": {"workload": f"serve3d_{len(reqs)}", "requests": len(reqs),
+                   "operators": len({q.shape for q, _, _ in reqs}), "arrival_rate_per_s": args.serve_rate,
+                   "slots": args.serve_slots, "device_budget_bytes": budget,
+                   "unknowns_x_rhs": sum(q.N * n for q, n, _ in reqs),
+                   "nodes_range": [min(min(q.shape) for q, _, _ in reqs), max(max(q.shape) for q, _, _ in reqs)],
+                   "nrhs_range": [min(n for _, n, _ in reqs), max(n for _, n, _ in reqs)],
+                   "precision": PATH_PRECISION["c64_ff"], "launch": "helm_server (plan cache, FIFO admission)",
+                   "parallelism": f"replicas x{world}"},
+        "latency": {"p50_s": st.latency_p50_s, "p99_s": st.latency_p99_s, "mean_s": st.latency_mean_s,
+                    "queue_p50_s": sorted(r.queue_s for r in results.values())[len(results) // 2]},
+        "server": {"completed": st.completed, "failed": st.failed, "plans_built": st.plans_built,
+                   "plans_reused": st.plans_reused, "plans_evicted": st.plans_evicted,
+                   "device_bytes_peak": st.device_bytes_peak},
+        "refinement": {"converged": len(ok), "requests": len(reqs),
+                       "worst_final_rel_residual": max((r.residual for r in results.values()), default=None),
+                       "tol": REFINE_TOL},
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def cpu_baseline_run(p, steps):
     from oracle import solvers
 
@@ -566,9 +652,14 @@ def main():
                     "(profiling cases; not a benchmark line)")
     ap.add_argument("--minimal", action="store_true", help="timed solves only (no e2e, variants, CPU baseline)")
     ap.add_argument("--batch-count", type=int, default=512, help="problems of --workload batch2d")
-    ap.add_argument("--workload", default="2d_large", choices=["2d_large", "3d", "batch2d"],
+    ap.add_argument("--workload", default="2d_large", choices=["2d_large", "3d", "batch2d", "serve3d"],
                     help="2d_large: the benchmark workload; 3d: the 512^3 workload; batch2d: 512 independent 2D "
-                    "problems in one graph launch (measurements, not the bench line)")
+                    "problems in one graph launch; serve3d: a Poisson stream of 3D requests through "
+                    "helm_server (measurements, not the bench line)")
+    ap.add_argument("--serve-count", type=int, default=32, help="requests of --workload serve3d")
+    ap.add_argument("--serve-rate", type=float, default=4.0, help="mean arrivals per second (serve3d)")
+    ap.add_argument("--serve-slots", type=int, default=4, help="server streams (serve3d)")
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="plan-cache device budget (serve3d)")
     ap.add_argument("--path", default="c64_ff", choices=list(PATHS_NAMES),
                     help="path timed as the main line (the others are reported as variants)")
     args = ap.parse_args()

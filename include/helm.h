@@ -292,7 +292,9 @@ int helm_solve_2d_static(int64_t nx, int64_t ny, double hx, double hy, double om
  * values each (complex64 for HELM_C64_RAW, complex128 otherwise; N = nx ny
  * (nz)), right-hand side after right-hand side; they must stay valid and
  * untouched until the request is reported done, and f must not overlap u.
- * The caller owns them. */
+ * The server's streams do not wait on the caller's: the work that writes f
+ * (or last touches u) must be complete when helm_server_submit is called
+ * (e.g. its stream synchronised).  The caller owns them. */
 typedef struct helm_server* helm_server_t;
 
 typedef struct helm_request {

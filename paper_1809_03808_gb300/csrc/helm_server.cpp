@@ -177,14 +177,15 @@ void helm_server::finish(Slot& sl, cudaError_t q) {
   if (q != cudaSuccess && r->status == HELM_OK) r->status = HELM_ECUDA;
   if (r->status == HELM_OK) {
     helm_info info;
-    const int rc = helm_get_info(sl.plan->plan, &info);  // the slot's work is complete
-    if (!rc) {
+    int rc = helm_get_info(sl.plan->plan, &info);  // the slot's work is complete
+    const bool filled = rc == HELM_OK || rc == HELM_ENOTCONV;  // ENOTCONV: info is filled
+    if (filled) {
       // a plan's first solve may add buffers (the float-float vectors)
       in_use = in_use - std::min(in_use, sl.plan->bytes) + info.device_bytes;
       sl.plan->bytes = info.device_bytes;
       peak = std::max(peak, in_use);
     }
-    if (rc) {
+    if (!filled) {
       r->status = rc;
     } else if (r->spec.dtype == HELM_C64_REFINED) {
       r->iterations = info.iterations;
@@ -276,7 +277,10 @@ bool helm_server::start_one(std::unique_lock<std::mutex>& lk) {
                                           sp.dtype);
       if (!rc) rc = configure(plan, sp);
       helm_info info;
-      if (!rc) rc = helm_get_info(plan, &info);
+      if (!rc) {
+        rc = helm_get_info(plan, &info);
+        if (rc == HELM_ENOTCONV) rc = HELM_OK;  // the state of the plan's trial solves: info is filled
+      }
       if (rc && plan) {
         helm_destroy(plan);
         plan = nullptr;

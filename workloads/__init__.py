@@ -120,6 +120,37 @@ def batch_2d(count: int = 512, seed: int = 1000) -> list:
     return out
 
 
+def serve_3d(count: int = 32, operators: int = 12, rate_per_s: float = 4.0, seed: int = 2000) -> list:
+    """Serving workload: a Poisson stream of `count` 3D requests over a pool of
+    `operators` box problems (domain-decomposition sweeps reuse one operator
+    for many right-hand sides).
+
+    Per operator: nx uniform on {31..255}; ny, nz (the transform axes) uniform
+    on the values in {31..255} whose prime factors are all <= 64; side lengths
+    uniform on [0.5, 2] per axis; omega for a uniform 8..12 nodes per
+    wavelength at max(h).  Per request: an operator drawn uniformly from the
+    pool, nrhs uniform on {1..64}, arrival after an exponential gap of mean
+    1 / rate_per_s.  Returns [(Problem, nrhs, arrival_s)]; the right-hand
+    sides are seeded complex Gaussians (Problem.seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    smooth = [n for n in range(31, 256) if _max_prime_factor(n) <= 64]
+    ops = []
+    for k in range(operators):
+        nx = int(rng.integers(31, 256))
+        ny = int(smooth[int(rng.integers(0, len(smooth)))])
+        nz = int(smooth[int(rng.integers(0, len(smooth)))])
+        h = tuple(float(rng.uniform(0.5, 2.0)) / (n - 1) for n in (nx, ny, nz))
+        omega = ppw_omega(max(h), float(rng.uniform(8.0, 12.0)))
+        ops.append(((nx, ny, nz), h, omega))
+    out, t = [], 0.0
+    for i in range(count):
+        shape, h, omega = ops[int(rng.integers(0, operators))]
+        nrhs = int(rng.integers(1, 65))
+        t += float(rng.exponential(1.0 / rate_per_s))
+        out.append((Problem(name=f"serve3d_{i}", shape=shape, h=h, omega=omega, seed=seed + 1 + i), nrhs, t))
+    return out
+
+
 def scaled(p: Problem, shape, seed=None, name=None) -> Problem:
     """Same spacing and wave number as `p` on a smaller node grid (bounded samples)."""
     return Problem(name=name or f"{p.name}_sample{'x'.join(map(str, shape))}",
