@@ -657,7 +657,8 @@ def main():
                     "problems in one graph launch; serve3d: a Poisson stream of 3D requests through "
                     "helm_server (measurements, not the bench line)")
     ap.add_argument("--serve-count", type=int, default=32, help="requests of --workload serve3d")
-    ap.add_argument("--serve-rate", type=float, default=4.0, help="mean arrivals per second (serve3d)")
+    ap.add_argument("--serve-rate", type=float, default=4.0,
+                    help="mean arrivals per second (serve3d); <= 0: all requests at once (capacity)")
     ap.add_argument("--serve-slots", type=int, default=4, help="server streams (serve3d)")
     ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="plan-cache device budget (serve3d)")
     ap.add_argument("--path", default="c64_ff", choices=list(PATHS_NAMES),

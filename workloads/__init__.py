@@ -130,7 +130,8 @@ def serve_3d(count: int = 32, operators: int = 12, rate_per_s: float = 4.0, seed
     uniform on [0.5, 2] per axis; omega for a uniform 8..12 nodes per
     wavelength at max(h).  Per request: an operator drawn uniformly from the
     pool, nrhs uniform on {1..64}, arrival after an exponential gap of mean
-    1 / rate_per_s.  Returns [(Problem, nrhs, arrival_s)]; the right-hand
+    1 / rate_per_s (rate_per_s <= 0: every request arrives at time 0, the
+    saturated stream).  Returns [(Problem, nrhs, arrival_s)]; the right-hand
     sides are seeded complex Gaussians (Problem.seed)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     smooth = [n for n in range(31, 256) if _max_prime_factor(n) <= 64]
@@ -146,7 +147,7 @@ def serve_3d(count: int = 32, operators: int = 12, rate_per_s: float = 4.0, seed
     for i in range(count):
         shape, h, omega = ops[int(rng.integers(0, operators))]
         nrhs = int(rng.integers(1, 65))
-        t += float(rng.exponential(1.0 / rate_per_s))
+        t += float(rng.exponential(1.0 / rate_per_s)) if rate_per_s > 0 else 0.0
         out.append((Problem(name=f"serve3d_{i}", shape=shape, h=h, omega=omega, seed=seed + 1 + i), nrhs, t))
     return out
 
