@@ -147,7 +147,8 @@ def serve_3d(count: int = 32, operators: int = 12, rate_per_s: float = 4.0, seed
     for i in range(count):
         shape, h, omega = ops[int(rng.integers(0, operators))]
         nrhs = int(rng.integers(1, 65))
-        t += float(rng.exponential(1.0 / rate_per_s)) if rate_per_s > 0 else 0.0
+        gap = float(rng.exponential(1.0))  # drawn in both modes: the same requests
+        t += gap / rate_per_s if rate_per_s > 0 else 0.0
         out.append((Problem(name=f"serve3d_{i}", shape=shape, h=h, omega=omega, seed=seed + 1 + i), nrhs, t))
     return out
 
