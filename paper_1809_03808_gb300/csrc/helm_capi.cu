@@ -1028,11 +1028,41 @@ int helm_solve_debug(helm_plan_t p, const void* f, void* u, void* fhat, void* v_
   return run_solve(p, f, u, fhat, v_b, w_b);
 }
 
+namespace {
+
+// Device address of page-locked host memory mapped into the device's address
+// space, or nullptr (pageable memory, or not mapped).
+void* mapped_host(const void* h) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+}  // namespace
+
 int helm_solve_host(helm_plan_t p, const void* f_host, void* u_host) {
   if (!p || !f_host || !u_host) return HELM_EINVAL;
   const int64_t N = p->n[0] * p->n[1] * p->n[2];
   const size_t eb = p->dtype == HELM_C64_RAW ? sizeof(float2) : sizeof(double2);
   int rc;
+  // The float-float refinement reads f only in its split and writes u only in
+  // its join: with mapped page-locked buffers those two kernels work on host
+  // memory directly (the transfers overlap the conversions; no staging).
+  if (p->dtype == HELM_C64_REFINED && refine_ff(p)) {
+    void* fd = mapped_host(f_host);
+    void* ud = mapped_host(u_host);
+    if (fd && ud) {
+      const char* f0 = static_cast<const char*>(f_host);
+      const char* u0 = static_cast<const char*>(u_host);
+      if (f0 < u0 + N * eb && u0 < f0 + N * eb) return HELM_EINVAL;
+      if ((rc = run_solve(p, fd, ud, nullptr, nullptr, nullptr))) return rc;
+      HELM_CK(cudaStreamSynchronize(p->stream));
+      return HELM_OK;
+    }
+  }
   if (!p->host_f) {
     if ((rc = dev_alloc(p, (void**)&p->host_f, N * eb)) || (rc = dev_alloc(p, (void**)&p->host_u, N * eb))) return rc;
   }

@@ -154,6 +154,27 @@ def test_repeated_solves_and_host_api(env):
     assert np.array_equal(uh, u1.cpu().numpy())
 
 
+def test_host_api_float_float_mapped_and_pageable(env):
+    """helm_solve_host with the float-float residual: page-locked host buffers
+    (split and join work on them directly) and pageable ones (staged copies)
+    give the device-buffer solve bit for bit."""
+    helm, torch = env
+    shape, h, omega = CASES["ragged_65x100"]
+    f, u_ref = _oracle(shape, h, omega, seed=7)
+    plan = helm.Plan(shape, h, omega, helm.HELM_C64_REFINED)
+    helm.helm_set_residual(plan.handle, helm.HELM_RESID_FF)
+    helm.helm_set_refinement(plan.handle, 1e-12, 12)
+    u1 = plan.solve(torch.from_numpy(f).cuda()).cpu().numpy()
+    fh = torch.from_numpy(f).pin_memory()
+    uh = torch.full(f.shape, float("nan"), dtype=torch.complex128).pin_memory()
+    helm.helm_solve_host(plan.handle, fh, uh)
+    up = np.empty_like(f)
+    helm.helm_solve_host(plan.handle, f, up)
+    plan.close()
+    assert np.array_equal(uh.numpy(), u1) and np.array_equal(up, u1)
+    assert np.linalg.norm(u1 - u_ref) / np.linalg.norm(u_ref) <= TOL
+
+
 def test_unsupported_and_invalid(env):
     helm, torch = env
     with pytest.raises(helm.HelmError) as e:
