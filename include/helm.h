@@ -170,7 +170,11 @@ int helm_solve(helm_plan_t p, const void* f, void* u);
 /* Same solve with HOST pointers: copies f to the device, solves, copies u
  * back and synchronises the stream before returning (for callers without
  * device buffers; the copies are part of the call).  Page-locked host memory
- * gives full copy bandwidth; pageable memory also works. */
+ * gives full copy bandwidth; pageable memory also works.  For
+ * HELM_C64_REFINED with HELM_RESID_FF and both buffers page-locked and
+ * mapped, no copies are made: the kernels that convert f to float-float and
+ * u back read and write the host buffers directly (same results).  f and u
+ * must not overlap (HELM_EINVAL). */
 int helm_solve_host(helm_plan_t p, const void* f_host, void* u_host);
 
 /* Step-by-step variant for verification: runs the same kernels as helm_solve
