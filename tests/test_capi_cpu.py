@@ -83,3 +83,22 @@ def test_abc_eigen_rejects_bad_input(helm):
         helm.helm_abc_eigen(1, 0.1, 1.0)
     with pytest.raises(helm.HelmError):
         helm.helm_abc_eigen(10, 0.1, 0.0)
+
+
+def test_server_rejects_bad_arguments_before_touching_the_device(helm):
+    """helm_server_*: argument checks that precede any CUDA call."""
+    import ctypes
+
+    h = ctypes.c_void_p(1)
+    assert helm.lib.helm_server_create(None, 2, 1 << 30) == helm.HELM_EINVAL
+    for nslots, budget in [(0, 1 << 30), (17, 1 << 30), (2, 0)]:
+        assert helm.lib.helm_server_create(ctypes.byref(h), nslots, budget) == helm.HELM_EINVAL
+        assert h.value is None
+    t = ctypes.c_int64(5)
+    req = helm.helm_request()
+    assert helm.lib.helm_server_submit(None, ctypes.byref(req), ctypes.byref(t)) == helm.HELM_EINVAL
+    assert helm.lib.helm_server_wait(None, 1, 0.0, None) == helm.HELM_EINVAL
+    assert helm.lib.helm_server_drain(None, 0.0) == helm.HELM_EINVAL
+    st = helm.helm_server_stats()
+    assert helm.lib.helm_server_get_stats(None, ctypes.byref(st)) == helm.HELM_EINVAL
+    assert helm.lib.helm_server_destroy(None) == helm.HELM_OK
