@@ -135,11 +135,15 @@ class ClockSampler:
 # complex64 residual, the last transform writes (or updates) complex128 u.
 # Flops: real operations of the algorithm as written (complex multiply 6,
 # complex add 2, complex reciprocal 5 counting each division as 1).
-def kernel_model(name, e, n1, accum=False, first=True, tables=False, ff=False):
+def kernel_model(name, e, n1, accum=False, first=True, tables=False, ff=False, per_solve=1.0):
     import math
 
     log2n = math.log2(n1)
-    fin = 16 if first else e
+    # forward-transform input, averaged over the per_solve launches of a
+    # refined solve: the first reads f (complex128; with the float-float
+    # residual the complex64 hi parts the split wrote), the sweeps read r
+    f0 = e if ff else 16
+    fin = (f0 + (per_solve - 1.0) * e) / per_solve if first else e
     if tables:
         # FP64 with per-plan line tables: pass 1 reads rhs, m_j, w_j; pass 2
         # reads rhs, m_j, 1/u_j (and step 3 writes x)
@@ -169,12 +173,14 @@ def kernel_model(name, e, n1, accum=False, first=True, tables=False, ff=False):
         return tab3[name]
     tab = {
         "dft_fwd": (fin + e, 5.0 * log2n),
-        "dft_inv": (e + (32 if accum else 16 if e == 16 else 8), 5.0 * log2n),
+        # refined paths: the first solve writes u (16 B), the sweeps update it (32 B)
+        "dft_inv": (e + ((16.0 + (per_solve - 1.0) * 32.0) / per_solve if accum else 16 if e == 16 else 8),
+                    5.0 * log2n),
         # f, u complex128 in, r complex64 out; 9-point complex stencil
         "residual_fp64": (40.0, 40.0),
         # f, u float-float (16 B each) in, r complex64 out
         "residual_ff": (40.0, 40.0),
-        "split_ff": (32.0, 4.0),
+        "split_ff": (40.0, 4.0),  # f in, float-float f and its hi parts out
         "join_ff": (32.0, 2.0),
     }
     tab.update(tri)
@@ -195,7 +201,7 @@ NCU_TRAFFIC_PER_UNKNOWN = {
 
 def roofline_entry(name, launches, tot_ms, steps, N, e, n1, peaks, fp64, accum=False, tables=False, ff=False):
     per_launch_ms = tot_ms / launches
-    model = kernel_model(name, e, n1, accum=accum, tables=tables, ff=ff)
+    model = kernel_model(name, e, n1, accum=accum, tables=tables, ff=ff, per_solve=max(1.0, launches / steps))
     out = {"kernel": name, "launches_per_step": launches / steps, "ms_per_launch": per_launch_ms}
     if model is None:
         return out

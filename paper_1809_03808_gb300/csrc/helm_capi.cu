@@ -365,7 +365,9 @@ bool refine_ff(const helm_plan* p) { return p->resid_kind == HELM_RESID_FF; }
 
 // u0 = S(f)
 int refine_first(helm_plan* p, const void* f, void* u, void* dbg_fhat, void* dbg_v, void* dbg_w) {
-  if (refine_ff(p)) return solve_core(p, p->ffb, kInFF, p->ufb, kOutFF, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
+  // the split left the hi parts of f in the residual buffer (complex64): the
+  // first transform reads 8 B per unknown
+  if (refine_ff(p)) return solve_core(p, p->rbuf, kInC64, p->ufb, kOutFF, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
   return solve_core(p, f, kInC128, u, kOutC128, 0.0, nullptr, dbg_fhat, dbg_v, dbg_w);
 }
 
@@ -488,7 +490,7 @@ int run_refined(helm_plan* p, const void* f, void* u, void* dbg_fhat, void* dbg_
           (rc = dev_alloc(p, (void**)&p->ufb, N * sizeof(float4))))
         return rc;
     }
-    HELM_PK("split_ff", launch_split_ff((const double2*)f, p->ffb, N, p->stream));
+    HELM_PK("split_ff", launch_split_ff((const double2*)f, p->ffb, p->rbuf, N, p->stream));
   }
   const bool graph = p->use_graphs && !p->prof.on && !dbg_fhat && !dbg_v && !dbg_w;
   if (graph) {
@@ -807,7 +809,7 @@ int append_solve(helm_plan* p, const void* f, void* u, cudaStream_t cap, cudaStr
   } else {
     cudaError_t e = launch_refine_init(p->state, p->tol, p->max_iter, cap);
     if (e != cudaSuccess) rc = cuda_fail(p, e, "refine init");
-    if (!rc && refine_ff(p) && (e = launch_split_ff((const double2*)f, p->ffb, N, cap)) != cudaSuccess)
+    if (!rc && refine_ff(p) && (e = launch_split_ff((const double2*)f, p->ffb, p->rbuf, N, cap)) != cudaSuccess)
       rc = cuda_fail(p, e, "split");
     if (!rc) rc = refine_first(p, f, u, nullptr, nullptr, nullptr);
     if (!rc) rc = append_refine_loop(p, f, u, cap, body);

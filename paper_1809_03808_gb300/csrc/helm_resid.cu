@@ -721,7 +721,10 @@ __device__ __forceinline__ double2 join_one(float4 v) {
 // Element-wise kernels: each thread issues kEw independent loads before it
 // converts and stores them (enough bytes in flight to cover HBM latency).
 constexpr int kEw = 4;
-__global__ void __launch_bounds__(256) k_split_ff(const double2* __restrict__ f, float4* __restrict__ o, int64_t N) {
+// hi (optional): the hi parts again as a complex64 vector, the first
+// transform's input
+__global__ void __launch_bounds__(256) k_split_ff(const double2* __restrict__ f, float4* __restrict__ o,
+                                                  float2* __restrict__ hi, int64_t N) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (; i + (kEw - 1) * stride < N; i += kEw * stride) {
@@ -734,6 +737,7 @@ __global__ void __launch_bounds__(256) k_split_ff(const double2* __restrict__ f,
       split_d(v[j].x, q.x, q.z);
       split_d(v[j].y, q.y, q.w);
       o[i + j * stride] = q;
+      if (hi) hi[i + j * stride] = make_float2(q.x, q.y);
     }
   }
   for (; i < N; i += stride) {
@@ -742,6 +746,7 @@ __global__ void __launch_bounds__(256) k_split_ff(const double2* __restrict__ f,
     split_d(v.x, q.x, q.z);
     split_d(v.y, q.y, q.w);
     o[i] = q;
+    if (hi) hi[i] = make_float2(q.x, q.y);
   }
 }
 __global__ void __launch_bounds__(256) k_join_ff(const float4* __restrict__ q, double2* __restrict__ o, int64_t N) {
@@ -966,10 +971,10 @@ static int64_t ew_grid(int64_t N) {
   return std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, (int64_t)nsm * 8));
 }
 
-cudaError_t launch_split_ff(const double2* f, float4* out, int64_t N, cudaStream_t st) {
+cudaError_t launch_split_ff(const double2* f, float4* out, float2* hi, int64_t N, cudaStream_t st) {
   if (N == 0) return cudaSuccess;
   const int64_t grid = ew_grid(N);
-  k_split_ff<<<(unsigned)grid, 256, 0, st>>>(f, out, N);
+  k_split_ff<<<(unsigned)grid, 256, 0, st>>>(f, out, hi, N);
   return cudaGetLastError();
 }
 

@@ -92,7 +92,9 @@ cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, doubl
                                const float4* u, float2* r, double* sums, int64_t* nblocks, const int* skip,
                                cudaStream_t st);
 // complex128 -> float-float (hi = round(x), lo = round(x - hi)) and back.
-cudaError_t launch_split_ff(const double2* f, float4* out, int64_t N, cudaStream_t st);
+// f (complex128) -> float-float out; hi (may be null) also receives the hi
+// parts as complex64.
+cudaError_t launch_split_ff(const double2* f, float4* out, float2* hi, int64_t N, cudaStream_t st);
 cudaError_t launch_join_ff(const float4* u, double2* out, int64_t N, cudaStream_t st);
 // Reset *st to the start of a refinement (a kernel, so that it can be captured).
 cudaError_t launch_refine_init(RefineState* st, double tol, int max_iter, cudaStream_t stream);
