@@ -351,7 +351,10 @@ typedef struct helm_server_stats {
  * helm_server_drain: waits (bounded as above) until every submitted request
  * has finished.  helm_server_get_stats: counters and latency percentiles of
  * the completed requests.  helm_server_destroy: waits for the queued and
- * running requests, frees the plans, streams and thread; NULL is allowed. */
+ * running requests, frees the plans, streams and thread; NULL is allowed.
+ * Submit, wait, drain and get_stats may be called from any threads at once;
+ * destroy must not overlap any other call on the same server.  Each
+ * request's record (about 200 bytes) is kept until destroy. */
 int helm_server_create(helm_server_t* out, int32_t nslots, size_t device_budget_bytes);
 int helm_server_submit(helm_server_t s, const helm_request* req, int64_t* ticket);
 int helm_server_wait(helm_server_t s, int64_t ticket, double timeout_s, helm_request_result* res);
