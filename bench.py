@@ -1,20 +1,25 @@
 """Benchmark: complex unknowns solved per second by the GB300 fast Helmholtz
-solver on the 8192 x 4096-node 2D workload (ABC on all sides, 10 nodes per
-wavelength, seeded complex Gaussian load times a Gaussian bump), at relative
-error <= 1e-10 against the FP64 oracle.
+solver at relative error <= 1e-10 against the FP64 oracle.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
-One step = one full solve (Steps 1-3 of the paper's Section 4.2, with the
-forward and inverse transforms) of the whole workload with inputs resident in
-HBM.  The main line (`--path`, default c64_ff) is the mixed-precision solve:
-complex64 solves with per-plan FP64-built pivot tables, iterative refinement
-on a float-float residual to ||r||/||f|| <= 2e-11, the loop launched as one
-CUDA graph.  Its sampled error against the stored oracle solution is checked
-in the run.  The plain complex128 path (FP64 arithmetic throughout) and the
-refinement with an FP64 residual are reported under "variants".  Under
-torchrun every rank solves its own replica of the workload (the solve does
-not shard: replicas only).
+Default workload: the 512^3-node 3D problem (unit cube, ABC on all six faces,
+10 nodes per wavelength, seeded complex Gaussian load), the largest
+single-GPU configuration.  One step = one full solve (outer Steps 1-3 of the
+paper's Section 5.2 with the inner 2D solves of Section 5.1.2, the forward
+and inverse transforms) of the whole workload with inputs resident in HBM.
+The main line (`--path`, default c64_refined) is the mixed-precision solve:
+complex64 transforms and tridiagonal solves with per-plan FP64-built pivot
+tables, iterative refinement on an FP64 residual (27-point stencil in FP64)
+to ||r||/||f|| <= 2e-11, the loop launched as one CUDA graph.  Its sampled
+error against the stored oracle solution is checked in the run.  The plain
+complex128 solve, the float-float-residual refinement and the 8192 x 4096 2D
+workload in plain complex128 are reported under "variants".  Under torchrun
+every rank solves its own replica of the workload (replicas only).
+
+The JSON line on stdout is kept short (per-kernel milliseconds, compact
+variants); the full per-kernel roofline table goes to stderr as a second
+JSON object.
 
 --impl reference times the CPU oracle (test infrastructure) on a bounded
 sample of the same workload on the host cores.
@@ -67,10 +72,22 @@ REFINE_TOL = 2e-11
 PROFILE_SOLVES = 2
 
 
-def sample_shape():
-    """Bounded CPU sample: 2048 x 1024 nodes with the workload's spacing and
-    wave number (about 10-30 s of oracle work on the host cores)."""
-    return (2048, 1024)
+def sample_shape(workload="3d"):
+    """Bounded CPU sample with the workload's spacing and wave number (about
+    10-30 s of oracle work on the host cores): 128^3 nodes in 3D, 2048 x 1024
+    in 2D."""
+    return (128, 128, 128) if workload == "3d" else (2048, 1024)
+
+
+def workload_problem(name):
+    return workloads.config_3d() if name == "3d" else workloads.config_2d_large()
+
+
+def sig(x, d=4):
+    """Round to d significant digits (compact JSON)."""
+    if x is None or isinstance(x, (bool, str)):
+        return x
+    return float(f"{x:.{d}g}")
 
 
 def dist_setup():
@@ -251,12 +268,6 @@ def run_gb300(args):
         return run_batch(args, helm, torch, dev, world, rank, local)
     if args.workload == "serve3d":
         return run_serve(args, helm, torch, dev, world, rank, local)
-    p = workloads.config_3d() if args.workload == "3d" else workloads.config_2d_large()
-    if args.shape:
-        p = workloads.scaled(p, tuple(int(x) for x in args.shape.split(",")))
-    N = p.N
-    f_host = workloads.rhs(p)
-    f = torch.from_numpy(f_host).to(dev)
     stream = torch.cuda.current_stream(dev)
 
     def barrier():
@@ -274,7 +285,14 @@ def run_gb300(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    def timed(plan, u):
+    def load_problem(wl):
+        p = workload_problem(wl)
+        if args.shape and wl == args.workload:
+            p = workloads.scaled(p, tuple(int(x) for x in args.shape.split(",")))
+        f_host = workloads.rhs(p)
+        return p, f_host, torch.from_numpy(f_host).to(dev)
+
+    def timed(plan, f, u):
         """K solves, CUDA events on the launching stream, no profiler."""
         helm.helm_set_stream(plan.handle, stream.cuda_stream)
         for _ in range(args.warmup):
@@ -295,7 +313,7 @@ def run_gb300(args):
         clocks = clk.stop()
         return max_over_ranks(e0.elapsed_time(e1)), clocks
 
-    def profiled(plan, u, path, sweeps):
+    def profiled(plan, f, u, path, sweeps):
         """Per-kernel device times from the library's event profiler (kernel by
         kernel), over PROFILE_SOLVES solves.  Refined paths run exactly the
         sweeps the timed solves took, so no skipped launch enters an average."""
@@ -311,20 +329,20 @@ def run_gb300(args):
             helm.helm_set_refinement(plan.handle, REFINE_TOL, 10)
         return prof
 
-    def sampled_error(u):
+    def sampled_error(wl, u):
         if args.shape:
             return None
         try:
             sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
             from make_golden import load
 
-            d, idx, vals = load(args.workload)
+            d, idx, vals = load("3d" if wl == "3d" else "2d_large")
             got = u.reshape(-1)[torch.from_numpy(idx).to(dev)].cpu().numpy()
             return float(np.linalg.norm(got - vals) / np.linalg.norm(vals))
         except FileNotFoundError:
             return None
 
-    def make_plan(path):
+    def make_plan(p, path):
         code, kind = PATHS[path]
         plan = helm.Plan(p.shape, p.h, p.omega, code)
         if kind is not None:
@@ -332,17 +350,42 @@ def run_gb300(args):
             helm.helm_set_refinement(plan.handle, REFINE_TOL, 10)
         return plan
 
+    def kernels_of(p, path, pr):
+        f64 = path == "c128"
+        return {k: roofline_entry(k, v[0], v[1], PROFILE_SOLVES, p.N, 16 if f64 else 8, p.shape[-1], peaks, fp64=f64,
+                                  accum=(k in ("dft_inv", "dft_z_inv") and not f64), tables=f64,
+                                  ff=(path == "c64_ff"))
+                for k, v in pr.items()}
+
+    def run_path(wl, p, f, path):
+        """Time one path on one workload; returns (summary, details)."""
+        plan = make_plan(p, path)
+        u = torch.empty_like(f)
+        ms, clocks = timed(plan, f, u)
+        info, _ = plan.info()
+        err = sampled_error(wl, u)
+        sweeps = int(info.iterations)
+        prof = profiled(plan, f, u, path, sweeps)
+        plan_s = info.plan_seconds
+        aux = {"rho": info.aux_rho, "q": info.aux_q, "trial_rel_residual": sig(info.aux_trial_residual)}
+        refine = None
+        if PATHS[path][1] is not None:
+            refine = {"sweeps": sweeps, "tol": REFINE_TOL, "converged": bool(info.converged),
+                      "history": [sig(float(x), 3) for x in info.residual[:sweeps + 1]]}
+            if err is not None and err > 1e-10:
+                raise RuntimeError(f"{wl} {path}: sampled error {err:.3e} above the 1e-10 bar")
+        return plan, u, {"ms": ms / args.steps, "clocks": clocks, "err": err, "prof": prof, "refine": refine,
+                         "plan_s": plan_s, "aux": aux, "device_bytes": int(info.device_bytes)}
+
+    peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
+    wl = args.workload
+    p, f_host, f = load_problem(wl)
+    N = p.N
+
     # --- the timed path (the headline) ---
-    plan = make_plan(args.path)
-    u = torch.empty_like(f)
-    ms, clocks = timed(plan, u)
-    info, _ = plan.info()
-    err_c128 = sampled_error(u)
-    prof = profiled(plan, u, args.path, int(info.iterations))
-    ms_step = ms / args.steps
+    plan, u, main = run_path(wl, p, f, args.path)
+    ms_step = main["ms"]
     value = world * N / (ms_step * 1e-3)
-    if args.path != "c128" and (err_c128 is not None and err_c128 > 1e-10):
-        raise RuntimeError(f"{args.path}: sampled error {err_c128:.3e} above the 1e-10 bar")
 
     # e2e through the host-buffer entry point (H2D of f, solve, D2H of u)
     e2e = None
@@ -359,85 +402,76 @@ def run_gb300(args):
                 raise RuntimeError(helm.lib.helm_status_string(st))
         t1 = time.perf_counter()
         dt = max_over_ranks((t1 - t0) / args.steps)
-        e2e = {"value": world * N / dt, "unit": UNIT, "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16,
-               "ms_per_step": dt * 1e3, "api": "helm_solve_host (pinned host buffers)"}
+        e2e = {"value": sig(world * N / dt), "unit": UNIT, "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16,
+               "ms_per_step": sig(dt * 1e3), "api": "helm_solve_host (pinned host buffers)"}
+        del fh, uh
     plan.close()
     del u
 
-    # --- the other paths ---
-    variants = {}
-    for vpath in ([] if args.no_variants else [q for q in PATHS if q != args.path]):
-        plan = make_plan(vpath)
-        u = torch.empty_like(f)
-        ms_r, _ = timed(plan, u)
-        info_r, st_r = plan.info()
-        err_r = sampled_error(u)
-        prof_r = profiled(plan, u, vpath, int(info_r.iterations))
-        variants[vpath] = {
-            "value": world * N / (ms_r / args.steps * 1e-3), "unit": UNIT, "ms_per_step": ms_r / args.steps,
-            "dtype": PATH_DTYPE[vpath], "rel_err_sampled": err_r,
-            "kernels_ms_per_step": {k: round(v[1] / PROFILE_SOLVES, 4) for k, v in prof_r.items()},
-            "_prof": prof_r,
-        }
-        if PATHS[vpath][1] is not None:
-            variants[vpath].update({
-                "refinement_sweeps": int(info_r.iterations), "tol": REFINE_TOL,
-                "final_rel_residual": float(info_r.residual[info_r.iterations]),
-                "converged": bool(info_r.converged)})
-        plan.close()
-        del u
+    # --- the other paths, and the 2D workload in plain complex128 ---
+    variants, details = {}, {}
+    todo = [] if args.no_variants else [(wl, q) for q in PATHS if q != args.path]
+    if not args.no_variants and not args.shape and wl == "3d":
+        todo.append(("2d_large", "c128"))
+    cur_wl, cur_p, cur_f = wl, p, f
+    for vwl, vpath in todo:
+        if vwl != cur_wl:
+            cur_f = f = None  # free the previous workload's load vector first
+            torch.cuda.empty_cache()
+            cur_p, _, cur_f = load_problem(vwl)
+            cur_wl = vwl
+        vp = cur_p
+        vplan, vu, r = run_path(vwl, vp, cur_f, vpath)
+        vplan.close()
+        del vu
+        key = vpath if vwl == wl else f"{workload_problem(vwl).name}/{vpath}"
+        variants[key] = {"value": sig(world * vp.N / (r["ms"] * 1e-3)), "ms": sig(r["ms"]),
+                         "err": sig(r["err"], 2), "dtype": PATH_DTYPE[vpath]}
+        if r["refine"]:
+            variants[key]["sweeps"] = r["refine"]["sweeps"]
+        variants[key]["kernels_ms"] = {k: sig(v[1] / PROFILE_SOLVES, 3) for k, v in r["prof"].items()}
+        details[key] = kernels_of(vp, vpath, r["prof"])
 
-    # --- roofline of the dominant kernel of the timed (c128) step ---
-    peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
-    n1 = p.shape[-1]
+    # --- roofline of the dominant kernel of the timed step ---
+    prof = main["prof"]
     name, (launches, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
-    def kernels_of(path, pr):
-        f64 = path == "c128"
-        return {k: roofline_entry(k, v[0], v[1], PROFILE_SOLVES, N, 16 if f64 else 8, n1, peaks, fp64=f64,
-                                  accum=(k == "dft_inv" and not f64), tables=f64, ff=(path == "c64_ff"))
-                for k, v in pr.items()}
-
-    kernels_main = kernels_of(args.path, prof)
+    kernels_main = kernels_of(p, args.path, prof)
     tkey = ("3d" if len(p.shape) == 3 else "2d", args.path, name)
     if tkey in NCU_TRAFFIC_PER_UNKNOWN and "achieved" in kernels_main[name]:
         per_u, src = NCU_TRAFFIC_PER_UNKNOWN[tkey]
         kernels_main[name]["traffic"] = per_u * N
         kernels_main[name]["traffic_source"] = src
-    roof = dict(kernels_main[name])
-    for vpath, v in variants.items():
-        v["kernels"] = kernels_of(vpath, v.pop("_prof"))
+    rk = kernels_main[name]
+    roof = {"kernel": name, "bound": rk.get("bound"), "achieved": sig(rk.get("achieved")), "peak": rk.get("peak"),
+            "unit": rk.get("unit"), "frac": sig(rk.get("frac"), 3), "traffic": sig(rk.get("traffic")),
+            "launches_per_step": rk.get("launches_per_step"), "ms_per_launch": sig(rk.get("ms_per_launch")),
+            "peak_source": "measured" if rk.get("bound") == "hbm" else "derived FP64 FMA peak"}
     # kernels of one solve (the profiled solves launch exactly the timed ones)
     gpu_launches = int(round(sum(v[0] for v in prof.values()) / PROFILE_SOLVES)) * args.steps
-    if info.iterations:
-        refine = {"refinement_sweeps": int(info.iterations), "tol": REFINE_TOL,
-                  "final_rel_residual": float(info.residual[info.iterations]), "converged": bool(info.converged),
-                  "residual_history": [float(x) for x in info.residual[:info.iterations + 1]]}
-    else:
-        refine = None
 
     # --- CPU oracle baseline (rank 0, N = 1 only) ---
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_run(p, 1)
+        cpu = cpu_baseline_run(wl, p, 1)
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": PATH_DTYPE[args.path],
-        "data": "synthetic (seeded complex Gaussian x Gaussian bump)",
-        "config": {"workload": p.name, "nodes": list(p.shape), "h": list(p.h), "omega": p.omega,
+        "metric": METRIC, "value": sig(value, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sig(ms_step, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": PATH_DTYPE[args.path], "data": "synthetic (seeded complex Gaussian"
+        + (" x Gaussian bump)" if p.rhs == "gaussian_bump" else ")"),
+        "config": {"workload": p.name, "nodes": list(p.shape), "omega": sig(p.omega, 8),
                    "precision": PATH_PRECISION[args.path], "rhs_per_step": 1,
-                   "l2": f"inputs larger than L2 (f and u are {N * 16 / 1e6:.0f} MB each)", "parallelism": f"replicas x{world}"},
-        "rel_err_sampled": err_c128, "refinement": refine,
-        "gpu_launches": gpu_launches,
-        "kernels_ms_per_step": {k: round(v[1] / PROFILE_SOLVES, 4) for k, v in prof.items()},
-        "kernels": kernels_main,
-        "roofline": roof, "clocks": clocks, "e2e": e2e, "variants": variants, "cpu_baseline": cpu,
-        "plan_seconds": info.plan_seconds,
-        "auxiliary": {"rho": info.aux_rho, "q": info.aux_q, "trial_rel_residual": info.aux_trial_residual},
-        "device_bytes": int(info.device_bytes),
+                   "l2": f"inputs larger than L2 ({N * 16 / 1e6:.0f} MB each)", "parallelism": f"replicas x{world}"},
+        "gpu_launches": gpu_launches, "rel_err_sampled": sig(main["err"], 3), "refinement": main["refine"],
+        "roofline": roof, "clocks": main["clocks"], "e2e": e2e, "cpu_baseline": cpu,
+        "kernels_ms_per_step": {k: sig(v[1] / PROFILE_SOLVES, 3) for k, v in prof.items()},
+        "variants": {k: {a: b for a, b in v.items() if a != "kernels_ms"} for k, v in variants.items()},
+        "plan_seconds": sig(main["plan_s"], 3),
     }
     if rank == 0:
+        full = {"kernels": kernels_main, "variants": variants, "variant_kernels": details, "auxiliary": main["aux"],
+                "device_bytes": main["device_bytes"]}
+        print(json.dumps(full), file=sys.stderr)
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
@@ -598,10 +632,10 @@ def run_serve(args, helm, torch, dev, world, rank, local):
         print(json.dumps(line))
 
 
-def cpu_baseline_run(p, steps):
+def cpu_baseline_run(wl, p, steps):
     from oracle import solvers
 
-    shape = sample_shape()
+    shape = sample_shape(wl)
     sp = workloads.scaled(p, shape)
     f = workloads.rhs(sp)
     t0 = time.perf_counter()
@@ -609,8 +643,8 @@ def cpu_baseline_run(p, steps):
         solvers.oracle_solve(f, sp.h, sp.omega, method="tensor", iters=2)
     dt = (time.perf_counter() - t0) / steps
     cores = len(os.sched_getaffinity(0))
-    return {"value": sp.N / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{shape[0]}x{shape[1]} nodes, same h and omega (O2 tensor eigen-solve + 2 double-double "
+    return {"value": sig(sp.N / dt), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{'x'.join(map(str, shape))} nodes, same h and omega (O2 tensor eigen-solve + 2 double-double "
                       f"refinement sweeps), {dt:.2f} s per solve; BLAS threads = host cores"}
 
 
@@ -618,10 +652,11 @@ def run_reference(args):
     world, rank, local = dist_setup()
     if rank != 0:
         return
-    p = workloads.config_2d_large()
+    wl = args.workload if args.workload in ("3d", "2d_large") else "3d"
+    p = workload_problem(wl)
     from oracle import solvers
 
-    shape = sample_shape()
+    shape = sample_shape(wl)
     sp = workloads.scaled(p, shape)
     f = workloads.rhs(sp)
     for _ in range(args.warmup):
@@ -635,11 +670,12 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded complex Gaussian x Gaussian bump)",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded complex Gaussian"
+        + (" x Gaussian bump)" if p.rhs == "gaussian_bump" else ")"),
         "config": {"workload": p.name, "nodes": list(p.shape), "h": list(p.h), "omega": p.omega,
-                   "sample": f"{shape[0]}x{shape[1]} nodes, same spacing and wave number"},
+                   "sample": f"{'x'.join(map(str, shape))} nodes, same spacing and wave number"},
         "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cores,
-                         "sample": f"{shape[0]}x{shape[1]} nodes per step, O2 + 2 dd refinement sweeps"},
+                         "sample": f"{'x'.join(map(str, shape))} nodes per step, O2 + 2 dd refinement sweeps"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -658,8 +694,9 @@ def main():
                     "(profiling cases; not a benchmark line)")
     ap.add_argument("--minimal", action="store_true", help="timed solves only (no e2e, variants, CPU baseline)")
     ap.add_argument("--batch-count", type=int, default=512, help="problems of --workload batch2d")
-    ap.add_argument("--workload", default="2d_large", choices=["2d_large", "3d", "batch2d", "serve3d"],
-                    help="2d_large: the benchmark workload; 3d: the 512^3 workload; batch2d: 512 independent 2D "
+    ap.add_argument("--workload", default="3d", choices=["2d_large", "3d", "batch2d", "serve3d"],
+                    help="3d: the 512^3 workload (the bench line); 2d_large: the 8192 x 4096 workload; "
+                    "batch2d: 512 independent 2D "
                     "problems in one graph launch; serve3d: a Poisson stream of 3D requests through "
                     "helm_server (measurements, not the bench line)")
     ap.add_argument("--serve-count", type=int, default=32, help="requests of --workload serve3d")
@@ -667,7 +704,7 @@ def main():
                     help="mean arrivals per second (serve3d); <= 0: all requests at once (capacity)")
     ap.add_argument("--serve-slots", type=int, default=4, help="server streams (serve3d)")
     ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="plan-cache device budget (serve3d)")
-    ap.add_argument("--path", default="c64_ff", choices=list(PATHS_NAMES),
+    ap.add_argument("--path", default="c64_refined", choices=list(PATHS_NAMES),
                     help="path timed as the main line (the others are reported as variants)")
     args = ap.parse_args()
     if args.minimal:

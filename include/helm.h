@@ -144,10 +144,11 @@ int helm_set_refinement(helm_plan_t p, double tol, int max_iter);
 
 /* Residual arithmetic of HELM_C64_REFINED (helm_residual; default
  * HELM_RESID_FP64).  Iterative refinement is not part of the paper's method;
- * this selects how its residual is formed.  HELM_RESID_FF allocates two more
- * float-float vectors (32 bytes per unknown) at its first solve.  Returns
- * HELM_EINVAL for another kind or a plan of another dtype.  Call between
- * solves. */
+ * this selects how its residual is formed.  Selecting HELM_RESID_FF allocates
+ * two more float-float vectors (32 bytes per unknown) here, once per plan
+ * (HELM_ENOMEM if they do not fit; the plan keeps its previous kind), so
+ * that no solve allocates.  Returns HELM_EINVAL for another kind or a plan of
+ * another dtype.  Call between solves. */
 int helm_set_residual(helm_plan_t p, int kind);
 
 /* HELM_C64_REFINED: launch the first solve and the refinement loop as one
@@ -162,19 +163,24 @@ int helm_set_graphs(helm_plan_t p, int enable);
 
 /* --- Solve (Sections 4.2 and 5.2: Steps 1-3) ------------------------------
  * f, u: DEVICE pointers to N = nx*ny(*nz) complex values in the layout above
- * (complex128 or complex64 per dtype).  f is read only, u is overwritten; f
- * and u must not overlap.  Asynchronous on the plan's stream: returns after
- * enqueueing.  Convergence of refinement is reported by helm_get_info. */
+ * (complex128 or complex64 per dtype).  f is read only, u is overwritten.
+ * The byte ranges [f, f + N*elem) and [u, u + N*elem) must be disjoint:
+ * any shared byte returns HELM_EINVAL before the device is touched.
+ * Asynchronous on the plan's stream: returns after enqueueing.  Allocates
+ * nothing (all scratch belongs to the plan).  Convergence of refinement is
+ * reported by helm_get_info. */
 int helm_solve(helm_plan_t p, const void* f, void* u);
 
 /* Same solve with HOST pointers: copies f to the device, solves, copies u
  * back and synchronises the stream before returning (for callers without
  * device buffers; the copies are part of the call).  Page-locked host memory
- * gives full copy bandwidth; pageable memory also works.  For
+ * gives full copy bandwidth; pageable memory also works.  Unlike helm_solve,
+ * the first call allocates two device staging vectors (N values each), kept
+ * by the plan until helm_destroy.  For
  * HELM_C64_REFINED with HELM_RESID_FF and both buffers page-locked and
  * mapped, no copies are made: the kernels that convert f to float-float and
  * u back read and write the host buffers directly (same results).  f and u
- * must not overlap (HELM_EINVAL). */
+ * must not share a byte (HELM_EINVAL). */
 int helm_solve_host(helm_plan_t p, const void* f_host, void* u_host);
 
 /* Step-by-step variant for verification: runs the same kernels as helm_solve
@@ -255,7 +261,8 @@ int helm_batch_destroy(helm_batch_t b);
  * scratch is one fixed 16 MiB array that the library reserves on every GPU
  * that loads it, held until the process exits.
  *   f, u: DEVICE pointers, complex128, [nx][ny] as for helm_solve; f read
- *         only, u overwritten, no overlap.
+ *         only, u overwritten; their byte ranges must be disjoint
+ *         (HELM_EINVAL otherwise).
  *   cuda_stream: stream the work is enqueued on (NULL = legacy default
  *         stream); asynchronous like helm_solve.
  * Limits: ny <= 1024, and about 47 bytes per unknown plus O(nx + ny) must

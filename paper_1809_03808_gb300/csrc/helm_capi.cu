@@ -3,6 +3,7 @@
 // mixed-precision refinement, host-buffer and step-by-step variants.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <complex>
 #include <cmath>
@@ -485,10 +486,9 @@ int run_refined(helm_plan* p, const void* f, void* u, void* dbg_fhat, void* dbg_
   init.max_iter = p->max_iter;
   HELM_CK(cudaMemcpyAsync(p->state, &init, sizeof(init), cudaMemcpyHostToDevice, p->stream));
   if (refine_ff(p)) {
-    if (!p->ffb) {
-      if ((rc = dev_alloc(p, (void**)&p->ffb, N * sizeof(float4))) ||
-          (rc = dev_alloc(p, (void**)&p->ufb, N * sizeof(float4))))
-        return rc;
+    if (!p->ffb) {  // allocated by helm_set_residual; the solve never allocates
+      p->err = "float-float vectors missing";
+      return HELM_EINVAL;
     }
     HELM_PK("split_ff", launch_split_ff((const double2*)f, p->ffb, p->rbuf, N, p->stream));
   }
@@ -578,6 +578,18 @@ int alloc_refine(helm_plan* p) {
       (rc = dev_alloc(p, (void**)&p->state, sizeof(RefineState))))
     return rc;
   return HELM_OK;
+}
+
+// Bytes of one f or u vector of plan p (complex64 for HELM_C64_RAW, else complex128).
+size_t plan_vec_bytes(const helm_plan* p) {
+  const int64_t N = p->n[0] * p->n[1] * p->n[2];
+  return (size_t)N * (p->dtype == HELM_C64_RAW ? sizeof(float2) : sizeof(double2));
+}
+
+// Do [a, a + bytes) and [b, b + bytes) share a byte?
+bool overlaps(const void* a, const void* b, size_t bytes) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + bytes && y < x + bytes;
 }
 
 void destroy_plan(helm_plan* p) {
@@ -1008,6 +1020,19 @@ int helm_set_refinement(helm_plan_t p, double tol, int max_iter) {
 
 int helm_set_residual(helm_plan_t p, int kind) {
   if (!p || p->dtype != HELM_C64_REFINED || (kind != HELM_RESID_FP64 && kind != HELM_RESID_FF)) return HELM_EINVAL;
+  if (kind == HELM_RESID_FF && !p->ffb) {
+    // the float-float f and u live as long as the plan: allocated here, never in a solve
+    const int64_t N = p->n[0] * p->n[1] * p->n[2];
+    int rc;
+    if ((rc = dev_alloc(p, (void**)&p->ffb, N * sizeof(float4))) ||
+        (rc = dev_alloc(p, (void**)&p->ufb, N * sizeof(float4)))) {
+      cudaFree(p->ffb);
+      p->ffb = nullptr;
+      p->ufb = nullptr;
+      p->bytes -= std::min(p->bytes, (size_t)N * sizeof(float4));
+      return rc;
+    }
+  }
   ++p->version;
   if (p->resid_kind != kind) drop_refine_graph(p);
   p->resid_kind = kind;
@@ -1021,12 +1046,12 @@ int helm_set_graphs(helm_plan_t p, int enable) {
 }
 
 int helm_solve(helm_plan_t p, const void* f, void* u) {
-  if (!p || !f || !u || f == u) return HELM_EINVAL;
+  if (!p || !f || !u || overlaps(f, u, plan_vec_bytes(p))) return HELM_EINVAL;
   return run_solve(p, f, u, nullptr, nullptr, nullptr);
 }
 
 int helm_solve_debug(helm_plan_t p, const void* f, void* u, void* fhat, void* v_b, void* w_b) {
-  if (!p || !f || !u || f == u) return HELM_EINVAL;
+  if (!p || !f || !u || overlaps(f, u, plan_vec_bytes(p))) return HELM_EINVAL;
   return run_solve(p, f, u, fhat, v_b, w_b);
 }
 
@@ -1046,7 +1071,7 @@ void* mapped_host(const void* h) {
 }  // namespace
 
 int helm_solve_host(helm_plan_t p, const void* f_host, void* u_host) {
-  if (!p || !f_host || !u_host) return HELM_EINVAL;
+  if (!p || !f_host || !u_host || overlaps(f_host, u_host, plan_vec_bytes(p))) return HELM_EINVAL;
   const int64_t N = p->n[0] * p->n[1] * p->n[2];
   const size_t eb = p->dtype == HELM_C64_RAW ? sizeof(float2) : sizeof(double2);
   int rc;
@@ -1057,9 +1082,6 @@ int helm_solve_host(helm_plan_t p, const void* f_host, void* u_host) {
     void* fd = mapped_host(f_host);
     void* ud = mapped_host(u_host);
     if (fd && ud) {
-      const char* f0 = static_cast<const char*>(f_host);
-      const char* u0 = static_cast<const char*>(u_host);
-      if (f0 < u0 + N * eb && u0 < f0 + N * eb) return HELM_EINVAL;
       if ((rc = run_solve(p, fd, ud, nullptr, nullptr, nullptr))) return rc;
       HELM_CK(cudaStreamSynchronize(p->stream));
       return HELM_OK;
@@ -1141,8 +1163,8 @@ int helm_batch_solve(helm_batch_t b, const void* const* f, void* const* u) {
   if (!b || !f || !u) return HELM_EINVAL;
   const size_t n = b->plans.size();
   for (size_t i = 0; i < n; ++i) {
-    if (!f[i] || !u[i] || f[i] == u[i]) return HELM_EINVAL;
     helm_plan* p = b->plans[i];
+    if (!f[i] || !u[i] || overlaps(f[i], u[i], plan_vec_bytes(p))) return HELM_EINVAL;
     if (p->prof.on) return HELM_EINVAL;  // event timing cannot live inside the graph
     if (p->dtype == HELM_C64_REFINED && refine_ff(p) && !p->ffb) return HELM_EINVAL;  // kind changed after create
   }
@@ -1234,7 +1256,7 @@ int helm_get_profile(helm_plan_t p, helm_profile_entry* out, int max_entries) {
 
 int helm_solve_2d_static(int64_t nx, int64_t ny, double hx, double hy, double omega, const void* f, void* u,
                          void* cuda_stream) {
-  if (!f || !u || f == u) return HELM_EINVAL;
+  if (!f || !u) return HELM_EINVAL;
   if (nx < 3 || ny < 3 || !(hx > 0) || !(hy > 0) || !std::isfinite(hx) || !std::isfinite(hy)) return HELM_EINVAL;
   if (validate_common(omega, HELM_C128)) return HELM_EINVAL;
   if (ny > kStaticMaxN1) return HELM_EUNSUPPORTED;
@@ -1277,6 +1299,7 @@ int helm_solve_2d_static(int64_t nx, int64_t ny, double hx, double hy, double om
     cur += sizes[i];
   }
   if (cur > kStaticScratchBytes) return HELM_EUNSUPPORTED;
+  if (overlaps(f, u, (size_t)N * sizeof(double2))) return HELM_EINVAL;
   // set-up once per device, with that device current: the device address of
   // the static array (the host-side symbol is not a device pointer)
   if (!g_static_addr[dev]) {

@@ -93,7 +93,7 @@ def test_solve_matches_oracle(env, name, dtype, aux):
     if dtype == "c64_raw":
         assert err < 5e-2
     else:
-        assert err <= TOL
+        assert err <= TOL and errmax <= TOL
         if dtype in ("c64_refined", "c64_ff"):
             assert st == helm.HELM_OK and info.converged == 1
 
@@ -184,6 +184,33 @@ def test_unsupported_and_invalid(env):
     x = torch.zeros(81, dtype=torch.complex128, device="cuda")
     with pytest.raises(helm.HelmError):
         helm.helm_solve(plan.handle, x, x)  # aliasing f and u is rejected
+    plan.close()
+
+
+def test_overlapping_buffers_rejected(env):
+    """f and u whose byte ranges share even one element are rejected with
+    HELM_EINVAL by every solve entry point, before any kernel runs."""
+    helm, torch = env
+    shape, h, omega = CASES["tiny_9x7"]
+    N = shape[0] * shape[1]
+    buf = torch.zeros(2 * N, dtype=torch.complex128, device="cuda")
+    f, u = buf.data_ptr(), buf.data_ptr() + (N - 1) * 16  # one shared element
+    for code in (helm.HELM_C128, helm.HELM_C64_REFINED):
+        plan = helm.Plan(shape, h, omega, code)
+        assert helm.lib.helm_solve(plan.handle, f, u) == helm.HELM_EINVAL
+        assert helm.lib.helm_solve(plan.handle, u, f) == helm.HELM_EINVAL
+        assert helm.lib.helm_solve_debug(plan.handle, f, u, None, None, None) == helm.HELM_EINVAL
+        # adjacent, disjoint ranges are fine
+        assert helm.lib.helm_solve(plan.handle, buf.data_ptr(), buf.data_ptr() + N * 16) == helm.HELM_OK
+        torch.cuda.synchronize()
+        plan.close()
+    plan = helm.Plan(shape, h, omega, helm.HELM_C64_RAW)
+    b32 = torch.zeros(2 * N, dtype=torch.complex64, device="cuda")
+    assert helm.lib.helm_solve(plan.handle, b32.data_ptr(), b32.data_ptr() + (N - 1) * 8) == helm.HELM_EINVAL
+    plan.close()
+    fh = np.zeros(2 * N, dtype=np.complex128)
+    plan = helm.Plan(shape, h, omega, helm.HELM_C128)
+    assert helm.lib.helm_solve_host(plan.handle, fh.ctypes.data, fh.ctypes.data + (N - 1) * 16) == helm.HELM_EINVAL
     plan.close()
 
 

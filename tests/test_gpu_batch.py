@@ -109,3 +109,59 @@ def test_batch_rejects_bad_arguments(env):
     assert helm.lib.helm_batch_destroy(h) == helm.HELM_OK
     assert helm.lib.helm_batch_destroy(None) == helm.HELM_OK
     plan.close()
+
+
+def _oracle_method(q):
+    return "banded" if q.N <= 40000 else "tensor"
+
+
+@pytest.mark.parametrize("residual", ["ff", "fp64"])
+def test_batch_workload_sample_matches_oracle(env, residual):
+    """A seeded sample of the 512-problem batch workload (mixed sizes up to
+    1004 x 1023, anisotropic spacings, 6-20 nodes per wavelength, three of
+    the near-resonant problems), solved as one batch with the benchmark's
+    settings (complex64 refined to ||r||/||f|| <= 2e-11) and checked problem
+    by problem against the CPU oracle (banded LU below 4e4 unknowns, the
+    tensor eigen-solve above) in the 2-norm and the max-norm."""
+    import numpy as np
+
+    import workloads
+    from oracle import solvers
+
+    helm, torch = env
+    probs = workloads.batch_2d(512)
+    resonant = sorted((i for i, q in enumerate(probs) if q.note), key=lambda i: probs[i].N)[:3]
+    rest = sorted((i for i, q in enumerate(probs) if not q.note), key=lambda i: probs[i].N)
+    rng = np.random.default_rng(7)
+    pick = resonant + [int(i) for i in rng.choice(rest[:256], 3, replace=False)] + [rest[-1]]
+    plans, fs, refs = [], [], []
+    for i in pick:
+        q = probs[i]
+        f = workloads.rhs(q)
+        u_ref, hist = solvers.oracle_solve(f, q.h, q.omega, method=_oracle_method(q))
+        assert hist[-1] < 1e-13
+        plan = helm.Plan(q.shape, q.h, q.omega, helm.HELM_C64_REFINED)
+        helm.helm_set_residual(plan.handle, helm.HELM_RESID_FF if residual == "ff" else helm.HELM_RESID_FP64)
+        helm.helm_set_refinement(plan.handle, 2e-11, 10)
+        plans.append(plan)
+        fs.append(torch.from_numpy(f).cuda())
+        refs.append(u_ref)
+    us = [torch.empty_like(f) for f in fs]
+    batch = helm.Batch(plans)
+    try:
+        batch.solve(fs, us)
+        torch.cuda.synchronize()
+        for i, plan, u, u_ref in zip(pick, plans, us, refs):
+            info, st = plan.info()
+            un = u.cpu().numpy()
+            err = np.linalg.norm(un - u_ref) / np.linalg.norm(u_ref)
+            errmax = np.abs(un - u_ref).max() / np.abs(u_ref).max()
+            res = float(info.residual[info.iterations])
+            print(f"BATCHSAMPLE {residual} #{i} {probs[i].shape} {probs[i].note or 'random'}: err={err:.3e} "
+                  f"max={errmax:.3e} sweeps={info.iterations} resid={res:.3e} err/resid={err / res:.2f}")
+            assert st == helm.HELM_OK and info.converged == 1
+            assert err <= 1e-10 and errmax <= 1e-10
+    finally:
+        batch.close()
+        for p in plans:
+            p.close()

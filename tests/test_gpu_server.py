@@ -177,3 +177,43 @@ def test_server_rejects_bad_requests(env):
     finally:
         srv.close()
     assert helm.lib.helm_server_destroy(None) == helm.HELM_OK
+
+
+def test_serving_workload_sample_matches_oracle(env):
+    """The three smallest operators of the 3D serving workload (0.6-0.8 M
+    unknowns, anisotropic, 8-12 nodes per wavelength), two right-hand sides
+    each, served with the benchmark's settings (complex64 refined on the
+    float-float residual to ||r||/||f|| <= 2e-11) through one server with two
+    streams, each result checked against the CPU oracle's tensor eigen-solve
+    in the 2-norm and the max-norm."""
+    import numpy as np
+
+    import workloads
+    from oracle import solvers
+
+    helm, torch = env
+    reqs = workloads.serve_3d(32)
+    ops = sorted({(q.shape, q.h, q.omega) for q, _, _ in reqs}, key=lambda o: int(np.prod(o[0])))[:3]
+    srv = helm.Server(nslots=2, device_budget_bytes=8 << 30)
+    try:
+        jobs = []
+        for k, (shape, h, omega) in enumerate(ops):
+            f = np.stack([workloads.random_rhs(shape, 900 + 10 * k + j) for j in range(2)])
+            fd = torch.from_numpy(f).cuda()
+            u = torch.empty_like(fd)
+            torch.cuda.synchronize()
+            t = srv.submit(shape, h, omega, fd, u, dtype=helm.HELM_C64_REFINED, residual=helm.HELM_RESID_FF,
+                           tol=2e-11, max_iter=10, nrhs=2)
+            jobs.append((t, shape, h, omega, f, fd, u))
+        for t, shape, h, omega, f, fd, u in jobs:
+            r = srv.wait(t, -1.0)
+            assert r.status == helm.HELM_OK and r.converged == 1
+            for j in range(2):
+                u_ref, hist = solvers.oracle_solve(f[j], h, omega, method="tensor")
+                un = u[j].cpu().numpy()
+                err = np.linalg.norm(un - u_ref) / np.linalg.norm(u_ref)
+                errmax = np.abs(un - u_ref).max() / np.abs(u_ref).max()
+                print(f"SERVESAMPLE {shape} rhs {j}: err={err:.3e} max={errmax:.3e} resid={r.residual:.3e}")
+                assert err <= 1e-10 and errmax <= 1e-10
+    finally:
+        srv.close()

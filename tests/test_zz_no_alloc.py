@@ -18,6 +18,7 @@ from workloads import ppw_omega, random_rhs
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-12  # same FP64 arithmetic on both paths; only rounding order may differ
+ORACLE_TOL = 1e-10  # against the CPU oracle, as every complex128 parity test
 
 
 @pytest.fixture(scope="module")
@@ -47,6 +48,9 @@ def test_static_solve_matches_plan_solve_twice(env, shape, lengths, ppw):
     f1 = torch.from_numpy(random_rhs(shape, 501)).cuda()
     f2 = torch.from_numpy(random_rhs(shape, 502)).cuda()
     plan = helm.Plan(shape, h, omega, helm.HELM_C128)
+    # the static entry point always uses the auxiliary (rho, q) = (1, 1); a
+    # plan picks its own by trial solves, so pin the plan to the same one
+    helm.helm_set_auxiliary(plan.handle, 1.0, 1)
     ref1 = plan.solve(f1)
     ref2 = plan.solve(f2)
     torch.cuda.synchronize()
@@ -71,3 +75,39 @@ def test_static_solve_rejects_oversize(env):
     st = helm.lib.helm_solve_2d_static(4096, 1024, 0.01, 0.01, 10.0, x.data_ptr(), y.data_ptr(), None)
     assert st == helm.HELM_EUNSUPPORTED
     assert helm.lib.helm_solve_2d_static(2, 5, 0.1, 0.1, 1.0, x.data_ptr(), y.data_ptr(), None) == helm.HELM_EINVAL
+
+
+@pytest.mark.parametrize("shape,lengths,ppw", [((129, 129), (1.0, 1.0), 10), ((200, 160), (1.3, 1.0), 8)])
+def test_static_solve_near_resonance_matches_oracle(env, shape, lengths, ppw):
+    """Near a closed-box resonance (w^2 at a sum of 1D Neumann eigenvalues,
+    the hardest case for the fixed auxiliary the static path keeps) the
+    static solve still meets the complex128 parity bound against the CPU
+    oracle, in the 2-norm and the max-norm."""
+    from oracle import fem, solvers
+
+    helm, torch = env
+    shape, h, omega0 = _problem(shape, lengths, ppw)
+    sums = (fem.eig_neumann(shape[0], h[0])[:, None] + fem.eig_neumann(shape[1], h[1])[None, :]).ravel()
+    omega = float(np.sqrt(sums[np.argmin(np.abs(sums - omega0 ** 2))]))
+    f = random_rhs(shape, 503)
+    u_ref, hist = solvers.oracle_solve(f, h, omega, method="banded")
+    fd = torch.from_numpy(f).cuda()
+    u = torch.empty_like(fd)
+    helm.helm_solve_2d_static(shape[0], shape[1], h[0], h[1], omega, fd, u,
+                              torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    un = u.cpu().numpy()
+    err = np.linalg.norm(un - u_ref) / np.linalg.norm(u_ref)
+    errmax = np.abs(un - u_ref).max() / np.abs(u_ref).max()
+    print(shape, "static near resonance: omega", omega, "err", err, "max", errmax)
+    assert err <= ORACLE_TOL and errmax <= ORACLE_TOL
+
+
+def test_static_solve_rejects_overlap(env):
+    """f and u sharing a single element are rejected before any device work."""
+    helm, torch = env
+    nx, ny = 9, 7
+    buf = torch.zeros(2 * nx * ny, dtype=torch.complex128, device="cuda")
+    p = buf.data_ptr()
+    st = helm.lib.helm_solve_2d_static(nx, ny, 0.1, 0.1, 5.0, p, p + (nx * ny - 1) * 16, None)
+    assert st == helm.HELM_EINVAL
