@@ -49,8 +49,11 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 FMA throughput: 2 DFMA per clock per SM (measured on this GB300 with an
 # FMA-chain probe: 1.197 TFLOP/s at 1.995 GHz over 152 SMs), at the 2.07 GHz
 # maximum clock.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-FP64_PEAK_NOTE = "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FMA rate measured by probe)"
+# The FP64 pipe issues 2 FP64 operations (add, multiply or fused
+# multiply-add, one element each) per clock per SM; ALU-bound kernels are
+# quoted in FP64 operations per second against that rate.
+FP64_PEAK_TFLOPS = 152 * 2 * 2.070e9 / 1e12  # T FP64-op/s
+FP64_PEAK_NOTE = "derived: 152 SMs x 2 FP64 ops/clk x 2.07 GHz (issue rate measured by an FMA-chain probe)"
 
 # Solve paths: (helm dtype, refinement residual kind or None).  dtype codes of
 # include/helm.h: HELM_C128 = 0, HELM_C64_REFINED = 1; residual kinds
@@ -152,7 +155,7 @@ class ClockSampler:
 # complex64 residual, the last transform writes (or updates) complex128 u.
 # Flops: real operations of the algorithm as written (complex multiply 6,
 # complex add 2, complex reciprocal 5 counting each division as 1).
-def kernel_model(name, e, n1, accum=False, first=True, tables=False, ff=False, per_solve=1.0):
+def kernel_model(name, e, n1, accum=False, first=True, tables=False, ff=False, per_solve=1.0, n1_dim=2):
     import math
 
     log2n = math.log2(n1)
@@ -176,6 +179,13 @@ def kernel_model(name, e, n1, accum=False, first=True, tables=False, ff=False, p
     # reads 1/den and writes d, the backward sweep reads both (4e), x3 steps,
     # plus f_hat read in inner Steps 1 and 3 (outer Steps 1, 3) and y3 written
     c128 = e == 16
+    # tiled inner sweeps (3D): the rhs read from f_hat in outer Steps 1, 3
+    # (inner Steps 1, 3), y3 written in inner Step 3; inner Step 2 and outer
+    # Step 2 generate their right-hand sides from face vectors (no bulk bytes)
+    if name.startswith("inner_o") and len(name) == 11:
+        o, i = int(name[7]), int(name[10])
+        byts = (e if (o != 2 and i != 2) else 0.0) + (e if i == 3 else 0.0)
+        return (byts, 80.0) if byts > 0 else None
     tab3 = {
         "dft_z_fwd": ((16 if c128 else 8) + e, 5.0 * log2n),
         "dft_y_fwd": (2 * e, 5.0 * log2n),
@@ -193,8 +203,9 @@ def kernel_model(name, e, n1, accum=False, first=True, tables=False, ff=False, p
         # refined paths: the first solve writes u (16 B), the sweeps update it (32 B)
         "dft_inv": (e + ((16.0 + (per_solve - 1.0) * 32.0) / per_solve if accum else 16 if e == 16 else 8),
                     5.0 * log2n),
-        # f, u complex128 in, r complex64 out; 9-point complex stencil
-        "residual_fp64": (40.0, 40.0),
+        # f, u complex128 in, r complex64 out; FP64 instructions per unknown of
+        # the monomial form (2D: 3 sums, 4 multiply-adds, ... = 14; 3D: 26)
+        "residual_fp64": (40.0, 14.0 if n1_dim == 2 else 26.0),
         # f, u float-float (16 B each) in, r complex64 out
         "residual_ff": (40.0, 40.0),
         "split_ff": (40.0, 4.0),  # f in, float-float f and its hi parts out
@@ -216,9 +227,10 @@ NCU_TRAFFIC_PER_UNKNOWN = {
 }
 
 
-def roofline_entry(name, launches, tot_ms, steps, N, e, n1, peaks, fp64, accum=False, tables=False, ff=False):
+def roofline_entry(name, launches, tot_ms, steps, N, e, n1, peaks, fp64, accum=False, tables=False, ff=False, dim=2):
     per_launch_ms = tot_ms / launches
-    model = kernel_model(name, e, n1, accum=accum, tables=tables, ff=ff, per_solve=max(1.0, launches / steps))
+    model = kernel_model(name, e, n1, accum=accum, tables=tables, ff=ff, per_solve=max(1.0, launches / steps),
+                         n1_dim=dim)
     out = {"kernel": name, "launches_per_step": launches / steps, "ms_per_launch": per_launch_ms}
     if model is None:
         return out
@@ -231,7 +243,7 @@ def roofline_entry(name, launches, tot_ms, steps, N, e, n1, peaks, fp64, accum=F
     # the binding resource: FP64 arithmetic for FP64 kernels unless the HBM
     # fraction is the larger one
     if (fp64 or name == "residual_fp64") and (hbm_frac is None or alu_frac >= hbm_frac):
-        out.update({"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+        out.update({"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "T FP64-op/s",
                     "frac": alu_frac, "peak_source": FP64_PEAK_NOTE,
                     "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": byts,
                     "hbm_GBps": gbs, "hbm_frac_of_measured": hbm_frac})
@@ -354,7 +366,7 @@ def run_gb300(args):
         f64 = path == "c128"
         return {k: roofline_entry(k, v[0], v[1], PROFILE_SOLVES, p.N, 16 if f64 else 8, p.shape[-1], peaks, fp64=f64,
                                   accum=(k in ("dft_inv", "dft_z_inv") and not f64), tables=f64,
-                                  ff=(path == "c64_ff"))
+                                  ff=(path == "c64_ff"), dim=len(p.shape))
                 for k, v in pr.items()}
 
     def run_path(wl, p, f, path):

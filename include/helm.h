@@ -68,6 +68,14 @@ enum helm_residual {
   HELM_RESID_FF = 1
 };
 
+/* Boundary condition on both faces of one axis (Section 2): the first-order
+ * absorbing condition du/dn - i w u = 0 (Gamma_A), or the natural condition
+ * du/dn = 0 (Gamma_N: the corner entries of eq. matrixK become 1). */
+enum helm_bc {
+  HELM_BC_ABC = 0,
+  HELM_BC_NEUMANN = 1
+};
+
 enum helm_status {
   HELM_OK = 0,
   HELM_EINVAL = -1,        /* bad argument (sizes, spacings, w, null pointer) */
@@ -98,6 +106,7 @@ typedef struct helm_info {
   double aux_rho;          /* ... and damping rho (see helm_set_auxiliary) */
   double aux_trial_residual; /* plan-time trial residual of the chosen auxiliary
                                 (-1 if set by helm_set_auxiliary) */
+  int32_t axis_bc[3];      /* helm_bc of each axis (HELM_BC_ABC beyond dim) */
 } helm_info;
 
 /* --- Plan (the paper's "Initialization", Section 6) -----------------------
@@ -116,6 +125,20 @@ int helm_plan_2d(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy,
                  double omega, int dtype);
 int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx,
                  double hy, double hz, double omega, int dtype);
+
+/* The same plans with a boundary condition per axis (Section 2's Gamma_A and
+ * Gamma_N; eq. matrixK with corners 1 - i w h or 1): axis_bc[k] is the
+ * helm_bc of both faces of axis k (2 entries in 2D, 3 in 3D; axis 0 = x).
+ * At least one axis must be absorbing (HELM_EINVAL otherwise): that keeps A
+ * non-singular for every w.  helm_plan_2d / helm_plan_3d are these with
+ * HELM_BC_ABC everywhere.  A Neumann periodic axis takes the closed-form
+ * cosine eigen-data in place of the absorbing pencil's, and C_bb's corner
+ * becomes 1/h - w^2 h/3; a Neumann x axis changes the end entries of the
+ * tridiagonal line matrices.  Everything else is unchanged. */
+int helm_plan_2d_bc(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy,
+                    double omega, int dtype, const int32_t* axis_bc);
+int helm_plan_3d_bc(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx,
+                    double hy, double hz, double omega, int dtype, const int32_t* axis_bc);
 
 /* Auxiliary problem B.  The paper makes x1 periodic (eqs. matrixKper,
  * matrixMper).  Here the wrap-around entries of those circulant matrices are
@@ -369,15 +392,40 @@ int helm_server_drain(helm_server_t s, double timeout_s);
 int helm_server_get_stats(helm_server_t s, helm_server_stats* st);
 int helm_server_destroy(helm_server_t s);
 
+/* --- Failure detection and allocation checks (for tests) -------------------
+ * The paper has no counterpart; these exist so that the library's failure
+ * paths can be exercised without faulting a GPU.
+ *
+ * helm_debug_fail_alloc: the k-th device allocation the library makes from
+ *   now on (k >= 1) fails as if the device were out of memory; k = 0
+ *   disarms.  Returns the number of failures injected so far in the process.
+ *   Plans report such a failure as HELM_ENOMEM (with *out = NULL and nothing
+ *   left allocated), except for optional memory (pivot tables, auxiliary
+ *   trial buffers, tiled-sweep buffers) whose absence the plan works around.
+ * helm_debug_live_allocations: number of the library's device allocations
+ *   alive now (plans, float-float vectors, staging buffers); *bytes (may be
+ *   NULL) receives their total size.
+ * helm_debug_wait_timeout: enqueues on the plan's stream one kernel whose
+ *   bounded mbarrier wait (the wait the bulk-copy kernels use) can never
+ *   complete, with a limit of `tries` polls (1 .. 2^22).  The wait gives up,
+ *   the kernel returns, and the plan's error word is set: helm_get_info then
+ *   returns HELM_ETIMEOUT, as it would for a real copy that never arrived.
+ *   The error word stays set for the life of the plan. */
+int helm_debug_fail_alloc(int k);
+int64_t helm_debug_live_allocations(size_t* bytes);
+int helm_debug_wait_timeout(helm_plan_t p, int64_t tries);
+
 /* --- Host-side plan helpers (no GPU needed) --------------------------------
  * Eigen-data of the 1D absorbing pencil K V = M V Lam (eq. EVP1a) with
  * V^T M V = I (eq. EVPcondA), K, M of eqs. matrixK / matrixM with n nodes,
- * spacing h and corner 1 - i w h.  Outputs, caller-owned host arrays:
+ * spacing h and corner 1 - i w h; w = 0 gives the Neumann pencil (corner 1,
+ * a Gamma_N axis), whose eigenpairs are the closed-form cosines.  Outputs,
+ * caller-owned host arrays:
  *   lam    : 2n doubles, eigenvalues (re, im) interleaved;
  *   sigma  : 2n doubles, V[1,l]^2 (re, im) for the same eigenvector;
  *   parity : n int8, +1 if V[n,l] = V[1,l], -1 if V[n,l] = -V[1,l].
  * Order of the eigenpairs is unspecified.  Returns HELM_EINVAL for n < 2,
- * h <= 0 or w <= 0, HELM_ENUMERIC if the eigenvalue iteration fails. */
+ * h <= 0 or w < 0, HELM_ENUMERIC if the eigenvalue iteration fails. */
 int helm_abc_eigen(int64_t n, double h, double omega, double* lam, double* sigma,
                    int8_t* parity);
 

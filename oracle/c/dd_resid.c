@@ -68,7 +68,8 @@ static inline cdd cdd_mul_cd(cdd a, double br, double bi) {
   return r;
 }
 
-/* 1D entries: X(i, i+d) for X = M (kind 0) or K (kind 1); K complex at ends. */
+/* 1D entries: X(i, i+d) for X = M (kind 0) or K (kind 1); K complex at
+ * absorbing ends (corner 1/h - i wc; wc = 0 for a Neumann axis). */
 static void entry(int64_t n, double h, double omega, int64_t i, int d, int kind, double* re, double* im) {
   int end = (i == 0 || i == n - 1);
   if (kind == 0) {
@@ -87,13 +88,14 @@ static void entry(int64_t n, double h, double omega, int64_t i, int d, int kind,
 
 /* Coefficient of neighbour offset d[] at index idx[]: sum over terms of
  * products of 1D entries, each product formed in complex double-double. */
-static cdd coefficient(int dim, const int64_t* n, const double* h, double omega, const int64_t* idx, const int* d) {
+static cdd coefficient(int dim, const int64_t* n, const double* h, double omega, const double* wc, const int64_t* idx,
+                       const int* d) {
   cdd total = {dd_d(0.0), dd_d(0.0)};
   for (int j = 0; j <= dim; ++j) {
     cdd prod = {dd_d(1.0), dd_d(0.0)};
     for (int k = 0; k < dim; ++k) {
       double er, ei;
-      entry(n[k], h[k], omega, idx[k], d[k], (k == j) ? 1 : 0, &er, &ei);
+      entry(n[k], h[k], wc[k], idx[k], d[k], (k == j) ? 1 : 0, &er, &ei);
       prod = cdd_mul_cd(prod, er, ei);
     }
     if (j == dim) {
@@ -107,8 +109,11 @@ static cdd coefficient(int dim, const int64_t* n, const double* h, double omega,
   return total;
 }
 
-void helm_oracle_dd_residual(int dim, const int64_t* n, const double* h, double omega, const double* f,
-                             const double* u, double* r) {
+/* r = f - A u in double-double.  wc[k]: the w of the absorbing corner of
+ * axis k (w itself on an absorbing axis, 0 on a Neumann axis, Section 2's
+ * Gamma_A / Gamma_N). */
+void helm_oracle_dd_residual_bc(int dim, const int64_t* n, const double* h, double omega, const double* wc,
+                                const double* f, const double* u, double* r) {
   int64_t N = 1;
   for (int k = 0; k < dim; ++k) N *= n[k];
   int64_t stride[3];
@@ -136,7 +141,7 @@ void helm_oracle_dd_residual(int dim, const int64_t* n, const double* h, double 
         off += d[k] * stride[k];
       }
       if (!ok) continue;
-      cdd co = coefficient(dim, n, h, omega, idx, d);
+      cdd co = coefficient(dim, n, h, omega, wc, idx, d);
       cdd term = cdd_mul_cd(co, u[2 * (g + off)], u[2 * (g + off) + 1]);
       acc.re = dd_add(acc.re, dd_neg(term.re));
       acc.im = dd_add(acc.im, dd_neg(term.im));
@@ -144,4 +149,11 @@ void helm_oracle_dd_residual(int dim, const int64_t* n, const double* h, double 
     r[2 * g] = acc.re.hi + acc.re.lo;
     r[2 * g + 1] = acc.im.hi + acc.im.lo;
   }
+}
+
+/* Absorbing conditions on every face. */
+void helm_oracle_dd_residual(int dim, const int64_t* n, const double* h, double omega, const double* f,
+                             const double* u, double* r) {
+  const double wc[3] = {omega, omega, omega};
+  helm_oracle_dd_residual_bc(dim, n, h, omega, wc, f, u, r);
 }

@@ -37,4 +37,8 @@ def lib():
         f.restype = None
         f.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
                       ctypes.c_void_p, ctypes.c_void_p]
+        g = _lib.helm_oracle_dd_residual_bc
+        g.restype = None
+        g.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     return _lib

@@ -234,12 +234,17 @@ def eig_dirichlet(n, h):
 # Separable operator application (for residuals), eqs. A2D / A3D
 # ---------------------------------------------------------------------------
 
-def _tri_coeffs(n, h, omega, kind):
+def _bc_tuple(bc, d):
+    return (bc,) * d if isinstance(bc, str) else tuple(bc)
+
+
+def _tri_coeffs(n, h, omega, kind, bc="abc"):
     """(sub, diag, super) coefficient vectors of a 1D matrix from eqs.
-    matrixK / matrixM; sub[j] multiplies x[j-1], super[j] multiplies x[j+1]."""
+    matrixK / matrixM; sub[j] multiplies x[j-1], super[j] multiplies x[j+1].
+    K's corners are 1/h - i w on an absorbing axis, 1/h on a Neumann one."""
     if kind == "K":
         diag = np.full(n, 2.0 / h, dtype=np.complex128)
-        diag[0] = diag[-1] = 1.0 / h - 1j * omega
+        diag[0] = diag[-1] = (1.0 / h - 1j * omega) if bc == "abc" else 1.0 / h
         off = -1.0 / h
     else:
         diag = np.full(n, 4.0 * h / 6.0, dtype=np.complex128)
@@ -258,10 +263,10 @@ def _bshape(n, axis, d):
     return s
 
 
-def apply_1d(u, axis, n, h, omega, kind):
+def apply_1d(u, axis, n, h, omega, kind, bc="abc"):
     """y = T u along `axis`, T the 1D matrix K or M, complex128."""
     d = u.ndim
-    sub, diag, sup = (c.reshape(_bshape(n, axis, d)) for c in _tri_coeffs(n, h, omega, kind))
+    sub, diag, sup = (c.reshape(_bshape(n, axis, d)) for c in _tri_coeffs(n, h, omega, kind, bc))
     y = diag * u
     lo = [slice(None)] * d
     hi = [slice(None)] * d
@@ -272,25 +277,27 @@ def apply_1d(u, axis, n, h, omega, kind):
     return y
 
 
-def apply_A(u, h, omega):
-    """A u for the Kronecker form of eqs. A2D / A3D, complex128."""
+def apply_A(u, h, omega, bc="abc"):
+    """A u for the Kronecker form of eqs. A2D / A3D, complex128 (bc: per
+    axis "abc" or "neumann", or one of them for every axis)."""
     shape = u.shape
     d = len(shape)
+    bc = _bc_tuple(bc, d)
     total = None
     for j in range(d + 1):
         t = u
         for k in range(d):
             kind = "K" if k == j else "M"
-            t = apply_1d(t, k, shape[k], h[k], omega, kind)
+            t = apply_1d(t, k, shape[k], h[k], omega, kind, bc[k])
         if j == d:
             t = -omega ** 2 * t
         total = t if total is None else total + t
     return total
 
 
-def _apply_1d_dd(x: ddm.CDD, axis, n, h, omega, kind):
+def _apply_1d_dd(x: ddm.CDD, axis, n, h, omega, kind, bc="abc"):
     d = x.re[0].ndim
-    sub, diag, sup = (c.reshape(_bshape(n, axis, d)) for c in _tri_coeffs(n, h, omega, kind))
+    sub, diag, sup = (c.reshape(_bshape(n, axis, d)) for c in _tri_coeffs(n, h, omega, kind, bc))
 
     def shift(a, direction):
         # direction +1: out[j] = a[j-1]; -1: out[j] = a[j+1]; zero fill
@@ -311,17 +318,18 @@ def _apply_1d_dd(x: ddm.CDD, axis, n, h, omega, kind):
     return y
 
 
-def residual_dd(f, u, h, omega):
+def residual_dd(f, u, h, omega, bc="abc"):
     """r = f - A u with A of eqs. A2D / A3D, every operation in double-double,
     rounded to complex128 at the end."""
     shape = u.shape
     d = len(shape)
+    bc = _bc_tuple(bc, d)
     U = ddm.CDD.from_complex(u)
     acc = ddm.CDD.from_complex(f)
     for j in range(d + 1):
         t = U
         for k in range(d):
-            t = _apply_1d_dd(t, k, shape[k], h[k], omega, "K" if k == j else "M")
+            t = _apply_1d_dd(t, k, shape[k], h[k], omega, "K" if k == j else "M", bc[k])
         if j == d:
             t = t.mul_c(-omega ** 2)
         acc = acc - t
@@ -364,7 +372,7 @@ def plane_wave_load(shape, h, omega, direction):
     return f, u_exact
 
 
-def residual_dd_c(f, u, h, omega):
+def residual_dd_c(f, u, h, omega, bc="abc"):
     """Same double-double residual as `residual_dd`, computed by the oracle's
     C helper (oracle/c/dd_resid.c) for large grids."""
     from . import cbuild
@@ -374,6 +382,11 @@ def residual_dd_c(f, u, h, omega):
     n = np.array(u.shape, dtype=np.int64)
     hh = np.array(h, dtype=np.float64)
     r = np.empty_like(u)
-    cbuild.lib().helm_oracle_dd_residual(u.ndim, n.ctypes.data, hh.ctypes.data, float(omega), f.ctypes.data,
-                                         u.ctypes.data, r.ctypes.data)
+    if isinstance(bc, str) and bc == "abc":
+        cbuild.lib().helm_oracle_dd_residual(u.ndim, n.ctypes.data, hh.ctypes.data, float(omega), f.ctypes.data,
+                                             u.ctypes.data, r.ctypes.data)
+        return r
+    wc = np.array([float(omega) if b == "abc" else 0.0 for b in _bc_tuple(bc, u.ndim)], dtype=np.float64)
+    cbuild.lib().helm_oracle_dd_residual_bc(u.ndim, n.ctypes.data, hh.ctypes.data, float(omega), wc.ctypes.data,
+                                            f.ctypes.data, u.ctypes.data, r.ctypes.data)
     return r

@@ -102,14 +102,15 @@ class TensorSolver:
     """O2: A^-1 = (V_a (x) ... (x) I) H^-1 (V_a^T (x) ... (x) I) with one axis
     (`tri_axis`) kept as tridiagonal blocks (eqs. A2Dinv, HA2D, A3Dinv, HA3D)."""
 
-    def __init__(self, shape, h, omega, tri_axis=None):
+    def __init__(self, shape, h, omega, tri_axis=None, bc="abc"):
         self.shape = tuple(shape)
         self.h = tuple(h)
         self.omega = float(omega)
         d = len(shape)
+        self.bc = fem._bc_tuple(bc, d)
         self.tri_axis = int(np.argmax(shape)) if tri_axis is None else tri_axis
         self.eig_axes = [j for j in range(d) if j != self.tri_axis]
-        self.eigs = {j: abc_pencil_eig(shape[j], h[j], omega) for j in self.eig_axes}
+        self.eigs = {j: abc_pencil_eig(shape[j], h[j], omega, self.bc[j]) for j in self.eig_axes}
 
     def _transform(self, x, transpose):
         for j in self.eig_axes:
@@ -135,7 +136,7 @@ class TensorSolver:
         lam_lines = np.moveaxis(lam, t, -1).reshape(-1)
         s = lam_lines - self.omega ** 2
         # line matrix: K_t + (lam - w^2) M_t   (eq. HA2D block)
-        subK, diagK, _ = fem._tri_coeffs(n, ht, self.omega, "K")
+        subK, diagK, _ = fem._tri_coeffs(n, ht, self.omega, "K", self.bc[t])
         subM, diagM, _ = fem._tri_coeffs(n, ht, self.omega, "M")
         diag = diagK[None, :] + s[:, None] * diagM[None, :]
         off = subK[1:][None, :] + s[:, None] * subM[1:][None, :]
@@ -145,38 +146,40 @@ class TensorSolver:
         return np.ascontiguousarray(self._transform(x, transpose=False))
 
 
-def refine(f, u, solve, h, omega, iters=2):
+def refine(f, u, solve, h, omega, iters=2, bc="abc"):
     """Iterative refinement u <- u + solve(f - A u) with the residual formed in
     double-double (fem.residual_dd).  Returns (u, [relative residuals])."""
     hist = []
     fn = np.linalg.norm(f)
     resid = fem.residual_dd_c if f.size > 4096 else fem.residual_dd
     for _ in range(iters):
-        r = resid(f, u, h, omega)
+        r = resid(f, u, h, omega, bc)
         hist.append(float(np.linalg.norm(r) / fn))
         u = u + solve(r)
-    r = resid(f, u, h, omega)
+    r = resid(f, u, h, omega, bc)
     hist.append(float(np.linalg.norm(r) / fn))
     return u, hist
 
 
-def oracle_solve(f, h, omega, method="auto", iters=2, tri_axis=None):
+def oracle_solve(f, h, omega, method="auto", iters=2, tri_axis=None, bc="abc"):
     """u = A^-1 f: O1 (banded LU) for small problems, O2 (tensor eigen-solve)
-    otherwise, followed by double-double iterative refinement."""
+    otherwise, followed by double-double iterative refinement.  bc: "abc"
+    (absorbing faces everywhere), or per axis "abc" / "neumann" (Section 2's
+    Gamma_A / Gamma_N: both faces of an axis of the same kind)."""
     f = np.asarray(f, dtype=np.complex128)
     if method == "auto":
         srt = sorted(f.shape)
         bw = int(np.prod(srt[:-1])) if f.ndim > 1 else 1
         method = "banded" if bw * f.size <= 3e8 else "tensor"
     if method == "banded":
-        solve = lambda r: solve_banded_lu(r, h, omega)
+        solve = lambda r: solve_banded_lu(r, h, omega, bc)
     elif method == "dense":
-        solve = lambda r: solve_dense(r, h, omega)
+        solve = lambda r: solve_dense(r, h, omega, bc)
     else:
-        ts = TensorSolver(f.shape, h, omega, tri_axis)
+        ts = TensorSolver(f.shape, h, omega, tri_axis, bc)
         solve = ts.solve
     u = solve(f)
-    u, hist = refine(f, u, solve, h, omega, iters=iters)
+    u, hist = refine(f, u, solve, h, omega, iters=iters, bc=bc)
     return u, hist
 
 

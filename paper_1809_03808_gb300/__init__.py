@@ -24,6 +24,7 @@ lib = ctypes.CDLL(_LIB_PATH)
 
 HELM_C128, HELM_C64_REFINED, HELM_C64_RAW = 0, 1, 2
 HELM_RESID_FP64, HELM_RESID_FF = 0, 1
+HELM_BC_ABC, HELM_BC_NEUMANN = 0, 1
 HELM_OK, HELM_EINVAL, HELM_ENOMEM, HELM_ECUDA, HELM_ENOTCONV, HELM_ETIMEOUT, HELM_EUNSUPPORTED, HELM_ENUMERIC = \
     0, -1, -2, -3, -4, -5, -6, -7
 
@@ -36,7 +37,8 @@ class helm_info(ctypes.Structure):
                 ("residual", ctypes.c_double * 16), ("plan_seconds", ctypes.c_double),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("n_dft_stages", ctypes.c_int32),
                 ("device_bytes", ctypes.c_size_t), ("residual_kind", ctypes.c_int32),
-                ("aux_q", ctypes.c_int32), ("aux_rho", ctypes.c_double), ("aux_trial_residual", ctypes.c_double)]
+                ("aux_q", ctypes.c_int32), ("aux_rho", ctypes.c_double), ("aux_trial_residual", ctypes.c_double),
+                ("axis_bc", ctypes.c_int32 * 3)]
 
 
 class helm_profile_entry(ctypes.Structure):
@@ -68,6 +70,9 @@ class helm_server_stats(ctypes.Structure):
 _SIGS = {
     "helm_plan_2d": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _dbl, _dbl, _dbl, _i32]),
     "helm_plan_3d": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _i64, _dbl, _dbl, _dbl, _dbl, _i32]),
+    "helm_plan_2d_bc": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _dbl, _dbl, _dbl, _i32, ctypes.POINTER(_i32)]),
+    "helm_plan_3d_bc": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _i64, _dbl, _dbl, _dbl, _dbl, _i32,
+                               ctypes.POINTER(_i32)]),
     "helm_set_stream": (_i32, [_vp, _vp]),
     "helm_set_refinement": (_i32, [_vp, _dbl, _i32]),
     "helm_set_auxiliary": (_i32, [_vp, _dbl, _i32]),
@@ -96,6 +101,9 @@ _SIGS = {
     "helm_server_drain": (_i32, [_vp, _dbl]),
     "helm_server_get_stats": (_i32, [_vp, ctypes.POINTER(helm_server_stats)]),
     "helm_server_destroy": (_i32, [_vp]),
+    "helm_debug_fail_alloc": (_i32, [_i32]),
+    "helm_debug_live_allocations": (_i64, [ctypes.POINTER(ctypes.c_size_t)]),
+    "helm_debug_wait_timeout": (_i32, [_vp, _i64]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -141,6 +149,22 @@ def helm_plan_3d(nx, ny, nz, hx, hy, hz, omega, dtype=HELM_C128):
     h = _vp()
     _check(lib.helm_plan_3d(ctypes.byref(h), int(nx), int(ny), int(nz), float(hx), float(hy), float(hz),
                             float(omega), int(dtype)), "helm_plan_3d")
+    return h
+
+
+def helm_plan_2d_bc(nx, ny, hx, hy, omega, dtype, axis_bc):
+    h = _vp()
+    bc = (_i32 * 2)(*[int(b) for b in axis_bc])
+    _check(lib.helm_plan_2d_bc(ctypes.byref(h), int(nx), int(ny), float(hx), float(hy), float(omega), int(dtype), bc),
+           "helm_plan_2d_bc")
+    return h
+
+
+def helm_plan_3d_bc(nx, ny, nz, hx, hy, hz, omega, dtype, axis_bc):
+    h = _vp()
+    bc = (_i32 * 3)(*[int(b) for b in axis_bc])
+    _check(lib.helm_plan_3d_bc(ctypes.byref(h), int(nx), int(ny), int(nz), float(hx), float(hy), float(hz),
+                               float(omega), int(dtype), bc), "helm_plan_3d_bc")
     return h
 
 
@@ -234,14 +258,20 @@ def helm_dft_factor(n):
 class Plan:
     """Owns one helm plan; solve(f, u) on torch CUDA tensors, current stream."""
 
-    def __init__(self, shape, h, omega, dtype=HELM_C128):
+    def __init__(self, shape, h, omega, dtype=HELM_C128, bc=None):
+        """bc: None (absorbing faces everywhere) or one HELM_BC_* (or "abc" /
+        "neumann") per axis."""
         shape = tuple(int(n) for n in shape)
         self.shape = shape
         self.dtype = dtype
+        if bc is not None:
+            bc = [HELM_BC_NEUMANN if b in ("neumann", HELM_BC_NEUMANN) else HELM_BC_ABC for b in bc]
         if len(shape) == 2:
-            self.handle = helm_plan_2d(shape[0], shape[1], h[0], h[1], omega, dtype)
+            self.handle = (helm_plan_2d(shape[0], shape[1], h[0], h[1], omega, dtype) if bc is None else
+                           helm_plan_2d_bc(shape[0], shape[1], h[0], h[1], omega, dtype, bc))
         elif len(shape) == 3:
-            self.handle = helm_plan_3d(shape[0], shape[1], shape[2], h[0], h[1], h[2], omega, dtype)
+            self.handle = (helm_plan_3d(shape[0], shape[1], shape[2], h[0], h[1], h[2], omega, dtype) if bc is None
+                           else helm_plan_3d_bc(shape[0], shape[1], shape[2], h[0], h[1], h[2], omega, dtype, bc))
         else:
             raise ValueError("shape must be 2D or 3D")
 

@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhelm.so")
 
 CUDA_SOURCES = ["helm_dft.cu", "helm_dft_pow2.cu", "helm_solve2d.cu", "helm_solve3d.cu", "helm_resid.cu", "helm_capi.cu"]
-CXX_SOURCES = ["helm_eigen.cpp", "helm_server.cpp"]
+CXX_SOURCES = ["helm_eigen.cpp", "helm_server.cpp", "helm_alloc.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

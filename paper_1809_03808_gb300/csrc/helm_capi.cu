@@ -19,6 +19,7 @@
 #include "helm_solve.h"
 #include "helm_prof.h"
 #include "helm_solve3d.h"
+#include "helm_async.cuh"
 
 using namespace helm;
 
@@ -27,6 +28,8 @@ struct helm_plan {
   int64_t n[3] = {1, 1, 1};
   double h[3] = {0, 0, 0};
   double omega = 0;
+  int32_t bc[3] = {HELM_BC_ABC, HELM_BC_ABC, HELM_BC_ABC};  // boundary kind of each axis (both faces)
+  double wc[3] = {0, 0, 0};  // w of each axis's absorbing ends: omega, or 0 on a Neumann axis
   int dtype = HELM_C128;
   int prec = kPrecF64;  // compute precision of the solves
   cudaStream_t stream = nullptr;
@@ -111,7 +114,7 @@ int cuda_fail(helm_plan* p, cudaError_t e, const char* what) {
 
 int dev_alloc(helm_plan* p, void** ptr, size_t bytes) {
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(ptr, bytes);
+  cudaError_t e = dmalloc((void**)ptr, bytes);
   if (e != cudaSuccess) {
     p->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
     *ptr = nullptr;
@@ -123,17 +126,17 @@ int dev_alloc(helm_plan* p, void** ptr, size_t bytes) {
 }
 
 void free_axis(AxisData& a) {
-  cudaFree(a.lamB);
-  cudaFree(a.invmu);
-  cudaFree(a.sc_in);
-  cudaFree(a.sc_out);
-  cudaFree(a.sc_in32);
-  cudaFree(a.sc_out32);
-  cudaFree(a.lamA);
-  cudaFree(a.sigA);
-  cudaFree(a.parA);
-  cudaFree(a.tw);
-  cudaFree(a.tw32);
+  dfree(a.lamB);
+  dfree(a.invmu);
+  dfree(a.sc_in);
+  dfree(a.sc_out);
+  dfree(a.sc_in32);
+  dfree(a.sc_out32);
+  dfree(a.lamA);
+  dfree(a.sigA);
+  dfree(a.parA);
+  dfree(a.tw);
+  dfree(a.tw32);
   a = AxisData{};
 }
 
@@ -209,10 +212,10 @@ int build_axis_aux(helm_plan* p, AxisData& a, double rho, int q) {
   a.ginv[0] = std::exp(-rho) * gr[a.q];
   a.ginv[1] = -std::exp(-rho) * gi[a.q];
   if (rho == 0.0 && a.q == 0) {
-    cudaFree(a.sc_in);
-    cudaFree(a.sc_out);
-    cudaFree(a.sc_in32);
-    cudaFree(a.sc_out32);
+    dfree(a.sc_in);
+    dfree(a.sc_out);
+    dfree(a.sc_in32);
+    dfree(a.sc_out32);
     a.sc_in = a.sc_out = nullptr;
     a.sc_in32 = a.sc_out32 = nullptr;
     return HELM_OK;
@@ -237,10 +240,12 @@ int build_axis_aux(helm_plan* p, AxisData& a, double rho, int q) {
 }
 
 // Eigen-data of one periodic axis (Section 3.2): absorbing-pencil eigen-data
-// (eqs. EVP1a, EVPcondA), DFT twiddles, and the auxiliary tables.
-int build_axis(helm_plan* p, AxisData& a, int64_t n, double h, double omega, double rho, int q) {
+// (eqs. EVP1a, EVPcondA; wc = 0: the Neumann pencil of a Gamma_N axis), DFT
+// twiddles, and the auxiliary tables.
+int build_axis(helm_plan* p, AxisData& a, int64_t n, double h, double wc, double rho, int q) {
   a.n = n;
   a.h = h;
+  a.wc = wc;
   dft_factor(n, &a.dft);
   std::vector<double> twre(n), twim(n);
   unit_roots(n, twre.data(), twim.data());
@@ -253,7 +258,7 @@ int build_axis(helm_plan* p, AxisData& a, int64_t n, double h, double omega, dou
     tw32[2 * l] = (float)twre[l];
     tw32[2 * l + 1] = (float)twim[l];
   }
-  int rc = abc_eigen(n, h, omega, lamA.data(), sigA.data(), par8.data());
+  int rc = abc_eigen(n, h, wc, lamA.data(), sigA.data(), par8.data());
   if (rc != HELM_OK) {
     p->err = "absorbing-pencil eigenvalue iteration failed";
     return rc;
@@ -279,6 +284,8 @@ Solve2DArgs args2d(const helm_plan* p) {
                 0, 0, {ax.eninv[0], ax.eninv[1]}};
   a.ch = p->prec == kPrecF64 ? kChunkF64 : kChunkF32;
   a.nchunks = (p->n[0] + a.ch - 1) / a.ch;
+  a.wx = p->wc[0];
+  a.wy = p->wc[1];
   return a;
 }
 
@@ -320,7 +327,7 @@ int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int 
   HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fv, nx, nparts, inv_n1, en_n1, skip, st));
   if (dbg_v) HELM_CK(cudaMemcpyAsync(dbg_v, fv, 2 * nx * cb, cudaMemcpyDeviceToDevice, st));
   // a3: Step 2
-  HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, nullptr, fc, nx, p->h[0], p->h[1], p->omega, p->omega * p->omega, ax.g,
+  HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, nullptr, fc, nx, p->h[0], p->h[1], p->wc[0], p->wc[1], p->omega * p->omega, ax.g,
                                         ax.ginv, skip, st));
   if (p->tabA && prec == kPrecF64)
     HELM_CK(launch_tri2d_tab(2, nullptr, fc, p->tabA, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr));
@@ -332,7 +339,7 @@ int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int 
   HELM_PK("reduce_faces", launch_reduce_faces(prec, p->partial, fw, nx, nparts, one, one, skip, st));
   if (dbg_w) HELM_CK(cudaMemcpyAsync(dbg_w, fw, 2 * nx * cb, cudaMemcpyDeviceToDevice, st));
   // a4: Step 3
-  HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, fw, fc, nx, p->h[0], p->h[1], p->omega, p->omega * p->omega, ax.g,
+  HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, fw, fc, nx, p->h[0], p->h[1], p->wc[0], p->wc[1], p->omega * p->omega, ax.g,
                                         ax.ginv, skip, st));
   if (p->tabB && prec == kPrecF64)
     HELM_CK(launch_tri2d_tab(3, p->fhat, fc, p->tabB, p->rec, p->dbuf, nullptr, a, skip, st, p->prof.on ? &p->prof : nullptr));
@@ -377,10 +384,10 @@ int refine_check(helm_plan* p, const void* f, const void* u, unsigned long long 
   const int* skip = &p->state->done;
   int64_t nblocks = 0;
   if (refine_ff(p))
-    HELM_PK("residual_ff", launch_residual_ff(p->dim, p->n, p->h, p->omega, p->ffb, p->ufb, p->rbuf, p->sums,
+    HELM_PK("residual_ff", launch_residual_ff(p->dim, p->n, p->h, p->omega, p->wc, p->ffb, p->ufb, p->rbuf, p->sums,
                                               &nblocks, skip, p->stream));
   else
-    HELM_PK("residual_fp64", launch_residual(p->dim, p->n, p->h, p->omega, (const double2*)f, (const double2*)u,
+    HELM_PK("residual_fp64", launch_residual(p->dim, p->n, p->h, p->omega, p->wc, (const double2*)f, (const double2*)u,
                                              p->rbuf, p->sums, &nblocks, skip, p->stream));
   HELM_PK("residual_finalize", launch_residual_finalize(p->sums, nblocks, p->state, cond, p->stream));
   return HELM_OK;
@@ -554,8 +561,8 @@ int alloc_buffers_2d(helm_plan* p) {
       HELM_CK(f64 ? launch_line_tables(p->tabB, a, 1, nullptr) : launch_line_tables32(p->tabB, a, 1, nullptr));
       HELM_CK(f64 ? launch_line_tables(p->tabA, a, 2, nullptr) : launch_line_tables32(p->tabA, a, 2, nullptr));
     } else {
-      cudaFree(p->tabB);
-      cudaFree(p->tabA);
+      dfree(p->tabB);
+      dfree(p->tabA);
       p->tabB = p->tabA = nullptr;
       p->err.clear();
     }
@@ -596,26 +603,26 @@ void destroy_plan(helm_plan* p) {
   if (!p) return;
   free_axis(p->axo);
   free_axis(p->axi);
-  cudaFree(p->fhat);
-  cudaFree(p->cbuf);
-  cudaFree(p->dbuf);
-  cudaFree(p->partial);
-  cudaFree(p->faces);
-  cudaFree(p->ustartB);
-  cudaFree(p->ustartA);
-  cudaFree(p->rec);
-  cudaFree(p->tabB);
-  cudaFree(p->tabA);
-  cudaFree(p->constB);
-  cudaFree(p->constA);
-  cudaFree(p->rbuf);
-  cudaFree(p->sums);
-  cudaFree(p->ffb);
-  cudaFree(p->ufb);
-  cudaFree(p->dev_err);
-  cudaFree(p->state);
-  cudaFree(p->host_f);
-  cudaFree(p->host_u);
+  dfree(p->fhat);
+  dfree(p->cbuf);
+  dfree(p->dbuf);
+  dfree(p->partial);
+  dfree(p->faces);
+  dfree(p->ustartB);
+  dfree(p->ustartA);
+  dfree(p->rec);
+  dfree(p->tabB);
+  dfree(p->tabA);
+  dfree(p->constB);
+  dfree(p->constA);
+  dfree(p->rbuf);
+  dfree(p->sums);
+  dfree(p->ffb);
+  dfree(p->ufb);
+  dfree(p->dev_err);
+  dfree(p->state);
+  dfree(p->host_f);
+  dfree(p->host_u);
   free_plan3d(p->p3);
   drop_refine_graph(p);
   for (int k = 0; k < 2; ++k)
@@ -742,23 +749,23 @@ int tune_auxiliary(helm_plan* p) {
   double* ts = p->sums;
   bool own_r = false;
   auto cleanup = [&]() {
-    cudaFree(tf);
-    cudaFree(tu);
+    dfree(tf);
+    dfree(tu);
     if (own_r) {
-      cudaFree(tr);
-      cudaFree(ts);
+      dfree(tr);
+      dfree(ts);
     }
     cudaGetLastError();
   };
   const int64_t nb_max = residual_blocks(p->dim, p->n);
-  if (cudaMalloc(&tf, N * sizeof(double2)) != cudaSuccess || cudaMalloc(&tu, N * sizeof(double2)) != cudaSuccess) {
+  if (dmalloc((void**)&tf, N * sizeof(double2)) != cudaSuccess || dmalloc((void**)&tu, N * sizeof(double2)) != cudaSuccess) {
     cleanup();
     return HELM_OK;  // no room for the trials: keep the default auxiliary
   }
   if (!tr) {
     own_r = true;
-    if (cudaMalloc(&tr, N * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc(&ts, nb_max * 2 * sizeof(double)) != cudaSuccess) {
+    if (dmalloc((void**)&tr, N * sizeof(float2)) != cudaSuccess ||
+        dmalloc((void**)&ts, nb_max * 2 * sizeof(double)) != cudaSuccess) {
       cleanup();
       return HELM_OK;
     }
@@ -775,12 +782,12 @@ int tune_auxiliary(helm_plan* p) {
     if ((rc = apply_aux(p, c.rho, c.q))) break;
     if ((rc = solve_core(p, tf, kInC128, tu, kOutC128, 0.0, nullptr, nullptr, nullptr, nullptr))) break;
     int64_t nb = 0;
-    cudaError_t e = launch_residual(p->dim, p->n, p->h, p->omega, tf, tu, tr, ts, &nb, nullptr, nullptr);
+    cudaError_t e = launch_residual(p->dim, p->n, p->h, p->omega, p->wc, tf, tu, tr, ts, &nb, nullptr, nullptr);
     if (e == cudaSuccess && p->dtype == HELM_C64_REFINED) {
       // refined plans: one correction sweep as well, so that the residual
       // measures the contraction of the sweeps, not only the first solve
       if ((rc = solve_core(p, tr, kInC64, tu, kOutAccumC128, 1.0, nullptr, nullptr, nullptr, nullptr))) break;
-      e = launch_residual(p->dim, p->n, p->h, p->omega, tf, tu, tr, ts, &nb, nullptr, nullptr);
+      e = launch_residual(p->dim, p->n, p->h, p->omega, p->wc, tf, tu, tr, ts, &nb, nullptr, nullptr);
     }
     if (e == cudaSuccess) e = cudaMemcpy(hs.data(), ts, nb * 2 * sizeof(double), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) {
@@ -893,15 +900,45 @@ int build_batch_graph(helm_batch* b, const void* const* f, void* const* u) {
   return HELM_OK;
 }
 
-}  // namespace
+// Failure-detection check: an mbarrier that expects 16 bytes of copies that
+// are never issued, waited on by the same bounded wait the bulk-copy kernels
+// use, with a short limit.  The wait gives up, sets the plan's error word and
+// the kernel returns; nothing is in flight.
+__global__ void k_debug_wait_timeout(int* err, uint32_t tries) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  mbar_arrive_expect_tx(&bar, 16);
+  mbar_wait_bounded(&bar, 0, err, tries);
+}
 
-extern "C" {
+// Boundary kinds per axis: each HELM_BC_ABC or HELM_BC_NEUMANN, at least one
+// absorbing axis (it keeps A non-singular for every real w).
+int validate_bc(int dim, const int32_t* bc) {
+  if (!bc) return HELM_OK;
+  int nabc = 0;
+  for (int k = 0; k < dim; ++k) {
+    if (bc[k] != HELM_BC_ABC && bc[k] != HELM_BC_NEUMANN) return HELM_EINVAL;
+    nabc += bc[k] == HELM_BC_ABC;
+  }
+  return nabc ? HELM_OK : HELM_EINVAL;
+}
 
-int helm_plan_2d(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy, double omega, int dtype) {
+void set_bc(helm_plan* p, const int32_t* bc) {
+  for (int k = 0; k < p->dim; ++k) {
+    p->bc[k] = bc ? bc[k] : HELM_BC_ABC;
+    p->wc[k] = p->bc[k] == HELM_BC_ABC ? p->omega : 0.0;
+  }
+}
+
+int plan_2d(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy, double omega, int dtype,
+            const int32_t* bc) {
   if (!out) return HELM_EINVAL;
   *out = nullptr;
   if (nx < 3 || ny < 3 || !(hx > 0) || !(hy > 0) || !std::isfinite(hx) || !std::isfinite(hy)) return HELM_EINVAL;
   if (int rc = validate_common(omega, dtype)) return rc;
+  if (int rc = validate_bc(2, bc)) return rc;
   auto t0 = std::chrono::steady_clock::now();
   helm_plan* p = new (std::nothrow) helm_plan();
   if (!p) return HELM_ENOMEM;
@@ -914,6 +951,7 @@ int helm_plan_2d(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy,
   p->omega = omega;
   p->dtype = dtype;
   p->prec = dtype == HELM_C128 ? kPrecF64 : kPrecF32;
+  set_bc(p, bc);
   DftPlan dp;
   dft_factor(ny, &dp);
   int dev = 0, smem = 0;
@@ -928,7 +966,7 @@ int helm_plan_2d(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy,
     delete p;
     return HELM_EUNSUPPORTED;
   }
-  int rc = build_axis(p, p->axo, ny, hy, omega, kDefaultAuxRho, kDefaultAuxQ);
+  int rc = build_axis(p, p->axo, ny, hy, p->wc[1], kDefaultAuxRho, kDefaultAuxQ);
   if (!rc) rc = alloc_buffers_2d(p);
   if (!rc) rc = alloc_refine(p);
   if (!rc) rc = tune_auxiliary(p);
@@ -941,14 +979,15 @@ int helm_plan_2d(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy,
   return HELM_OK;
 }
 
-int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx, double hy, double hz,
-                 double omega, int dtype) {
+int plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx, double hy, double hz, double omega,
+            int dtype, const int32_t* bc) {
   if (!out) return HELM_EINVAL;
   *out = nullptr;
   if (nx < 3 || ny < 3 || nz < 3 || !(hx > 0) || !(hy > 0) || !(hz > 0) || !std::isfinite(hx) ||
       !std::isfinite(hy) || !std::isfinite(hz))
     return HELM_EINVAL;
   if (int rc = validate_common(omega, dtype)) return rc;
+  if (int rc = validate_bc(3, bc)) return rc;
   auto t0 = std::chrono::steady_clock::now();
   helm_plan* p = new (std::nothrow) helm_plan();
   if (!p) return HELM_ENOMEM;
@@ -962,6 +1001,7 @@ int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx
   p->omega = omega;
   p->dtype = dtype;
   p->prec = dtype == HELM_C128 ? kPrecF64 : kPrecF32;
+  set_bc(p, bc);
   int smem = 0, dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -975,14 +1015,14 @@ int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx
     delete p;
     return HELM_EUNSUPPORTED;
   }
-  int rc = build_axis(p, p->axo, ny, hy, omega, kDefaultAuxRho, kDefaultAuxQ3D);
-  if (!rc) rc = build_axis(p, p->axi, nz, hz, omega, kDefaultAuxRho, kDefaultAuxQ3D);
+  int rc = build_axis(p, p->axo, ny, hy, p->wc[1], kDefaultAuxRho, kDefaultAuxQ3D);
+  if (!rc) rc = build_axis(p, p->axi, nz, hz, p->wc[2], kDefaultAuxRho, kDefaultAuxQ3D);
   if (!rc) {
     DftPlan a = p->axo.dft, b = p->axi.dft;
     if (!dft_supported(a, cbytes(p->prec), smem) || !dft_supported(b, cbytes(p->prec), smem)) rc = HELM_EUNSUPPORTED;
   }
   if (!rc) {
-    cudaError_t ce = plan3d_init(p->p3, p->prec, p->n, p->h, omega, p->axo, p->axi, &p->bytes);
+    cudaError_t ce = plan3d_init(p->p3, p->prec, p->n, p->h, omega, p->wc, p->axo, p->axi, &p->bytes);
     if (ce == cudaErrorMemoryAllocation) rc = HELM_ENOMEM;
     else if (ce != cudaSuccess) rc = cuda_fail(p, ce, "plan3d_init");
   }
@@ -995,6 +1035,38 @@ int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx
   p->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *out = p;
   return HELM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int helm_debug_wait_timeout(helm_plan_t p, int64_t tries) {
+  if (!p || tries < 1 || tries > (int64_t)kMbarWaitLimit) return HELM_EINVAL;
+  k_debug_wait_timeout<<<1, 32, 0, p->stream>>>(p->dev_err, (uint32_t)tries);
+  HELM_CK(cudaGetLastError());
+  return HELM_OK;
+}
+
+int helm_plan_2d(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy, double omega, int dtype) {
+  return plan_2d(out, nx, ny, hx, hy, omega, dtype, nullptr);
+}
+
+int helm_plan_2d_bc(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy, double omega, int dtype,
+                    const int32_t* axis_bc) {
+  if (!axis_bc) return HELM_EINVAL;
+  return plan_2d(out, nx, ny, hx, hy, omega, dtype, axis_bc);
+}
+
+int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx, double hy, double hz,
+                 double omega, int dtype) {
+  return plan_3d(out, nx, ny, nz, hx, hy, hz, omega, dtype, nullptr);
+}
+
+int helm_plan_3d_bc(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx, double hy, double hz,
+                    double omega, int dtype, const int32_t* axis_bc) {
+  if (!axis_bc) return HELM_EINVAL;
+  return plan_3d(out, nx, ny, nz, hx, hy, hz, omega, dtype, axis_bc);
 }
 
 int helm_set_auxiliary(helm_plan_t p, double rho, int phase_quarters) {
@@ -1026,7 +1098,7 @@ int helm_set_residual(helm_plan_t p, int kind) {
     int rc;
     if ((rc = dev_alloc(p, (void**)&p->ffb, N * sizeof(float4))) ||
         (rc = dev_alloc(p, (void**)&p->ufb, N * sizeof(float4)))) {
-      cudaFree(p->ffb);
+      dfree(p->ffb);
       p->ffb = nullptr;
       p->ufb = nullptr;
       p->bytes -= std::min(p->bytes, (size_t)N * sizeof(float4));
@@ -1119,6 +1191,7 @@ int helm_get_info(helm_plan_t p, helm_info* info) {
   info->aux_q = p->axo.q;
   info->aux_rho = p->axo.rho;
   info->aux_trial_residual = p->aux_trial_resid;
+  for (int k = 0; k < 3; ++k) info->axis_bc[k] = k < p->dim ? p->bc[k] : HELM_BC_ABC;
   int derr = 0;
   if (p->dev_err) HELM_CK(cudaMemcpy(&derr, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (derr) {
@@ -1269,12 +1342,14 @@ int helm_solve_2d_static(int64_t nx, int64_t ny, double hx, double hy, double om
   sp.h[0] = hx;
   sp.h[1] = hy;
   sp.omega = omega;
+  sp.wc[0] = sp.wc[1] = omega;
   sp.dtype = HELM_C128;
   sp.prec = kPrecF64;
   sp.stream = st;
   AxisData& ax = sp.axo;
   ax.n = ny;
   ax.h = hy;
+  ax.wc = omega;
   dft_factor(ny, &ax.dft);
   int dev = 0, smem = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices ||

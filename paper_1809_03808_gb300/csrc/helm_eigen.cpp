@@ -162,7 +162,7 @@ int solve_class(const std::vector<double>& lk, const std::vector<double>& wk, do
 }  // namespace
 
 int abc_eigen(int64_t n, double h, double omega, double* lam, double* sigma, int8_t* parity) {
-  if (n < 2 || !(h > 0) || !(omega > 0) || !std::isfinite(h) || !std::isfinite(omega))
+  if (n < 2 || !(h > 0) || !(omega >= 0) || !std::isfinite(h) || !std::isfinite(omega))
     return HELM_EINVAL;
   const double pi = 3.14159265358979323846;
   std::vector<double> lamN(n), w(n);
@@ -174,6 +174,19 @@ int abc_eigen(int64_t n, double h, double omega, double* lam, double* sigma, int
     double mu = h * (2.0 + c) / 3.0;
     w[k] = 2.0 / (mu * (double)(n - 1));
     if (k == 0 || k == n - 1) w[k] *= 0.5;
+  }
+  if (omega == 0.0) {
+    // w = 0: the Neumann pencil itself (corner k11 = 1 of eq. matrixK, a
+    // Gamma_N axis); its eigenvectors are the cosines, V[1,k]^2 = w_k and
+    // V[n,k] = (-1)^k V[1,k]
+    for (int64_t k = 0; k < n; ++k) {
+      lam[2 * k] = lamN[k];
+      lam[2 * k + 1] = 0.0;
+      sigma[2 * k] = w[k];
+      sigma[2 * k + 1] = 0.0;
+      parity[k] = (k & 1) ? -1 : 1;
+    }
+    return HELM_OK;
   }
   int64_t pos = 0;
   for (int cls = 0; cls < 2; ++cls) {

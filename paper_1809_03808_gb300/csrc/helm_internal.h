@@ -4,11 +4,18 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda_runtime.h>
+
 #include "helm.h"
 
 namespace helm {
 
 constexpr int kMaxStages = 24;
+
+// Counted device allocations of plan memory (helm_alloc.cpp): the library
+// allocates and frees device memory only through these.
+cudaError_t dmalloc(void** ptr, size_t bytes);
+void dfree(void* ptr);
 
 // Mixed-radix factorisation of a DFT length: 8, 4, 2 first, then odd primes.
 struct DftPlan {
@@ -43,6 +50,7 @@ void unit_roots(int64_t n, double* re, double* im);
 struct AxisData {
   int64_t n = 0;
   double h = 0;
+  double wc = 0;   // w of this axis's absorbing end rows (0: Neumann axis, Gamma_N)
   double rho = 0;  // damping of the auxiliary (0: periodic)
   int q = 0;       // phase of the auxiliary in quarter turns
   // device arrays (double)

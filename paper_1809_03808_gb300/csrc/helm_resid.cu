@@ -6,6 +6,7 @@
 // (1D matrices of eqs. matrixK / matrixM).  Interior points use precomputed
 // real coefficients; points on a face use the complex corner entries.
 #include <algorithm>
+#include <complex>
 
 #include "helm_kernels.cuh"
 #include "helm_solve.h"
@@ -14,32 +15,10 @@ namespace helm {
 
 namespace {
 
-struct Axis1D {
-  int64_t n;
-  double h;
-};
-
-// 1D entries M(i, i+d) and K(i, i+d) (K complex at the absorbing corners).
-__device__ __forceinline__ void entries(const Axis1D& ax, int64_t i, int d, double omega, double& m,
-                                        double& kre, double& kim) {
-  const bool end = (i == 0 || i == ax.n - 1);
-  if (d == 0) {
-    m = (end ? 2.0 : 4.0) * ax.h / 6.0;
-    kre = (end ? 1.0 : 2.0) / ax.h;
-    kim = end ? -omega : 0.0;
-  } else {
-    m = ax.h / 6.0;
-    kre = -1.0 / ax.h;
-    kim = 0.0;
-  }
-}
-
-struct ResidArgs {
-  Axis1D ax[3];
-  int dim;
-  double omega;
-  double cin[27];  // interior coefficients, index (d0+1)*9 + (d1+1)*3 + (d2+1) (3D) or (d0+1)*3+(d1+1)
-};
+// Tile shapes of the float-float residuals: 2D rows per thread; 3D z, y
+// tile and x planes per CTA.
+constexpr int RX2 = 16;
+constexpr int TZ3 = 32, TY3 = 8, RX3 = 32;
 
 // Float-float copies of the coefficients (each value as hi + lo floats).
 struct FF2 {
@@ -62,347 +41,261 @@ struct ResidFFArgs {
   FF2 per[3][3][9][2];
 };
 
-__global__ void __launch_bounds__(256) k_residual(ResidArgs a, const double2* __restrict__ f,
-                                                  const double2* __restrict__ u, float2* __restrict__ r,
-                                                  double* __restrict__ sums, int64_t N,
-                                                  const int* __restrict__ skip) {
-  if (skip && *skip) return;
-  __shared__ double sr[8], sf[8];
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double r2 = 0.0, f2 = 0.0;
-  if (gid < N) {
-    int64_t idx[3] = {0, 0, 0};
-    int64_t rem = gid;
-    for (int k = a.dim - 1; k >= 0; --k) {
-      idx[k] = rem % a.ax[k].n;
-      rem /= a.ax[k].n;
-    }
-    int64_t stride[3];
-    stride[a.dim - 1] = 1;
-    for (int k = a.dim - 2; k >= 0; --k) stride[k] = stride[k + 1] * a.ax[k + 1].n;
-    bool interior = true;
-    for (int k = 0; k < a.dim; ++k) interior = interior && idx[k] > 0 && idx[k] < a.ax[k].n - 1;
-    double ar = 0.0, ai = 0.0;
-    if (a.dim == 2) {
-      for (int d0 = -1; d0 <= 1; ++d0) {
-        const int64_t i0 = idx[0] + d0;
-        if (i0 < 0 || i0 >= a.ax[0].n) continue;
-        for (int d1 = -1; d1 <= 1; ++d1) {
-          const int64_t i1 = idx[1] + d1;
-          if (i1 < 0 || i1 >= a.ax[1].n) continue;
-          const double2 v = u[i0 * stride[0] + i1];
-          double cre, cim;
-          if (interior) {
-            cre = a.cin[(d0 + 1) * 3 + (d1 + 1)];
-            cim = 0.0;
-          } else {
-            double m0, k0r, k0i, m1, k1r, k1i;
-            entries(a.ax[0], idx[0], d0, a.omega, m0, k0r, k0i);
-            entries(a.ax[1], idx[1], d1, a.omega, m1, k1r, k1i);
-            cre = k0r * m1 + m0 * k1r - a.omega * a.omega * m0 * m1;
-            cim = k0i * m1 + m0 * k1i;
-          }
-          ar += cre * v.x - cim * v.y;
-          ai += cre * v.y + cim * v.x;
-        }
-      }
-    } else {
-      for (int d0 = -1; d0 <= 1; ++d0) {
-        const int64_t i0 = idx[0] + d0;
-        if (i0 < 0 || i0 >= a.ax[0].n) continue;
-        for (int d1 = -1; d1 <= 1; ++d1) {
-          const int64_t i1 = idx[1] + d1;
-          if (i1 < 0 || i1 >= a.ax[1].n) continue;
-          for (int d2 = -1; d2 <= 1; ++d2) {
-            const int64_t i2 = idx[2] + d2;
-            if (i2 < 0 || i2 >= a.ax[2].n) continue;
-            const double2 v = u[i0 * stride[0] + i1 * stride[1] + i2];
-            double cre, cim;
-            if (interior) {
-              cre = a.cin[(d0 + 1) * 9 + (d1 + 1) * 3 + (d2 + 1)];
-              cim = 0.0;
-            } else {
-              double m0, k0r, k0i, m1, k1r, k1i, m2, k2r, k2i;
-              entries(a.ax[0], idx[0], d0, a.omega, m0, k0r, k0i);
-              entries(a.ax[1], idx[1], d1, a.omega, m1, k1r, k1i);
-              entries(a.ax[2], idx[2], d2, a.omega, m2, k2r, k2i);
-              cre = k0r * m1 * m2 + m0 * k1r * m2 + m0 * m1 * k2r - a.omega * a.omega * m0 * m1 * m2;
-              cim = k0i * m1 * m2 + m0 * k1i * m2 + m0 * m1 * k2i;
-            }
-            ar += cre * v.x - cim * v.y;
-            ai += cre * v.y + cim * v.x;
-          }
-        }
-      }
-    }
-    const double2 fv = f[gid];
-    const double rr = fv.x - ar, ri = fv.y - ai;
-    r[gid] = make_float2((float)rr, (float)ri);
-    r2 = rr * rr + ri * ri;
-    f2 = fv.x * fv.x + fv.y * fv.y;
-  }
-  // block reduction (deterministic)
-  for (int off = 16; off > 0; off >>= 1) {
-    r2 += __shfl_down_sync(0xffffffffu, r2, off);
-    f2 += __shfl_down_sync(0xffffffffu, f2, off);
-  }
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    sr[w] = r2;
-    sf[w] = f2;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a2 = 0, b2 = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-      a2 += sr[i];
-      b2 += sf[i];
-    }
-    sums[2 * blockIdx.x] = a2;
-    sums[2 * blockIdx.x + 1] = b2;
-  }
+// ---------------------------------------------------------------------------
+// FP64 residual with the fewest FP64 instructions.  On this GPU an FP64
+// instruction costs the SM about as much issue time as 64 FP32 ones, so the
+// stencil is rearranged to minimise them; everything else (staging, norms,
+// conversions) runs on the FP32 and integer pipes.
+//
+// Per axis k the 1D matrices of eqs. matrixK / matrixM are
+//   M_k = m0 I + m1 S_k,  K_k = k0 I + k1 S_k,
+// with S_k the sum of the two neighbours along axis k (one at an end node),
+// m1 = h/6, k1 = -1/h, and m0 = 4h/6, k0 = 2/h inside, m0 = 2h/6,
+// k0 = 1/h - i w at the absorbing ends.  So the operator of eq. A3D is
+//   A u = sum_{a,b,c in {0,1}} C_abc Sx^a Sy^b Sz^c u,
+//   C_abc = Kx_a My_b Mz_c + Mx_a Ky_b Mz_c + Mx_a My_b Kz_c - w^2 Mx_a My_b Mz_c,
+// where X_0 / X_1 are the I / S coefficients of X; C_abc depends on whether
+// the node is an end node of each axis (real inside, complex on a face).  The
+// S_x part (a = 1) uses only the off-diagonal entries, so it does not depend
+// on the x class.  With the plane monomials P_bc = Sy^b Sz^c u of each
+// x-plane,
+//   Q(x) = sum_bc C_0bc P_bc(x),  R(x) = sum_bc C_1bc P_bc(x),
+//   r(x) = f(x) - Q(x) - R(x-1) - R(x+1).
+// Per real component inside: 3 neighbour sums, 4 + 4 multiply-adds (Q from
+// f), 2 subtractions: 13 FP64 instructions (26 per complex unknown; 2D: 7).
+// ---------------------------------------------------------------------------
+
+// x rounded to the nearest float (ties to even) on the integer pipe; values
+// outside the normal float range take the plain conversion.
+__device__ __forceinline__ float round_d2f(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e - 896 <= 0 || e - 896 >= 254) return (float)x;
+  const uint32_t sgn = (uint32_t)(b >> 32) & 0x80000000u;
+  const uint64_t m = b & 0xfffffffffffffull;
+  const uint32_t top = (uint32_t)(m >> 29), rem = (uint32_t)(m & 0x1fffffffull);
+  const bool up = rem > 0x10000000u || (rem == 0x10000000u && (top & 1u));
+  return __uint_as_float((sgn | ((uint32_t)(e - 896) << 23) | top) + (up ? 1u : 0u));
 }
 
-// 2D residual, one thread per y column segment of RX rows: rolling
-// registers over x (rows x-1, x, x+1 of the three y neighbours), interior
-// points with the nine precomputed real coefficients.
-constexpr int RX2 = 16;
-
-__global__ void __launch_bounds__(256) k_residual2d(ResidArgs a, const double2* __restrict__ f,
-                                                    const double2* __restrict__ u, float2* __restrict__ r,
-                                                    double* __restrict__ sums, const int* __restrict__ skip) {
-  if (skip && *skip) return;
-  __shared__ double sr[8], sf[8];
-  const int64_t nx = a.ax[0].n, ny = a.ax[1].n;
-  const int64_t iy = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t x0 = (int64_t)blockIdx.y * RX2;
-  // |r|^2 and |f|^2 only decide convergence: per-thread sums in FP32 (from the
-  // rounded values), FP64 across threads and blocks
-  float r2f = 0.f, f2f = 0.f;
-  double r2 = 0.0, f2 = 0.0;
-  if (iy < ny) {
-    const bool ym = iy > 0, yp = iy < ny - 1;
-    auto ld = [&](int64_t ix, int64_t jy) -> double2 {
-      return (ix >= 0 && ix < nx) ? __ldg(&u[ix * ny + jy]) : make_double2(0.0, 0.0);
-    };
-    double2 w[3][3];  // [dx+1][dy+1]
-    for (int d = 0; d < 2; ++d) {
-      const int64_t ix = x0 - 1 + d;
-      w[d][0] = ym ? ld(ix, iy - 1) : make_double2(0, 0);
-      w[d][1] = ld(ix, iy);
-      w[d][2] = yp ? ld(ix, iy + 1) : make_double2(0, 0);
-    }
-    const int64_t x1 = min(x0 + RX2, nx);
-    for (int64_t ix = x0; ix < x1; ++ix) {
-      w[2][0] = ym ? ld(ix + 1, iy - 1) : make_double2(0, 0);
-      w[2][1] = ld(ix + 1, iy);
-      w[2][2] = yp ? ld(ix + 1, iy + 1) : make_double2(0, 0);
-      double ar = 0.0, ai = 0.0;
-      const bool interior = ix > 0 && ix < nx - 1 && iy > 0 && iy < ny - 1;
-      if (interior) {
-#pragma unroll
-        for (int dx = 0; dx < 3; ++dx)
-#pragma unroll
-          for (int dy = 0; dy < 3; ++dy) {
-            const double c = a.cin[dx * 3 + dy];
-            ar = fma(c, w[dx][dy].x, ar);
-            ai = fma(c, w[dx][dy].y, ai);
-          }
-      } else {
-        for (int dx = -1; dx <= 1; ++dx) {
-          if (ix + dx < 0 || ix + dx >= nx) continue;
-          double m0, k0r, k0i;
-          entries(a.ax[0], ix, dx, a.omega, m0, k0r, k0i);
-          for (int dy = -1; dy <= 1; ++dy) {
-            if (iy + dy < 0 || iy + dy >= ny) continue;
-            double m1, k1r, k1i;
-            entries(a.ax[1], iy, dy, a.omega, m1, k1r, k1i);
-            const double cre = k0r * m1 + m0 * k1r - a.omega * a.omega * m0 * m1;
-            const double cim = k0i * m1 + m0 * k1i;
-            const double2 v = w[dx + 1][dy + 1];
-            ar += cre * v.x - cim * v.y;
-            ai += cre * v.y + cim * v.x;
-          }
-        }
-      }
-      const double2 fv = __ldg(&f[ix * ny + iy]);
-      const float2 rf = make_float2((float)(fv.x - ar), (float)(fv.y - ai));
-      r[ix * ny + iy] = rf;
-      const float2 ff = make_float2((float)fv.x, (float)fv.y);
-      r2f = fmaf(rf.x, rf.x, fmaf(rf.y, rf.y, r2f));
-      f2f = fmaf(ff.x, ff.x, fmaf(ff.y, ff.y, f2f));
-#pragma unroll
-      for (int dy = 0; dy < 3; ++dy) {
-        w[0][dy] = w[1][dy];
-        w[1][dy] = w[2][dy];
-      }
-    }
-  }
-  r2 = r2f;
-  f2 = f2f;
-  for (int off = 16; off > 0; off >>= 1) {
-    r2 += __shfl_down_sync(0xffffffffu, r2, off);
-    f2 += __shfl_down_sync(0xffffffffu, f2, off);
-  }
-  const int wp = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    sr[wp] = r2;
-    sf[wp] = f2;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a2 = 0, b2 = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-      a2 += sr[i];
-      b2 += sf[i];
-    }
-    const int64_t bid = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-    sums[2 * bid] = a2;
-    sums[2 * bid + 1] = b2;
-  }
-}
-
-// 3D residual through the tensor structure of eq. A3D:
-//   A = (Kx - w^2 Mx) (x) My (x) Mz + Mx (x) (Ky (x) Mz + My (x) Kz).
-// A CTA owns a TY x TZ tile of (y, z) columns and a run of RX3 x-planes.  For
-// each x-plane (one before and one after the run included) it stages the
-// tile plus a one-point halo in shared memory, applies Mz and Kz along z,
-// then My, Ky along y, giving P_M = (My Mz) u and P_K = (Ky Mz + My Kz) u of
-// that plane; the last three planes' (P_M, P_K) stay in registers and the x
-// operators finish A u.  The 1D entries follow eqs. matrixK / matrixM, with
-// the absorbing corner 1/h - i w at both ends of every axis.
-constexpr int TZ3 = 32, TY3 = 8, RX3 = 32;
-
-struct Coef1D {
-  double md, mo;   // M diagonal (2h/6 at an end, 4h/6 inside), off-diagonal h/6
-  double kdr, kdi; // K diagonal (1/h - i w at an end, 2/h inside)
-  double ko;       // K off-diagonal -1/h
+struct ResidQArgs {
+  int64_t n[3];
+  // 3D: c0[4 cx + 2 cy + cz][2 b + c], c1[2 cy + cz][2 b + c]; 2D: c0[2 cx + cy][b], c1[cy][b]
+  double2 c0[8][4];
+  double2 c1[4][4];
 };
 
-__device__ __forceinline__ Coef1D coef1d(const Axis1D& ax, int64_t i, double omega) {
-  const bool end = (i == 0 || i == ax.n - 1);
-  Coef1D c;
-  c.md = (end ? 2.0 : 4.0) * ax.h / 6.0;
-  c.mo = ax.h / 6.0;
-  c.kdr = (end ? 1.0 : 2.0) / ax.h;
-  c.kdi = end ? -omega : 0.0;
-  c.ko = -1.0 / ax.h;
-  return c;
+// (acc.x, acc.y) -= c v for complex c (boundary classes)
+__device__ __forceinline__ void csub_mul(double2& acc, double2 c, double2 v) {
+  acc.x = fma(-c.x, v.x, fma(c.y, v.y, acc.x));
+  acc.y = fma(-c.x, v.y, fma(-c.y, v.x, acc.y));
 }
 
-// d * v with d = (dr, di); di is nonzero only at an absorbing end
-__device__ __forceinline__ double2 cmul_rd(double dr, double di, double2 v) {
-  double2 o;
-  o.x = dr * v.x;
-  o.y = dr * v.y;
-  if (di != 0.0) {
-    o.x = fma(-di, v.y, o.x);
-    o.y = fma(di, v.x, o.y);
-  }
-  return o;
-}
-
-__global__ void __launch_bounds__(TZ3* TY3) k_residual3d(ResidArgs a, const double2* __restrict__ f,
-                                                         const double2* __restrict__ u, float2* __restrict__ r,
-                                                         double* __restrict__ sums, const int* __restrict__ skip) {
-  if (skip && *skip) return;
-  __shared__ double2 sU[TY3 + 2][TZ3 + 2];
-  __shared__ double2 sTM[TY3 + 2][TZ3], sTK[TY3 + 2][TZ3];
-  __shared__ double sr[TY3], sf[TY3];
-  const int64_t nx = a.ax[0].n, ny = a.ax[1].n, nz = a.ax[2].n;
-  const int tz = threadIdx.x, ty = threadIdx.y;
-  const int tid = ty * TZ3 + tz;
-  const int64_t z0 = (int64_t)blockIdx.x * TZ3, y0 = (int64_t)blockIdx.y * TY3;
-  const int64_t xs = (int64_t)blockIdx.z * RX3, xe = min(xs + RX3, nx);  // outputs [xs, xe)
-  const int64_t gz = z0 + tz, gy = y0 + ty;
-  const bool own = gz < nz && gy < ny;
-  const double w2 = a.omega * a.omega;
-  const Coef1D cy = coef1d(a.ax[1], gy, a.omega);
-  float r2f = 0.f, f2f = 0.f;
-  const double2 zero = make_double2(0, 0);
-  double2 PM[3] = {zero, zero, zero}, PK[3] = {zero, zero, zero};  // planes x-1, x, x+1
-  for (int64_t ip = xs - 1; ip <= xe; ++ip) {
-    // stage plane ip (zero outside the domain)
-    const bool pin = ip >= 0 && ip < nx;
-    for (int e = tid; e < (TY3 + 2) * (TZ3 + 2); e += TZ3 * TY3) {
-      const int yy = e / (TZ3 + 2), zz = e - yy * (TZ3 + 2);
-      const int64_t jy = y0 - 1 + yy, jz = z0 - 1 + zz;
-      double2 v = zero;
-      if (pin && jy >= 0 && jy < ny && jz >= 0 && jz < nz) v = __ldg(&u[(ip * ny + jy) * nz + jz]);
-      sU[yy][zz] = v;
-    }
-    __syncthreads();
-    // Mz and Kz along z for the TY+2 staged rows
-    for (int e = tid; e < (TY3 + 2) * TZ3; e += TZ3 * TY3) {
-      const int yy = e / TZ3, zc = e - yy * TZ3;
-      const Coef1D cz = coef1d(a.ax[2], z0 + zc, a.omega);
-      const double2 c0 = sU[yy][zc + 1];
-      const double2 sn = make_double2(sU[yy][zc].x + sU[yy][zc + 2].x, sU[yy][zc].y + sU[yy][zc + 2].y);
-      sTM[yy][zc] = make_double2(fma(cz.md, c0.x, cz.mo * sn.x), fma(cz.md, c0.y, cz.mo * sn.y));
-      const double2 kc = cmul_rd(cz.kdr, cz.kdi, c0);
-      sTK[yy][zc] = make_double2(fma(cz.ko, sn.x, kc.x), fma(cz.ko, sn.y, kc.y));
-    }
-    __syncthreads();
-    // My and Ky along y: this plane's P_M, P_K at the thread's column
-    {
-      const double2 m0 = sTM[ty + 1][tz], mm = sTM[ty][tz], mp = sTM[ty + 2][tz];
-      const double2 k0 = sTK[ty + 1][tz], km = sTK[ty][tz], kp = sTK[ty + 2][tz];
-      const double2 sm = make_double2(mm.x + mp.x, mm.y + mp.y), sk = make_double2(km.x + kp.x, km.y + kp.y);
-      PM[0] = PM[1];
-      PK[0] = PK[1];
-      PM[1] = PM[2];
-      PK[1] = PK[2];
-      PM[2] = make_double2(fma(cy.md, m0.x, cy.mo * sm.x), fma(cy.md, m0.y, cy.mo * sm.y));
-      const double2 km0 = cmul_rd(cy.kdr, cy.kdi, m0);
-      double2 pk;
-      pk.x = fma(cy.ko, sm.x, km0.x);
-      pk.y = fma(cy.ko, sm.y, km0.y);
-      pk.x = fma(cy.md, k0.x, fma(cy.mo, sk.x, pk.x));
-      pk.y = fma(cy.md, k0.y, fma(cy.mo, sk.y, pk.y));
-      PK[2] = pk;
-    }
-    // along x: output plane ix = ip - 1 once planes ix-1, ix, ix+1 are in
-    const int64_t ix = ip - 1;
-    if (own && ix >= xs && ix < xe) {
-      const Coef1D cx = coef1d(a.ax[0], ix, a.omega);
-      const double2 spm = make_double2(PM[0].x + PM[2].x, PM[0].y + PM[2].y);
-      const double2 spk = make_double2(PK[0].x + PK[2].x, PK[0].y + PK[2].y);
-      // (Kx - w^2 Mx) P_M + Mx P_K
-      double2 au = cmul_rd(cx.kdr - w2 * cx.md, cx.kdi, PM[1]);
-      const double od = cx.ko - w2 * cx.mo;
-      au.x = fma(od, spm.x, au.x);
-      au.y = fma(od, spm.y, au.y);
-      au.x = fma(cx.md, PK[1].x, fma(cx.mo, spk.x, au.x));
-      au.y = fma(cx.md, PK[1].y, fma(cx.mo, spk.y, au.y));
-      const int64_t gi = (ix * ny + gy) * nz + gz;
-      const double2 fv = __ldg(&f[gi]);
-      const float2 rf = make_float2((float)(fv.x - au.x), (float)(fv.y - au.y));
-      r[gi] = rf;
-      const float2 ff = make_float2((float)fv.x, (float)fv.y);
-      r2f = fmaf(rf.x, rf.x, fmaf(rf.y, rf.y, r2f));
-      f2f = fmaf(ff.x, ff.x, fmaf(ff.y, ff.y, f2f));
-    }
-  }
-  double r2 = r2f, f2 = f2f;
+// Block sums of |r|^2 and |f|^2 (per-thread FP32 sums of the rounded
+// values; the norms only decide convergence), fixed order.
+template <int NT>
+__device__ __forceinline__ void block_norms(float r2f, float f2f, double* sums, int64_t bid) {
+  __shared__ float sr[NT / 32], sf[NT / 32];
   for (int off = 16; off > 0; off >>= 1) {
-    r2 += __shfl_down_sync(0xffffffffu, r2, off);
-    f2 += __shfl_down_sync(0xffffffffu, f2, off);
+    r2f += __shfl_down_sync(0xffffffffu, r2f, off);
+    f2f += __shfl_down_sync(0xffffffffu, f2f, off);
   }
-  if (tz == 0) {
-    sr[ty] = r2;
-    sf[ty] = f2;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if ((tid & 31) == 0) {
+    sr[tid >> 5] = r2f;
+    sf[tid >> 5] = f2f;
   }
   __syncthreads();
   if (tid == 0) {
     double a2 = 0, b2 = 0;
-    for (int i = 0; i < TY3; ++i) {
-      a2 += sr[i];
-      b2 += sf[i];
+    for (int i = 0; i < NT / 32; ++i) {
+      a2 += (double)sr[i];
+      b2 += (double)sf[i];
     }
-    const int64_t bid = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     sums[2 * bid] = a2;
     sums[2 * bid + 1] = b2;
   }
+}
+
+constexpr int QZ = 32, QY = 16, QX = 32;  // 3D tile: z, y columns, x planes per CTA
+constexpr int QE = ((QY + 2) * (QZ + 2) + QZ * QY - 1) / (QZ * QY);  // staged values per thread
+
+__global__ void __launch_bounds__(QZ* QY) k_residual3d_q(ResidQArgs a, const double2* __restrict__ f,
+                                                         const double2* __restrict__ u, float2* __restrict__ r,
+                                                         double* __restrict__ sums, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ double2 sU[QY + 2][QZ + 2];
+  __shared__ double2 sSz[QY + 2][QZ];
+  const int64_t nx = a.n[0], ny = a.n[1], nz = a.n[2];
+  const int tz = threadIdx.x, ty = threadIdx.y, tid = ty * QZ + tz;
+  const int64_t z0 = (int64_t)blockIdx.x * QZ, y0 = (int64_t)blockIdx.y * QY;
+  const int64_t xs = (int64_t)blockIdx.z * QX, xe = min(xs + QX, nx);
+  const int64_t gz = z0 + tz, gy = y0 + ty;
+  const bool own = gz < nz && gy < ny;
+  const int cy = (gy == 0 || gy == ny - 1) ? 1 : 0, cz = (gz == 0 || gz == nz - 1) ? 1 : 0;
+  const int cyz = 2 * cy + cz;
+  const double2 zero = make_double2(0.0, 0.0);
+  float r2f = 0.f, f2f = 0.f;
+  // staging prefetch of the next plane
+  double2 pf[QE];
+  auto fetch = [&](int64_t ip) {
+#pragma unroll
+    for (int k = 0; k < QE; ++k) {
+      const int e = tid + k * QZ * QY;
+      pf[k] = zero;
+      if (e < (QY + 2) * (QZ + 2) && ip >= 0 && ip < nx) {
+        const int yy = e / (QZ + 2), zz = e - yy * (QZ + 2);
+        const int64_t jy = y0 - 1 + yy, jz = z0 - 1 + zz;
+        if (jy >= 0 && jy < ny && jz >= 0 && jz < nz) pf[k] = __ldg(&u[(ip * ny + jy) * nz + jz]);
+      }
+    }
+  };
+  fetch(xs - 1);
+  double2 Rm = zero, Rc = zero, Qc = zero;  // R(x-2), R(x-1), f - Q at x-1
+  for (int64_t ip = xs - 1; ip <= xe; ++ip) {
+    __syncthreads();  // the previous plane's reads of sU, sSz are done
+#pragma unroll
+    for (int k = 0; k < QE; ++k) {
+      const int e = tid + k * QZ * QY;
+      if (e < (QY + 2) * (QZ + 2)) (&sU[0][0])[e] = pf[k];
+    }
+    if (ip + 1 <= xe) fetch(ip + 1);
+    const bool outp = own && ip >= xs && ip < xe;
+    double2 fv = zero;
+    if (outp) fv = __ldg(&f[(ip * ny + gy) * nz + gz]);
+    __syncthreads();
+    for (int e = tid; e < (QY + 2) * QZ; e += QZ * QY) {
+      const int yy = e / QZ, zc = e - yy * QZ;
+      const double2 lo = sU[yy][zc], hi = sU[yy][zc + 2];
+      sSz[yy][zc] = make_double2(lo.x + hi.x, lo.y + hi.y);
+    }
+    __syncthreads();
+    double2 Rn = zero, Qn = fv;
+    if (own && ip >= 0 && ip < nx) {
+      const double2 P00 = sU[ty + 1][tz + 1], P01 = sSz[ty + 1][tz];
+      const double2 ym = sU[ty][tz + 1], yp = sU[ty + 2][tz + 1];
+      const double2 sm = sSz[ty][tz], sp = sSz[ty + 2][tz];
+      const double2 P10 = make_double2(ym.x + yp.x, ym.y + yp.y), P11 = make_double2(sm.x + sp.x, sm.y + sp.y);
+      const int cx = (ip == 0 || ip == nx - 1) ? 1 : 0;
+      if (cyz == 0) {
+        // inside along y and z: C_1bc real
+        Rn.x = fma(a.c1[0][3].x, P11.x, fma(a.c1[0][2].x, P10.x, fma(a.c1[0][1].x, P01.x, a.c1[0][0].x * P00.x)));
+        Rn.y = fma(a.c1[0][3].x, P11.y, fma(a.c1[0][2].x, P10.y, fma(a.c1[0][1].x, P01.y, a.c1[0][0].x * P00.y)));
+        if (outp) {
+          if (cx == 0) {
+            Qn.x = fma(-a.c0[0][3].x, P11.x, fma(-a.c0[0][2].x, P10.x, fma(-a.c0[0][1].x, P01.x, fma(-a.c0[0][0].x, P00.x, Qn.x))));
+            Qn.y = fma(-a.c0[0][3].x, P11.y, fma(-a.c0[0][2].x, P10.y, fma(-a.c0[0][1].x, P01.y, fma(-a.c0[0][0].x, P00.y, Qn.y))));
+          } else {
+            csub_mul(Qn, a.c0[4][0], P00);
+            csub_mul(Qn, a.c0[4][1], P01);
+            csub_mul(Qn, a.c0[4][2], P10);
+            csub_mul(Qn, a.c0[4][3], P11);
+          }
+        }
+      } else {
+        csub_mul(Rn, a.c1[cyz][0], P00);
+        csub_mul(Rn, a.c1[cyz][1], P01);
+        csub_mul(Rn, a.c1[cyz][2], P10);
+        csub_mul(Rn, a.c1[cyz][3], P11);
+        Rn = make_double2(-Rn.x, -Rn.y);
+        if (outp) {
+          const int cls = 4 * cx + cyz;
+          csub_mul(Qn, a.c0[cls][0], P00);
+          csub_mul(Qn, a.c0[cls][1], P01);
+          csub_mul(Qn, a.c0[cls][2], P10);
+          csub_mul(Qn, a.c0[cls][3], P11);
+        }
+      }
+    }
+    // output plane ip - 1: r = (f - Q)(x) - R(x-1) - R(x+1)
+    const int64_t ix = ip - 1;
+    if (own && ix >= xs && ix < xe) {
+      const float2 rf = make_float2(round_d2f(Qc.x - Rm.x - Rn.x), round_d2f(Qc.y - Rm.y - Rn.y));
+      r[(ix * ny + gy) * nz + gz] = rf;
+      r2f = fmaf(rf.x, rf.x, fmaf(rf.y, rf.y, r2f));
+    }
+    if (outp) {
+      const float fx = round_d2f(fv.x), fy = round_d2f(fv.y);
+      f2f = fmaf(fx, fx, fmaf(fy, fy, f2f));
+    }
+    Rm = Rc;
+    Rc = Rn;
+    Qc = Qn;
+  }
+  block_norms<QZ * QY>(r2f, f2f, sums, ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+}
+
+// 2D: thread per y column, QR2 rows rolling along x; monomials P_0 = u,
+// P_1 = Sy u of each row; r(x) = f(x) - Q(x) - R(x-1) - R(x+1).
+constexpr int QR2 = 32;
+__global__ void __launch_bounds__(256) k_residual2d_q(ResidQArgs a, const double2* __restrict__ f,
+                                                      const double2* __restrict__ u, float2* __restrict__ r,
+                                                      double* __restrict__ sums, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t nx = a.n[0], ny = a.n[1];
+  const int64_t iy = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t xs = (int64_t)blockIdx.y * QR2, xe = min(xs + QR2, nx);
+  const bool own = iy < ny;
+  const int cy = (iy == 0 || iy == ny - 1) ? 1 : 0;
+  const double2 zero = make_double2(0.0, 0.0);
+  float r2f = 0.f, f2f = 0.f;
+  double2 Rm = zero, Rc = zero, Qc = zero;
+  if (own) {
+    const bool ym = iy > 0, yp = iy < ny - 1;
+    // row loads one row ahead
+    double2 c0v = zero, cmv = zero, cpv = zero, fv = zero;
+    auto load = [&](int64_t ix, double2& c, double2& m, double2& p) {
+      c = m = p = zero;
+      if (ix >= 0 && ix < nx) {
+        const double2* row = u + ix * ny + iy;
+        c = __ldg(row);
+        if (ym) m = __ldg(row - 1);
+        if (yp) p = __ldg(row + 1);
+      }
+    };
+    load(xs - 1, c0v, cmv, cpv);
+    for (int64_t ip = xs - 1; ip <= xe; ++ip) {
+      const double2 P0 = c0v;
+      const double2 P1 = make_double2(cmv.x + cpv.x, cmv.y + cpv.y);
+      const bool outp = ip >= xs && ip < xe;
+      if (outp) fv = __ldg(&f[ip * ny + iy]);
+      if (ip + 1 <= xe) load(ip + 1, c0v, cmv, cpv);
+      double2 Rn = zero, Qn = fv;
+      if (ip >= 0 && ip < nx) {
+        const int cx = (ip == 0 || ip == nx - 1) ? 1 : 0;
+        if (cy == 0 && cx == 0) {
+          Rn.x = fma(a.c1[0][1].x, P1.x, a.c1[0][0].x * P0.x);
+          Rn.y = fma(a.c1[0][1].x, P1.y, a.c1[0][0].x * P0.y);
+          if (outp) {
+            Qn.x = fma(-a.c0[0][1].x, P1.x, fma(-a.c0[0][0].x, P0.x, Qn.x));
+            Qn.y = fma(-a.c0[0][1].x, P1.y, fma(-a.c0[0][0].x, P0.y, Qn.y));
+          }
+        } else {
+          csub_mul(Rn, a.c1[cy][0], P0);
+          csub_mul(Rn, a.c1[cy][1], P1);
+          Rn = make_double2(-Rn.x, -Rn.y);
+          if (outp) {
+            csub_mul(Qn, a.c0[2 * cx + cy][0], P0);
+            csub_mul(Qn, a.c0[2 * cx + cy][1], P1);
+          }
+        }
+      }
+      const int64_t ix = ip - 1;
+      if (ix >= xs && ix < xe) {
+        const float2 rf = make_float2(round_d2f(Qc.x - Rm.x - Rn.x), round_d2f(Qc.y - Rm.y - Rn.y));
+        r[ix * ny + iy] = rf;
+        r2f = fmaf(rf.x, rf.x, fmaf(rf.y, rf.y, r2f));
+      }
+      if (outp) {
+        const float fx = round_d2f(fv.x), fy = round_d2f(fv.y);
+        f2f = fmaf(fx, fx, fmaf(fy, fy, f2f));
+      }
+      Rm = Rc;
+      Rc = Rn;
+      Qc = Qn;
+    }
+  }
+  block_norms<256>(r2f, f2f, sums, (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -828,56 +721,53 @@ __global__ void __launch_bounds__(1024) k_residual_finalize(const double* __rest
 
 }  // namespace
 
-cudaError_t launch_residual(int dim, const int64_t* n, const double* h, double omega, const double2* f,
+cudaError_t launch_residual(int dim, const int64_t* n, const double* h, double omega, const double* wc,
+                            const double2* f,
                             const double2* u, float2* r, double* sums, int64_t* nblocks, const int* skip,
                             cudaStream_t st) {
-  ResidArgs a{};
-  a.dim = dim;
-  a.omega = omega;
-  int64_t N = 1;
-  for (int k = 0; k < dim; ++k) {
-    a.ax[k].n = n[k];
-    a.ax[k].h = h[k];
-    N *= n[k];
-  }
-  // interior coefficients (all entries real away from the corners)
-  double m[3][3], kk[3][3];
-  for (int k = 0; k < dim; ++k) {
-    m[k][0] = m[k][2] = h[k] / 6.0;
-    m[k][1] = 4.0 * h[k] / 6.0;
-    kk[k][0] = kk[k][2] = -1.0 / h[k];
-    kk[k][1] = 2.0 / h[k];
-  }
-  if (dim == 2) {
-    for (int d0 = 0; d0 < 3; ++d0)
-      for (int d1 = 0; d1 < 3; ++d1)
-        a.cin[d0 * 3 + d1] = kk[0][d0] * m[1][d1] + m[0][d0] * kk[1][d1] - omega * omega * m[0][d0] * m[1][d1];
-  } else {
-    for (int d0 = 0; d0 < 3; ++d0)
-      for (int d1 = 0; d1 < 3; ++d1)
-        for (int d2 = 0; d2 < 3; ++d2)
-          a.cin[d0 * 9 + d1 * 3 + d2] = kk[0][d0] * m[1][d1] * m[2][d2] + m[0][d0] * kk[1][d1] * m[2][d2] +
-                                        m[0][d0] * m[1][d1] * kk[2][d2] -
-                                        omega * omega * m[0][d0] * m[1][d1] * m[2][d2];
-  }
   const int bs = 256;
-  if (dim == 2) {
-    const dim3 grid((unsigned)((n[1] + bs - 1) / bs), (unsigned)((n[0] + RX2 - 1) / RX2));
+  if (dim == 2 || dim == 3) {
+    // monomial coefficients by end class (see the FP64-instruction-lean kernels)
+    ResidQArgs q{};
+    for (int k = 0; k < dim; ++k) q.n[k] = n[k];
+    using cd = std::complex<double>;
+    auto Mk = [&](int k, int end, int bit) -> cd { return bit ? h[k] / 6.0 : (end ? 2.0 : 4.0) * h[k] / 6.0; };
+    auto Kk = [&](int k, int end, int bit) -> cd {
+      return bit ? cd(-1.0 / h[k], 0.0) : (end ? cd(1.0 / h[k], -wc[k]) : cd(2.0 / h[k], 0.0));
+    };
+    const double w2 = omega * omega;
+    auto put = [](double2& d, cd v) { d = make_double2(v.real(), v.imag()); };
+    if (dim == 3) {
+      for (int cx = 0; cx < 2; ++cx)
+        for (int cy = 0; cy < 2; ++cy)
+          for (int cz = 0; cz < 2; ++cz)
+            for (int a1 = 0; a1 < 2; ++a1)
+              for (int b = 0; b < 2; ++b)
+                for (int c = 0; c < 2; ++c) {
+                  const cd v = Kk(0, cx, a1) * Mk(1, cy, b) * Mk(2, cz, c) + Mk(0, cx, a1) * Kk(1, cy, b) * Mk(2, cz, c) +
+                               Mk(0, cx, a1) * Mk(1, cy, b) * Kk(2, cz, c) - w2 * Mk(0, cx, a1) * Mk(1, cy, b) * Mk(2, cz, c);
+                  if (a1 == 0) put(q.c0[4 * cx + 2 * cy + cz][2 * b + c], v);
+                  else if (cx == 0) put(q.c1[2 * cy + cz][2 * b + c], v);
+                }
+      const dim3 grid((unsigned)((n[2] + QZ - 1) / QZ), (unsigned)((n[1] + QY - 1) / QY), (unsigned)((n[0] + QX - 1) / QX));
+      *nblocks = (int64_t)grid.x * grid.y * grid.z;
+      k_residual3d_q<<<grid, dim3(QZ, QY), 0, st>>>(q, f, u, r, sums, skip);
+      return cudaGetLastError();
+    }
+    for (int cx = 0; cx < 2; ++cx)
+      for (int cy = 0; cy < 2; ++cy)
+        for (int a1 = 0; a1 < 2; ++a1)
+          for (int b = 0; b < 2; ++b) {
+            const cd v = Kk(0, cx, a1) * Mk(1, cy, b) + Mk(0, cx, a1) * Kk(1, cy, b) - w2 * Mk(0, cx, a1) * Mk(1, cy, b);
+            if (a1 == 0) put(q.c0[2 * cx + cy][b], v);
+            else if (cx == 0) put(q.c1[cy][b], v);
+          }
+    const dim3 grid((unsigned)((n[1] + bs - 1) / bs), (unsigned)((n[0] + QR2 - 1) / QR2));
     *nblocks = (int64_t)grid.x * grid.y;
-    k_residual2d<<<grid, bs, 0, st>>>(a, f, u, r, sums, skip);
+    k_residual2d_q<<<grid, bs, 0, st>>>(q, f, u, r, sums, skip);
     return cudaGetLastError();
   }
-  if (dim == 3) {
-    const dim3 grid((unsigned)((n[2] + TZ3 - 1) / TZ3), (unsigned)((n[1] + TY3 - 1) / TY3),
-                    (unsigned)((n[0] + RX3 - 1) / RX3));
-    *nblocks = (int64_t)grid.x * grid.y * grid.z;
-    k_residual3d<<<grid, dim3(TZ3, TY3), 0, st>>>(a, f, u, r, sums, skip);
-    return cudaGetLastError();
-  }
-  const int64_t grid = (N + bs - 1) / bs;
-  *nblocks = grid;
-  k_residual<<<(unsigned)grid, bs, 0, st>>>(a, f, u, r, sums, N, skip);
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 static FF2 split_host(double x) {
@@ -887,7 +777,8 @@ static FF2 split_host(double x) {
   return c;
 }
 
-cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, double omega, const float4* f,
+cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, double omega, const double* wc,
+                               const float4* f,
                                const float4* u, float2* r, double* sums, int64_t* nblocks, const int* skip,
                                cudaStream_t st) {
   ResidFFArgs a{};
@@ -904,7 +795,7 @@ cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, doubl
     x.kdi = split_host(2.0 / hk);
     x.kder = split_host(1.0 / hk);
     x.ko = split_host(-1.0 / hk);
-    x.kdei = split_host(-omega);
+    x.kdei = split_host(-wc[k]);
     x.cdi = split_host(2.0 / hk - w2 * (4.0 * hk / 6.0));
     x.cde = split_host(1.0 / hk - w2 * (2.0 * hk / 6.0));
     x.co = split_host(-1.0 / hk - w2 * (hk / 6.0));
@@ -928,7 +819,7 @@ cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, doubl
       if (d == 0) {
         m = (end ? 2.0 : 4.0) * h[k] / 6.0;
         kr = (end ? 1.0 : 2.0) / h[k];
-        ki = end ? -omega : 0.0;
+        ki = end ? -wc[k] : 0.0;
       } else {
         m = h[k] / 6.0;
         kr = -1.0 / h[k];
@@ -1024,11 +915,13 @@ cudaError_t launch_refine_init(RefineState* st, double tol, int max_iter, cudaSt
 int64_t residual_blocks(int dim, const int64_t* n) {
   if (dim == 2) {
     // the larger of the FP64 grid and the float-float interior + perimeter grids
-    const int64_t fp64 = ((n[1] + 255) / 256) * ((n[0] + RX2 - 1) / RX2);
+    const int64_t fp64 = ((n[1] + 255) / 256) * ((n[0] + QR2 - 1) / QR2);
     const int64_t ff = ((n[1] - 2 + 255) / 256) * ((n[0] - 2 + RX2 - 1) / RX2) + (2 * n[1] + 2 * (n[0] - 2) + 255) / 256;
     return std::max(fp64, ff);
   }
-  return ((n[2] + TZ3 - 1) / TZ3) * ((n[1] + TY3 - 1) / TY3) * ((n[0] + RX3 - 1) / RX3);
+  const int64_t ff = ((n[2] + TZ3 - 1) / TZ3) * ((n[1] + TY3 - 1) / TY3) * ((n[0] + RX3 - 1) / RX3);
+  const int64_t q = ((n[2] + QZ - 1) / QZ) * ((n[1] + QY - 1) / QY) * ((n[0] + QX - 1) / QX);
+  return std::max(ff, q);
 }
 
 cudaError_t launch_residual_finalize(const double* sums, int64_t nblocks, RefineState* state,

@@ -27,6 +27,8 @@ struct Solve2DArgs {
   int64_t ch;       // rows per chunk of the tridiagonal sweeps
   int64_t nchunks;  // ceil(nx / ch)
   double eninv[2];  // e^{-t (n1-1)}: weight of the last x1 face in the Step-3 rhs
+  double wx = 0;    // w of the absorbing corners along x (0: Neumann x faces)
+  double wy = 0;    // w of the absorbing x1 faces (0: Neumann), in C_bb
 };
 
 constexpr int kChunkF32 = 16;
@@ -64,8 +66,9 @@ size_t chunk_record_bytes(int prec);
 cudaError_t launch_reduce_faces(int prec, const void* partial, void* out, int64_t nx, int64_t nwarps,
                                 const double* scale0, const double* scale1, const int* skip, cudaStream_t st);
 // C_bb of the auxiliary with wrap factor g (eq. Cbb; g = 1: periodic).
+// wx, wy: w of the absorbing x ends and x1 faces (0 on a Neumann axis).
 cudaError_t launch_apply_cbb(int prec, const void* in, const void* in2, void* out, int64_t nx, double hx,
-                             double h1, double omega, double p, const double* g, const double* ginv,
+                             double h1, double wx, double wy, double p, const double* g, const double* ginv,
                              const int* skip, cudaStream_t st);
 
 // Refinement state kept on the device (one per plan).
@@ -82,13 +85,16 @@ struct RefineState {
 // r = f - A u in FP64 (eq. A2D / A3D), r stored as complex64, per-block sums
 // of |r|^2 and |f|^2 into `sums` (2 doubles per block).  Returns the number of
 // blocks used through *nblocks.
-cudaError_t launch_residual(int dim, const int64_t* n, const double* h, double omega, const double2* f,
+// wc[k]: w of the absorbing ends of axis k (0 on a Neumann axis).
+cudaError_t launch_residual(int dim, const int64_t* n, const double* h, double omega, const double* wc,
+                            const double2* f,
                             const double2* u, float2* r, double* sums, int64_t* nblocks, const int* skip,
                             cudaStream_t st);
 // The same residual with f and u as float-float complex vectors (float4 per
 // point: re_hi, im_hi, re_lo, im_lo), about 48 significant bits, computed on
 // the FP32 pipes.  Same grid and sums layout as launch_residual.
-cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, double omega, const float4* f,
+cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, double omega, const double* wc,
+                               const float4* f,
                                const float4* u, float2* r, double* sums, int64_t* nblocks, const int* skip,
                                cudaStream_t st);
 // complex128 -> float-float (hi = round(x), lo = round(x - hi)) and back.

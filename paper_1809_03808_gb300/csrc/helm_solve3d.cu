@@ -27,6 +27,7 @@ namespace {
 struct Plane3DArgs {
   int64_t nx, ny, nz;
   double hx, hy, hz, omega;
+  double wx, wy, wz;  // w of the absorbing ends of each axis (0: Neumann axis)
   // outer axis (y) eigen-data (Lam^B and 1/mu complex: gamma-circulant auxiliary)
   const double *lamBo, *invmuo, *lamAo, *sigAo, *parAo, *two;
   // inner axis (z) eigen-data
@@ -64,7 +65,7 @@ struct ThomasRow {
 //   D11 = (1 + i w hz)/hz - p hz/3, D1n = -1/hz - p hz/6, E11 = hz/3, E1n = hz/6,
 // M, K along x; p = w^2 - Lam_{1,l} (complex for outer A modes).
 template <typename C>
-__device__ void plane_cbb(const C* v, const C* w2, C* out, int nx, double hx, double hz, double omega,
+__device__ void plane_cbb(const C* v, const C* w2, C* out, int nx, double hx, double hz, double wx, double wz,
                           double pre, double pim, C g, C ginv) {
   for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
     auto get = [&](int face, int j) -> C {
@@ -74,7 +75,7 @@ __device__ void plane_cbb(const C* v, const C* w2, C* out, int nx, double hx, do
     };
     const bool end = (ix == 0 || ix == nx - 1);
     const double md = end ? 2.0 * hx / 6.0 : 4.0 * hx / 6.0, mo = hx / 6.0;
-    const double kdr = end ? 1.0 / hx : 2.0 / hx, kdi = end ? -omega : 0.0, ko = -1.0 / hx;
+    const double kdr = end ? 1.0 / hx : 2.0 / hx, kdi = end ? -wx : 0.0, ko = -1.0 / hx;
     C Mv[2], Kv[2];
     for (int f = 0; f < 2; ++f) {
       C v0 = get(f, ix);
@@ -84,7 +85,7 @@ __device__ void plane_cbb(const C* v, const C* w2, C* out, int nx, double hx, do
       Mv[f] = cadd(cscale(v0, (decltype(v0.x))md), cscale(nb, (decltype(v0.x))mo));
       Kv[f] = cadd(cmul(v0, mk<C>(kdr, kdi)), cscale(nb, (decltype(v0.x))ko));
     }
-    const C D11 = mk<C>(1.0 / hz - pre * hz / 3.0, omega - pim * hz / 3.0);
+    const C D11 = mk<C>(1.0 / hz - pre * hz / 3.0, wz - pim * hz / 3.0);
     const C D1n = mk<C>(-1.0 / hz - pre * hz / 6.0, -pim * hz / 6.0);
     const auto E11 = (decltype(D11.x))(hz / 3.0), E1n = (decltype(D11.x))(hz / 6.0);
     out[ix] = cadd(cadd(cmul(D11, Mv[0]), cscale(Kv[0], E11)), cmul(ginv, cadd(cmul(D1n, Mv[1]), cscale(Kv[1], E1n))));
@@ -156,9 +157,9 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
     return cmul(v, gscale);
   };
   ThomasRow<C> thB, thA;
-  thB.k = line_coef<C>(lo_re + lBi_re - w2, lo_im + lBi_im, a.hx, a.omega);
+  thB.k = line_coef<C>(lo_re + lBi_re - w2, lo_im + lBi_im, a.hx, a.wx);
   thB.n = nx;
-  thA.k = line_coef<C>(lo_re + a.lamAi[2 * mc] - w2, lo_im + a.lamAi[2 * mc + 1], a.hx, a.omega);
+  thA.k = line_coef<C>(lo_re + a.lamAi[2 * mc] - w2, lo_im + a.lamAi[2 * mc + 1], a.hx, a.wx);
   thA.n = nx;
   const double pre = w2 - lo_re, pim = -lo_im;
 
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
         sn = ac ? cmul(x, twm) : mk<C>(0, 0);
       },
       vin, mk<C>(1.0 / (double)nz, 0), mk<C>(a.en_i[0] / (double)nz, a.en_i[1] / (double)nz));
-  plane_cbb(vin, (const C*)nullptr, cin, nx, a.hx, a.hz, a.omega, pre, pim, gi, giv);
+  plane_cbb(vin, (const C*)nullptr, cin, nx, a.hx, a.hz, a.wx, a.wz, pre, pim, gi, giv);
   __syncthreads();
   // inner Step 2: A solve on the generated rhs, reduce to w_in
   forward(thA, tabA, [&](int ix) { return cadd(cin[ix], cscale(cin[nx + ix], pari)); });
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
         sn = cscale(t, pari);
       },
       win, mk<C>(1, 0), mk<C>(1, 0));
-  plane_cbb(vin, win, cin, nx, a.hx, a.hz, a.omega, pre, pim, gi, giv);
+  plane_cbb(vin, win, cin, nx, a.hx, a.hz, a.wx, a.wz, pre, pim, gi, giv);
   __syncthreads();
   // inner Step 3: corrected B-aux solve, y3 written over the scratch
   forward(thB, tabB, [&](int ix) {
@@ -373,12 +374,12 @@ __global__ void k_outer_cbb(const typename cpx<T>::type* __restrict__ v, const t
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nx * nz) return;
   const int64_t ix = i / nz, iz = i - ix * nz;
-  auto ent = [&](int64_t n, double h, int64_t j, int d, double& m, double& kr, double& ki) {
+  auto ent = [&](int64_t n, double h, double w, int64_t j, int d, double& m, double& kr, double& ki) {
     const bool end = (j == 0 || j == n - 1);
     if (d == 0) {
       m = (end ? 2.0 : 4.0) * h / 6.0;
       kr = (end ? 1.0 : 2.0) / h;
-      ki = end ? -a.omega : 0.0;
+      ki = end ? -w : 0.0;
     } else {
       m = h / 6.0;
       kr = -1.0 / h;
@@ -391,12 +392,12 @@ __global__ void k_outer_cbb(const typename cpx<T>::type* __restrict__ v, const t
     const int64_t jx = ix + dx;
     if (jx < 0 || jx >= nx) continue;
     double mx, kxr, kxi;
-    ent(nx, a.hx, ix, dx, mx, kxr, kxi);
+    ent(nx, a.hx, a.wx, ix, dx, mx, kxr, kxi);
     for (int dz = -1; dz <= 1; ++dz) {
       const int64_t jz = iz + dz;
       if (jz < 0 || jz >= nz) continue;
       double mz, kzr, kzi;
-      ent(nz, a.hz, iz, dz, mz, kzr, kzi);
+      ent(nz, a.hz, a.wz, iz, dz, mz, kzr, kzi);
       const C cs = mk<C>(kxr * mz + mx * kzr - w2 * mx * mz, kxi * mz + mx * kzi);
       const auto cp = (decltype(cs.x))(mx * mz);
       for (int f = 0; f < 2; ++f) {
@@ -409,7 +410,7 @@ __global__ void k_outer_cbb(const typename cpx<T>::type* __restrict__ v, const t
   }
   using T2 = decltype(Sv[0].x);
   const T2 e11 = (T2)(a.hy / 3.0), e1n = (T2)(a.hy / 6.0);
-  const C d11 = mk<C>(1.0 / a.hy, a.omega);
+  const C d11 = mk<C>(1.0 / a.hy, a.wy);
   const T2 d1n = (T2)(-1.0 / a.hy);
   const C g = mk<C>(a.g_o[0], a.g_o[1]), gv = mk<C>(a.ginv_o[0], a.ginv_o[1]);
   out[i] = cadd(cadd(cscale(Sv[0], e11), cmul(d11, Pv[0])), cmul(gv, cadd(cscale(Sv[1], e1n), cscale(Pv[1], d1n))));
@@ -419,8 +420,31 @@ __global__ void k_outer_cbb(const typename cpx<T>::type* __restrict__ v, const t
 // Reciprocal pivots of the inner tridiagonal lines of one line type (outer
 // mode type x inner mode type), for every (x, l, m): the FP64 recurrence of
 // ThomasRow, stored in the compute precision at the layout of the scratch.
+//
+// Per line it also records where the recurrence u_j = a - b^2 / u_{j-1}
+// (constant a, b inside the line) has settled at its attracting fixed point
+// u_inf, the root of u^2 - a u + b^2 = 0 of larger modulus: rows j >= len
+// (below the last row) satisfy |1/u_j - 1/u_inf| <= tol |1/u_inf| (tol 2^-27
+// for complex64 tables, a quarter of the FP32 rounding; 2^-50 for
+// complex128), so the tiled sweeps read the table only for rows < len and use
+// 1/u_inf beyond.  lend[2 * line] = 1/u_inf, lend[2 * line + 1] = 1/u_{nx-1}
+// (the absorbing corner row); line = l * nz + m.  For propagating modes the
+// pivots keep oscillating and len covers the whole line.
+__device__ __forceinline__ double2 csqrt_d(double2 z) {
+  const double r = hypot(z.x, z.y);
+  double re = sqrt(0.5 * (r + fabs(z.x))), im = 0.0;
+  if (re > 0.0) im = 0.5 * z.y / re;
+  if (z.x < 0.0) {  // sqrt(z) = |im| + i sign(y) re
+    const double t = fabs(im);
+    im = z.y < 0.0 ? -re : re;
+    re = t;
+  }
+  return make_double2(re, im);
+}
+
 template <typename T>
-__global__ void k_plane_tables(typename cpx<T>::type* __restrict__ tab, Plane3DArgs a, int outerA, int innerA) {
+__global__ void k_plane_tables(typename cpx<T>::type* __restrict__ tab, typename cpx<T>::type* __restrict__ lend,
+                               int* __restrict__ lenL, Plane3DArgs a, int outerA, int innerA) {
   using C = typename cpx<T>::type;
   const int64_t ny = a.ny, nz = a.nz, nx = a.nx;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // l * nz + m
@@ -429,14 +453,32 @@ __global__ void k_plane_tables(typename cpx<T>::type* __restrict__ tab, Plane3DA
   const double* lo = outerA ? a.lamAo : a.lamBo;
   const double* li = innerA ? a.lamAi : a.lamBi;
   const double w2 = a.omega * a.omega;
-  const LineCoef<double2> k = line_coef<double2>(lo[2 * l] + li[2 * m] - w2, lo[2 * l + 1] + li[2 * m + 1], a.hx, a.omega);
+  const LineCoef<double2> k = line_coef<double2>(lo[2 * l] + li[2 * m] - w2, lo[2 * l + 1] + li[2 * m + 1], a.hx, a.wx);
+  // attracting fixed point of the interior recurrence
+  const double2 disc = csqrt_d(csub(cmul(k.a, k.a), cscale(cmul(k.b, k.b), 4.0)));
+  const double2 r1 = cscale(cadd(k.a, disc), 0.5), r2 = cscale(csub(k.a, disc), 0.5);
+  const double2 uinf = (r1.x * r1.x + r1.y * r1.y >= r2.x * r2.x + r2.y * r2.y) ? r1 : r2;
+  const double2 iinf = crecip(uinf);
+  const double tol = sizeof(T) == 4 ? 7.450580596923828e-09 : 8.881784197001252e-16;  // 2^-27, 2^-50
+  const double tol2 = tol * tol * (iinf.x * iinf.x + iinf.y * iinf.y);
   double2 c = make_double2(0, 0);
+  int64_t last_bad = -1;
+  double2 inv = make_double2(0, 0);
   for (int64_t ix = 0; ix < nx; ++ix) {
     const double2 aj = (ix == 0 || ix == nx - 1) ? k.ac : k.a;
     const double2 den = ix == 0 ? aj : csub(aj, cmul(k.b, c));
-    const double2 inv = crecip(den);
+    inv = crecip(den);
     c = cmul(k.b, inv);
     tab[ix * ny * nz + i] = cvt<C>(inv);
+    if (ix < nx - 1) {
+      const double dx = inv.x - iinf.x, dy = inv.y - iinf.y;
+      if (!(dx * dx + dy * dy <= tol2)) last_bad = ix;
+    }
+  }
+  if (lend) {
+    lend[2 * i] = cvt<C>(iinf);
+    lend[2 * i + 1] = cvt<C>(inv);
+    lenL[i] = (int)(last_bad + 1);
   }
 }
 
@@ -449,6 +491,9 @@ Plane3DArgs make_args(const Plan3D& p) {
   a.hy = p.h[1];
   a.hz = p.h[2];
   a.omega = p.omega;
+  a.wx = p.wc[0];
+  a.wy = p.wc[1];
+  a.wz = p.wc[2];
   a.lamBo = p.axo->lamB;
   a.invmuo = p.axo->invmu;
   a.lamAo = p.axo->lamA;
@@ -474,6 +519,324 @@ Plane3DArgs make_args(const Plan3D& p) {
   return a;
 }
 
+// ---------------------------------------------------------------------------
+// Tiled inner sweeps (a6).  The inner Steps 1-3 of Section 5.1.2 for outer
+// mode l run as three launches (k_inner3d) with a per-plane reduction between
+// them (k_inner_reduce), instead of one CTA per plane that streams its Thomas
+// scratch through HBM.
+//
+// A CTA of k_inner3d owns kMW consecutive inner modes m of one outer mode l
+// (the lines (x, l, m0..m0+kMW-1), x = 0..nx-1).  It stages their right-hand
+// sides in shared memory ([x][kMW], read from HBM once), and solves each line
+// by the chunked LU of Section 4.1.2's per-mode solves: thread (m, c) owns rows
+// [c*ch, c*ch + ch) of line m.
+//   pass 1: with the carries d_{s-1} = 0, x_{e+1} = 0 the chunk's forward
+//     substitution d_j = (r_j - b d_{j-1}) / u_j gives d_loc at its last row
+//     and, through the running products alpha_j = prod_{i<=j} (-b / u_i), the
+//     backward substitution's value x_loc at its first row, plus the
+//     rhs-independent alpha_e and beta = sum_j alpha_{j-1} alpha_j, so that
+//       d_e = d_loc + alpha_e d_{s-1},
+//       x_s = x_loc + beta d_{s-1} + alpha_e x_{e+1};
+//   scan: these affine maps composed over the chunks of each line by one warp
+//     (Kogge-Stone over lanes), forward for d and backward for x;
+//   pass 2: the chunk's substitutions again from the exact carries; d and then
+//     x overwrite the staged right-hand sides.
+// The pivots 1/u_j come from the per-plan FP64 tables, read only for rows
+// before the line's pivots settle (k_plane_tables); later rows use 1/u_inf and
+// the corner row 1/u_{nx-1}.  Inner Steps 1 and 2 then form the CTA's share of
+// the inner boundary rows (eqs. 2dBs1, step2-3 on the plane) from the solved
+// tile, summing its inner modes in a fixed order, and accumulate them over the
+// CTA's nmb tiles into one face partial per CTA; inner Step 3 writes the
+// plane solution y3(x, l, m).
+// ---------------------------------------------------------------------------
+constexpr int kMW = 16;  // inner modes per tile
+
+struct InnerArgs {
+  Plane3DArgs a;
+  int ch;      // rows per chunk
+  int nc;      // chunks per line
+  int nmb;     // tiles per CTA (inner modes kMW * nmb per CTA)
+  int nparts;  // face partials per plane = gridDim.x
+};
+
+// affine map x -> p x + q, composed as (p2, q2) o (p1, q1) = (p2 p1, p2 q1 + q2)
+template <typename C>
+__device__ __forceinline__ void affine_compose(C& p, C& q, C p1, C q1) {
+  q = cadd(cmul(p, q1), q);
+  p = cmul(p, p1);
+}
+
+template <typename C>
+__device__ __forceinline__ C shfl_up_c(C v, int off) {
+  v.x = __shfl_up_sync(0xffffffffu, v.x, off);
+  v.y = __shfl_up_sync(0xffffffffu, v.y, off);
+  return v;
+}
+
+// Launch bound: 1024 threads (64 chunks of kMW lines) in complex64, 512 in
+// complex128 (its wider registers).
+template <typename T>
+constexpr int inner_max_threads() {
+  return sizeof(T) == 4 ? 1024 : 512;
+}
+
+template <typename T, int OSTEP, int ISTEP>
+__global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
+    InnerArgs ia, const typename cpx<T>::type* __restrict__ fhat, const typename cpx<T>::type* __restrict__ gfaces,
+    const typename cpx<T>::type* __restrict__ cin, const typename cpx<T>::type* __restrict__ tab,
+    const typename cpx<T>::type* __restrict__ lend, const int* __restrict__ lenL,
+    typename cpx<T>::type* __restrict__ part, typename cpx<T>::type* __restrict__ y3, const int* __restrict__ skip) {
+  using C = typename cpx<T>::type;
+  if (skip && *skip) return;
+  const Plane3DArgs& a = ia.a;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nx = (int)a.nx;
+  const int64_t ny = a.ny, nz = a.nz;
+  const int nc = ia.nc, ch = ia.ch;
+  C* tile = reinterpret_cast<C*>(smem_raw);  // [nx][kMW]
+  C* sums = tile + (size_t)nx * kMW;         // [4][nc][kMW]: d_loc, x_loc, alpha, beta; then the carries
+  C* facc = sums + 4 * nc * kMW;             // [2][nx] face accumulators (inner Steps 1, 2)
+  C* mw = facc + 2 * nx;                     // [kMW] rhs scale, [kMW] rhs weight of the last face, [2][kMW] face weights
+  const int64_t l = blockIdx.y;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int mi = tid & (kMW - 1), c = tid / kMW;
+  const double w2 = a.omega * a.omega;
+  // outer-mode quantities (outer A modes in outer Step 2)
+  const double lo_re = OSTEP == 2 ? a.lamAo[2 * l] : a.lamBo[2 * l];
+  const double lo_im = OSTEP == 2 ? a.lamAo[2 * l + 1] : a.lamBo[2 * l + 1];
+  const C gscale = OSTEP == 2 ? mk<C>(1, 0) : mk<C>(a.invmuo[2 * l], a.invmuo[2 * l + 1]);
+  const T paro = (T)a.parAo[l];
+  const C wl = cmul(mk<C>(a.two[2 * l], -a.two[2 * l + 1]), mk<C>(a.eninv_o[0], a.eninv_o[1]));
+  const C* cin1 = cin ? cin + l * 2 * nx : nullptr;  // inner C_bb faces of this plane
+  const C* cinn = cin ? cin1 + nx : nullptr;
+  const C* g1 = gfaces;  // outer faces [2][nx][nz]
+  const C* gn = gfaces ? gfaces + (int64_t)nx * nz : nullptr;
+  if (ISTEP != 3)
+    for (int e = tid; e < 2 * nx; e += nthr) facc[e] = mk<C>(0, 0);
+
+  for (int mb = 0; mb < ia.nmb; ++mb) {
+    const int64_t m0 = ((int64_t)blockIdx.x * ia.nmb + mb) * kMW;
+    if (m0 >= nz) break;
+    __syncthreads();  // the previous tile's face sums are done
+    if (tid < kMW) {
+      const int64_t m = m0 + tid;
+      const bool on = m < nz;
+      const int64_t mc = on ? m : 0;
+      // right-hand side of inner Step 1 / 3: (G + [C_bb terms]) / mu_m; Step 2: c_1 + par_m c_n
+      mw[tid] = on ? (ISTEP == 2 ? mk<C>(1, 0) : mk<C>(a.invmui[2 * mc], a.invmui[2 * mc + 1])) : mk<C>(0, 0);
+      mw[kMW + tid] = ISTEP == 2 ? mk<C>(a.parAi[mc], 0)
+                                 : cmul(mk<C>(a.twi[2 * mc], -a.twi[2 * mc + 1]), mk<C>(a.eninv_i[0], a.eninv_i[1]));
+      // face weights of the inner boundary rows: Step 1 (1, e^{-i theta_m}), Step 2 (sigma_m, par_m sigma_m)
+      C w1 = mk<C>(1, 0), wn = mk<C>(a.twi[2 * mc], a.twi[2 * mc + 1]);
+      if (ISTEP == 2) {
+        w1 = mk<C>(a.sigAi[2 * mc], a.sigAi[2 * mc + 1]);
+        wn = cscale(w1, (T)a.parAi[mc]);
+      }
+      mw[2 * kMW + tid] = on ? w1 : mk<C>(0, 0);
+      mw[3 * kMW + tid] = on ? wn : mk<C>(0, 0);
+    }
+    __syncthreads();
+    // ---- stage the right-hand sides ----
+    {
+      constexpr int B = 8;
+      for (int e0 = tid; e0 < nx * kMW; e0 += B * nthr) {
+        C v[B];
+#pragma unroll
+        for (int t = 0; t < B; ++t) {
+          const int e = e0 + t * nthr;
+          v[t] = mk<C>(0, 0);
+          if (e < nx * kMW) {
+            const int x = e / kMW, mm = e - x * kMW;
+            const int64_t m = m0 + mm;
+            if (m < nz) {
+              if (ISTEP == 2) {
+                v[t] = cadd(cin1[x], cmul(cinn[x], mw[kMW + mm]));
+              } else {
+                C g;
+                if (OSTEP == 1) g = cmul(fhat[((int64_t)x * ny + l) * nz + m], gscale);
+                else if (OSTEP == 2) g = cadd(g1[(int64_t)x * nz + m], cscale(gn[(int64_t)x * nz + m], paro));
+                else
+                  g = cmul(cadd(cadd(fhat[((int64_t)x * ny + l) * nz + m], g1[(int64_t)x * nz + m]),
+                                cmul(gn[(int64_t)x * nz + m], wl)),
+                           gscale);
+                if (ISTEP == 3) g = cadd(g, cadd(cin1[x], cmul(cinn[x], mw[kMW + mm])));
+                v[t] = cmul(g, mw[mm]);
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < B; ++t) {
+          const int e = e0 + t * nthr;
+          if (e < nx * kMW) tile[e] = v[t];
+        }
+      }
+    }
+    // ---- line constants of thread (mi, c) ----
+    const int64_t m = m0 + mi;
+    const bool act = m < nz && c < nc;
+    const int64_t line = l * nz + (m < nz ? m : 0);
+    const double li_re = ISTEP == 2 ? a.lamAi[2 * (line - l * nz)] : a.lamBi[2 * (line - l * nz)];
+    const double li_im = ISTEP == 2 ? a.lamAi[2 * (line - l * nz) + 1] : a.lamBi[2 * (line - l * nz) + 1];
+    const double sre = lo_re + li_re - w2, sim = lo_im + li_im;
+    const C b = mk<C>(sre * (a.hx / 6.0) - 1.0 / a.hx, sim * (a.hx / 6.0));
+    const C nb = mk<C>(-(sre * (a.hx / 6.0) - 1.0 / a.hx), -sim * (a.hx / 6.0));
+    const C iinf = lend[2 * line], ilast = lend[2 * line + 1];
+    const int L = lenL[line];
+    const C* tcol = tab + l * nz + (m < nz ? m : 0);
+    const int64_t xs = ny * nz;
+    auto pivot = [&](int j) -> C { return j < L ? tcol[(int64_t)j * xs] : (j == nx - 1 ? ilast : iinf); };
+    const int s0 = c * ch, e0 = min(s0 + ch, nx) - 1;
+    __syncthreads();  // tile staged
+    // ---- pass 1 ----
+    if (act) {
+      C d = mk<C>(0, 0), al = mk<C>(1, 0), xl = mk<C>(0, 0), be = mk<C>(0, 0);
+      for (int j = s0; j <= e0; ++j) {
+        const C inv = pivot(j);
+        d = cmul(csub(tile[j * kMW + mi], cmul(b, d)), inv);
+        xl = cadd(xl, cmul(al, d));
+        const C an = cmul(al, cmul(nb, inv));
+        be = cadd(be, cmul(al, an));
+        al = an;
+      }
+      sums[(0 * nc + c) * kMW + mi] = d;
+      sums[(1 * nc + c) * kMW + mi] = xl;
+      sums[(2 * nc + c) * kMW + mi] = al;
+      sums[(3 * nc + c) * kMW + mi] = be;
+    }
+    __syncthreads();
+    // ---- scan over the chunks of each line: one warp per line ----
+    {
+      const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+      const int g = (nc + 31) / 32;  // chunks per lane
+      for (int mm = warp; mm < kMW; mm += nw) {
+        const int c0 = lane * g, c1 = min(c0 + g, nc);
+        // forward: D_c = dloc_c + alpha_c D_{c-1}; the lane's group as one map
+        C P = mk<C>(1, 0), Q = mk<C>(0, 0);
+        for (int cc = c0; cc < c1; ++cc) {
+          const C alc = sums[(2 * nc + cc) * kMW + mm];
+          Q = cadd(cmul(alc, Q), sums[(0 * nc + cc) * kMW + mm]);
+          P = cmul(alc, P);
+        }
+        for (int off = 1; off < 32; off <<= 1) {
+          const C Pu = shfl_up_c(P, off), Qu = shfl_up_c(Q, off);
+          if (lane >= off) affine_compose(P, Q, Pu, Qu);
+        }
+        C Din = shfl_up_c(Q, 1);  // D before the lane's group (inclusive scan shifted)
+        if (lane == 0) Din = mk<C>(0, 0);
+        // carry-in d_{s-1} of each chunk; keep E_c = xloc_c + beta_c D_{c-1}
+        for (int cc = c0; cc < c1; ++cc) {
+          const C dl = sums[(0 * nc + cc) * kMW + mm], alc = sums[(2 * nc + cc) * kMW + mm];
+          const C E = cadd(sums[(1 * nc + cc) * kMW + mm], cmul(sums[(3 * nc + cc) * kMW + mm], Din));
+          sums[(0 * nc + cc) * kMW + mm] = Din;
+          sums[(1 * nc + cc) * kMW + mm] = E;
+          Din = cadd(dl, cmul(alc, Din));
+        }
+        // backward: X_c = E_c + alpha_c X_{c+1}; the lane's group as one map of X after the group
+        P = mk<C>(1, 0);
+        Q = mk<C>(0, 0);
+        for (int cc = c1 - 1; cc >= c0; --cc) {
+          const C alc = sums[(2 * nc + cc) * kMW + mm];
+          Q = cadd(cmul(alc, Q), sums[(1 * nc + cc) * kMW + mm]);
+          P = cmul(alc, P);
+        }
+        for (int off = 1; off < 32; off <<= 1) {
+          const C Pd = shfl_down(P, off), Qd = shfl_down(Q, off);
+          if (lane + off < 32) affine_compose(P, Q, Pd, Qd);
+        }
+        C Xin = shfl_down(Q, 1);  // X just after the lane's group
+        if (lane == 31) Xin = mk<C>(0, 0);
+        for (int cc = c1 - 1; cc >= c0; --cc) {
+          const C alc = sums[(2 * nc + cc) * kMW + mm];
+          const C E = sums[(1 * nc + cc) * kMW + mm];
+          sums[(1 * nc + cc) * kMW + mm] = Xin;  // carry-in x_{e+1} of chunk cc
+          Xin = cadd(E, cmul(alc, Xin));
+        }
+      }
+    }
+    __syncthreads();
+    // ---- pass 2 ----
+    if (act) {
+      C d = sums[(0 * nc + c) * kMW + mi];
+      for (int j = s0; j <= e0; ++j) {
+        d = cmul(csub(tile[j * kMW + mi], cmul(b, d)), pivot(j));
+        tile[j * kMW + mi] = d;
+      }
+      C x = sums[(1 * nc + c) * kMW + mi];
+      for (int j = e0; j >= s0; --j) {
+        x = csub(tile[j * kMW + mi], cmul(cmul(b, pivot(j)), x));
+        if (ISTEP == 3) y3[((int64_t)j * ny + l) * nz + m] = x;
+        else tile[j * kMW + mi] = x;
+      }
+    }
+    if (ISTEP != 3) {
+      __syncthreads();
+      // this tile's share of the inner boundary rows, inner modes summed in a
+      // fixed (row-rotated, bank-conflict-free) order
+      for (int x = tid; x < nx; x += nthr) {
+        C s1 = mk<C>(0, 0), sn = mk<C>(0, 0);
+#pragma unroll
+        for (int k = 0; k < kMW; ++k) {
+          const int mm = (k + x) & (kMW - 1);
+          const C v = tile[x * kMW + mm];
+          s1 = cadd(s1, cmul(v, mw[2 * kMW + mm]));
+          sn = cadd(sn, cmul(v, mw[3 * kMW + mm]));
+        }
+        facc[x] = cadd(facc[x], s1);
+        facc[nx + x] = cadd(facc[nx + x], sn);
+      }
+    }
+  }
+  if (ISTEP != 3) {
+    __syncthreads();
+    C* out = part + ((int64_t)l * ia.nparts + blockIdx.x) * 2 * nx;
+    for (int e = tid; e < 2 * nx; e += nthr) out[e] = facc[e];
+  }
+}
+
+// Per outer mode l: the inner boundary rows from the CTAs' partials (fixed
+// order), scaled as in eq. 2dBs1 (Step 1: 1/nz and e^{t(nz-1)}/nz) or eq.
+// step2-3 (Step 2: 1), kept in vw[l] (v_in after Step 1, w_in after Step 2),
+// and the inner C_bb of eq. Cbb applied (Step 1: to v_in; Step 2: to
+// v_in + w_in) for the next inner Step's right-hand side.
+template <typename T, int OSTEP, int ISTEP>
+__global__ void __launch_bounds__(256) k_inner_reduce(InnerArgs ia, const typename cpx<T>::type* __restrict__ part,
+                                                      typename cpx<T>::type* __restrict__ vw,
+                                                      typename cpx<T>::type* __restrict__ cin,
+                                                      const int* __restrict__ skip) {
+  using C = typename cpx<T>::type;
+  if (skip && *skip) return;
+  const Plane3DArgs& a = ia.a;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nx = (int)a.nx;
+  const int64_t l = blockIdx.x;
+  C* sv = reinterpret_cast<C*>(smem_raw);  // [2][nx] v_in
+  C* sw = sv + 2 * nx;                     // [2][nx] w_in
+  C* vwl = vw + l * 4 * nx;                // [v_in 2 nx][w_in 2 nx]
+  const C* pp = part + l * (int64_t)ia.nparts * 2 * nx;
+  const C sc1 = ISTEP == 1 ? mk<C>(1.0 / (double)a.nz, 0) : mk<C>(1, 0);
+  const C scn = ISTEP == 1 ? mk<C>(a.en_i[0] / (double)a.nz, a.en_i[1] / (double)a.nz) : mk<C>(1, 0);
+  for (int e = threadIdx.x; e < 2 * nx; e += blockDim.x) {
+    C acc = mk<C>(0, 0);
+    for (int q = 0; q < ia.nparts; ++q) acc = cadd(acc, pp[(int64_t)q * 2 * nx + e]);
+    acc = cmul(acc, e < nx ? sc1 : scn);
+    if (ISTEP == 1) {
+      sv[e] = acc;
+      vwl[e] = acc;
+    } else {
+      sv[e] = vwl[e];
+      sw[e] = acc;
+      vwl[2 * nx + e] = acc;
+    }
+  }
+  __syncthreads();
+  const double lo_re = OSTEP == 2 ? a.lamAo[2 * l] : a.lamBo[2 * l];
+  const double lo_im = OSTEP == 2 ? a.lamAo[2 * l + 1] : a.lamBo[2 * l + 1];
+  const double pre = a.omega * a.omega - lo_re, pim = -lo_im;
+  plane_cbb(sv, ISTEP == 2 ? (const C*)sw : (const C*)nullptr, cin + l * 2 * nx, nx, a.hx, a.hz, a.wx, a.wz, pre, pim,
+            mk<C>(a.g_i[0], a.g_i[1]), mk<C>(a.ginv_i[0], a.ginv_i[1]));
+}
+
 template <typename T>
 cudaError_t launch_plane(int ostep, const Plan3D& p, const void* gfaces, const int* skip, cudaStream_t st) {
   using C = typename cpx<T>::type;
@@ -495,6 +858,56 @@ cudaError_t launch_plane(int ostep, const Plan3D& p, const void* gfaces, const i
   else if (ostep == 2) tab ? run(k_plane3d<T, 2, true>) : run(k_plane3d<T, 2, false>);
   else tab ? run(k_plane3d<T, 3, true>) : run(k_plane3d<T, 3, false>);
   return cudaGetLastError();
+}
+
+// Inner Steps 1-3 of every outer mode by the tiled sweeps: three k_inner3d
+// launches with the per-plane reductions between them; y3 goes to p.dbuf.
+template <typename T, int OSTEP>
+cudaError_t launch_inner_t(const Plan3D& p, const void* gfaces, const int* skip, cudaStream_t st, Profiler* prof) {
+  using C = typename cpx<T>::type;
+  InnerArgs ia{make_args(p), p.inner_ch, p.inner_nc, p.inner_nmb, p.inner_nparts};
+  const int nx = (int)p.n[0];
+  const int nthr = kMW * ((p.inner_nc + 1) & ~1);
+  const size_t smem = ((size_t)nx * kMW + 4 * (size_t)p.inner_nc * kMW + 2 * (size_t)nx + 4 * kMW) * sizeof(C);
+  const dim3 grid((unsigned)p.inner_nparts, (unsigned)p.n[1]);
+  const int oA = OSTEP == 2 ? 1 : 0;
+  const C* fh = (const C*)p.fhat;
+  const C* gf = (const C*)gfaces;
+  C* part = (C*)p.ipart;
+  C* vw = (C*)p.ivw;
+  C* cin = (C*)p.icin;
+  const size_t rsm = 4 * (size_t)nx * sizeof(C);
+  static const char* const names[3][3] = {{"inner_o1_i1", "inner_o1_i2", "inner_o1_i3"},
+                                          {"inner_o2_i1", "inner_o2_i2", "inner_o2_i3"},
+                                          {"inner_o3_i1", "inner_o3_i2", "inner_o3_i3"}};
+  cudaError_t e;
+  auto sweep = [&](auto kern, int istep, int innerA) -> cudaError_t {
+    const int t = 2 * oA + innerA;
+    ProfScope ps(prof, names[OSTEP - 1][istep - 1], st);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, nthr, smem, st>>>(ia, fh, gf, cin, (const C*)p.tab[t], (const C*)p.lend[t], p.lenL[t], part,
+                                   (C*)p.dbuf, skip);
+    return cudaGetLastError();
+  };
+  auto reduce = [&](auto kern) -> cudaError_t {
+    ProfScope ps(prof, "inner_reduce", st);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    kern<<<(unsigned)p.n[1], 256, rsm, st>>>(ia, part, vw, cin, skip);
+    return cudaGetLastError();
+  };
+  if ((e = sweep(k_inner3d<T, OSTEP, 1>, 1, 0)) != cudaSuccess) return e;
+  if ((e = reduce(k_inner_reduce<T, OSTEP, 1>)) != cudaSuccess) return e;
+  if ((e = sweep(k_inner3d<T, OSTEP, 2>, 2, 1)) != cudaSuccess) return e;
+  if ((e = reduce(k_inner_reduce<T, OSTEP, 2>)) != cudaSuccess) return e;
+  return sweep(k_inner3d<T, OSTEP, 3>, 3, 0);
+}
+
+template <typename T>
+cudaError_t launch_inner(int ostep, const Plan3D& p, const void* gfaces, const int* skip, cudaStream_t st,
+                         Profiler* prof) {
+  if (ostep == 1) return launch_inner_t<T, 1>(p, gfaces, skip, st, prof);
+  if (ostep == 2) return launch_inner_t<T, 2>(p, gfaces, skip, st, prof);
+  return launch_inner_t<T, 3>(p, gfaces, skip, st, prof);
 }
 
 template <typename T>
@@ -555,21 +968,24 @@ cudaError_t solve3d_t(Plan3D& p, const void* in, int in_is_double, void* out, in
                                   skip, st));
   if (dbg_fhat) CK(cudaMemcpyAsync(dbg_fhat, p.fhat, nx * ny * nz * sizeof(C), cudaMemcpyDeviceToDevice, st));
   // outer Step 1
-  PK("plane3d_step1", launch_plane<T>(1, p, nullptr, skip, st));
+  if (p.inner_nmb) CK(launch_inner<T>(1, p, nullptr, skip, st, prof));
+  else PK("plane3d_step1", launch_plane<T>(1, p, nullptr, skip, st));
   PK("reduce_outer", launch_reduce_outer<T>(1, p, Vh, skip, st));
   CK(launch_dft_rows(prec, Vh, f64, v, cmode, 2 * nx, p.axi->dft, twi, +1, 1.0 / (double)nz, 0.0, nullptr, sco_i, skip, st));
   if (dbg_v) CK(cudaMemcpyAsync(dbg_v, v, 2 * F * sizeof(C), cudaMemcpyDeviceToDevice, st));
   CK(launch_outer_cbb<T>(p, v, nullptr, c, skip, st));
   CK(launch_dft_rows(prec, c, f64, ch, cmode, 2 * nx, p.axi->dft, twi, -1, 1.0, 0.0, sci_i, nullptr, skip, st));
   // outer Step 2
-  PK("plane3d_step2", launch_plane<T>(2, p, ch, skip, st));
+  if (p.inner_nmb) CK(launch_inner<T>(2, p, ch, skip, st, prof));
+  else PK("plane3d_step2", launch_plane<T>(2, p, ch, skip, st));
   PK("reduce_outer", launch_reduce_outer<T>(2, p, Vh, skip, st));
   CK(launch_dft_rows(prec, Vh, f64, w, cmode, 2 * nx, p.axi->dft, twi, +1, 1.0 / (double)nz, 0.0, nullptr, sco_i, skip, st));
   if (dbg_w) CK(cudaMemcpyAsync(dbg_w, w, 2 * F * sizeof(C), cudaMemcpyDeviceToDevice, st));
   CK(launch_outer_cbb<T>(p, v, w, c, skip, st));
   CK(launch_dft_rows(prec, c, f64, ch, cmode, 2 * nx, p.axi->dft, twi, -1, 1.0, 0.0, sci_i, nullptr, skip, st));
   // outer Step 3, then the inverse 2D DFT
-  PK("plane3d_step3", launch_plane<T>(3, p, ch, skip, st));
+  if (p.inner_nmb) CK(launch_inner<T>(3, p, ch, skip, st, prof));
+  else PK("plane3d_step3", launch_plane<T>(3, p, ch, skip, st));
   PK("dft_y_inv", launch_dft_cols(prec, p.dbuf, f64, p.dbuf, cmode, nx, nz, p.axo->dft, two, +1, 1.0 / (double)ny, 0.0,
                                   nullptr, sco_o, skip, st));
   PK("dft_z_inv", launch_dft_rows(prec, p.dbuf, f64, out, out_mode, nx * ny, p.axi->dft, twi, +1, 1.0 / (double)nz,
@@ -581,12 +997,13 @@ cudaError_t solve3d_t(Plan3D& p, const void* in, int in_is_double, void* out, in
 
 }  // namespace
 
-cudaError_t plan3d_init(Plan3D& p, int prec, const int64_t* n, const double* h, double omega, const AxisData& axo,
-                        const AxisData& axi, size_t* bytes) {
+cudaError_t plan3d_init(Plan3D& p, int prec, const int64_t* n, const double* h, double omega, const double* wc,
+                        const AxisData& axo, const AxisData& axi, size_t* bytes) {
   p.prec = prec;
   for (int k = 0; k < 3; ++k) {
     p.n[k] = n[k];
     p.h[k] = h[k];
+    p.wc[k] = wc[k];
   }
   p.omega = omega;
   p.axo = &axo;
@@ -598,25 +1015,67 @@ cudaError_t plan3d_init(Plan3D& p, int prec, const int64_t* n, const double* h, 
   void** bufs[4] = {&p.fhat, &p.cbuf, &p.dbuf, &p.faces};
   size_t sizes[4] = {N * cb, N * cb, N * cb, 10 * F * cb};
   for (int i = 0; i < 4; ++i) {
-    if ((e = cudaMalloc(bufs[i], sizes[i])) != cudaSuccess) {
+    if ((e = dmalloc((void**)bufs[i], sizes[i])) != cudaSuccess) {
       cudaGetLastError();
       return e;
     }
     *bytes += sizes[i];
   }
-  // per-plan pivot tables of the four inner line types; without room for
-  // them the kernels recompute the pivots
+  // per-plan pivot tables of the four inner line types (with the per-line
+  // settling data of the tiled sweeps); without room for them the kernels
+  // recompute the pivots
+  const int64_t lines = n[1] * n[2];
+  const size_t per_type = N * cb + lines * (2 * cb + sizeof(int));
   for (int t = 0; t < 4; ++t) {
-    if (cudaMalloc(&p.tab[t], N * cb) != cudaSuccess) {
+    if (dmalloc((void**)&p.tab[t], N * cb) != cudaSuccess || dmalloc((void**)&p.lend[t], lines * 2 * cb) != cudaSuccess ||
+        dmalloc((void**)&p.lenL[t], lines * sizeof(int)) != cudaSuccess) {
       cudaGetLastError();
       for (int u = 0; u < 4; ++u) {
-        cudaFree(p.tab[u]);
-        p.tab[u] = nullptr;
+        dfree(p.tab[u]);
+        dfree(p.lend[u]);
+        dfree(p.lenL[u]);
+        p.tab[u] = p.lend[u] = nullptr;
+        p.lenL[u] = nullptr;
       }
-      *bytes -= (size_t)t * N * cb;
+      *bytes -= (size_t)t * per_type;
       break;
     }
-    *bytes += N * cb;
+    *bytes += per_type;
+  }
+  // tiled inner sweeps: when the tables exist and a tile of kMW lines fits
+  // the shared memory of one CTA
+  int dev = 0, smem_max = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int max_nc = (prec == kPrecF64 ? 512 : 1024) / kMW;
+  int ch = 16, nc = (int)((n[0] + 15) / 16);
+  if (nc > max_nc) {
+    ch = (int)((n[0] + max_nc - 1) / max_nc);
+    nc = (int)((n[0] + ch - 1) / ch);
+  }
+  const size_t ismem = ((size_t)n[0] * kMW + 4 * (size_t)nc * kMW + 2 * (size_t)n[0] + 4 * kMW) * cb;
+  if (p.tab[0] && ismem <= (size_t)smem_max) {
+    const int64_t tiles = (n[2] + kMW - 1) / kMW;
+    const int64_t total = tiles * n[1];
+    int nmb = (int)std::max<int64_t>(1, std::min<int64_t>(4, total / (152 * 8)));
+    nmb = (int)std::min<int64_t>(nmb, tiles);
+    const int nparts = (int)((tiles + nmb - 1) / nmb);
+    const size_t sz[3] = {(size_t)n[1] * nparts * 2 * n[0] * cb, (size_t)n[1] * 4 * n[0] * cb,
+                          (size_t)n[1] * 2 * n[0] * cb};
+    void** dst[3] = {&p.ipart, &p.ivw, &p.icin};
+    bool ok = true;
+    for (int i = 0; i < 3 && ok; ++i) {
+      ok = dmalloc((void**)dst[i], sz[i]) == cudaSuccess;
+      if (ok) *bytes += sz[i];
+    }
+    if (ok) {
+      p.inner_ch = ch;
+      p.inner_nc = nc;
+      p.inner_nmb = nmb;
+      p.inner_nparts = nparts;
+    } else {
+      cudaGetLastError();
+    }
   }
   p.ready = true;
   return plan3d_tables(p);
@@ -629,9 +1088,9 @@ cudaError_t plan3d_tables(Plan3D& p) {
   const unsigned grid = (unsigned)((p.n[1] * p.n[2] + bs - 1) / bs);
   for (int t = 0; t < 4; ++t) {
     if (p.prec == kPrecF64)
-      k_plane_tables<double><<<grid, bs>>>((double2*)p.tab[t], a, t >> 1, t & 1);
+      k_plane_tables<double><<<grid, bs>>>((double2*)p.tab[t], (double2*)p.lend[t], p.lenL[t], a, t >> 1, t & 1);
     else
-      k_plane_tables<float><<<grid, bs>>>((float2*)p.tab[t], a, t >> 1, t & 1);
+      k_plane_tables<float><<<grid, bs>>>((float2*)p.tab[t], (float2*)p.lend[t], p.lenL[t], a, t >> 1, t & 1);
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -639,13 +1098,20 @@ cudaError_t plan3d_tables(Plan3D& p) {
 }
 
 void free_plan3d(Plan3D& p) {
-  for (int t = 0; t < 4; ++t) cudaFree(p.tab[t]);
-  cudaFree(p.fhat);
-  cudaFree(p.cbuf);
-  cudaFree(p.dbuf);
-  cudaFree(p.ybuf);
-  cudaFree(p.faces);
-  cudaFree(p.partial);
+  for (int t = 0; t < 4; ++t) {
+    dfree(p.tab[t]);
+    dfree(p.lend[t]);
+    dfree(p.lenL[t]);
+  }
+  dfree(p.ipart);
+  dfree(p.ivw);
+  dfree(p.icin);
+  dfree(p.fhat);
+  dfree(p.cbuf);
+  dfree(p.dbuf);
+  dfree(p.ybuf);
+  dfree(p.faces);
+  dfree(p.partial);
   p = Plan3D{};
 }
 

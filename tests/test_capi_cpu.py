@@ -23,7 +23,7 @@ def helm():
 
 def test_every_header_symbol_is_exported(helm):
     hdr = open(os.path.join(ROOT, "include", "helm.h")).read()
-    names = set(re.findall(r"^\s*(?:int|const char\*)\s+(helm_\w+)\s*\(", hdr, flags=re.M))
+    names = set(re.findall(r"^\s*(?:int|int64_t|const char\*)\s+(helm_\w+)\s*\(", hdr, flags=re.M))
     assert len(names) >= 12
     for n in names:
         assert hasattr(helm.lib, n), n
@@ -82,7 +82,26 @@ def test_abc_eigen_rejects_bad_input(helm):
     with pytest.raises(helm.HelmError):
         helm.helm_abc_eigen(1, 0.1, 1.0)
     with pytest.raises(helm.HelmError):
-        helm.helm_abc_eigen(10, 0.1, 0.0)
+        helm.helm_abc_eigen(10, 0.1, -1.0)
+    with pytest.raises(helm.HelmError):
+        helm.helm_abc_eigen(10, 0.0, 1.0)
+
+
+@pytest.mark.parametrize("n,h", [(9, 0.125), (64, 1 / 63), (301, 0.002)])
+def test_neumann_eigen_matches_dense_oracle(helm, n, h):
+    """w = 0: the Neumann pencil of a Gamma_N axis (corner 1 of eq. matrixK),
+    against the oracle's dense generalized eigen-decomposition."""
+    from oracle import solvers
+
+    lam, sig, par = helm.helm_abc_eigen(n, h, 0.0)
+    lo, V = solvers.abc_pencil_eig(n, h, 5.0, "neumann")
+    scale = np.abs(lo).max()
+    assert np.abs(lam.imag).max() == 0 and np.abs(sig.imag).max() == 0
+    for i, l in enumerate(lam):
+        j = int(np.argmin(np.abs(lo - l)))
+        assert abs(lo[j] - l) <= 1e-9 * scale
+        assert abs(V[0, j] ** 2 - sig[i]) <= 1e-9 * abs(sig[i])
+        assert abs(V[-1, j] - par[i] * V[0, j]) <= 1e-7 * abs(V[0, j])
 
 
 def test_server_rejects_bad_arguments_before_touching_the_device(helm):

@@ -320,3 +320,55 @@ def test_damped_auxiliary_step_identities():
     iy = np.unravel_index(np.arange(A.shape[0]), shape)[1]
     onb = (iy == 0) | (iy == shape[1] - 1)
     assert np.all(onb[D.row[keep]]) and np.all(onb[D.col[keep]])
+
+
+# --------------------------- mixed absorbing / Neumann axes -----------------
+
+MIXED = [((6, 5), (0.2, 0.3), ("neumann", "abc")), ((6, 5), (0.2, 0.3), ("abc", "neumann")),
+         ((4, 5, 3), (0.5, 0.25, 0.4), ("abc", "neumann", "abc")),
+         ((4, 5, 3), (0.5, 0.25, 0.4), ("neumann", "neumann", "abc"))]
+
+
+@pytest.mark.parametrize("shape,h,bc", MIXED)
+def test_mixed_boundaries_assembly_and_operators(shape, h, bc):
+    """Gamma_N on some axes (Section 2, k11 = 1 in eq. matrixK): the element
+    assembly (boundary mass only on absorbing faces) equals the Kronecker form
+    with per-axis K corners, and apply_A / residual_dd (numpy and C) apply that
+    same matrix."""
+    om = 3.7
+    A1 = fem.assemble(shape, h, om, bc)
+    A2 = fem.kron_operator(shape, h, om, bc=bc)
+    assert abs(A1 - A2).max() < 1e-12 * abs(A2).max()
+    # a Neumann axis has real corners: the boundary term is only on absorbing faces
+    assert abs(A1 - fem.assemble(shape, h, om, "abc")).max() > 0.1
+    u = random_rhs(shape, 5)
+    np.testing.assert_allclose(fem.apply_A(u, h, om, bc).ravel(), A1 @ u.ravel(), rtol=0, atol=1e-12)
+    f = fem.apply_A(u, h, om, bc) + 1e-9 * random_rhs(shape, 6)
+    r1 = fem.residual_dd(f, u, h, om, bc)
+    np.testing.assert_allclose(r1.ravel(), f.ravel() - A1 @ u.ravel(), rtol=0, atol=1e-13)
+    assert np.array_equal(r1, fem.residual_dd_c(f, u, h, om, bc))
+
+
+@pytest.mark.parametrize("shape,h,bc", MIXED)
+def test_mixed_boundaries_solvers_agree_with_dense_lu(shape, h, bc):
+    om = 5.1
+    f = random_rhs(shape, 8)
+    u0 = solvers.solve_dense(f, h, om, bc)
+    n0 = np.linalg.norm(u0)
+    assert np.linalg.norm(solvers.solve_banded_lu(f, h, om, bc) - u0) / n0 < 1e-12
+    for t in range(len(shape)):
+        u3 = solvers.TensorSolver(shape, h, om, tri_axis=t, bc=bc).solve(f)
+        assert np.linalg.norm(u3 - u0) / n0 < 1e-11
+    u4, hist = solvers.oracle_solve(f, h, om, method="tensor", bc=bc)
+    assert np.linalg.norm(u4 - u0) / n0 < 1e-12 and hist[-1] < 1e-14
+
+
+def test_neumann_pencil_eigen_is_the_cosine_basis():
+    """abc_pencil_eig of a Neumann axis: eigenvalues of the closed form and
+    V^T M V = I with V[0, k]^2 = V[n-1, k]^2 (cosines, parity (-1)^k)."""
+    n, h = 12, 0.09
+    lam, V = solvers.abc_pencil_eig(n, h, 4.0, "neumann")
+    np.testing.assert_allclose(np.sort(lam.real), np.sort(fem.eig_neumann(n, h)), rtol=1e-10, atol=1e-8)
+    M = fem.M1d(n, h)
+    np.testing.assert_allclose(V.T @ M @ V, np.eye(n), atol=1e-10)
+    np.testing.assert_allclose(V[0] ** 2, V[-1] ** 2, rtol=1e-8, atol=1e-12)
