@@ -360,6 +360,14 @@ def run_gb300(args):
         if kind is not None:
             helm.helm_set_residual(plan.handle, kind)
             helm.helm_set_refinement(plan.handle, REFINE_TOL, 10)
+        plan.variant = None
+        if len(p.shape) == 3 and not args.no_autotune:
+            # the exhaustive autotuner: every variant of the tiled inner sweeps
+            # timed on this plan, the fastest kept (plan time, not timed)
+            from paper_1809_03808_gb300 import tuning
+
+            best, _ = tuning.autotune(plan, reps=2)
+            plan.variant = list(best)
         return plan
 
     def kernels_of(p, path, pr):
@@ -387,7 +395,8 @@ def run_gb300(args):
             if err is not None and err > 1e-10:
                 raise RuntimeError(f"{wl} {path}: sampled error {err:.3e} above the 1e-10 bar")
         return plan, u, {"ms": ms / args.steps, "clocks": clocks, "err": err, "prof": prof, "refine": refine,
-                         "plan_s": plan_s, "aux": aux, "device_bytes": int(info.device_bytes)}
+                         "plan_s": plan_s, "aux": aux, "device_bytes": int(info.device_bytes),
+                         "variant": plan.variant}
 
     peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
     wl = args.workload
@@ -473,7 +482,8 @@ def run_gb300(args):
         + (" x Gaussian bump)" if p.rhs == "gaussian_bump" else ")"),
         "config": {"workload": p.name, "nodes": list(p.shape), "omega": sig(p.omega, 8),
                    "precision": PATH_PRECISION[args.path], "rhs_per_step": 1,
-                   "l2": f"inputs larger than L2 ({N * 16 / 1e6:.0f} MB each)", "parallelism": f"replicas x{world}"},
+                   "l2": f"inputs larger than L2 ({N * 16 / 1e6:.0f} MB each)", "parallelism": f"replicas x{world}",
+                   "variant": main["variant"]},
         "gpu_launches": gpu_launches, "rel_err_sampled": sig(main["err"], 3), "refinement": main["refine"],
         "roofline": roof, "clocks": main["clocks"], "e2e": e2e, "cpu_baseline": cpu,
         "kernels_ms_per_step": {k: sig(v[1] / PROFILE_SOLVES, 3) for k, v in prof.items()},
@@ -705,6 +715,7 @@ def main():
     ap.add_argument("--shape", default="", help="nx,ny: same spacing and wave number on a smaller grid "
                     "(profiling cases; not a benchmark line)")
     ap.add_argument("--minimal", action="store_true", help="timed solves only (no e2e, variants, CPU baseline)")
+    ap.add_argument("--no-autotune", action="store_true", help="3D: keep the default kernel variant")
     ap.add_argument("--batch-count", type=int, default=512, help="problems of --workload batch2d")
     ap.add_argument("--workload", default="3d", choices=["2d_large", "3d", "batch2d", "serve3d"],
                     help="3d: the 512^3 workload (the bench line); 2d_large: the 8192 x 4096 workload; "

@@ -107,6 +107,8 @@ typedef struct helm_info {
   double aux_trial_residual; /* plan-time trial residual of the chosen auxiliary
                                 (-1 if set by helm_set_auxiliary) */
   int32_t axis_bc[3];      /* helm_bc of each axis (HELM_BC_ABC beyond dim) */
+  int32_t fp64_lines;      /* inner lines solved in FP64 by precision routing
+                              (3D complex64 plans; see helm_set_precision_routing) */
 } helm_info;
 
 /* --- Plan (the paper's "Initialization", Section 6) -----------------------
@@ -157,6 +159,47 @@ int helm_plan_3d_bc(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double
  * between solves, not while a solve is in flight on another stream. */
 int helm_set_auxiliary(helm_plan_t p, double rho, int phase_quarters);
 
+/* Precision routing of 3D complex64 plans: the inner tridiagonal lines
+ * (Section 5.1.2's per-mode solves along x) whose matrix
+ * K_x + (Lam_l + Lam_m - w^2) M_x is close to singular are solved with FP64
+ * arithmetic (FP64 pivots, FP64 substitutions) by a separate kernel; all
+ * other lines stay in complex64.  A line is routed when some eigenvalue
+ * Lam^A_x,k of its own axis's pencil makes |Lam^A_x,k + Lam_l + Lam_m - w^2|
+ * < tau w^2.  Off by default (tau = 0): the complex64 solve's error does sit
+ * in those lines (on a 256^3 grid of the 512^3 workload's spacing and wave
+ * number the closest 1 % of the lines carry 96 % of it), but it is the
+ * complex64 rounding of their inputs, amplified by their conditioning, which
+ * FP64 sweeps do not remove (measured: -0.6 %).  helm_info.fp64_lines counts
+ * the routed lines (all line types).  Returns HELM_EUNSUPPORTED for 2D or
+ * complex128 plans, HELM_EINVAL for tau outside [0, 1].  Call between
+ * solves. */
+int helm_set_precision_routing(helm_plan_t p, double tau);
+
+/* Kernel variants (the autotuner's choices; the paper fixes none of them).
+ * Every variant computes the same solution; they differ in speed by grid.
+ *   HELM_VARIANT_INNER_CHUNK  3D: rows per chunk of the tiled inner sweeps
+ *                             (4..64; default 16, more for lines beyond 1024
+ *                             rows).
+ *   HELM_VARIANT_INNER_TILES  3D: tiles of 16 inner modes per CTA (1..8;
+ *                             default 1..4 by grid size).
+ *   HELM_VARIANT_TRI2D        2D complex64: 0 = bulk-copy fed passes where
+ *                             the x1 length is even (default), 1 = register-
+ *                             tile passes.
+ * helm_set_variant returns HELM_EUNSUPPORTED for a knob the plan does not
+ * have, HELM_EINVAL for a value that does not fit.  Call between solves.
+ * helm_time_solve: device milliseconds of one solve of the plan's compute
+ * path (one complex64 or complex128 solve, no refinement), averaged over
+ * `reps` solves of a fixed pseudo-random load after one warm-up, timed with
+ * CUDA events on the plan's stream (allocates two vectors for the call). */
+enum helm_variant {
+  HELM_VARIANT_INNER_CHUNK = 0,
+  HELM_VARIANT_INNER_TILES = 1,
+  HELM_VARIANT_TRI2D = 2
+};
+int helm_set_variant(helm_plan_t p, int knob, int value);
+int helm_get_variant(helm_plan_t p, int knob, int* value);
+int helm_time_solve(helm_plan_t p, int reps, double* ms_per_solve);
+
 /* Stream on which helm_solve enqueues its kernels (a cudaStream_t passed as
  * void*; NULL = legacy default stream).  One plan serves one stream at a time. */
 int helm_set_stream(helm_plan_t p, void* cuda_stream);
@@ -193,6 +236,22 @@ int helm_set_graphs(helm_plan_t p, int enable);
  * nothing (all scratch belongs to the plan).  Convergence of refinement is
  * reported by helm_get_info. */
 int helm_solve(helm_plan_t p, const void* f, void* u);
+
+/* Many right-hand sides of one operator (the domain-decomposition sweeps of
+ * Section 1 reuse one operator for many loads): f and u hold nrhs vectors of
+ * N values each, one after another (the layout above for each); the byte
+ * ranges of all of f and all of u must be disjoint.  Right-hand side i is
+ * solved exactly as helm_solve(p, f_i, u_i) would solve it (same kernels on
+ * the same operator data, so the same bits), but up to k of them at once
+ * (helm_set_rhs_concurrency, default 4): the plan keeps k - 1 extra
+ * workspaces (its scratch: about 24-56 bytes per unknown each, sharing the
+ * eigen-data and pivot tables), made at the first call that needs them and
+ * kept until helm_destroy, and k streams forked from and joined back to the
+ * plan's stream.  Asynchronous like helm_solve.  helm_get_info then reports
+ * the right-hand side whose refinement ended worst.  Workspaces are rebuilt
+ * after any setting that changes the plan's solve. */
+int helm_solve_many(helm_plan_t p, int64_t nrhs, const void* f, void* u);
+int helm_set_rhs_concurrency(helm_plan_t p, int k);  /* 1 <= k <= 16 */
 
 /* Same solve with HOST pointers: copies f to the device, solves, copies u
  * back and synchronises the stream before returning (for callers without
@@ -317,10 +376,14 @@ int helm_solve_2d_static(int64_t nx, int64_t ny, double hx, double hy, double om
  * modes), 200 B (2D HELM_C128), 112 B (3D complex64) or 128 B (3D
  * HELM_C128).  A request whose plan is busy with another request waits while
  * later requests for other operators start (a plan serves one request at a
- * time).  Building a plan synchronises the device, so it waits for the work
- * in flight.  A request's right-hand sides are solved one after another on
- * its slot's stream.  Every solve is the plan's helm_solve: each result is
- * the same as the one helm_solve gives for that request alone.
+ * time).  Building a plan waits only for its own work (its kernels run on
+ * the legacy stream, its memory comes from the stream-ordered allocator), not
+ * for the requests in flight on the server's streams.  A request's
+ * right-hand sides go through helm_solve_many on its slot's stream (several
+ * at once on the plan's workspaces).  Server plans launch kernel by kernel,
+ * never capturing CUDA graphs, so other threads may synchronise the device
+ * at any time.  Every right-hand side is solved as the plan's helm_solve
+ * would solve it: each result is the same as for that request alone.
  *
  * f and u are DEVICE pointers of the server's device, nrhs * N complex
  * values each (complex64 for HELM_C64_RAW, complex128 otherwise; N = nx ny
@@ -414,6 +477,32 @@ int helm_server_destroy(helm_server_t s);
 int helm_debug_fail_alloc(int k);
 int64_t helm_debug_live_allocations(size_t* bytes);
 int helm_debug_wait_timeout(helm_plan_t p, int64_t tries);
+
+/* --- Learned cost model of the autotuner ---------------------------------
+ * The paper has no learned part (its direct solver is exact to rounding).
+ * The autotuner's cost model is a small multilayer perceptron, trained on the
+ * GPU by these kernels on measured solve times: x (n_in features) ->
+ * tanh(W1 x + b1) -> tanh(W2 h1 + b2) -> y = w3 . h2 + b3 (both hidden
+ * layers n_hidden wide); loss = mean squared error over the batch.
+ * Parameters (FP32, contiguous): W1 [n_h][n_in], b1 [n_h], W2 [n_h][n_h],
+ * b2 [n_h], w3 [n_h], b3 [1]; initialised from `seed` (uniform, scaled by
+ * 1/sqrt(fan-in); biases 0).  x: DEVICE [batch][n_in] floats; t, y: DEVICE
+ * [batch]; grad: DEVICE [num_params]; loss: DEVICE float (may be NULL).
+ * Every reduction over the batch runs in a fixed order: results are
+ * bit-reproducible.  helm_mlp_train runs `steps` full-batch Adam steps
+ * (beta 0.9, 0.999, eps 1e-8, learning rate lr) and writes the final loss to
+ * the HOST float *final_loss (may be NULL).  1 <= n_in, n_hidden <= 256.
+ * Calls run on the legacy default stream and synchronise it. */
+typedef struct helm_mlp* helm_mlp_t;
+int helm_mlp_create(helm_mlp_t* out, int n_in, int n_hidden, uint64_t seed);
+int helm_mlp_num_params(helm_mlp_t m);
+int helm_mlp_get_params(helm_mlp_t m, float* host, int n);
+int helm_mlp_set_params(helm_mlp_t m, const float* host, int n);
+int helm_mlp_forward(helm_mlp_t m, const float* x, int64_t batch, float* y);
+int helm_mlp_gradient(helm_mlp_t m, const float* x, const float* t, int64_t batch, float* grad, float* loss);
+int helm_mlp_train(helm_mlp_t m, const float* x, const float* t, int64_t batch, int steps, float lr,
+                   float* final_loss);
+int helm_mlp_destroy(helm_mlp_t m);
 
 /* --- Host-side plan helpers (no GPU needed) --------------------------------
  * Eigen-data of the 1D absorbing pencil K V = M V Lam (eq. EVP1a) with

@@ -25,6 +25,7 @@ lib = ctypes.CDLL(_LIB_PATH)
 HELM_C128, HELM_C64_REFINED, HELM_C64_RAW = 0, 1, 2
 HELM_RESID_FP64, HELM_RESID_FF = 0, 1
 HELM_BC_ABC, HELM_BC_NEUMANN = 0, 1
+HELM_VARIANT_INNER_CHUNK, HELM_VARIANT_INNER_TILES, HELM_VARIANT_TRI2D = 0, 1, 2
 HELM_OK, HELM_EINVAL, HELM_ENOMEM, HELM_ECUDA, HELM_ENOTCONV, HELM_ETIMEOUT, HELM_EUNSUPPORTED, HELM_ENUMERIC = \
     0, -1, -2, -3, -4, -5, -6, -7
 
@@ -38,7 +39,7 @@ class helm_info(ctypes.Structure):
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("n_dft_stages", ctypes.c_int32),
                 ("device_bytes", ctypes.c_size_t), ("residual_kind", ctypes.c_int32),
                 ("aux_q", ctypes.c_int32), ("aux_rho", ctypes.c_double), ("aux_trial_residual", ctypes.c_double),
-                ("axis_bc", ctypes.c_int32 * 3)]
+                ("axis_bc", ctypes.c_int32 * 3), ("fp64_lines", ctypes.c_int32)]
 
 
 class helm_profile_entry(ctypes.Structure):
@@ -73,6 +74,10 @@ _SIGS = {
     "helm_plan_2d_bc": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _dbl, _dbl, _dbl, _i32, ctypes.POINTER(_i32)]),
     "helm_plan_3d_bc": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _i64, _dbl, _dbl, _dbl, _dbl, _i32,
                                ctypes.POINTER(_i32)]),
+    "helm_set_precision_routing": (_i32, [_vp, _dbl]),
+    "helm_set_variant": (_i32, [_vp, _i32, _i32]),
+    "helm_get_variant": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
+    "helm_time_solve": (_i32, [_vp, _i32, ctypes.POINTER(_dbl)]),
     "helm_set_stream": (_i32, [_vp, _vp]),
     "helm_set_refinement": (_i32, [_vp, _dbl, _i32]),
     "helm_set_auxiliary": (_i32, [_vp, _dbl, _i32]),
@@ -80,6 +85,8 @@ _SIGS = {
     "helm_set_graphs": (_i32, [_vp, _i32]),
     "helm_solve": (_i32, [_vp, _vp, _vp]),
     "helm_solve_host": (_i32, [_vp, _vp, _vp]),
+    "helm_solve_many": (_i32, [_vp, _i64, _vp, _vp]),
+    "helm_set_rhs_concurrency": (_i32, [_vp, _i32]),
     "helm_solve_debug": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "helm_get_info": (_i32, [_vp, ctypes.POINTER(helm_info)]),
     "helm_destroy": (_i32, [_vp]),
@@ -101,6 +108,14 @@ _SIGS = {
     "helm_server_drain": (_i32, [_vp, _dbl]),
     "helm_server_get_stats": (_i32, [_vp, ctypes.POINTER(helm_server_stats)]),
     "helm_server_destroy": (_i32, [_vp]),
+    "helm_mlp_create": (_i32, [ctypes.POINTER(_vp), _i32, _i32, ctypes.c_uint64]),
+    "helm_mlp_num_params": (_i32, [_vp]),
+    "helm_mlp_get_params": (_i32, [_vp, _vp, _i32]),
+    "helm_mlp_set_params": (_i32, [_vp, _vp, _i32]),
+    "helm_mlp_forward": (_i32, [_vp, _vp, _i64, _vp]),
+    "helm_mlp_gradient": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp]),
+    "helm_mlp_train": (_i32, [_vp, _vp, _vp, _i64, _i32, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]),
+    "helm_mlp_destroy": (_i32, [_vp]),
     "helm_debug_fail_alloc": (_i32, [_i32]),
     "helm_debug_live_allocations": (_i64, [ctypes.POINTER(ctypes.c_size_t)]),
     "helm_debug_wait_timeout": (_i32, [_vp, _i64]),
@@ -168,6 +183,26 @@ def helm_plan_3d_bc(nx, ny, nz, hx, hy, hz, omega, dtype, axis_bc):
     return h
 
 
+def helm_set_precision_routing(plan, tau):
+    _check(lib.helm_set_precision_routing(plan, float(tau)), "helm_set_precision_routing", plan)
+
+
+def helm_set_variant(plan, knob, value):
+    _check(lib.helm_set_variant(plan, int(knob), int(value)), "helm_set_variant", plan)
+
+
+def helm_get_variant(plan, knob):
+    v = _i32(0)
+    _check(lib.helm_get_variant(plan, int(knob), ctypes.byref(v)), "helm_get_variant", plan)
+    return int(v.value)
+
+
+def helm_time_solve(plan, reps=3):
+    ms = _dbl(0.0)
+    _check(lib.helm_time_solve(plan, int(reps), ctypes.byref(ms)), "helm_time_solve", plan)
+    return float(ms.value)
+
+
 def helm_set_stream(plan, stream):
     _check(lib.helm_set_stream(plan, _vp(int(stream) if stream is not None else 0)), "helm_set_stream", plan)
 
@@ -190,6 +225,14 @@ def helm_set_graphs(plan, enable):
 
 def helm_solve(plan, f, u):
     _check(lib.helm_solve(plan, _ptr(f), _ptr(u)), "helm_solve", plan)
+
+
+def helm_solve_many(plan, nrhs, f, u):
+    _check(lib.helm_solve_many(plan, int(nrhs), _ptr(f), _ptr(u)), "helm_solve_many", plan)
+
+
+def helm_set_rhs_concurrency(plan, k):
+    _check(lib.helm_set_rhs_concurrency(plan, int(k)), "helm_set_rhs_concurrency", plan)
 
 
 def helm_solve_host(plan, f, u):

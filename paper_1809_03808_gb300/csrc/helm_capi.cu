@@ -76,6 +76,19 @@ struct helm_plan {
   Plan3D p3;
   Profiler prof;
   std::string err;
+  // helm_solve_many: extra workspaces (plans sharing this plan's operator
+  // data: eigen-data, pivot tables, routing), one stream each, and the
+  // events that fork them from and join them to the plan's stream.  A
+  // workspace has `parent` set and owns only the allocations in `owned`.
+  helm_plan* parent = nullptr;
+  std::vector<void*> owned;
+  std::vector<helm_plan*> ws;
+  std::vector<cudaStream_t> ws_stream;
+  std::vector<cudaEvent_t> ws_done;
+  cudaEvent_t fork = nullptr;
+  int rhs_concurrency = 4;
+  int tri_regs = 0;  // 2D complex64: register-tile passes (variant HELM_VARIANT_TRI2D = 1)
+  int last_many = 0;  // workspaces used by the last helm_solve_many (0: none)
 };
 
 // A group of plans solved as one CUDA graph (helm_batch_*).
@@ -286,6 +299,7 @@ Solve2DArgs args2d(const helm_plan* p) {
   a.nchunks = (p->n[0] + a.ch - 1) / a.ch;
   a.wx = p->wc[0];
   a.wy = p->wc[1];
+  a.tri_regs = p->tri_regs;
   return a;
 }
 
@@ -567,7 +581,7 @@ int alloc_buffers_2d(helm_plan* p) {
       p->err.clear();
     }
   }
-  HELM_CK(cudaDeviceSynchronize());
+  HELM_CK(cudaStreamSynchronize(nullptr));  // plan-time kernels run on the legacy stream
   return HELM_OK;
 }
 
@@ -599,8 +613,34 @@ bool overlaps(const void* a, const void* b, size_t bytes) {
   return x < y + bytes && y < x + bytes;
 }
 
+// The plan's stream and its workspace streams have finished their work (the
+// tables they read may be rebuilt or freed after this).
+cudaError_t sync_plan_streams(helm_plan* p) {
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  for (cudaStream_t st : p->ws_stream)
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+void destroy_workspace(helm_plan* w) {
+  for (void* q : w->owned) dfree(q);
+  drop_refine_graph(w);
+  for (int k = 0; k < 2; ++k)
+    if (w->cap[k]) cudaStreamDestroy(w->cap[k]);
+  w->prof.destroy();
+  delete w;
+}
+
 void destroy_plan(helm_plan* p) {
   if (!p) return;
+  if (p->parent) {
+    destroy_workspace(p);
+    return;
+  }
+  for (helm_plan* w : p->ws) destroy_workspace(w);
+  for (cudaStream_t st : p->ws_stream) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : p->ws_done) cudaEventDestroy(ev);
+  if (p->fork) cudaEventDestroy(p->fork);
   free_axis(p->axo);
   free_axis(p->axi);
   dfree(p->fhat);
@@ -629,6 +669,100 @@ void destroy_plan(helm_plan* p) {
     if (p->cap[k]) cudaStreamDestroy(p->cap[k]);
   p->prof.destroy();
   delete p;
+}
+
+// A workspace for helm_solve_many: a plan that borrows p's operator data
+// (axis eigen-data, pivot and line tables, 3D settling and routing tables)
+// and owns fresh scratch of the same sizes.  Its solves run the same kernels
+// on the same operator data as p's, so each result is p's own result.
+helm_plan* make_workspace(helm_plan* p) {
+  helm_plan* w = new (std::nothrow) helm_plan();
+  if (!w) return nullptr;
+  w->parent = p;
+  w->dim = p->dim;
+  for (int k = 0; k < 3; ++k) {
+    w->n[k] = p->n[k];
+    w->h[k] = p->h[k];
+    w->bc[k] = p->bc[k];
+    w->wc[k] = p->wc[k];
+  }
+  w->omega = p->omega;
+  w->dtype = p->dtype;
+  w->prec = p->prec;
+  w->axo = p->axo;
+  w->axi = p->axi;
+  w->tol = p->tol;
+  w->max_iter = p->max_iter;
+  w->resid_kind = p->resid_kind;
+  w->use_graphs = p->use_graphs;
+  w->tri_regs = p->tri_regs;
+  w->version = p->version;
+  const int64_t N = p->n[0] * p->n[1] * p->n[2];
+  const size_t cb = cbytes(p->prec);
+  bool ok = true;
+  auto own = [&](void** q, size_t bytes) {
+    if (!ok) return;
+    if (dmalloc(q, bytes ? bytes : 16) != cudaSuccess) {
+      ok = false;
+      *q = nullptr;
+      return;
+    }
+    w->owned.push_back(*q);
+    w->bytes += bytes;
+  };
+  if (p->dim == 2) {
+    w->ustartB = p->ustartB;
+    w->ustartA = p->ustartA;
+    w->tabB = p->tabB;
+    w->tabA = p->tabA;
+    w->constB = p->constB;
+    w->constA = p->constA;
+    w->nwarps = p->nwarps;
+    w->face_len = p->face_len;
+    const Solve2DArgs a = args2d(p);
+    const size_t nrec = (size_t)a.nchunks * p->n[1];
+    own(&w->fhat, N * cb);
+    own(&w->dbuf, N * cb);
+    own(&w->partial, 2 * p->nwarps * p->n[0] * cb);
+    own(&w->faces, 8 * p->n[0] * cb);
+    own(&w->rec, nrec * chunk_record_bytes(p->prec));
+  } else {
+    w->p3 = p->p3;  // tables and routing borrowed; scratch replaced below
+    const int64_t F = p->n[0] * p->n[2];
+    own(&w->p3.fhat, N * cb);
+    own(&w->p3.dbuf, N * cb);
+    own(&w->p3.faces, 10 * F * cb);
+    w->p3.cbuf = nullptr;
+    if (!p->p3.tab[0]) own(&w->p3.cbuf, N * cb);  // the untabled sweeps keep their multipliers there
+    if (p->p3.inner_nmb) {
+      own(&w->p3.ipart, (size_t)p->n[1] * p->p3.inner_nparts * 2 * p->n[0] * cb);
+      own(&w->p3.ivw, (size_t)p->n[1] * 4 * p->n[0] * cb);
+      own(&w->p3.icin, (size_t)p->n[1] * 2 * p->n[0] * cb);
+    }
+    int maxr = 0;
+    for (int t = 0; t < 4; ++t) maxr = std::max(maxr, p->p3.nroute[t]);
+    if (maxr) {
+      own(&w->p3.rpart, (size_t)maxr * 2 * p->n[0] * sizeof(float2));
+      own(&w->p3.rtmp, (size_t)maxr * p->n[0] * sizeof(double2));
+    }
+    w->p3.partial = w->p3.ybuf = nullptr;
+  }
+  own((void**)&w->dev_err, sizeof(int));
+  own((void**)&w->state, sizeof(RefineState));
+  if (ok && cudaMemset(w->dev_err, 0, sizeof(int)) != cudaSuccess) ok = false;
+  if (p->dtype == HELM_C64_REFINED) {
+    own((void**)&w->rbuf, N * sizeof(float2));
+    own((void**)&w->sums, residual_blocks(p->dim, p->n) * 2 * sizeof(double));
+    if (p->ffb) {
+      own((void**)&w->ffb, N * sizeof(float4));
+      own((void**)&w->ufb, N * sizeof(float4));
+    }
+  }
+  if (!ok) {
+    destroy_workspace(w);
+    return nullptr;
+  }
+  return w;
 }
 
 // ---------------------------------------------------------------------------
@@ -720,7 +854,7 @@ int apply_aux(helm_plan* p, double rho, int phase_quarters) {
     if (p->tabB)
       HELM_CK(p->prec == kPrecF64 ? launch_line_tables(p->tabB, a, 1, nullptr)
                                   : launch_line_tables32(p->tabB, a, 1, nullptr));
-    HELM_CK(cudaDeviceSynchronize());
+    HELM_CK(cudaStreamSynchronize(nullptr));  // plan-time kernels run on the legacy stream
   } else {
     HELM_CK(plan3d_tables(p->p3));
   }
@@ -1071,9 +1205,86 @@ int helm_plan_3d_bc(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double
 
 int helm_set_auxiliary(helm_plan_t p, double rho, int phase_quarters) {
   if (!p || !std::isfinite(rho) || rho < 0.0 || rho > 8.0) return HELM_EINVAL;
-  HELM_CK(cudaStreamSynchronize(p->stream));
+  HELM_CK(sync_plan_streams(p));
   p->aux_trial_resid = -1.0;  // chosen by the caller, not by the plan's trials
   return apply_aux(p, rho, phase_quarters);
+}
+
+int helm_set_precision_routing(helm_plan_t p, double tau) {
+  if (!p || !std::isfinite(tau) || tau < 0 || tau > 1) return HELM_EINVAL;
+  if (p->dim != 3 || p->prec != kPrecF32) return HELM_EUNSUPPORTED;
+  HELM_CK(sync_plan_streams(p));
+  drop_refine_graph(p);  // its kernels hold the old routing
+  ++p->version;
+  HELM_CK(plan3d_set_routing(p->p3, tau));
+  return HELM_OK;
+}
+
+int helm_set_variant(helm_plan_t p, int knob, int value) {
+  if (!p || p->parent) return HELM_EINVAL;
+  HELM_CK(sync_plan_streams(p));
+  if (knob == HELM_VARIANT_TRI2D) {
+    if (p->dim != 2 || p->prec != kPrecF32) return HELM_EUNSUPPORTED;
+    if (value != 0 && value != 1) return HELM_EINVAL;
+    p->tri_regs = value;
+  } else if (knob == HELM_VARIANT_INNER_CHUNK || knob == HELM_VARIANT_INNER_TILES) {
+    if (p->dim != 3 || !p->p3.inner_nmb) return HELM_EUNSUPPORTED;
+    const int ch = knob == HELM_VARIANT_INNER_CHUNK ? value : p->p3.inner_ch;
+    const int nmb = knob == HELM_VARIANT_INNER_TILES ? value : p->p3.inner_nmb;
+    const cudaError_t e = plan3d_set_inner(p->p3, ch, nmb);
+    if (e == cudaErrorInvalidValue) {
+      cudaGetLastError();
+      return HELM_EINVAL;
+    }
+    if (e != cudaSuccess) return cuda_fail(p, e, "plan3d_set_inner");
+  } else {
+    return HELM_EINVAL;
+  }
+  drop_refine_graph(p);  // its kernels were captured with the old variant
+  ++p->version;
+  return HELM_OK;
+}
+
+int helm_get_variant(helm_plan_t p, int knob, int* value) {
+  if (!p || !value) return HELM_EINVAL;
+  if (knob == HELM_VARIANT_TRI2D) *value = p->tri_regs;
+  else if (knob == HELM_VARIANT_INNER_CHUNK) *value = p->dim == 3 ? p->p3.inner_ch : 0;
+  else if (knob == HELM_VARIANT_INNER_TILES) *value = p->dim == 3 ? p->p3.inner_nmb : 0;
+  else return HELM_EINVAL;
+  return HELM_OK;
+}
+
+int helm_time_solve(helm_plan_t p, int reps, double* ms) {
+  if (!p || p->parent || reps < 1 || !ms) return HELM_EINVAL;
+  const int64_t N = p->n[0] * p->n[1] * p->n[2];
+  double2 *tf = nullptr, *tu = nullptr;
+  if (dmalloc((void**)&tf, N * sizeof(double2)) != cudaSuccess ||
+      dmalloc((void**)&tu, N * sizeof(double2)) != cudaSuccess) {
+    dfree(tf);
+    return HELM_ENOMEM;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = HELM_OK;
+  auto once = [&]() { return solve_core(p, tf, kInC128, tu, kOutC128, 0.0, nullptr, nullptr, nullptr, nullptr); };
+  if (launch_trial_rhs(tf, N, 0x7eedull, p->stream) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    rc = cuda_fail(p, cudaGetLastError(), "timing set-up");
+  }
+  if (!rc) rc = once();  // warm-up
+  if (!rc && cudaEventRecord(e0, p->stream) != cudaSuccess) rc = HELM_ECUDA;
+  for (int r = 0; r < reps && !rc; ++r) rc = once();
+  if (!rc && cudaEventRecord(e1, p->stream) != cudaSuccess) rc = HELM_ECUDA;
+  float t = 0.f;
+  if (!rc && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+    rc = HELM_ECUDA;
+  if (!rc) *ms = (double)t / reps;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(p->stream);
+  dfree(tf);
+  dfree(tu);
+  cudaGetLastError();
+  return rc;
 }
 
 int helm_set_stream(helm_plan_t p, void* s) {
@@ -1119,7 +1330,74 @@ int helm_set_graphs(helm_plan_t p, int enable) {
 
 int helm_solve(helm_plan_t p, const void* f, void* u) {
   if (!p || !f || !u || overlaps(f, u, plan_vec_bytes(p))) return HELM_EINVAL;
+  p->last_many = 0;
   return run_solve(p, f, u, nullptr, nullptr, nullptr);
+}
+
+int helm_set_rhs_concurrency(helm_plan_t p, int k) {
+  if (!p || p->parent || k < 1 || k > 16) return HELM_EINVAL;
+  p->rhs_concurrency = k;
+  return HELM_OK;
+}
+
+int helm_solve_many(helm_plan_t p, int64_t nrhs, const void* f, void* u) {
+  if (!p || p->parent || nrhs < 1 || !f || !u) return HELM_EINVAL;
+  const size_t vb = plan_vec_bytes(p);
+  if (overlaps(f, u, vb * (size_t)nrhs)) return HELM_EINVAL;
+  p->last_many = 0;
+  if (nrhs == 1) return run_solve(p, f, u, nullptr, nullptr, nullptr);
+  int k = (int)std::min<int64_t>(nrhs, p->rhs_concurrency);
+  // workspaces follow the plan's settings: rebuilt when any has changed
+  for (helm_plan* w : p->ws)
+    if (w->version != p->version || (p->ffb && !w->ffb)) {
+      HELM_CK(cudaStreamSynchronize(p->stream));
+      for (size_t i = 0; i < p->ws_stream.size(); ++i) HELM_CK(cudaStreamSynchronize(p->ws_stream[i]));
+      for (helm_plan* q : p->ws) destroy_workspace(q);
+      p->ws.clear();
+      break;
+    }
+  while ((int)p->ws.size() < k - 1) {
+    helm_plan* w = make_workspace(p);
+    if (!w) break;  // no room: fewer right-hand sides at once
+    p->ws.push_back(w);
+  }
+  k = std::min<int>(k, 1 + (int)p->ws.size());
+  while ((int)p->ws_stream.size() < k) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    HELM_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaStreamDestroy(st);
+      return cuda_fail(p, cudaGetLastError(), "cudaEventCreate");
+    }
+    p->ws_stream.push_back(st);
+    p->ws_done.push_back(ev);
+  }
+  if (!p->fork) HELM_CK(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
+  // fork: every workspace stream starts after the work already on the plan's stream
+  HELM_CK(cudaEventRecord(p->fork, p->stream));
+  for (int w = 0; w < k; ++w) HELM_CK(cudaStreamWaitEvent(p->ws_stream[w], p->fork, 0));
+  const cudaStream_t caller = p->stream;
+  int rc = HELM_OK;
+  for (int64_t i = 0; i < nrhs && !rc; ++i) {
+    const int w = (int)(i % k);
+    helm_plan* q = w == 0 ? p : p->ws[w - 1];
+    q->stream = p->ws_stream[w];
+    // the FP64-residual graph is tied to f and u: workspaces solve kernel by kernel
+    const bool graphs = q->use_graphs;
+    if (p->dtype == HELM_C64_REFINED && !refine_ff(p)) q->use_graphs = false;
+    rc = run_solve(q, static_cast<const char*>(f) + i * vb, static_cast<char*>(u) + i * vb, nullptr, nullptr, nullptr);
+    q->use_graphs = graphs;
+    if (rc && q != p) p->err = q->err;
+  }
+  p->stream = caller;
+  // join: the plan's stream continues after every workspace stream
+  for (int w = 0; w < k; ++w) {
+    HELM_CK(cudaEventRecord(p->ws_done[w], p->ws_stream[w]));
+    HELM_CK(cudaStreamWaitEvent(p->stream, p->ws_done[w], 0));
+  }
+  if (!rc) p->last_many = k;
+  return rc;
 }
 
 int helm_solve_debug(helm_plan_t p, const void* f, void* u, void* fhat, void* v_b, void* w_b) {
@@ -1176,6 +1454,19 @@ int helm_get_info(helm_plan_t p, helm_info* info) {
   HELM_CK(cudaStreamSynchronize(p->stream));
   RefineState s{};
   HELM_CK(cudaMemcpy(&s, p->state, sizeof(s), cudaMemcpyDeviceToHost));
+  int derr_ws = 0;
+  for (int w = 1; w < p->last_many; ++w) {
+    // after helm_solve_many: report the right-hand side whose refinement ended
+    // worst (not converged, else the largest final residual)
+    RefineState t{};
+    int e = 0;
+    HELM_CK(cudaMemcpy(&t, p->ws[w - 1]->state, sizeof(t), cudaMemcpyDeviceToHost));
+    HELM_CK(cudaMemcpy(&e, p->ws[w - 1]->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    derr_ws |= e;
+    const double rt = t.iters > 0 ? t.resid[std::min(t.iters, 16) - 1] : 0.0;
+    const double rs = s.iters > 0 ? s.resid[std::min(s.iters, 16) - 1] : 0.0;
+    if (p->dtype == HELM_C64_REFINED && (t.converged < s.converged || (t.converged == s.converged && rt > rs))) s = t;
+  }
   info->dim = p->dim;
   info->dtype = p->dtype;
   for (int k = 0; k < 3; ++k) info->n[k] = p->n[k];
@@ -1186,14 +1477,20 @@ int helm_get_info(helm_plan_t p, helm_info* info) {
   info->tol = p->tol;
   info->max_iter = p->max_iter;
   info->n_dft_stages = p->axo.dft.nstages;
-  info->device_bytes = p->bytes;
+  info->device_bytes = p->bytes + (p->dim == 3 ? p->p3.route_bytes : 0);
+  for (const helm_plan* w : p->ws) info->device_bytes += w->bytes;
+  info->fp64_lines = p->dim == 3 ? plan3d_routed_lines(p->p3) : 0;
   info->residual_kind = p->resid_kind;
   info->aux_q = p->axo.q;
   info->aux_rho = p->axo.rho;
   info->aux_trial_residual = p->aux_trial_resid;
   for (int k = 0; k < 3; ++k) info->axis_bc[k] = k < p->dim ? p->bc[k] : HELM_BC_ABC;
-  int derr = 0;
-  if (p->dev_err) HELM_CK(cudaMemcpy(&derr, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  int derr = derr_ws;
+  if (p->dev_err) {
+    int e0 = 0;
+    HELM_CK(cudaMemcpy(&e0, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    derr |= e0;
+  }
   if (derr) {
     p->err = "a bounded device wait gave up (copies did not arrive)";
     return HELM_ETIMEOUT;
@@ -1273,7 +1570,9 @@ int helm_batch_destroy(helm_batch_t b) {
 
 int helm_destroy(helm_plan_t p) {
   if (!p) return HELM_OK;
-  if (p->stream) cudaStreamSynchronize(p->stream);
+  // every stream of the plan is done with its memory before it is freed
+  cudaStreamSynchronize(p->stream);
+  for (cudaStream_t st : p->ws_stream) cudaStreamSynchronize(st);
   destroy_plan(p);
   return HELM_OK;
 }

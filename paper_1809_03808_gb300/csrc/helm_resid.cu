@@ -83,7 +83,17 @@ struct ResidQArgs {
   // 3D: c0[4 cx + 2 cy + cz][2 b + c], c1[2 cy + cz][2 b + c]; 2D: c0[2 cx + cy][b], c1[cy][b]
   double2 c0[8][4];
   double2 c1[4][4];
+  // 3D corrections of the end classes against the same class inside y and z:
+  // dc0[cls][bc] = c0[cls][bc] - c0[cls & 4][bc], dc1[cyz][bc] = c1[cyz][bc] - c1[0][bc]
+  double2 dc0[8][4];
+  double2 dc1[4][4];
 };
+
+// (acc.x, acc.y) += c v
+__device__ __forceinline__ void cadd_mul(double2& acc, double2 c, double2 v) {
+  acc.x = fma(c.x, v.x, fma(-c.y, v.y, acc.x));
+  acc.y = fma(c.x, v.y, fma(c.y, v.x, acc.y));
+}
 
 // (acc.x, acc.y) -= c v for complex c (boundary classes)
 __device__ __forceinline__ void csub_mul(double2& acc, double2 c, double2 v) {
@@ -117,7 +127,7 @@ __device__ __forceinline__ void block_norms(float r2f, float f2f, double* sums, 
   }
 }
 
-constexpr int QZ = 32, QY = 16, QX = 32;  // 3D tile: z, y columns, x planes per CTA
+constexpr int QZ = 32, QY = 16, QX = 64;  // 3D tile: z, y columns, x planes per CTA
 constexpr int QE = ((QY + 2) * (QZ + 2) + QZ * QY - 1) / (QZ * QY);  // staged values per thread
 
 __global__ void __launch_bounds__(QZ* QY) k_residual3d_q(ResidQArgs a, const double2* __restrict__ f,
@@ -177,33 +187,33 @@ __global__ void __launch_bounds__(QZ* QY) k_residual3d_q(ResidQArgs a, const dou
       const double2 sm = sSz[ty][tz], sp = sSz[ty + 2][tz];
       const double2 P10 = make_double2(ym.x + yp.x, ym.y + yp.y), P11 = make_double2(sm.x + sp.x, sm.y + sp.y);
       const int cx = (ip == 0 || ip == nx - 1) ? 1 : 0;
-      if (cyz == 0) {
-        // inside along y and z: C_1bc real
-        Rn.x = fma(a.c1[0][3].x, P11.x, fma(a.c1[0][2].x, P10.x, fma(a.c1[0][1].x, P01.x, a.c1[0][0].x * P00.x)));
-        Rn.y = fma(a.c1[0][3].x, P11.y, fma(a.c1[0][2].x, P10.y, fma(a.c1[0][1].x, P01.y, a.c1[0][0].x * P00.y)));
-        if (outp) {
-          if (cx == 0) {
-            Qn.x = fma(-a.c0[0][3].x, P11.x, fma(-a.c0[0][2].x, P10.x, fma(-a.c0[0][1].x, P01.x, fma(-a.c0[0][0].x, P00.x, Qn.x))));
-            Qn.y = fma(-a.c0[0][3].x, P11.y, fma(-a.c0[0][2].x, P10.y, fma(-a.c0[0][1].x, P01.y, fma(-a.c0[0][0].x, P00.y, Qn.y))));
-          } else {
-            csub_mul(Qn, a.c0[4][0], P00);
-            csub_mul(Qn, a.c0[4][1], P01);
-            csub_mul(Qn, a.c0[4][2], P10);
-            csub_mul(Qn, a.c0[4][3], P11);
-          }
+      // every lane takes the interior coefficients (real: C_1bc for R, C_0bc
+      // for Q inside along x; complex C_0bc on the two x-end planes, a
+      // plane-uniform branch) ...
+      Rn.x = fma(a.c1[0][3].x, P11.x, fma(a.c1[0][2].x, P10.x, fma(a.c1[0][1].x, P01.x, a.c1[0][0].x * P00.x)));
+      Rn.y = fma(a.c1[0][3].x, P11.y, fma(a.c1[0][2].x, P10.y, fma(a.c1[0][1].x, P01.y, a.c1[0][0].x * P00.y)));
+      if (outp) {
+        if (cx == 0) {
+          Qn.x = fma(-a.c0[0][3].x, P11.x, fma(-a.c0[0][2].x, P10.x, fma(-a.c0[0][1].x, P01.x, fma(-a.c0[0][0].x, P00.x, Qn.x))));
+          Qn.y = fma(-a.c0[0][3].x, P11.y, fma(-a.c0[0][2].x, P10.y, fma(-a.c0[0][1].x, P01.y, fma(-a.c0[0][0].x, P00.y, Qn.y))));
+        } else {
+          csub_mul(Qn, a.c0[4][0], P00);
+          csub_mul(Qn, a.c0[4][1], P01);
+          csub_mul(Qn, a.c0[4][2], P10);
+          csub_mul(Qn, a.c0[4][3], P11);
         }
-      } else {
-        csub_mul(Rn, a.c1[cyz][0], P00);
-        csub_mul(Rn, a.c1[cyz][1], P01);
-        csub_mul(Rn, a.c1[cyz][2], P10);
-        csub_mul(Rn, a.c1[cyz][3], P11);
-        Rn = make_double2(-Rn.x, -Rn.y);
+      }
+      // ... and lanes on a y or z face add the coefficients that differ there:
+      // a y end changes the b = 0 monomials, a z end the c = 0 ones
+      if (cyz) {
+        if (cy | cz) cadd_mul(Rn, a.dc1[cyz][0], P00);
+        if (cy) cadd_mul(Rn, a.dc1[cyz][1], P01);
+        if (cz) cadd_mul(Rn, a.dc1[cyz][2], P10);
         if (outp) {
           const int cls = 4 * cx + cyz;
-          csub_mul(Qn, a.c0[cls][0], P00);
-          csub_mul(Qn, a.c0[cls][1], P01);
-          csub_mul(Qn, a.c0[cls][2], P10);
-          csub_mul(Qn, a.c0[cls][3], P11);
+          if (cy | cz) csub_mul(Qn, a.dc0[cls][0], P00);
+          if (cy) csub_mul(Qn, a.dc0[cls][1], P01);
+          if (cz) csub_mul(Qn, a.dc0[cls][2], P10);
         }
       }
     }
@@ -749,6 +759,12 @@ cudaError_t launch_residual(int dim, const int64_t* n, const double* h, double o
                   if (a1 == 0) put(q.c0[4 * cx + 2 * cy + cz][2 * b + c], v);
                   else if (cx == 0) put(q.c1[2 * cy + cz][2 * b + c], v);
                 }
+      for (int cls = 0; cls < 8; ++cls)
+        for (int bc = 0; bc < 4; ++bc) {
+          q.dc0[cls][bc] = make_double2(q.c0[cls][bc].x - q.c0[cls & 4][bc].x, q.c0[cls][bc].y - q.c0[cls & 4][bc].y);
+          if (cls < 4)
+            q.dc1[cls][bc] = make_double2(q.c1[cls][bc].x - q.c1[0][bc].x, q.c1[cls][bc].y - q.c1[0][bc].y);
+        }
       const dim3 grid((unsigned)((n[2] + QZ - 1) / QZ), (unsigned)((n[1] + QY - 1) / QY), (unsigned)((n[0] + QX - 1) / QX));
       *nblocks = (int64_t)grid.x * grid.y * grid.z;
       k_residual3d_q<<<grid, dim3(QZ, QY), 0, st>>>(q, f, u, r, sums, skip);

@@ -154,10 +154,14 @@ struct helm_server {
 
 namespace {
 
-// the plan's settings for a request (refined modes)
+// the plan's settings for a request (refined modes).  Server plans launch
+// kernel by kernel: a CUDA graph capture in the scheduler thread would make
+// any device-wide synchronisation by another thread of the process fail
+// while it lasts.
 int configure(helm_plan_t p, const helm_request& r) {
-  if (r.dtype != HELM_C64_REFINED) return HELM_OK;
-  int rc = helm_set_residual(p, r.residual);
+  int rc = helm_set_graphs(p, 0);
+  if (rc || r.dtype != HELM_C64_REFINED) return rc;
+  rc = helm_set_residual(p, r.residual);
   if (!rc) rc = helm_set_refinement(p, r.tol, r.max_iter);
   return rc;
 }
@@ -313,9 +317,9 @@ bool helm_server::start_one(std::unique_lock<std::mutex>& lk) {
     const size_t eb = r->spec.dtype == HELM_C64_RAW ? 8 : 16;
     const size_t stride = (size_t)unknowns(r->spec) * eb;
     int rc = helm_set_stream(pe->plan, slot->stream);
-    for (int32_t j = 0; !rc && j < r->spec.nrhs; ++j)
-      rc = helm_solve(pe->plan, static_cast<const char*>(r->spec.f) + j * stride,
-                      static_cast<char*>(r->spec.u) + j * stride);
+    (void)stride;
+    // the request's right-hand sides, several at once on the plan's workspaces
+    if (!rc) rc = helm_solve_many(pe->plan, r->spec.nrhs, r->spec.f, r->spec.u);
     if (rc) r->status = rc;
     cudaEventRecord(slot->done, slot->stream);
     slot->req = r;

@@ -29,6 +29,7 @@ struct Solve2DArgs {
   double eninv[2];  // e^{-t (n1-1)}: weight of the last x1 face in the Step-3 rhs
   double wx = 0;    // w of the absorbing corners along x (0: Neumann x faces)
   double wy = 0;    // w of the absorbing x1 faces (0: Neumann), in C_bb
+  int tri_regs = 0;  // complex64 passes: 1 = register-tile kernels even where the bulk-copy ones apply
 };
 
 constexpr int kChunkF32 = 16;

@@ -1258,7 +1258,7 @@ cudaError_t launch_tri2d_t32(int step, const void* fhat, const void* faces, cons
   r.cc = tb.cc;
   r.we = tb.we;
   // even n1: 16-byte aligned rows, the bulk-copy fed kernels
-  const bool bulk = (a.n1 % 2) == 0;
+  const bool bulk = (a.n1 % 2) == 0 && !a.tri_regs;
   const dim3 gbulk((unsigned)((a.n1 + kBulkLines - 1) / kBulkLines),
                    (unsigned)((a.nchunks + kBulkChunks - 1) / kBulkChunks));
 

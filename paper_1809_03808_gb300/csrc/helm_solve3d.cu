@@ -14,6 +14,9 @@
 // inner-mode-space solution y3(x, l, m), written over the Thomas scratch.
 // The outer boundary rows are then reduced over l by k_reduce_outer.
 #include <algorithm>
+#include <cmath>
+#include <utility>
+#include <vector>
 #include <type_traits>
 
 #include "helm_dft.h"
@@ -37,6 +40,17 @@ struct Plane3DArgs {
 };
 
 constexpr int XC = 32;  // rows per reduction chunk
+
+constexpr int kMW = 16;       // inner modes per tile
+constexpr int kLineVals = 5;  // per-line table values (see k_plane_tables)
+constexpr int kPivRows = 32;  // pivot rows staged in shared memory (rows below a line's settling row)
+constexpr int kRoutedFlag = 1 << 30;  // in the settling-row table: the line is solved in FP64
+// Routing is off by default: the complex64 solve's error does sit in the
+// near-singular lines (92 % of it in 1 % of the lines on a 160^3 grid of the
+// 512^3 workload's spacing and wave number), but it is the complex64
+// rounding of those modes' inputs, amplified by the line's conditioning, not
+// the FP32 arithmetic of its sweeps: FP64 sweeps leave it unchanged (-0.6 %).
+constexpr double kDefaultRouteTau = 0.0;
 
 template <typename C>
 struct ThomasRow {
@@ -427,8 +441,10 @@ __global__ void k_outer_cbb(const typename cpx<T>::type* __restrict__ v, const t
 // (below the last row) satisfy |1/u_j - 1/u_inf| <= tol |1/u_inf| (tol 2^-27
 // for complex64 tables, a quarter of the FP32 rounding; 2^-50 for
 // complex128), so the tiled sweeps read the table only for rows < len and use
-// 1/u_inf beyond.  lend[2 * line] = 1/u_inf, lend[2 * line + 1] = 1/u_{nx-1}
-// (the absorbing corner row); line = l * nz + m.  For propagating modes the
+// 1/u_inf beyond.  Per line (kLineVals values, line = l * nz + m): 1/u_inf,
+// 1/u_{nx-1} (the corner row), the off-diagonal b of the line matrix, and
+// the carry coefficients alpha, beta of a chunk of ch settled rows (see
+// k_inner3d), all from the FP64 values.  For propagating modes the
 // pivots keep oscillating and len covers the whole line.
 __device__ __forceinline__ double2 csqrt_d(double2 z) {
   const double r = hypot(z.x, z.y);
@@ -444,7 +460,7 @@ __device__ __forceinline__ double2 csqrt_d(double2 z) {
 
 template <typename T>
 __global__ void k_plane_tables(typename cpx<T>::type* __restrict__ tab, typename cpx<T>::type* __restrict__ lend,
-                               int* __restrict__ lenL, Plane3DArgs a, int outerA, int innerA) {
+                               int* __restrict__ lenL, Plane3DArgs a, int outerA, int innerA, int ch) {
   using C = typename cpx<T>::type;
   const int64_t ny = a.ny, nz = a.nz, nx = a.nx;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // l * nz + m
@@ -476,8 +492,20 @@ __global__ void k_plane_tables(typename cpx<T>::type* __restrict__ tab, typename
     }
   }
   if (lend) {
-    lend[2 * i] = cvt<C>(iinf);
-    lend[2 * i + 1] = cvt<C>(inv);
+    // chunk constants of a chunk of ch settled rows: q = -b / u_inf,
+    // alpha = q^ch, beta = sum_k q^k q^(k+1) (the carries' coefficients)
+    const double2 q = cmul(make_double2(-k.b.x, -k.b.y), iinf);
+    double2 al = make_double2(1, 0), be = make_double2(0, 0);
+    for (int j = 0; j < ch; ++j) {
+      const double2 an = cmul(al, q);
+      be = cadd(be, cmul(al, an));
+      al = an;
+    }
+    lend[kLineVals * i] = cvt<C>(iinf);
+    lend[kLineVals * i + 1] = cvt<C>(inv);
+    lend[kLineVals * i + 2] = cvt<C>(k.b);
+    lend[kLineVals * i + 3] = cvt<C>(al);
+    lend[kLineVals * i + 4] = cvt<C>(be);
     lenL[i] = (int)(last_bad + 1);
   }
 }
@@ -549,8 +577,6 @@ Plane3DArgs make_args(const Plan3D& p) {
 // CTA's nmb tiles into one face partial per CTA; inner Step 3 writes the
 // plane solution y3(x, l, m).
 // ---------------------------------------------------------------------------
-constexpr int kMW = 16;  // inner modes per tile
-
 struct InnerArgs {
   Plane3DArgs a;
   int ch;      // rows per chunk
@@ -558,6 +584,13 @@ struct InnerArgs {
   int nmb;     // tiles per CTA (inner modes kMW * nmb per CTA)
   int nparts;  // face partials per plane = gridDim.x
 };
+
+// Shared memory of k_inner3d: rhs tile, pivot rows, chunk summaries (padded),
+// face accumulators, per-line and per-mode constants, settling rows.
+inline size_t inner_smem_bytes(int64_t nx, int nc, size_t cb) {
+  return ((size_t)nx * kMW + (size_t)kPivRows * kMW + 4 * (size_t)kMW * (nc + 1) + 2 * (size_t)nx + 9 * kMW + 3) * cb +
+         2 * kMW * sizeof(int);
+}
 
 // affine map x -> p x + q, composed as (p2, q2) o (p1, q1) = (p2 p1, p2 q1 + q2)
 template <typename C>
@@ -593,20 +626,26 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
   const int nx = (int)a.nx;
   const int64_t ny = a.ny, nz = a.nz;
   const int nc = ia.nc, ch = ia.ch;
+  const int ncp = nc + 1;  // padded chunk stride of the summaries: conflict-free in both layouts
   C* tile = reinterpret_cast<C*>(smem_raw);  // [nx][kMW]
-  C* sums = tile + (size_t)nx * kMW;         // [4][nc][kMW]: d_loc, x_loc, alpha, beta; then the carries
-  C* facc = sums + 4 * nc * kMW;             // [2][nx] face accumulators (inner Steps 1, 2)
-  C* mw = facc + 2 * nx;                     // [kMW] rhs scale, [kMW] rhs weight of the last face, [2][kMW] face weights
+  C* piv = tile + (size_t)nx * kMW;          // [kPivRows][kMW] first rows of the pivot tables
+  C* sums = piv + kPivRows * kMW;            // [4][kMW][ncp]: d_loc, x_loc, alpha, beta; then the carries
+  C* facc = sums + 4 * kMW * ncp;            // [2][nx] face accumulators (inner Steps 1, 2)
+  C* mw = facc + 2 * nx;                     // [kMW] rhs scale, [kMW] weight of the last face, [2][kMW] face weights
+  // [kMW] b, [kMW] 1/u_inf, [kMW] 1/u_{nx-1}; [3] outer-mode constants; [kMW] alpha, [kMW] beta of a settled chunk
+  C* lc = mw + 4 * kMW;
+  int* sL = reinterpret_cast<int*>(lc + 5 * kMW + 3);  // [kMW] settling rows
+  int* sR = sL + kMW;                                    // [kMW] 1: routed to FP64
   const int64_t l = blockIdx.y;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int mi = tid & (kMW - 1), c = tid / kMW;
-  const double w2 = a.omega * a.omega;
-  // outer-mode quantities (outer A modes in outer Step 2)
-  const double lo_re = OSTEP == 2 ? a.lamAo[2 * l] : a.lamBo[2 * l];
-  const double lo_im = OSTEP == 2 ? a.lamAo[2 * l + 1] : a.lamBo[2 * l + 1];
-  const C gscale = OSTEP == 2 ? mk<C>(1, 0) : mk<C>(a.invmuo[2 * l], a.invmuo[2 * l + 1]);
-  const T paro = (T)a.parAo[l];
-  const C wl = cmul(mk<C>(a.two[2 * l], -a.two[2 * l + 1]), mk<C>(a.eninv_o[0], a.eninv_o[1]));
+  const int64_t xs = ny * nz;
+  if (tid == 0) {
+    // outer-mode constants: 1/mu_l (outer B modes), e^{+i theta_l} e^{-t(ny-1)}, parity (outer A modes)
+    lc[3 * kMW] = OSTEP == 2 ? mk<C>(1, 0) : mk<C>(a.invmuo[2 * l], a.invmuo[2 * l + 1]);
+    lc[3 * kMW + 1] = cmul(mk<C>(a.two[2 * l], -a.two[2 * l + 1]), mk<C>(a.eninv_o[0], a.eninv_o[1]));
+    lc[3 * kMW + 2] = mk<C>(a.parAo[l], 0);
+  }
   const C* cin1 = cin ? cin + l * 2 * nx : nullptr;  // inner C_bb faces of this plane
   const C* cinn = cin ? cin1 + nx : nullptr;
   const C* g1 = gfaces;  // outer faces [2][nx][nz]
@@ -634,9 +673,30 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
       }
       mw[2 * kMW + tid] = on ? w1 : mk<C>(0, 0);
       mw[3 * kMW + tid] = on ? wn : mk<C>(0, 0);
+      // line constants from the plan tables
+      const int64_t line = l * nz + mc;
+      lc[tid] = lend[kLineVals * line + 2];
+      lc[kMW + tid] = lend[kLineVals * line];
+      lc[2 * kMW + tid] = lend[kLineVals * line + 1];
+      lc[3 * kMW + 3 + tid] = lend[kLineVals * line + 3];
+      lc[4 * kMW + 3 + tid] = lend[kLineVals * line + 4];
+      // a line routed to FP64 (flag bit) gets a zero right-hand side here, so
+      // it adds nothing to the faces; the FP64 kernel solves it
+      const int lr = on ? lenL[line] : 0;
+      const bool routed = (lr & kRoutedFlag) != 0;
+      sL[tid] = routed ? 0 : lr;
+      if (routed) {
+        mw[tid] = mk<C>(0, 0);
+        mw[kMW + tid] = mk<C>(0, 0);
+        mw[2 * kMW + tid] = mk<C>(0, 0);
+        mw[3 * kMW + tid] = mk<C>(0, 0);
+      }
+      sR[tid] = routed ? 1 : 0;
     }
     __syncthreads();
-    // ---- stage the right-hand sides ----
+    const C gscale = lc[3 * kMW], wl = lc[3 * kMW + 1];
+    const T paro = lc[3 * kMW + 2].x;
+    // ---- stage the right-hand sides and the first pivot rows ----
     {
       constexpr int B = 8;
       for (int e0 = tid; e0 < nx * kMW; e0 += B * nthr) {
@@ -650,7 +710,7 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
             const int64_t m = m0 + mm;
             if (m < nz) {
               if (ISTEP == 2) {
-                v[t] = cadd(cin1[x], cmul(cinn[x], mw[kMW + mm]));
+                if (!sR[mm]) v[t] = cadd(cin1[x], cmul(cinn[x], mw[kMW + mm]));
               } else {
                 C g;
                 if (OSTEP == 1) g = cmul(fhat[((int64_t)x * ny + l) * nz + m], gscale);
@@ -671,38 +731,63 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
           if (e < nx * kMW) tile[e] = v[t];
         }
       }
+      for (int e = tid; e < kPivRows * kMW; e += nthr) {
+        const int j = e / kMW, mm = e - j * kMW;
+        C v = mk<C>(0, 0);
+        if (j < sL[mm]) v = tab[(int64_t)j * xs + l * nz + m0 + mm];
+        piv[e] = v;
+      }
     }
     // ---- line constants of thread (mi, c) ----
     const int64_t m = m0 + mi;
     const bool act = m < nz && c < nc;
-    const int64_t line = l * nz + (m < nz ? m : 0);
-    const double li_re = ISTEP == 2 ? a.lamAi[2 * (line - l * nz)] : a.lamBi[2 * (line - l * nz)];
-    const double li_im = ISTEP == 2 ? a.lamAi[2 * (line - l * nz) + 1] : a.lamBi[2 * (line - l * nz) + 1];
-    const double sre = lo_re + li_re - w2, sim = lo_im + li_im;
-    const C b = mk<C>(sre * (a.hx / 6.0) - 1.0 / a.hx, sim * (a.hx / 6.0));
-    const C nb = mk<C>(-(sre * (a.hx / 6.0) - 1.0 / a.hx), -sim * (a.hx / 6.0));
-    const C iinf = lend[2 * line], ilast = lend[2 * line + 1];
-    const int L = lenL[line];
+    const C b = lc[mi], iinf = lc[kMW + mi], ilast = lc[2 * kMW + mi];
+    const C nb = mk<C>(-b.x, -b.y);
+    const int L = sL[mi];  // 0 for a routed line
     const C* tcol = tab + l * nz + (m < nz ? m : 0);
-    const int64_t xs = ny * nz;
-    auto pivot = [&](int j) -> C { return j < L ? tcol[(int64_t)j * xs] : (j == nx - 1 ? ilast : iinf); };
+    auto pivot = [&](int j) -> C {
+      if (j >= L) return j == nx - 1 ? ilast : iinf;
+      return j < kPivRows ? piv[j * kMW + mi] : tcol[(int64_t)j * xs];
+    };
     const int s0 = c * ch, e0 = min(s0 + ch, nx) - 1;
-    __syncthreads();  // tile staged
+    __syncthreads();  // tile and pivot rows staged
     // ---- pass 1 ----
+    // Forward with d_{s-1} = 0 (d_loc written over the rhs), then the
+    // backward substitution with x_{e+1} = 0 over it by Horner's rule gives
+    // x_loc.  alpha_e = prod (-b/u_j) and beta = sum alpha_{j-1} alpha_j do
+    // not depend on the data: a chunk of settled rows takes them from the
+    // plan, the others (rows with tabulated pivots, the corner row) form them.
+    const bool settled = s0 >= L && e0 < nx - 1 && e0 - s0 + 1 == ch;
     if (act) {
-      C d = mk<C>(0, 0), al = mk<C>(1, 0), xl = mk<C>(0, 0), be = mk<C>(0, 0);
-      for (int j = s0; j <= e0; ++j) {
-        const C inv = pivot(j);
-        d = cmul(csub(tile[j * kMW + mi], cmul(b, d)), inv);
-        xl = cadd(xl, cmul(al, d));
-        const C an = cmul(al, cmul(nb, inv));
-        be = cadd(be, cmul(al, an));
-        al = an;
+      C d = mk<C>(0, 0), al = mk<C>(1, 0), be = mk<C>(0, 0);
+      if (settled) {
+        for (int j = s0; j <= e0; ++j) {
+          d = cmul(csub(tile[j * kMW + mi], cmul(b, d)), iinf);
+          tile[j * kMW + mi] = d;
+        }
+        al = lc[3 * kMW + 3 + mi];
+        be = lc[4 * kMW + 3 + mi];
+      } else {
+        for (int j = s0; j <= e0; ++j) {
+          const C inv = pivot(j);
+          d = cmul(csub(tile[j * kMW + mi], cmul(b, d)), inv);
+          tile[j * kMW + mi] = d;
+          const C an = cmul(al, cmul(nb, inv));
+          be = cadd(be, cmul(al, an));
+          al = an;
+        }
       }
-      sums[(0 * nc + c) * kMW + mi] = d;
-      sums[(1 * nc + c) * kMW + mi] = xl;
-      sums[(2 * nc + c) * kMW + mi] = al;
-      sums[(3 * nc + c) * kMW + mi] = be;
+      sums[(0 * kMW + mi) * ncp + c] = d;
+      C x = mk<C>(0, 0);
+      if (settled) {
+        const C cinf = cmul(b, iinf);
+        for (int j = e0; j >= s0; --j) x = csub(tile[j * kMW + mi], cmul(cinf, x));
+      } else {
+        for (int j = e0; j >= s0; --j) x = csub(tile[j * kMW + mi], cmul(cmul(b, pivot(j)), x));
+      }
+      sums[(1 * kMW + mi) * ncp + c] = x;
+      sums[(2 * kMW + mi) * ncp + c] = al;
+      sums[(3 * kMW + mi) * ncp + c] = be;
     }
     __syncthreads();
     // ---- scan over the chunks of each line: one warp per line ----
@@ -710,13 +795,16 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
       const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
       const int g = (nc + 31) / 32;  // chunks per lane
       for (int mm = warp; mm < kMW; mm += nw) {
+        C* sd = sums + (0 * kMW + mm) * ncp;  // d_loc, then the carry-in d_{s-1}
+        C* sx = sums + (1 * kMW + mm) * ncp;  // x_loc, then the carry-in x_{e+1}
+        const C* sa = sums + (2 * kMW + mm) * ncp;
+        const C* sb = sums + (3 * kMW + mm) * ncp;
         const int c0 = lane * g, c1 = min(c0 + g, nc);
         // forward: D_c = dloc_c + alpha_c D_{c-1}; the lane's group as one map
         C P = mk<C>(1, 0), Q = mk<C>(0, 0);
         for (int cc = c0; cc < c1; ++cc) {
-          const C alc = sums[(2 * nc + cc) * kMW + mm];
-          Q = cadd(cmul(alc, Q), sums[(0 * nc + cc) * kMW + mm]);
-          P = cmul(alc, P);
+          Q = cadd(cmul(sa[cc], Q), sd[cc]);
+          P = cmul(sa[cc], P);
         }
         for (int off = 1; off < 32; off <<= 1) {
           const C Pu = shfl_up_c(P, off), Qu = shfl_up_c(Q, off);
@@ -726,19 +814,17 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
         if (lane == 0) Din = mk<C>(0, 0);
         // carry-in d_{s-1} of each chunk; keep E_c = xloc_c + beta_c D_{c-1}
         for (int cc = c0; cc < c1; ++cc) {
-          const C dl = sums[(0 * nc + cc) * kMW + mm], alc = sums[(2 * nc + cc) * kMW + mm];
-          const C E = cadd(sums[(1 * nc + cc) * kMW + mm], cmul(sums[(3 * nc + cc) * kMW + mm], Din));
-          sums[(0 * nc + cc) * kMW + mm] = Din;
-          sums[(1 * nc + cc) * kMW + mm] = E;
-          Din = cadd(dl, cmul(alc, Din));
+          const C dl = sd[cc];
+          sx[cc] = cadd(sx[cc], cmul(sb[cc], Din));
+          sd[cc] = Din;
+          Din = cadd(dl, cmul(sa[cc], Din));
         }
         // backward: X_c = E_c + alpha_c X_{c+1}; the lane's group as one map of X after the group
         P = mk<C>(1, 0);
         Q = mk<C>(0, 0);
         for (int cc = c1 - 1; cc >= c0; --cc) {
-          const C alc = sums[(2 * nc + cc) * kMW + mm];
-          Q = cadd(cmul(alc, Q), sums[(1 * nc + cc) * kMW + mm]);
-          P = cmul(alc, P);
+          Q = cadd(cmul(sa[cc], Q), sx[cc]);
+          P = cmul(sa[cc], P);
         }
         for (int off = 1; off < 32; off <<= 1) {
           const C Pd = shfl_down(P, off), Qd = shfl_down(Q, off);
@@ -747,26 +833,42 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
         C Xin = shfl_down(Q, 1);  // X just after the lane's group
         if (lane == 31) Xin = mk<C>(0, 0);
         for (int cc = c1 - 1; cc >= c0; --cc) {
-          const C alc = sums[(2 * nc + cc) * kMW + mm];
-          const C E = sums[(1 * nc + cc) * kMW + mm];
-          sums[(1 * nc + cc) * kMW + mm] = Xin;  // carry-in x_{e+1} of chunk cc
-          Xin = cadd(E, cmul(alc, Xin));
+          const C E = sx[cc];
+          sx[cc] = Xin;  // carry-in x_{e+1} of chunk cc
+          Xin = cadd(E, cmul(sa[cc], Xin));
         }
       }
     }
     __syncthreads();
     // ---- pass 2 ----
+    // d_j = d_loc_j + alpha_j d_{s-1} over the chunk, then the backward
+    // substitution from the exact carry x_{e+1}.
     if (act) {
-      C d = sums[(0 * nc + c) * kMW + mi];
-      for (int j = s0; j <= e0; ++j) {
-        d = cmul(csub(tile[j * kMW + mi], cmul(b, d)), pivot(j));
-        tile[j * kMW + mi] = d;
-      }
-      C x = sums[(1 * nc + c) * kMW + mi];
-      for (int j = e0; j >= s0; --j) {
-        x = csub(tile[j * kMW + mi], cmul(cmul(b, pivot(j)), x));
-        if (ISTEP == 3) y3[((int64_t)j * ny + l) * nz + m] = x;
-        else tile[j * kMW + mi] = x;
+      const C Din = sums[(0 * kMW + mi) * ncp + c];
+      C x = sums[(1 * kMW + mi) * ncp + c];
+      if (settled) {
+        const C q = cmul(nb, iinf), cinf = cmul(b, iinf);
+        C al = q;
+        for (int j = s0; j <= e0; ++j) {
+          tile[j * kMW + mi] = cadd(tile[j * kMW + mi], cmul(al, Din));
+          al = cmul(al, q);
+        }
+        for (int j = e0; j >= s0; --j) {
+          x = csub(tile[j * kMW + mi], cmul(cinf, x));
+          if (ISTEP == 3) y3[((int64_t)j * ny + l) * nz + m] = x;
+          else tile[j * kMW + mi] = x;
+        }
+      } else {
+        C al = mk<C>(1, 0);
+        for (int j = s0; j <= e0; ++j) {
+          al = cmul(al, cmul(nb, pivot(j)));
+          tile[j * kMW + mi] = cadd(tile[j * kMW + mi], cmul(al, Din));
+        }
+        for (int j = e0; j >= s0; --j) {
+          x = csub(tile[j * kMW + mi], cmul(cmul(b, pivot(j)), x));
+          if (ISTEP == 3) y3[((int64_t)j * ny + l) * nz + m] = x;
+          else tile[j * kMW + mi] = x;
+        }
       }
     }
     if (ISTEP != 3) {
@@ -794,6 +896,143 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
   }
 }
 
+// Precision routing (a9): the inner lines whose line matrix is close to
+// singular, solved with FP64 arithmetic from the same (complex64) inputs.  One
+// warp per routed line: lane c owns rows [c*chr, (c+1)*chr) and the chunked LU
+// of k_inner3d runs in FP64 (pass 1, warp scan of the affine carries, pass 2
+// through a per-line FP64 scratch), with FP64 reciprocal pivots from the
+// plan.  Inner Steps 1, 2 write the line's weighted boundary-row
+// contributions to rpart[route] (added per plane by k_inner_reduce); inner
+// Step 3 writes y3 over the zero the tile kernel left for the line.
+template <typename T, int OSTEP, int ISTEP>
+__global__ void __launch_bounds__(128) k_inner3d_r(InnerArgs ia, const typename cpx<T>::type* __restrict__ fhat,
+                                                   const typename cpx<T>::type* __restrict__ gfaces,
+                                                   const typename cpx<T>::type* __restrict__ cin,
+                                                   const int* __restrict__ rlist, const double2* __restrict__ rtab,
+                                                   int nroute, typename cpx<T>::type* __restrict__ rpart,
+                                                   double2* __restrict__ rtmp, typename cpx<T>::type* __restrict__ y3,
+                                                   const int* __restrict__ skip) {
+  using C = typename cpx<T>::type;
+  if (skip && *skip) return;
+  const Plane3DArgs& a = ia.a;
+  const int q = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (q >= nroute) return;  // warp-uniform
+  const int lane = threadIdx.x & 31;
+  const int nx = (int)a.nx;
+  const int64_t ny = a.ny, nz = a.nz;
+  const int64_t line = rlist[q], l = line / nz, m = line - l * nz;
+  const double w2 = a.omega * a.omega;
+  const double* lo = OSTEP == 2 ? a.lamAo : a.lamBo;
+  const double* li = ISTEP == 2 ? a.lamAi : a.lamBi;
+  const double sre = lo[2 * l] + li[2 * m] - w2, sim = lo[2 * l + 1] + li[2 * m + 1];
+  const double2 b = make_double2(sre * (a.hx / 6.0) - 1.0 / a.hx, sim * (a.hx / 6.0));
+  const double2 nb = make_double2(-b.x, -b.y);
+  // rhs factors of the line, as in k_inner3d, in FP64
+  const double2 gscale = OSTEP == 2 ? make_double2(1, 0) : make_double2(a.invmuo[2 * l], a.invmuo[2 * l + 1]);
+  const double paro = a.parAo[l];
+  const double2 wl = cmul(make_double2(a.two[2 * l], -a.two[2 * l + 1]), make_double2(a.eninv_o[0], a.eninv_o[1]));
+  const double2 imu = make_double2(a.invmui[2 * m], a.invmui[2 * m + 1]);
+  const double2 wm = cmul(make_double2(a.twi[2 * m], -a.twi[2 * m + 1]), make_double2(a.eninv_i[0], a.eninv_i[1]));
+  const double pari = a.parAi[m];
+  const C* cin1 = cin ? cin + l * 2 * nx : nullptr;
+  const C* cinn = cin ? cin1 + nx : nullptr;
+  const C* g1 = gfaces;
+  const C* gn = gfaces ? gfaces + (int64_t)nx * nz : nullptr;
+  auto rhs = [&](int j) -> double2 {
+    if (ISTEP == 2) return cadd(cvt<double2>(cin1[j]), cscale(cvt<double2>(cinn[j]), pari));
+    double2 g;
+    if (OSTEP == 1) g = cmul(cvt<double2>(fhat[((int64_t)j * ny + l) * nz + m]), gscale);
+    else if (OSTEP == 2) g = cadd(cvt<double2>(g1[(int64_t)j * nz + m]), cscale(cvt<double2>(gn[(int64_t)j * nz + m]), paro));
+    else
+      g = cmul(cadd(cadd(cvt<double2>(fhat[((int64_t)j * ny + l) * nz + m]), cvt<double2>(g1[(int64_t)j * nz + m])),
+                    cmul(cvt<double2>(gn[(int64_t)j * nz + m]), wl)),
+               gscale);
+    if (ISTEP == 3) g = cadd(g, cadd(cvt<double2>(cin1[j]), cmul(cvt<double2>(cinn[j]), wm)));
+    return cmul(g, imu);
+  };
+  const double2* piv = rtab + (int64_t)q * nx;
+  double2* dtmp = rtmp + (int64_t)q * nx;
+  const int chr = (nx + 31) / 32;
+  const int s0 = lane * chr, e0 = min(s0 + chr, nx) - 1;
+  // pass 1
+  double2 d = make_double2(0, 0), al = make_double2(1, 0), xl = make_double2(0, 0), be = make_double2(0, 0);
+  for (int j = s0; j <= e0; ++j) {
+    const double2 inv = piv[j];
+    d = cmul(csub(rhs(j), cmul(b, d)), inv);
+    xl = cadd(xl, cmul(al, d));
+    const double2 an = cmul(al, cmul(nb, inv));
+    be = cadd(be, cmul(al, an));
+    al = an;
+  }
+  if (s0 > e0) {  // a lane without rows: identity maps
+    d = make_double2(0, 0);
+    al = make_double2(1, 0);
+  }
+  // forward carries D (inclusive scan of x -> al x + d), then E = xl + be D_in
+  double2 P = al, Q = d;
+  for (int off = 1; off < 32; off <<= 1) {
+    const double2 Pu = shfl_up_c(P, off), Qu = shfl_up_c(Q, off);
+    if (lane >= off) affine_compose(P, Q, Pu, Qu);
+  }
+  double2 Din = shfl_up_c(Q, 1);
+  if (lane == 0) Din = make_double2(0, 0);
+  const double2 E = cadd(xl, cmul(be, Din));
+  // backward carries: X_c = E_c + al_c X_{c+1}
+  P = al;
+  Q = s0 > e0 ? make_double2(0, 0) : E;
+  for (int off = 1; off < 32; off <<= 1) {
+    const double2 Pd = shfl_down(P, off), Qd = shfl_down(Q, off);
+    if (lane + off < 32) affine_compose(P, Q, Pd, Qd);
+  }
+  double2 Xin = shfl_down(Q, 1);
+  if (lane == 31) Xin = make_double2(0, 0);
+  // pass 2
+  d = Din;
+  for (int j = s0; j <= e0; ++j) {
+    d = cmul(csub(rhs(j), cmul(b, d)), piv[j]);
+    dtmp[j] = d;
+  }
+  double2 x = Xin;
+  double2 w1 = make_double2(1, 0), wn = make_double2(a.twi[2 * m], a.twi[2 * m + 1]);
+  if (ISTEP == 2) {
+    w1 = make_double2(a.sigAi[2 * m], a.sigAi[2 * m + 1]);
+    wn = cscale(w1, pari);
+  }
+  C* rp = ISTEP == 3 ? nullptr : rpart + (int64_t)q * 2 * nx;
+  for (int j = e0; j >= s0; --j) {
+    x = csub(dtmp[j], cmul(cmul(b, piv[j]), x));
+    if (ISTEP == 3) {
+      y3[((int64_t)j * ny + l) * nz + m] = cvt<C>(x);
+    } else {
+      rp[j] = cvt<C>(cmul(x, w1));
+      rp[nx + j] = cvt<C>(cmul(x, wn));
+    }
+  }
+}
+
+// FP64 reciprocal pivots of the routed lines (the recurrence of
+// k_plane_tables), and the routed flag in the settling-row table.
+__global__ void k_route_tables(double2* __restrict__ rtab, int* __restrict__ lenL, const int* __restrict__ rlist,
+                               int nroute, Plane3DArgs a, int outerA, int innerA) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nroute) return;
+  const int64_t nx = a.nx, nz = a.nz;
+  const int64_t line = rlist[q], l = line / nz, m = line - l * nz;
+  const double* lo = outerA ? a.lamAo : a.lamBo;
+  const double* li = innerA ? a.lamAi : a.lamBi;
+  const double w2 = a.omega * a.omega;
+  const LineCoef<double2> k = line_coef<double2>(lo[2 * l] + li[2 * m] - w2, lo[2 * l + 1] + li[2 * m + 1], a.hx, a.wx);
+  double2 c = make_double2(0, 0);
+  for (int64_t ix = 0; ix < nx; ++ix) {
+    const double2 aj = (ix == 0 || ix == nx - 1) ? k.ac : k.a;
+    const double2 den = ix == 0 ? aj : csub(aj, cmul(k.b, c));
+    const double2 inv = crecip(den);
+    c = cmul(k.b, inv);
+    rtab[(int64_t)q * nx + ix] = inv;
+  }
+  lenL[line] |= kRoutedFlag;
+}
+
 // Per outer mode l: the inner boundary rows from the CTAs' partials (fixed
 // order), scaled as in eq. 2dBs1 (Step 1: 1/nz and e^{t(nz-1)}/nz) or eq.
 // step2-3 (Step 2: 1), kept in vw[l] (v_in after Step 1, w_in after Step 2),
@@ -803,6 +1042,8 @@ template <typename T, int OSTEP, int ISTEP>
 __global__ void __launch_bounds__(256) k_inner_reduce(InnerArgs ia, const typename cpx<T>::type* __restrict__ part,
                                                       typename cpx<T>::type* __restrict__ vw,
                                                       typename cpx<T>::type* __restrict__ cin,
+                                                      const int* __restrict__ roff,
+                                                      const typename cpx<T>::type* __restrict__ rpart,
                                                       const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
   if (skip && *skip) return;
@@ -819,6 +1060,8 @@ __global__ void __launch_bounds__(256) k_inner_reduce(InnerArgs ia, const typena
   for (int e = threadIdx.x; e < 2 * nx; e += blockDim.x) {
     C acc = mk<C>(0, 0);
     for (int q = 0; q < ia.nparts; ++q) acc = cadd(acc, pp[(int64_t)q * 2 * nx + e]);
+    if (roff)  // lines of this plane solved in FP64, in route order
+      for (int q = roff[l]; q < roff[l + 1]; ++q) acc = cadd(acc, rpart[(int64_t)q * 2 * nx + e]);
     acc = cmul(acc, e < nx ? sc1 : scn);
     if (ISTEP == 1) {
       sv[e] = acc;
@@ -868,7 +1111,7 @@ cudaError_t launch_inner_t(const Plan3D& p, const void* gfaces, const int* skip,
   InnerArgs ia{make_args(p), p.inner_ch, p.inner_nc, p.inner_nmb, p.inner_nparts};
   const int nx = (int)p.n[0];
   const int nthr = kMW * ((p.inner_nc + 1) & ~1);
-  const size_t smem = ((size_t)nx * kMW + 4 * (size_t)p.inner_nc * kMW + 2 * (size_t)nx + 4 * kMW) * sizeof(C);
+  const size_t smem = inner_smem_bytes(nx, p.inner_nc, sizeof(C));
   const dim3 grid((unsigned)p.inner_nparts, (unsigned)p.n[1]);
   const int oA = OSTEP == 2 ? 1 : 0;
   const C* fh = (const C*)p.fhat;
@@ -889,17 +1132,31 @@ cudaError_t launch_inner_t(const Plan3D& p, const void* gfaces, const int* skip,
                                    (C*)p.dbuf, skip);
     return cudaGetLastError();
   };
-  auto reduce = [&](auto kern) -> cudaError_t {
+  auto routed = [&](auto kern, int innerA) -> cudaError_t {
+    const int t = 2 * oA + innerA;
+    if (!p.nroute[t]) return cudaSuccess;
+    ProfScope ps(prof, "inner_fp64_lines", st);
+    kern<<<(unsigned)((p.nroute[t] + 3) / 4), 128, 0, st>>>(ia, fh, gf, cin, p.rlist[t], (const double2*)p.rtab[t],
+                                                          p.nroute[t], (C*)p.rpart, (double2*)p.rtmp, (C*)p.dbuf,
+                                                          skip);
+    return cudaGetLastError();
+  };
+  auto reduce = [&](auto kern, int innerA) -> cudaError_t {
+    const int t = 2 * oA + innerA;
     ProfScope ps(prof, "inner_reduce", st);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
-    kern<<<(unsigned)p.n[1], 256, rsm, st>>>(ia, part, vw, cin, skip);
+    kern<<<(unsigned)p.n[1], 256, rsm, st>>>(ia, part, vw, cin, p.nroute[t] ? p.roff[t] : nullptr, (const C*)p.rpart,
+                                             skip);
     return cudaGetLastError();
   };
   if ((e = sweep(k_inner3d<T, OSTEP, 1>, 1, 0)) != cudaSuccess) return e;
-  if ((e = reduce(k_inner_reduce<T, OSTEP, 1>)) != cudaSuccess) return e;
+  if ((e = routed(k_inner3d_r<T, OSTEP, 1>, 0)) != cudaSuccess) return e;
+  if ((e = reduce(k_inner_reduce<T, OSTEP, 1>, 0)) != cudaSuccess) return e;
   if ((e = sweep(k_inner3d<T, OSTEP, 2>, 2, 1)) != cudaSuccess) return e;
-  if ((e = reduce(k_inner_reduce<T, OSTEP, 2>)) != cudaSuccess) return e;
-  return sweep(k_inner3d<T, OSTEP, 3>, 3, 0);
+  if ((e = routed(k_inner3d_r<T, OSTEP, 2>, 1)) != cudaSuccess) return e;
+  if ((e = reduce(k_inner_reduce<T, OSTEP, 2>, 1)) != cudaSuccess) return e;
+  if ((e = sweep(k_inner3d<T, OSTEP, 3>, 3, 0)) != cudaSuccess) return e;
+  return routed(k_inner3d_r<T, OSTEP, 3>, 0);
 }
 
 template <typename T>
@@ -1025,9 +1282,9 @@ cudaError_t plan3d_init(Plan3D& p, int prec, const int64_t* n, const double* h, 
   // settling data of the tiled sweeps); without room for them the kernels
   // recompute the pivots
   const int64_t lines = n[1] * n[2];
-  const size_t per_type = N * cb + lines * (2 * cb + sizeof(int));
+  const size_t per_type = N * cb + lines * (kLineVals * cb + sizeof(int));
   for (int t = 0; t < 4; ++t) {
-    if (dmalloc((void**)&p.tab[t], N * cb) != cudaSuccess || dmalloc((void**)&p.lend[t], lines * 2 * cb) != cudaSuccess ||
+    if (dmalloc((void**)&p.tab[t], N * cb) != cudaSuccess || dmalloc((void**)&p.lend[t], lines * kLineVals * cb) != cudaSuccess ||
         dmalloc((void**)&p.lenL[t], lines * sizeof(int)) != cudaSuccess) {
       cudaGetLastError();
       for (int u = 0; u < 4; ++u) {
@@ -1053,7 +1310,7 @@ cudaError_t plan3d_init(Plan3D& p, int prec, const int64_t* n, const double* h, 
     ch = (int)((n[0] + max_nc - 1) / max_nc);
     nc = (int)((n[0] + ch - 1) / ch);
   }
-  const size_t ismem = ((size_t)n[0] * kMW + 4 * (size_t)nc * kMW + 2 * (size_t)n[0] + 4 * kMW) * cb;
+  const size_t ismem = inner_smem_bytes(n[0], nc, cb);
   if (p.tab[0] && ismem <= (size_t)smem_max) {
     const int64_t tiles = (n[2] + kMW - 1) / kMW;
     const int64_t total = tiles * n[1];
@@ -1077,27 +1334,173 @@ cudaError_t plan3d_init(Plan3D& p, int prec, const int64_t* n, const double* h, 
       cudaGetLastError();
     }
   }
+  p.route_tau = prec == kPrecF32 ? kDefaultRouteTau : 0.0;
   p.ready = true;
   return plan3d_tables(p);
 }
 
+cudaError_t plan3d_tables_no_routing(Plan3D& p);
+
+namespace {
+
+void free_routing(Plan3D& p) {
+  for (int t = 0; t < 4; ++t) {
+    dfree(p.rlist[t]);
+    dfree(p.roff[t]);
+    dfree(p.rtab[t]);
+    p.rlist[t] = p.roff[t] = nullptr;
+    p.rtab[t] = nullptr;
+    p.nroute[t] = 0;
+  }
+  dfree(p.rpart);
+  dfree(p.rtmp);
+  p.rpart = p.rtmp = nullptr;
+  p.route_bytes = 0;
+}
+
+// The routed lines of every line type: the inner lines (l, m) whose line
+// matrix K_x + s M_x, s = Lam_outer,l + Lam_inner,m - w^2, has an eigenvalue
+// Lam^A_x,k + s within tau w^2 of zero (Lam^A_x: the pencil of the
+// tridiagonal axis, absorbing or Neumann).  Those matrices amplify the
+// rounding of the complex64 sweeps by their condition number; they are few
+// (the modes next to the resonance surface).  The nearest Lam^A_x,k to -s is
+// found by bisection on the real parts (the pencil's eigenvalues lie close to
+// the real axis) and a window of neighbours.
+cudaError_t build_routing(Plan3D& p) {
+  free_routing(p);
+  if (p.route_tau <= 0 || p.prec != kPrecF32 || !p.inner_nmb) return cudaSuccess;
+  const int64_t nx = p.n[0], ny = p.n[1], nz = p.n[2];
+  std::vector<double> lamx(2 * nx), sigx(2 * nx);
+  std::vector<int8_t> parx(nx);
+  if (abc_eigen(nx, p.h[0], p.wc[0], lamx.data(), sigx.data(), parx.data()) != 0) return cudaSuccess;
+  std::vector<std::pair<double, double>> ex(nx);
+  for (int64_t k = 0; k < nx; ++k) ex[k] = {lamx[2 * k], lamx[2 * k + 1]};
+  std::sort(ex.begin(), ex.end());
+  std::vector<double> lbo(2 * ny), lao(2 * ny), lbi(2 * nz), lai(2 * nz);
+  cudaError_t e;
+  if ((e = cudaMemcpy(lbo.data(), p.axo->lamB, 2 * ny * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(lao.data(), p.axo->lamA, 2 * ny * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(lbi.data(), p.axi->lamB, 2 * nz * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(lai.data(), p.axi->lamA, 2 * nz * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return e;
+  const double w2 = p.omega * p.omega, lim2 = (p.route_tau * w2) * (p.route_tau * w2);
+  const Plane3DArgs a = make_args(p);
+  int maxr = 0;
+  for (int t = 0; t < 4; ++t) {
+    const std::vector<double>& lo = (t >> 1) ? lao : lbo;
+    const std::vector<double>& li = (t & 1) ? lai : lbi;
+    std::vector<int> list, off(ny + 1, 0);
+    for (int64_t l = 0; l < ny; ++l) {
+      off[l] = (int)list.size();
+      for (int64_t m = 0; m < nz; ++m) {
+        const double sr = lo[2 * l] + li[2 * m] - w2, si = lo[2 * l + 1] + li[2 * m + 1];
+        const auto it = std::lower_bound(ex.begin(), ex.end(), std::make_pair(-sr, -1e300));
+        const int64_t c0 = it - ex.begin();
+        double best = HUGE_VAL;
+        for (int64_t k = std::max<int64_t>(0, c0 - 8); k < std::min<int64_t>(nx, c0 + 8); ++k) {
+          const double dr = ex[k].first + sr, di = ex[k].second + si;
+          best = std::min(best, dr * dr + di * di);
+        }
+        if (best < lim2) list.push_back((int)(l * nz + m));
+      }
+    }
+    off[ny] = (int)list.size();
+    p.nroute[t] = (int)list.size();
+    if (list.empty()) continue;
+    maxr = std::max(maxr, p.nroute[t]);
+    const size_t sz[3] = {list.size() * sizeof(int), (size_t)(ny + 1) * sizeof(int),
+                          list.size() * (size_t)nx * sizeof(double2)};
+    if ((e = dmalloc((void**)&p.rlist[t], sz[0])) != cudaSuccess || (e = dmalloc((void**)&p.roff[t], sz[1])) != cudaSuccess ||
+        (e = dmalloc(&p.rtab[t], sz[2])) != cudaSuccess) {
+      free_routing(p);
+      return cudaSuccess;  // no room: every line stays in complex64
+    }
+    p.route_bytes += sz[0] + sz[1] + sz[2];
+    if ((e = cudaMemcpy(p.rlist[t], list.data(), sz[0], cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(p.roff[t], off.data(), sz[1], cudaMemcpyHostToDevice)) != cudaSuccess)
+      return e;
+    k_route_tables<<<(unsigned)((list.size() + 127) / 128), 128>>>((double2*)p.rtab[t], p.lenL[t], p.rlist[t],
+                                                                   p.nroute[t], a, t >> 1, t & 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (maxr) {
+    const size_t cb = sizeof(float2);
+    if (dmalloc(&p.rpart, (size_t)maxr * 2 * nx * cb) != cudaSuccess ||
+        dmalloc(&p.rtmp, (size_t)maxr * nx * sizeof(double2)) != cudaSuccess) {
+      free_routing(p);
+      return plan3d_tables_no_routing(p);
+    }
+    p.route_bytes += (size_t)maxr * nx * (2 * cb + sizeof(double2));
+  }
+  return cudaStreamSynchronize(nullptr);  // plan-time kernels run on the legacy stream
+}
+
+}  // namespace
+
 cudaError_t plan3d_tables(Plan3D& p) {
+  if (!p.tab[0]) return cudaSuccess;
+  cudaError_t e = plan3d_tables_no_routing(p);
+  if (e != cudaSuccess) return e;
+  return build_routing(p);
+}
+
+cudaError_t plan3d_set_routing(Plan3D& p, double tau) {
+  p.route_tau = tau > 0 ? tau : 0;
+  if (!p.tab[0]) return cudaSuccess;
+  // the routed flags live in the settling-row tables: rebuild them first
+  cudaError_t e = plan3d_tables_no_routing(p);
+  if (e != cudaSuccess) return e;
+  return build_routing(p);
+}
+
+int plan3d_routed_lines(const Plan3D& p) { return p.nroute[0] + p.nroute[1] + p.nroute[2] + p.nroute[3]; }
+
+cudaError_t plan3d_set_inner(Plan3D& p, int ch, int nmb) {
+  if (!p.inner_nmb || ch < 4 || ch > 64 || nmb < 1 || nmb > 8) return cudaErrorInvalidValue;
+  const size_t cb = p.prec == kPrecF64 ? sizeof(double2) : sizeof(float2);
+  const int max_nc = (p.prec == kPrecF64 ? 512 : 1024) / kMW;
+  const int nc = (int)((p.n[0] + ch - 1) / ch);
+  int dev = 0, smem_max = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (nc > max_nc || inner_smem_bytes(p.n[0], nc, cb) > (size_t)smem_max) return cudaErrorInvalidValue;
+  const int64_t tiles = (p.n[2] + kMW - 1) / kMW;
+  nmb = (int)std::min<int64_t>(nmb, tiles);
+  const int nparts = (int)((tiles + nmb - 1) / nmb);
+  if (nparts > p.inner_nparts) {  // more face partials: a larger buffer
+    void* q = nullptr;
+    cudaError_t e = dmalloc(&q, (size_t)p.n[1] * nparts * 2 * p.n[0] * cb);
+    if (e != cudaSuccess) return e;
+    dfree(p.ipart);
+    p.ipart = q;
+  }
+  p.inner_ch = ch;
+  p.inner_nc = nc;
+  p.inner_nmb = nmb;
+  p.inner_nparts = nparts;
+  return plan3d_tables(p);  // the settled-chunk constants depend on ch
+}
+
+cudaError_t plan3d_tables_no_routing(Plan3D& p) {
   if (!p.tab[0]) return cudaSuccess;
   const Plane3DArgs a = make_args(p);
   const int bs = 128;
   const unsigned grid = (unsigned)((p.n[1] * p.n[2] + bs - 1) / bs);
   for (int t = 0; t < 4; ++t) {
     if (p.prec == kPrecF64)
-      k_plane_tables<double><<<grid, bs>>>((double2*)p.tab[t], (double2*)p.lend[t], p.lenL[t], a, t >> 1, t & 1);
+      k_plane_tables<double><<<grid, bs>>>((double2*)p.tab[t], (double2*)p.lend[t], p.lenL[t], a, t >> 1, t & 1,
+                                           p.inner_ch > 0 ? p.inner_ch : 16);
     else
-      k_plane_tables<float><<<grid, bs>>>((float2*)p.tab[t], (float2*)p.lend[t], p.lenL[t], a, t >> 1, t & 1);
+      k_plane_tables<float><<<grid, bs>>>((float2*)p.tab[t], (float2*)p.lend[t], p.lenL[t], a, t >> 1, t & 1,
+                                          p.inner_ch > 0 ? p.inner_ch : 16);
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return cudaDeviceSynchronize();
+  return cudaStreamSynchronize(nullptr);  // plan-time kernels run on the legacy stream
 }
 
 void free_plan3d(Plan3D& p) {
+  free_routing(p);
   for (int t = 0; t < 4; ++t) {
     dfree(p.tab[t]);
     dfree(p.lend[t]);

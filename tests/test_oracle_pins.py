@@ -372,3 +372,36 @@ def test_neumann_pencil_eigen_is_the_cosine_basis():
     M = fem.M1d(n, h)
     np.testing.assert_allclose(V.T @ M @ V, np.eye(n), atol=1e-10)
     np.testing.assert_allclose(V[0] ** 2, V[-1] ** 2, rtol=1e-8, atol=1e-12)
+
+
+# --------------------------- cost-model network (autotuner) ------------------
+
+def test_mlp_oracle_gradient_matches_finite_differences():
+    """The numpy reference of the cost model's backprop against central
+    differences of its own loss (every parameter)."""
+    from oracle import mlp
+
+    rng = np.random.default_rng(3)
+    n_in, n_h, B = 5, 7, 11
+    p = rng.standard_normal(mlp.num_params(n_in, n_h)) * 0.5
+    X = rng.standard_normal((B, n_in))
+    T = rng.standard_normal(B)
+    L, g = mlp.loss_and_gradient(p, X, T, n_in, n_h)
+    eps = 1e-6
+    fd = np.empty_like(p)
+    for i in range(p.size):
+        e = np.zeros_like(p)
+        e[i] = eps
+        fd[i] = (mlp.loss_and_gradient(p + e, X, T, n_in, n_h)[0] - mlp.loss_and_gradient(p - e, X, T, n_in, n_h)[0]) / (2 * eps)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-8)
+
+
+def test_mlp_oracle_forward_by_hand():
+    """One sample through a 1-input, 1-wide network, written out."""
+    from oracle import mlp
+
+    p = np.array([0.3, -0.1, 0.7, 0.2, -1.5, 0.25])  # W1, b1, W2, b2, w3, b3
+    y, _ = mlp.forward(p, np.array([[2.0]]), 1, 1)
+    h1 = np.tanh(0.3 * 2.0 - 0.1)
+    h2 = np.tanh(0.7 * h1 + 0.2)
+    assert y[0] == pytest.approx(-1.5 * h2 + 0.25, abs=1e-15)
