@@ -334,11 +334,11 @@ int helm_batch_destroy(helm_batch_t b);
 
 /* --- Allocation-free small solve (the paper has no counterpart) -------------
  * For callers that cannot allocate device memory when they need a solve:
- * code running inside a host callback or a CUDA-graph host node, under a
- * larger framework's allocator lock, or in a process whose device memory is
- * reserved up front.  Such callers cannot build a plan (helm_plan_2d
- * allocates), so this entry point does the whole complex128 2D solve (the
- * HELM_C128 arithmetic of helm_solve, default auxiliary) without a plan.  It
+ * code running under a larger framework's allocator lock, or in a process
+ * whose device memory is reserved up front.  Such callers cannot build a
+ * plan (helm_plan_2d allocates), so this entry point does the whole
+ * complex128 2D solve (the HELM_C128 arithmetic of helm_solve, fixed
+ * auxiliary rho = q = 1, no residual check) without a plan.  It
  * calls no cudaMalloc, cudaFree or allocating library routine.  Its device
  * scratch is one fixed 16 MiB array that the library reserves on every GPU
  * that loads it, held until the process exits.
@@ -351,10 +351,9 @@ int helm_batch_destroy(helm_batch_t b);
  * fit the 16 MiB (about 350,000 unknowns; 512 x 512 fits); larger problems
  * return HELM_EUNSUPPORTED before touching the device.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one array: calls whose
- * work overlaps on the GPU (different streams, or threads calling at once)
- * race and give wrong results, so serialise them.  Each call rebuilds its
+ * (cudaGetSymbolAddress) with that device current.  Every call shares the
+ * one array: calls whose work overlaps on the GPU (different streams, or
+ * threads calling at once) race and give wrong results, so serialise them.  Each call rebuilds its
  * eigen-data on the host (O(ny^2) work) and copies it into the array. */
 int helm_solve_2d_static(int64_t nx, int64_t ny, double hx, double hy, double omega,
                          const void* f, void* u, void* cuda_stream);

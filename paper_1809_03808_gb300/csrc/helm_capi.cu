@@ -150,6 +150,7 @@ void free_axis(AxisData& a) {
   dfree(a.parA);
   dfree(a.tw);
   dfree(a.tw32);
+  for (void* q : a.bs) dfree(q);
   a = AxisData{};
 }
 
@@ -252,6 +253,62 @@ int build_axis_aux(helm_plan* p, AxisData& a, double rho, int q) {
   return HELM_OK;
 }
 
+// Bluestein tables of an axis whose length has a prime factor above 64, in
+// the compute precision `prec`: the chirp w_j = e^{i pi j^2/n} (j^2 reduced
+// mod 2n in integers), the length-m DFTs of the chirp sequence b (b_j = w_j
+// for |j| < n, cyclic) for the forward transform and of conj(b) for the
+// inverse one, both divided by m, and the length-m twiddles.  FP64 on the
+// host (the spectra by a direct O(m^2) sum).
+int build_bluestein(helm_plan* p, AxisData& a, int prec) {
+  const int64_t n = a.n, m = bluestein_length(n);
+  const double pi = 3.14159265358979323846;
+  std::vector<std::complex<double>> w(n), b(m, 0.0), f0(m), f1(m);
+  for (int64_t j = 0; j < n; ++j) {
+    const int64_t r = (j * j) % (2 * n);
+    w[j] = std::polar(1.0, pi * (double)r / (double)n);
+    b[j] = w[j];
+    if (j) b[m - j] = w[j];
+  }
+  std::vector<double> rre(m), rim(m);
+  unit_roots(m, rre.data(), rim.data());  // e^{-2 pi i k/m}
+  for (int64_t k = 0; k < m; ++k) {
+    std::complex<double> s0 = 0.0, s1 = 0.0;
+    for (int64_t j = 0; j < m; ++j) {
+      const int64_t e = (j * k) % m;
+      const std::complex<double> t(rre[e], rim[e]);
+      s0 += b[j] * t;
+      s1 += std::conj(b[j]) * t;
+    }
+    f0[k] = s0 / (double)m;
+    f1[k] = s1 / (double)m;
+  }
+  const size_t es = prec == kPrecF64 ? sizeof(double2) : sizeof(float2);
+  auto put = [&](void** dst, const std::vector<std::complex<double>>& v) -> int {
+    std::vector<char> host(v.size() * es);
+    for (size_t i = 0; i < v.size(); ++i) {
+      if (prec == kPrecF64) reinterpret_cast<double2*>(host.data())[i] = make_double2(v[i].real(), v[i].imag());
+      else reinterpret_cast<float2*>(host.data())[i] = make_float2((float)v[i].real(), (float)v[i].imag());
+    }
+    if (int rc = dev_alloc(p, dst, host.size())) return rc;
+    return cudaMemcpy(*dst, host.data(), host.size(), cudaMemcpyHostToDevice) == cudaSuccess ? HELM_OK : HELM_ECUDA;
+  };
+  std::vector<std::complex<double>> twm(m);
+  for (int64_t k = 0; k < m; ++k) twm[k] = {rre[k], rim[k]};
+  int rc;
+  if ((rc = put(&a.bs[0], w)) || (rc = put(&a.bs[1], f0)) || (rc = put(&a.bs[2], f1)) || (rc = put(&a.bs[3], twm)))
+    return rc;
+  DftPlan mp;
+  dft_factor(m, &mp);
+  a.dft.bm = (int)m;
+  a.dft.bstages = mp.nstages;
+  for (int s = 0; s < mp.nstages; ++s) a.dft.bradix[s] = mp.radix[s];
+  a.dft.bw = a.bs[0];
+  a.dft.bf[0] = a.bs[1];
+  a.dft.bf[1] = a.bs[2];
+  a.dft.btw = a.bs[3];
+  return HELM_OK;
+}
+
 // Eigen-data of one periodic axis (Section 3.2): absorbing-pencil eigen-data
 // (eqs. EVP1a, EVPcondA; wc = 0: the Neumann pencil of a Gamma_N axis), DFT
 // twiddles, and the auxiliary tables.
@@ -260,6 +317,8 @@ int build_axis(helm_plan* p, AxisData& a, int64_t n, double h, double wc, double
   a.h = h;
   a.wc = wc;
   dft_factor(n, &a.dft);
+  if (dft_needs_bluestein(a.dft))
+    if (int rc = build_bluestein(p, a, p->prec)) return rc;
   std::vector<double> twre(n), twim(n);
   unit_roots(n, twre.data(), twim.data());
   std::vector<double> tw(2 * n), lamA(2 * n), sigA(2 * n), parA(n);
@@ -1656,7 +1715,7 @@ int helm_solve_2d_static(int64_t nx, int64_t ny, double hx, double hy, double om
     cudaGetLastError();
     return HELM_ECUDA;
   }
-  if (!dft_supported(ax.dft, sizeof(double2), smem)) return HELM_EUNSUPPORTED;
+  if (!dft_supported(ax.dft, sizeof(double2), smem) || dft_needs_bluestein(ax.dft)) return HELM_EUNSUPPORTED;
   // scratch layout
   const int64_t N = nx * ny;
   const Solve2DArgs a0 = args2d(&sp);

@@ -269,11 +269,155 @@ __global__ void __launch_bounds__(256) k_dft_cols(const void* __restrict__ in, i
   }
 }
 
+// Bluestein's chirp-z transform for lengths with a prime factor above 64.
+// With w_j = e^{i pi j^2 / n} and jk = (j^2 + k^2 - (k - j)^2) / 2,
+//   sum_j x_j e^{-2 pi i jk/n} = conj(w_k) sum_j (x_j conj(w_j)) w_{k-j},
+//   sum_j x_j e^{+2 pi i jk/n} = w_k sum_j (x_j w_j) conj(w_{k-j}),
+// a convolution computed as a cyclic one of length m >= 2n - 1 (a power of
+// two): the zero-padded sequence is transformed, multiplied by the plan's
+// transform of the chirp sequence (already divided by m), and transformed
+// back.  Each line stays in shared memory; HBM sees one read and one write.
+template <typename C>
+__device__ __forceinline__ C chirp(const C* __restrict__ w, int j, int sign) {
+  C v = w[j];
+  if (sign < 0) v.y = -v.y;  // forward: conj(w_j)
+  return v;
+}
+
+// In-smem length-m transform of one or several lines (point stride ps, line
+// offset lo between lines handled by the caller's index map): radices of m.
+template <typename C>
+__device__ __forceinline__ C* bs_fft(C* cur, C* nxt, int ps, int nlines, int lstride, const DftPlan& p,
+                                     const C* __restrict__ tw, int sign) {
+  const int m = p.bm;
+  int Ns = 1;
+  for (int s = 0; s < p.bstages; ++s) {
+    const int R = p.bradix[s];
+    const int nb = m / R;
+    const int work = nlines * nb;
+    for (int b = threadIdx.x; b < work; b += blockDim.x) {
+      const int line = b / nb, j = b - line * nb;
+      butterfly<C>(cur + line * lstride, nxt + line * lstride, ps, m, R, Ns, j, tw, sign, nullptr);
+    }
+    __syncthreads();
+    C* t = cur;
+    cur = nxt;
+    nxt = t;
+    Ns *= R;
+  }
+  return cur;
+}
+
+// Rows: one line per CTA.
+template <typename T>
+__global__ void __launch_bounds__(256) k_dft_rows_bs(const void* __restrict__ in, int in_is_double,
+                                                     void* __restrict__ out, int out_mode, int64_t nrows, DftPlan p,
+                                                     int sign, T scale, double accum_scale,
+                                                     const typename cpx<T>::type* __restrict__ sc_in,
+                                                     const typename cpx<T>::type* __restrict__ sc_out,
+                                                     const int* __restrict__ skip) {
+  using C = typename cpx<T>::type;
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = p.n, m = p.bm;
+  const C* w = reinterpret_cast<const C*>(p.bw);
+  const C* bf = reinterpret_cast<const C*>(p.bf[sign > 0 ? 1 : 0]);
+  const C* tw = reinterpret_cast<const C*>(p.btw);
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + m;
+  const int64_t g0 = (int64_t)blockIdx.x * n;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    C v = mk<C>(0, 0);
+    if (j < n) {
+      v = load_in<T>(in, in_is_double, g0 + j);
+      if (sc_in) v = cmul(v, sc_in[j]);
+      v = cmul(v, chirp(w, j, sign));
+    }
+    buf0[j] = v;
+  }
+  __syncthreads();
+  C* cur = bs_fft<C>(buf0, buf1, 1, 1, 0, p, tw, -1);
+  for (int k = threadIdx.x; k < m; k += blockDim.x) cur[k] = cmul(cur[k], bf[k]);
+  __syncthreads();
+  C* oth = cur == buf0 ? buf1 : buf0;
+  cur = bs_fft<C>(cur, oth, 1, 1, 0, p, tw, +1);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    C v = cscale(cmul(cur[k], chirp(w, k, sign)), scale);
+    if (sc_out) v = cmul(v, sc_out[k]);
+    store_out<C>(out, out_mode, g0 + k, v, accum_scale);
+  }
+}
+
+// Columns along a middle axis ([outer][n][inner]): TC columns per CTA, point
+// k of column c at buf[k * TC + c].
+template <typename T>
+__global__ void __launch_bounds__(256) k_dft_cols_bs(const void* __restrict__ in, int in_is_double,
+                                                     void* __restrict__ out, int out_mode, int64_t outer,
+                                                     int64_t inner, int TC, DftPlan p, int sign, T scale,
+                                                     double accum_scale,
+                                                     const typename cpx<T>::type* __restrict__ sc_in,
+                                                     const typename cpx<T>::type* __restrict__ sc_out,
+                                                     const int* __restrict__ skip) {
+  using C = typename cpx<T>::type;
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = p.n, m = p.bm;
+  const C* w = reinterpret_cast<const C*>(p.bw);
+  const C* bf = reinterpret_cast<const C*>(p.bf[sign > 0 ? 1 : 0]);
+  const C* tw = reinterpret_cast<const C*>(p.btw);
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + (size_t)TC * m;
+  const int64_t tiles_per_slab = (inner + TC - 1) / TC;
+  const int64_t slab = blockIdx.x / tiles_per_slab;
+  const int64_t c0 = (blockIdx.x - slab * tiles_per_slab) * TC;
+  const int TCh = (int)min((int64_t)TC, inner - c0);
+  const int64_t g0 = slab * (int64_t)n * inner + c0;
+  for (int e = threadIdx.x; e < m * TC; e += blockDim.x) {
+    const int k = e / TC, c = e - k * TC;
+    C v = mk<C>(0, 0);
+    if (k < n && c < TCh) {
+      v = load_in<T>(in, in_is_double, g0 + (int64_t)k * inner + c);
+      if (sc_in) v = cmul(v, sc_in[k]);
+      v = cmul(v, chirp(w, k, sign));
+    }
+    buf0[e] = v;
+  }
+  __syncthreads();
+  // TC lines of stride 1 between lines, point stride TC
+  C* cur = bs_fft<C>(buf0, buf1, TC, TC, 1, p, tw, -1);
+  for (int e = threadIdx.x; e < m * TC; e += blockDim.x) cur[e] = cmul(cur[e], bf[e / TC]);
+  __syncthreads();
+  C* oth = cur == buf0 ? buf1 : buf0;
+  cur = bs_fft<C>(cur, oth, TC, TC, 1, p, tw, +1);
+  for (int e = threadIdx.x; e < n * TC; e += blockDim.x) {
+    const int k = e / TC, c = e - k * TC;
+    if (c < TCh) {
+      C v = cscale(cmul(cur[e], chirp(w, k, sign)), scale);
+      if (sc_out) v = cmul(v, sc_out[k]);
+      store_out<C>(out, out_mode, g0 + (int64_t)k * inner + c, v, accum_scale);
+    }
+  }
+}
+
 }  // namespace
 
-bool dft_supported(const DftPlan& p, size_t elem_bytes, int max_smem) {
+bool dft_needs_bluestein(const DftPlan& p) {
   for (int s = 0; s < p.nstages; ++s)
-    if (p.radix[s] > kMaxGenericRadix) return false;
+    if (p.radix[s] > kMaxGenericRadix) return true;
+  return false;
+}
+
+int64_t bluestein_length(int64_t n) {
+  int64_t m = 1;
+  while (m < 2 * n - 1) m <<= 1;
+  return m;
+}
+
+bool dft_supported(const DftPlan& p, size_t elem_bytes, int max_smem) {
+  if (dft_needs_bluestein(p)) {
+    const int64_t m = bluestein_length(p.n);
+    return m <= 8192 && (size_t)2 * m * elem_bytes <= (size_t)max_smem;
+  }
   return (size_t)2 * p.n * elem_bytes <= (size_t)max_smem;
 }
 
@@ -281,6 +425,24 @@ cudaError_t launch_dft_rows(int prec, const void* in, int in_is_double, void* ou
                             int64_t nrows, const DftPlan& p, const void* tw, int sign, double scale,
                             double accum_scale, const void* sc_in, const void* sc_out, const int* skip,
                             cudaStream_t st, int* err) {
+  if (p.bm) {
+    if (nrows == 0) return cudaSuccess;
+    const size_t es = prec == kPrecF64 ? sizeof(double2) : sizeof(float2);
+    const size_t smem = (size_t)2 * p.bm * es;
+    if (prec == kPrecF64) {
+      auto k = k_dft_rows_bs<double>;
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k<<<(unsigned)nrows, 256, smem, st>>>(in, in_is_double, out, out_mode, nrows, p, sign, scale, accum_scale,
+                                            (const double2*)sc_in, (const double2*)sc_out, skip);
+    } else {
+      auto k = k_dft_rows_bs<float>;
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k<<<(unsigned)nrows, 256, smem, st>>>(in, in_is_double, out, out_mode, nrows, p, sign, (float)scale,
+                                            accum_scale, (const float2*)sc_in, (const float2*)sc_out, skip);
+    }
+    return cudaGetLastError();
+  }
+  if (dft_needs_bluestein(p)) return cudaErrorInvalidValue;  // large prime without its chirp tables
   if (dft_rows_pow2_supported(p.n))
     return launch_dft_rows_pow2(prec, in, in_is_double, out, out_mode, nrows, p.n, tw, sign, scale, accum_scale,
                                 sc_in, sc_out, skip, st, err);
@@ -311,6 +473,29 @@ cudaError_t launch_dft_cols(int prec, const void* in, int in_is_double, void* ou
                             int64_t outer, int64_t inner, const DftPlan& p, const void* tw, int sign,
                             double scale, double accum_scale, const void* sc_in, const void* sc_out,
                             const int* skip, cudaStream_t st) {
+  if (p.bm) {
+    const size_t es = prec == kPrecF64 ? sizeof(double2) : sizeof(float2);
+    int TC = 16;
+    while (TC > 1 && (size_t)2 * TC * p.bm * es > 200 * 1024) TC /= 2;
+    if (TC > inner) TC = (int)inner;
+    const size_t smem = (size_t)2 * TC * p.bm * es;
+    const int64_t grid = outer * ((inner + TC - 1) / TC);
+    if (grid == 0) return cudaSuccess;
+    if (prec == kPrecF64) {
+      auto k = k_dft_cols_bs<double>;
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k<<<(unsigned)grid, 256, smem, st>>>(in, in_is_double, out, out_mode, outer, inner, TC, p, sign, scale,
+                                           accum_scale, (const double2*)sc_in, (const double2*)sc_out, skip);
+    } else {
+      auto k = k_dft_cols_bs<float>;
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k<<<(unsigned)grid, 256, smem, st>>>(in, in_is_double, out, out_mode, outer, inner, TC, p, sign,
+                                           (float)scale, accum_scale, (const float2*)sc_in, (const float2*)sc_out,
+                                           skip);
+    }
+    return cudaGetLastError();
+  }
+  if (dft_needs_bluestein(p)) return cudaErrorInvalidValue;
   if (dft_cols_pow2_supported(p.n))
     return launch_dft_cols_pow2(prec, in, in_is_double, out, out_mode, outer, inner, p.n, tw, sign, scale,
                                 accum_scale, sc_in, sc_out, skip, st);

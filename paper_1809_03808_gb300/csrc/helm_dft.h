@@ -17,6 +17,10 @@ enum { kOutC128 = 0, kOutC64 = 1, kOutAccumC128 = 2, kOutFF = 3, kOutAccumFF = 4
 enum { kInC64 = 0, kInC128 = 1, kInFF = 2 };
 
 bool dft_supported(const DftPlan& p, size_t elem_bytes, int max_smem);
+// A length whose factorisation has a prime above 64 is transformed by
+// Bluestein's chirp-z method; its power-of-two convolution length (>= 2n - 1).
+bool dft_needs_bluestein(const DftPlan& p);
+int64_t bluestein_length(int64_t n);
 
 // Lines along the contiguous (last) axis: nrows lines of length p.n.
 // in: of kind in_is_double (kIn*); computed in `prec`; out per out_mode

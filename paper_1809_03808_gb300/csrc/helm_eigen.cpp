@@ -362,6 +362,10 @@ void unit_roots(int64_t n, double* re, double* im) {
 int dft_factor(int64_t n, DftPlan* p) {
   p->n = (int)n;
   p->nstages = 0;
+  p->bm = 0;
+  p->bstages = 0;
+  p->bw = p->btw = nullptr;
+  p->bf[0] = p->bf[1] = nullptr;
   if (n < 1) return 0;
   int64_t m = n;
   auto push = [&](int r) {

@@ -22,6 +22,18 @@ struct DftPlan {
   int n;
   int nstages;
   int radix[kMaxStages];
+  // Lengths with a prime factor above 64 (Bluestein's chirp-z transform):
+  // bm = the power-of-two convolution length (0: not used), its radices, and
+  // device tables in the plan's compute precision: bw the chirp
+  // e^{i pi j^2 / n} (n values), bf[0] / bf[1] the length-bm DFT of the chirp
+  // sequence for the forward / inverse transform, scaled by 1/bm, btw the
+  // twiddles e^{-2 pi i k / bm}.
+  int bm;
+  int bstages;
+  int bradix[kMaxStages];
+  const void* bw;
+  const void* bf[2];
+  const void* btw;
 };
 
 int dft_factor(int64_t n, DftPlan* p);
@@ -69,6 +81,7 @@ struct AxisData {
   double* parA = nullptr;   // +-1 : V[n,l] = par * V[1,l]
   double* tw = nullptr;     // e^{-2 pi i k/n} (re, im) interleaved, FP64
   float* tw32 = nullptr;    // same, FP32
+  void* bs[4] = {nullptr, nullptr, nullptr, nullptr};  // Bluestein tables of dft (chirp, 2 spectra, twiddles)
   DftPlan dft{};
 };
 

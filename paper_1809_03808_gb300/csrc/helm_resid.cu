@@ -65,12 +65,16 @@ struct ResidFFArgs {
 // f), 2 subtractions: 13 FP64 instructions (26 per complex unknown; 2D: 7).
 // ---------------------------------------------------------------------------
 
+// The plain conversion, out of line so that the common path of round_d2f
+// holds no FP64 instruction (a select would evaluate both sides).
+__device__ __noinline__ float round_d2f_plain(double x) { return (float)x; }
+
 // x rounded to the nearest float (ties to even) on the integer pipe; values
 // outside the normal float range take the plain conversion.
 __device__ __forceinline__ float round_d2f(double x) {
   const uint64_t b = (uint64_t)__double_as_longlong(x);
   const int e = (int)((b >> 52) & 0x7ff);
-  if (e - 896 <= 0 || e - 896 >= 254) return (float)x;
+  if (e - 896 <= 0 || e - 896 >= 254) return round_d2f_plain(x);
   const uint32_t sgn = (uint32_t)(b >> 32) & 0x80000000u;
   const uint64_t m = b & 0xfffffffffffffull;
   const uint32_t top = (uint32_t)(m >> 29), rem = (uint32_t)(m & 0x1fffffffull);

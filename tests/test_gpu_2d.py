@@ -53,6 +53,11 @@ CASES = {
     "pow2_5x256": _case((5, 256), (0.1, 2.0), ppw=10),
     "pow2_7x2048": _case((7, 2048), (0.1, 8.0), ppw=10),
     "pow2_4x4096": _case((4, 4096), (0.05, 10.0), ppw=12),
+    # x1 lengths with a prime factor above 64: Bluestein's chirp-z transform
+    "bluestein_40x67": _case((40, 67), (0.6, 1.0), ppw=8),
+    "bluestein_33x257": _case((33, 257), (0.2, 1.6), ppw=10),
+    "bluestein_6x1021": _case((6, 1021), (0.05, 6.0), ppw=10),
+    "bluestein_20x586": _case((20, 586), (0.3, 4.0), ppw=9),  # 2 x 293
 }
 
 

@@ -87,34 +87,43 @@ def _max_prime_factor(n: int) -> int:
 def batch_2d(count: int = 512, seed: int = 1000) -> list:
     """Batched 2D workload: `count` independent problems.
 
-    nx uniform on {63..1023}; ny (the x1 / transform length) uniform on the
-    values in {63..1023} whose prime factors are all <= 64 (the transform
-    lengths the library supports); anisotropic spacings h_j = s_j / (n_j - 1)
-    with s_j uniform on [0.5, 2]; omega for a uniform 6..20 nodes per
-    wavelength at max(h).  One problem in eight is moved next to a discrete
-    resonance: omega^2 is set to the nearest sum of the closed-form
-    Neumann-Laplacian eigenvalues of linear elements,
-    6/h^2 (1 - cos(k pi/(n-1))) / (2 + cos(k pi/(n-1))), of the two axes (the
-    absorbing boundary keeps the problem solvable).  Right-hand sides are
+    nx and ny (the x1 / transform length) uniform on {63..1023}; anisotropic
+    spacings h_j = s_j / (n_j - 1) with s_j uniform on [0.5, 2]; omega for a
+    uniform 6..20 nodes per wavelength at max(h).  Two problems in eight are
+    moved next to a discrete resonance, omega^2 set to the nearest of
+      (i)  (i % 8 == 7) a sum of closed-box (Neumann) eigenvalues of the
+           linear-element pencils of the two axes,
+           6/h^2 (1 - cos(k pi/(n-1))) / (2 + cos(k pi/(n-1))), and
+      (ii) (i % 8 == 3) a periodic eigenvalue of the x1 axis,
+           6/h^2 (1 - cos(2 pi l/n)) / (2 + cos(2 pi l/n)), plus a Neumann
+           eigenvalue of the other axis -- the mode sums at which the periodic
+           auxiliary's line matrices come close to singular.
+    The absorbing boundary keeps every problem solvable.  Right-hand sides are
     seeded complex Gaussians (seed + 1 + index)."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    smooth = [n for n in range(63, 1024) if _max_prime_factor(n) <= 64]
+
+    def closed(theta, h):
+        return 6.0 / h ** 2 * (1.0 - np.cos(theta)) / (2.0 + np.cos(theta))
+
     out = []
     for i in range(count):
         nx = int(rng.integers(63, 1024))
-        ny = int(smooth[int(rng.integers(0, len(smooth)))])
+        ny = int(rng.integers(63, 1024))
         hx = float(rng.uniform(0.5, 2.0)) / (nx - 1)
         hy = float(rng.uniform(0.5, 2.0)) / (ny - 1)
         ppw = float(rng.uniform(6.0, 20.0))
         omega = ppw_omega(max(hx, hy), ppw)
         note = ""
-        if i % 8 == 7:
-            def eig(n, h):
-                t = np.pi * np.arange(n) / (n - 1)
-                return 6.0 / h ** 2 * (1.0 - np.cos(t)) / (2.0 + np.cos(t))
-            sums = (eig(nx, hx)[:, None] + eig(ny, hy)[None, :]).ravel()
+        if i % 8 in (3, 7):
+            ex = closed(np.pi * np.arange(nx) / (nx - 1), hx)
+            if i % 8 == 7:
+                ey = closed(np.pi * np.arange(ny) / (ny - 1), hy)
+                note = "near resonance"
+            else:
+                ey = closed(2.0 * np.pi * np.arange(ny) / ny, hy)
+                note = "near periodic-mode resonance"
+            sums = (ex[:, None] + ey[None, :]).ravel()
             omega = float(np.sqrt(sums[np.argmin(np.abs(sums - omega ** 2))]))
-            note = "near resonance"
         out.append(Problem(name=f"batch2d_{i}", shape=(nx, ny), h=(hx, hy), omega=omega, seed=seed + 1 + i,
                            note=note))
     return out
@@ -125,21 +134,19 @@ def serve_3d(count: int = 32, operators: int = 12, rate_per_s: float = 4.0, seed
     `operators` box problems (domain-decomposition sweeps reuse one operator
     for many right-hand sides).
 
-    Per operator: nx uniform on {31..255}; ny, nz (the transform axes) uniform
-    on the values in {31..255} whose prime factors are all <= 64; side lengths
-    uniform on [0.5, 2] per axis; omega for a uniform 8..12 nodes per
-    wavelength at max(h).  Per request: an operator drawn uniformly from the
+    Per operator: nx, ny, nz uniform on {31..255}; side lengths uniform on
+    [0.5, 2] per axis; omega for a uniform 8..12 nodes per wavelength at
+    max(h).  Per request: an operator drawn uniformly from the
     pool, nrhs uniform on {1..64}, arrival after an exponential gap of mean
     1 / rate_per_s (rate_per_s <= 0: every request arrives at time 0, the
     saturated stream).  Returns [(Problem, nrhs, arrival_s)]; the right-hand
     sides are seeded complex Gaussians (Problem.seed)."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    smooth = [n for n in range(31, 256) if _max_prime_factor(n) <= 64]
     ops = []
     for k in range(operators):
         nx = int(rng.integers(31, 256))
-        ny = int(smooth[int(rng.integers(0, len(smooth)))])
-        nz = int(smooth[int(rng.integers(0, len(smooth)))])
+        ny = int(rng.integers(31, 256))
+        nz = int(rng.integers(31, 256))
         h = tuple(float(rng.uniform(0.5, 2.0)) / (n - 1) for n in (nx, ny, nz))
         omega = ppw_omega(max(h), float(rng.uniform(8.0, 12.0)))
         ops.append(((nx, ny, nz), h, omega))
