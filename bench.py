@@ -332,9 +332,13 @@ def run_gb300(args):
         if PATHS[path][1] is not None:
             helm.helm_set_refinement(plan.handle, REFINE_TOL, max(1, sweeps))
         helm.helm_set_profiling(plan.handle, True)
+        # an NVTX range around exactly these solves, so that an ncu launch
+        # list can take them alone (--nvtx --nvtx-include "profiled_solves/")
+        torch.cuda.nvtx.range_push("profiled_solves")
         for _ in range(PROFILE_SOLVES):
             helm.helm_solve(plan.handle, f, u)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         prof = helm.helm_get_profile(plan.handle)
         helm.helm_set_profiling(plan.handle, False)
         if PATHS[path][1] is not None:
@@ -361,7 +365,12 @@ def run_gb300(args):
             helm.helm_set_residual(plan.handle, kind)
             helm.helm_set_refinement(plan.handle, REFINE_TOL, 10)
         plan.variant = None
-        if len(p.shape) == 3 and not args.no_autotune:
+        if len(p.shape) == 3 and args.variant:
+            from paper_1809_03808_gb300 import tuning
+
+            plan.variant = [int(x) for x in args.variant.split(",")]
+            tuning.set_variant(plan, tuple(plan.variant))
+        elif len(p.shape) == 3 and not args.no_autotune:
             # the exhaustive autotuner: every variant of the tiled inner sweeps
             # timed on this plan, the fastest kept (plan time, not timed)
             from paper_1809_03808_gb300 import tuning
@@ -703,6 +712,47 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def summarize_launches(path, top=40):
+    """Per-kernel table of an ncu launch list (``ncu --metrics
+    gpu__time_duration.sum --csv --log-file PATH``): launches, total device
+    time and share of each kernel, template arguments kept, parameters
+    dropped.  Per-launch times under ncu are cold-cache and serialised, so
+    the shares are the comparable figure."""
+    import csv
+
+    scale = {"nsecond": 1e-6, "usecond": 1e-3, "msecond": 1.0, "second": 1e3}
+    with open(path, newline="") as fh:
+        lines = [ln for ln in fh if ln.startswith('"')]
+    rows = list(csv.reader(lines))
+    hdr = next(i for i, r in enumerate(rows) if "Kernel Name" in r and "Metric Value" in r)
+    col = {h: i for i, h in enumerate(rows[hdr])}
+    agg = {}
+    for r in rows[hdr + 1:]:
+        if len(r) < len(col) or r[col["Metric Name"]] != "gpu__time_duration.sum":
+            continue
+        name = r[col["Kernel Name"]]
+        name = name[5:] if name.startswith("void ") else name
+        for ns in ("(anonymous namespace)::", "<unnamed>::", "unnamed>::"):
+            name = name.replace(ns, "")
+        name = name.replace("(int)", "")
+        depth, cut = 0, len(name)
+        for i, ch in enumerate(name):  # drop the parameter list, keep template arguments
+            depth += ch == "<"
+            depth -= ch == ">"
+            if ch == "(" and depth == 0:
+                cut = i
+                break
+        name = name[:cut]
+        ms = float(r[col["Metric Value"]].replace(",", "")) * scale.get(r[col["Metric Unit"]], 1e-6)
+        n, t = agg.get(name, (0, 0.0))
+        agg[name] = (n + 1, t + ms)
+    total = sum(t for _, t in agg.values())
+    print(f"{'kernel':<58} {'launches':>8} {'total ms':>10} {'share':>7}")
+    for name, (n, t) in sorted(agg.items(), key=lambda kv: -kv[1][1])[:top]:
+        print(f"{name[:58]:<58} {n:>8} {t:>10.3f} {100 * t / total:>6.1f}%")
+    print(f"{'all kernels':<58} {sum(n for n, _ in agg.values()):>8} {total:>10.3f} {100.0:>6.1f}%")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -716,6 +766,9 @@ def main():
                     "(profiling cases; not a benchmark line)")
     ap.add_argument("--minimal", action="store_true", help="timed solves only (no e2e, variants, CPU baseline)")
     ap.add_argument("--no-autotune", action="store_true", help="3D: keep the default kernel variant")
+    ap.add_argument("--variant", default="", metavar="CH,NMB",
+                    help="3D: take this variant of the tiled inner sweeps (rows per chunk, tiles per CTA) "
+                    "instead of autotuning")
     ap.add_argument("--batch-count", type=int, default=512, help="problems of --workload batch2d")
     ap.add_argument("--workload", default="3d", choices=["2d_large", "3d", "batch2d", "serve3d"],
                     help="3d: the 512^3 workload (the bench line); 2d_large: the 8192 x 4096 workload; "
@@ -729,7 +782,12 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="plan-cache device budget (serve3d)")
     ap.add_argument("--path", default="c64_refined", choices=list(PATHS_NAMES),
                     help="path timed as the main line (the others are reported as variants)")
+    ap.add_argument("--summarize-launches", default="", metavar="CSV",
+                    help="print the per-kernel table of an ncu launch list and exit (no GPU needed)")
     args = ap.parse_args()
+    if args.summarize_launches:
+        summarize_launches(args.summarize_launches)
+        return
     if args.minimal:
         args.no_e2e = args.no_variants = args.no_cpu_baseline = True
     if args.warmup < 3 and args.impl == "gb300":

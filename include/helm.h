@@ -230,8 +230,11 @@ int helm_set_graphs(helm_plan_t p, int enable);
 /* --- Solve (Sections 4.2 and 5.2: Steps 1-3) ------------------------------
  * f, u: DEVICE pointers to N = nx*ny(*nz) complex values in the layout above
  * (complex128 or complex64 per dtype).  f is read only, u is overwritten.
- * The byte ranges [f, f + N*elem) and [u, u + N*elem) must be disjoint:
- * any shared byte returns HELM_EINVAL before the device is touched.
+ * The byte ranges [f, f + N*elem) and [u, u + N*elem) must be disjoint, and
+ * f and u must be multiples of elem (16 B complex128, 8 B complex64): a
+ * shared byte or a misaligned pointer returns HELM_EINVAL before the device
+ * is touched.  (The same rules hold for every entry point below that takes
+ * f and u.)
  * Asynchronous on the plan's stream: returns after enqueueing.  Allocates
  * nothing (all scratch belongs to the plan).  Convergence of refinement is
  * reported by helm_get_info. */
@@ -343,8 +346,8 @@ int helm_batch_destroy(helm_batch_t b);
  * scratch is one fixed 16 MiB array that the library reserves on every GPU
  * that loads it, held until the process exits.
  *   f, u: DEVICE pointers, complex128, [nx][ny] as for helm_solve; f read
- *         only, u overwritten; their byte ranges must be disjoint
- *         (HELM_EINVAL otherwise).
+ *         only, u overwritten; their byte ranges must be disjoint and
+ *         both must be 16-byte aligned (HELM_EINVAL otherwise).
  *   cuda_stream: stream the work is enqueued on (NULL = legacy default
  *         stream); asynchronous like helm_solve.
  * Limits: ny <= 1024, and about 47 bytes per unknown plus O(nx + ny) must

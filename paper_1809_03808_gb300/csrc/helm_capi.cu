@@ -461,7 +461,7 @@ int refine_check(helm_plan* p, const void* f, const void* u, unsigned long long 
                                               &nblocks, skip, p->stream));
   else
     HELM_PK("residual_fp64", launch_residual(p->dim, p->n, p->h, p->omega, p->wc, (const double2*)f, (const double2*)u,
-                                             p->rbuf, p->sums, &nblocks, skip, p->stream));
+                                             p->rbuf, p->sums, &nblocks, skip, p->stream, p->dev_err));
   HELM_PK("residual_finalize", launch_residual_finalize(p->sums, nblocks, p->state, cond, p->stream));
   return HELM_OK;
 }
@@ -671,6 +671,16 @@ bool overlaps(const void* a, const void* b, size_t bytes) {
   const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
   return x < y + bytes && y < x + bytes;
 }
+
+// f and u of a solve: overlapping ranges, or an address that is not a
+// multiple of the element size (16 B complex128, 8 B complex64), which the
+// kernels' vector loads and stores need.
+bool bad_pair(const void* f, const void* u, size_t bytes, size_t elem) {
+  const uintptr_t m = (uintptr_t)(elem - 1);
+  return overlaps(f, u, bytes) || ((uintptr_t)f & m) || ((uintptr_t)u & m);
+}
+
+size_t plan_elem_bytes(const helm_plan* p) { return p->dtype == HELM_C64_RAW ? sizeof(float2) : sizeof(double2); }
 
 // The plan's stream and its workspace streams have finished their work (the
 // tables they read may be rebuilt or freed after this).
@@ -975,12 +985,12 @@ int tune_auxiliary(helm_plan* p) {
     if ((rc = apply_aux(p, c.rho, c.q))) break;
     if ((rc = solve_core(p, tf, kInC128, tu, kOutC128, 0.0, nullptr, nullptr, nullptr, nullptr))) break;
     int64_t nb = 0;
-    cudaError_t e = launch_residual(p->dim, p->n, p->h, p->omega, p->wc, tf, tu, tr, ts, &nb, nullptr, nullptr);
+    cudaError_t e = launch_residual(p->dim, p->n, p->h, p->omega, p->wc, tf, tu, tr, ts, &nb, nullptr, nullptr, p->dev_err);
     if (e == cudaSuccess && p->dtype == HELM_C64_REFINED) {
       // refined plans: one correction sweep as well, so that the residual
       // measures the contraction of the sweeps, not only the first solve
       if ((rc = solve_core(p, tr, kInC64, tu, kOutAccumC128, 1.0, nullptr, nullptr, nullptr, nullptr))) break;
-      e = launch_residual(p->dim, p->n, p->h, p->omega, p->wc, tf, tu, tr, ts, &nb, nullptr, nullptr);
+      e = launch_residual(p->dim, p->n, p->h, p->omega, p->wc, tf, tu, tr, ts, &nb, nullptr, nullptr, p->dev_err);
     }
     if (e == cudaSuccess) e = cudaMemcpy(hs.data(), ts, nb * 2 * sizeof(double), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) {
@@ -1388,7 +1398,7 @@ int helm_set_graphs(helm_plan_t p, int enable) {
 }
 
 int helm_solve(helm_plan_t p, const void* f, void* u) {
-  if (!p || !f || !u || overlaps(f, u, plan_vec_bytes(p))) return HELM_EINVAL;
+  if (!p || !f || !u || bad_pair(f, u, plan_vec_bytes(p), plan_elem_bytes(p))) return HELM_EINVAL;
   p->last_many = 0;
   return run_solve(p, f, u, nullptr, nullptr, nullptr);
 }
@@ -1402,7 +1412,7 @@ int helm_set_rhs_concurrency(helm_plan_t p, int k) {
 int helm_solve_many(helm_plan_t p, int64_t nrhs, const void* f, void* u) {
   if (!p || p->parent || nrhs < 1 || !f || !u) return HELM_EINVAL;
   const size_t vb = plan_vec_bytes(p);
-  if (overlaps(f, u, vb * (size_t)nrhs)) return HELM_EINVAL;
+  if (bad_pair(f, u, vb * (size_t)nrhs, plan_elem_bytes(p))) return HELM_EINVAL;
   p->last_many = 0;
   if (nrhs == 1) return run_solve(p, f, u, nullptr, nullptr, nullptr);
   int k = (int)std::min<int64_t>(nrhs, p->rhs_concurrency);
@@ -1460,7 +1470,7 @@ int helm_solve_many(helm_plan_t p, int64_t nrhs, const void* f, void* u) {
 }
 
 int helm_solve_debug(helm_plan_t p, const void* f, void* u, void* fhat, void* v_b, void* w_b) {
-  if (!p || !f || !u || overlaps(f, u, plan_vec_bytes(p))) return HELM_EINVAL;
+  if (!p || !f || !u || bad_pair(f, u, plan_vec_bytes(p), plan_elem_bytes(p))) return HELM_EINVAL;
   return run_solve(p, f, u, fhat, v_b, w_b);
 }
 
@@ -1480,7 +1490,7 @@ void* mapped_host(const void* h) {
 }  // namespace
 
 int helm_solve_host(helm_plan_t p, const void* f_host, void* u_host) {
-  if (!p || !f_host || !u_host || overlaps(f_host, u_host, plan_vec_bytes(p))) return HELM_EINVAL;
+  if (!p || !f_host || !u_host || bad_pair(f_host, u_host, plan_vec_bytes(p), plan_elem_bytes(p))) return HELM_EINVAL;
   const int64_t N = p->n[0] * p->n[1] * p->n[2];
   const size_t eb = p->dtype == HELM_C64_RAW ? sizeof(float2) : sizeof(double2);
   int rc;
@@ -1593,7 +1603,7 @@ int helm_batch_solve(helm_batch_t b, const void* const* f, void* const* u) {
   const size_t n = b->plans.size();
   for (size_t i = 0; i < n; ++i) {
     helm_plan* p = b->plans[i];
-    if (!f[i] || !u[i] || overlaps(f[i], u[i], plan_vec_bytes(p))) return HELM_EINVAL;
+    if (!f[i] || !u[i] || bad_pair(f[i], u[i], plan_vec_bytes(p), plan_elem_bytes(p))) return HELM_EINVAL;
     if (p->prof.on) return HELM_EINVAL;  // event timing cannot live inside the graph
     if (p->dtype == HELM_C64_REFINED && refine_ff(p) && !p->ffb) return HELM_EINVAL;  // kind changed after create
   }
@@ -1732,7 +1742,7 @@ int helm_solve_2d_static(int64_t nx, int64_t ny, double hx, double hy, double om
     cur += sizes[i];
   }
   if (cur > kStaticScratchBytes) return HELM_EUNSUPPORTED;
-  if (overlaps(f, u, (size_t)N * sizeof(double2))) return HELM_EINVAL;
+  if (bad_pair(f, u, (size_t)N * sizeof(double2), sizeof(double2))) return HELM_EINVAL;
   // set-up once per device, with that device current: the device address of
   // the static array (the host-side symbol is not a device pointer)
   if (!g_static_addr[dev]) {

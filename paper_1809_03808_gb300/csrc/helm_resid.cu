@@ -5,9 +5,13 @@
 // - w^2 prod_k M_k(i_k, i_k + d_k), with X^{(j)}_k = K_k if k == j else M_k
 // (1D matrices of eqs. matrixK / matrixM).  Interior points use precomputed
 // real coefficients; points on a face use the complex corner entries.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <complex>
 
+#include "helm_async.cuh"
 #include "helm_kernels.cuh"
 #include "helm_solve.h"
 
@@ -237,6 +241,162 @@ __global__ void __launch_bounds__(QZ* QY) k_residual3d_q(ResidQArgs a, const dou
     Qc = Qn;
   }
   block_norms<QZ * QY>(r2f, f2f, sums, ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+}
+
+// The same 3D residual with the u planes brought in by the tensor memory
+// accelerator: one thread issues a tiled load of the plane's (QY+2) x (QZ+2)
+// halo box, whose parts outside the grid arrive as zeros, so the staging
+// needs no per-thread index or bounds arithmetic and no registers.  Three
+// plane buffers: while plane i is used, planes i+1 and i+2 are in flight; the
+// z sums are double-buffered, so one barrier per plane separates every reuse.
+// Every wait is bounded: a copy that does not arrive sets *err, the whole CTA
+// stops, and thread 0 lets its copies still in flight land before it exits.
+constexpr int QUB = (QY + 2) * (QZ + 2) * (int)sizeof(double2);  // bytes of one staged plane
+constexpr int QUS = (QUB + 127) / 128 * 128;                      // its stride (TMA destinations: 128 B)
+constexpr int QNB = 3;                                            // plane buffers
+
+__global__ void __launch_bounds__(QZ* QY, 2)
+    k_residual3d_tma(const __grid_constant__ CUtensorMap umap, ResidQArgs a, const double2* __restrict__ f,
+                     float2* __restrict__ r, double* __restrict__ sums, const int* __restrict__ skip, int* err) {
+  if (skip && *skip) return;
+  __shared__ __align__(128) unsigned char sUb[QNB * QUS];
+  __shared__ double2 sSz[2][QY + 2][QZ];
+  __shared__ __align__(8) uint64_t bar[QNB];
+  const int64_t nx = a.n[0], ny = a.n[1], nz = a.n[2];
+  const int tz = threadIdx.x, ty = threadIdx.y, tid = ty * QZ + tz;
+  const int64_t z0 = (int64_t)blockIdx.x * QZ, y0 = (int64_t)blockIdx.y * QY;
+  const int64_t xs = (int64_t)blockIdx.z * QX, xe = min(xs + QX, nx);
+  const int np = (int)(xe - xs + 2);  // planes xs-1 .. xe (at least 3)
+  const int64_t gz = z0 + tz, gy = y0 + ty;
+  const bool own = gz < nz && gy < ny;
+  const int cy = (gy == 0 || gy == ny - 1) ? 1 : 0, cz = (gz == 0 || gz == nz - 1) ? 1 : 0;
+  const int cyz = 2 * cy + cz;
+  const double2 zero = make_double2(0.0, 0.0);
+  float r2f = 0.f, f2f = 0.f;
+  if (tid == 0) {
+    for (int b = 0; b < QNB; ++b) mbar_init(&bar[b], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  // plane xs - 1 + i into buffer i % QNB (thread 0 only)
+  auto issue = [&](int i) {
+    const int b = i % QNB;
+    mbar_arrive_expect_tx(&bar[b], (uint32_t)QUB);
+    tma_load_3d(sUb + b * QUS, &umap, (int)(2 * (z0 - 1)), (int)(y0 - 1), (int)(xs - 1 + i), &bar[b]);
+  };
+  int issued = 0;
+  if (tid == 0) {
+    issue(0);
+    issue(1);
+    issued = 2;
+  }
+  double2 Rm = zero, Rc = zero, Qc = zero;  // R(x-2), R(x-1), f - Q at x-1
+  int i = 0;
+  bool failed = false;
+  for (; i < np; ++i) {
+    const int64_t ip = xs - 1 + i;
+    const double2* U = reinterpret_cast<const double2*>(sUb + (i % QNB) * QUS);  // [QY+2][QZ+2]
+    double2(*Sz)[QZ] = sSz[i & 1];
+    const bool outp = own && ip >= xs && ip < xe;
+    double2 fv = zero;
+    if (outp) fv = __ldg(&f[(ip * ny + gy) * nz + gz]);
+    const bool got = mbar_wait_bounded(&bar[i % QNB], (uint32_t)((i / QNB) & 1), err);
+    for (int e = tid; e < (QY + 2) * QZ; e += QZ * QY) {
+      const int yy = e / QZ, zc = e - yy * QZ;
+      const double2 lo = U[yy * (QZ + 2) + zc], hi = U[yy * (QZ + 2) + zc + 2];
+      Sz[yy][zc] = make_double2(lo.x + hi.x, lo.y + hi.y);
+    }
+    if (__syncthreads_or(!got)) {  // block-uniform
+      failed = true;
+      break;
+    }
+    // every thread is past plane i - 1: its buffer takes plane i + 2
+    if (tid == 0 && i + 2 < np) {
+      issue(i + 2);
+      issued = i + 3;
+    }
+    double2 Rn = zero, Qn = fv;
+    if (own && ip >= 0 && ip < nx) {
+      const double2 P00 = U[(ty + 1) * (QZ + 2) + tz + 1], P01 = Sz[ty + 1][tz];
+      const double2 ym = U[ty * (QZ + 2) + tz + 1], yp = U[(ty + 2) * (QZ + 2) + tz + 1];
+      const double2 sm = Sz[ty][tz], sp = Sz[ty + 2][tz];
+      const double2 P10 = make_double2(ym.x + yp.x, ym.y + yp.y), P11 = make_double2(sm.x + sp.x, sm.y + sp.y);
+      const int cx = (ip == 0 || ip == nx - 1) ? 1 : 0;
+      Rn.x = fma(a.c1[0][3].x, P11.x, fma(a.c1[0][2].x, P10.x, fma(a.c1[0][1].x, P01.x, a.c1[0][0].x * P00.x)));
+      Rn.y = fma(a.c1[0][3].x, P11.y, fma(a.c1[0][2].x, P10.y, fma(a.c1[0][1].x, P01.y, a.c1[0][0].x * P00.y)));
+      if (outp) {
+        if (cx == 0) {
+          Qn.x = fma(-a.c0[0][3].x, P11.x, fma(-a.c0[0][2].x, P10.x, fma(-a.c0[0][1].x, P01.x, fma(-a.c0[0][0].x, P00.x, Qn.x))));
+          Qn.y = fma(-a.c0[0][3].x, P11.y, fma(-a.c0[0][2].x, P10.y, fma(-a.c0[0][1].x, P01.y, fma(-a.c0[0][0].x, P00.y, Qn.y))));
+        } else {
+          csub_mul(Qn, a.c0[4][0], P00);
+          csub_mul(Qn, a.c0[4][1], P01);
+          csub_mul(Qn, a.c0[4][2], P10);
+          csub_mul(Qn, a.c0[4][3], P11);
+        }
+      }
+      if (cyz) {
+        if (cy | cz) cadd_mul(Rn, a.dc1[cyz][0], P00);
+        if (cy) cadd_mul(Rn, a.dc1[cyz][1], P01);
+        if (cz) cadd_mul(Rn, a.dc1[cyz][2], P10);
+        if (outp) {
+          const int cls = 4 * cx + cyz;
+          if (cy | cz) csub_mul(Qn, a.dc0[cls][0], P00);
+          if (cy) csub_mul(Qn, a.dc0[cls][1], P01);
+          if (cz) csub_mul(Qn, a.dc0[cls][2], P10);
+        }
+      }
+    }
+    const int64_t ix = ip - 1;
+    if (own && ix >= xs && ix < xe) {
+      const float2 rf = make_float2(round_d2f(Qc.x - Rm.x - Rn.x), round_d2f(Qc.y - Rm.y - Rn.y));
+      r[(ix * ny + gy) * nz + gz] = rf;
+      r2f = fmaf(rf.x, rf.x, fmaf(rf.y, rf.y, r2f));
+    }
+    if (outp) {
+      const float fx = round_d2f(fv.x), fy = round_d2f(fv.y);
+      f2f = fmaf(fx, fx, fmaf(fy, fy, f2f));
+    }
+    Rm = Rc;
+    Rc = Rn;
+    Qc = Qn;
+  }
+  if (failed && tid == 0)
+    for (int j = i; j < issued; ++j) mbar_wait_bounded(&bar[j % QNB], (uint32_t)((j / QNB) & 1), nullptr);
+  block_norms<QZ * QY>(r2f, f2f, sums, ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+}
+
+// The driver's tensor-map encoder, looked up once through the runtime (no
+// link-time dependence on the driver library); null if unavailable.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* q = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &q, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
+        qr != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      q = nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(q);
+  }();
+  return fn;
+}
+
+// Tensor map of u ([nx][ny][nz] complex128 viewed as [nx][ny][2 nz] FP64)
+// with the residual's halo box; false if it cannot be made (the caller then
+// stages the planes with plain loads).
+bool residual_umap(CUtensorMap* m, const double2* u, const int64_t* n) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || ((uintptr_t)u & 15) || 2 * n[2] > (int64_t)UINT32_MAX || n[1] > (int64_t)UINT32_MAX ||
+      n[0] > (int64_t)INT32_MAX - 2)
+    return false;
+  const cuuint64_t gdim[3] = {(cuuint64_t)(2 * n[2]), (cuuint64_t)n[1], (cuuint64_t)n[0]};
+  const cuuint64_t gstride[2] = {(cuuint64_t)(2 * n[2] * sizeof(double)), (cuuint64_t)(n[1] * 2 * n[2] * sizeof(double))};
+  const cuuint32_t box[3] = {2 * (QZ + 2), QY + 2, 1};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<double2*>(u), gdim, gstride, box, estride,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // 2D: thread per y column, QR2 rows rolling along x; monomials P_0 = u,
@@ -738,7 +898,7 @@ __global__ void __launch_bounds__(1024) k_residual_finalize(const double* __rest
 cudaError_t launch_residual(int dim, const int64_t* n, const double* h, double omega, const double* wc,
                             const double2* f,
                             const double2* u, float2* r, double* sums, int64_t* nblocks, const int* skip,
-                            cudaStream_t st) {
+                            cudaStream_t st, int* err) {
   const int bs = 256;
   if (dim == 2 || dim == 3) {
     // monomial coefficients by end class (see the FP64-instruction-lean kernels)
@@ -771,7 +931,9 @@ cudaError_t launch_residual(int dim, const int64_t* n, const double* h, double o
         }
       const dim3 grid((unsigned)((n[2] + QZ - 1) / QZ), (unsigned)((n[1] + QY - 1) / QY), (unsigned)((n[0] + QX - 1) / QX));
       *nblocks = (int64_t)grid.x * grid.y * grid.z;
-      k_residual3d_q<<<grid, dim3(QZ, QY), 0, st>>>(q, f, u, r, sums, skip);
+      CUtensorMap um;
+      if (residual_umap(&um, u, n)) k_residual3d_tma<<<grid, dim3(QZ, QY), 0, st>>>(um, q, f, r, sums, skip, err);
+      else k_residual3d_q<<<grid, dim3(QZ, QY), 0, st>>>(q, f, u, r, sums, skip);
       return cudaGetLastError();
     }
     for (int cx = 0; cx < 2; ++cx)

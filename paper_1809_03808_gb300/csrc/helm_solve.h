@@ -86,11 +86,12 @@ struct RefineState {
 // r = f - A u in FP64 (eq. A2D / A3D), r stored as complex64, per-block sums
 // of |r|^2 and |f|^2 into `sums` (2 doubles per block).  Returns the number of
 // blocks used through *nblocks.
-// wc[k]: w of the absorbing ends of axis k (0 on a Neumann axis).
+// wc[k]: w of the absorbing ends of axis k (0 on a Neumann axis).  err: the
+// device error word set if a bounded wait of the 3D kernel runs out.
 cudaError_t launch_residual(int dim, const int64_t* n, const double* h, double omega, const double* wc,
                             const double2* f,
                             const double2* u, float2* r, double* sums, int64_t* nblocks, const int* skip,
-                            cudaStream_t st);
+                            cudaStream_t st, int* err);
 // The same residual with f and u as float-float complex vectors (float4 per
 // point: re_hi, im_hi, re_lo, im_lo), about 48 significant bits, computed on
 // the FP32 pipes.  Same grid and sums layout as launch_residual.

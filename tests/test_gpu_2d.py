@@ -219,6 +219,32 @@ def test_overlapping_buffers_rejected(env):
     plan.close()
 
 
+def test_misaligned_buffers_rejected(env):
+    """f or u not on a multiple of the element size (16 B complex128, 8 B
+    complex64) is rejected with HELM_EINVAL by every solve entry point, before
+    any kernel runs."""
+    helm, torch = env
+    shape, h, omega = CASES["tiny_9x7"]
+    N = shape[0] * shape[1]
+    buf = torch.zeros(4 * N, dtype=torch.complex128, device="cuda")
+    p = buf.data_ptr()
+    for code, es in ((helm.HELM_C128, 16), (helm.HELM_C64_REFINED, 16), (helm.HELM_C64_RAW, 8)):
+        plan = helm.Plan(shape, h, omega, code)
+        f, u = p, p + 2 * N * 16
+        for ff, uu in ((f + es // 2, u), (f, u + es // 2), (f + 4, u + 4)):
+            assert helm.lib.helm_solve(plan.handle, ff, uu) == helm.HELM_EINVAL
+            assert helm.lib.helm_solve_debug(plan.handle, ff, uu, None, None, None) == helm.HELM_EINVAL
+            assert helm.lib.helm_solve_many(plan.handle, 2, ff, uu) == helm.HELM_EINVAL
+        # a multiple of the element size is fine
+        assert helm.lib.helm_solve(plan.handle, f + es, u + es) == helm.HELM_OK
+        torch.cuda.synchronize()
+        plan.close()
+    fh = np.zeros(4 * N, dtype=np.complex128)
+    plan = helm.Plan(shape, h, omega, helm.HELM_C128)
+    assert helm.lib.helm_solve_host(plan.handle, fh.ctypes.data + 8, fh.ctypes.data + 2 * N * 16) == helm.HELM_EINVAL
+    plan.close()
+
+
 def test_set_residual_validation(env):
     helm, torch = env
     shape, h, omega = CASES["tiny_9x7"]

@@ -98,3 +98,51 @@ def test_many_argument_checks(env):
     assert helm.lib.helm_solve_many(plan.handle, 3, p, p + 3 * N * 16) == helm.HELM_OK
     torch.cuda.synchronize()
     plan.close()
+
+
+MANY_TIMING = [((64, 64, 64), (1.0, 1.0, 1.0), 10, "c64_refined"), ((96, 80, 72), (1.2, 1.0, 0.9), 10, "c64_ff"),
+               ((257, 257), (1.0, 1.0), 10, "c64_refined"), ((48, 48, 48), (1.0, 1.0, 1.0), 8, "c128")]
+
+
+@pytest.mark.parametrize("case", MANY_TIMING)
+def test_many_cheaper_than_single_solves(env, case):
+    """64 right-hand sides of one serving-size operator: helm_solve_many
+    (right-hand sides spread over concurrent workspaces) against 64
+    helm_solve calls one after another, both timed with CUDA events on the
+    caller's stream after a warm-up."""
+    helm, torch = env
+    shape, lengths, ppw, mode = case
+    shape, h, omega = _problem(shape, lengths, ppw)
+    nrhs = 64
+    f = torch.from_numpy(np.stack([random_rhs(shape, 500 + j) for j in range(nrhs)])).cuda()
+    u = torch.empty_like(f)
+    plan = _plan(helm, shape, h, omega, mode)
+    if mode != "c128":
+        helm.helm_set_refinement(plan.handle, 2e-11, 10)
+    s = torch.cuda.current_stream()
+    helm.helm_set_stream(plan.handle, s.cuda_stream)
+
+    def singles():
+        for j in range(nrhs):
+            helm.helm_solve(plan.handle, f[j], u[j])
+
+    def many():
+        helm.helm_solve_many(plan.handle, nrhs, f, u)
+
+    times = {}
+    for name, fn in (("single", singles), ("many", many)):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(2):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1) / 2
+    info, st = plan.info()
+    assert st == helm.HELM_OK
+    print(f"MANY {shape} {mode}: 64 single solves {times['single']:.2f} ms, helm_solve_many {times['many']:.2f} ms "
+          f"({times['many'] / times['single']:.2f}x)")
+    plan.close()
+    assert times["many"] < times["single"]

@@ -111,3 +111,14 @@ def test_static_solve_rejects_overlap(env):
     p = buf.data_ptr()
     st = helm.lib.helm_solve_2d_static(nx, ny, 0.1, 0.1, 5.0, p, p + (nx * ny - 1) * 16, None)
     assert st == helm.HELM_EINVAL
+
+
+def test_static_solve_rejects_misaligned(env):
+    """f or u off a 16-byte boundary is rejected before any device work."""
+    helm, torch = env
+    nx, ny = 9, 7
+    buf = torch.zeros(4 * nx * ny, dtype=torch.complex128, device="cuda")
+    p = buf.data_ptr()
+    u = p + 2 * nx * ny * 16
+    assert helm.lib.helm_solve_2d_static(nx, ny, 0.1, 0.1, 5.0, p + 8, u, None) == helm.HELM_EINVAL
+    assert helm.lib.helm_solve_2d_static(nx, ny, 0.1, 0.1, 5.0, p, u + 8, None) == helm.HELM_EINVAL
