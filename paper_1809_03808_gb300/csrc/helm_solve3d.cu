@@ -638,7 +638,13 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
   int* sR = sL + kMW;                                    // [kMW] 1: routed to FP64
   const int64_t l = blockIdx.y;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int mi = tid & (kMW - 1), c = tid / kMW;
+  // thread (mi, c): the two half-warps of warp w take chunks w and nc-1-w, so
+  // that the first and the last chunk of a line (never settled: the first
+  // rows and the corner row) share a warp; with nc odd the middle warp's
+  // second half idles
+  const int mi = tid & (kMW - 1), wk = tid / (2 * kMW), half = (tid / kMW) & 1;
+  const int c = half ? nc - 1 - wk : wk;
+  const bool cok = half ? (nc - 1 - wk > wk) : (wk < nc);
   const int64_t xs = ny * nz;
   if (tid == 0) {
     // outer-mode constants: 1/mu_l (outer B modes), e^{+i theta_l} e^{-t(ny-1)}, parity (outer A modes)
@@ -740,7 +746,7 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
     }
     // ---- line constants of thread (mi, c) ----
     const int64_t m = m0 + mi;
-    const bool act = m < nz && c < nc;
+    const bool act = m < nz && cok;
     const C b = lc[mi], iinf = lc[kMW + mi], ilast = lc[2 * kMW + mi];
     const C nb = mk<C>(-b.x, -b.y);
     const int L = sL[mi];  // 0 for a routed line
@@ -757,7 +763,9 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
     // x_loc.  alpha_e = prod (-b/u_j) and beta = sum alpha_{j-1} alpha_j do
     // not depend on the data: a chunk of settled rows takes them from the
     // plan, the others (rows with tabulated pivots, the corner row) form them.
-    const bool settled = s0 >= L && e0 < nx - 1 && e0 - s0 + 1 == ch;
+    // warp-uniform: a warp takes the settled path only if all its chunks
+    // are settled (the general path is exact for settled rows too)
+    const bool settled = __all_sync(0xffffffffu, !act || (s0 >= L && e0 < nx - 1 && e0 - s0 + 1 == ch));
     if (act) {
       C d = mk<C>(0, 0), al = mk<C>(1, 0), be = mk<C>(0, 0);
       if (settled) {
@@ -881,7 +889,9 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
         for (int k = 0; k < kMW; ++k) {
           const int mm = (k + x) & (kMW - 1);
           const C v = tile[x * kMW + mm];
-          s1 = cadd(s1, cmul(v, mw[2 * kMW + mm]));
+          // Step 1's first-row weight is 1 (modes off the grid or routed
+          // hold zeros in the tile)
+          s1 = cadd(s1, ISTEP == 1 ? v : cmul(v, mw[2 * kMW + mm]));
           sn = cadd(sn, cmul(v, mw[3 * kMW + mm]));
         }
         facc[x] = cadd(facc[x], s1);
