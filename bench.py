@@ -224,6 +224,11 @@ NCU_TRAFFIC_PER_UNKNOWN = {
         (546.5e6 + 118.0e6 + 2.5e6) / (4096 * 4096),
         "ncu --set full, 4096 x 4096: k_residual2d_ff + k_perimeter2d_ff "
         "(profiles/ncu_2d_kernels_4096x4096.md)"),
+    # DRAM bytes of one k_residual3d_tma launch on 256^3 (same spacing and wave
+    # number), per unknown; the traffic of a launch is proportional to them
+    ("3d", "c64_refined", "residual_fp64"): (
+        (569.948416e6 + 118.337536e6) / 256 ** 3,
+        "ncu --set full, 256^3: k_residual3d_tma (profiles/ncu_residual3d_tma_256cube.md), scaled by unknowns"),
 }
 
 

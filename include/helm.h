@@ -178,13 +178,25 @@ int helm_set_precision_routing(helm_plan_t p, double tau);
 /* Kernel variants (the autotuner's choices; the paper fixes none of them).
  * Every variant computes the same solution; they differ in speed by grid.
  *   HELM_VARIANT_INNER_CHUNK  3D: rows per chunk of the tiled inner sweeps
- *                             (4..64; default 16, more for lines beyond 1024
- *                             rows).
+ *                             (8, 16 or 32; default 16, 32 for lines beyond
+ *                             1024 rows, 512 in complex128).
  *   HELM_VARIANT_INNER_TILES  3D: tiles of 16 inner modes per CTA (1..8;
  *                             default 1..4 by grid size).
  *   HELM_VARIANT_TRI2D        2D complex64: 0 = bulk-copy fed passes where
  *                             the x1 length is even (default), 1 = register-
  *                             tile passes.
+ *   HELM_VARIANT_DFT          complex64 plans whose contiguous transformed
+ *                             axis (x1 in 2D, the inner axis in 3D) has at
+ *                             most 128 nodes: 0 = FFT kernels (default), 1 =
+ *                             that axis's transforms as dense products with
+ *                             the scaled DFT matrix on the tensor cores
+ *                             (TF32 with high/low splitting of both operands,
+ *                             FP32 accumulation: 22-bit operands, so a raw
+ *                             complex64 solve is up to ~15x less accurate
+ *                             than with the FFT kernels at n = 128;
+ *                             refinement removes the difference); the
+ *                             matrix tables (2 x 8 (2n)^2 bytes at most) are
+ *                             built when it is switched on.
  * helm_set_variant returns HELM_EUNSUPPORTED for a knob the plan does not
  * have, HELM_EINVAL for a value that does not fit.  Call between solves.
  * helm_time_solve: device milliseconds of one solve of the plan's compute
@@ -194,7 +206,8 @@ int helm_set_precision_routing(helm_plan_t p, double tau);
 enum helm_variant {
   HELM_VARIANT_INNER_CHUNK = 0,
   HELM_VARIANT_INNER_TILES = 1,
-  HELM_VARIANT_TRI2D = 2
+  HELM_VARIANT_TRI2D = 2,
+  HELM_VARIANT_DFT = 3
 };
 int helm_set_variant(helm_plan_t p, int knob, int value);
 int helm_get_variant(helm_plan_t p, int knob, int* value);

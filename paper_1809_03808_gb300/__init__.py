@@ -25,7 +25,7 @@ lib = ctypes.CDLL(_LIB_PATH)
 HELM_C128, HELM_C64_REFINED, HELM_C64_RAW = 0, 1, 2
 HELM_RESID_FP64, HELM_RESID_FF = 0, 1
 HELM_BC_ABC, HELM_BC_NEUMANN = 0, 1
-HELM_VARIANT_INNER_CHUNK, HELM_VARIANT_INNER_TILES, HELM_VARIANT_TRI2D = 0, 1, 2
+HELM_VARIANT_INNER_CHUNK, HELM_VARIANT_INNER_TILES, HELM_VARIANT_TRI2D, HELM_VARIANT_DFT = 0, 1, 2, 3
 HELM_OK, HELM_EINVAL, HELM_ENOMEM, HELM_ECUDA, HELM_ENOTCONV, HELM_ETIMEOUT, HELM_EUNSUPPORTED, HELM_ENUMERIC = \
     0, -1, -2, -3, -4, -5, -6, -7
 

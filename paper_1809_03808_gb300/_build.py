@@ -13,7 +13,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhelm.so")
 
-CUDA_SOURCES = ["helm_dft.cu", "helm_dft_pow2.cu", "helm_solve2d.cu", "helm_solve3d.cu", "helm_resid.cu", "helm_capi.cu",
+CUDA_SOURCES = ["helm_dft.cu", "helm_dft_pow2.cu", "helm_dft_tc.cu", "helm_solve2d.cu", "helm_solve3d.cu", "helm_resid.cu", "helm_capi.cu",
                 "helm_mlp.cu"]
 CXX_SOURCES = ["helm_eigen.cpp", "helm_server.cpp", "helm_alloc.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -87,6 +87,7 @@ struct helm_plan {
   std::vector<cudaEvent_t> ws_done;
   cudaEvent_t fork = nullptr;
   int rhs_concurrency = 4;
+  int dft_gemm = 0;  // HELM_VARIANT_DFT: row transforms on the tensor cores
   int tri_regs = 0;  // 2D complex64: register-tile passes (variant HELM_VARIANT_TRI2D = 1)
   int last_many = 0;  // workspaces used by the last helm_solve_many (0: none)
 };
@@ -151,7 +152,57 @@ void free_axis(AxisData& a) {
   dfree(a.tw);
   dfree(a.tw32);
   for (void* q : a.bs) dfree(q);
+  for (float* q : a.gemm) dfree(q);
   a = AxisData{};
+}
+
+void free_dft_gemm(helm_plan* p, AxisData& a) {
+  for (float*& q : a.gemm) {
+    if (q) p->bytes -= dft_gemm_table_floats(a.n) * sizeof(float);
+    dfree(q);
+    q = nullptr;
+  }
+  a.dft.gw[0] = a.dft.gw[1] = nullptr;
+  a.dft.gsc[0] = a.dft.gsc[1] = nullptr;
+}
+
+// Tables of the tensor-core transform of axis a (complex64 plans, lines of
+// at most 128 points): forward W[j][k] = s_j e^{-2 pi i jk/n} with the input
+// scaling s = e^{-t j}, inverse W[k][j] = (1/n) e^{+2 pi i jk/n} d_j with the
+// output scaling d = e^{+t j} (eqs. step1FFTfcoeff, step3IFFTz3coeff with
+// the auxiliary's D^-1, D folded in), in FP64 on the host.
+int build_dft_gemm(helm_plan* p, AxisData& a) {
+  free_dft_gemm(p, a);
+  const int64_t n = a.n;
+  if (!dft_gemm_supported(n)) return HELM_EUNSUPPORTED;
+  using cd = std::complex<double>;
+  std::vector<cd> si(n, cd(1, 0)), so(n, cd(1, 0));
+  if (a.sc_in) {
+    HELM_CK(cudaMemcpy(si.data(), a.sc_in, n * sizeof(cd), cudaMemcpyDeviceToHost));
+    HELM_CK(cudaMemcpy(so.data(), a.sc_out, n * sizeof(cd), cudaMemcpyDeviceToHost));
+  }
+  const double tp = 2.0 * M_PI / (double)n;
+  std::vector<cd> W((size_t)n * n);
+  std::vector<float> tab(dft_gemm_table_floats(n));
+  for (int dir = 0; dir < 2; ++dir) {
+    for (int64_t j = 0; j < n; ++j)
+      for (int64_t k = 0; k < n; ++k) {
+        const double ang = tp * (double)((j * k) % n);
+        if (dir == 0) W[(size_t)j * n + k] = si[j] * cd(std::cos(ang), -std::sin(ang));
+        else W[(size_t)k * n + j] = so[j] * cd(std::cos(ang), std::sin(ang)) / (double)n;
+      }
+    dft_gemm_table(n, W.data(), tab.data());
+    void* d = nullptr;
+    if (int rc = dev_alloc(p, &d, tab.size() * sizeof(float))) return rc;
+    a.gemm[dir] = static_cast<float*>(d);
+    HELM_CK(cudaMemcpy(d, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  a.dft.gw[0] = a.gemm[0];
+  a.dft.gw[1] = a.gemm[1];
+  a.dft.gsc[0] = a.sc_in32;
+  a.dft.gsc[1] = a.sc_out32;
+  a.dft.gscale = 1.0 / (double)n;
+  return HELM_OK;
 }
 
 // Default auxiliary: damped periodic wrap g = e^{rho + i q pi/2} (see helm.h):
@@ -915,6 +966,8 @@ int apply_aux(helm_plan* p, double rho, int phase_quarters) {
   ++p->version;
   int rc = build_axis_aux(p, p->axo, rho, phase_quarters);
   if (!rc && p->dim == 3) rc = build_axis_aux(p, p->axi, rho, phase_quarters);
+  // the tensor-core transform tables hold the scalings of the auxiliary
+  if (!rc && p->dft_gemm) rc = build_dft_gemm(p, p->dim == 3 ? p->axi : p->axo);
   if (rc) return rc;
   if (p->dim == 2) {
     const Solve2DArgs a = args2d(p);
@@ -1296,6 +1349,16 @@ int helm_set_variant(helm_plan_t p, int knob, int value) {
     if (p->dim != 2 || p->prec != kPrecF32) return HELM_EUNSUPPORTED;
     if (value != 0 && value != 1) return HELM_EINVAL;
     p->tri_regs = value;
+  } else if (knob == HELM_VARIANT_DFT) {
+    if (value != 0 && value != 1) return HELM_EINVAL;
+    AxisData& ax = p->dim == 3 ? p->axi : p->axo;  // the axis transformed along rows
+    if (value && (p->prec != kPrecF32 || !dft_gemm_supported(ax.n))) return HELM_EUNSUPPORTED;
+    if (value) {
+      if (int rc = build_dft_gemm(p, ax)) return rc;
+    } else {
+      free_dft_gemm(p, ax);
+    }
+    p->dft_gemm = value;
   } else if (knob == HELM_VARIANT_INNER_CHUNK || knob == HELM_VARIANT_INNER_TILES) {
     if (p->dim != 3 || !p->p3.inner_nmb) return HELM_EUNSUPPORTED;
     const int ch = knob == HELM_VARIANT_INNER_CHUNK ? value : p->p3.inner_ch;
@@ -1319,6 +1382,7 @@ int helm_get_variant(helm_plan_t p, int knob, int* value) {
   if (knob == HELM_VARIANT_TRI2D) *value = p->tri_regs;
   else if (knob == HELM_VARIANT_INNER_CHUNK) *value = p->dim == 3 ? p->p3.inner_ch : 0;
   else if (knob == HELM_VARIANT_INNER_TILES) *value = p->dim == 3 ? p->p3.inner_nmb : 0;
+  else if (knob == HELM_VARIANT_DFT) *value = p->dft_gemm;
   else return HELM_EINVAL;
   return HELM_OK;
 }

@@ -425,6 +425,16 @@ cudaError_t launch_dft_rows(int prec, const void* in, int in_is_double, void* ou
                             int64_t nrows, const DftPlan& p, const void* tw, int sign, double scale,
                             double accum_scale, const void* sc_in, const void* sc_out, const int* skip,
                             cudaStream_t st, int* err) {
+  // the tensor-core variant, for calls whose scalings are those its tables hold
+  if (prec == kPrecF32 && p.gw[sign < 0 ? 0 : 1] && (in_is_double == kInC64 || in_is_double == kInC128) &&
+      (out_mode == kOutC64 || out_mode == kOutC128 || out_mode == kOutAccumC128)) {
+    const bool fwd = sign < 0;
+    const bool same = fwd ? (sc_in == p.gsc[0] && !sc_out && scale == 1.0)
+                          : (sc_out == p.gsc[1] && !sc_in && scale == p.gscale);
+    if (same)
+      return launch_dft_rows_tc(p.gw[fwd ? 0 : 1], p.n, in, in_is_double, out, out_mode, nrows, accum_scale, skip, st,
+                                err);
+  }
   if (p.bm) {
     if (nrows == 0) return cudaSuccess;
     const size_t es = prec == kPrecF64 ? sizeof(double2) : sizeof(float2);

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <complex>
 #include <cstdint>
 
 #include "helm_internal.h"
@@ -20,6 +21,21 @@ bool dft_supported(const DftPlan& p, size_t elem_bytes, int max_smem);
 // A length whose factorisation has a prime above 64 is transformed by
 // Bluestein's chirp-z method; its power-of-two convolution length (>= 2n - 1).
 bool dft_needs_bluestein(const DftPlan& p);
+
+// Tensor-core (tcgen05, kind::tf32 with high/low operand splitting) dense
+// DFT of complex64 lines of n <= kDftGemmMaxN points; see helm_dft_tc.cu.
+constexpr int kDftGemmMaxN = 128;
+bool dft_gemm_supported(int64_t n);
+// Floats of one table (one direction) for length n.
+size_t dft_gemm_table_floats(int64_t n);
+// The table of the matrix W (n x n, input index major, FP64) in the kernel's
+// operand layout.
+void dft_gemm_table(int64_t n, const std::complex<double>* W, float* out);
+// nrows lines: in (kInC64 / kInC128) times the table's matrix to out
+// (kOutC64, kOutC128 or kOutAccumC128 with accum_scale).
+cudaError_t launch_dft_rows_tc(const float* table, int64_t n, const void* in, int in_is_double, void* out,
+                               int out_mode, int64_t nrows, double accum_scale, const int* skip, cudaStream_t st,
+                               int* err);
 int64_t bluestein_length(int64_t n);
 
 // Lines along the contiguous (last) axis: nrows lines of length p.n.

@@ -366,6 +366,9 @@ int dft_factor(int64_t n, DftPlan* p) {
   p->bstages = 0;
   p->bw = p->btw = nullptr;
   p->bf[0] = p->bf[1] = nullptr;
+  p->gw[0] = p->gw[1] = nullptr;
+  p->gsc[0] = p->gsc[1] = nullptr;
+  p->gscale = 0.0;
   if (n < 1) return 0;
   int64_t m = n;
   auto push = [&](int r) {

@@ -34,6 +34,14 @@ struct DftPlan {
   const void* bw;
   const void* bf[2];
   const void* btw;
+  // Tensor-core variant (complex64 lines of at most 128 points): gw[0] /
+  // gw[1] the forward / inverse matrix tables of launch_dft_rows_tc (null:
+  // not built), made with the FP32 scalings gsc[0] (input, forward) and
+  // gsc[1] (output, inverse) and the inverse's scale gscale folded in; used
+  // only by calls that pass exactly those.
+  const float* gw[2];
+  const void* gsc[2];
+  double gscale;
 };
 
 int dft_factor(int64_t n, DftPlan* p);
@@ -82,6 +90,7 @@ struct AxisData {
   double* tw = nullptr;     // e^{-2 pi i k/n} (re, im) interleaved, FP64
   float* tw32 = nullptr;    // same, FP32
   void* bs[4] = {nullptr, nullptr, nullptr, nullptr};  // Bluestein tables of dft (chirp, 2 spectra, twiddles)
+  float* gemm[2] = {nullptr, nullptr};                  // tensor-core DFT tables of dft (forward, inverse)
   DftPlan dft{};
 };
 

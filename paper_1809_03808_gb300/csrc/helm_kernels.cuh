@@ -53,6 +53,35 @@ __device__ __forceinline__ C cmul(C a, C b) {
   r.y = a.x * b.y + a.y * b.x;
   return r;
 }
+// c + a * b and c - a * b as four fused multiply-adds (one rounding per
+// component step instead of a product rounded before the sum)
+template <typename C>
+__device__ __forceinline__ C cfma(C a, C b, C c) {
+  c.x = fma(a.x, b.x, fma(-a.y, b.y, c.x));
+  c.y = fma(a.x, b.y, fma(a.y, b.x, c.y));
+  return c;
+}
+template <typename C>
+__device__ __forceinline__ C cfms(C c, C a, C b) {
+  c.x = fma(-a.x, b.x, fma(a.y, b.y, c.x));
+  c.y = fma(-a.x, b.y, fma(-a.y, b.x, c.y));
+  return c;
+}
+// Principal square root of a complex FP64 value.
+__device__ __forceinline__ double2 csqrt_d(double2 z) {
+  const double r = hypot(z.x, z.y);
+  double re = sqrt(0.5 * (r + fabs(z.x))), im = 0.0;
+  if (re > 0.0) im = 0.5 * z.y / re;
+  if (z.x < 0.0) {  // sqrt(z) = |im| + i sign(y) re
+    const double t = fabs(im);
+    im = z.y < 0.0 ? -re : re;
+    re = t;
+  }
+  return make_double2(re, im);
+}
+
+// Prefetch the global-memory line holding p into L2 (no data returned).
+__device__ __forceinline__ void l2_prefetch(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 // a * conj(b)
 template <typename C>
 __device__ __forceinline__ C cmulc(C a, C b) {

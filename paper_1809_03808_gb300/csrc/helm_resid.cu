@@ -249,19 +249,25 @@ __global__ void __launch_bounds__(QZ* QY) k_residual3d_q(ResidQArgs a, const dou
 // needs no per-thread index or bounds arithmetic and no registers.  Three
 // plane buffers: while plane i is used, planes i+1 and i+2 are in flight; the
 // z sums are double-buffered, so one barrier per plane separates every reuse.
+// The plane's f tile comes by the same kind of load on the same barrier.
 // Every wait is bounded: a copy that does not arrive sets *err, the whole CTA
 // stops, and thread 0 lets its copies still in flight land before it exits.
-constexpr int QUB = (QY + 2) * (QZ + 2) * (int)sizeof(double2);  // bytes of one staged plane
+constexpr int QUB = (QY + 2) * (QZ + 2) * (int)sizeof(double2);  // bytes of one staged u plane
 constexpr int QUS = (QUB + 127) / 128 * 128;                      // its stride (TMA destinations: 128 B)
+constexpr int QFB = QY * QZ * (int)sizeof(double2);               // bytes of one f plane tile
 constexpr int QNB = 3;                                            // plane buffers
+constexpr int QSZB = 2 * (QY + 2) * QZ * (int)sizeof(double2);    // the two z-sum buffers
+constexpr size_t kResidTmaSmem = (size_t)QNB * (QUS + QFB) + QSZB + QNB * sizeof(uint64_t);
 
 __global__ void __launch_bounds__(QZ* QY, 2)
-    k_residual3d_tma(const __grid_constant__ CUtensorMap umap, ResidQArgs a, const double2* __restrict__ f,
+    k_residual3d_tma(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap fmap, ResidQArgs a,
                      float2* __restrict__ r, double* __restrict__ sums, const int* __restrict__ skip, int* err) {
   if (skip && *skip) return;
-  __shared__ __align__(128) unsigned char sUb[QNB * QUS];
-  __shared__ double2 sSz[2][QY + 2][QZ];
-  __shared__ __align__(8) uint64_t bar[QNB];
+  extern __shared__ __align__(128) unsigned char rsm[];
+  unsigned char* sUb = rsm;                                               // [QNB][QUS] u halo planes
+  unsigned char* sFb = sUb + QNB * QUS;                                   // [QNB][QFB] f plane tiles
+  double2(*sSz)[QY + 2][QZ] = reinterpret_cast<double2(*)[QY + 2][QZ]>(sFb + QNB * QFB);  // [2]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sFb + QNB * QFB + QSZB);
   const int64_t nx = a.n[0], ny = a.n[1], nz = a.n[2];
   const int tz = threadIdx.x, ty = threadIdx.y, tid = ty * QZ + tz;
   const int64_t z0 = (int64_t)blockIdx.x * QZ, y0 = (int64_t)blockIdx.y * QY;
@@ -278,11 +284,13 @@ __global__ void __launch_bounds__(QZ* QY, 2)
     fence_mbar_init();
   }
   __syncthreads();
-  // plane xs - 1 + i into buffer i % QNB (thread 0 only)
+  // plane xs - 1 + i of u (halo box) and of f (the tile) into buffer i % QNB
+  // (thread 0 only; boxes outside the grid arrive as zeros)
   auto issue = [&](int i) {
     const int b = i % QNB;
-    mbar_arrive_expect_tx(&bar[b], (uint32_t)QUB);
+    mbar_arrive_expect_tx(&bar[b], (uint32_t)(QUB + QFB));
     tma_load_3d(sUb + b * QUS, &umap, (int)(2 * (z0 - 1)), (int)(y0 - 1), (int)(xs - 1 + i), &bar[b]);
+    tma_load_3d(sFb + b * QFB, &fmap, (int)(2 * z0), (int)y0, (int)(xs - 1 + i), &bar[b]);
   };
   int issued = 0;
   if (tid == 0) {
@@ -296,10 +304,9 @@ __global__ void __launch_bounds__(QZ* QY, 2)
   for (; i < np; ++i) {
     const int64_t ip = xs - 1 + i;
     const double2* U = reinterpret_cast<const double2*>(sUb + (i % QNB) * QUS);  // [QY+2][QZ+2]
+    const double2* F = reinterpret_cast<const double2*>(sFb + (i % QNB) * QFB);  // [QY][QZ]
     double2(*Sz)[QZ] = sSz[i & 1];
     const bool outp = own && ip >= xs && ip < xe;
-    double2 fv = zero;
-    if (outp) fv = __ldg(&f[(ip * ny + gy) * nz + gz]);
     const bool got = mbar_wait_bounded(&bar[i % QNB], (uint32_t)((i / QNB) & 1), err);
     for (int e = tid; e < (QY + 2) * QZ; e += QZ * QY) {
       const int yy = e / QZ, zc = e - yy * QZ;
@@ -310,11 +317,12 @@ __global__ void __launch_bounds__(QZ* QY, 2)
       failed = true;
       break;
     }
-    // every thread is past plane i - 1: its buffer takes plane i + 2
+    // every thread is past plane i - 1: its buffers take plane i + 2
     if (tid == 0 && i + 2 < np) {
       issue(i + 2);
       issued = i + 3;
     }
+    const double2 fv = outp ? F[ty * QZ + tz] : zero;
     double2 Rn = zero, Qn = fv;
     if (own && ip >= 0 && ip < nx) {
       const double2 P00 = U[(ty + 1) * (QZ + 2) + tz + 1], P01 = Sz[ty + 1][tz];
@@ -382,19 +390,19 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// Tensor map of u ([nx][ny][nz] complex128 viewed as [nx][ny][2 nz] FP64)
-// with the residual's halo box; false if it cannot be made (the caller then
-// stages the planes with plain loads).
-bool residual_umap(CUtensorMap* m, const double2* u, const int64_t* n) {
+// Tensor map of a [nx][ny][nz] complex128 array viewed as [nx][ny][2 nz]
+// FP64, with a box of bz complex values x by rows along y; false if it cannot
+// be made (the caller then stages the planes with plain loads).
+bool residual_map(CUtensorMap* m, const double2* v, const int64_t* n, int bz, int by) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc || ((uintptr_t)u & 15) || 2 * n[2] > (int64_t)UINT32_MAX || n[1] > (int64_t)UINT32_MAX ||
+  if (!enc || ((uintptr_t)v & 15) || 2 * n[2] > (int64_t)UINT32_MAX || n[1] > (int64_t)UINT32_MAX ||
       n[0] > (int64_t)INT32_MAX - 2)
     return false;
   const cuuint64_t gdim[3] = {(cuuint64_t)(2 * n[2]), (cuuint64_t)n[1], (cuuint64_t)n[0]};
   const cuuint64_t gstride[2] = {(cuuint64_t)(2 * n[2] * sizeof(double)), (cuuint64_t)(n[1] * 2 * n[2] * sizeof(double))};
-  const cuuint32_t box[3] = {2 * (QZ + 2), QY + 2, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * bz), (cuuint32_t)by, 1};
   const cuuint32_t estride[3] = {1, 1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<double2*>(u), gdim, gstride, box, estride,
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<double2*>(v), gdim, gstride, box, estride,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -931,9 +939,13 @@ cudaError_t launch_residual(int dim, const int64_t* n, const double* h, double o
         }
       const dim3 grid((unsigned)((n[2] + QZ - 1) / QZ), (unsigned)((n[1] + QY - 1) / QY), (unsigned)((n[0] + QX - 1) / QX));
       *nblocks = (int64_t)grid.x * grid.y * grid.z;
-      CUtensorMap um;
-      if (residual_umap(&um, u, n)) k_residual3d_tma<<<grid, dim3(QZ, QY), 0, st>>>(um, q, f, r, sums, skip, err);
-      else k_residual3d_q<<<grid, dim3(QZ, QY), 0, st>>>(q, f, u, r, sums, skip);
+      CUtensorMap um, fm;
+      static const cudaError_t attr = cudaFuncSetAttribute(k_residual3d_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           (int)kResidTmaSmem);
+      if (attr == cudaSuccess && residual_map(&um, u, n, QZ + 2, QY + 2) && residual_map(&fm, f, n, QZ, QY))
+        k_residual3d_tma<<<grid, dim3(QZ, QY), kResidTmaSmem, st>>>(um, fm, q, r, sums, skip, err);
+      else
+        k_residual3d_q<<<grid, dim3(QZ, QY), 0, st>>>(q, f, u, r, sums, skip);
       return cudaGetLastError();
     }
     for (int cx = 0; cx < 2; ++cx)

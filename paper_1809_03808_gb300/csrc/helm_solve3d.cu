@@ -446,17 +446,6 @@ __global__ void k_outer_cbb(const typename cpx<T>::type* __restrict__ v, const t
 // the carry coefficients alpha, beta of a chunk of ch settled rows (see
 // k_inner3d), all from the FP64 values.  For propagating modes the
 // pivots keep oscillating and len covers the whole line.
-__device__ __forceinline__ double2 csqrt_d(double2 z) {
-  const double r = hypot(z.x, z.y);
-  double re = sqrt(0.5 * (r + fabs(z.x))), im = 0.0;
-  if (re > 0.0) im = 0.5 * z.y / re;
-  if (z.x < 0.0) {  // sqrt(z) = |im| + i sign(y) re
-    const double t = fabs(im);
-    im = z.y < 0.0 ? -re : re;
-    re = t;
-  }
-  return make_double2(re, im);
-}
 
 template <typename T>
 __global__ void k_plane_tables(typename cpx<T>::type* __restrict__ tab, typename cpx<T>::type* __restrict__ lend,
@@ -585,10 +574,13 @@ struct InnerArgs {
   int nparts;  // face partials per plane = gridDim.x
 };
 
-// Shared memory of k_inner3d: rhs tile, pivot rows, chunk summaries (padded),
-// face accumulators, per-line and per-mode constants, settling rows.
-inline size_t inner_smem_bytes(int64_t nx, int nc, size_t cb) {
-  return ((size_t)nx * kMW + (size_t)kPivRows * kMW + 4 * (size_t)kMW * (nc + 1) + 2 * (size_t)nx + 9 * kMW + 3) * cb +
+// Shared memory of k_inner3d: solved-row tile, pivot rows, chunk summaries
+// (padded), face accumulators, per-line and per-mode constants, powers of the
+// settled pivot ratio, settling rows.
+inline size_t inner_smem_bytes(int64_t nx, int nc, int ch, size_t cb) {
+  return ((size_t)nx * kMW + (size_t)kPivRows * kMW + 4 * (size_t)kMW * (nc + 1) + 2 * (size_t)nx + 9 * kMW + 3 +
+          (size_t)ch * kMW) *
+             cb +
          2 * kMW * sizeof(int);
 }
 
@@ -613,7 +605,31 @@ constexpr int inner_max_threads() {
   return sizeof(T) == 4 ? 1024 : 512;
 }
 
-template <typename T, int OSTEP, int ISTEP>
+// Chunks per line the tiled sweeps allow for (precision, rows per chunk); 0
+// unless CH is one of the compiled 8, 16, 32.
+inline int inner_max_chunks(int prec, int ch) {
+  if (ch != 8 && ch != 16 && ch != 32) return 0;
+  return (prec == kPrecF64 ? inner_max_threads<double>() : inner_max_threads<float>()) / kMW;
+}
+
+// Lanes per line in the chunk scan (a warp scans 32 / kScanLanes lines).
+constexpr int kScanLanes = 8;
+
+template <typename C>
+__device__ __forceinline__ C shfl_up_w(C v, int off) {
+  v.x = __shfl_up_sync(0xffffffffu, v.x, off, kScanLanes);
+  v.y = __shfl_up_sync(0xffffffffu, v.y, off, kScanLanes);
+  return v;
+}
+
+template <typename C>
+__device__ __forceinline__ C shfl_down_w(C v, int off) {
+  v.x = __shfl_down_sync(0xffffffffu, v.x, off, kScanLanes);
+  v.y = __shfl_down_sync(0xffffffffu, v.y, off, kScanLanes);
+  return v;
+}
+
+template <typename T, int OSTEP, int ISTEP, int CH>
 __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
     InnerArgs ia, const typename cpx<T>::type* __restrict__ fhat, const typename cpx<T>::type* __restrict__ gfaces,
     const typename cpx<T>::type* __restrict__ cin, const typename cpx<T>::type* __restrict__ tab,
@@ -625,7 +641,7 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nx = (int)a.nx;
   const int64_t ny = a.ny, nz = a.nz;
-  const int nc = ia.nc, ch = ia.ch;
+  const int nc = ia.nc;
   const int ncp = nc + 1;  // padded chunk stride of the summaries: conflict-free in both layouts
   C* tile = reinterpret_cast<C*>(smem_raw);  // [nx][kMW]
   C* piv = tile + (size_t)nx * kMW;          // [kPivRows][kMW] first rows of the pivot tables
@@ -634,8 +650,9 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
   C* mw = facc + 2 * nx;                     // [kMW] rhs scale, [kMW] weight of the last face, [2][kMW] face weights
   // [kMW] b, [kMW] 1/u_inf, [kMW] 1/u_{nx-1}; [3] outer-mode constants; [kMW] alpha, [kMW] beta of a settled chunk
   C* lc = mw + 4 * kMW;
-  int* sL = reinterpret_cast<int*>(lc + 5 * kMW + 3);  // [kMW] settling rows
-  int* sR = sL + kMW;                                    // [kMW] 1: routed to FP64
+  C* apow = lc + 5 * kMW + 3;                         // [CH][kMW] q^(k+1), q = -b / u_inf
+  int* sL = reinterpret_cast<int*>(apow + CH * kMW);  // [kMW] settling rows
+  int* sR = sL + kMW;                                 // [kMW] 1: routed to FP64
   const int64_t l = blockIdx.y;
   const int tid = threadIdx.x, nthr = blockDim.x;
   // thread (mi, c): the two half-warps of warp w take chunks w and nc-1-w, so
@@ -654,10 +671,24 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
   }
   const C* cin1 = cin ? cin + l * 2 * nx : nullptr;  // inner C_bb faces of this plane
   const C* cinn = cin ? cin1 + nx : nullptr;
-  const C* g1 = gfaces;  // outer faces [2][nx][nz]
-  const C* gn = gfaces ? gfaces + (int64_t)nx * nz : nullptr;
   if (ISTEP != 3)
     for (int e = tid; e < 2 * nx; e += nthr) facc[e] = mk<C>(0, 0);
+  // the right-hand sides of this CTA's later tiles into L2 while the first
+  // is staged and solved: one 128-byte line (16 inner modes) per row,
+  // prefetched by lane 0 of each half-warp for its chunk's rows
+  if (ISTEP != 2 && mi == 0 && cok)
+    for (int mb = 1; mb < ia.nmb; ++mb) {
+      const int64_t mq = ((int64_t)blockIdx.x * ia.nmb + mb) * kMW;
+      if (mq >= nz) break;
+      for (int k = 0; k < CH && c * CH + k < nx; ++k) {
+        const int64_t x = c * CH + k;
+        if (OSTEP != 2) l2_prefetch(fhat + (x * ny + l) * nz + mq);
+        if (OSTEP != 1) {
+          l2_prefetch(gfaces + x * nz + mq);
+          l2_prefetch(gfaces + ((int64_t)nx + x) * nz + mq);
+        }
+      }
+    }
 
   for (int mb = 0; mb < ia.nmb; ++mb) {
     const int64_t m0 = ((int64_t)blockIdx.x * ia.nmb + mb) * kMW;
@@ -681,11 +712,19 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
       mw[3 * kMW + tid] = on ? wn : mk<C>(0, 0);
       // line constants from the plan tables
       const int64_t line = l * nz + mc;
-      lc[tid] = lend[kLineVals * line + 2];
-      lc[kMW + tid] = lend[kLineVals * line];
+      const C b = lend[kLineVals * line + 2], iinf = lend[kLineVals * line];
+      lc[tid] = b;
+      lc[kMW + tid] = iinf;
       lc[2 * kMW + tid] = lend[kLineVals * line + 1];
       lc[3 * kMW + 3 + tid] = lend[kLineVals * line + 3];
       lc[4 * kMW + 3 + tid] = lend[kLineVals * line + 4];
+      // powers of q = -b / u_inf: the forward carry's weight in a settled chunk
+      const C q = cmul(mk<C>(-b.x, -b.y), iinf);
+      C qk = q;
+      for (int k = 0; k < CH; ++k) {
+        apow[k * kMW + tid] = qk;
+        qk = cmul(qk, q);
+      }
       // a line routed to FP64 (flag bit) gets a zero right-hand side here, so
       // it adds nothing to the faces; the FP64 kernel solves it
       const int lr = on ? lenL[line] : 0;
@@ -700,82 +739,82 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
       sR[tid] = routed ? 1 : 0;
     }
     __syncthreads();
-    const C gscale = lc[3 * kMW], wl = lc[3 * kMW + 1];
-    const T paro = lc[3 * kMW + 2].x;
-    // ---- stage the right-hand sides and the first pivot rows ----
-    {
-      constexpr int B = 8;
-      for (int e0 = tid; e0 < nx * kMW; e0 += B * nthr) {
-        C v[B];
-#pragma unroll
-        for (int t = 0; t < B; ++t) {
-          const int e = e0 + t * nthr;
-          v[t] = mk<C>(0, 0);
-          if (e < nx * kMW) {
-            const int x = e / kMW, mm = e - x * kMW;
-            const int64_t m = m0 + mm;
-            if (m < nz) {
-              if (ISTEP == 2) {
-                if (!sR[mm]) v[t] = cadd(cin1[x], cmul(cinn[x], mw[kMW + mm]));
-              } else {
-                C g;
-                if (OSTEP == 1) g = cmul(fhat[((int64_t)x * ny + l) * nz + m], gscale);
-                else if (OSTEP == 2) g = cadd(g1[(int64_t)x * nz + m], cscale(gn[(int64_t)x * nz + m], paro));
-                else
-                  g = cmul(cadd(cadd(fhat[((int64_t)x * ny + l) * nz + m], g1[(int64_t)x * nz + m]),
-                                cmul(gn[(int64_t)x * nz + m], wl)),
-                           gscale);
-                if (ISTEP == 3) g = cadd(g, cadd(cin1[x], cmul(cinn[x], mw[kMW + mm])));
-                v[t] = cmul(g, mw[mm]);
-              }
+    // ---- the first pivot rows of the tile's lines ----
+    for (int e = tid; e < kPivRows * kMW; e += nthr) {
+      const int j = e / kMW, mm = e - j * kMW;
+      C v = mk<C>(0, 0);
+      if (j < sL[mm]) v = tab[(int64_t)j * xs + l * nz + m0 + mm];
+      piv[e] = v;
+    }
+    // ---- thread (mi, c) stages its own chunk rows: for each row the 16
+    // lanes of a half-warp read 16 consecutive inner modes ----
+    const int64_t m = m0 + mi;
+    const bool act = m < nz && cok;
+    const int s0 = c * CH, e0 = min(s0 + CH, nx) - 1;
+    C* trow = tile + s0 * kMW + mi;  // row s0 + k of this line: trow[k * kMW]
+    if (cok) {
+      const C gscale = lc[3 * kMW], wl = lc[3 * kMW + 1];
+      const T paro = lc[3 * kMW + 2].x;
+      const C sc = mw[mi], wk2 = mw[kMW + mi];
+      const C gs = cmul(gscale, sc);
+      const bool zero_rhs = !act || (ISTEP == 2 && sR[mi]);
+      const int64_t mcl = act ? m : 0;
+      const C* fp = fhat + ((int64_t)s0 * ny + l) * nz + mcl;  // f_hat rows of this line
+      const C* g1p = OSTEP != 1 ? gfaces + (int64_t)s0 * nz + mcl : nullptr;  // outer faces (Steps 2, 3)
+      const C* gnp = OSTEP != 1 ? g1p + (int64_t)nx * nz : nullptr;
+#pragma unroll(CH <= 16 ? CH : 8)
+      for (int k = 0; k < CH; ++k) {
+        if (s0 + k <= e0) {
+          C v = mk<C>(0, 0);
+          if (!zero_rhs) {
+            if (ISTEP == 2) {
+              v = cadd(cin1[s0 + k], cmul(cinn[s0 + k], wk2));
+            } else {
+              if (OSTEP == 1) v = cmul(fp[k * xs], gs);
+              else if (OSTEP == 2) v = cmul(cadd(g1p[k * nz], cscale(gnp[k * nz], paro)), sc);
+              else v = cmul(cadd(cadd(fp[k * xs], g1p[k * nz]), cmul(gnp[k * nz], wl)), gs);
+              if (ISTEP == 3) v = cadd(v, cmul(cadd(cin1[s0 + k], cmul(cinn[s0 + k], wk2)), sc));
             }
           }
+          trow[k * kMW] = v;
         }
-#pragma unroll
-        for (int t = 0; t < B; ++t) {
-          const int e = e0 + t * nthr;
-          if (e < nx * kMW) tile[e] = v[t];
-        }
-      }
-      for (int e = tid; e < kPivRows * kMW; e += nthr) {
-        const int j = e / kMW, mm = e - j * kMW;
-        C v = mk<C>(0, 0);
-        if (j < sL[mm]) v = tab[(int64_t)j * xs + l * nz + m0 + mm];
-        piv[e] = v;
       }
     }
     // ---- line constants of thread (mi, c) ----
-    const int64_t m = m0 + mi;
-    const bool act = m < nz && cok;
     const C b = lc[mi], iinf = lc[kMW + mi], ilast = lc[2 * kMW + mi];
     const C nb = mk<C>(-b.x, -b.y);
+    const C cinf = cmul(b, iinf);
     const int L = sL[mi];  // 0 for a routed line
     const C* tcol = tab + l * nz + (m < nz ? m : 0);
     auto pivot = [&](int j) -> C {
       if (j >= L) return j == nx - 1 ? ilast : iinf;
       return j < kPivRows ? piv[j * kMW + mi] : tcol[(int64_t)j * xs];
     };
-    const int s0 = c * ch, e0 = min(s0 + ch, nx) - 1;
-    __syncthreads();  // tile and pivot rows staged
+    __syncthreads();  // pivot rows staged
     // ---- pass 1 ----
     // Forward with d_{s-1} = 0 (d_loc written over the rhs), then the
     // backward substitution with x_{e+1} = 0 over it by Horner's rule gives
     // x_loc.  alpha_e = prod (-b/u_j) and beta = sum alpha_{j-1} alpha_j do
-    // not depend on the data: a chunk of settled rows takes them from the
-    // plan, the others (rows with tabulated pivots, the corner row) form them.
-    // warp-uniform: a warp takes the settled path only if all its chunks
-    // are settled (the general path is exact for settled rows too)
-    const bool settled = __all_sync(0xffffffffu, !act || (s0 >= L && e0 < nx - 1 && e0 - s0 + 1 == ch));
+    // not depend on the data: a settled chunk takes them from the plan, the
+    // others form them.  Warp-uniform: a warp takes the settled path only if
+    // all its chunks are settled (the general path is exact for them too).
+    const bool settled = __all_sync(0xffffffffu, !act || (s0 >= L && e0 < nx - 1 && e0 - s0 + 1 == CH));
     if (act) {
-      C d = mk<C>(0, 0), al = mk<C>(1, 0), be = mk<C>(0, 0);
+      C d = mk<C>(0, 0), al = mk<C>(1, 0), be = mk<C>(0, 0), x = mk<C>(0, 0);
       if (settled) {
-        for (int j = s0; j <= e0; ++j) {
-          d = cmul(csub(tile[j * kMW + mi], cmul(b, d)), iinf);
-          tile[j * kMW + mi] = d;
+        // d_j = r_j / u_inf + q d_{j-1}, q = -b / u_inf (= apow[0])
+        const C q = apow[mi];
+#pragma unroll 16
+        for (int k = 0; k < CH; ++k) {
+          d = cfma(q, d, cmul(trow[k * kMW], iinf));
+          trow[k * kMW] = d;
         }
+#pragma unroll 16
+        for (int k = CH - 1; k >= 0; --k) x = cfms(trow[k * kMW], cinf, x);
         al = lc[3 * kMW + 3 + mi];
         be = lc[4 * kMW + 3 + mi];
       } else {
+#pragma unroll 1
         for (int j = s0; j <= e0; ++j) {
           const C inv = pivot(j);
           d = cmul(csub(tile[j * kMW + mi], cmul(b, d)), inv);
@@ -784,42 +823,41 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
           be = cadd(be, cmul(al, an));
           al = an;
         }
-      }
-      sums[(0 * kMW + mi) * ncp + c] = d;
-      C x = mk<C>(0, 0);
-      if (settled) {
-        const C cinf = cmul(b, iinf);
-        for (int j = e0; j >= s0; --j) x = csub(tile[j * kMW + mi], cmul(cinf, x));
-      } else {
+#pragma unroll 1
         for (int j = e0; j >= s0; --j) x = csub(tile[j * kMW + mi], cmul(cmul(b, pivot(j)), x));
       }
+      sums[(0 * kMW + mi) * ncp + c] = d;
       sums[(1 * kMW + mi) * ncp + c] = x;
       sums[(2 * kMW + mi) * ncp + c] = al;
       sums[(3 * kMW + mi) * ncp + c] = be;
     }
     __syncthreads();
-    // ---- scan over the chunks of each line: one warp per line ----
+    // ---- scan over the chunks of each line: kScanLanes lanes per line, each
+    // lane a group of consecutive chunks, the groups composed by shuffles ----
     {
       const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
-      const int g = (nc + 31) / 32;  // chunks per lane
-      for (int mm = warp; mm < kMW; mm += nw) {
+      const int sl = lane & (kScanLanes - 1), seg = lane / kScanLanes;
+      constexpr int lpw = 32 / kScanLanes;             // lines per warp
+      const int g = (nc + kScanLanes - 1) / kScanLanes;  // chunks per lane
+      for (int mm0 = warp * lpw; mm0 < kMW; mm0 += nw * lpw) {
+        const int mm = mm0 + seg;
         C* sd = sums + (0 * kMW + mm) * ncp;  // d_loc, then the carry-in d_{s-1}
         C* sx = sums + (1 * kMW + mm) * ncp;  // x_loc, then the carry-in x_{e+1}
         const C* sa = sums + (2 * kMW + mm) * ncp;
         const C* sb = sums + (3 * kMW + mm) * ncp;
-        const int c0 = lane * g, c1 = min(c0 + g, nc);
+        const int c0 = sl * g, c1 = min(c0 + g, nc);
         // forward: D_c = dloc_c + alpha_c D_{c-1}; the lane's group as one map
         C P = mk<C>(1, 0), Q = mk<C>(0, 0);
         for (int cc = c0; cc < c1; ++cc) {
           Q = cadd(cmul(sa[cc], Q), sd[cc]);
           P = cmul(sa[cc], P);
         }
-        for (int off = 1; off < 32; off <<= 1) {
-          const C Pu = shfl_up_c(P, off), Qu = shfl_up_c(Q, off);
-          if (lane >= off) affine_compose(P, Q, Pu, Qu);
+        for (int off = 1; off < kScanLanes; off <<= 1) {
+          const C Pu = shfl_up_w(P, off), Qu = shfl_up_w(Q, off);
+          if (sl >= off) affine_compose(P, Q, Pu, Qu);
         }
-        C Din = shfl_up_c(Q, 1);  // D before the lane's group (inclusive scan shifted)
-        if (lane == 0) Din = mk<C>(0, 0);
+        C Din = shfl_up_w(Q, 1);  // D before the lane's group (inclusive scan shifted)
+        if (sl == 0) Din = mk<C>(0, 0);
         // carry-in d_{s-1} of each chunk; keep E_c = xloc_c + beta_c D_{c-1}
         for (int cc = c0; cc < c1; ++cc) {
           const C dl = sd[cc];
@@ -834,12 +872,12 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
           Q = cadd(cmul(sa[cc], Q), sx[cc]);
           P = cmul(sa[cc], P);
         }
-        for (int off = 1; off < 32; off <<= 1) {
-          const C Pd = shfl_down(P, off), Qd = shfl_down(Q, off);
-          if (lane + off < 32) affine_compose(P, Q, Pd, Qd);
+        for (int off = 1; off < kScanLanes; off <<= 1) {
+          const C Pd = shfl_down_w(P, off), Qd = shfl_down_w(Q, off);
+          if (sl + off < kScanLanes) affine_compose(P, Q, Pd, Qd);
         }
-        C Xin = shfl_down(Q, 1);  // X just after the lane's group
-        if (lane == 31) Xin = mk<C>(0, 0);
+        C Xin = shfl_down_w(Q, 1);  // X just after the lane's group
+        if (sl == kScanLanes - 1) Xin = mk<C>(0, 0);
         for (int cc = c1 - 1; cc >= c0; --cc) {
           const C E = sx[cc];
           sx[cc] = Xin;  // carry-in x_{e+1} of chunk cc
@@ -850,31 +888,30 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
     __syncthreads();
     // ---- pass 2 ----
     // d_j = d_loc_j + alpha_j d_{s-1} over the chunk, then the backward
-    // substitution from the exact carry x_{e+1}.
+    // substitution from the exact carry x_{e+1}; in a settled chunk
+    // alpha_j = q^(j-s+1) and both run in one backward sweep.
     if (act) {
       const C Din = sums[(0 * kMW + mi) * ncp + c];
       C x = sums[(1 * kMW + mi) * ncp + c];
+      C* yrow = y3 + ((int64_t)s0 * ny + l) * nz + m;  // y3 rows of this line (Step 3)
       if (settled) {
-        const C q = cmul(nb, iinf), cinf = cmul(b, iinf);
-        C al = q;
-        for (int j = s0; j <= e0; ++j) {
-          tile[j * kMW + mi] = cadd(tile[j * kMW + mi], cmul(al, Din));
-          al = cmul(al, q);
-        }
-        for (int j = e0; j >= s0; --j) {
-          x = csub(tile[j * kMW + mi], cmul(cinf, x));
-          if (ISTEP == 3) y3[((int64_t)j * ny + l) * nz + m] = x;
-          else tile[j * kMW + mi] = x;
+#pragma unroll 16
+        for (int k = CH - 1; k >= 0; --k) {
+          x = cfms(cfma(apow[k * kMW + mi], Din, trow[k * kMW]), cinf, x);
+          if (ISTEP == 3) yrow[k * xs] = x;
+          else trow[k * kMW] = x;
         }
       } else {
         C al = mk<C>(1, 0);
+#pragma unroll 1
         for (int j = s0; j <= e0; ++j) {
           al = cmul(al, cmul(nb, pivot(j)));
           tile[j * kMW + mi] = cadd(tile[j * kMW + mi], cmul(al, Din));
         }
+#pragma unroll 1
         for (int j = e0; j >= s0; --j) {
           x = csub(tile[j * kMW + mi], cmul(cmul(b, pivot(j)), x));
-          if (ISTEP == 3) y3[((int64_t)j * ny + l) * nz + m] = x;
+          if (ISTEP == 3) yrow[(int64_t)(j - s0) * xs] = x;
           else tile[j * kMW + mi] = x;
         }
       }
@@ -891,8 +928,8 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
           const C v = tile[x * kMW + mm];
           // Step 1's first-row weight is 1 (modes off the grid or routed
           // hold zeros in the tile)
-          s1 = cadd(s1, ISTEP == 1 ? v : cmul(v, mw[2 * kMW + mm]));
-          sn = cadd(sn, cmul(v, mw[3 * kMW + mm]));
+          s1 = ISTEP == 1 ? cadd(s1, v) : cfma(v, mw[2 * kMW + mm], s1);
+          sn = cfma(v, mw[3 * kMW + mm], sn);
         }
         facc[x] = cadd(facc[x], s1);
         facc[nx + x] = cadd(facc[nx + x], sn);
@@ -1121,7 +1158,7 @@ cudaError_t launch_inner_t(const Plan3D& p, const void* gfaces, const int* skip,
   InnerArgs ia{make_args(p), p.inner_ch, p.inner_nc, p.inner_nmb, p.inner_nparts};
   const int nx = (int)p.n[0];
   const int nthr = kMW * ((p.inner_nc + 1) & ~1);
-  const size_t smem = inner_smem_bytes(nx, p.inner_nc, sizeof(C));
+  const size_t smem = inner_smem_bytes(nx, p.inner_nc, p.inner_ch, sizeof(C));
   const dim3 grid((unsigned)p.inner_nparts, (unsigned)p.n[1]);
   const int oA = OSTEP == 2 ? 1 : 0;
   const C* fh = (const C*)p.fhat;
@@ -1159,13 +1196,23 @@ cudaError_t launch_inner_t(const Plan3D& p, const void* gfaces, const int* skip,
                                              skip);
     return cudaGetLastError();
   };
-  if ((e = sweep(k_inner3d<T, OSTEP, 1>, 1, 0)) != cudaSuccess) return e;
+  // the sweep kernel of inner step ISTEP for the plan's rows per chunk
+  auto sweep_ch = [&](auto istep, int innerA) -> cudaError_t {
+    constexpr int IS = decltype(istep)::value;
+    switch (p.inner_ch) {
+      case 8: return sweep(k_inner3d<T, OSTEP, IS, 8>, IS, innerA);
+      case 16: return sweep(k_inner3d<T, OSTEP, IS, 16>, IS, innerA);
+      case 32: return sweep(k_inner3d<T, OSTEP, IS, 32>, IS, innerA);
+      default: return cudaErrorInvalidValue;
+    }
+  };
+  if ((e = sweep_ch(std::integral_constant<int, 1>{}, 0)) != cudaSuccess) return e;
   if ((e = routed(k_inner3d_r<T, OSTEP, 1>, 0)) != cudaSuccess) return e;
   if ((e = reduce(k_inner_reduce<T, OSTEP, 1>, 0)) != cudaSuccess) return e;
-  if ((e = sweep(k_inner3d<T, OSTEP, 2>, 2, 1)) != cudaSuccess) return e;
+  if ((e = sweep_ch(std::integral_constant<int, 2>{}, 1)) != cudaSuccess) return e;
   if ((e = routed(k_inner3d_r<T, OSTEP, 2>, 1)) != cudaSuccess) return e;
   if ((e = reduce(k_inner_reduce<T, OSTEP, 2>, 1)) != cudaSuccess) return e;
-  if ((e = sweep(k_inner3d<T, OSTEP, 3>, 3, 0)) != cudaSuccess) return e;
+  if ((e = sweep_ch(std::integral_constant<int, 3>{}, 0)) != cudaSuccess) return e;
   return routed(k_inner3d_r<T, OSTEP, 3>, 0);
 }
 
@@ -1314,14 +1361,15 @@ cudaError_t plan3d_init(Plan3D& p, int prec, const int64_t* n, const double* h, 
   int dev = 0, smem_max = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const int max_nc = (prec == kPrecF64 ? 512 : 1024) / kMW;
+  // 16 rows per chunk, 32 for lines too long for 16 (the kernels hold a
+  // chunk in registers, so CH is one of 8, 16, 32)
   int ch = 16, nc = (int)((n[0] + 15) / 16);
-  if (nc > max_nc) {
-    ch = (int)((n[0] + max_nc - 1) / max_nc);
-    nc = (int)((n[0] + ch - 1) / ch);
+  if (nc > inner_max_chunks(prec, ch)) {
+    ch = 32;
+    nc = (int)((n[0] + 31) / 32);
   }
-  const size_t ismem = inner_smem_bytes(n[0], nc, cb);
-  if (p.tab[0] && ismem <= (size_t)smem_max) {
+  const size_t ismem = inner_smem_bytes(n[0], nc, ch, cb);
+  if (p.tab[0] && nc <= inner_max_chunks(prec, ch) && ismem <= (size_t)smem_max) {
     const int64_t tiles = (n[2] + kMW - 1) / kMW;
     const int64_t total = tiles * n[1];
     int nmb = (int)std::max<int64_t>(1, std::min<int64_t>(4, total / (152 * 8)));
@@ -1466,14 +1514,14 @@ cudaError_t plan3d_set_routing(Plan3D& p, double tau) {
 int plan3d_routed_lines(const Plan3D& p) { return p.nroute[0] + p.nroute[1] + p.nroute[2] + p.nroute[3]; }
 
 cudaError_t plan3d_set_inner(Plan3D& p, int ch, int nmb) {
-  if (!p.inner_nmb || ch < 4 || ch > 64 || nmb < 1 || nmb > 8) return cudaErrorInvalidValue;
+  if (!p.inner_nmb || nmb < 1 || nmb > 8) return cudaErrorInvalidValue;
   const size_t cb = p.prec == kPrecF64 ? sizeof(double2) : sizeof(float2);
-  const int max_nc = (p.prec == kPrecF64 ? 512 : 1024) / kMW;
+  const int max_nc = inner_max_chunks(p.prec, ch);  // 0 unless ch is 8, 16 or 32
   const int nc = (int)((p.n[0] + ch - 1) / ch);
   int dev = 0, smem_max = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (nc > max_nc || inner_smem_bytes(p.n[0], nc, cb) > (size_t)smem_max) return cudaErrorInvalidValue;
+  if (nc > max_nc || inner_smem_bytes(p.n[0], nc, ch, cb) > (size_t)smem_max) return cudaErrorInvalidValue;
   const int64_t tiles = (p.n[2] + kMW - 1) / kMW;
   nmb = (int)std::min<int64_t>(nmb, tiles);
   const int nparts = (int)((tiles + nmb - 1) / nmb);

@@ -21,8 +21,8 @@ from __future__ import annotations
 import ctypes
 import math
 
-from . import (HELM_VARIANT_INNER_CHUNK, HELM_VARIANT_INNER_TILES, HELM_VARIANT_TRI2D, _check, helm_get_variant,
-               helm_set_variant, helm_time_solve, lib)
+from . import (HELM_C128, HELM_OK, HELM_VARIANT_DFT, HELM_VARIANT_INNER_CHUNK, HELM_VARIANT_INNER_TILES,
+               HELM_VARIANT_TRI2D, _check, helm_get_variant, helm_set_variant, helm_time_solve, lib)
 
 # variants of 3D plans: (rows per chunk, tiles per CTA) of the tiled inner sweeps
 VARIANTS_3D = tuple((ch, nmb) for ch in (8, 16, 32) for nmb in (1, 2, 4))
@@ -67,11 +67,27 @@ def measure(plan, variants=None, reps=3):
     return out
 
 
+def dft_variant_possible(plan):
+    """Complex64 plans whose contiguous transformed axis has at most 128
+    nodes can take their transforms on the tensor cores (HELM_VARIANT_DFT)."""
+    return plan.dtype != HELM_C128 and plan.shape[-1] <= 128
+
+
 def autotune(plan, reps=3):
-    """Time every variant and keep the fastest; returns (variant, timings)."""
+    """Time every variant and keep the fastest; then, where the plan allows
+    it, the tensor-core transforms against the FFT kernels with that variant
+    (kept only if faster).  Returns (variant, timings); timings has the key
+    "dft_tensor_cores" when that was tried."""
+    dft = dft_variant_possible(plan)
+    if dft:
+        helm_set_variant(plan.handle, HELM_VARIANT_DFT, 0)  # the variants are timed with the FFT kernels
     t = measure(plan, reps=reps)
     best = min(t, key=t.get)
     set_variant(plan, best)
+    if dft and lib.helm_set_variant(plan.handle, HELM_VARIANT_DFT, 1) == HELM_OK:
+        t["dft_tensor_cores"] = helm_time_solve(plan.handle, reps)
+        if t["dft_tensor_cores"] >= t[best]:
+            helm_set_variant(plan.handle, HELM_VARIANT_DFT, 0)
     return best, t
 
 
