@@ -171,9 +171,11 @@ def kernel_model(name, e, n1, accum=False, first=True, tables=False, ff=False, p
                "tri_step3_pass1": (3 * e, 24.0), "tri_step1_pass2": (3 * e, 34.0),
                "tri_step2_pass2": (2 * e, 36.0), "tri_step3_pass2": (4 * e, 30.0)}
     else:
-        # complex64: each pass reads the per-plan 1/u_j table beside the rhs
-        tri = {"tri_step1_pass1": (2 * e, 67.0), "tri_step2_pass1": (e, 61.0), "tri_step3_pass1": (2 * e, 75.0),
-               "tri_step1_pass2": (2 * e, 53.0), "tri_step2_pass2": (e, 47.0), "tri_step3_pass2": (3 * e, 55.0)}
+        # complex64: the rhs (f_hat; Step 2 only face vectors) and, in Step 3,
+        # the solution; the per-plan 1/u_j table is read only for rows before
+        # the pivots settle, so it is not counted
+        tri = {"tri_step1_pass1": (e, 67.0), "tri_step2_pass1": (0.0, 61.0), "tri_step3_pass1": (e, 75.0),
+               "tri_step1_pass2": (e, 53.0), "tri_step2_pass2": (0.0, 47.0), "tri_step3_pass2": (2 * e, 55.0)}
     # 3D (n1 = the y / z length): z transforms on rows, y transforms in place
     # on columns; k_plane3d per outer step: per inner step the forward sweep
     # reads 1/den and writes d, the backward sweep reads both (4e), x3 steps,
@@ -237,7 +239,7 @@ def roofline_entry(name, launches, tot_ms, steps, N, e, n1, peaks, fp64, accum=F
     model = kernel_model(name, e, n1, accum=accum, tables=tables, ff=ff, per_solve=max(1.0, launches / steps),
                          n1_dim=dim)
     out = {"kernel": name, "launches_per_step": launches / steps, "ms_per_launch": per_launch_ms}
-    if model is None:
+    if model is None or model[0] == 0:  # no bulk bytes: timed only
         return out
     byts, flops = model[0] * N, model[1] * N
     gbs = byts / (per_launch_ms * 1e-3) / 1e9

@@ -500,6 +500,13 @@ __global__ void k_line_tables(LineTables t, Solve2DArgs a, int step) {
   const LineCoef<double2> co = line_coef<double2>(lp.sre, lp.sim, a.hx, a.wx);
   const double2 zero = make_double2(0, 0);
   const double2 mb = make_double2(-co.b.x, -co.b.y);
+  // limit of the pivots and the settling row of this line
+  const double2 disc = csqrt_d(csub(cmul(co.a, co.a), cscale(cmul(co.b, co.b), 4.0)));
+  const double2 r1 = cscale(cadd(co.a, disc), 0.5), r2 = cscale(csub(co.a, disc), 0.5);
+  const double2 iinf = crecip((r1.x * r1.x + r1.y * r1.y >= r2.x * r2.x + r2.y * r2.y) ? r1 : r2);
+  const double tol = 7.450580596923828e-09;  // 2^-27
+  const double tol2 = tol * tol * (iinf.x * iinf.x + iinf.y * iinf.y);
+  int64_t last_bad = -1;
   double2 iu = zero, P = zero, w = zero, cc = zero;
   for (int64_t j = 0; j < nx; ++j) {
     const int64_t k = j / a.ch, s = k * a.ch;
@@ -646,16 +653,29 @@ __global__ void __launch_bounds__(128) k_tri_pass2_tab(const double2* __restrict
 // chunk weights w_j from the table with one complex multiply each, so no
 // division is left in the recurrences.
 // ---------------------------------------------------------------------------
+// Lines per CTA and chunks per CTA of the bulk-copy fed tridiagonal kernels.
+constexpr int kBulkLines = 128;
+constexpr int kBulkChunks = 8;
+
+// iinf: per line 1/u_inf, the limit of the pivots (u_inf the root of
+// u^2 - a u + b^2 = 0 of larger modulus); lcta: per block of kBulkLines
+// lines, the first row from which every line's 1/u_j (below the last row)
+// is within 2^-27 |1/u_inf| of it, so the bulk kernels read no table rows
+// for chunks past it (propagating modes never settle: their blocks read the
+// whole table).
 struct LineTables32 {
   float2* iu;
   float2* pe;
   float2* cc;
   float2* we;
+  float2* iinf;
+  int* lcta;
 };
 
-inline LineTables32 line_tables32(void* base, size_t N, size_t nrec) {
+inline LineTables32 line_tables32(void* base, size_t N, size_t nrec, size_t n1) {
   float2* b = reinterpret_cast<float2*>(base);
-  return LineTables32{b, b + N, b + N + nrec, b + N + 2 * nrec};
+  float2* ii = b + N + 3 * nrec;
+  return LineTables32{b, b + N, b + N + nrec, b + N + 2 * nrec, ii, reinterpret_cast<int*>(ii + n1)};
 }
 
 __global__ void k_line_tables32(LineTables32 t, Solve2DArgs a, int step) {
@@ -666,6 +686,13 @@ __global__ void k_line_tables32(LineTables32 t, Solve2DArgs a, int step) {
   const LineCoef<double2> co = line_coef<double2>(lp.sre, lp.sim, a.hx, a.wx);
   const double2 zero = make_double2(0, 0);
   const double2 mb = make_double2(-co.b.x, -co.b.y);
+  // limit of the pivots and the settling row of this line
+  const double2 disc = csqrt_d(csub(cmul(co.a, co.a), cscale(cmul(co.b, co.b), 4.0)));
+  const double2 r1 = cscale(cadd(co.a, disc), 0.5), r2 = cscale(csub(co.a, disc), 0.5);
+  const double2 iinf = crecip((r1.x * r1.x + r1.y * r1.y >= r2.x * r2.x + r2.y * r2.y) ? r1 : r2);
+  const double tol = 7.450580596923828e-09;  // 2^-27
+  const double tol2 = tol * tol * (iinf.x * iinf.x + iinf.y * iinf.y);
+  int64_t last_bad = -1;
   double2 iu = zero, P = zero, w = zero, cc = zero;
   for (int64_t j = 0; j < nx; ++j) {
     const int64_t k = j / a.ch, s = k * a.ch;
@@ -683,12 +710,18 @@ __global__ void k_line_tables32(LineTables32 t, Solve2DArgs a, int step) {
     w = (j == s) ? iu : cmul(cmul(w, mb), iu);
     cc = (j == s) ? cmul(w, P) : cadd(cc, cmul(w, P));
     t.iu[j * n1 + l] = cvt<float2>(iu);
+    if (j < nx - 1) {
+      const double dx = iu.x - iinf.x, dy = iu.y - iinf.y;
+      if (!(dx * dx + dy * dy <= tol2)) last_bad = j;
+    }
     if (j == min(s + a.ch, nx) - 1) {
       t.pe[k * n1 + l] = cvt<float2>((k > 0) ? P : zero);
       t.cc[k * n1 + l] = cvt<float2>((k > 0) ? cc : zero);
       t.we[k * n1 + l] = cvt<float2>(cmul(mb, w));  // q = -b we
     }
   }
+  t.iinf[l] = cvt<float2>(iinf);
+  atomicMax(&t.lcta[l / kBulkLines], (int)(last_bad + 1));
 }
 
 template <int STEP, int CH>
@@ -803,8 +836,6 @@ __global__ void __launch_bounds__(128) k_tri_pass2_t32(const float2* __restrict_
 // without holding the tiles in registers.  Same arithmetic as
 // k_tri_pass1_t32 / k_tri_pass2_t32.  Needs 16-byte aligned rows (even n1).
 // ---------------------------------------------------------------------------
-constexpr int kBulkLines = 128;
-constexpr int kBulkChunks = 8;
 
 // Tile of one buffer, per kernel instance: [f_hat rows (Steps 1, 3)][1/u
 // rows][face values f1 (CH) and fn (CH + 2, from the even index at or before
@@ -883,6 +914,10 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
   const int tid = threadIdx.x;
   const bool act = tid < nl;
   const int64_t l = l0 + (act ? tid : 0);
+  // chunks from row lset on (except the one holding the last row) use each
+  // line's 1/u_inf: their table rows are not copied
+  const int64_t lset = tb.lcta[blockIdx.x];
+  auto settled = [&](int64_t k) { return k * CH >= lset && min((k + 1) * CH, nx) < nx; };
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -902,11 +937,13 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
     const uint32_t n_fn = (uint32_t)((((nx + s + cnt + 1) & ~(int64_t)1)) - fa);
     const uint32_t face_bytes = FACES ? (n_f1 + n_fn) * (uint32_t)sizeof(C) : 0u;
     const uint32_t carry_bytes = PASS == 2 ? 2u * row_bytes : 0u;
-    mbar_arrive_expect_tx(&bar[bsel], (uint32_t)cnt * row_bytes * (RHS ? 2u : 1u) + face_bytes + carry_bytes);
+    const bool tab = !settled(k);
+    mbar_arrive_expect_tx(&bar[bsel],
+                          (uint32_t)cnt * row_bytes * ((RHS ? 1u : 0u) + (tab ? 1u : 0u)) + face_bytes + carry_bytes);
     C* buf = tile + bsel * TILE;
     for (int t = 0; t < cnt; ++t) {
       if (RHS) bulk_g2s(buf + t * kBulkLines, fhat + (s + t) * n1 + l0, row_bytes, &bar[bsel]);
-      bulk_g2s(buf + IU + t * kBulkLines, tb.iu + (s + t) * n1 + l0, row_bytes, &bar[bsel]);
+      if (tab) bulk_g2s(buf + IU + t * kBulkLines, tb.iu + (s + t) * n1 + l0, row_bytes, &bar[bsel]);
     }
     if (FACES) {
       C* fb = buf + FO;
@@ -932,6 +969,7 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
   }
   const LineValues<float, C> lv = line_values<float>(STEP, a, l, consts);
   const C b = lv.co.b, mb = mk<C>(-b.x, -b.y);
+  const C iinf = tb.iinf[l];
   const C zero = mk<C>(0, 0);
   const int64_t nparts = (n1 + kBulkLines - 1) / kBulkLines;
   C iprev = (PASS == 2 && kb > 0) ? tb.iu[(kb * CH - 1) * n1 + l] : zero;  // 1/u of the row before the run
@@ -948,7 +986,9 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
     }
     if (tid == 0) pending &= ~(1u << bsel);
     const C* const frow = tile + bsel * TILE;  // [CH][128] f_hat rows (Steps 1, 3)
-    const C* const irow = frow + IU;           // [CH][128] 1/u rows
+    const C* const irow = frow + IU;           // [CH][128] 1/u rows (not copied for a settled chunk)
+    const bool set = settled(k);                 // block-uniform
+    auto piv = [&](int t) -> C { return set ? iinf : irow[t * kBulkLines + tid]; };
     const C* const sf1 = frow + FO;            // f1[s + t]
     const C* const sfn = sf1 + CH + (int)((nx + s) & 1);  // fn[s + t]
     C yp = zero, xn = zero;
@@ -964,14 +1004,14 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
       return cmul(v, lv.scal);
     };
     if (PASS == 1) {
-      C ylo = rhs(0), w = irow[tid];
+      C ylo = rhs(0), w = piv(0);
       C bsum = cmul(w, ylo);
 #pragma unroll
       for (int t = 1; t < CH; ++t) {
         if (t >= cnt) break;
-        const C m = cmul(b, irow[(t - 1) * kBulkLines + tid]);
+        const C m = cmul(b, piv(t - 1));
         ylo = csub(rhs(t), cmul(m, ylo));
-        w = cmul(cmul(w, mb), irow[t * kBulkLines + tid]);
+        w = cmul(cmul(w, mb), piv(t));
         bsum = cadd(bsum, cmul(w, ylo));
       }
       if (act) {
@@ -985,7 +1025,7 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
         if (t < cnt) {
           yp = csub(rhs(t), cmul(cmul(b, iprev), yp));
           y[t] = yp;
-          iprev = irow[t * kBulkLines + tid];
+          iprev = piv(t);
         }
       }
       // backward sweep; Steps 1, 2 keep their face contributions in
@@ -994,7 +1034,7 @@ __global__ void __launch_bounds__(kBulkLines) k_tri_bulk_t32(const float2* __res
 #pragma unroll
       for (int t = CH - 1; t >= 0; --t) {
         if (t < cnt) {
-          const C x = cmul(csub(y[t], cmul(b, xn)), irow[t * kBulkLines + tid]);
+          const C x = cmul(csub(y[t], cmul(b, xn)), piv(t));
           xn = x;
           if constexpr (!SUMS) {
             if (act) out[(s + t) * n1 + l] = x;
@@ -1252,7 +1292,7 @@ cudaError_t launch_tri2d_t32(int step, const void* fhat, const void* faces, cons
   const unsigned gcar = (unsigned)((a.n1 + kCarryLines - 1) / kCarryLines);
   const dim3 bcar(kCarryLines, kCarrySeg);
   const size_t nrec = (size_t)a.nchunks * a.n1;
-  const LineTables32 tb = line_tables32(const_cast<void*>(tables), (size_t)a.nx * a.n1, nrec);
+  const LineTables32 tb = line_tables32(const_cast<void*>(tables), (size_t)a.nx * a.n1, nrec, (size_t)a.n1);
   RecSoA<float2> r = rec_soa<float2>(rec, nrec);
   r.pe = tb.pe;  // rhs-independent chunk constants live in the tables
   r.cc = tb.cc;
@@ -1309,13 +1349,16 @@ cudaError_t launch_tri2d_t32(int step, const void* fhat, const void* faces, cons
 }
 
 size_t line_tables32_bytes(int64_t nx, int64_t n1, int64_t nchunks) {
-  return (size_t)(nx * n1 + 3 * nchunks * n1) * sizeof(float2);
+  return (size_t)(nx * n1 + 3 * nchunks * n1 + n1) * sizeof(float2) +
+         (size_t)((n1 + kBulkLines - 1) / kBulkLines) * sizeof(int);
 }
 
 cudaError_t launch_line_tables32(void* tables, const Solve2DArgs& a, int step, cudaStream_t st) {
   const int bs = 128;
   const unsigned grid = (unsigned)((a.n1 + bs - 1) / bs);
-  const LineTables32 tb = line_tables32(tables, (size_t)a.nx * a.n1, (size_t)a.nchunks * a.n1);
+  const LineTables32 tb = line_tables32(tables, (size_t)a.nx * a.n1, (size_t)a.nchunks * a.n1, (size_t)a.n1);
+  cudaError_t e = cudaMemsetAsync(tb.lcta, 0, (size_t)((a.n1 + kBulkLines - 1) / kBulkLines) * sizeof(int), st);
+  if (e != cudaSuccess) return e;
   k_line_tables32<<<grid, bs, 0, st>>>(tb, a, step);
   return cudaGetLastError();
 }
