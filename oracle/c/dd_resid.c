@@ -69,11 +69,14 @@ static inline cdd cdd_mul_cd(cdd a, double br, double bi) {
 }
 
 /* 1D entries: X(i, i+d) for X = M (kind 0) or K (kind 1); K complex at
- * absorbing ends (corner 1/h - i wc; wc = 0 for a Neumann axis). */
-static void entry(int64_t n, double h, double omega, int64_t i, int d, int kind, double* re, double* im) {
+ * absorbing ends (corner 1/h - i wc; wc = 0 for a Neumann axis).  M is
+ * h [(den-2)/den on the diagonal, 1/den off it, half the diagonal at the
+ * ends]: den = 6 for the paper's elements, 12 for the modified ones. */
+static void entry(int64_t n, double h, double omega, double den, int64_t i, int d, int kind, double* re,
+                  double* im) {
   int end = (i == 0 || i == n - 1);
   if (kind == 0) {
-    *re = (d == 0) ? (end ? 2.0 : 4.0) * h / 6.0 : h / 6.0;
+    *re = (d == 0) ? (end ? (den - 2.0) / 2.0 : den - 2.0) * h / den : h / den;
     *im = 0.0;
   } else {
     if (d == 0) {
@@ -88,14 +91,14 @@ static void entry(int64_t n, double h, double omega, int64_t i, int d, int kind,
 
 /* Coefficient of neighbour offset d[] at index idx[]: sum over terms of
  * products of 1D entries, each product formed in complex double-double. */
-static cdd coefficient(int dim, const int64_t* n, const double* h, double omega, const double* wc, const int64_t* idx,
-                       const int* d) {
+static cdd coefficient(int dim, const int64_t* n, const double* h, double omega, const double* wc, double den,
+                       const int64_t* idx, const int* d) {
   cdd total = {dd_d(0.0), dd_d(0.0)};
   for (int j = 0; j <= dim; ++j) {
     cdd prod = {dd_d(1.0), dd_d(0.0)};
     for (int k = 0; k < dim; ++k) {
       double er, ei;
-      entry(n[k], h[k], wc[k], idx[k], d[k], (k == j) ? 1 : 0, &er, &ei);
+      entry(n[k], h[k], wc[k], den, idx[k], d[k], (k == j) ? 1 : 0, &er, &ei);
       prod = cdd_mul_cd(prod, er, ei);
     }
     if (j == dim) {
@@ -111,9 +114,9 @@ static cdd coefficient(int dim, const int64_t* n, const double* h, double omega,
 
 /* r = f - A u in double-double.  wc[k]: the w of the absorbing corner of
  * axis k (w itself on an absorbing axis, 0 on a Neumann axis, Section 2's
- * Gamma_A / Gamma_N). */
-void helm_oracle_dd_residual_bc(int dim, const int64_t* n, const double* h, double omega, const double* wc,
-                                const double* f, const double* u, double* r) {
+ * Gamma_A / Gamma_N); den: the mass matrix's denominator (element). */
+void helm_oracle_dd_residual_el(int dim, const int64_t* n, const double* h, double omega, const double* wc,
+                                double den, const double* f, const double* u, double* r) {
   int64_t N = 1;
   for (int k = 0; k < dim; ++k) N *= n[k];
   int64_t stride[3];
@@ -141,7 +144,7 @@ void helm_oracle_dd_residual_bc(int dim, const int64_t* n, const double* h, doub
         off += d[k] * stride[k];
       }
       if (!ok) continue;
-      cdd co = coefficient(dim, n, h, omega, wc, idx, d);
+      cdd co = coefficient(dim, n, h, omega, wc, den, idx, d);
       cdd term = cdd_mul_cd(co, u[2 * (g + off)], u[2 * (g + off) + 1]);
       acc.re = dd_add(acc.re, dd_neg(term.re));
       acc.im = dd_add(acc.im, dd_neg(term.im));
@@ -149,6 +152,12 @@ void helm_oracle_dd_residual_bc(int dim, const int64_t* n, const double* h, doub
     r[2 * g] = acc.re.hi + acc.re.lo;
     r[2 * g + 1] = acc.im.hi + acc.im.lo;
   }
+}
+
+/* The paper's elements, per-axis conditions. */
+void helm_oracle_dd_residual_bc(int dim, const int64_t* n, const double* h, double omega, const double* wc,
+                                const double* f, const double* u, double* r) {
+  helm_oracle_dd_residual_el(dim, n, h, omega, wc, 6.0, f, u, r);
 }
 
 /* Absorbing conditions on every face. */

@@ -13,6 +13,16 @@ Arrays are C-ordered with the last axis fastest.  The 1D matrices are those of
 eqs. matrixK / matrixM; the Kronecker forms are eqs. A2D / A3D; the periodic
 auxiliary operator uses the circulant matrices of eqs. matrixKper / matrixMper
 (eq. B2D / B3D).
+
+Elements (`elem`): "q1", the paper's bilinear / trilinear elements with every
+element integral exact (2-point Gauss rule per axis); "q1mod", the modified
+elements with reduced dispersion that the paper names as applicable (Section
+1, the modified integration rules it cites): every element integral
+(stiffness, mass, boundary mass) by the tensor-product 2-point rule at
++-sqrt(2/3) of the reference half-width.  Both keep the Kronecker form with
+one 1D mass matrix per axis, h [(den-2)/den on the diagonal, 1/den off it,
+half the diagonal at the ends]: den = 6 for "q1", 12 for "q1mod" (the mean of
+the consistent and the lumped mass).
 """
 from __future__ import annotations
 
@@ -27,6 +37,23 @@ from . import dd as ddm
 # appear in products of two linear (per-axis) shape functions.
 _GAUSS_X = np.array([0.5 - 0.5 / np.sqrt(3.0), 0.5 + 0.5 / np.sqrt(3.0)])
 _GAUSS_W = np.array([0.5, 0.5])
+# the modified rule: points at +-sqrt(2/3) of the half-width, equal weights
+_MOD_X = np.array([0.5 - 0.5 * np.sqrt(2.0 / 3.0), 0.5 + 0.5 * np.sqrt(2.0 / 3.0)])
+
+ELEMENTS = ("q1", "q1mod")
+
+
+def _quad_x(elem):
+    if elem not in ELEMENTS:
+        raise ValueError(f"element must be one of {ELEMENTS}")
+    return _GAUSS_X if elem == "q1" else _MOD_X
+
+
+def mass_den(elem):
+    """den of the 1D mass matrix h [(den-2)/den, 1/den] of the element."""
+    if elem not in ELEMENTS:
+        raise ValueError(f"element must be one of {ELEMENTS}")
+    return 6.0 if elem == "q1" else 12.0
 
 
 def _shape_1d(s):
@@ -34,16 +61,18 @@ def _shape_1d(s):
     return np.array([1.0 - s, s]), np.array([-1.0, 1.0])
 
 
-def element_matrix(h, omega):
+def element_matrix(h, omega, elem="q1"):
     """Element matrix of int grad phi_a . grad phi_b - w^2 phi_a phi_b over one
-    box element with edge lengths h (d = len(h)), by tensor Gauss quadrature of
-    the multilinear shape functions (Section 2, weak form).  Local node a is the
-    multi-index (a_1, ..., a_d) in {0,1}^d, in C order."""
+    box element with edge lengths h (d = len(h)), by the element's tensor
+    2-point quadrature of the multilinear shape functions (Section 2, weak
+    form).  Local node a is the multi-index (a_1, ..., a_d) in {0,1}^d, in C
+    order."""
     d = len(h)
+    xq = _quad_x(elem)
     locs = list(itertools.product((0, 1), repeat=d))
     E = np.zeros((2 ** d, 2 ** d), dtype=np.complex128)
     for q in itertools.product(range(2), repeat=d):
-        s = [_GAUSS_X[qi] for qi in q]
+        s = [xq[qi] for qi in q]
         wq = np.prod([_GAUSS_W[qi] * hj for qi, hj in zip(q, h)])
         vals, grads = [], []
         for a in locs:
@@ -60,23 +89,25 @@ def element_matrix(h, omega):
     return E, locs
 
 
-def face_mass_matrix(h_face):
+def face_mass_matrix(h_face, elem="q1"):
     """int_face phi_a phi_b over a (d-1)-dimensional element face with edge
-    lengths h_face, by Gauss quadrature (boundary term of the weak form)."""
+    lengths h_face, by the element's quadrature (boundary term of the weak
+    form)."""
     m = len(h_face)
+    xq = _quad_x(elem)
     locs = list(itertools.product((0, 1), repeat=m))
     F = np.zeros((2 ** m, 2 ** m))
     if m == 0:
         return np.ones((1, 1)), [()]
     for q in itertools.product(range(2), repeat=m):
-        s = [_GAUSS_X[qi] for qi in q]
+        s = [xq[qi] for qi in q]
         wq = np.prod([_GAUSS_W[qi] * hj for qi, hj in zip(q, h_face)])
         vals = [np.prod([_shape_1d(s[j])[0][a[j]] for j in range(m)]) for a in locs]
         F += wq * np.outer(vals, vals)
     return F, locs
 
 
-def assemble(shape, h, omega, bc="abc"):
+def assemble(shape, h, omega, bc="abc", elem="q1"):
     """Global sparse matrix A (CSR, complex128) assembled element by element.
 
     shape: node counts per axis; h: spacings; bc: "abc" on every face, or
@@ -91,7 +122,7 @@ def assemble(shape, h, omega, bc="abc"):
     N = int(np.prod(shape))
     idx = np.arange(N).reshape(shape)
     rows, cols, vals = [], [], []
-    E, locs = element_matrix(h, omega)
+    E, locs = element_matrix(h, omega, elem)
     # element origin nodes
     origin = idx[tuple(slice(0, n - 1) for n in shape)].ravel()
     strides = [int(np.prod(shape[j + 1:])) for j in range(d)]
@@ -107,7 +138,7 @@ def assemble(shape, h, omega, bc="abc"):
         if bc[j] != "abc":
             continue
         other = [k for k in range(d) if k != j]
-        F, flocs = face_mass_matrix([h[k] for k in other])
+        F, flocs = face_mass_matrix([h[k] for k in other], elem)
         for side in (0, shape[j] - 1):
             sl = [slice(0, n - 1) for n in shape]
             sl[j] = side
@@ -137,11 +168,13 @@ def K1d(n, h, omega, bc="abc"):
     return K
 
 
-def M1d(n, h):
-    """Dense 1D mass matrix (eq. matrixM): (h/6) tridiag(1, 4, 1), corners 2."""
-    M = 4.0 * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)
-    M[0, 0] = M[-1, -1] = 2.0
-    return M * (h / 6.0)
+def M1d(n, h, elem="q1"):
+    """Dense 1D mass matrix (eq. matrixM): (h/6) tridiag(1, 4, 1), corners 2;
+    for the modified element (h/12) tridiag(1, 10, 1), corners 5."""
+    den = mass_den(elem)
+    M = (den - 2.0) * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)
+    M[0, 0] = M[-1, -1] = (den - 2.0) / 2.0
+    return M * (h / den)
 
 
 def K1d_periodic(n, h, gamma=1.0):
@@ -155,15 +188,16 @@ def K1d_periodic(n, h, gamma=1.0):
     return K / h
 
 
-def M1d_periodic(n, h, gamma=1.0):
+def M1d_periodic(n, h, gamma=1.0, elem="q1"):
     """Circulant mass matrix of eq. matrixMper (gamma-circulant as above)."""
-    M = (4.0 * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)).astype(np.complex128)
+    den = mass_den(elem)
+    M = ((den - 2.0) * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)).astype(np.complex128)
     M[-1, 0] = 1.0 * gamma
     M[0, -1] = 1.0 / gamma
-    return M * (h / 6.0)
+    return M * (h / den)
 
 
-def kron_operator(shape, h, omega, periodic_axis=None, bc="abc", gamma=None):
+def kron_operator(shape, h, omega, periodic_axis=None, bc="abc", gamma=None, elem="q1"):
     """Sparse Kronecker-form operator: eq. A2D / A3D, or with `periodic_axis`
     replaced by the circulant matrices, eq. B2D / B3D.  `gamma` (a scalar,
     or a dict axis -> gamma; periodic_axis may then be a tuple) selects the
@@ -180,10 +214,10 @@ def kron_operator(shape, h, omega, periodic_axis=None, bc="abc", gamma=None):
         if j in paxes:
             g = 1.0 if gamma is None else (gamma[j] if isinstance(gamma, dict) else gamma)
             Ks.append(sp.csr_matrix(K1d_periodic(shape[j], h[j], g)))
-            Ms.append(sp.csr_matrix(M1d_periodic(shape[j], h[j], g)))
+            Ms.append(sp.csr_matrix(M1d_periodic(shape[j], h[j], g, elem)))
         else:
             Ks.append(sp.csr_matrix(K1d(shape[j], h[j], omega, bc[j])))
-            Ms.append(sp.csr_matrix(M1d(shape[j], h[j])))
+            Ms.append(sp.csr_matrix(M1d(shape[j], h[j], elem)))
 
     def kron_all(mats):
         out = mats[0]
@@ -201,8 +235,11 @@ def kron_operator(shape, h, omega, periodic_axis=None, bc="abc", gamma=None):
 # Closed-form 1D eigenvalues of the linear-FEM pencils
 # ---------------------------------------------------------------------------
 
-def _ratio(theta, h):
-    return 6.0 / h ** 2 * (1.0 - np.cos(theta)) / (2.0 + np.cos(theta))
+def _ratio(theta, h, elem="q1"):
+    if elem == "q1":
+        return 6.0 / h ** 2 * (1.0 - np.cos(theta)) / (2.0 + np.cos(theta))
+    den = mass_den(elem)
+    return (2.0 - 2.0 * np.cos(theta)) / h / (h * ((den - 2.0) + 2.0 * np.cos(theta)) / den)
 
 
 def eig_periodic(n, h):
@@ -219,9 +256,9 @@ def eig_periodic_closed(n, h):
     return _ratio(2.0 * np.pi * np.arange(n) / n, h)
 
 
-def eig_neumann(n, h):
+def eig_neumann(n, h, elem="q1"):
     """Eigenvalues of the Neumann pencil (k11 = 1): theta_k = k pi/(n-1), k=0..n-1."""
-    return _ratio(np.pi * np.arange(n) / (n - 1), h)
+    return _ratio(np.pi * np.arange(n) / (n - 1), h, elem)
 
 
 def eig_dirichlet(n, h):
@@ -238,7 +275,7 @@ def _bc_tuple(bc, d):
     return (bc,) * d if isinstance(bc, str) else tuple(bc)
 
 
-def _tri_coeffs(n, h, omega, kind, bc="abc"):
+def _tri_coeffs(n, h, omega, kind, bc="abc", elem="q1"):
     """(sub, diag, super) coefficient vectors of a 1D matrix from eqs.
     matrixK / matrixM; sub[j] multiplies x[j-1], super[j] multiplies x[j+1].
     K's corners are 1/h - i w on an absorbing axis, 1/h on a Neumann one."""
@@ -247,9 +284,10 @@ def _tri_coeffs(n, h, omega, kind, bc="abc"):
         diag[0] = diag[-1] = (1.0 / h - 1j * omega) if bc == "abc" else 1.0 / h
         off = -1.0 / h
     else:
-        diag = np.full(n, 4.0 * h / 6.0, dtype=np.complex128)
-        diag[0] = diag[-1] = 2.0 * h / 6.0
-        off = h / 6.0
+        den = mass_den(elem)
+        diag = np.full(n, (den - 2.0) * h / den, dtype=np.complex128)
+        diag[0] = diag[-1] = ((den - 2.0) / 2.0) * h / den
+        off = h / den
     sub = np.full(n, off, dtype=np.complex128)
     sup = np.full(n, off, dtype=np.complex128)
     sub[0] = 0.0
@@ -263,10 +301,10 @@ def _bshape(n, axis, d):
     return s
 
 
-def apply_1d(u, axis, n, h, omega, kind, bc="abc"):
+def apply_1d(u, axis, n, h, omega, kind, bc="abc", elem="q1"):
     """y = T u along `axis`, T the 1D matrix K or M, complex128."""
     d = u.ndim
-    sub, diag, sup = (c.reshape(_bshape(n, axis, d)) for c in _tri_coeffs(n, h, omega, kind, bc))
+    sub, diag, sup = (c.reshape(_bshape(n, axis, d)) for c in _tri_coeffs(n, h, omega, kind, bc, elem))
     y = diag * u
     lo = [slice(None)] * d
     hi = [slice(None)] * d
@@ -277,7 +315,7 @@ def apply_1d(u, axis, n, h, omega, kind, bc="abc"):
     return y
 
 
-def apply_A(u, h, omega, bc="abc"):
+def apply_A(u, h, omega, bc="abc", elem="q1"):
     """A u for the Kronecker form of eqs. A2D / A3D, complex128 (bc: per
     axis "abc" or "neumann", or one of them for every axis)."""
     shape = u.shape
@@ -288,16 +326,16 @@ def apply_A(u, h, omega, bc="abc"):
         t = u
         for k in range(d):
             kind = "K" if k == j else "M"
-            t = apply_1d(t, k, shape[k], h[k], omega, kind, bc[k])
+            t = apply_1d(t, k, shape[k], h[k], omega, kind, bc[k], elem)
         if j == d:
             t = -omega ** 2 * t
         total = t if total is None else total + t
     return total
 
 
-def _apply_1d_dd(x: ddm.CDD, axis, n, h, omega, kind, bc="abc"):
+def _apply_1d_dd(x: ddm.CDD, axis, n, h, omega, kind, bc="abc", elem="q1"):
     d = x.re[0].ndim
-    sub, diag, sup = (c.reshape(_bshape(n, axis, d)) for c in _tri_coeffs(n, h, omega, kind, bc))
+    sub, diag, sup = (c.reshape(_bshape(n, axis, d)) for c in _tri_coeffs(n, h, omega, kind, bc, elem))
 
     def shift(a, direction):
         # direction +1: out[j] = a[j-1]; -1: out[j] = a[j+1]; zero fill
@@ -318,7 +356,7 @@ def _apply_1d_dd(x: ddm.CDD, axis, n, h, omega, kind, bc="abc"):
     return y
 
 
-def residual_dd(f, u, h, omega, bc="abc"):
+def residual_dd(f, u, h, omega, bc="abc", elem="q1"):
     """r = f - A u with A of eqs. A2D / A3D, every operation in double-double,
     rounded to complex128 at the end."""
     shape = u.shape
@@ -329,7 +367,7 @@ def residual_dd(f, u, h, omega, bc="abc"):
     for j in range(d + 1):
         t = U
         for k in range(d):
-            t = _apply_1d_dd(t, k, shape[k], h[k], omega, "K" if k == j else "M", bc[k])
+            t = _apply_1d_dd(t, k, shape[k], h[k], omega, "K" if k == j else "M", bc[k], elem)
         if j == d:
             t = t.mul_c(-omega ** 2)
         acc = acc - t
@@ -340,7 +378,7 @@ def residual_dd(f, u, h, omega, bc="abc"):
 # Plane-wave manufactured solution with inhomogeneous absorbing data
 # ---------------------------------------------------------------------------
 
-def plane_wave_load(shape, h, omega, direction):
+def plane_wave_load(shape, h, omega, direction, elem="q1"):
     """Load vector and nodal exact solution for u* = exp(i w d.x), |d| = 1.
 
     u* solves -Lap u - w^2 u = 0 exactly.  On the face with outward normal n the
@@ -366,13 +404,13 @@ def plane_wave_load(shape, h, omega, direction):
             for k in range(d):
                 if k == j:
                     continue
-                t = apply_1d(t, ax, shape[k], h[k], omega, "M")
+                t = apply_1d(t, ax, shape[k], h[k], omega, "M", elem=elem)
                 ax += 1
             f[sl] += t
     return f, u_exact
 
 
-def residual_dd_c(f, u, h, omega, bc="abc"):
+def residual_dd_c(f, u, h, omega, bc="abc", elem="q1"):
     """Same double-double residual as `residual_dd`, computed by the oracle's
     C helper (oracle/c/dd_resid.c) for large grids."""
     from . import cbuild
@@ -382,11 +420,11 @@ def residual_dd_c(f, u, h, omega, bc="abc"):
     n = np.array(u.shape, dtype=np.int64)
     hh = np.array(h, dtype=np.float64)
     r = np.empty_like(u)
-    if isinstance(bc, str) and bc == "abc":
+    if isinstance(bc, str) and bc == "abc" and elem == "q1":
         cbuild.lib().helm_oracle_dd_residual(u.ndim, n.ctypes.data, hh.ctypes.data, float(omega), f.ctypes.data,
                                              u.ctypes.data, r.ctypes.data)
         return r
     wc = np.array([float(omega) if b == "abc" else 0.0 for b in _bc_tuple(bc, u.ndim)], dtype=np.float64)
-    cbuild.lib().helm_oracle_dd_residual_bc(u.ndim, n.ctypes.data, hh.ctypes.data, float(omega), wc.ctypes.data,
-                                            f.ctypes.data, u.ctypes.data, r.ctypes.data)
+    cbuild.lib().helm_oracle_dd_residual_el(u.ndim, n.ctypes.data, hh.ctypes.data, float(omega), wc.ctypes.data,
+                                            float(mass_den(elem)), f.ctypes.data, u.ctypes.data, r.ctypes.data)
     return r

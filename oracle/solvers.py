@@ -34,7 +34,7 @@ from . import fem
 # O1: assembled banded LU
 # ---------------------------------------------------------------------------
 
-def solve_banded_lu(f, h, omega, bc="abc"):
+def solve_banded_lu(f, h, omega, bc="abc", elem="q1"):
     """u = A^-1 f with A assembled element by element (fem.assemble) and
     factorised by banded LU with partial pivoting.  Axes are reordered so the
     longest axis is slowest, which minimises the bandwidth."""
@@ -44,7 +44,7 @@ def solve_banded_lu(f, h, omega, bc="abc"):
     fp = np.ascontiguousarray(np.transpose(f, order))
     hp = tuple(h[j] for j in order)
     bcp = bc if isinstance(bc, str) else tuple(bc[j] for j in order)
-    A = fem.assemble(fp.shape, hp, omega, bcp).tocoo()
+    A = fem.assemble(fp.shape, hp, omega, bcp, elem).tocoo()
     bw = int(np.max(np.abs(A.row - A.col)))
     N = fp.size
     ab = np.zeros((2 * bw + 1, N), dtype=np.complex128)
@@ -55,10 +55,10 @@ def solve_banded_lu(f, h, omega, bc="abc"):
     return np.ascontiguousarray(np.transpose(u, inv))
 
 
-def solve_dense(f, h, omega, bc="abc"):
+def solve_dense(f, h, omega, bc="abc", elem="q1"):
     """Brute force for tiny grids: dense LU of the assembled A."""
     f = np.asarray(f, dtype=np.complex128)
-    A = fem.assemble(f.shape, h, omega, bc).toarray()
+    A = fem.assemble(f.shape, h, omega, bc, elem).toarray()
     return np.linalg.solve(A, f.ravel()).reshape(f.shape)
 
 
@@ -66,7 +66,7 @@ def solve_dense(f, h, omega, bc="abc"):
 # O2: tensor-product eigen-solve
 # ---------------------------------------------------------------------------
 
-def abc_pencil_eig(n, h, omega, bc="abc"):
+def abc_pencil_eig(n, h, omega, bc="abc", elem="q1"):
     """Eigenpairs of K V = M V Lam (eq. EVP1a) normalised so V^T M V = I
     (eq. EVPcondA; transpose, not conjugate transpose).
 
@@ -74,7 +74,7 @@ def abc_pencil_eig(n, h, omega, bc="abc"):
     complex symmetric, C Y = Y Lam by LAPACK geev, V = L^-T Y, then each column
     is scaled by 1/sqrt(v^T M v) (eqs. sA, sAnorm)."""
     K = fem.K1d(n, h, omega, bc)
-    M = fem.M1d(n, h)
+    M = fem.M1d(n, h, elem)
     L = np.linalg.cholesky(M)
     Li = sl.solve_triangular(L, np.eye(n), lower=True)
     C = Li @ K @ Li.T
@@ -102,15 +102,16 @@ class TensorSolver:
     """O2: A^-1 = (V_a (x) ... (x) I) H^-1 (V_a^T (x) ... (x) I) with one axis
     (`tri_axis`) kept as tridiagonal blocks (eqs. A2Dinv, HA2D, A3Dinv, HA3D)."""
 
-    def __init__(self, shape, h, omega, tri_axis=None, bc="abc"):
+    def __init__(self, shape, h, omega, tri_axis=None, bc="abc", elem="q1"):
         self.shape = tuple(shape)
         self.h = tuple(h)
         self.omega = float(omega)
         d = len(shape)
         self.bc = fem._bc_tuple(bc, d)
+        self.elem = elem
         self.tri_axis = int(np.argmax(shape)) if tri_axis is None else tri_axis
         self.eig_axes = [j for j in range(d) if j != self.tri_axis]
-        self.eigs = {j: abc_pencil_eig(shape[j], h[j], omega, self.bc[j]) for j in self.eig_axes}
+        self.eigs = {j: abc_pencil_eig(shape[j], h[j], omega, self.bc[j], elem) for j in self.eig_axes}
 
     def _transform(self, x, transpose):
         for j in self.eig_axes:
@@ -137,7 +138,7 @@ class TensorSolver:
         s = lam_lines - self.omega ** 2
         # line matrix: K_t + (lam - w^2) M_t   (eq. HA2D block)
         subK, diagK, _ = fem._tri_coeffs(n, ht, self.omega, "K", self.bc[t])
-        subM, diagM, _ = fem._tri_coeffs(n, ht, self.omega, "M")
+        subM, diagM, _ = fem._tri_coeffs(n, ht, self.omega, "M", elem=self.elem)
         diag = diagK[None, :] + s[:, None] * diagM[None, :]
         off = subK[1:][None, :] + s[:, None] * subM[1:][None, :]
         x = _tridiag_solve_lines(off.copy(), diag, off.copy(), g_lines.copy())
@@ -146,40 +147,42 @@ class TensorSolver:
         return np.ascontiguousarray(self._transform(x, transpose=False))
 
 
-def refine(f, u, solve, h, omega, iters=2, bc="abc"):
+def refine(f, u, solve, h, omega, iters=2, bc="abc", elem="q1"):
     """Iterative refinement u <- u + solve(f - A u) with the residual formed in
     double-double (fem.residual_dd).  Returns (u, [relative residuals])."""
     hist = []
     fn = np.linalg.norm(f)
     resid = fem.residual_dd_c if f.size > 4096 else fem.residual_dd
     for _ in range(iters):
-        r = resid(f, u, h, omega, bc)
+        r = resid(f, u, h, omega, bc, elem)
         hist.append(float(np.linalg.norm(r) / fn))
         u = u + solve(r)
-    r = resid(f, u, h, omega, bc)
+    r = resid(f, u, h, omega, bc, elem)
     hist.append(float(np.linalg.norm(r) / fn))
     return u, hist
 
 
-def oracle_solve(f, h, omega, method="auto", iters=2, tri_axis=None, bc="abc"):
+def oracle_solve(f, h, omega, method="auto", iters=2, tri_axis=None, bc="abc", elem="q1"):
     """u = A^-1 f: O1 (banded LU) for small problems, O2 (tensor eigen-solve)
     otherwise, followed by double-double iterative refinement.  bc: "abc"
     (absorbing faces everywhere), or per axis "abc" / "neumann" (Section 2's
-    Gamma_A / Gamma_N: both faces of an axis of the same kind)."""
+    Gamma_A / Gamma_N: both faces of an axis of the same kind).  elem: "q1"
+    (the paper's elements) or "q1mod" (the modified elements, see
+    oracle.fem)."""
     f = np.asarray(f, dtype=np.complex128)
     if method == "auto":
         srt = sorted(f.shape)
         bw = int(np.prod(srt[:-1])) if f.ndim > 1 else 1
         method = "banded" if bw * f.size <= 3e8 else "tensor"
     if method == "banded":
-        solve = lambda r: solve_banded_lu(r, h, omega, bc)
+        solve = lambda r: solve_banded_lu(r, h, omega, bc, elem)
     elif method == "dense":
-        solve = lambda r: solve_dense(r, h, omega, bc)
+        solve = lambda r: solve_dense(r, h, omega, bc, elem)
     else:
-        ts = TensorSolver(f.shape, h, omega, tri_axis, bc)
+        ts = TensorSolver(f.shape, h, omega, tri_axis, bc, elem)
         solve = ts.solve
     u = solve(f)
-    u, hist = refine(f, u, solve, h, omega, iters=iters, bc=bc)
+    u, hist = refine(f, u, solve, h, omega, iters=iters, bc=bc, elem=elem)
     return u, hist
 
 

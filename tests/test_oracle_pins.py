@@ -405,3 +405,96 @@ def test_mlp_oracle_forward_by_hand():
     h1 = np.tanh(0.3 * 2.0 - 0.1)
     h2 = np.tanh(0.7 * h1 + 0.2)
     assert y[0] == pytest.approx(-1.5 * h2 + 0.25, abs=1e-15)
+
+
+# ------------------ the modified (reduced-dispersion) elements -------------
+
+def test_modified_element_1d_matrices_by_hand():
+    """The modified rule's 1D mass: h/12 (1, 10, 1) with corners 5h/12 (the
+    mean of the consistent and the lumped mass); the stiffness is unchanged
+    (the quadrature integrates the constant derivatives exactly)."""
+    n, h = 5, 0.3
+    M = fem.M1d(n, h, "q1mod")
+    ref = (np.diag([5, 10, 10, 10, 5]) + np.eye(n, k=1) + np.eye(n, k=-1)) * h / 12
+    np.testing.assert_allclose(M, ref, rtol=1e-15, atol=0)
+    Mc, Ml = fem.M1d(n, h, "q1"), np.diag([0.5, 1, 1, 1, 0.5]) * h
+    np.testing.assert_allclose(M, 0.5 * (Mc + Ml), rtol=1e-14, atol=1e-16)
+    # element assembly in 1D reproduces it
+    A1 = fem.assemble((n,), (h,), 0.0, "neumann", elem="q1mod").toarray()
+    A2 = fem.assemble((n,), (h,), 1.0, "neumann", elem="q1mod").toarray()
+    np.testing.assert_allclose(A1 - A2, M, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("shape,h,bc", [((5, 7), (0.3, 0.2), "abc"), ((6, 4), (0.1, 0.25), ("neumann", "abc")),
+                                        ((4, 5, 3), (0.2, 0.15, 0.3), "abc"),
+                                        ((3, 4, 5), (0.3, 0.2, 0.1), ("abc", "neumann", "abc"))])
+def test_modified_element_assembly_equals_kronecker_form(shape, h, bc):
+    """Element-by-element assembly with the modified rule (every integral,
+    boundary mass included) equals the Kronecker form with the modified 1D
+    mass on every axis: the tensor structure the fast solver needs."""
+    om = 3.7
+    A = fem.assemble(shape, h, om, bc, elem="q1mod").toarray()
+    B = fem.kron_operator(shape, h, om, bc=bc, elem="q1mod").toarray()
+    assert np.abs(A - B).max() <= 1e-12 * np.abs(B).max()
+    assert np.abs(A - fem.assemble(shape, h, om, bc).toarray()).max() > 1e-3 * np.abs(B).max()
+    u = random_rhs(shape, 3)
+    np.testing.assert_allclose(fem.apply_A(u, h, om, bc, elem="q1mod").ravel(), B @ u.ravel(), rtol=1e-12, atol=1e-12)
+
+
+def test_modified_element_dispersion_is_fourth_order():
+    """A sampled plane wave exp(i k d.x) with |k| = w makes the interior
+    stencil's defect (A u) / ((M (x) M) u) = sum_j K^_j/M^_j - w^2 vanish to
+    fourth order in w h for the modified elements, to second order for the
+    paper's (the defect falls ~16x and ~4x per halving of h)."""
+    om, d = 20.0, np.array([np.cos(0.7), np.sin(0.7)])
+    defects = {}
+    for elem in ("q1", "q1mod"):
+        out = []
+        for n in (41, 81, 161):
+            h = (1.0 / (n - 1),) * 2
+            x = np.meshgrid(*[np.arange(n) * hh for hh in h], indexing="ij")
+            u = np.exp(1j * om * (d[0] * x[0] + d[1] * x[1]))
+            Au = fem.apply_A(u, h, om, "neumann", elem=elem)
+            Mu = fem.apply_1d(fem.apply_1d(u, 0, n, h[0], om, "M", "neumann", elem), 1, n, h[1], om, "M", "neumann",
+                              elem)
+            c = n // 2
+            out.append(abs(Au[c, c] / Mu[c, c]) / om ** 2)
+        defects[elem] = out
+    r2 = [defects["q1"][i] / defects["q1"][i + 1] for i in range(2)]
+    r4 = [defects["q1mod"][i] / defects["q1mod"][i + 1] for i in range(2)]
+    assert all(3.8 < r < 4.2 for r in r2), defects
+    assert all(15.0 < r < 17.0 for r in r4), defects
+    assert defects["q1mod"][-1] < 1e-3 * defects["q1"][-1]
+
+
+@pytest.mark.parametrize("n,h", [(9, 0.125), (16, 0.07)])
+def test_modified_element_closed_form_eigenvalues(n, h):
+    """Neumann pencil with the modified mass: the cosine closed form equals
+    LAPACK's generalised symmetric eigenvalues."""
+    K = fem.K1d(n, h, 0.0, "neumann").real
+    M = fem.M1d(n, h, "q1mod")
+    ref = np.sort(sl.eigh(K, M, eigvals_only=True))
+    np.testing.assert_allclose(np.sort(fem.eig_neumann(n, h, "q1mod")), ref, rtol=1e-11, atol=1e-9)
+
+
+@pytest.mark.parametrize("shape,h,bc", [((9, 7), (0.11, 0.14), "abc"), ((6, 5, 7), (0.2, 0.25, 0.15), "abc"),
+                                        ((8, 6), (0.12, 0.2), ("neumann", "abc"))])
+def test_modified_element_solvers_and_residual(shape, h, bc):
+    """O1 and O2 with the modified elements agree with dense LU of the
+    element-assembled matrix; the C double-double residual equals the numpy
+    one bit for bit."""
+    om = 6.1
+    f = random_rhs(shape, 21)
+    u0 = solvers.solve_dense(f, h, om, bc, elem="q1mod")
+    n0 = np.linalg.norm(u0)
+    assert np.linalg.norm(solvers.solve_banded_lu(f, h, om, bc, elem="q1mod") - u0) / n0 < 1e-12
+    for t in range(len(shape)):
+        u3 = solvers.TensorSolver(shape, h, om, tri_axis=t, bc=bc, elem="q1mod").solve(f)
+        assert np.linalg.norm(u3 - u0) / n0 < 1e-11
+    # residual of a perturbed load (|r| ~ 1e-9: the two summation orders agree
+    # after rounding to double)
+    A = fem.assemble(shape, h, om, bc, elem="q1mod")
+    f2 = (A @ u0.ravel()).reshape(shape) + 1e-9 * random_rhs(shape, 22)
+    r1 = fem.residual_dd(f2, u0, h, om, bc, elem="q1mod")
+    assert np.array_equal(r1, fem.residual_dd_c(f2, u0, h, om, bc, elem="q1mod"))
+    np.testing.assert_allclose(r1.ravel(), f2.ravel() - A @ u0.ravel(), rtol=0, atol=1e-13)
