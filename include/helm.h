@@ -76,6 +76,26 @@ enum helm_bc {
   HELM_BC_NEUMANN = 1
 };
 
+/* Elements (Section 1 names the modified ones as applicable to the solver).
+ * HELM_ELEMENT_Q1: the bilinear / trilinear elements of Section 2 with every
+ *   integral exact (eqs. matrixK, matrixM: M = (h/6) tridiag(1, 4, 1)).
+ * HELM_ELEMENT_Q1_MODIFIED: every element integral (stiffness, mass and the
+ *   absorbing boundary term) by the tensor-product 2-point rule at +-sqrt(2/3)
+ *   of the reference half-width, the modified integration that cuts the
+ *   dispersion error to fourth order: K unchanged, M = (h/12) tridiag(1, 10,
+ *   1) with corners 5h/12 on every axis.  The operator keeps the Kronecker
+ *   form of eqs. A2D / A3D, so Steps 1-3 apply unchanged. */
+enum helm_element {
+  HELM_ELEMENT_Q1 = 0,
+  HELM_ELEMENT_Q1_MODIFIED = 1
+};
+
+/* Plan options of helm_plan_2d_ex / helm_plan_3d_ex. */
+struct helm_plan_opts {
+  int32_t axis_bc[3]; /* helm_bc of each axis (entries beyond the dimension ignored) */
+  int32_t element;    /* helm_element */
+};
+
 enum helm_status {
   HELM_OK = 0,
   HELM_EINVAL = -1,        /* bad argument (sizes, spacings, w, null pointer) */
@@ -109,6 +129,7 @@ typedef struct helm_info {
   int32_t axis_bc[3];      /* helm_bc of each axis (HELM_BC_ABC beyond dim) */
   int32_t fp64_lines;      /* inner lines solved in FP64 by precision routing
                               (3D complex64 plans; see helm_set_precision_routing) */
+  int32_t element;         /* helm_element of the plan */
 } helm_info;
 
 /* --- Plan (the paper's "Initialization", Section 6) -----------------------
@@ -141,6 +162,15 @@ int helm_plan_2d_bc(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double 
                     double omega, int dtype, const int32_t* axis_bc);
 int helm_plan_3d_bc(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx,
                     double hy, double hz, double omega, int dtype, const int32_t* axis_bc);
+
+/* The same plans with options: per-axis boundary conditions as for the _bc
+ * calls, and the element (helm_element; HELM_EINVAL for another value).
+ * opts = NULL: absorbing faces everywhere and HELM_ELEMENT_Q1. */
+int helm_plan_2d_ex(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy,
+                    double omega, int dtype, const struct helm_plan_opts* opts);
+int helm_plan_3d_ex(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx,
+                    double hy, double hz, double omega, int dtype,
+                    const struct helm_plan_opts* opts);
 
 /* Auxiliary problem B.  The paper makes x1 periodic (eqs. matrixKper,
  * matrixMper).  Here the wrap-around entries of those circulant matrices are

@@ -25,6 +25,7 @@ lib = ctypes.CDLL(_LIB_PATH)
 HELM_C128, HELM_C64_REFINED, HELM_C64_RAW = 0, 1, 2
 HELM_RESID_FP64, HELM_RESID_FF = 0, 1
 HELM_BC_ABC, HELM_BC_NEUMANN = 0, 1
+HELM_ELEMENT_Q1, HELM_ELEMENT_Q1_MODIFIED = 0, 1
 HELM_VARIANT_INNER_CHUNK, HELM_VARIANT_INNER_TILES, HELM_VARIANT_TRI2D, HELM_VARIANT_DFT = 0, 1, 2, 3
 HELM_OK, HELM_EINVAL, HELM_ENOMEM, HELM_ECUDA, HELM_ENOTCONV, HELM_ETIMEOUT, HELM_EUNSUPPORTED, HELM_ENUMERIC = \
     0, -1, -2, -3, -4, -5, -6, -7
@@ -39,7 +40,11 @@ class helm_info(ctypes.Structure):
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("n_dft_stages", ctypes.c_int32),
                 ("device_bytes", ctypes.c_size_t), ("residual_kind", ctypes.c_int32),
                 ("aux_q", ctypes.c_int32), ("aux_rho", ctypes.c_double), ("aux_trial_residual", ctypes.c_double),
-                ("axis_bc", ctypes.c_int32 * 3), ("fp64_lines", ctypes.c_int32)]
+                ("axis_bc", ctypes.c_int32 * 3), ("fp64_lines", ctypes.c_int32), ("element", ctypes.c_int32)]
+
+
+class helm_plan_opts(ctypes.Structure):
+    _fields_ = [("axis_bc", ctypes.c_int32 * 3), ("element", ctypes.c_int32)]
 
 
 class helm_profile_entry(ctypes.Structure):
@@ -72,6 +77,8 @@ _SIGS = {
     "helm_plan_2d": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _dbl, _dbl, _dbl, _i32]),
     "helm_plan_3d": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _i64, _dbl, _dbl, _dbl, _dbl, _i32]),
     "helm_plan_2d_bc": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _dbl, _dbl, _dbl, _i32, ctypes.POINTER(_i32)]),
+    "helm_plan_2d_ex": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _dbl, _dbl, _dbl, _i32, _vp]),
+    "helm_plan_3d_ex": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _i64, _dbl, _dbl, _dbl, _dbl, _i32, _vp]),
     "helm_plan_3d_bc": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _i64, _dbl, _dbl, _dbl, _dbl, _i32,
                                ctypes.POINTER(_i32)]),
     "helm_set_precision_routing": (_i32, [_vp, _dbl]),
@@ -172,6 +179,30 @@ def helm_plan_2d_bc(nx, ny, hx, hy, omega, dtype, axis_bc):
     bc = (_i32 * 2)(*[int(b) for b in axis_bc])
     _check(lib.helm_plan_2d_bc(ctypes.byref(h), int(nx), int(ny), float(hx), float(hy), float(omega), int(dtype), bc),
            "helm_plan_2d_bc")
+    return h
+
+
+def plan_opts(axis_bc=None, element=HELM_ELEMENT_Q1):
+    """helm_plan_opts: per-axis helm_bc values (default absorbing) and the
+    element."""
+    o = helm_plan_opts()
+    for k, b in enumerate(axis_bc or ()):
+        o.axis_bc[k] = int(b)
+    o.element = int(element)
+    return o
+
+
+def helm_plan_2d_ex(nx, ny, hx, hy, omega, dtype, opts):
+    h = _vp()
+    _check(lib.helm_plan_2d_ex(ctypes.byref(h), int(nx), int(ny), float(hx), float(hy), float(omega), int(dtype),
+                               ctypes.byref(opts)), "helm_plan_2d_ex")
+    return h
+
+
+def helm_plan_3d_ex(nx, ny, nz, hx, hy, hz, omega, dtype, opts):
+    h = _vp()
+    _check(lib.helm_plan_3d_ex(ctypes.byref(h), int(nx), int(ny), int(nz), float(hx), float(hy), float(hz),
+                               float(omega), int(dtype), ctypes.byref(opts)), "helm_plan_3d_ex")
     return h
 
 
@@ -301,15 +332,23 @@ def helm_dft_factor(n):
 class Plan:
     """Owns one helm plan; solve(f, u) on torch CUDA tensors, current stream."""
 
-    def __init__(self, shape, h, omega, dtype=HELM_C128, bc=None):
+    def __init__(self, shape, h, omega, dtype=HELM_C128, bc=None, element=HELM_ELEMENT_Q1):
         """bc: None (absorbing faces everywhere) or one HELM_BC_* (or "abc" /
-        "neumann") per axis."""
+        "neumann") per axis; element: HELM_ELEMENT_Q1 (or "q1") or
+        HELM_ELEMENT_Q1_MODIFIED (or "q1mod")."""
         shape = tuple(int(n) for n in shape)
         self.shape = shape
         self.dtype = dtype
         if bc is not None:
             bc = [HELM_BC_NEUMANN if b in ("neumann", HELM_BC_NEUMANN) else HELM_BC_ABC for b in bc]
-        if len(shape) == 2:
+        element = {"q1": HELM_ELEMENT_Q1, "q1mod": HELM_ELEMENT_Q1_MODIFIED}.get(element, element)
+        if len(shape) not in (2, 3):
+            raise ValueError("shape must be 2D or 3D")
+        if element != HELM_ELEMENT_Q1:
+            opts = plan_opts(bc, element)
+            self.handle = (helm_plan_2d_ex(shape[0], shape[1], h[0], h[1], omega, dtype, opts) if len(shape) == 2
+                           else helm_plan_3d_ex(shape[0], shape[1], shape[2], h[0], h[1], h[2], omega, dtype, opts))
+        elif len(shape) == 2:
             self.handle = (helm_plan_2d(shape[0], shape[1], h[0], h[1], omega, dtype) if bc is None else
                            helm_plan_2d_bc(shape[0], shape[1], h[0], h[1], omega, dtype, bc))
         elif len(shape) == 3:

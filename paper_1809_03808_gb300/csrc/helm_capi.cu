@@ -88,6 +88,8 @@ struct helm_plan {
   cudaEvent_t fork = nullptr;
   int rhs_concurrency = 4;
   int dft_gemm = 0;  // HELM_VARIANT_DFT: row transforms on the tensor cores
+  int element = HELM_ELEMENT_Q1;  // helm_element of the plan
+  double mden = 6.0;              // its mass matrix denominator (MassCoef)
   int tri_regs = 0;  // 2D complex64: register-tile passes (variant HELM_VARIANT_TRI2D = 1)
   int last_many = 0;  // workspaces used by the last helm_solve_many (0: none)
 };
@@ -251,7 +253,9 @@ int build_axis_aux(helm_plan* p, AxisData& a, double rho, int q) {
     const std::complex<double> sh(std::sinh(ar) * std::cos(b), std::cosh(ar) * std::sin(b));
     const std::complex<double> s2 = sh * sh;
     const std::complex<double> kappa = -4.0 * s2 / h;
-    const std::complex<double> mu = h * (1.0 + (2.0 / 3.0) * s2);
+    // mu = h ((den - 2) + 2 cosh z)/den = h (1 + (4/den) sinh^2(z/2)),
+    // den = 6 for the paper's elements
+    const std::complex<double> mu = h * (1.0 + (4.0 / p->mden) * s2);
     const std::complex<double> lb = kappa / mu, im = 1.0 / mu;
     lamB[2 * l] = lb.real();
     lamB[2 * l + 1] = lb.imag();
@@ -381,7 +385,7 @@ int build_axis(helm_plan* p, AxisData& a, int64_t n, double h, double wc, double
     tw32[2 * l] = (float)twre[l];
     tw32[2 * l + 1] = (float)twim[l];
   }
-  int rc = abc_eigen(n, h, wc, lamA.data(), sigA.data(), par8.data());
+  int rc = abc_eigen(n, h, wc, lamA.data(), sigA.data(), par8.data(), p->mden);
   if (rc != HELM_OK) {
     p->err = "absorbing-pencil eigenvalue iteration failed";
     return rc;
@@ -410,6 +414,7 @@ Solve2DArgs args2d(const helm_plan* p) {
   a.wx = p->wc[0];
   a.wy = p->wc[1];
   a.tri_regs = p->tri_regs;
+  a.mden = p->mden;
   return a;
 }
 
@@ -452,7 +457,7 @@ int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int 
   if (dbg_v) HELM_CK(cudaMemcpyAsync(dbg_v, fv, 2 * nx * cb, cudaMemcpyDeviceToDevice, st));
   // a3: Step 2
   HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, nullptr, fc, nx, p->h[0], p->h[1], p->wc[0], p->wc[1], p->omega * p->omega, ax.g,
-                                        ax.ginv, skip, st));
+                                        ax.ginv, skip, st, p->mden));
   if (p->tabA && prec == kPrecF64)
     HELM_CK(launch_tri2d_tab(2, nullptr, fc, p->tabA, p->rec, nullptr, p->partial, a, skip, st, p->prof.on ? &p->prof : nullptr));
   else if (p->tabA)
@@ -464,7 +469,7 @@ int solve2d_core(helm_plan* p, const void* in, int in_is_double, void* out, int 
   if (dbg_w) HELM_CK(cudaMemcpyAsync(dbg_w, fw, 2 * nx * cb, cudaMemcpyDeviceToDevice, st));
   // a4: Step 3
   HELM_PK("apply_cbb", launch_apply_cbb(prec, fv, fw, fc, nx, p->h[0], p->h[1], p->wc[0], p->wc[1], p->omega * p->omega, ax.g,
-                                        ax.ginv, skip, st));
+                                        ax.ginv, skip, st, p->mden));
   if (p->tabB && prec == kPrecF64)
     HELM_CK(launch_tri2d_tab(3, p->fhat, fc, p->tabB, p->rec, p->dbuf, nullptr, a, skip, st, p->prof.on ? &p->prof : nullptr));
   else if (p->tabB)
@@ -509,10 +514,10 @@ int refine_check(helm_plan* p, const void* f, const void* u, unsigned long long 
   int64_t nblocks = 0;
   if (refine_ff(p))
     HELM_PK("residual_ff", launch_residual_ff(p->dim, p->n, p->h, p->omega, p->wc, p->ffb, p->ufb, p->rbuf, p->sums,
-                                              &nblocks, skip, p->stream));
+                                              &nblocks, skip, p->stream, p->mden));
   else
     HELM_PK("residual_fp64", launch_residual(p->dim, p->n, p->h, p->omega, p->wc, (const double2*)f, (const double2*)u,
-                                             p->rbuf, p->sums, &nblocks, skip, p->stream, p->dev_err));
+                                             p->rbuf, p->sums, &nblocks, skip, p->stream, p->dev_err, p->mden));
   HELM_PK("residual_finalize", launch_residual_finalize(p->sums, nblocks, p->state, cond, p->stream));
   return HELM_OK;
 }
@@ -816,6 +821,8 @@ helm_plan* make_workspace(helm_plan* p) {
   w->resid_kind = p->resid_kind;
   w->use_graphs = p->use_graphs;
   w->tri_regs = p->tri_regs;
+  w->element = p->element;
+  w->mden = p->mden;
   w->version = p->version;
   const int64_t N = p->n[0] * p->n[1] * p->n[2];
   const size_t cb = cbytes(p->prec);
@@ -1038,12 +1045,12 @@ int tune_auxiliary(helm_plan* p) {
     if ((rc = apply_aux(p, c.rho, c.q))) break;
     if ((rc = solve_core(p, tf, kInC128, tu, kOutC128, 0.0, nullptr, nullptr, nullptr, nullptr))) break;
     int64_t nb = 0;
-    cudaError_t e = launch_residual(p->dim, p->n, p->h, p->omega, p->wc, tf, tu, tr, ts, &nb, nullptr, nullptr, p->dev_err);
+    cudaError_t e = launch_residual(p->dim, p->n, p->h, p->omega, p->wc, tf, tu, tr, ts, &nb, nullptr, nullptr, p->dev_err, p->mden);
     if (e == cudaSuccess && p->dtype == HELM_C64_REFINED) {
       // refined plans: one correction sweep as well, so that the residual
       // measures the contraction of the sweeps, not only the first solve
       if ((rc = solve_core(p, tr, kInC64, tu, kOutAccumC128, 1.0, nullptr, nullptr, nullptr, nullptr))) break;
-      e = launch_residual(p->dim, p->n, p->h, p->omega, p->wc, tf, tu, tr, ts, &nb, nullptr, nullptr, p->dev_err);
+      e = launch_residual(p->dim, p->n, p->h, p->omega, p->wc, tf, tu, tr, ts, &nb, nullptr, nullptr, p->dev_err, p->mden);
     }
     if (e == cudaSuccess) e = cudaMemcpy(hs.data(), ts, nb * 2 * sizeof(double), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) {
@@ -1181,6 +1188,11 @@ int validate_bc(int dim, const int32_t* bc) {
   return nabc ? HELM_OK : HELM_EINVAL;
 }
 
+void set_element(helm_plan* p, int element) {
+  p->element = element;
+  p->mden = element == HELM_ELEMENT_Q1_MODIFIED ? 12.0 : 6.0;
+}
+
 void set_bc(helm_plan* p, const int32_t* bc) {
   for (int k = 0; k < p->dim; ++k) {
     p->bc[k] = bc ? bc[k] : HELM_BC_ABC;
@@ -1189,12 +1201,13 @@ void set_bc(helm_plan* p, const int32_t* bc) {
 }
 
 int plan_2d(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy, double omega, int dtype,
-            const int32_t* bc) {
+            const int32_t* bc, int element) {
   if (!out) return HELM_EINVAL;
   *out = nullptr;
   if (nx < 3 || ny < 3 || !(hx > 0) || !(hy > 0) || !std::isfinite(hx) || !std::isfinite(hy)) return HELM_EINVAL;
   if (int rc = validate_common(omega, dtype)) return rc;
   if (int rc = validate_bc(2, bc)) return rc;
+  if (element != HELM_ELEMENT_Q1 && element != HELM_ELEMENT_Q1_MODIFIED) return HELM_EINVAL;
   auto t0 = std::chrono::steady_clock::now();
   helm_plan* p = new (std::nothrow) helm_plan();
   if (!p) return HELM_ENOMEM;
@@ -1208,6 +1221,7 @@ int plan_2d(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy, doub
   p->dtype = dtype;
   p->prec = dtype == HELM_C128 ? kPrecF64 : kPrecF32;
   set_bc(p, bc);
+  set_element(p, element);
   DftPlan dp;
   dft_factor(ny, &dp);
   int dev = 0, smem = 0;
@@ -1236,8 +1250,9 @@ int plan_2d(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy, doub
 }
 
 int plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx, double hy, double hz, double omega,
-            int dtype, const int32_t* bc) {
+            int dtype, const int32_t* bc, int element) {
   if (!out) return HELM_EINVAL;
+  if (element != HELM_ELEMENT_Q1 && element != HELM_ELEMENT_Q1_MODIFIED) return HELM_EINVAL;
   *out = nullptr;
   if (nx < 3 || ny < 3 || nz < 3 || !(hx > 0) || !(hy > 0) || !(hz > 0) || !std::isfinite(hx) ||
       !std::isfinite(hy) || !std::isfinite(hz))
@@ -1258,6 +1273,7 @@ int plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx, dou
   p->dtype = dtype;
   p->prec = dtype == HELM_C128 ? kPrecF64 : kPrecF32;
   set_bc(p, bc);
+  set_element(p, element);
   int smem = 0, dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -1278,7 +1294,7 @@ int plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx, dou
     if (!dft_supported(a, cbytes(p->prec), smem) || !dft_supported(b, cbytes(p->prec), smem)) rc = HELM_EUNSUPPORTED;
   }
   if (!rc) {
-    cudaError_t ce = plan3d_init(p->p3, p->prec, p->n, p->h, omega, p->wc, p->axo, p->axi, &p->bytes);
+    cudaError_t ce = plan3d_init(p->p3, p->prec, p->n, p->h, omega, p->wc, p->mden, p->axo, p->axi, &p->bytes);
     if (ce == cudaErrorMemoryAllocation) rc = HELM_ENOMEM;
     else if (ce != cudaSuccess) rc = cuda_fail(p, ce, "plan3d_init");
   }
@@ -1305,24 +1321,36 @@ int helm_debug_wait_timeout(helm_plan_t p, int64_t tries) {
 }
 
 int helm_plan_2d(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy, double omega, int dtype) {
-  return plan_2d(out, nx, ny, hx, hy, omega, dtype, nullptr);
+  return plan_2d(out, nx, ny, hx, hy, omega, dtype, nullptr, HELM_ELEMENT_Q1);
 }
 
 int helm_plan_2d_bc(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy, double omega, int dtype,
                     const int32_t* axis_bc) {
   if (!axis_bc) return HELM_EINVAL;
-  return plan_2d(out, nx, ny, hx, hy, omega, dtype, axis_bc);
+  return plan_2d(out, nx, ny, hx, hy, omega, dtype, axis_bc, HELM_ELEMENT_Q1);
+}
+
+int helm_plan_2d_ex(helm_plan_t* out, int64_t nx, int64_t ny, double hx, double hy, double omega, int dtype,
+                    const struct helm_plan_opts* opts) {
+  if (!opts) return plan_2d(out, nx, ny, hx, hy, omega, dtype, nullptr, HELM_ELEMENT_Q1);
+  return plan_2d(out, nx, ny, hx, hy, omega, dtype, opts->axis_bc, opts->element);
 }
 
 int helm_plan_3d(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx, double hy, double hz,
                  double omega, int dtype) {
-  return plan_3d(out, nx, ny, nz, hx, hy, hz, omega, dtype, nullptr);
+  return plan_3d(out, nx, ny, nz, hx, hy, hz, omega, dtype, nullptr, HELM_ELEMENT_Q1);
 }
 
 int helm_plan_3d_bc(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx, double hy, double hz,
                     double omega, int dtype, const int32_t* axis_bc) {
   if (!axis_bc) return HELM_EINVAL;
-  return plan_3d(out, nx, ny, nz, hx, hy, hz, omega, dtype, axis_bc);
+  return plan_3d(out, nx, ny, nz, hx, hy, hz, omega, dtype, axis_bc, HELM_ELEMENT_Q1);
+}
+
+int helm_plan_3d_ex(helm_plan_t* out, int64_t nx, int64_t ny, int64_t nz, double hx, double hy, double hz,
+                    double omega, int dtype, const struct helm_plan_opts* opts) {
+  if (!opts) return plan_3d(out, nx, ny, nz, hx, hy, hz, omega, dtype, nullptr, HELM_ELEMENT_Q1);
+  return plan_3d(out, nx, ny, nz, hx, hy, hz, omega, dtype, opts->axis_bc, opts->element);
 }
 
 int helm_set_auxiliary(helm_plan_t p, double rho, int phase_quarters) {
@@ -1613,6 +1641,7 @@ int helm_get_info(helm_plan_t p, helm_info* info) {
   info->device_bytes = p->bytes + (p->dim == 3 ? p->p3.route_bytes : 0);
   for (const helm_plan* w : p->ws) info->device_bytes += w->bytes;
   info->fp64_lines = p->dim == 3 ? plan3d_routed_lines(p->p3) : 0;
+  info->element = p->element;
   info->residual_kind = p->resid_kind;
   info->aux_q = p->axo.q;
   info->aux_rho = p->axo.rho;

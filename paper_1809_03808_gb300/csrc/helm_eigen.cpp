@@ -11,9 +11,12 @@
 //
 // where K^N is the Neumann stiffness (k11 = knn = 1, eq. matrixK).  The
 // Neumann pencil (K^N, M) is diagonalised by cosines phi_k(j) = c_k cos(k pi
-// (j-1)/(n-1)), k = 0..n-1, with eigenvalues 6/h^2 (1 - cos t_k)/(2 + cos t_k)
-// and M-normalisation weights w_k = phi_k(1)^2 = 2/(mu_k (n-1)) (halved for
-// k = 0 and k = n-1), mu_k = h (2 + cos t_k)/3.  The pencil is symmetric under
+// (j-1)/(n-1)), k = 0..n-1, with eigenvalues kappa_k/mu_k, kappa_k =
+// (2 - 2 cos t_k)/h, and M-normalisation weights w_k = phi_k(1)^2 =
+// 2/(mu_k (n-1)) (halved for k = 0 and k = n-1), mu_k = h ((den - 2) +
+// 2 cos t_k)/den for the mass h [(den-2)/den, 1/den] with half-weight ends
+// (den = 6: eq. matrixM, mu_k = h (2 + cos t_k)/3; den = 12: the modified
+// elements).  The pencil is symmetric under
 // j -> n+1-j, so eigenvectors are even (v_1 = v_n, only even k) or odd
 // (v_n = -v_1, only odd k), and each eigenvalue solves the secular equation
 //
@@ -161,8 +164,8 @@ int solve_class(const std::vector<double>& lk, const std::vector<double>& wk, do
 
 }  // namespace
 
-int abc_eigen(int64_t n, double h, double omega, double* lam, double* sigma, int8_t* parity) {
-  if (n < 2 || !(h > 0) || !(omega >= 0) || !std::isfinite(h) || !std::isfinite(omega))
+int abc_eigen(int64_t n, double h, double omega, double* lam, double* sigma, int8_t* parity, double mden) {
+  if (n < 2 || !(h > 0) || !(omega >= 0) || !std::isfinite(h) || !std::isfinite(omega) || !(mden > 2.0))
     return HELM_EINVAL;
   const double pi = 3.14159265358979323846;
   std::vector<double> lamN(n), w(n);
@@ -170,8 +173,11 @@ int abc_eigen(int64_t n, double h, double omega, double* lam, double* sigma, int
     double c = std::cos(pi * (double)k / (double)(n - 1));
     // 1 - cos t computed as 2 sin^2(t/2) to keep small eigenvalues accurate
     double s = std::sin(0.5 * pi * (double)k / (double)(n - 1));
-    lamN[k] = 6.0 / (h * h) * (2.0 * s * s) / (2.0 + c);
-    double mu = h * (2.0 + c) / 3.0;
+    // cosine eigenvalues of the Neumann pencil: kappa/mu with kappa =
+    // (2 - 2 cos t)/h and mu = h ((den - 2) + 2 cos t)/den (the paper's
+    // elements: den = 6, mu = h (2 + cos t)/3)
+    double mu = mden == 6.0 ? h * (2.0 + c) / 3.0 : h * ((mden - 2.0) + 2.0 * c) / mden;
+    lamN[k] = mden == 6.0 ? 6.0 / (h * h) * (2.0 * s * s) / (2.0 + c) : (4.0 * s * s / h) / mu;
     w[k] = 2.0 / (mu * (double)(n - 1));
     if (k == 0 || k == n - 1) w[k] *= 0.5;
   }

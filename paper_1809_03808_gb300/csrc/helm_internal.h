@@ -47,7 +47,9 @@ struct DftPlan {
 int dft_factor(int64_t n, DftPlan* p);
 
 // Eigen-data of the absorbing 1D pencil (see helm_eigen.cpp).
-int abc_eigen(int64_t n, double h, double omega, double* lam, double* sigma, int8_t* parity);
+// mden: the mass matrix denominator (6: the paper's elements, 12: the
+// modified ones; see MassCoef).
+int abc_eigen(int64_t n, double h, double omega, double* lam, double* sigma, int8_t* parity, double mden = 6.0);
 
 // abc_eigen in a caller workspace of >= 2n + 9 ceil(n/2) + 16 doubles,
 // single-threaded, no heap use.

@@ -167,6 +167,18 @@ __device__ __forceinline__ void ff_add_f(float& hi, float& lo, float v) {
   fast_two_sum(s, lo + e, hi, lo);
 }
 
+// Entries of the 1D mass matrix of one axis: h [(den-2)/den on the interior
+// diagonal, half of it at the ends, 1/den off the diagonal].  den = 6 is
+// eq. matrixM (the paper's elements, exact integrals); den = 12 the modified
+// elements with every integral by the 2-point rule at +-sqrt(2/3) (the mean
+// of the consistent and the lumped mass; fourth-order dispersion).
+struct MassCoef {
+  double in, end, off;
+};
+__host__ __device__ __forceinline__ MassCoef mass_coef(double h, double den) {
+  return MassCoef{(den - 2.0) * h / den, ((den - 2.0) / 2.0) * h / den, h / den};
+}
+
 // Line matrix T = K + s M along the tridiagonal axis (eqs. matrixK/matrixM;
 // K with absorbing corners 1 - i w h).  diag in the interior, diag at both
 // ends, constant off-diagonal.
@@ -178,11 +190,12 @@ struct LineCoef {
 };
 
 template <typename C>
-__device__ __forceinline__ LineCoef<C> line_coef(double sre, double sim, double h, double omega) {
+__device__ __forceinline__ LineCoef<C> line_coef(double sre, double sim, double h, double omega, double den) {
+  const MassCoef m = mass_coef(h, den);
   LineCoef<C> c;
-  c.a = mk<C>(sre * (4.0 * h / 6.0) + 2.0 / h, sim * (4.0 * h / 6.0));
-  c.ac = mk<C>(sre * (2.0 * h / 6.0) + 1.0 / h, sim * (2.0 * h / 6.0) - omega);
-  c.b = mk<C>(sre * (h / 6.0) - 1.0 / h, sim * (h / 6.0));
+  c.a = mk<C>(sre * m.in + 2.0 / h, sim * m.in);
+  c.ac = mk<C>(sre * m.end + 1.0 / h, sim * m.end - omega);
+  c.b = mk<C>(sre * m.off - 1.0 / h, sim * m.off);
   return c;
 }
 

@@ -906,14 +906,17 @@ __global__ void __launch_bounds__(1024) k_residual_finalize(const double* __rest
 cudaError_t launch_residual(int dim, const int64_t* n, const double* h, double omega, const double* wc,
                             const double2* f,
                             const double2* u, float2* r, double* sums, int64_t* nblocks, const int* skip,
-                            cudaStream_t st, int* err) {
+                            cudaStream_t st, int* err, double mden) {
   const int bs = 256;
   if (dim == 2 || dim == 3) {
     // monomial coefficients by end class (see the FP64-instruction-lean kernels)
     ResidQArgs q{};
     for (int k = 0; k < dim; ++k) q.n[k] = n[k];
     using cd = std::complex<double>;
-    auto Mk = [&](int k, int end, int bit) -> cd { return bit ? h[k] / 6.0 : (end ? 2.0 : 4.0) * h[k] / 6.0; };
+    auto Mk = [&](int k, int end, int bit) -> cd {
+      const MassCoef m = mass_coef(h[k], mden);
+      return bit ? m.off : (end ? m.end : m.in);
+    };
     auto Kk = [&](int k, int end, int bit) -> cd {
       return bit ? cd(-1.0 / h[k], 0.0) : (end ? cd(1.0 / h[k], -wc[k]) : cd(2.0 / h[k], 0.0));
     };
@@ -974,7 +977,7 @@ static FF2 split_host(double x) {
 cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, double omega, const double* wc,
                                const float4* f,
                                const float4* u, float2* r, double* sums, int64_t* nblocks, const int* skip,
-                               cudaStream_t st) {
+                               cudaStream_t st, double mden) {
   ResidFFArgs a{};
   a.omega = omega;
   const double w2 = omega * omega;
@@ -982,23 +985,25 @@ cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, doubl
     a.n[k] = n[k];
     a.h[k] = h[k];
     const double hk = h[k];
+    const MassCoef mk_ = mass_coef(hk, mden);
     AxisFF& x = a.ax[k];
-    x.mdi = split_host(4.0 * hk / 6.0);
-    x.mde = split_host(2.0 * hk / 6.0);
-    x.mo = split_host(hk / 6.0);
+    x.mdi = split_host(mk_.in);
+    x.mde = split_host(mk_.end);
+    x.mo = split_host(mk_.off);
     x.kdi = split_host(2.0 / hk);
     x.kder = split_host(1.0 / hk);
     x.ko = split_host(-1.0 / hk);
     x.kdei = split_host(-wc[k]);
-    x.cdi = split_host(2.0 / hk - w2 * (4.0 * hk / 6.0));
-    x.cde = split_host(1.0 / hk - w2 * (2.0 * hk / 6.0));
-    x.co = split_host(-1.0 / hk - w2 * (hk / 6.0));
+    x.cdi = split_host(2.0 / hk - w2 * mk_.in);
+    x.cde = split_host(1.0 / hk - w2 * mk_.end);
+    x.co = split_host(-1.0 / hk - w2 * mk_.off);
   }
   if (dim == 2) {
     double m[2][3], kk[2][3];
     for (int k = 0; k < 2; ++k) {
-      m[k][0] = m[k][2] = h[k] / 6.0;
-      m[k][1] = 4.0 * h[k] / 6.0;
+      const MassCoef mk_ = mass_coef(h[k], mden);
+      m[k][0] = m[k][2] = mk_.off;
+      m[k][1] = mk_.in;
       kk[k][0] = kk[k][2] = -1.0 / h[k];
       kk[k][1] = 2.0 / h[k];
     }
@@ -1010,12 +1015,13 @@ cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, doubl
     // and the last index of each axis
     auto ent = [&](int k, int64_t i, int d, double& m, double& kr, double& ki) {
       const bool end = (i == 0 || i == n[k] - 1);
+      const MassCoef mk_ = mass_coef(h[k], mden);
       if (d == 0) {
-        m = (end ? 2.0 : 4.0) * h[k] / 6.0;
+        m = end ? mk_.end : mk_.in;
         kr = (end ? 1.0 : 2.0) / h[k];
         ki = end ? -wc[k] : 0.0;
       } else {
-        m = h[k] / 6.0;
+        m = mk_.off;
         kr = -1.0 / h[k];
         ki = 0.0;
       }

@@ -30,6 +30,7 @@ struct Solve2DArgs {
   double wx = 0;    // w of the absorbing corners along x (0: Neumann x faces)
   double wy = 0;    // w of the absorbing x1 faces (0: Neumann), in C_bb
   int tri_regs = 0;  // complex64 passes: 1 = register-tile kernels even where the bulk-copy ones apply
+  double mden = 6.0;  // mass matrix denominator: 6 the paper's elements, 12 the modified ones (MassCoef)
 };
 
 constexpr int kChunkF32 = 16;
@@ -70,7 +71,7 @@ cudaError_t launch_reduce_faces(int prec, const void* partial, void* out, int64_
 // wx, wy: w of the absorbing x ends and x1 faces (0 on a Neumann axis).
 cudaError_t launch_apply_cbb(int prec, const void* in, const void* in2, void* out, int64_t nx, double hx,
                              double h1, double wx, double wy, double p, const double* g, const double* ginv,
-                             const int* skip, cudaStream_t st);
+                             const int* skip, cudaStream_t st, double mden);
 
 // Refinement state kept on the device (one per plan).
 struct RefineState {
@@ -87,18 +88,19 @@ struct RefineState {
 // of |r|^2 and |f|^2 into `sums` (2 doubles per block).  Returns the number of
 // blocks used through *nblocks.
 // wc[k]: w of the absorbing ends of axis k (0 on a Neumann axis).  err: the
-// device error word set if a bounded wait of the 3D kernel runs out.
+// device error word set if a bounded wait of the 3D kernel runs out.  mden:
+// the mass matrix denominator of the elements (MassCoef).
 cudaError_t launch_residual(int dim, const int64_t* n, const double* h, double omega, const double* wc,
                             const double2* f,
                             const double2* u, float2* r, double* sums, int64_t* nblocks, const int* skip,
-                            cudaStream_t st, int* err);
+                            cudaStream_t st, int* err, double mden);
 // The same residual with f and u as float-float complex vectors (float4 per
 // point: re_hi, im_hi, re_lo, im_lo), about 48 significant bits, computed on
 // the FP32 pipes.  Same grid and sums layout as launch_residual.
 cudaError_t launch_residual_ff(int dim, const int64_t* n, const double* h, double omega, const double* wc,
                                const float4* f,
                                const float4* u, float2* r, double* sums, int64_t* nblocks, const int* skip,
-                               cudaStream_t st);
+                               cudaStream_t st, double mden);
 // complex128 -> float-float (hi = round(x), lo = round(x - hi)) and back.
 // f (complex128) -> float-float out; hi (may be null) also receives the hi
 // parts as complex64.

@@ -143,7 +143,7 @@ __device__ __forceinline__ LineValues<T, typename cpx<T>::type> line_values(int 
     return v;
   }
   const LineParams lp = line_params(step, a, lc);
-  v.co = line_coef<C>(lp.sre, lp.sim, a.hx, a.wx);
+  v.co = line_coef<C>(lp.sre, lp.sim, a.hx, a.wx, a.mden);
   v.scal = (step == 2) ? mk<C>(1, 0) : mk<C>(a.invmu[2 * lc], a.invmu[2 * lc + 1]);
   v.wl = step3_weight<C>(a, lc);
   v.twl = mk<C>(a.tw[2 * lc], a.tw[2 * lc + 1]);
@@ -497,7 +497,7 @@ __global__ void k_line_tables(LineTables t, Solve2DArgs a, int step) {
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n1) return;
   const LineParams lp = line_params(step, a, l);
-  const LineCoef<double2> co = line_coef<double2>(lp.sre, lp.sim, a.hx, a.wx);
+  const LineCoef<double2> co = line_coef<double2>(lp.sre, lp.sim, a.hx, a.wx, a.mden);
   const double2 zero = make_double2(0, 0);
   const double2 mb = make_double2(-co.b.x, -co.b.y);
   // limit of the pivots and the settling row of this line
@@ -589,7 +589,7 @@ __global__ void __launch_bounds__(128) k_tri_pass2_tab(const double2* __restrict
   const int64_t s = k * CH, e = min(s + (int64_t)CH, nx) - 1;
   const int cnt = (int)(e - s + 1);
   const LineParams lp = line_params(STEP, a, lc);
-  const LineCoef<C> co = line_coef<C>(lp.sre, lp.sim, a.hx, a.wx);
+  const LineCoef<C> co = line_coef<C>(lp.sre, lp.sim, a.hx, a.wx, a.mden);
   const C scal = (STEP == 2) ? mk<C>(1, 0) : mk<C>(a.invmu[2 * lc], a.invmu[2 * lc + 1]);
   const C twl = mk<C>(a.tw[2 * lc], a.tw[2 * lc + 1]);
   const C wl = step3_weight<C>(a, lc);
@@ -683,7 +683,7 @@ __global__ void k_line_tables32(LineTables32 t, Solve2DArgs a, int step) {
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n1) return;
   const LineParams lp = line_params(step, a, l);
-  const LineCoef<double2> co = line_coef<double2>(lp.sre, lp.sim, a.hx, a.wx);
+  const LineCoef<double2> co = line_coef<double2>(lp.sre, lp.sim, a.hx, a.wx, a.mden);
   const double2 zero = make_double2(0, 0);
   const double2 mb = make_double2(-co.b.x, -co.b.y);
   // limit of the pivots and the settling row of this line
@@ -1099,7 +1099,7 @@ __global__ void k_pivots(typename cpx<T>::type* __restrict__ ustart, Solve2DArgs
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n1) return;
   const LineParams lp = line_params(step, a, l);
-  const LineCoef<double2> co = line_coef<double2>(lp.sre, lp.sim, a.hx, a.wx);
+  const LineCoef<double2> co = line_coef<double2>(lp.sre, lp.sim, a.hx, a.wx, a.mden);
   double2 u = co.ac;
   const double2 b2 = cmul(co.b, co.b);
   if ((a.ch - 1) == 0 && a.nchunks > 1) ustart[1 * n1 + l] = cvt<C>(u);
@@ -1414,21 +1414,22 @@ cudaError_t launch_reduce_faces(int prec, const void* partial, void* out, int64_
 
 cudaError_t launch_apply_cbb(int prec, const void* in, const void* in2, void* out, int64_t nx, double hx,
                              double h1, double wx, double wy, double p, const double* g, const double* ginv,
-                             const int* skip, cudaStream_t st) {
+                             const int* skip, cudaStream_t st, double mden) {
   // the entries of eqs. BminA, Cbb once, in double, on the host
+  const MassCoef mx = mass_coef(hx, mden), m1 = mass_coef(h1, mden);
   CbbConsts k;
-  k.md_end = 2.0 * hx / 6.0;
-  k.md_in = 4.0 * hx / 6.0;
-  k.mo = hx / 6.0;
+  k.md_end = mx.end;
+  k.md_in = mx.in;
+  k.mo = mx.off;
   k.kd_end_re = 1.0 / hx;
   k.kd_end_im = -wx;
   k.kd_in = 2.0 / hx;
   k.ko = -1.0 / hx;
-  k.d11_re = 1.0 / h1 - p * h1 / 3.0;
+  k.d11_re = 1.0 / h1 - p * m1.end;
   k.d11_im = wy;
-  k.d1n_re = -1.0 / h1 - p * h1 / 6.0;
-  k.e11 = h1 / 3.0;
-  k.e1n = h1 / 6.0;
+  k.d1n_re = -1.0 / h1 - p * m1.off;
+  k.e11 = m1.end;
+  k.e1n = m1.off;
   k.gr = g[0];
   k.gi = g[1];
   k.gir = ginv[0];

@@ -37,6 +37,7 @@ struct Plane3DArgs {
   const double *lamBi, *invmui, *lamAi, *sigAi, *parAi, *twi;
   double en_o[2], eninv_o[2], g_o[2], ginv_o[2];
   double en_i[2], eninv_i[2], g_i[2], ginv_i[2];
+  double mden;  // mass matrix denominator (MassCoef): 6 the paper's elements, 12 the modified ones
 };
 
 constexpr int XC = 32;  // rows per reduction chunk
@@ -80,7 +81,7 @@ struct ThomasRow {
 // M, K along x; p = w^2 - Lam_{1,l} (complex for outer A modes).
 template <typename C>
 __device__ void plane_cbb(const C* v, const C* w2, C* out, int nx, double hx, double hz, double wx, double wz,
-                          double pre, double pim, C g, C ginv) {
+                          double pre, double pim, C g, C ginv, double mden) {
   for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
     auto get = [&](int face, int j) -> C {
       C t = v[face * nx + j];
@@ -88,7 +89,8 @@ __device__ void plane_cbb(const C* v, const C* w2, C* out, int nx, double hx, do
       return t;
     };
     const bool end = (ix == 0 || ix == nx - 1);
-    const double md = end ? 2.0 * hx / 6.0 : 4.0 * hx / 6.0, mo = hx / 6.0;
+    const MassCoef mc = mass_coef(hx, mden), mcz = mass_coef(hz, mden);
+    const double md = end ? mc.end : mc.in, mo = mc.off;
     const double kdr = end ? 1.0 / hx : 2.0 / hx, kdi = end ? -wx : 0.0, ko = -1.0 / hx;
     C Mv[2], Kv[2];
     for (int f = 0; f < 2; ++f) {
@@ -99,9 +101,9 @@ __device__ void plane_cbb(const C* v, const C* w2, C* out, int nx, double hx, do
       Mv[f] = cadd(cscale(v0, (decltype(v0.x))md), cscale(nb, (decltype(v0.x))mo));
       Kv[f] = cadd(cmul(v0, mk<C>(kdr, kdi)), cscale(nb, (decltype(v0.x))ko));
     }
-    const C D11 = mk<C>(1.0 / hz - pre * hz / 3.0, wz - pim * hz / 3.0);
-    const C D1n = mk<C>(-1.0 / hz - pre * hz / 6.0, -pim * hz / 6.0);
-    const auto E11 = (decltype(D11.x))(hz / 3.0), E1n = (decltype(D11.x))(hz / 6.0);
+    const C D11 = mk<C>(1.0 / hz - pre * mcz.end, wz - pim * mcz.end);
+    const C D1n = mk<C>(-1.0 / hz - pre * mcz.off, -pim * mcz.off);
+    const auto E11 = (decltype(D11.x))mcz.end, E1n = (decltype(D11.x))mcz.off;
     out[ix] = cadd(cadd(cmul(D11, Mv[0]), cscale(Kv[0], E11)), cmul(ginv, cadd(cmul(D1n, Mv[1]), cscale(Kv[1], E1n))));
     out[nx + ix] = cadd(cmul(g, cadd(cmul(D1n, Mv[0]), cscale(Kv[0], E1n))), cadd(cmul(D11, Mv[1]), cscale(Kv[1], E11)));
   }
@@ -171,9 +173,9 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
     return cmul(v, gscale);
   };
   ThomasRow<C> thB, thA;
-  thB.k = line_coef<C>(lo_re + lBi_re - w2, lo_im + lBi_im, a.hx, a.wx);
+  thB.k = line_coef<C>(lo_re + lBi_re - w2, lo_im + lBi_im, a.hx, a.wx, a.mden);
   thB.n = nx;
-  thA.k = line_coef<C>(lo_re + a.lamAi[2 * mc] - w2, lo_im + a.lamAi[2 * mc + 1], a.hx, a.wx);
+  thA.k = line_coef<C>(lo_re + a.lamAi[2 * mc] - w2, lo_im + a.lamAi[2 * mc + 1], a.hx, a.wx, a.mden);
   thA.n = nx;
   const double pre = w2 - lo_re, pim = -lo_im;
 
@@ -265,7 +267,7 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
         sn = ac ? cmul(x, twm) : mk<C>(0, 0);
       },
       vin, mk<C>(1.0 / (double)nz, 0), mk<C>(a.en_i[0] / (double)nz, a.en_i[1] / (double)nz));
-  plane_cbb(vin, (const C*)nullptr, cin, nx, a.hx, a.hz, a.wx, a.wz, pre, pim, gi, giv);
+  plane_cbb(vin, (const C*)nullptr, cin, nx, a.hx, a.hz, a.wx, a.wz, pre, pim, gi, giv, a.mden);
   __syncthreads();
   // inner Step 2: A solve on the generated rhs, reduce to w_in
   forward(thA, tabA, [&](int ix) { return cadd(cin[ix], cscale(cin[nx + ix], pari)); });
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(1024) k_plane3d(const typename cpx<T>::type* _
         sn = cscale(t, pari);
       },
       win, mk<C>(1, 0), mk<C>(1, 0));
-  plane_cbb(vin, win, cin, nx, a.hx, a.hz, a.wx, a.wz, pre, pim, gi, giv);
+  plane_cbb(vin, win, cin, nx, a.hx, a.hz, a.wx, a.wz, pre, pim, gi, giv, a.mden);
   __syncthreads();
   // inner Step 3: corrected B-aux solve, y3 written over the scratch
   forward(thB, tabB, [&](int ix) {
@@ -390,12 +392,13 @@ __global__ void k_outer_cbb(const typename cpx<T>::type* __restrict__ v, const t
   const int64_t ix = i / nz, iz = i - ix * nz;
   auto ent = [&](int64_t n, double h, double w, int64_t j, int d, double& m, double& kr, double& ki) {
     const bool end = (j == 0 || j == n - 1);
+    const MassCoef mc = mass_coef(h, a.mden);
     if (d == 0) {
-      m = (end ? 2.0 : 4.0) * h / 6.0;
+      m = end ? mc.end : mc.in;
       kr = (end ? 1.0 : 2.0) / h;
       ki = end ? -w : 0.0;
     } else {
-      m = h / 6.0;
+      m = mc.off;
       kr = -1.0 / h;
       ki = 0.0;
     }
@@ -423,7 +426,8 @@ __global__ void k_outer_cbb(const typename cpx<T>::type* __restrict__ v, const t
     }
   }
   using T2 = decltype(Sv[0].x);
-  const T2 e11 = (T2)(a.hy / 3.0), e1n = (T2)(a.hy / 6.0);
+  const MassCoef mcy = mass_coef(a.hy, a.mden);
+  const T2 e11 = (T2)mcy.end, e1n = (T2)mcy.off;
   const C d11 = mk<C>(1.0 / a.hy, a.wy);
   const T2 d1n = (T2)(-1.0 / a.hy);
   const C g = mk<C>(a.g_o[0], a.g_o[1]), gv = mk<C>(a.ginv_o[0], a.ginv_o[1]);
@@ -458,7 +462,7 @@ __global__ void k_plane_tables(typename cpx<T>::type* __restrict__ tab, typename
   const double* lo = outerA ? a.lamAo : a.lamBo;
   const double* li = innerA ? a.lamAi : a.lamBi;
   const double w2 = a.omega * a.omega;
-  const LineCoef<double2> k = line_coef<double2>(lo[2 * l] + li[2 * m] - w2, lo[2 * l + 1] + li[2 * m + 1], a.hx, a.wx);
+  const LineCoef<double2> k = line_coef<double2>(lo[2 * l] + li[2 * m] - w2, lo[2 * l + 1] + li[2 * m + 1], a.hx, a.wx, a.mden);
   // attracting fixed point of the interior recurrence
   const double2 disc = csqrt_d(csub(cmul(k.a, k.a), cscale(cmul(k.b, k.b), 4.0)));
   const double2 r1 = cscale(cadd(k.a, disc), 0.5), r2 = cscale(csub(k.a, disc), 0.5);
@@ -511,6 +515,7 @@ Plane3DArgs make_args(const Plan3D& p) {
   a.wx = p.wc[0];
   a.wy = p.wc[1];
   a.wz = p.wc[2];
+  a.mden = p.mden;
   a.lamBo = p.axo->lamB;
   a.invmuo = p.axo->invmu;
   a.lamAo = p.axo->lamA;
@@ -972,7 +977,8 @@ __global__ void __launch_bounds__(128) k_inner3d_r(InnerArgs ia, const typename 
   const double* lo = OSTEP == 2 ? a.lamAo : a.lamBo;
   const double* li = ISTEP == 2 ? a.lamAi : a.lamBi;
   const double sre = lo[2 * l] + li[2 * m] - w2, sim = lo[2 * l + 1] + li[2 * m + 1];
-  const double2 b = make_double2(sre * (a.hx / 6.0) - 1.0 / a.hx, sim * (a.hx / 6.0));
+  const double mo = mass_coef(a.hx, a.mden).off;
+  const double2 b = make_double2(sre * mo - 1.0 / a.hx, sim * mo);
   const double2 nb = make_double2(-b.x, -b.y);
   // rhs factors of the line, as in k_inner3d, in FP64
   const double2 gscale = OSTEP == 2 ? make_double2(1, 0) : make_double2(a.invmuo[2 * l], a.invmuo[2 * l + 1]);
@@ -1068,7 +1074,7 @@ __global__ void k_route_tables(double2* __restrict__ rtab, int* __restrict__ len
   const double* lo = outerA ? a.lamAo : a.lamBo;
   const double* li = innerA ? a.lamAi : a.lamBi;
   const double w2 = a.omega * a.omega;
-  const LineCoef<double2> k = line_coef<double2>(lo[2 * l] + li[2 * m] - w2, lo[2 * l + 1] + li[2 * m + 1], a.hx, a.wx);
+  const LineCoef<double2> k = line_coef<double2>(lo[2 * l] + li[2 * m] - w2, lo[2 * l + 1] + li[2 * m + 1], a.hx, a.wx, a.mden);
   double2 c = make_double2(0, 0);
   for (int64_t ix = 0; ix < nx; ++ix) {
     const double2 aj = (ix == 0 || ix == nx - 1) ? k.ac : k.a;
@@ -1124,7 +1130,7 @@ __global__ void __launch_bounds__(256) k_inner_reduce(InnerArgs ia, const typena
   const double lo_im = OSTEP == 2 ? a.lamAo[2 * l + 1] : a.lamBo[2 * l + 1];
   const double pre = a.omega * a.omega - lo_re, pim = -lo_im;
   plane_cbb(sv, ISTEP == 2 ? (const C*)sw : (const C*)nullptr, cin + l * 2 * nx, nx, a.hx, a.hz, a.wx, a.wz, pre, pim,
-            mk<C>(a.g_i[0], a.g_i[1]), mk<C>(a.ginv_i[0], a.ginv_i[1]));
+            mk<C>(a.g_i[0], a.g_i[1]), mk<C>(a.ginv_i[0], a.ginv_i[1]), a.mden);
 }
 
 template <typename T>
@@ -1311,7 +1317,7 @@ cudaError_t solve3d_t(Plan3D& p, const void* in, int in_is_double, void* out, in
 
 }  // namespace
 
-cudaError_t plan3d_init(Plan3D& p, int prec, const int64_t* n, const double* h, double omega, const double* wc,
+cudaError_t plan3d_init(Plan3D& p, int prec, const int64_t* n, const double* h, double omega, const double* wc, double mden,
                         const AxisData& axo, const AxisData& axi, size_t* bytes) {
   p.prec = prec;
   for (int k = 0; k < 3; ++k) {
@@ -1320,6 +1326,7 @@ cudaError_t plan3d_init(Plan3D& p, int prec, const int64_t* n, const double* h, 
     p.wc[k] = wc[k];
   }
   p.omega = omega;
+  p.mden = mden;
   p.axo = &axo;
   p.axi = &axi;
   const size_t cb = prec == kPrecF64 ? sizeof(double2) : sizeof(float2);
@@ -1430,7 +1437,7 @@ cudaError_t build_routing(Plan3D& p) {
   const int64_t nx = p.n[0], ny = p.n[1], nz = p.n[2];
   std::vector<double> lamx(2 * nx), sigx(2 * nx);
   std::vector<int8_t> parx(nx);
-  if (abc_eigen(nx, p.h[0], p.wc[0], lamx.data(), sigx.data(), parx.data()) != 0) return cudaSuccess;
+  if (abc_eigen(nx, p.h[0], p.wc[0], lamx.data(), sigx.data(), parx.data(), p.mden) != 0) return cudaSuccess;
   std::vector<std::pair<double, double>> ex(nx);
   for (int64_t k = 0; k < nx; ++k) ex[k] = {lamx[2 * k], lamx[2 * k + 1]};
   std::sort(ex.begin(), ex.end());

@@ -16,6 +16,7 @@ struct Plan3D {
   double h[3] = {0, 0, 0};
   double omega = 0;
   double wc[3] = {0, 0, 0};  // w of the absorbing ends of each axis (0: Neumann axis)
+  double mden = 6.0;         // mass matrix denominator of the elements (MassCoef)
   const AxisData* axo = nullptr;  // outer periodic axis (array axis 1)
   const AxisData* axi = nullptr;  // inner periodic axis (array axis 2)
   void* fhat = nullptr;
@@ -56,7 +57,7 @@ struct Plan3D {
   bool ready = false;
 };
 
-cudaError_t plan3d_init(Plan3D& p, int prec, const int64_t* n, const double* h, double omega, const double* wc,
+cudaError_t plan3d_init(Plan3D& p, int prec, const int64_t* n, const double* h, double omega, const double* wc, double mden,
                         const AxisData& axo, const AxisData& axi, size_t* bytes);
 // (Re)build the pivot tables from the current eigen-data (after a change of
 // the auxiliary), and the precision routing of complex64 plans.
