@@ -194,6 +194,55 @@ __device__ __forceinline__ typename cpx<T>::type load_pt(const void* p, int in_i
   return cvt<C>(__ldg(reinterpret_cast<const float2*>(p) + i));
 }
 
+// The 16 input points of thread t in the first pass (point e = q R0 + r at
+// base + in_index(t, q, r) * stride), scaled by sc_in: the input kind is
+// resolved once and every load of a batch is issued before any is used, so
+// the loads of a thread are in flight together (8 at a time for 16-byte
+// points, all 16 for 8-byte ones).
+template <typename T, int N, int R0>
+__device__ __forceinline__ void load16(typename cpx<T>::type (&v)[16], const void* in, int kind, int64_t base,
+                                       int64_t stride, bool act, int t, const typename cpx<T>::type* sc_in) {
+  using C = typename cpx<T>::type;
+  auto idx = [&](int e) -> int64_t { return (int64_t)in_index<N, R0>(t, e / R0, e % R0) * stride; };
+  if (!act) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = mk<C>(0, 0);
+    return;
+  }
+  if (kind == kInC128) {
+    const double2* p = reinterpret_cast<const double2*>(in) + base;
+#pragma unroll
+    for (int hb = 0; hb < 2; ++hb) {
+      double2 tmp[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) tmp[k] = __ldg(p + idx(8 * hb + k));
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[8 * hb + k] = cvt<C>(tmp[k]);
+    }
+  } else if (kind == kInFF) {
+    const float4* p = reinterpret_cast<const float4*>(in) + base;
+#pragma unroll
+    for (int hb = 0; hb < 2; ++hb) {
+      float4 tmp[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) tmp[k] = __ldg(p + idx(8 * hb + k));
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[8 * hb + k] = mk<C>(tmp[k].x, tmp[k].y);
+    }
+  } else {
+    const float2* p = reinterpret_cast<const float2*>(in) + base;
+    float2 tmp[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) tmp[e] = __ldg(p + idx(e));
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = cvt<C>(tmp[e]);
+  }
+  if (sc_in) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = cmul(v[e], __ldg(&sc_in[in_index<N, R0>(t, e / R0, e % R0)]));
+  }
+}
+
 template <typename C>
 __device__ __forceinline__ void store_pt(void* p, int mode, int64_t i, C v, double accum_scale) {
   if (mode == kOutC128) {
@@ -274,18 +323,7 @@ __global__ void __launch_bounds__(pow2_threads<LOG2N>())
   C* buf = reinterpret_cast<C*>(smem_raw) + line * NPAD;
   C v[16];
   // pass 0 (radix R0, no twiddles): global memory in
-#pragma unroll
-  for (int q = 0; q < 16 / R0; ++q)
-#pragma unroll
-    for (int r = 0; r < R0; ++r) {
-      const int i = in_index<N, R0>(t, q, r);
-      C x = mk<C>(0, 0);
-      if (act) {
-        x = load_pt<T>(in, in_is_double, g0 + i);
-        if (sc_in) x = cmul(x, __ldg(&sc_in[i]));
-      }
-      v[q * R0 + r] = x;
-    }
+  load16<T, N, R0>(v, in, in_is_double, g0, 1, act, t, sc_in);
   pass_compute<C, N, R0, 1, SIGN>(v, t, tw);
   if constexpr (NP == 1) {
     if (act) {
@@ -375,18 +413,7 @@ __global__ void __launch_bounds__(cols_tc<T, LOG2N>() * (1 << LOG2N) / 16)
   const bool act = col < inner;
   const int64_t g0 = slab * (int64_t)N * inner + col;  // point i at g0 + i * inner
   C v[16];
-#pragma unroll
-  for (int q = 0; q < 16 / R0; ++q)
-#pragma unroll
-    for (int r = 0; r < R0; ++r) {
-      const int i = in_index<N, R0>(t, q, r);
-      C x = mk<C>(0, 0);
-      if (act) {
-        x = load_pt<T>(in, in_is_double, g0 + (int64_t)i * inner);
-        if (sc_in) x = cmul(x, __ldg(&sc_in[i]));
-      }
-      v[q * R0 + r] = x;
-    }
+  load16<T, N, R0>(v, in, in_is_double, g0, inner, act, t, sc_in);
   pass_compute<C, N, R0, 1, SIGN>(v, t, tw);
   if constexpr (NP == 1) {
     if (act) {
