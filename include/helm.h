@@ -410,14 +410,17 @@ int helm_solve_2d_static(int64_t nx, int64_t ny, double hx, double hy, double om
  * solve one operator for many right-hand sides), and overlaps independent
  * requests on the GPU.
  *
- * A server owns one scheduler thread, `nslots` CUDA streams (1..16) and a
- * cache of plans keyed by (dim, n, h, omega, dtype, residual, tol, max_iter).
- * Requests enter a FIFO queue.  The scheduler starts the oldest request that
- * can start whenever a slot is free: its operator's plan is taken from the
- * cache, or built if the device memory in use (cached plans, counted by
- * their helm_info.device_bytes) plus an estimate of the new plan stays within
- * `device_budget_bytes` after idle cached plans are evicted least recently
- * used first.  The estimate is 64 MiB plus, per unknown, 100 B (2D complex64
+ * A server owns a scheduler thread, a builder thread, `nslots` CUDA streams
+ * (1..16) and a cache of plans keyed by (dim, n, h, omega, dtype, residual,
+ * tol, max_iter).  Requests enter a FIFO queue.  The scheduler starts the
+ * oldest request that can start whenever a slot is free: its operator's plan
+ * is taken from the cache, or handed to the builder thread if the device
+ * memory in use (cached plans, counted by their helm_info.device_bytes, and
+ * the estimates of plans being built) plus an estimate of the new plan stays
+ * within `device_budget_bytes` after idle cached plans are evicted least
+ * recently used first.  While a plan is built the scheduler goes on starting
+ * other requests; requests for that operator wait for it, and the request it
+ * was built for goes back to the front of the queue.  The estimate is 64 MiB plus, per unknown, 100 B (2D complex64
  * modes), 200 B (2D HELM_C128), 112 B (3D complex64) or 128 B (3D
  * HELM_C128).  A request whose plan is busy with another request waits while
  * later requests for other operators start (a plan serves one request at a

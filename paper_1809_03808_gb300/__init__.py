@@ -440,7 +440,8 @@ class Batch:
 
 class Server:
     """A request server (helm_server_*): plan cache under a device-memory
-    budget, `nslots` CUDA streams, one scheduler thread.
+    budget, `nslots` CUDA streams, a scheduler thread and a plan-builder
+    thread.
 
     submit() takes CUDA tensors f and u holding nrhs right-hand sides one
     after another (shape (nrhs, *shape) or the plan layout when nrhs = 1);

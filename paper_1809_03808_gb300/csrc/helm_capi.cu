@@ -1612,17 +1612,23 @@ int helm_solve_host(helm_plan_t p, const void* f_host, void* u_host) {
 int helm_get_info(helm_plan_t p, helm_info* info) {
   if (!p || !info) return HELM_EINVAL;
   std::memset(info, 0, sizeof(*info));
-  HELM_CK(cudaStreamSynchronize(p->stream));
+  // The state is read on the plan's own stream (the workspaces' streams join
+  // it at the end of helm_solve_many), not the legacy stream: with another
+  // thread building plans on the legacy stream, reading a finished plan's
+  // state does not wait for that work.
+  const cudaStream_t st = p->stream;
   RefineState s{};
-  HELM_CK(cudaMemcpy(&s, p->state, sizeof(s), cudaMemcpyDeviceToHost));
+  HELM_CK(cudaMemcpyAsync(&s, p->state, sizeof(s), cudaMemcpyDeviceToHost, st));
+  HELM_CK(cudaStreamSynchronize(st));
   int derr_ws = 0;
   for (int w = 1; w < p->last_many; ++w) {
     // after helm_solve_many: report the right-hand side whose refinement ended
     // worst (not converged, else the largest final residual)
     RefineState t{};
     int e = 0;
-    HELM_CK(cudaMemcpy(&t, p->ws[w - 1]->state, sizeof(t), cudaMemcpyDeviceToHost));
-    HELM_CK(cudaMemcpy(&e, p->ws[w - 1]->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    HELM_CK(cudaMemcpyAsync(&t, p->ws[w - 1]->state, sizeof(t), cudaMemcpyDeviceToHost, st));
+    HELM_CK(cudaMemcpyAsync(&e, p->ws[w - 1]->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HELM_CK(cudaStreamSynchronize(st));
     derr_ws |= e;
     const double rt = t.iters > 0 ? t.resid[std::min(t.iters, 16) - 1] : 0.0;
     const double rs = s.iters > 0 ? s.resid[std::min(s.iters, 16) - 1] : 0.0;
@@ -1650,7 +1656,8 @@ int helm_get_info(helm_plan_t p, helm_info* info) {
   int derr = derr_ws;
   if (p->dev_err) {
     int e0 = 0;
-    HELM_CK(cudaMemcpy(&e0, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    HELM_CK(cudaMemcpyAsync(&e0, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HELM_CK(cudaStreamSynchronize(st));
     derr |= e0;
   }
   if (derr) {

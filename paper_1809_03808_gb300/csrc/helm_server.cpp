@@ -1,11 +1,15 @@
 // Request server over the public plan API (helm.h): a FIFO of independent
-// solve requests, a device-memory-budgeted plan cache, and one scheduler
-// thread that starts requests on a pool of CUDA streams as slots and plans
-// free up, so independent requests overlap on the GPU.  The paper's method
-// has no counterpart: this is the serving layer around its solver.
+// solve requests, a device-memory-budgeted plan cache, one scheduler thread
+// that starts requests on a pool of CUDA streams as slots and plans free up,
+// so independent requests overlap on the GPU, and one builder thread that
+// makes new plans meanwhile (a plan build works on the legacy stream and the
+// slots' streams are non-blocking, so builds and solves overlap too).  The
+// paper's method has no counterpart: this is the serving layer around its
+// solver.
 //
-// Only the scheduler thread makes CUDA calls after creation; submitters and
-// waiters touch the queue and the results under the server mutex.
+// Only the scheduler and the builder make CUDA calls after creation;
+// submitters and waiters touch the queue and the results under the server
+// mutex.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -88,6 +92,8 @@ struct Request {
   bool started = false, done = false;
   int status = HELM_OK;
   int plan_reused = 0;
+  size_t reserve = 0;  // device memory reserved while its plan is built
+  bool fresh = false;  // its plan was built for it (not a reuse)
   int iterations = 0, converged = 1;
   double residual = 0.0;
 };
@@ -140,8 +146,25 @@ struct helm_server {
   Clock::time_point t_first, t_last;
   std::vector<double> latencies;
   std::thread worker;
+  // plan builds: requests waiting for the builder, the operators being built
+  std::deque<Request*> build_queue;
+  std::vector<PlanKey> building;
+  int builds_in_flight = 0;
+  bool stop_build = false;
+  // bumped (under the mutex) by every event that may let a waiting request
+  // start: a submission, a finished build, stop
+  uint64_t wake = 0;
+  std::condition_variable cv_build;
+  std::thread builder;
 
   void run();
+  void build_loop();
+  bool being_built(const PlanKey& k) const {
+    for (const PlanKey& b : building)
+      if (b == k) return true;
+    return false;
+  }
+  bool builds_pending() const { return builds_in_flight > 0 || !build_queue.empty(); }
   bool start_one(std::unique_lock<std::mutex>& lk);
   void finish(Slot& sl, cudaError_t q);
   void fail(Request* r, int status);
@@ -237,9 +260,11 @@ bool helm_server::start_one(std::unique_lock<std::mutex>& lk) {
         else found_busy = true;
         if (pe) break;
       }
-    bool reuse = pe != nullptr;
+    bool reuse = pe != nullptr && !r->fresh;
     if (!pe) {
-      if (found_busy || memory_blocked) continue;  // its plan is busy; one instance per operator
+      // its plan is busy or being built (one instance per operator), or an
+      // older request waits for memory
+      if (found_busy || memory_blocked || being_built(key)) continue;
       const size_t est = plan_bytes_estimate(r->spec);
       if (est > budget) {
         pending.erase(pending.begin() + (std::ptrdiff_t)qi);
@@ -262,7 +287,7 @@ bool helm_server::start_one(std::unique_lock<std::mutex>& lk) {
         ++evicted;
       }
       if (in_use + est > budget) {
-        if (!running()) {  // nothing will free memory: it can never fit
+        if (!running() && !builds_pending()) {  // nothing will free memory: it can never fit
           pending.erase(pending.begin() + (std::ptrdiff_t)qi);
           fail(r, HELM_ENOMEM);
           return true;
@@ -270,43 +295,18 @@ bool helm_server::start_one(std::unique_lock<std::mutex>& lk) {
         memory_blocked = true;
         continue;
       }
-      // build the plan without the lock (submitters and waiters go on)
+      // the builder thread makes the plan; the scheduler goes on with other
+      // requests, and this one returns to the front of the queue when built
       pending.erase(pending.begin() + (std::ptrdiff_t)qi);
       in_use += est;  // reserved while building
-      lk.unlock();
-      helm_plan_t plan = nullptr;
-      const helm_request& sp = r->spec;
-      int rc = sp.dim == 2 ? helm_plan_2d(&plan, sp.n[0], sp.n[1], sp.h[0], sp.h[1], sp.omega, sp.dtype)
-                           : helm_plan_3d(&plan, sp.n[0], sp.n[1], sp.n[2], sp.h[0], sp.h[1], sp.h[2], sp.omega,
-                                          sp.dtype);
-      if (!rc) rc = configure(plan, sp);
-      helm_info info;
-      if (!rc) {
-        rc = helm_get_info(plan, &info);
-        if (rc == HELM_ENOTCONV) rc = HELM_OK;  // the state of the plan's trial solves: info is filled
-      }
-      if (rc && plan) {
-        helm_destroy(plan);
-        plan = nullptr;
-      }
-      lk.lock();
-      in_use -= est;
-      if (rc) {
-        fail(r, rc);
-        return true;
-      }
-      auto e = std::make_unique<PlanEntry>();
-      e->key = key;
-      e->plan = plan;
-      e->bytes = info.device_bytes;
-      in_use += e->bytes;
-      peak = std::max(peak, in_use);
-      pe = e.get();
-      cache.push_back(std::move(e));
-      ++built;
+      r->reserve = est;
+      building.push_back(key);
+      build_queue.push_back(r);
+      cv_build.notify_one();
+      return true;
     } else {
       pending.erase(pending.begin() + (std::ptrdiff_t)qi);
-      ++reused;
+      if (reuse) ++reused;
     }
     // launch its right-hand sides on the slot's stream
     pe->busy = true;
@@ -333,6 +333,7 @@ void helm_server::run() {
   cudaSetDevice(device);
   std::unique_lock<std::mutex> lk(mu);
   for (;;) {
+    const uint64_t seen = wake;
     bool progress = false;
     for (Slot& sl : slots)
       if (sl.req) {
@@ -343,10 +344,71 @@ void helm_server::run() {
       }
     while (start_one(lk)) progress = true;
     const bool busy = running();
-    if (stop && pending.empty() && !busy) break;
+    if (stop && pending.empty() && !busy && !builds_pending()) break;
     if (progress) continue;
+    // nothing started: sleep until a slot may have finished (polled) or
+    // something else changed; requests that wait for a plan being built
+    // must not keep the mutex from the builder
     if (busy) cv_work.wait_for(lk, std::chrono::microseconds(50));
-    else cv_work.wait(lk, [&] { return stop || !pending.empty(); });
+    else cv_work.wait(lk, [&] { return wake != seen; });
+  }
+}
+
+// The builder: plans for the requests the scheduler queued, one at a time,
+// with the lock released while building.  A built plan joins the cache idle
+// and its request goes back to the front of the queue.
+void helm_server::build_loop() {
+  cudaSetDevice(device);
+  std::unique_lock<std::mutex> lk(mu);
+  for (;;) {
+    cv_build.wait(lk, [&] { return stop_build || !build_queue.empty(); });
+    if (build_queue.empty()) break;  // stop_build
+    Request* r = build_queue.front();
+    build_queue.pop_front();
+    ++builds_in_flight;
+    const helm_request sp = r->spec;
+    const PlanKey key = key_of(sp);
+    lk.unlock();
+    helm_plan_t plan = nullptr;
+    int rc = sp.dim == 2 ? helm_plan_2d(&plan, sp.n[0], sp.n[1], sp.h[0], sp.h[1], sp.omega, sp.dtype)
+                         : helm_plan_3d(&plan, sp.n[0], sp.n[1], sp.n[2], sp.h[0], sp.h[1], sp.h[2], sp.omega,
+                                        sp.dtype);
+    if (!rc) rc = configure(plan, sp);
+    helm_info info;
+    if (!rc) {
+      rc = helm_get_info(plan, &info);
+      if (rc == HELM_ENOTCONV) rc = HELM_OK;  // the state of the plan's trial solves: info is filled
+    }
+    if (rc && plan) {
+      helm_destroy(plan);
+      plan = nullptr;
+    }
+    lk.lock();
+    --builds_in_flight;
+    in_use -= std::min(in_use, r->reserve);
+    r->reserve = 0;
+    for (size_t i = 0; i < building.size(); ++i)
+      if (building[i] == key) {
+        building.erase(building.begin() + (std::ptrdiff_t)i);
+        break;
+      }
+    if (rc) {
+      fail(r, rc);
+    } else {
+      auto e = std::make_unique<PlanEntry>();
+      e->key = key;
+      e->plan = plan;
+      e->bytes = info.device_bytes;
+      e->last_use = ++use_clock;
+      in_use += e->bytes;
+      peak = std::max(peak, in_use);
+      cache.push_back(std::move(e));
+      ++built;
+      r->fresh = true;
+      pending.push_front(r);
+    }
+    ++wake;
+    cv_work.notify_one();
   }
 }
 
@@ -399,6 +461,7 @@ int helm_server_create(helm_server_t* out, int32_t nslots, size_t device_budget_
   }
   helm_server* raw = s.release();
   raw->worker = std::thread([raw] { raw->run(); });
+  raw->builder = std::thread([raw] { raw->build_loop(); });
   *out = raw;
   return HELM_OK;
 }
@@ -421,6 +484,7 @@ int helm_server_submit(helm_server_t s, const helm_request* req, int64_t* ticket
       s->t_first = r->t_submit;
     }
     ++s->submitted;
+    ++s->wake;
     s->pending.push_back(r.get());
     s->requests.emplace(r->ticket, std::move(r));
   }
@@ -483,9 +547,16 @@ int helm_server_destroy(helm_server_t s) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
+    ++s->wake;
   }
   s->cv_work.notify_one();
-  if (s->worker.joinable()) s->worker.join();
+  if (s->worker.joinable()) s->worker.join();  // after every queued request, builds included
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop_build = true;
+  }
+  s->cv_build.notify_one();
+  if (s->builder.joinable()) s->builder.join();
   cudaSetDevice(s->device);
   for (auto& e : s->cache) helm_destroy(e->plan);
   for (Slot& sl : s->slots) {

@@ -155,6 +155,42 @@ def test_server_evicts_under_budget(env):
         srv.close()
 
 
+def test_server_builds_plans_off_the_scheduler(env):
+    """While the plan of a large 3D request is being built, a later request
+    whose plan is cached starts and finishes: its whole latency is shorter
+    than the large request's wait for its plan.  Both results equal their
+    solves alone."""
+    helm, torch = env
+    small = _problem((40, 24), (1.3, 0.7), 8)
+    big = _problem((192, 160, 128), (1.0, 0.9, 0.7), 10)
+    srv = helm.Server(nslots=2, device_budget_bytes=8 << 30)
+    try:
+        f0 = _inputs(torch, small[0], 1, 5)
+        u0 = torch.empty_like(f0)
+        torch.cuda.synchronize()
+        assert srv.wait(_submit(srv, *small, "c64_ff", f0, u0), 60.0).status == helm.HELM_OK  # caches its plan
+        fb = _inputs(torch, big[0], 1, 6)
+        fs = _inputs(torch, small[0], 1, 7)
+        ub, us = torch.empty_like(fb), torch.empty_like(fs)
+        torch.cuda.synchronize()
+        tb = _submit(srv, *big, "c64_fp64", fb, ub)
+        ts = _submit(srv, *small, "c64_ff", fs, us)
+        rs = srv.wait(ts, 60.0)
+        rb = srv.wait(tb, 120.0)
+        torch.cuda.synchronize()
+        assert rs.status == helm.HELM_OK and rb.status == helm.HELM_OK
+        assert rs.plan_reused == 1 and rb.plan_reused == 0
+        print(f"SERVER small request latency {rs.latency_s * 1e3:.2f} ms, large request's wait for its plan "
+              f"{rb.queue_s * 1e3:.2f} ms")
+        assert rs.latency_s < rb.queue_s
+        assert torch.equal(us, _alone(helm, torch, *small, "c64_ff", fs))
+        assert torch.equal(ub, _alone(helm, torch, *big, "c64_fp64", fb))
+        st = srv.stats()
+        assert st.plans_built == 2 and st.plans_reused == 1 and st.completed == 3
+    finally:
+        srv.close()
+
+
 def test_server_rejects_bad_requests(env):
     helm, torch = env
     import ctypes
