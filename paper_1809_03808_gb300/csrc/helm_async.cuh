@@ -55,6 +55,18 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* map, int c0, 
       : "memory");
 }
 
+// Asynchronous copy of N = 4, 8 or 16 bytes global -> shared (cp.async; both
+// addresses N-byte aligned).  No barrier counts it: the issuing thread waits
+// for all its copies with cp_async_wait_all(), after which a block barrier
+// makes them visible to the other threads.
+template <int N>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  static_assert(N == 4 || N == 8 || N == 16, "cp.async copies 4, 8 or 16 bytes");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src), "n"(N) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(

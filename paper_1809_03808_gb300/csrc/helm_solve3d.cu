@@ -19,6 +19,7 @@
 #include <vector>
 #include <type_traits>
 
+#include "helm_async.cuh"
 #include "helm_dft.h"
 #include "helm_kernels.cuh"
 #include "helm_solve3d.h"
@@ -641,6 +642,7 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
     const typename cpx<T>::type* __restrict__ lend, const int* __restrict__ lenL,
     typename cpx<T>::type* __restrict__ part, typename cpx<T>::type* __restrict__ y3, const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
+  constexpr bool kFhatRows = OSTEP != 2 && ISTEP != 2;  // the right-hand side reads f_hat
   if (skip && *skip) return;
   const Plane3DArgs& a = ia.a;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -699,6 +701,25 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
     const int64_t m0 = ((int64_t)blockIdx.x * ia.nmb + mb) * kMW;
     if (m0 >= nz) break;
     __syncthreads();  // the previous tile's face sums are done
+    // ---- asynchronous copies of the tile's f_hat rows (thread (mi, c): its
+    // own chunk rows; the 16 lanes of a half-warp read 16 consecutive inner
+    // modes of a row) and of the first pivot rows, all in flight while the
+    // line constants are formed; no registers hold them ----
+    {
+      const int64_t m = m0 + mi;
+      const int s0 = c * CH, e0 = min(s0 + CH, nx) - 1;
+      if (kFhatRows && cok && m < nz) {
+        const C* fp = fhat + ((int64_t)s0 * ny + l) * nz + m;
+#pragma unroll
+        for (int k = 0; k < CH; ++k)
+          if (s0 + k <= e0) cp_async<sizeof(C)>(tile + (s0 + k) * kMW + mi, fp + k * xs);
+      }
+      // rows below the settling row are read from here, the others never
+      for (int e = tid; e < kPivRows * kMW; e += nthr) {
+        const int j = e / kMW, mm = e - j * kMW;
+        if (j < nx && m0 + mm < nz) cp_async<sizeof(C)>(piv + e, tab + (int64_t)j * xs + l * nz + m0 + mm);
+      }
+    }
     if (tid < kMW) {
       const int64_t m = m0 + tid;
       const bool on = m < nz;
@@ -743,16 +764,11 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
       }
       sR[tid] = routed ? 1 : 0;
     }
-    __syncthreads();
-    // ---- the first pivot rows of the tile's lines ----
-    for (int e = tid; e < kPivRows * kMW; e += nthr) {
-      const int j = e / kMW, mm = e - j * kMW;
-      C v = mk<C>(0, 0);
-      if (j < sL[mm]) v = tab[(int64_t)j * xs + l * nz + m0 + mm];
-      piv[e] = v;
-    }
-    // ---- thread (mi, c) stages its own chunk rows: for each row the 16
-    // lanes of a half-warp read 16 consecutive inner modes ----
+    cp_async_wait_all();
+    __syncthreads();  // line constants formed, every thread's copies landed
+    // ---- thread (mi, c) forms the right-hand sides of its own chunk rows in
+    // place (from the copied f_hat rows, the outer faces, the inner C_bb
+    // faces) ----
     const int64_t m = m0 + mi;
     const bool act = m < nz && cok;
     const int s0 = c * CH, e0 = min(s0 + CH, nx) - 1;
@@ -764,7 +780,6 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
       const C gs = cmul(gscale, sc);
       const bool zero_rhs = !act || (ISTEP == 2 && sR[mi]);
       const int64_t mcl = act ? m : 0;
-      const C* fp = fhat + ((int64_t)s0 * ny + l) * nz + mcl;  // f_hat rows of this line
       const C* g1p = OSTEP != 1 ? gfaces + (int64_t)s0 * nz + mcl : nullptr;  // outer faces (Steps 2, 3)
       const C* gnp = OSTEP != 1 ? g1p + (int64_t)nx * nz : nullptr;
 #pragma unroll(CH <= 16 ? CH : 8)
@@ -775,9 +790,9 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
             if (ISTEP == 2) {
               v = cadd(cin1[s0 + k], cmul(cinn[s0 + k], wk2));
             } else {
-              if (OSTEP == 1) v = cmul(fp[k * xs], gs);
+              if (OSTEP == 1) v = cmul(trow[k * kMW], gs);
               else if (OSTEP == 2) v = cmul(cadd(g1p[k * nz], cscale(gnp[k * nz], paro)), sc);
-              else v = cmul(cadd(cadd(fp[k * xs], g1p[k * nz]), cmul(gnp[k * nz], wl)), gs);
+              else v = cmul(cadd(cadd(trow[k * kMW], g1p[k * nz]), cmul(gnp[k * nz], wl)), gs);
               if (ISTEP == 3) v = cadd(v, cmul(cadd(cin1[s0 + k], cmul(cinn[s0 + k], wk2)), sc));
             }
           }
@@ -795,7 +810,6 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
       if (j >= L) return j == nx - 1 ? ilast : iinf;
       return j < kPivRows ? piv[j * kMW + mi] : tcol[(int64_t)j * xs];
     };
-    __syncthreads();  // pivot rows staged
     // ---- pass 1 ----
     // Forward with d_{s-1} = 0 (d_loc written over the rhs), then the
     // backward substitution with x_{e+1} = 0 over it by Horner's rule gives
@@ -1099,6 +1113,7 @@ __global__ void __launch_bounds__(256) k_inner_reduce(InnerArgs ia, const typena
                                                       const typename cpx<T>::type* __restrict__ rpart,
                                                       const int* __restrict__ skip) {
   using C = typename cpx<T>::type;
+  constexpr bool kFhatRows = OSTEP != 2 && ISTEP != 2;  // the right-hand side reads f_hat
   if (skip && *skip) return;
   const Plane3DArgs& a = ia.a;
   extern __shared__ __align__(16) unsigned char smem_raw[];
