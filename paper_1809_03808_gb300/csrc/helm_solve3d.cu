@@ -806,9 +806,43 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
     const C cinf = cmul(b, iinf);
     const int L = sL[mi];  // 0 for a routed line
     const C* tcol = tab + l * nz + (m < nz ? m : 0);
-    auto pivot = [&](int j) -> C {
-      if (j >= L) return j == nx - 1 ? ilast : iinf;
-      return j < kPivRows ? piv[j * kMW + mi] : tcol[(int64_t)j * xs];
+    // The rows of a chunk that is not settled, in three runs: rows [s0, jt)
+    // below the settling row take 1/u_j from the pivot table (four loads in
+    // flight at a time), rows [jt, jc) take 1/u_inf, and the corner row nx - 1
+    // (if the chunk holds it) 1/u_{nx-1}.  fn(j, 1/u_j, g_j) with
+    // g_j = -b / u_j, the weight of the previous row's value in
+    // d_j = r_j / u_j + g_j d_{j-1} and of the next row's in x_j = d_j + g_j x_{j+1}.
+    const int jt = min(e0 + 1, max(s0, L));
+    const int jc = e0 == nx - 1 ? e0 : e0 + 1;
+    const C q = cmul(nb, iinf), glast = cmul(nb, ilast);
+    auto tpiv = [&](int j) -> C { return j < kPivRows ? piv[j * kMW + mi] : tcol[(int64_t)j * xs]; };
+    auto rows_up = [&](auto&& fn) {
+#pragma unroll 1
+      for (int j0 = s0; j0 < jt; j0 += 4) {
+        C pv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pv[k] = j0 + k < jt ? tpiv(j0 + k) : iinf;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (j0 + k < jt) fn(j0 + k, pv[k], cmul(nb, pv[k]));
+      }
+#pragma unroll 4
+      for (int j = jt; j < jc; ++j) fn(j, iinf, q);
+      if (jc == e0) fn(e0, ilast, glast);
+    };
+    auto rows_down = [&](auto&& fn) {
+      if (jc == e0) fn(e0, ilast, glast);
+#pragma unroll 4
+      for (int j = jc - 1; j >= jt; --j) fn(j, iinf, q);
+#pragma unroll 1
+      for (int j0 = jt - 1; j0 >= s0; j0 -= 4) {
+        C pv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pv[k] = j0 - k >= s0 ? tpiv(j0 - k) : iinf;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (j0 - k >= s0) fn(j0 - k, pv[k], cmul(nb, pv[k]));
+      }
     };
     // ---- pass 1 ----
     // Forward with d_{s-1} = 0 (d_loc written over the rhs), then the
@@ -821,8 +855,7 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
     if (act) {
       C d = mk<C>(0, 0), al = mk<C>(1, 0), be = mk<C>(0, 0), x = mk<C>(0, 0);
       if (settled) {
-        // d_j = r_j / u_inf + q d_{j-1}, q = -b / u_inf (= apow[0])
-        const C q = apow[mi];
+        // d_j = r_j / u_inf + q d_{j-1}, q = -b / u_inf
 #pragma unroll 16
         for (int k = 0; k < CH; ++k) {
           d = cfma(q, d, cmul(trow[k * kMW], iinf));
@@ -833,17 +866,14 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
         al = lc[3 * kMW + 3 + mi];
         be = lc[4 * kMW + 3 + mi];
       } else {
-#pragma unroll 1
-        for (int j = s0; j <= e0; ++j) {
-          const C inv = pivot(j);
-          d = cmul(csub(tile[j * kMW + mi], cmul(b, d)), inv);
+        rows_up([&](int j, C inv, C g) {
+          d = cfma(g, d, cmul(tile[j * kMW + mi], inv));
           tile[j * kMW + mi] = d;
-          const C an = cmul(al, cmul(nb, inv));
-          be = cadd(be, cmul(al, an));
+          const C an = cmul(al, g);
+          be = cfma(al, an, be);
           al = an;
-        }
-#pragma unroll 1
-        for (int j = e0; j >= s0; --j) x = csub(tile[j * kMW + mi], cmul(cmul(b, pivot(j)), x));
+        });
+        rows_down([&](int j, C, C g) { x = cfma(g, x, tile[j * kMW + mi]); });
       }
       sums[(0 * kMW + mi) * ncp + c] = d;
       sums[(1 * kMW + mi) * ncp + c] = x;
@@ -922,17 +952,15 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
         }
       } else {
         C al = mk<C>(1, 0);
-#pragma unroll 1
-        for (int j = s0; j <= e0; ++j) {
-          al = cmul(al, cmul(nb, pivot(j)));
-          tile[j * kMW + mi] = cadd(tile[j * kMW + mi], cmul(al, Din));
-        }
-#pragma unroll 1
-        for (int j = e0; j >= s0; --j) {
-          x = csub(tile[j * kMW + mi], cmul(cmul(b, pivot(j)), x));
+        rows_up([&](int j, C, C g) {
+          al = cmul(al, g);
+          tile[j * kMW + mi] = cfma(al, Din, tile[j * kMW + mi]);
+        });
+        rows_down([&](int j, C, C g) {
+          x = cfma(g, x, tile[j * kMW + mi]);
           if (ISTEP == 3) yrow[(int64_t)(j - s0) * xs] = x;
           else tile[j * kMW + mi] = x;
-        }
+        });
       }
     }
     if (ISTEP != 3) {
