@@ -582,10 +582,11 @@ struct InnerArgs {
 
 // Shared memory of k_inner3d: solved-row tile, pivot rows, chunk summaries
 // (padded), face accumulators, per-line and per-mode constants, powers of the
-// settled pivot ratio, settling rows.
-inline size_t inner_smem_bytes(int64_t nx, int nc, int ch, size_t cb) {
+// settled pivot ratio, the plane's inner C_bb faces (inner Steps 2 and 3),
+// settling rows.  istep 0: the largest of the three steps.
+inline size_t inner_smem_bytes(int64_t nx, int nc, int ch, size_t cb, int istep = 0) {
   return ((size_t)nx * kMW + (size_t)kPivRows * kMW + 4 * (size_t)kMW * (nc + 1) + 2 * (size_t)nx + 9 * kMW + 3 +
-          (size_t)ch * kMW) *
+          (size_t)ch * kMW + (istep != 1 ? 2 * (size_t)nx : 0)) *
              cb +
          2 * kMW * sizeof(int);
 }
@@ -657,8 +658,9 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
   C* mw = facc + 2 * nx;                     // [kMW] rhs scale, [kMW] weight of the last face, [2][kMW] face weights
   // [kMW] b, [kMW] 1/u_inf, [kMW] 1/u_{nx-1}; [3] outer-mode constants; [kMW] alpha, [kMW] beta of a settled chunk
   C* lc = mw + 4 * kMW;
-  C* apow = lc + 5 * kMW + 3;                         // [CH][kMW] q^(k+1), q = -b / u_inf
-  int* sL = reinterpret_cast<int*>(apow + CH * kMW);  // [kMW] settling rows
+  C* apow = lc + 5 * kMW + 3;  // [CH][kMW] q^(k+1), q = -b / u_inf
+  C* scin = apow + CH * kMW;   // [2][nx] inner C_bb faces of this plane (inner Steps 2, 3)
+  int* sL = reinterpret_cast<int*>(scin + (ISTEP != 1 ? 2 * nx : 0));  // [kMW] settling rows
   int* sR = sL + kMW;                                 // [kMW] 1: routed to FP64
   const int64_t l = blockIdx.y;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -676,8 +678,12 @@ __global__ void __launch_bounds__(inner_max_threads<T>()) k_inner3d(
     lc[3 * kMW + 1] = cmul(mk<C>(a.two[2 * l], -a.two[2 * l + 1]), mk<C>(a.eninv_o[0], a.eninv_o[1]));
     lc[3 * kMW + 2] = mk<C>(a.parAo[l], 0);
   }
-  const C* cin1 = cin ? cin + l * 2 * nx : nullptr;  // inner C_bb faces of this plane
-  const C* cinn = cin ? cin1 + nx : nullptr;
+  // the plane's inner C_bb faces into shared memory (they land with the
+  // first tile's copies)
+  if (ISTEP != 1)
+    for (int e = tid; e < 2 * nx; e += nthr) cp_async<sizeof(C)>(scin + e, cin + l * 2 * nx + e);
+  const C* cin1 = scin;
+  const C* cinn = scin + nx;
   if (ISTEP != 3)
     for (int e = tid; e < 2 * nx; e += nthr) facc[e] = mk<C>(0, 0);
   // the right-hand sides of this CTA's later tiles into L2 while the first
@@ -1207,7 +1213,6 @@ cudaError_t launch_inner_t(const Plan3D& p, const void* gfaces, const int* skip,
   InnerArgs ia{make_args(p), p.inner_ch, p.inner_nc, p.inner_nmb, p.inner_nparts};
   const int nx = (int)p.n[0];
   const int nthr = kMW * ((p.inner_nc + 1) & ~1);
-  const size_t smem = inner_smem_bytes(nx, p.inner_nc, p.inner_ch, sizeof(C));
   const dim3 grid((unsigned)p.inner_nparts, (unsigned)p.n[1]);
   const int oA = OSTEP == 2 ? 1 : 0;
   const C* fh = (const C*)p.fhat;
@@ -1223,6 +1228,7 @@ cudaError_t launch_inner_t(const Plan3D& p, const void* gfaces, const int* skip,
   auto sweep = [&](auto kern, int istep, int innerA) -> cudaError_t {
     const int t = 2 * oA + innerA;
     ProfScope ps(prof, names[OSTEP - 1][istep - 1], st);
+    const size_t smem = inner_smem_bytes(nx, p.inner_nc, p.inner_ch, sizeof(C), istep);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<grid, nthr, smem, st>>>(ia, fh, gf, cin, (const C*)p.tab[t], (const C*)p.lend[t], p.lenL[t], part,
                                    (C*)p.dbuf, skip);
