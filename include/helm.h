@@ -500,6 +500,12 @@ int helm_server_create(helm_server_t* out, int32_t nslots, size_t device_budget_
 int helm_server_submit(helm_server_t s, const helm_request* req, int64_t* ticket);
 int helm_server_wait(helm_server_t s, int64_t ticket, double timeout_s, helm_request_result* res);
 int helm_server_drain(helm_server_t s, double timeout_s);
+/* What failed for a request that finished with a status other than HELM_OK
+ * or HELM_ENOTCONV: the step (plan build, solve, completion, helm_get_info),
+ * its status and the plan's last error string; "" for a request that
+ * completed, is still pending or is unknown.  The string belongs to the
+ * server and stays valid until helm_server_destroy. */
+const char* helm_server_error(helm_server_t s, int64_t ticket);
 int helm_server_get_stats(helm_server_t s, helm_server_stats* st);
 int helm_server_destroy(helm_server_t s);
 

@@ -113,6 +113,7 @@ _SIGS = {
     "helm_server_submit": (_i32, [_vp, ctypes.POINTER(helm_request), ctypes.POINTER(_i64)]),
     "helm_server_wait": (_i32, [_vp, _i64, _dbl, ctypes.POINTER(helm_request_result)]),
     "helm_server_drain": (_i32, [_vp, _dbl]),
+    "helm_server_error": (ctypes.c_char_p, [_vp, _i64]),
     "helm_server_get_stats": (_i32, [_vp, ctypes.POINTER(helm_server_stats)]),
     "helm_server_destroy": (_i32, [_vp]),
     "helm_mlp_create": (_i32, [ctypes.POINTER(_vp), _i32, _i32, ctypes.c_uint64]),
@@ -480,6 +481,10 @@ class Server:
         if res.done:
             self._keep.pop(int(ticket), None)
         return res
+
+    def error(self, ticket):
+        """What failed for a request that did not complete ("" otherwise)."""
+        return lib.helm_server_error(self.handle, int(ticket)).decode()
 
     def drain(self, timeout_s=-1.0):
         st = lib.helm_server_drain(self.handle, float(timeout_s))

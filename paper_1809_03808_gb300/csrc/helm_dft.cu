@@ -441,12 +441,12 @@ cudaError_t launch_dft_rows(int prec, const void* in, int in_is_double, void* ou
     const size_t smem = (size_t)2 * p.bm * es;
     if (prec == kPrecF64) {
       auto k = k_dft_rows_bs<double>;
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      allow_dynamic_smem((const void*)k, smem);
       k<<<(unsigned)nrows, 256, smem, st>>>(in, in_is_double, out, out_mode, nrows, p, sign, scale, accum_scale,
                                             (const double2*)sc_in, (const double2*)sc_out, skip);
     } else {
       auto k = k_dft_rows_bs<float>;
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      allow_dynamic_smem((const void*)k, smem);
       k<<<(unsigned)nrows, 256, smem, st>>>(in, in_is_double, out, out_mode, nrows, p, sign, (float)scale,
                                             accum_scale, (const float2*)sc_in, (const float2*)sc_out, skip);
     }
@@ -465,13 +465,13 @@ cudaError_t launch_dft_rows(int prec, const void* in, int in_is_double, void* ou
   if (grid == 0) return cudaSuccess;
   if (prec == kPrecF64) {
     auto k = k_dft_rows<double>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_dynamic_smem((const void*)k, smem);
     k<<<(unsigned)grid, 256, smem, st>>>(in, in_is_double, out, out_mode, nrows, L, p,
                                          reinterpret_cast<const double2*>(tw), sign, scale, accum_scale,
                                          (const double2*)sc_in, (const double2*)sc_out, skip);
   } else {
     auto k = k_dft_rows<float>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_dynamic_smem((const void*)k, smem);
     k<<<(unsigned)grid, 256, smem, st>>>(in, in_is_double, out, out_mode, nrows, L, p,
                                          reinterpret_cast<const float2*>(tw), sign, (float)scale, accum_scale,
                                          (const float2*)sc_in, (const float2*)sc_out, skip);
@@ -493,12 +493,12 @@ cudaError_t launch_dft_cols(int prec, const void* in, int in_is_double, void* ou
     if (grid == 0) return cudaSuccess;
     if (prec == kPrecF64) {
       auto k = k_dft_cols_bs<double>;
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      allow_dynamic_smem((const void*)k, smem);
       k<<<(unsigned)grid, 256, smem, st>>>(in, in_is_double, out, out_mode, outer, inner, TC, p, sign, scale,
                                            accum_scale, (const double2*)sc_in, (const double2*)sc_out, skip);
     } else {
       auto k = k_dft_cols_bs<float>;
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      allow_dynamic_smem((const void*)k, smem);
       k<<<(unsigned)grid, 256, smem, st>>>(in, in_is_double, out, out_mode, outer, inner, TC, p, sign,
                                            (float)scale, accum_scale, (const float2*)sc_in, (const float2*)sc_out,
                                            skip);
@@ -518,13 +518,13 @@ cudaError_t launch_dft_cols(int prec, const void* in, int in_is_double, void* ou
   if (grid == 0) return cudaSuccess;
   if (prec == kPrecF64) {
     auto k = k_dft_cols<double>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_dynamic_smem((const void*)k, smem);
     k<<<(unsigned)grid, 256, smem, st>>>(in, in_is_double, out, out_mode, outer, inner, TC, p,
                                          reinterpret_cast<const double2*>(tw), sign, scale, accum_scale,
                                          (const double2*)sc_in, (const double2*)sc_out, skip);
   } else {
     auto k = k_dft_cols<float>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_dynamic_smem((const void*)k, smem);
     k<<<(unsigned)grid, 256, smem, st>>>(in, in_is_double, out, out_mode, outer, inner, TC, p,
                                          reinterpret_cast<const float2*>(tw), sign, (float)scale, accum_scale,
                                          (const float2*)sc_in, (const float2*)sc_out, skip);

@@ -453,7 +453,7 @@ cudaError_t launch_cols_pow2_t(const void* in, int in_is_double, void* out, int 
   if (grid == 0) return cudaSuccess;
   auto k = k_dft_cols_pow2<T, LOG2N, SIGN>;
   if (smem > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = allow_dynamic_smem((const void*)k, smem);
     if (e != cudaSuccess) return e;
   }
   k<<<(unsigned)grid, threads, smem, st>>>(in, in_is_double, out, out_mode, outer, inner, (const C*)tw, (T)scale,
@@ -581,7 +581,7 @@ cudaError_t launch_pow2_bulk(const void* in, void* out, int out_mode, int64_t nr
   constexpr int N = 1 << LOG2N;
   const size_t smem = (size_t)(2 * N + N + N / 16) * sizeof(float2);
   auto k = k_dft_rows_pow2_bulk<LOG2N, SIGN>;
-  const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const cudaError_t e = allow_dynamic_smem((const void*)k, smem);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -609,7 +609,7 @@ cudaError_t launch_pow2_t(const void* in, int in_is_double, void* out, int out_m
   if (grid == 0) return cudaSuccess;
   auto k = k_dft_rows_pow2<T, LOG2N, SIGN>;
   if (smem > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = allow_dynamic_smem((const void*)k, smem);
     if (e != cudaSuccess) return e;
   }
   k<<<(unsigned)grid, threads, smem, st>>>(in, in_is_double, out, out_mode, nrows, (const C*)tw, (T)scale,

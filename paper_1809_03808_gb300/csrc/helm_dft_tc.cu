@@ -308,7 +308,7 @@ cudaError_t launch_dft_rows_tc(const float* table, int64_t n, const void* in, in
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   const size_t per_sm = 512 / tcols;  // CTAs whose accumulators fit at once
   smem = std::max(smem, (size_t)smem_sm / (per_sm + 1) + 1024);
-  cudaError_t e = cudaFuncSetAttribute(k_dft_rows_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_dynamic_smem((const void*)k_dft_rows_tc, smem);
   if (e != cudaSuccess) return e;
   const int64_t grid = (nrows + kTcM - 1) / kTcM;
   k_dft_rows_tc<<<(unsigned)grid, kTcM, smem, st>>>(table, (int)n, np, kp / kTcKc, tcols, in, in_is_double, out,

@@ -16,6 +16,11 @@ constexpr int kMaxStages = 24;
 // allocates and frees device memory only through these.
 cudaError_t dmalloc(void** ptr, size_t bytes);
 void dfree(void* ptr);
+// Lets `func` launch with up to `bytes` of dynamic shared memory on the
+// current device.  The attribute is process-wide, so it is only ever raised
+// (under a lock): threads that launch the same kernel with different sizes
+// (a plan build beside a served solve) cannot lower it under one another.
+cudaError_t allow_dynamic_smem(const void* func, size_t bytes);
 
 // Mixed-radix factorisation of a DFT length: 8, 4, 2 first, then odd primes.
 struct DftPlan {

@@ -943,8 +943,7 @@ cudaError_t launch_residual(int dim, const int64_t* n, const double* h, double o
       const dim3 grid((unsigned)((n[2] + QZ - 1) / QZ), (unsigned)((n[1] + QY - 1) / QY), (unsigned)((n[0] + QX - 1) / QX));
       *nblocks = (int64_t)grid.x * grid.y * grid.z;
       CUtensorMap um, fm;
-      static const cudaError_t attr = cudaFuncSetAttribute(k_residual3d_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                           (int)kResidTmaSmem);
+      const cudaError_t attr = allow_dynamic_smem((const void*)k_residual3d_tma, kResidTmaSmem);
       if (attr == cudaSuccess && residual_map(&um, u, n, QZ + 2, QY + 2) && residual_map(&fm, f, n, QZ, QY))
         k_residual3d_tma<<<grid, dim3(QZ, QY), kResidTmaSmem, st>>>(um, fm, q, r, sums, skip, err);
       else

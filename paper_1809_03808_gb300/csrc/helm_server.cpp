@@ -20,6 +20,7 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -96,6 +97,7 @@ struct Request {
   bool fresh = false;  // its plan was built for it (not a reuse)
   int iterations = 0, converged = 1;
   double residual = 0.0;
+  std::string error;  // what failed, for a request that did not complete
 };
 
 struct Slot {
@@ -167,7 +169,7 @@ struct helm_server {
   bool builds_pending() const { return builds_in_flight > 0 || !build_queue.empty(); }
   bool start_one(std::unique_lock<std::mutex>& lk);
   void finish(Slot& sl, cudaError_t q);
-  void fail(Request* r, int status);
+  void fail(Request* r, int status, const std::string& why);
   bool running() const {
     for (const Slot& s : slots)
       if (s.req) return true;
@@ -191,8 +193,9 @@ int configure(helm_plan_t p, const helm_request& r) {
 
 }  // namespace
 
-void helm_server::fail(Request* r, int status) {
+void helm_server::fail(Request* r, int status, const std::string& why) {
   r->status = status;
+  r->error = why;
   r->done = true;
   r->t_done = Clock::now();
   ++failed;
@@ -201,7 +204,10 @@ void helm_server::fail(Request* r, int status) {
 
 void helm_server::finish(Slot& sl, cudaError_t q) {
   Request* r = sl.req;
-  if (q != cudaSuccess && r->status == HELM_OK) r->status = HELM_ECUDA;
+  if (q != cudaSuccess && r->status == HELM_OK) {
+    r->status = HELM_ECUDA;
+    r->error = std::string("completion event: ") + cudaGetErrorString(q);
+  }
   if (r->status == HELM_OK) {
     helm_info info;
     int rc = helm_get_info(sl.plan->plan, &info);  // the slot's work is complete
@@ -214,6 +220,7 @@ void helm_server::finish(Slot& sl, cudaError_t q) {
     }
     if (!filled) {
       r->status = rc;
+      r->error = std::string("helm_get_info: ") + helm_status_string(rc) + ": " + helm_last_error(sl.plan->plan);
     } else if (r->spec.dtype == HELM_C64_REFINED) {
       r->iterations = info.iterations;
       r->converged = info.converged;
@@ -268,7 +275,7 @@ bool helm_server::start_one(std::unique_lock<std::mutex>& lk) {
       const size_t est = plan_bytes_estimate(r->spec);
       if (est > budget) {
         pending.erase(pending.begin() + (std::ptrdiff_t)qi);
-        fail(r, HELM_ENOMEM);
+        fail(r, HELM_ENOMEM, "the plan's estimate exceeds the device budget");
         return true;
       }
       // evict idle plans, least recently used first, until the estimate fits
@@ -289,7 +296,7 @@ bool helm_server::start_one(std::unique_lock<std::mutex>& lk) {
       if (in_use + est > budget) {
         if (!running() && !builds_pending()) {  // nothing will free memory: it can never fit
           pending.erase(pending.begin() + (std::ptrdiff_t)qi);
-          fail(r, HELM_ENOMEM);
+          fail(r, HELM_ENOMEM, "the plan does not fit the device budget beside the cached plans");
           return true;
         }
         memory_blocked = true;
@@ -320,7 +327,10 @@ bool helm_server::start_one(std::unique_lock<std::mutex>& lk) {
     (void)stride;
     // the request's right-hand sides, several at once on the plan's workspaces
     if (!rc) rc = helm_solve_many(pe->plan, r->spec.nrhs, r->spec.f, r->spec.u);
-    if (rc) r->status = rc;
+    if (rc) {
+      r->status = rc;
+      r->error = std::string("solve: ") + helm_status_string(rc) + ": " + helm_last_error(pe->plan);
+    }
     cudaEventRecord(slot->done, slot->stream);
     slot->req = r;
     slot->plan = pe;
@@ -379,6 +389,11 @@ void helm_server::build_loop() {
       rc = helm_get_info(plan, &info);
       if (rc == HELM_ENOTCONV) rc = HELM_OK;  // the state of the plan's trial solves: info is filled
     }
+    std::string why;
+    if (rc) {
+      why = std::string("plan build: ") + helm_status_string(rc);
+      if (plan) why += std::string(": ") + helm_last_error(plan);
+    }
     if (rc && plan) {
       helm_destroy(plan);
       plan = nullptr;
@@ -393,7 +408,7 @@ void helm_server::build_loop() {
         break;
       }
     if (rc) {
-      fail(r, rc);
+      fail(r, rc, why);
     } else {
       auto e = std::make_unique<PlanEntry>();
       e->key = key;
@@ -511,6 +526,13 @@ int helm_server_wait(helm_server_t s, int64_t ticket, double timeout_s, helm_req
     if (r->done) res->latency_s = seconds_between(r->t_submit, r->t_done);
   }
   return done ? HELM_OK : HELM_ETIMEOUT;
+}
+
+const char* helm_server_error(helm_server_t s, int64_t ticket) {
+  if (!s) return "";
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->requests.find(ticket);
+  return it == s->requests.end() ? "" : it->second->error.c_str();
 }
 
 int helm_server_drain(helm_server_t s, double timeout_s) {

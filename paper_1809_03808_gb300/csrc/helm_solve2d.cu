@@ -1308,8 +1308,8 @@ cudaError_t launch_tri2d_t32(int step, const void* fhat, const void* faces, cons
       auto k1 = k_tri_bulk_t32<1, S, kChunkF32>;                                                              \
       auto k2 = k_tri_bulk_t32<2, S, kChunkF32>;                                                              \
       const size_t sb1 = bulk_tile_bytes<1, S, kChunkF32>(), sb2 = bulk_tile_bytes<2, S, kChunkF32>();        \
-      cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb1);                       \
-      cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb2);                       \
+      allow_dynamic_smem((const void*)k1, sb1);                                                               \
+      allow_dynamic_smem((const void*)k2, sb2);                                                               \
       {                                                                                                       \
         ProfScope ps(prof, n1s[S - 1], st);                                                                   \
         k1<<<gbulk, kBulkLines, sb1, st>>>((const float2*)fhat, (const float2*)faces, tb, r, nullptr, nullptr, \

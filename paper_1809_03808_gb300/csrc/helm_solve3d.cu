@@ -1194,7 +1194,7 @@ cudaError_t launch_plane(int ostep, const Plan3D& p, const void* gfaces, const i
   const C* tB = (const C*)p.tab[2 * oA + 0];
   const C* tA = (const C*)p.tab[2 * oA + 1];
   auto run = [&](auto kern) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_dynamic_smem((const void*)kern, smem);
     kern<<<(unsigned)p.n[1], bs, smem, st>>>((const C*)p.fhat, (C*)p.cbuf, (C*)p.dbuf, (const C*)gfaces, tB, tA, a,
                                              skip);
   };
@@ -1229,7 +1229,7 @@ cudaError_t launch_inner_t(const Plan3D& p, const void* gfaces, const int* skip,
     const int t = 2 * oA + innerA;
     ProfScope ps(prof, names[OSTEP - 1][istep - 1], st);
     const size_t smem = inner_smem_bytes(nx, p.inner_nc, p.inner_ch, sizeof(C), istep);
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_dynamic_smem((const void*)kern, smem);
     kern<<<grid, nthr, smem, st>>>(ia, fh, gf, cin, (const C*)p.tab[t], (const C*)p.lend[t], p.lenL[t], part,
                                    (C*)p.dbuf, skip);
     return cudaGetLastError();
@@ -1246,7 +1246,7 @@ cudaError_t launch_inner_t(const Plan3D& p, const void* gfaces, const int* skip,
   auto reduce = [&](auto kern, int innerA) -> cudaError_t {
     const int t = 2 * oA + innerA;
     ProfScope ps(prof, "inner_reduce", st);
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    allow_dynamic_smem((const void*)kern, rsm);
     kern<<<(unsigned)p.n[1], 256, rsm, st>>>(ia, part, vw, cin, p.nroute[t] ? p.roff[t] : nullptr, (const C*)p.rpart,
                                              skip);
     return cudaGetLastError();

@@ -118,6 +118,7 @@ def test_server_rejects_bad_arguments_before_touching_the_device(helm):
     assert helm.lib.helm_server_submit(None, ctypes.byref(req), ctypes.byref(t)) == helm.HELM_EINVAL
     assert helm.lib.helm_server_wait(None, 1, 0.0, None) == helm.HELM_EINVAL
     assert helm.lib.helm_server_drain(None, 0.0) == helm.HELM_EINVAL
+    assert helm.lib.helm_server_error(None, 1) == b""
     st = helm.helm_server_stats()
     assert helm.lib.helm_server_get_stats(None, ctypes.byref(st)) == helm.HELM_EINVAL
     assert helm.lib.helm_server_destroy(None) == helm.HELM_OK

@@ -93,7 +93,8 @@ def test_server_mix_equals_alone(env):
         results = [srv.wait(t, 120.0) for t in tickets]
         torch.cuda.synchronize()
         for i, ((shape, h, omega, mode, f, ua), u, res) in enumerate(zip(cases, us, results)):
-            assert res.done == 1 and res.status == helm.HELM_OK, (i, res.status)
+            assert res.done == 1 and res.status == helm.HELM_OK, (i, res.status, srv.error(tickets[i]))
+            assert srv.error(tickets[i]) == ""
             if mode != "c128":
                 assert res.converged == 1 and res.residual <= MODES[mode]["tol"]
             assert torch.equal(u, ua), f"request {i} ({shape}, {mode}) differs from its solve alone"
@@ -138,7 +139,7 @@ def test_server_evicts_under_budget(env):
         srv.drain(120.0)
         for k, f, u, t in jobs:
             res = srv.wait(t, 0.0)
-            assert res.done == 1 and res.status == helm.HELM_OK
+            assert res.done == 1 and res.status == helm.HELM_OK, (res.status, srv.error(t))
             shape, h, omega = ops[k]
             assert torch.equal(u, _alone(helm, torch, shape, h, omega, "c64_ff", f))
         st = srv.stats()
@@ -149,8 +150,10 @@ def test_server_evicts_under_budget(env):
         f = _inputs(torch, shape, 1, 1)
         u = torch.empty_like(f)
         torch.cuda.synchronize()
-        res = srv.wait(_submit(srv, shape, h, omega, "c64_ff", f, u), 60.0)
+        t = _submit(srv, shape, h, omega, "c64_ff", f, u)
+        res = srv.wait(t, 60.0)
         assert res.done == 1 and res.status == helm.HELM_ENOMEM
+        assert "budget" in srv.error(t)
     finally:
         srv.close()
 
@@ -178,7 +181,7 @@ def test_server_builds_plans_off_the_scheduler(env):
         rs = srv.wait(ts, 60.0)
         rb = srv.wait(tb, 120.0)
         torch.cuda.synchronize()
-        assert rs.status == helm.HELM_OK and rb.status == helm.HELM_OK
+        assert rs.status == helm.HELM_OK and rb.status == helm.HELM_OK, (srv.error(ts), srv.error(tb))
         assert rs.plan_reused == 1 and rb.plan_reused == 0
         print(f"SERVER small request latency {rs.latency_s * 1e3:.2f} ms, large request's wait for its plan "
               f"{rb.queue_s * 1e3:.2f} ms")
