@@ -307,8 +307,14 @@ int helm_set_rhs_concurrency(helm_plan_t p, int k);  /* 1 <= k <= 16 */
  * by the plan until helm_destroy.  For
  * HELM_C64_REFINED with HELM_RESID_FF and both buffers page-locked and
  * mapped, no copies are made: the kernels that convert f to float-float and
- * u back read and write the host buffers directly (same results).  f and u
- * must not share a byte (HELM_EINVAL). */
+ * u back read and write the host buffers directly (same results).  For
+ * HELM_C64_REFINED with HELM_RESID_FP64 the refinement runs sweep by sweep,
+ * the call reading each convergence test's state before it enqueues the
+ * next correction, and the copy of u back starts beside the test that the
+ * last two residuals predict to converge (on a second stream of the plan,
+ * made at the first call): the same kernels in the same order as the
+ * kernel-by-kernel loop, so the same bits as helm_solve.  f and u must not
+ * share a byte (HELM_EINVAL). */
 int helm_solve_host(helm_plan_t p, const void* f_host, void* u_host);
 
 /* Step-by-step variant for verification: runs the same kernels as helm_solve

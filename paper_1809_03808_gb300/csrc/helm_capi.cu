@@ -56,6 +56,8 @@ struct helm_plan {
   RefineState* state = nullptr;
   double2* host_f = nullptr;  // staging for helm_solve_host (allocated on first use)
   double2* host_u = nullptr;
+  cudaStream_t out_stream = nullptr;  // helm_solve_host: the early copy of u to the host
+  cudaEvent_t out_ready = nullptr, out_done = nullptr;
   size_t bytes = 0;
   double plan_seconds = 0;
   double tol = 1e-14;
@@ -788,6 +790,9 @@ void destroy_plan(helm_plan* p) {
   dfree(p->state);
   dfree(p->host_f);
   dfree(p->host_u);
+  if (p->out_stream) cudaStreamDestroy(p->out_stream);
+  if (p->out_ready) cudaEventDestroy(p->out_ready);
+  if (p->out_done) cudaEventDestroy(p->out_done);
   free_plan3d(p->p3);
   drop_refine_graph(p);
   for (int k = 0; k < 2; ++k)
@@ -1581,8 +1586,60 @@ void* mapped_host(const void* h) {
 
 }  // namespace
 
+namespace {
+
+// helm_solve_host with the FP64 residual, f already in p->host_f: the
+// refinement runs sweep by sweep, the host reading each test's state (a few
+// bytes) before it enqueues the next correction.  When the last two
+// residuals predict that the next test converges, the copy of u to the host
+// starts beside that test (both only read u) on a second stream; if the test
+// does not converge after all, the next correction waits for the copy, and u
+// is copied again at the end.  The kernels and their order are those of the
+// kernel-by-kernel refinement loop, so u is the same bit for bit.
+int solve_host_refined(helm_plan* p, void* u_host, size_t bytes) {
+  if (!p->out_stream) {
+    HELM_CK(cudaStreamCreateWithFlags(&p->out_stream, cudaStreamNonBlocking));
+    HELM_CK(cudaEventCreateWithFlags(&p->out_ready, cudaEventDisableTiming));
+    HELM_CK(cudaEventCreateWithFlags(&p->out_done, cudaEventDisableTiming));
+  }
+  RefineState init{};
+  init.tol = p->tol;
+  init.max_iter = p->max_iter;
+  HELM_CK(cudaMemcpyAsync(p->state, &init, sizeof(init), cudaMemcpyHostToDevice, p->stream));
+  int rc;
+  if ((rc = refine_first(p, p->host_f, p->host_u, nullptr, nullptr, nullptr))) return rc;
+  bool copying = false;  // a copy of the current u to u_host is on out_stream
+  for (int it = 0; it <= p->max_iter; ++it) {
+    if ((rc = refine_check(p, p->host_f, p->host_u, 0))) return rc;
+    RefineState st{};
+    HELM_CK(cudaMemcpyAsync(&st, p->state, sizeof(st), cudaMemcpyDeviceToHost, p->stream));
+    HELM_CK(cudaStreamSynchronize(p->stream));
+    if (st.done || it == p->max_iter) break;
+    if (copying) {  // the prediction missed: no correction changes u under the copy
+      HELM_CK(cudaStreamWaitEvent(p->stream, p->out_done, 0));
+      copying = false;
+    }
+    if ((rc = refine_correct(p, p->host_u))) return rc;
+    const int k = std::min(st.iters, 16) - 1;  // resid[k]: the last test's ||r|| / ||f||
+    if (k >= 1 && st.resid[k - 1] > 0 && st.resid[k] * (st.resid[k] / st.resid[k - 1]) <= st.tol) {
+      HELM_CK(cudaEventRecord(p->out_ready, p->stream));
+      HELM_CK(cudaStreamWaitEvent(p->out_stream, p->out_ready, 0));
+      HELM_CK(cudaMemcpyAsync(u_host, p->host_u, bytes, cudaMemcpyDeviceToHost, p->out_stream));
+      HELM_CK(cudaEventRecord(p->out_done, p->out_stream));
+      copying = true;
+    }
+  }
+  if (!copying) HELM_CK(cudaMemcpyAsync(u_host, p->host_u, bytes, cudaMemcpyDeviceToHost, p->stream));
+  HELM_CK(cudaStreamSynchronize(p->stream));
+  HELM_CK(cudaStreamSynchronize(p->out_stream));
+  return HELM_OK;
+}
+
+}  // namespace
+
 int helm_solve_host(helm_plan_t p, const void* f_host, void* u_host) {
   if (!p || !f_host || !u_host || bad_pair(f_host, u_host, plan_vec_bytes(p), plan_elem_bytes(p))) return HELM_EINVAL;
+  p->last_many = 0;
   const int64_t N = p->n[0] * p->n[1] * p->n[2];
   const size_t eb = p->dtype == HELM_C64_RAW ? sizeof(float2) : sizeof(double2);
   int rc;
@@ -1602,6 +1659,7 @@ int helm_solve_host(helm_plan_t p, const void* f_host, void* u_host) {
     if ((rc = dev_alloc(p, (void**)&p->host_f, N * eb)) || (rc = dev_alloc(p, (void**)&p->host_u, N * eb))) return rc;
   }
   HELM_CK(cudaMemcpyAsync(p->host_f, f_host, N * eb, cudaMemcpyHostToDevice, p->stream));
+  if (p->dtype == HELM_C64_REFINED && !refine_ff(p)) return solve_host_refined(p, u_host, N * eb);
   rc = run_solve(p, p->host_f, p->host_u, nullptr, nullptr, nullptr);
   if (rc) return rc;
   HELM_CK(cudaMemcpyAsync(u_host, p->host_u, N * eb, cudaMemcpyDeviceToHost, p->stream));

@@ -159,6 +159,35 @@ def test_repeated_solves_and_host_api(env):
     assert np.array_equal(uh, u1.cpu().numpy())
 
 
+@pytest.mark.parametrize("shape,lengths", [((65, 100), (0.64, 1.0)), ((20, 24, 18), (0.8, 1.0, 0.7))])
+@pytest.mark.parametrize("tol", [1e-8, 2e-11, 1e-12, 3e-13])
+def test_host_api_fp64_sweep_by_sweep(env, shape, lengths, tol):
+    """helm_solve_host with the FP64 residual runs the refinement sweep by
+    sweep and starts the copy of u to the host beside the test that the last
+    two residuals predict to converge.  Over tolerances where that copy is
+    taken early, where the prediction misses and where one sweep or none is
+    needed, the host result (page-locked buffers) equals the device-buffer
+    solve bit for bit with the same sweeps and residual history."""
+    helm, torch = env
+    h = tuple(L / (n - 1) for n, L in zip(shape, lengths))
+    omega = ppw_omega(max(h), 8)
+    f = random_rhs(shape, 19)
+    plan = helm.Plan(shape, h, omega, helm.HELM_C64_REFINED)
+    helm.helm_set_refinement(plan.handle, tol, 12)
+    u1 = plan.solve(torch.from_numpy(f).cuda()).cpu().numpy()
+    i1, s1 = plan.info()
+    fh = torch.from_numpy(f).pin_memory()
+    uh = torch.full(f.shape, float("nan"), dtype=torch.complex128).pin_memory()
+    helm.helm_solve_host(plan.handle, fh, uh)
+    i2, s2 = plan.info()
+    plan.close()
+    print(f"HOST {shape} tol {tol:g}: sweeps {i2.iterations}, residuals {list(i2.residual[:i2.iterations + 1])}")
+    assert s1 == s2 == helm.HELM_OK
+    assert i1.iterations == i2.iterations
+    assert list(i1.residual[:i1.iterations + 1]) == list(i2.residual[:i2.iterations + 1])
+    assert np.array_equal(uh.numpy(), u1)
+
+
 def test_host_api_float_float_mapped_and_pageable(env):
     """helm_solve_host with the float-float residual: page-locked host buffers
     (split and join work on them directly) and pageable ones (staged copies)
