@@ -1602,37 +1602,48 @@ int solve_host_refined(helm_plan* p, void* u_host, size_t bytes) {
     HELM_CK(cudaEventCreateWithFlags(&p->out_ready, cudaEventDisableTiming));
     HELM_CK(cudaEventCreateWithFlags(&p->out_done, cudaEventDisableTiming));
   }
+  bool copying = false;  // a copy of the current u to u_host is on out_stream
+  // every return waits for that copy: the caller may reuse u_host at once
+  auto fail = [&](int rc) {
+    if (copying) cudaStreamSynchronize(p->out_stream);
+    return rc;
+  };
+  auto ck = [&](cudaError_t e, const char* what) { return e == cudaSuccess ? HELM_OK : fail(cuda_fail(p, e, what)); };
+  int rc;
   RefineState init{};
   init.tol = p->tol;
   init.max_iter = p->max_iter;
-  HELM_CK(cudaMemcpyAsync(p->state, &init, sizeof(init), cudaMemcpyHostToDevice, p->stream));
-  int rc;
+  if ((rc = ck(cudaMemcpyAsync(p->state, &init, sizeof(init), cudaMemcpyHostToDevice, p->stream), "refinement state")))
+    return rc;
   if ((rc = refine_first(p, p->host_f, p->host_u, nullptr, nullptr, nullptr))) return rc;
-  bool copying = false;  // a copy of the current u to u_host is on out_stream
   for (int it = 0; it <= p->max_iter; ++it) {
-    if ((rc = refine_check(p, p->host_f, p->host_u, 0))) return rc;
+    if ((rc = refine_check(p, p->host_f, p->host_u, 0))) return fail(rc);
     RefineState st{};
-    HELM_CK(cudaMemcpyAsync(&st, p->state, sizeof(st), cudaMemcpyDeviceToHost, p->stream));
-    HELM_CK(cudaStreamSynchronize(p->stream));
+    if ((rc = ck(cudaMemcpyAsync(&st, p->state, sizeof(st), cudaMemcpyDeviceToHost, p->stream), "refinement state")) ||
+        (rc = ck(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize")))
+      return rc;
     if (st.done || it == p->max_iter) break;
     if (copying) {  // the prediction missed: no correction changes u under the copy
-      HELM_CK(cudaStreamWaitEvent(p->stream, p->out_done, 0));
+      if ((rc = ck(cudaStreamWaitEvent(p->stream, p->out_done, 0), "cudaStreamWaitEvent"))) return rc;
       copying = false;
     }
-    if ((rc = refine_correct(p, p->host_u))) return rc;
+    if ((rc = refine_correct(p, p->host_u))) return fail(rc);
     const int k = std::min(st.iters, 16) - 1;  // resid[k]: the last test's ||r|| / ||f||
     if (k >= 1 && st.resid[k - 1] > 0 && st.resid[k] * (st.resid[k] / st.resid[k - 1]) <= st.tol) {
-      HELM_CK(cudaEventRecord(p->out_ready, p->stream));
-      HELM_CK(cudaStreamWaitEvent(p->out_stream, p->out_ready, 0));
-      HELM_CK(cudaMemcpyAsync(u_host, p->host_u, bytes, cudaMemcpyDeviceToHost, p->out_stream));
-      HELM_CK(cudaEventRecord(p->out_done, p->out_stream));
+      if ((rc = ck(cudaEventRecord(p->out_ready, p->stream), "cudaEventRecord")) ||
+          (rc = ck(cudaStreamWaitEvent(p->out_stream, p->out_ready, 0), "cudaStreamWaitEvent")))
+        return rc;
       copying = true;
+      if ((rc = ck(cudaMemcpyAsync(u_host, p->host_u, bytes, cudaMemcpyDeviceToHost, p->out_stream), "copy of u")) ||
+          (rc = ck(cudaEventRecord(p->out_done, p->out_stream), "cudaEventRecord")))
+        return rc;
     }
   }
-  if (!copying) HELM_CK(cudaMemcpyAsync(u_host, p->host_u, bytes, cudaMemcpyDeviceToHost, p->stream));
-  HELM_CK(cudaStreamSynchronize(p->stream));
-  HELM_CK(cudaStreamSynchronize(p->out_stream));
-  return HELM_OK;
+  if (!copying && (rc = ck(cudaMemcpyAsync(u_host, p->host_u, bytes, cudaMemcpyDeviceToHost, p->stream), "copy of u")))
+    return rc;
+  if ((rc = ck(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize"))) return rc;
+  copying = false;
+  return ck(cudaStreamSynchronize(p->out_stream), "copy of u");
 }
 
 }  // namespace
